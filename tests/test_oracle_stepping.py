@@ -1,0 +1,115 @@
+"""Pins of the oracle's step solve and sequential stepping (Eq. (2.4), Eqs. (3.5)-(3.7))."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import sfde
+from sfde_workloads import (manufactured_exact, manufactured_forcing, manufactured_initial,
+                            gaussian_bump_forcing, time_grid, sine_mode_amplitudes, sine_mode_nodal)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")
+
+
+def _prob(nx=5, ny=7, nt=8, grid="uniform", beta=0.6, gamma=0.9, kx=1.3, ky=0.4, omega=(0, 1, 0, 2)):
+    return sfde.SFDE(beta, gamma, kx, ky, nx, ny, time_grid(nt, 1.0, grid), omega)
+
+
+def test_operator_equals_assembled_kronecker():
+    P = _prob()
+    U = np.random.default_rng(1).standard_normal((P.ny, P.nx))
+    for tau in (0.0, 0.013, 2.5):
+        np.testing.assert_allclose(P.apply_S(U, tau).reshape(-1), P.kron_S(tau) @ U.reshape(-1),
+                                   rtol=1e-13, atol=1e-13)
+    # the assembled operator is symmetric positive definite (Lemma 3.2)
+    S = P.kron_S(0.3)
+    assert np.allclose(S, S.T)
+    np.linalg.cholesky(S)
+
+
+def test_fdm_step_equals_dense_solve():
+    P = _prob(grid="graded")
+    rng = np.random.default_rng(2)
+    U = rng.standard_normal((P.ny, P.nx))
+    F = rng.standard_normal((P.ny, P.nx))
+    for n in (1, 4, 8):
+        a = P.step(U, n, F, dense=True)
+        b = P.step(U, n, F, dense=False)
+        assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
+    for dt in (1e-3, 0.7):
+        for scheme in ("cn", "be"):
+            a = P.propagate(U, dt, scheme, dense=True)
+            b = P.propagate(U, dt, scheme)
+            assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
+
+
+def test_generalised_eigenpairs():
+    P = _prob(nx=11, ny=9)
+    lx, Vx, ly, Vy = P.eig()
+    np.testing.assert_allclose(Vx.T @ P.Mx @ Vx, np.eye(11), atol=1e-12)
+    np.testing.assert_allclose(Vx.T @ P.Ax @ Vx, np.diag(lx), atol=1e-10 * lx.max())
+    assert lx.min() > 0 and ly.min() > 0  # Lemma 3.2: sigma real and positive
+
+
+def test_rho_one_eigenvalues_closed_form():
+    """For rho = 1, (A, M) = ((1/h) tridiag(-1,2,-1), (h/6) tridiag(1,4,1)) has the sine
+    eigenvalues lambda_k = (6/h^2)(1 - cos k pi h)/(2 + cos k pi h)."""
+    n = 15
+    h = 1.0 / (n + 1)
+    P = sfde.SFDE(1.0, 1.0, 1.0, 1.0, n, n, time_grid(2))
+    lx = P.eig()[0]
+    k = np.arange(1, n + 1)
+    ref = 6.0 / h ** 2 * (1 - np.cos(k * np.pi * h)) / (2 + np.cos(k * np.pi * h))
+    np.testing.assert_allclose(np.sort(lx), np.sort(ref), rtol=1e-12)
+
+
+def test_propagator_eigenvalues_eq_3_7():
+    """Psi x_w = lambda_w x_w with lambda_w = (2 - dt sigma_w)/(2 + dt sigma_w), |lambda| < 1."""
+    P = _prob(nx=6, ny=5)
+    lx, Vx, ly, Vy = P.eig()
+    dt = 0.37
+    for (j, i) in [(0, 0), (2, 3), (4, 5)]:
+        X = np.outer(Vy[:, j], Vx[:, i])
+        s = P.kx * lx[i] + P.ky * ly[j]
+        lam = (2 - dt * s) / (2 + dt * s)
+        assert abs(lam) < 1
+        np.testing.assert_allclose(P.propagate(X, dt, "cn", dense=True), lam * X, atol=1e-12)
+
+
+def test_spectral_recurrence_equals_stepping():
+    P = _prob(nx=6, ny=8, nt=12, grid="graded", omega=(0, 1, 0, 1))
+    U0 = sine_mode_nodal(sine_mode_amplitudes(3), 6, 8)
+    F, _ = gaussian_bump_forcing(4, 6, 8, P.t)
+    seq = sfde.seq_timestep(P, U0, F, dense=True)
+    sp = sfde.spectral_sequential(P, U0, F)
+    for n in range(P.nt + 1):
+        assert np.abs(sp[n] - seq[n]).max() <= 1e-13 * np.abs(seq).max()
+
+
+def _example41_errors(beta, gamma, kx, ky, Ms):
+    errs = []
+    for M in Ms:
+        n = M - 1
+        t = time_grid(M, 1.0)
+        P = sfde.SFDE(beta, gamma, kx, ky, n, n, t)
+        U0 = manufactured_initial(n, n, "10exp(-t)")
+        F = manufactured_forcing(n, n, t, beta, gamma, kx, ky, "10exp(-t)")
+        UT = sfde.seq_timestep(P, U0, F, keep_all=False)
+        errs.append(sfde.l2_error_bilinear(UT, lambda X, Y: manufactured_exact(X, Y, 1.0, "10exp(-t)")))
+    return np.array(errs)
+
+
+@pytest.mark.parametrize("pair", ["beta0.6_gamma0.7", "beta0.95_gamma0.65", "beta0.8_gamma0.8"])
+def test_saturation_error_order_example_4_1(pair):
+    """Example 4.1, tau = h (Table 1 setting): O(h^2 + tau^2) error, rates near 2, and errors of
+    the printed magnitude (the printed values are for P1 triangles; this operator is the
+    tensor-product one, which differs from them by up to ~40% at these sizes)."""
+    tab = json.load(open(GOLDEN))["table1"]
+    b, g = (float(v) for v in pair.replace("beta", "").split("_gamma"))
+    errs = _example41_errors(b, g, 2.0, 0.5, tab["M"])
+    rates = np.log2(errs[:-1] / errs[1:])
+    assert np.all(rates > 1.75) and np.all(rates < 2.3), rates
+    ratio = errs / np.array(tab[pair])
+    assert np.all(ratio > 0.5) and np.all(ratio < 1.6), ratio
