@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Throughput of the MGRIT solve of the 2-D Riesz SFDE on GB300: space-time DOF-updates/s.
+
+One "step" is one complete MGRIT solve (all V-cycles to the stopping tolerance) of the
+workload ``sine_N255_Nt1024``: N_x = N_y = 255, N_t = 1024 uniform steps on (0,1]^3,
+beta = 0.6, gamma = 0.9, K_x = 1, K_y = 0.5, sixteen seeded sine modes for psi_0, f = 0,
+V-cycle with m = 8.  value = N_x N_y N_t / (device seconds per solve), summed over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision ...]
+
+--impl reference times the FP64 CPU oracle (the slow, plain implementation that the tests
+compare against) on the host cores; it never touches the GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from sfde_workloads import WORKLOADS  # noqa: E402
+
+METRIC = "space-time DOF-updates/s to 1e-8 rel. residual: mixed/batched vs FP64 MGRIT, 1 GB300"
+UNIT = "DOF-updates/s"
+WORKLOAD = "sine_N255_Nt1024"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Nominal GB300 rates (TFLOP/s): FP64 and BF16 dense; FP64 peak = measured BF16 x nominal ratio.
+NOMINAL_FP64_TFLOPS = 1.25
+NOMINAL_BF16_TFLOPS = 2250.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def peaks():
+    try:
+        p = json.load(open(PEAKS_FILE))
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("step_fp64.cu",):
+        h.update(open(os.path.join(ROOT, "paper_1805_06688_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(kernel: str, flops_per_launch: float):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))[kernel]
+    except Exception:
+        return None
+    if d.get("source_sha") != kernel_source_sha():
+        return None
+    return d["dram_bytes_per_flop"] * flops_per_launch
+
+
+# ----------------------------------------------------------------------------- oracle timing
+
+def oracle_rate(w, iters_needed: int, coarse: str, budget_s: float = 20.0):
+    """FP64 CPU oracle on a bounded sample: one V-cycle of the nodal Algorithm 1 (all levels),
+    extrapolated to the V-cycles the full solve needs.  Returns (rate, seconds, cores, sample)."""
+    from oracle import mgrit as omgrit, sfde as osfde
+    t = w.t()
+    prob = osfde.SFDE(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t)
+    prob.eig()
+    psi = w.initial()
+    t0 = time.perf_counter()
+    r = omgrit.mgrit(prob, psi, w.forcing(), m=w.m, max_levels=w.max_levels, coarse=coarse,
+                     rel_tol=0.0, max_iter=1)
+    dt = time.perf_counter() - t0
+    rate = w.space_time_updates / (dt * iters_needed)
+    sample = (f"one V-cycle ({r.step_solves} step solves, all {r.levels} levels) of the oracle's nodal "
+              f"FP64 MGRIT on {w.name}, extrapolated to the {iters_needed} V-cycles of the full solve")
+    return rate, dt, os.cpu_count(), sample
+
+
+def oracle_iterations(w, coarse: str) -> int:
+    from oracle import mgrit as omgrit, sfde as osfde
+    prob = osfde.SFDE(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, w.t())
+    r = omgrit.mgrit_modal(prob, w.initial(), w.forcing(), m=w.m, max_levels=w.max_levels,
+                           coarse=coarse, rel_tol=w.rel_tol, max_iter=400)
+    return r.iters
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    coarse = "be"  # the coarse propagator the solver picks for this workload (bound of Thm 3.1 > 1)
+    iters = oracle_iterations(w, coarse)
+    rates, secs = [], []
+    for k in range(args.warmup + args.steps):
+        rate, dt, cores, sample = oracle_rate(w, iters, coarse)
+        if k >= args.warmup:
+            rates.append(rate)
+            secs.append(dt * iters)
+    value = statistics.median(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nt": w.nt, "m": w.m,
+                   "rel_tol": w.rel_tol, "coarse": coarse, "solver": "FP64 CPU oracle, Algorithm 1"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_ours(args, w):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_1805_06688_gb300 as sfde
+    if not os.path.exists(sfde.library_path):
+        from paper_1805_06688_gb300.build import build
+        build()
+
+    stream = torch.cuda.current_stream(dev)
+    prec = {"fp64": sfde.PREC_FP64, "mixed-bf16": sfde.PREC_MIXED_BF16,
+            "mixed-tf32": sfde.PREC_MIXED_TF32}[args.precision]
+    t = w.t()
+    psi = w.initial()
+    P = sfde.Problem(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t, w.omega, precision=prec,
+                     stream=stream.cuda_stream)
+    P.set_initial(torch.from_numpy(psi).to(dev))
+    P.set_forcing(w.forcing())
+    tol = w.rel_tol if prec == sfde.PREC_FP64 else 1e-8
+    kw = dict(m=w.m, max_levels=w.max_levels, coarse=sfde.COARSE_AUTO, rel_tol=tol, max_iter=400)
+    UT = torch.zeros((w.ny, w.nx), dtype=torch.float64, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    stats = None
+    for _ in range(args.warmup):
+        _, stats = P.mgrit(U_T=UT, **kw)
+    # timed region: inputs (the 1025-slice FP64 space-time iterate, 537 MB) exceed L2
+    P.profile_enable(False)
+    barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, stats = P.mgrit(U_T=UT, **kw)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = P.profile_read().kernel_launches
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * w.space_time_updates / (ms * 1e-3)
+
+    # dominant kernel: per-launch CUDA-event durations over one more solve
+    P.profile_enable(True)
+    P.mgrit(U_T=UT, **kw)
+    prof = P.profile_read()
+    P.profile_enable(False)
+    pk, src = peaks()
+    fp64_peak = pk["bf16_tflops"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
+    achieved = prof.gemm_flops / (prof.gemm_ms * 1e-3) / 1e12 if prof.gemm_ms > 0 else 0.0
+    flops_per_launch = prof.gemm_flops / max(prof.gemm_launches, 1)
+    roofline = {
+        "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+        "frac": achieved / fp64_peak if fp64_peak else None,
+        "traffic": traffic_from_profile("k_slice_gemm_fp64", flops_per_launch),
+        "kernel": "k_slice_gemm_fp64 (FP64 slice GEMM of the spectral step)",
+        "peak_source": f"{src} BF16 {pk['bf16_tflops']} TFLOP/s x nominal FP64/BF16 {NOMINAL_FP64_TFLOPS}/{NOMINAL_BF16_TFLOPS}",
+        "launches": prof.gemm_launches, "avg_launch_us": 1e3 * prof.gemm_ms / max(prof.gemm_launches, 1),
+        "algorithmic_flops_per_launch": flops_per_launch,
+    }
+
+    # end to end through the C ABI with host buffers: psi_0 host -> device, u(T) device -> host
+    psi_host = torch.from_numpy(psi).pin_memory()
+    UT_host = torch.zeros((w.ny, w.nx), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(dev)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        P.set_initial(psi_host)
+        P.mgrit(U_T=UT_host, **kw)
+    torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": world * w.space_time_updates / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": psi_host.numel() * 8, "d2h_bytes_per_step": UT_host.numel() * 8}
+
+    # comparator: FP64 sequential time stepping on the GPU
+    seq_s = P.seq(U_T=UT)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == sfde.PREC_FP64 else args.precision,
+        "data": "synthetic",
+        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nt": w.nt, "beta": w.beta,
+                   "gamma": w.gamma, "kx": w.kx, "ky": w.ky, "m": w.m, "rel_tol": tol,
+                   "precision": args.precision, "iters": stats.iters, "levels": stats.levels,
+                   "coarse": ["cn", "be"][stats.coarse_used], "step_solves": stats.step_solves,
+                   "l2": "space-time iterate (537 MB) larger than L2; no flush needed",
+                   "parallelism": f"replicas x{world} (independent instances per GPU)"},
+        "roofline": roofline,
+        "e2e": e2e,
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+        "comparators": {"fp64_seq_timestep_gpu": w.space_time_updates / seq_s},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        coarse = ["cn", "be"][stats.coarse_used]
+        rate, dt, cores, sample = oracle_rate(w, stats.iters, coarse)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed-bf16", "mixed-tf32"], default="fp64")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_ours(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

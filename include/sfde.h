@@ -1,0 +1,189 @@
+/*
+ * sfde.h -- C ABI of the GB300 MGRIT solver for the 2-D Riesz space-fractional diffusion
+ * equation (Yue, Shu, Xu, Bu, Pan, arXiv 1805.06688).
+ *
+ * Problem (Sec. 1, Eq. (1.1)):
+ *   u_t = K_x d^{2beta}u/d|x|^{2beta} + K_y d^{2gamma}u/d|y|^{2gamma} + f on (a,b)x(c,d),
+ *   u = 0 on the boundary, u(.,0) = psi_0, 1/2 < beta, gamma < 1, K_x, K_y > 0.
+ * Discretisation (Sec. 2, Eq. (2.4)): linear elements in space (tensor-product hats; the 1-D
+ * stiffness is the symmetric Toeplitz matrix obtained from the paper's element integrals) and
+ * continuous-P1 / discontinuous-P0 space-time elements in time, which give the step
+ *   S_n U_n = B_n U_{n-1} + F_n,  S_n = M_h + tau_n K,  B_n = M_h - tau_n K,
+ *   tau_n = (t_n - t_{n-1})/2,  M_h U = M_y U M_x,  K U = K_x M_y U A_x + K_y A_y U M_x.
+ * Solver (Sec. 3, Algorithm 1): MGRIT V-cycle on the block bidiagonal system of Eq. (3.1).
+ *
+ * Data layout shared by every call.  A spatial field is an N_y x N_x row-major array of
+ * doubles, U[j*N_x + i] = u(x_i, y_j), x_i = a + i*h_x (i = 1..N_x), h_x = (b-a)/(N_x+1);
+ * a space-time field is N_t+1 such slices, time slowest.  Pointers may be host or device
+ * memory: the library asks the CUDA runtime which (cudaPointerGetAttributes) and copies
+ * as needed.  All device work runs on the stream given at setup; every call below returns
+ * only after that work is finished (synchronous).
+ *
+ * Errors: every call returns an sfde_status; nothing throws across the ABI.  After
+ * SFDE_ECUDA the context must be destroyed.  A context is not thread-safe; distinct
+ * contexts are independent.  Ownership: inputs are copied during the call; outputs are
+ * caller-allocated; the context owns all internal device memory and frees it in
+ * sfde_destroy.
+ */
+#ifndef SFDE_H
+#define SFDE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SFDE_OK = 0,
+    SFDE_EINVAL = 1,        /* invalid argument (range, size, NULL, ordering)            */
+    SFDE_ENOMEM = 2,        /* a device or host allocation failed                        */
+    SFDE_ECUDA = 3,         /* a CUDA runtime call or kernel failed; context unusable    */
+    SFDE_ENOCONV = 4,       /* no convergence within max_iter, or a non-finite residual  */
+    SFDE_ETIMEOUT = 5,      /* a bounded device wait ran out                             */
+    SFDE_EUNSUPPORTED = 6   /* option not available in this build                        */
+} sfde_status;
+
+typedef struct sfde_ctx sfde_ctx;
+
+/* Arithmetic of the fine steps (the MGRIT iterate, residual and norm are FP64 in all forms). */
+typedef enum {
+    SFDE_PREC_FP64 = 0,        /* every step in FP64                                              */
+    SFDE_PREC_MIXED_BF16 = 1,  /* inner V-cycles on BF16 tensor cores (FP32 accumulate), FP64
+                                  space-time residual and iterative refinement                    */
+    SFDE_PREC_MIXED_TF32 = 2   /* as above with TF32 operands                                     */
+} sfde_precision;
+
+typedef struct {
+    int precision;     /* sfde_precision                                                   */
+    void* stream;      /* cudaStream_t for all device work; NULL = the legacy default stream */
+} sfde_opts;
+
+/*
+ * sfde_setup -- build one problem instance (Sec. 2).
+ *   beta, gamma : fractional orders, 1/2 < beta, gamma <= 1 (1 gives the classical Laplacian).
+ *   kx, ky      : diffusivities K_x, K_y > 0.
+ *   omega       : host array {a, b, c, d}, a < b, c < d.
+ *   nx, ny      : interior nodes per direction, 1 <= nx, ny <= 4096.
+ *   t           : host array t[0..nt], t[0] = 0, strictly increasing (any grid; the fine
+ *                 propagator depends on n through t_n - t_{n-1}).
+ *   nt          : number of time steps, nt >= 1.
+ *   opts        : may be NULL (FP64, default stream).
+ *   out         : receives the new context.
+ * On the device this computes, in FP64, the Toeplitz coefficients of A_x, A_y from the element
+ * integrals (Sec. 2), the dense matrices, the generalised eigenpairs A V = M V diag(lambda)
+ * with V^T M V = I (Jacobi rotations on L^{-1} A L^{-T}, M = L L^T), and W = M V.
+ * psi_0 defaults to 0 and f to 0.
+ */
+sfde_status sfde_setup(double beta, double gamma, double kx, double ky, const double omega[4],
+                       int nx, int ny, const double* t, int nt, const sfde_opts* opts,
+                       sfde_ctx** out);
+
+/* Nodal initial values psi_0^I (Sec. 2, below Eq. (2.4)): N_y x N_x doubles, host or device. */
+sfde_status sfde_set_initial(sfde_ctx* ctx, const double* psi0);
+
+/*
+ * Separable load vectors (Sec. 2, below Eq. (2.4)):
+ *   F_n[j][i] = sum_{r<rank} time_w[(n-1)*rank + r] * by[r*N_y + j] * bx[r*N_x + i], n = 1..N_t,
+ * i.e. f = sum_r c_r(t) f_x^r(x) f_y^r(y) with time_w = int_{I_n} c_r dt, bx = (f_x^r, phi_i),
+ * by = (f_y^r, phi_j).  0 <= rank <= 4 (rank 0 clears the load).  Host or device arrays.
+ */
+sfde_status sfde_set_forcing(sfde_ctx* ctx, int rank, const double* time_w, const double* bx,
+                             const double* by);
+
+typedef enum { SFDE_RELAX_FCF = 0, SFDE_RELAX_F = 1 } sfde_relax;
+typedef enum {
+    SFDE_COARSE_CN = 0,    /* rediscretisation with the same Crank-Nicolson-type step, Eq. (3.4) */
+    SFDE_COARSE_BE = 1,    /* L-stable backward-Euler rediscretisation (M_h + dt K)^{-1} M_h      */
+    SFDE_COARSE_AUTO = 2   /* CN when Theorem 3.1's two-level bound (Eq. (3.11)) is below 1,
+                              otherwise BE; decided at solve time from the eigenvalues            */
+} sfde_coarse;
+
+typedef struct {
+    int m;               /* coarsening factor, >= 2                                           */
+    int max_levels;      /* >= 1; levels are added while N_l % m == 0 and N_l/m >= min_coarse   */
+    int min_coarse;      /* >= 1                                                              */
+    int relax;           /* sfde_relax (Step 1 of Algorithm 1)                                */
+    int coarse;          /* sfde_coarse                                                       */
+    int max_iter;        /* >= 1                                                              */
+    double rel_tol;      /* stop when ||r||_2 <= max(rel_tol*||r_first||_2, abs_tol); r is the  */
+    double abs_tol;      /* C-point residual Phi_{km}(u_{km-1}) - u_{km} over all level-0 C-points */
+    uint64_t init_seed;  /* 0: zero initial guess; else SplitMix64 uniform[-1,1) values at
+                            t_1..t_N, value index (n*N_y + j)*N_x + i (Sec. 3.2)              */
+} mgrit_opts;
+
+#define SFDE_HISTORY_MAX 512
+
+typedef struct {
+    int iters;            /* V-cycles done (outer refinement iterations for mixed precision)    */
+    int levels;
+    int converged;
+    int coarse_used;      /* sfde_coarse actually used (CN or BE)                               */
+    double res0, res_final;
+    double conv_factor_last5;   /* mean ratio of successive residuals over the last five      */
+    double seconds;       /* wall time of the solve on the device (CUDA events), no setup       */
+    double tub;           /* Theorem 3.1 bound for the CN coarse propagator (computed for AUTO) */
+    long long step_solves;      /* fine/coarse step applications executed, all levels       */
+    long long inner_vcycles;    /* low-precision V-cycles (mixed precision only)             */
+    double history[SFDE_HISTORY_MAX];  /* residual norm per iteration                         */
+} mgrit_stats;
+
+/*
+ * mgrit_solve -- Algorithm 1: V-cycles of FCF (or F) relaxation, injection of the C-point
+ * residual, recursion with zero initial guess, sequential solve on the coarsest level,
+ * C-point correction (F-relaxation after the correction on levels >= 1).
+ *   opts  : NULL gives m = 2, all levels, FCF, AUTO, max_iter 100, rel_tol 1e-10.
+ *   U     : (N_t+1) x N_y x N_x doubles receiving all time points, or NULL.
+ *   U_T   : N_y x N_x doubles receiving u at t_N, or NULL.
+ *   stats : may be NULL.
+ * Returns SFDE_ENOCONV (with U, U_T and stats filled) when max_iter is reached or the
+ * residual is not finite.
+ */
+sfde_status mgrit_solve(sfde_ctx* ctx, const mgrit_opts* opts, double* U, double* U_T,
+                        mgrit_stats* stats);
+
+/* Sequential time stepping U_n = S_n^{-1}(B_n U_{n-1} + F_n), n = 1..N_t (Eq. (2.4)), one step
+ * after another.  U and U_T as in mgrit_solve; seconds (may be NULL) = device time. */
+sfde_status seq_timestep(sfde_ctx* ctx, double* U, double* U_T, double* seconds);
+
+/*
+ * sfde_step_batch -- apply the fine step Phi_n (Eq. (2.4)) to `batch` fields at once:
+ *   out[b] = S_{n_b}^{-1}(B_{n_b} in[b] + F_{n_b}),  n_b = n0 + b*dn,  1 <= n_b <= N_t.
+ * in, out: batch x N_y x N_x doubles (host or device, may not overlap).  This is the unit of
+ * work every relaxation sweep runs; exposed for testing and benchmarking.
+ */
+sfde_status sfde_step_batch(sfde_ctx* ctx, int n0, int dn, int batch, const double* in,
+                            double* out);
+
+/* Read back setup data (for verification).  dir = 0 for x, 1 for y.
+ *   coeffs : N doubles a_0..a_{N-1} of the Toeplitz stiffness (may be NULL)
+ *   lambda : N generalised eigenvalues (may be NULL)
+ *   V      : N x N doubles, V[i*N + k] = component i of eigenvector k (may be NULL)
+ * Host pointers. */
+sfde_status sfde_get_operator(sfde_ctx* ctx, int dir, double* coeffs, double* lambda, double* V);
+
+/*
+ * Kernel accounting for roofline reports (no counterpart in the paper).
+ * sfde_profile_enable resets the counters; with enable != 0 every launch of the step GEMM kernel
+ * is additionally bracketed by CUDA events on the context's stream and its device time and
+ * algorithmic work (2 n_R n_C n_out flops, unpadded sizes; X read + Mat read + Out written, bytes)
+ * are accumulated.  kernel_launches counts every kernel this library launched on the context.
+ */
+typedef struct {
+    long long kernel_launches;
+    long long gemm_launches;
+    double gemm_ms;
+    double gemm_flops;
+    double gemm_bytes;
+} sfde_profile;
+
+sfde_status sfde_profile_enable(sfde_ctx* ctx, int enable);
+sfde_status sfde_profile_read(sfde_ctx* ctx, sfde_profile* out);
+
+void sfde_destroy(sfde_ctx* ctx);
+const char* sfde_strerror(sfde_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFDE_H */

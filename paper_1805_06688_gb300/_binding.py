@@ -1,0 +1,239 @@
+"""ctypes marshalling for ``libsfde.so`` (names and semantics follow ``include/sfde.h``)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(HERE, "libsfde.so")
+
+SFDE_OK, SFDE_EINVAL, SFDE_ENOMEM, SFDE_ECUDA, SFDE_ENOCONV, SFDE_ETIMEOUT, SFDE_EUNSUPPORTED = range(7)
+PREC_FP64, PREC_MIXED_BF16, PREC_MIXED_TF32 = 0, 1, 2
+RELAX_FCF, RELAX_F = 0, 1
+COARSE_CN, COARSE_BE, COARSE_AUTO = 0, 1, 2
+HISTORY_MAX = 512
+
+# every entry point declared in include/sfde.h (checked by the tests)
+exported_symbols = (
+    "sfde_setup", "sfde_set_initial", "sfde_set_forcing", "mgrit_solve", "seq_timestep",
+    "sfde_step_batch", "sfde_get_operator", "sfde_profile_enable", "sfde_profile_read",
+    "sfde_destroy", "sfde_strerror",
+)
+
+
+class SfdeProfile(C.Structure):
+    _fields_ = [("kernel_launches", C.c_longlong), ("gemm_launches", C.c_longlong),
+                ("gemm_ms", C.c_double), ("gemm_flops", C.c_double), ("gemm_bytes", C.c_double)]
+
+
+class SfdeError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {sfde_strerror(status)} (status {status})")
+        self.status = status
+
+
+class SfdeOpts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("stream", C.c_void_p)]
+
+
+class MgritOpts(C.Structure):
+    _fields_ = [("m", C.c_int), ("max_levels", C.c_int), ("min_coarse", C.c_int),
+                ("relax", C.c_int), ("coarse", C.c_int), ("max_iter", C.c_int),
+                ("rel_tol", C.c_double), ("abs_tol", C.c_double), ("init_seed", C.c_uint64)]
+
+
+class MgritStats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("levels", C.c_int), ("converged", C.c_int),
+                ("coarse_used", C.c_int), ("res0", C.c_double), ("res_final", C.c_double),
+                ("conv_factor_last5", C.c_double), ("seconds", C.c_double), ("tub", C.c_double),
+                ("step_solves", C.c_longlong), ("inner_vcycles", C.c_longlong),
+                ("history", C.c_double * HISTORY_MAX)]
+
+    def residual_history(self):
+        return [self.history[i] for i in range(min(self.iters, HISTORY_MAX))]
+
+
+_LIB = None
+
+
+def lib() -> C.CDLL:
+    """Load the compiled library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(library_path):
+            raise RuntimeError(f"{library_path} is missing: build it with "
+                               "`python -m paper_1805_06688_gb300.build` (needs nvcc)")
+        L = C.CDLL(library_path)
+        vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+        L.sfde_setup.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, dp, ip, ip, dp, ip,
+                                 C.POINTER(SfdeOpts), C.POINTER(vp)]
+        L.sfde_set_initial.argtypes = [vp, vp]
+        L.sfde_set_forcing.argtypes = [vp, ip, vp, vp, vp]
+        L.mgrit_solve.argtypes = [vp, C.POINTER(MgritOpts), vp, vp, C.POINTER(MgritStats)]
+        L.seq_timestep.argtypes = [vp, vp, vp, dp]
+        L.sfde_step_batch.argtypes = [vp, ip, ip, ip, vp, vp]
+        L.sfde_get_operator.argtypes = [vp, ip, vp, vp, vp]
+        L.sfde_profile_enable.argtypes = [vp, ip]
+        L.sfde_profile_read.argtypes = [vp, C.POINTER(SfdeProfile)]
+        L.sfde_destroy.argtypes = [vp]
+        L.sfde_destroy.restype = None
+        L.sfde_strerror.argtypes = [ip]
+        L.sfde_strerror.restype = C.c_char_p
+        for name in exported_symbols:
+            if name not in ("sfde_destroy", "sfde_strerror"):
+                getattr(L, name).restype = ip
+        _LIB = L
+    return _LIB
+
+
+def _ptr(a):
+    """Raw pointer of a NumPy array or torch tensor (None -> NULL); must be C-contiguous float64."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous float64")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise ValueError("tensors must be contiguous float64")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(status: int, where: str, allow=(SFDE_OK,)):
+    if status not in allow:
+        raise SfdeError(status, where)
+    return status
+
+
+def sfde_strerror(status: int) -> str:
+    return lib().sfde_strerror(int(status)).decode()
+
+
+def sfde_setup(beta, gamma, kx, ky, omega, nx, ny, t, precision=PREC_FP64, stream=None):
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    opts = SfdeOpts(int(precision), stream)
+    ctx = C.c_void_p()
+    st = lib().sfde_setup(float(beta), float(gamma), float(kx), float(ky),
+                          om.ctypes.data_as(C.POINTER(C.c_double)), int(nx), int(ny),
+                          t.ctypes.data_as(C.POINTER(C.c_double)), len(t) - 1, C.byref(opts),
+                          C.byref(ctx))
+    _check(st, "sfde_setup")
+    return ctx
+
+
+def sfde_set_initial(ctx, psi0):
+    return _check(lib().sfde_set_initial(ctx, _ptr(psi0)), "sfde_set_initial")
+
+
+def sfde_set_forcing(ctx, rank, time_w=None, bx=None, by=None):
+    return _check(lib().sfde_set_forcing(ctx, int(rank), _ptr(time_w), _ptr(bx), _ptr(by)),
+                  "sfde_set_forcing")
+
+
+def mgrit_solve(ctx, opts: MgritOpts | None, U=None, U_T=None, check=True):
+    stats = MgritStats()
+    st = lib().mgrit_solve(ctx, C.byref(opts) if opts is not None else None, _ptr(U), _ptr(U_T),
+                           C.byref(stats))
+    if check:
+        _check(st, "mgrit_solve")
+    return st, stats
+
+
+def seq_timestep(ctx, U=None, U_T=None):
+    sec = C.c_double(0.0)
+    _check(lib().seq_timestep(ctx, _ptr(U), _ptr(U_T), C.byref(sec)), "seq_timestep")
+    return sec.value
+
+
+def sfde_step_batch(ctx, n0, dn, batch, src, dst):
+    return _check(lib().sfde_step_batch(ctx, int(n0), int(dn), int(batch), _ptr(src), _ptr(dst)),
+                  "sfde_step_batch")
+
+
+def sfde_get_operator(ctx, direction, n):
+    coeffs = np.zeros(n)
+    lam = np.zeros(n)
+    V = np.zeros((n, n))
+    _check(lib().sfde_get_operator(ctx, int(direction), _ptr(coeffs), _ptr(lam), _ptr(V)),
+           "sfde_get_operator")
+    return coeffs, lam, V
+
+
+def sfde_profile_enable(ctx, enable: bool):
+    return _check(lib().sfde_profile_enable(ctx, int(bool(enable))), "sfde_profile_enable")
+
+
+def sfde_profile_read(ctx) -> SfdeProfile:
+    p = SfdeProfile()
+    _check(lib().sfde_profile_read(ctx, C.byref(p)), "sfde_profile_read")
+    return p
+
+
+def sfde_destroy(ctx):
+    if ctx:
+        lib().sfde_destroy(ctx)
+
+
+def make_opts(m=2, max_levels=64, min_coarse=2, relax=RELAX_FCF, coarse=COARSE_AUTO, max_iter=100,
+              rel_tol=1e-10, abs_tol=0.0, init_seed=0) -> MgritOpts:
+    return MgritOpts(int(m), int(max_levels), int(min_coarse), int(relax), int(coarse),
+                     int(max_iter), float(rel_tol), float(abs_tol), int(init_seed))
+
+
+class Problem:
+    """Owning wrapper around one ``sfde_ctx`` (destroyed with the object)."""
+
+    def __init__(self, beta, gamma, kx, ky, nx, ny, t, omega=(0.0, 1.0, 0.0, 1.0),
+                 precision=PREC_FP64, stream=None):
+        self.nx, self.ny = int(nx), int(ny)
+        self.t = np.ascontiguousarray(t, dtype=np.float64)
+        self.nt = len(self.t) - 1
+        self.ctx = sfde_setup(beta, gamma, kx, ky, omega, nx, ny, self.t, precision, stream)
+
+    def set_initial(self, psi0):
+        sfde_set_initial(self.ctx, psi0)
+
+    def set_forcing(self, forcing):
+        """``forcing``: an object with time_w (N_t, R), bx (R, N_x), by (R, N_y), or None."""
+        if forcing is None:
+            sfde_set_forcing(self.ctx, 0)
+            return
+        tw = np.ascontiguousarray(forcing.time_w, dtype=np.float64)
+        bx = np.ascontiguousarray(forcing.bx, dtype=np.float64)
+        by = np.ascontiguousarray(forcing.by, dtype=np.float64)
+        sfde_set_forcing(self.ctx, tw.shape[1], tw, bx, by)
+
+    def mgrit(self, U=None, U_T=None, check=True, **kw):
+        return mgrit_solve(self.ctx, make_opts(**kw), U, U_T, check=check)
+
+    def seq(self, U=None, U_T=None):
+        return seq_timestep(self.ctx, U, U_T)
+
+    def step_batch(self, n0, dn, src, dst):
+        return sfde_step_batch(self.ctx, n0, dn, src.shape[0], src, dst)
+
+    def operator(self, direction):
+        return sfde_get_operator(self.ctx, direction, self.nx if direction == 0 else self.ny)
+
+    def profile_enable(self, enable=True):
+        sfde_profile_enable(self.ctx, enable)
+
+    def profile_read(self) -> SfdeProfile:
+        return sfde_profile_read(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            sfde_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,140 @@
+// Internal declarations of the sm_103a MGRIT solver (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <vector>
+
+#include "../../include/sfde.h"
+
+#define SFDE_MAX_RANK 4
+
+// Return SFDE_ECUDA from the enclosing function on any CUDA error.
+#define SFDE_CUDA(call)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) { sfde_set_last_cuda_error(e_, #call, __FILE__, __LINE__); return SFDE_ECUDA; } \
+    } while (0)
+
+#define SFDE_TRY(call)                                    \
+    do {                                                  \
+        sfde_status s_ = (call);                          \
+        if (s_ != SFDE_OK) return s_;                     \
+    } while (0)
+
+void sfde_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// One spatial direction: N interior nodes padded to P (a multiple of 32, >= 32).
+struct SfdeDir {
+    int n = 0, P = 0;
+    double h = 0, rho = 0;
+    double* coeffs = nullptr;  // n Toeplitz coefficients a_k (device)
+    double* A = nullptr;       // P x P dense stiffness, zero padded (device)
+    double* lam = nullptr;     // P generalised eigenvalues, padding = 1 (device)
+    double* V = nullptr;       // P x P eigenvectors, V[i*P + k], zero padded (device)
+    double* W = nullptr;       // M V, P x P (device)
+    double* VT = nullptr;      // V^T (device)
+    double* WT = nullptr;      // W^T (device)
+    float* V32 = nullptr;      // low-precision operand copies (mixed precision), see gemm_tc.cu
+    float* W32 = nullptr;
+};
+
+// Per-level storage of the MGRIT hierarchy.
+struct SfdeLevel {
+    int N = 0;                  // steps on this level
+    std::vector<double> t;      // N+1 times (host)
+    double* dt = nullptr;       // N step sizes (device): dt[n-1] = t_n - t_{n-1}
+    double* u = nullptr;        // (N+1) x P^2 iterate (level 0: the solution) (device)
+    double* g = nullptr;        // (N+1) x P^2 right-hand side, levels >= 1 (device)
+};
+
+// Event ring for per-launch kernel timing (see sfde_profile_enable).
+struct SfdeProf {
+    bool on = false;
+    static const int CAP = 512;
+    cudaEvent_t ev[2 * CAP] = {};
+    double flops[CAP] = {}, bytes[CAP] = {};
+    int head = 0, count = 0;
+    long long launches = 0, gemm_launches = 0;
+    double ms = 0, tot_flops = 0, tot_bytes = 0;
+};
+
+struct sfde_ctx {
+    SfdeDir x, y;
+    double kx = 0, ky = 0;
+    double omega[4] = {0, 1, 0, 1};
+    int nt = 0;
+    std::vector<double> t;      // host copy of the time grid
+    double* dt0 = nullptr;      // level-0 step sizes (device)
+    int precision = SFDE_PREC_FP64;
+    cudaStream_t stream = nullptr;
+    // data
+    double* U0 = nullptr;       // padded psi_0 (device, Py x Px)
+    int rank = 0;
+    double* time_w = nullptr;   // nt x rank (device)
+    double* px = nullptr;       // rank x Px : V_x^T b_x^r (device)
+    double* py = nullptr;       // rank x Py : V_y^T b_y^r (device)
+    // workspace for batched steps
+    size_t ws_slices = 0;
+    double* T1 = nullptr;       // ws_slices x P^2 scratch
+    double* T2 = nullptr;
+    double* T3 = nullptr;
+    double* partial = nullptr;  // per-CTA partial sums for deterministic norms
+    size_t partial_cap = 0;
+    double* scalar = nullptr;   // device scalar (norm^2)
+    double* host_scalar = nullptr;  // pinned
+    // level hierarchy (built by mgrit_solve)
+    std::vector<SfdeLevel> levels;
+    int lev_m = 0, lev_max = 0, lev_min = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    SfdeProf prof;
+    size_t P2() const { return (size_t)x.P * (size_t)y.P; }
+};
+
+// ---- setup (setup.cu)
+sfde_status sfde_setup_direction(SfdeDir& d, int n, double rho, double length, cudaStream_t s);
+void sfde_free_direction(SfdeDir& d);
+sfde_status sfde_project_forcing(sfde_ctx* c, const double* bx_dev, const double* by_dev);
+
+// ---- FP64 step kernels (step_fp64.cu)
+enum SfdeScheme { SCHEME_CN = 0, SCHEME_BE = 1 };
+
+struct StepBatch {
+    int batch;                 // number of slices
+    const double* src; long long src_stride;   // input slice b at src + b*src_stride (elements)
+    double* dst; long long dst_stride;         // output slice b (relax) or residual slice b
+    const double* g; long long g_stride;       // coarse right-hand side slice b (or nullptr)
+    const double* utgt; long long utgt_stride; // residual mode: u at the target (or nullptr)
+    const double* dt;          // step sizes of the level: dt[n_b - 1]
+    int n0, dn;                // target time index n_b = n0 + b*dn
+    int scheme;                // SfdeScheme
+    bool level0;               // add the level-0 load F_n (if rank > 0)
+    double* norm_partial;      // residual mode: per-CTA sums of squares (or nullptr)
+};
+
+sfde_status sfde_step_fp64(sfde_ctx* c, const StepBatch& sb, int* n_partials);
+sfde_status sfde_reduce_partials(sfde_ctx* c, int n_partials, double* host_out);
+
+// ---- MGRIT engine (mgrit.cu)
+sfde_status sfde_mgrit_fp64(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st);
+sfde_status sfde_seq_fp64(sfde_ctx* c, double* seconds);
+sfde_status sfde_ensure_workspace(sfde_ctx* c, size_t slices);
+
+// ---- kernel accounting (api.cu)
+int sfde_prof_begin(sfde_ctx* c);                               // slot or -1 when timing is off
+void sfde_prof_end(sfde_ctx* c, int slot, double flops, double bytes);
+inline void sfde_count_launch(sfde_ctx* c, int n = 1) { c->prof.launches += n; }
+
+// ---- helpers (api.cu)
+bool sfde_is_device_ptr(const void* p);
+sfde_status sfde_copy_in(void* dst_dev, const void* src, size_t bytes, cudaStream_t s);
+sfde_status sfde_copy_out(void* dst, const void* src_dev, size_t bytes, cudaStream_t s);
+
+// padded <-> unpadded slice copies (setup.cu)
+void sfde_launch_pad(const double* src, double* dst, int ny, int nx, int Py, int Px, int slices,
+                     cudaStream_t s);
+void sfde_launch_unpad(const double* src, double* dst, int ny, int nx, int Py, int Px, int slices,
+                       cudaStream_t s);
+void sfde_launch_fill_random(double* u, int nt, int ny, int nx, int Py, int Px, uint64_t seed,
+                             cudaStream_t s);
+void sfde_launch_axpy_strided(double* y, long long y_stride, const double* x, long long x_stride,
+                              int slices, size_t P2, cudaStream_t s);

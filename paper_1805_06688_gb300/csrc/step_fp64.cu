@@ -1,0 +1,234 @@
+// FP64 fine/coarse step on a batch of time slices: the "spectral step" form of one step solve.
+//
+// For the Kronecker operator of Eq. (2.4) with generalised eigenpairs A V = M V diag(lambda),
+// V^T M V = I, W = M V and sigma[j][i] = K_x lambda_x[i] + K_y lambda_y[j], the solution of
+// S_n X = B_n U + F_n is
+//     X = V_y [ Lt_n o (W_y^T U W_x) + (V_y^T F_n V_x) / (1 + tau_n sigma) ] V_x^T,
+//     Lt_n = (1 - tau_n sigma)/(1 + tau_n sigma)   (the eigenvalues of Psi_n, Eq. (3.7)),
+// i.e. four dense GEMMs with the fast-diagonalisation scaling fused into the second one; for the
+// backward-Euler coarse propagator Lt = 1/(1 + dt sigma).  The load term uses the separable
+// factors px = V_x^T b_x, py = V_y^T b_y.
+//
+// Every GEMM has the form  Out_b = (X_b Mat)^T  for slices b of a batch: X_b is R x C (row-major),
+// Mat is C x C' (row-major), Out_b is C' x R.  Storing the transpose lets all four products be
+// right-multiplications of stacked slices:
+//     T1 = (U W_x)^T,  T2 = (T1 W_y)^T = W_y^T U W_x (scaled),  T3 = (T2 V_x^T)^T,  X = (T3 V_y^T)^T.
+// On GB300 FP64 runs at a small fraction of the tensor-core rate, so this kernel is bound by the
+// FP64 pipe; tiles are sized so that even a batch of one slice fills all SMs.
+#include "sfde_internal.cuh"
+
+namespace {
+
+enum Epi { EPI_STORE = 0, EPI_MODAL = 1, EPI_FINAL = 2 };
+
+struct GemmParams {
+    const double* X; long long x_stride; int R, C;
+    const double* Mat; int Cout;
+    double* Out; long long out_stride;
+    int batch;
+    // EPI_MODAL
+    const double* lamx; const double* lamy; double kx, ky;
+    const double* dt; int n0, dn, scheme;
+    int rank; const double* time_w; const double* px; const double* py;
+    // EPI_FINAL
+    const double* g; long long g_stride;
+    const double* utgt; long long utgt_stride;
+    double* partial;
+};
+
+constexpr int BK = 16;
+
+template <int T, int EPI>
+__global__ void __launch_bounds__(256) k_slice_gemm_fp64(GemmParams p) {
+    constexpr int MT = T / 16;  // micro-tile edge
+    __shared__ double As[BK][T + 1];
+    __shared__ double Bs[BK][T + 1];
+    __shared__ double red[256];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const long long m0 = (long long)blockIdx.x * T;
+    const int n0 = blockIdx.y * T;
+    const long long Mtot = (long long)p.batch * p.R;
+
+    double acc[MT][MT];
+#pragma unroll
+    for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int j = 0; j < MT; ++j) acc[i][j] = 0.0;
+
+    for (int k0 = 0; k0 < p.C; k0 += BK) {
+        for (int e = threadIdx.x; e < T * BK; e += 256) {
+            int row = e / BK, kk = e % BK;
+            long long m = m0 + row;
+            double v = 0.0;
+            if (m < Mtot) {
+                long long b = m / p.R, r = m % p.R;
+                v = p.X[b * p.x_stride + r * p.C + k0 + kk];
+            }
+            As[kk][row] = v;
+        }
+        for (int e = threadIdx.x; e < T * BK; e += 256) {
+            int kk = e / T, col = e % T;
+            Bs[kk][col] = p.Mat[(size_t)(k0 + kk) * p.Cout + n0 + col];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double a[MT], bv[MT];
+#pragma unroll
+            for (int i = 0; i < MT; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < MT; ++j) bv[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < MT; ++i)
+#pragma unroll
+                for (int j = 0; j < MT; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+
+    double sq = 0.0;
+#pragma unroll
+    for (int i = 0; i < MT; ++i) {
+        long long m = m0 + tx + 16 * i;
+        if (m >= Mtot) continue;
+        long long b = m / p.R;
+        int r = (int)(m % p.R);
+#pragma unroll
+        for (int j = 0; j < MT; ++j) {
+            int n = n0 + ty + 16 * j;
+            double v = acc[i][j];
+            long long o = (long long)n * p.R + r;
+            if (EPI == EPI_MODAL) {
+                // element (j = n, i = r) of W_y^T U W_x for slice b
+                int tn = p.n0 + (int)b * p.dn;            // target time index of this slice
+                double dt = p.dt[tn - 1];
+                double sig = p.kx * p.lamx[r] + p.ky * p.lamy[n];
+                double lt;
+                if (p.scheme == SCHEME_CN) {
+                    double ts = 0.5 * dt * sig;
+                    lt = (1.0 - ts) / (1.0 + ts);
+                } else {
+                    lt = 1.0 / (1.0 + dt * sig);
+                }
+                v *= lt;
+                if (p.rank > 0) {
+                    double f = 0.0;
+                    for (int q = 0; q < p.rank; ++q)
+                        f += p.time_w[(size_t)(tn - 1) * p.rank + q] * p.py[(size_t)q * p.Cout + n] *
+                             p.px[(size_t)q * p.R + r];
+                    v += f / (1.0 + 0.5 * dt * sig);
+                }
+            } else if (EPI == EPI_FINAL) {
+                if (p.g) v += p.g[b * p.g_stride + o];
+                if (p.utgt) {
+                    v -= p.utgt[b * p.utgt_stride + o];
+                    sq += v * v;
+                }
+            }
+            p.Out[b * p.out_stride + o] = v;
+        }
+    }
+    if (EPI == EPI_FINAL && p.partial) {
+        red[threadIdx.x] = sq;
+        __syncthreads();
+        for (int s = 128; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) p.partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+    }
+}
+
+// Fixed-order sum of the per-CTA partials (deterministic norms).
+__global__ void k_reduce_partials(const double* partial, int n, double* out) {
+    __shared__ double s[1024];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += partial[i];
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) s[threadIdx.x] += s[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+int choose_tile(long long rows, int cout, int pmin) {
+    const long long target = 2 * 152;
+    int T = 64;
+    while (T > 16 && (T > pmin || ((rows + T - 1) / T) * (cout / T) < target)) T /= 2;
+    return T;
+}
+
+// nr, nc, nout: unpadded extents of one slice product (algorithmic work for the profile)
+template <int EPI>
+void launch_T(sfde_ctx* c, int T, const GemmParams& p, int nr, int nc, int nout) {
+    long long rows = (long long)p.batch * p.R;
+    dim3 grid((unsigned)((rows + T - 1) / T), p.Cout / T);
+    int slot = sfde_prof_begin(c);
+    if (T == 64) k_slice_gemm_fp64<64, EPI><<<grid, 256, 0, c->stream>>>(p);
+    else if (T == 32) k_slice_gemm_fp64<32, EPI><<<grid, 256, 0, c->stream>>>(p);
+    else k_slice_gemm_fp64<16, EPI><<<grid, 256, 0, c->stream>>>(p);
+    const double b = p.batch;
+    sfde_prof_end(c, slot, 2.0 * b * nr * nc * nout,
+                  8.0 * (b * nr * nc + b * nr * nout + (double)nc * nout + (EPI == EPI_FINAL && p.utgt ? b * nr * nout : 0.0)));
+    sfde_count_launch(c);
+}
+
+}  // namespace
+
+sfde_status sfde_reduce_partials(sfde_ctx* c, int n_partials, double* host_out) {
+    k_reduce_partials<<<1, 1024, 0, c->stream>>>(c->partial, n_partials, c->scalar);
+    sfde_count_launch(c);
+    SFDE_CUDA(cudaGetLastError());
+    SFDE_CUDA(cudaMemcpyAsync(c->host_scalar, c->scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    SFDE_CUDA(cudaStreamSynchronize(c->stream));
+    *host_out = *c->host_scalar;
+    return SFDE_OK;
+}
+
+sfde_status sfde_step_fp64(sfde_ctx* c, const StepBatch& sb, int* n_partials) {
+    const int Px = c->x.P, Py = c->y.P;
+    const size_t P2 = c->P2();
+    const int pmin = Px < Py ? Px : Py;
+    int total_partials = 0;
+    for (int b0 = 0; b0 < sb.batch; b0 += (int)c->ws_slices) {
+        int nb = sb.batch - b0;
+        if (nb > (int)c->ws_slices) nb = (int)c->ws_slices;
+        GemmParams p{};
+        p.batch = nb;
+        // G1: T1 = (U W_x)^T
+        p.X = sb.src + (long long)b0 * sb.src_stride; p.x_stride = sb.src_stride; p.R = Py; p.C = Px;
+        p.Mat = c->x.W; p.Cout = Px; p.Out = c->T1; p.out_stride = (long long)P2;
+        launch_T<EPI_STORE>(c, choose_tile((long long)nb * Py, Px, pmin), p, c->y.n, c->x.n, c->x.n);
+        // G2: T2 = (T1 W_y)^T, scaled in the modal basis (+ load)
+        GemmParams q{};
+        q.batch = nb; q.X = c->T1; q.x_stride = (long long)P2; q.R = Px; q.C = Py;
+        q.Mat = c->y.W; q.Cout = Py; q.Out = c->T2; q.out_stride = (long long)P2;
+        q.lamx = c->x.lam; q.lamy = c->y.lam; q.kx = c->kx; q.ky = c->ky;
+        q.dt = sb.dt; q.n0 = sb.n0 + b0 * sb.dn; q.dn = sb.dn; q.scheme = sb.scheme;
+        q.rank = (sb.level0 ? c->rank : 0); q.time_w = c->time_w; q.px = c->px; q.py = c->py;
+        launch_T<EPI_MODAL>(c, choose_tile((long long)nb * Px, Py, pmin), q, c->x.n, c->y.n, c->y.n);
+        // G3: T3 = (T2 V_x^T)^T
+        GemmParams r{};
+        r.batch = nb; r.X = c->T2; r.x_stride = (long long)P2; r.R = Py; r.C = Px;
+        r.Mat = c->x.VT; r.Cout = Px; r.Out = c->T3; r.out_stride = (long long)P2;
+        launch_T<EPI_STORE>(c, choose_tile((long long)nb * Py, Px, pmin), r, c->y.n, c->x.n, c->x.n);
+        // G4: X = (T3 V_y^T)^T (+ g) (- u_target, squared into partial sums)
+        GemmParams f{};
+        f.batch = nb; f.X = c->T3; f.x_stride = (long long)P2; f.R = Px; f.C = Py;
+        f.Mat = c->y.VT; f.Cout = Py;
+        f.Out = sb.dst + (long long)b0 * sb.dst_stride; f.out_stride = sb.dst_stride;
+        f.g = sb.g ? sb.g + (long long)b0 * sb.g_stride : nullptr; f.g_stride = sb.g_stride;
+        f.utgt = sb.utgt ? sb.utgt + (long long)b0 * sb.utgt_stride : nullptr; f.utgt_stride = sb.utgt_stride;
+        int T = choose_tile((long long)nb * Px, Py, pmin);
+        long long ctas = (((long long)nb * Px + T - 1) / T) * (Py / T);
+        f.partial = sb.norm_partial ? sb.norm_partial + total_partials : nullptr;
+        if (sb.norm_partial && (size_t)(total_partials + ctas) > c->partial_cap) return SFDE_EINVAL;
+        launch_T<EPI_FINAL>(c, T, f, c->x.n, c->y.n, c->y.n);
+        total_partials += (int)ctas;
+    }
+    SFDE_CUDA(cudaGetLastError());
+    if (n_partials) *n_partials = total_partials;
+    return SFDE_OK;
+}

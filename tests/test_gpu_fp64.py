@@ -1,0 +1,179 @@
+"""GPU parity of the FP64 path against the FP64 CPU oracle, through the C ABI.
+
+Tolerances: the FP64 path and the oracle evaluate the same algebra in a different order
+(series vs 40-digit coefficients, Jacobi vs LAPACK eigenpairs, tiled vs BLAS products), so
+results agree to a small multiple of cond * eps; 1e-11 relative (max norm) is used for fields,
+1e-12 for coefficients.  The MGRIT target in FP64 is 1e-10 relative to the oracle.
+"""
+import numpy as np
+import pytest
+
+from oracle import mgrit as omgrit
+from oracle import sfde as osfde
+from sfde_workloads import (WORKLOADS, gaussian_bump_forcing, sine_mode_amplitudes,
+                            sine_mode_nodal, time_grid)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1805_06688_gb300 as sfde  # noqa: E402
+
+
+def relerr(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+def make(beta, gamma, kx, ky, nx, ny, t, omega=(0.0, 1.0, 0.0, 1.0), forcing=None, psi0=None):
+    P = sfde.Problem(beta, gamma, kx, ky, nx, ny, t, omega)
+    if psi0 is not None:
+        P.set_initial(np.ascontiguousarray(psi0))
+    P.set_forcing(forcing)
+    O = osfde.SFDE(beta, gamma, kx, ky, nx, ny, t, omega)
+    return P, O
+
+
+@pytest.mark.parametrize("n,rho", [(31, 0.75), (255, 0.6), (1023, 0.55), (1, 0.9), (100, 0.99)])
+def test_toeplitz_coefficients(n, rho):
+    P = sfde.Problem(rho, 0.8, 1.0, 1.0, n, 3, time_grid(2))
+    a, _, _ = P.operator(0)
+    ref = osfde.riesz_coefficients(n, rho)
+    assert np.all(np.abs(a - ref) <= 1e-12 * np.abs(ref) + 1e-15 * abs(ref[0]))
+
+
+@pytest.mark.parametrize("n,rho", [(31, 0.75), (200, 0.6), (511, 0.95)])
+def test_generalised_eigenpairs(n, rho):
+    P = sfde.Problem(rho, 0.8, 1.0, 1.0, n, 3, time_grid(2))
+    _, lam, V = P.operator(0)
+    A, M = osfde.stiffness_1d(n, rho), osfde.mass_1d(n)
+    ref = np.sort(np.linalg.eigvalsh(np.linalg.solve(np.linalg.cholesky(M), np.linalg.solve(np.linalg.cholesky(M), A).T)))
+    assert relerr(np.sort(lam), ref) < 1e-12
+    assert np.abs(V.T @ M @ V - np.eye(n)).max() < 1e-12
+    assert np.abs(A @ V - M @ V * lam[None, :]).max() < 1e-11 * lam.max() * np.abs(M @ V).max()
+
+
+@pytest.mark.parametrize("nx,ny,grid", [(5, 7, "uniform"), (50, 70, "graded"), (63, 33, "uniform"), (129, 64, "graded")])
+def test_step_batch_matches_oracle(nx, ny, grid):
+    t = time_grid(24, 1.0, grid)
+    F, _ = gaussian_bump_forcing(3, nx, ny, t)
+    P, O = make(0.7, 0.85, 1.3, 0.4, nx, ny, t, forcing=F)
+    rng = np.random.default_rng(0)
+    batch, n0, dn = 6, 2, 4
+    src = rng.standard_normal((batch, ny, nx))
+    dst = np.zeros_like(src)
+    P.step_batch(n0, dn, src, dst)
+    for b in range(batch):
+        n = n0 + b * dn
+        ref = O.step(src[b], n, F.dense(n))
+        assert relerr(dst[b], ref) < 1e-11, (b, relerr(dst[b], ref))
+
+
+def test_step_batch_device_tensors():
+    t = time_grid(8)
+    P, O = make(0.6, 0.9, 1.0, 0.5, 40, 24, t)
+    src = torch.randn(3, 24, 40, dtype=torch.float64, device="cuda")
+    dst = torch.empty_like(src)
+    P.step_batch(1, 1, src, dst)
+    s = src.cpu().numpy()
+    for b in range(3):
+        assert relerr(dst[b].cpu().numpy(), O.step(s[b], 1 + b)) < 1e-11
+
+
+@pytest.mark.parametrize("nx,ny,nt,grid", [(31, 31, 64, "uniform"), (20, 45, 37, "graded"), (1, 6, 5, "uniform")])
+def test_seq_timestep_matches_oracle(nx, ny, nt, grid):
+    t = time_grid(nt, 1.0, grid)
+    F, _ = gaussian_bump_forcing(9, nx, ny, t)
+    psi = sine_mode_nodal(sine_mode_amplitudes(2), nx, ny)
+    P, O = make(0.65, 0.8, 0.7, 1.9, nx, ny, t, forcing=F, psi0=psi)
+    U = np.zeros((nt + 1, ny, nx))
+    UT = np.zeros((ny, nx))
+    P.seq(U, UT)
+    ref = osfde.seq_timestep(O, psi, F)
+    assert relerr(U, ref) < 1e-11
+    assert np.array_equal(UT, U[-1])
+
+
+def test_manufactured_two_level_matches_oracle():
+    w = WORKLOADS["manufactured_N31_Nt64"]
+    t = w.t()
+    P, O = make(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t, forcing=w.forcing(), psi0=w.initial())
+    for coarse, cname in ((sfde.COARSE_BE, "be"), (sfde.COARSE_CN, "cn")):
+        U = np.zeros((w.nt + 1, w.ny, w.nx))
+        _, st = P.mgrit(U=U, m=w.m, max_levels=2, coarse=coarse, rel_tol=1e-10)
+        ref = omgrit.mgrit(O, w.initial(), w.forcing(), m=w.m, max_levels=2, coarse=cname, rel_tol=1e-10)
+        assert st.converged and st.iters == ref.iters and st.levels == 2
+        h = st.residual_history()
+        for a, b in zip(h, ref.history):
+            assert abs(a - b) <= 1e-9 * ref.history[0]
+        assert relerr(U, ref.U) < 1e-11
+
+
+@pytest.mark.parametrize("relax", ["FCF", "F"])
+@pytest.mark.parametrize("coarse", ["cn", "be"])
+def test_multilevel_graded_random_init_matches_oracle(relax, coarse):
+    nx, ny, nt, m = 20, 13, 64, 4
+    t = time_grid(nt, 1.0, "graded")
+    F, _ = gaussian_bump_forcing(5, nx, ny, t)
+    psi = sine_mode_nodal(sine_mode_amplitudes(4), nx, ny)
+    P, O = make(0.6, 0.9, 1.0, 0.5, nx, ny, t, forcing=F, psi0=psi)
+    U = np.zeros((nt + 1, ny, nx))
+    _, st = P.mgrit(U=U, m=m, max_levels=3, coarse={"cn": sfde.COARSE_CN, "be": sfde.COARSE_BE}[coarse],
+                    relax={"FCF": sfde.RELAX_FCF, "F": sfde.RELAX_F}[relax], rel_tol=1e-11, max_iter=60,
+                    init_seed=12345, check=False)
+    ref = omgrit.mgrit(O, psi, F, m=m, max_levels=3, coarse=coarse, relax=relax, rel_tol=1e-11,
+                       max_iter=60, init_seed=12345)
+    assert st.levels == ref.levels == 3
+    assert st.iters == ref.iters
+    h = st.residual_history()
+    for a, b in zip(h, ref.history):
+        assert abs(a - b) <= 1e-9 * ref.history[0]
+    assert relerr(U, ref.U) < 1e-10
+
+
+def test_sine_N255_Nt1024_full_size():
+    """The benchmarked workload at full size in the launch configuration bench.py times: GPU
+    FP64 MGRIT against the oracle's modal execution of the same iteration (same iterates up to
+    rounding) and against the exact sequential solution at sampled time points."""
+    w = WORKLOADS["sine_N255_Nt1024"]
+    t = w.t()
+    psi = w.initial()
+    P, O = make(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t, psi0=psi)
+    U = torch.zeros((w.nt + 1, w.ny, w.nx), dtype=torch.float64, device="cuda")
+    _, st = P.mgrit(U=U, m=w.m, max_levels=32, coarse=sfde.COARSE_AUTO, rel_tol=w.rel_tol, max_iter=200)
+    assert st.converged and st.levels == 4
+    ref = omgrit.mgrit_modal(O, psi, None, m=w.m, max_levels=32, coarse="be" if st.coarse_used == 1 else "cn",
+                             rel_tol=w.rel_tol, max_iter=200)
+    assert st.iters == ref.iters
+    h = st.residual_history()
+    for a, b in zip(h, ref.history):
+        assert abs(a - b) <= 1e-8 * ref.history[0]
+    UT = U[-1].cpu().numpy()
+    assert relerr(UT, ref.U) < 1e-10
+    exact = osfde.spectral_sequential(O, psi, None, keep=[128, 512, 1024])
+    scale = np.abs(psi).max()
+    for n in (128, 512, 1024):
+        assert np.abs(U[n].cpu().numpy() - exact[n]).max() < 1e-8 * scale
+
+
+def test_edge_cases_and_errors():
+    t = time_grid(1)
+    P, O = make(0.8, 0.7, 1.0, 1.0, 3, 4, t, psi0=np.ones((4, 3)))
+    U = np.zeros((2, 4, 3))
+    _, st = P.mgrit(U=U, m=2)       # a single step: one level, sequential
+    assert st.levels == 1
+    assert relerr(U[1], O.step(np.ones((4, 3)), 1)) < 1e-12
+    # max_iter reached -> ENOCONV with stats filled
+    t = time_grid(64)
+    P, _ = make(0.6, 0.9, 1.0, 0.5, 16, 16, t, psi0=sine_mode_nodal(sine_mode_amplitudes(1), 16, 16))
+    st_code, st = P.mgrit(m=4, max_iter=2, rel_tol=1e-14, coarse=sfde.COARSE_BE, check=False)
+    assert st_code == sfde.SFDE_ENOCONV and st.iters == 2 and not st.converged
+    # non-finite initial data -> ENOCONV
+    bad = np.full((16, 16), np.nan)
+    P.set_initial(bad)
+    st_code, st = P.mgrit(m=4, max_iter=5, check=False)
+    assert st_code == sfde.SFDE_ENOCONV
+    # step index out of range
+    with pytest.raises(sfde.SfdeError):
+        P.step_batch(64, 1, np.zeros((2, 16, 16)), np.zeros((2, 16, 16)))
