@@ -88,6 +88,7 @@ static void free_ctx(sfde_ctx* c) {
     sfde_free_direction(c->x);
     sfde_free_direction(c->y);
     cudaFree(c->dt0); cudaFree(c->U0); cudaFree(c->time_w); cudaFree(c->px); cudaFree(c->py);
+    cudaFree(c->bxn); cudaFree(c->byn);
     cudaFree(c->T1); cudaFree(c->T2); cudaFree(c->T3); cudaFree(c->partial); cudaFree(c->scalar);
     if (c->host_scalar) cudaFreeHost(c->host_scalar);
     if (c->prof.ev[0])
@@ -181,8 +182,8 @@ sfde_status sfde_set_initial(sfde_ctx* c, const double* psi0) {
 sfde_status sfde_set_forcing(sfde_ctx* c, int rank, const double* time_w, const double* bx,
                              const double* by) {
     if (!c || rank < 0 || rank > SFDE_MAX_RANK) return SFDE_EINVAL;
-    cudaFree(c->time_w); cudaFree(c->px); cudaFree(c->py);
-    c->time_w = c->px = c->py = nullptr;
+    cudaFree(c->time_w); cudaFree(c->px); cudaFree(c->py); cudaFree(c->bxn); cudaFree(c->byn);
+    c->time_w = c->px = c->py = c->bxn = c->byn = nullptr;
     c->rank = 0;
     if (rank == 0) return SFDE_OK;
     if (!time_w || !bx || !by) return SFDE_EINVAL;
@@ -197,6 +198,15 @@ sfde_status sfde_set_forcing(sfde_ctx* c, int rank, const double* time_w, const 
     if (st == SFDE_OK) st = sfde_copy_in(bxd, bx, sizeof(double) * (size_t)rank * c->x.n, c->stream);
     if (st == SFDE_OK) st = sfde_copy_in(byd, by, sizeof(double) * (size_t)rank * c->y.n, c->stream);
     if (st == SFDE_OK) st = sfde_project_forcing(c, bxd, byd);
+    if (st == SFDE_OK) {  // padded nodal factors for the FP64 space-time residual
+        cudaError_t e1 = cudaMalloc(&c->bxn, sizeof(double) * (size_t)rank * c->x.P);
+        cudaError_t e2 = cudaMalloc(&c->byn, sizeof(double) * (size_t)rank * c->y.P);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) st = SFDE_ENOMEM;
+        else {
+            sfde_launch_pad(bxd, c->bxn, rank, c->x.n, rank, c->x.P, 1, c->stream);
+            sfde_launch_pad(byd, c->byn, rank, c->y.n, rank, c->y.P, 1, c->stream);
+        }
+    }
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (st == SFDE_OK && e != cudaSuccess) { sfde_set_last_cuda_error(e, "set_forcing", __FILE__, __LINE__); st = SFDE_ECUDA; }
     cudaFree(bxd);

@@ -322,7 +322,8 @@ void sfde_launch_axpy_strided(double* y, long long y_stride, const double* x, lo
     k_axpy_strided<<<grid, 256, 0, s>>>(y, y_stride, x, x_stride, P2);
 }
 
-static int pad_dim(int n) { return n <= 32 ? 32 : ((n + 63) / 64) * 64; }
+// 32, 64, then multiples of 128 so that a 128-row tensor-core tile never straddles two slices
+static int pad_dim(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : ((n + 127) / 128) * 128; }
 
 sfde_status sfde_setup_direction(SfdeDir& d, int n, double rho, double length, cudaStream_t s) {
     d.n = n;

@@ -1,5 +1,6 @@
 // Internal declarations of the sm_103a MGRIT solver (not part of the C ABI).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <vector>
@@ -73,6 +74,8 @@ struct sfde_ctx {
     double* time_w = nullptr;   // nt x rank (device)
     double* px = nullptr;       // rank x Px : V_x^T b_x^r (device)
     double* py = nullptr;       // rank x Py : V_y^T b_y^r (device)
+    double* bxn = nullptr;      // rank x Px : nodal load factors b_x^r, zero padded (device)
+    double* byn = nullptr;      // rank x Py (device)
     // workspace for batched steps
     size_t ws_slices = 0;
     double* T1 = nullptr;       // ws_slices x P^2 scratch
@@ -113,6 +116,36 @@ struct StepBatch {
 
 sfde_status sfde_step_fp64(sfde_ctx* c, const StepBatch& sb, int* n_partials);
 sfde_status sfde_reduce_partials(sfde_ctx* c, int n_partials, double* host_out);
+// rho_n = F_n + M_h (U_{n-1} - U_n) - tau_n K (U_{n-1} + U_n), n = n_first .. n_first+count-1, in FP64;
+// written as BF16 (out_kind 0) or FP32 (1) to rout (slice stride rout_stride elements), with
+// per-CTA sums of rho^2 in partial.
+sfde_status sfde_residual_fp64(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
+                               long long rout_stride, int out_kind, double* partial, int* n_partials);
+
+// ---- tensor-core slice GEMM (gemm_tc.cu)
+enum { SCHEME_SOLVE = 2 };  // modal factor 1/(1 + tau sigma): the solve S^{-1} alone
+enum { TC_EPI_STORE = 0, TC_EPI_SCALE = 1, TC_EPI_FINAL = 2 };
+
+struct TcEpi {
+    const float* lamx; const float* lamy; float kx, ky;   // TC_EPI_SCALE
+    const double* dt; int n0, dn, scheme;
+    const void* g; long long g_stride;                    // TC_EPI_FINAL
+    const void* utgt; long long utgt_stride;
+    double* partial;
+};
+
+struct TcArgs {
+    int R, C, Cout, batch, BN, s0, ds;   // X slices s0 + b*ds, R x C each; Out_b is Cout x R
+    void* out; long long out_stride;
+    TcEpi e;
+    int* err;                            // device error word (bounded waits)
+};
+
+int sfde_tc_tile_n(int cout);
+sfde_status sfde_tc_map_slices(CUtensorMap* map, const void* base, int esz, int K, int R, int ds, long long nslices);
+sfde_status sfde_tc_map_matrix(CUtensorMap* map, const void* matT, int esz, int K, int N);
+sfde_status sfde_tc_gemm(int kind, int epi, const CUtensorMap& A, const CUtensorMap& B, const TcArgs& p,
+                         cudaStream_t s);
 
 // ---- MGRIT engine (mgrit.cu)
 sfde_status sfde_mgrit_fp64(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st);

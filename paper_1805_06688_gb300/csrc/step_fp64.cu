@@ -15,14 +15,17 @@
 //     T1 = (U W_x)^T,  T2 = (T1 W_y)^T = W_y^T U W_x (scaled),  T3 = (T2 V_x^T)^T,  X = (T3 V_y^T)^T.
 // On GB300 FP64 runs at a small fraction of the tensor-core rate, so this kernel is bound by the
 // FP64 pipe; tiles are sized so that even a batch of one slice fills all SMs.
+#include <cuda_bf16.h>
+
 #include "sfde_internal.cuh"
 
 namespace {
 
-enum Epi { EPI_STORE = 0, EPI_MODAL = 1, EPI_FINAL = 2 };
+enum Epi { EPI_STORE = 0, EPI_MODAL = 1, EPI_FINAL = 2, EPI_RESID_BF16 = 3, EPI_RESID_F32 = 4 };
 
 struct GemmParams {
     const double* X; long long x_stride; int R, C;
+    const double* X2;   // optional second operand slice: the A operand is X_b + X2_b (same layout)
     const double* Mat; int Cout;
     double* Out; long long out_stride;
     int batch;
@@ -34,9 +37,24 @@ struct GemmParams {
     const double* g; long long g_stride;
     const double* utgt; long long utgt_stride;
     double* partial;
+    // EPI_RESID_*: space-time residual rho_n = F_n + M_h (U_{n-1} - U_n) - tau_n K (U_{n-1} + U_n)
+    const double* t1;          // (V A_x)^T slices, Px x Py
+    const double* U;           // FP64 iterate, slice n at U + n * P2
+    const double* bxn; const double* byn;   // nodal load factors (padded)
+    double hx, hy;
+    int Px, Py;
+    void* rout;                // residual output (BF16 or FP32), slice b at rout + b * out_stride
 };
 
 constexpr int BK = 16;
+
+template <int EPI> struct ResidOut { using T = double; };
+template <> struct ResidOut<EPI_RESID_BF16> { using T = __nv_bfloat16; };
+template <> struct ResidOut<EPI_RESID_F32> { using T = float; };
+
+__device__ __forceinline__ void store_as(__nv_bfloat16* p, double v) { *p = __float2bfloat16_rn((float)v); }
+__device__ __forceinline__ void store_as(float* p, double v) { *p = (float)v; }
+__device__ __forceinline__ void store_as(double* p, double v) { *p = v; }
 
 template <int T, int EPI>
 __global__ void __launch_bounds__(256) k_slice_gemm_fp64(GemmParams p) {
@@ -62,7 +80,9 @@ __global__ void __launch_bounds__(256) k_slice_gemm_fp64(GemmParams p) {
             double v = 0.0;
             if (m < Mtot) {
                 long long b = m / p.R, r = m % p.R;
-                v = p.X[b * p.x_stride + r * p.C + k0 + kk];
+                const long long a = b * p.x_stride + r * p.C + k0 + kk;
+                v = p.X[a];
+                if (p.X2) v += p.X2[a];
             }
             As[kk][row] = v;
         }
@@ -124,11 +144,50 @@ __global__ void __launch_bounds__(256) k_slice_gemm_fp64(GemmParams p) {
                     v -= p.utgt[b * p.utgt_stride + o];
                     sq += v * v;
                 }
+            } else if (EPI == EPI_RESID_BF16 || EPI == EPI_RESID_F32) {
+                // element (j = n, i = r) of slice b; acc = (A_y (V M_x))[j][i]
+                const int i = r, j = n;
+                const int tn = p.n0 + (int)b;            // time index of this residual
+                const double tau = 0.5 * p.dt[tn - 1];
+                const size_t P2 = (size_t)p.Px * p.Py;
+                const double* T1 = p.t1 + (size_t)b * P2 + (size_t)i * p.Py;   // row i of (V A_x)^T
+                const double my = p.hy / 6.0;
+                double y1 = 4.0 * T1[j];
+                if (j > 0) y1 += T1[j - 1];
+                if (j + 1 < p.Py) y1 += T1[j + 1];
+                const double stiff = p.kx * my * y1 + p.ky * v;
+                const double* Ua = p.U + (size_t)(tn - 1) * P2;
+                const double* Ub = p.U + (size_t)tn * P2;
+                const double wx[3] = {p.hx / 6.0, 4.0 * p.hx / 6.0, p.hx / 6.0};
+                const double wy[3] = {my, 4.0 * my, my};
+                double mass = 0.0;
+#pragma unroll
+                for (int a = -1; a <= 1; ++a) {
+                    const int jj = j + a;
+                    if (jj < 0 || jj >= p.Py) continue;
+                    double row = 0.0;
+#pragma unroll
+                    for (int cc = -1; cc <= 1; ++cc) {
+                        const int ii = i + cc;
+                        if (ii < 0 || ii >= p.Px) continue;
+                        const size_t e = (size_t)jj * p.Px + ii;
+                        row += wx[cc + 1] * (Ua[e] - Ub[e]);
+                    }
+                    mass += wy[a + 1] * row;
+                }
+                double f = 0.0;
+                for (int q = 0; q < p.rank; ++q)
+                    f += p.time_w[(size_t)(tn - 1) * p.rank + q] * p.byn[(size_t)q * p.Py + j] * p.bxn[(size_t)q * p.Px + i];
+                const double rho = f + mass - tau * stiff;
+                sq += rho * rho;
+                using OT = typename ResidOut<EPI>::T;
+                store_as((OT*)p.rout + b * p.out_stride + o, rho);
+                continue;
             }
             p.Out[b * p.out_stride + o] = v;
         }
     }
-    if (EPI == EPI_FINAL && p.partial) {
+    if ((EPI == EPI_FINAL || EPI == EPI_RESID_BF16 || EPI == EPI_RESID_F32) && p.partial) {
         red[threadIdx.x] = sq;
         __syncthreads();
         for (int s = 128; s > 0; s >>= 1) {
@@ -230,5 +289,78 @@ sfde_status sfde_step_fp64(sfde_ctx* c, const StepBatch& sb, int* n_partials) {
     }
     SFDE_CUDA(cudaGetLastError());
     if (n_partials) *n_partials = total_partials;
+    return SFDE_OK;
+}
+
+namespace {
+
+// T2_b = ((U_n + U_{n-1}) M_x)^T for a batch of consecutive n: the x-direction mass stencil
+// (h_x/6)(v_{i-1} + 4 v_i + v_{i+1}) fused with the sum of two time slices and a tile transpose.
+__global__ void k_mass_x_transpose(const double* Un, const double* Um, double* T2, int Px, int Py, double hx) {
+    __shared__ double tile[32][35];
+    const size_t P2 = (size_t)Px * Py;
+    const size_t sl = blockIdx.z;
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    const double* a = Un + sl * P2;
+    const double* b = Um + sl * P2;
+    // rows j0..j0+31, columns i0-1..i0+32 (halo) into tile[j][1 + i]
+    for (int jj = threadIdx.y; jj < 32; jj += blockDim.y) {
+        const int j = j0 + jj;
+        for (int ii = threadIdx.x; ii < 34; ii += 32) {
+            const int i = i0 + ii - 1;
+            double v = 0.0;
+            if (i >= 0 && i < Px) v = a[(size_t)j * Px + i] + b[(size_t)j * Px + i];
+            tile[jj][ii] = v;
+        }
+    }
+    __syncthreads();
+    const double w = hx / 6.0;
+    for (int ii = threadIdx.y; ii < 32; ii += blockDim.y) {
+        const int jj = threadIdx.x;
+        const double v = w * (tile[jj][ii] + 4.0 * tile[jj][ii + 1] + tile[jj][ii + 2]);
+        T2[sl * P2 + (size_t)(i0 + ii) * Py + j0 + jj] = v;
+    }
+}
+
+}  // namespace
+
+sfde_status sfde_residual_fp64(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
+                               long long rout_stride, int out_kind, double* partial, int* n_partials) {
+    const int Px = c->x.P, Py = c->y.P;
+    const size_t P2 = c->P2();
+    const int pmin = Px < Py ? Px : Py;
+    const size_t esz = out_kind == 0 ? 2 : 4;
+    int total = 0;
+    for (int b0 = 0; b0 < count; b0 += (int)c->ws_slices) {
+        int nb = count - b0;
+        if (nb > (int)c->ws_slices) nb = (int)c->ws_slices;
+        const int n0 = n_first + b0;
+        // (V A_x)^T with V = U_n + U_{n-1} formed while loading
+        GemmParams p{};
+        p.batch = nb; p.X = U + (size_t)n0 * P2; p.X2 = U + (size_t)(n0 - 1) * P2; p.x_stride = (long long)P2;
+        p.R = Py; p.C = Px; p.Mat = c->x.A; p.Cout = Px; p.Out = c->T1; p.out_stride = (long long)P2;
+        launch_T<EPI_STORE>(c, choose_tile((long long)nb * Py, Px, pmin), p, c->y.n, c->x.n, c->x.n);
+        // ((U_n + U_{n-1}) M_x)^T
+        k_mass_x_transpose<<<dim3(Px / 32, Py / 32, nb), dim3(32, 8), 0, c->stream>>>(
+            U + (size_t)n0 * P2, U + (size_t)(n0 - 1) * P2, c->T2, Px, Py, c->x.h);
+        sfde_count_launch(c);
+        // A_y (V M_x), then the residual epilogue
+        GemmParams q{};
+        q.batch = nb; q.X = c->T2; q.x_stride = (long long)P2; q.R = Px; q.C = Py;
+        q.Mat = c->y.A; q.Cout = Py; q.out_stride = rout_stride;
+        q.kx = c->kx; q.ky = c->ky; q.dt = c->dt0; q.n0 = n0;
+        q.rank = c->rank; q.time_w = c->time_w; q.bxn = c->bxn; q.byn = c->byn;
+        q.t1 = c->T1; q.U = U; q.hx = c->x.h; q.hy = c->y.h; q.Px = Px; q.Py = Py;
+        q.rout = (char*)rout + (size_t)b0 * rout_stride * esz;
+        const int T = choose_tile((long long)nb * Px, Py, pmin);
+        const long long ctas = (((long long)nb * Px + T - 1) / T) * (Py / T);
+        if ((size_t)(total + ctas) > c->partial_cap) return SFDE_EINVAL;
+        q.partial = partial + total;
+        if (out_kind == 0) launch_T<EPI_RESID_BF16>(c, T, q, c->x.n, c->y.n, c->y.n);
+        else launch_T<EPI_RESID_F32>(c, T, q, c->x.n, c->y.n, c->y.n);
+        total += (int)ctas;
+    }
+    SFDE_CUDA(cudaGetLastError());
+    if (n_partials) *n_partials = total;
     return SFDE_OK;
 }
