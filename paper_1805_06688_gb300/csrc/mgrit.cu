@@ -207,6 +207,13 @@ sfde_status sfde_ensure_workspace(sfde_ctx* c, size_t slices) {
 
 void sfde_free_levels(sfde_ctx* c) { free_levels(c); }
 
+// The FP64 level-0 buffer ((N_t+1) padded slices), built on demand; shared by every solver form.
+sfde_status sfde_level0(sfde_ctx* c, double** u) {
+    if (c->levels.empty()) SFDE_TRY(build_levels(c, 2, 1, 1));
+    *u = c->levels[0].u;
+    return SFDE_OK;
+}
+
 sfde_status sfde_mgrit_fp64(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) {
     SFDE_TRY(build_levels(c, o->m, o->max_levels, o->min_coarse));
     const int L = (int)c->levels.size();

@@ -89,6 +89,7 @@ struct sfde_ctx {
     std::vector<SfdeLevel> levels;
     int lev_m = 0, lev_max = 0, lev_min = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    struct SfdeMixed* mixed = nullptr;  // tensor-core operands and inner hierarchy (mixed.cu)
     SfdeProf prof;
     size_t P2() const { return (size_t)x.P * (size_t)y.P; }
 };
@@ -116,6 +117,7 @@ struct StepBatch {
 
 sfde_status sfde_step_fp64(sfde_ctx* c, const StepBatch& sb, int* n_partials);
 sfde_status sfde_reduce_partials(sfde_ctx* c, int n_partials, double* host_out);
+sfde_status sfde_step_fp64_into(sfde_ctx* c, const StepBatch& sb, double* T1, double* T2, double* T3);
 // rho_n = F_n + M_h (U_{n-1} - U_n) - tau_n K (U_{n-1} + U_n), n = n_first .. n_first+count-1, in FP64;
 // written as BF16 (out_kind 0) or FP32 (1) to rout (slice stride rout_stride elements), with
 // per-CTA sums of rho^2 in partial.

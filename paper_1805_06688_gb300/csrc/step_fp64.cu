@@ -294,6 +294,50 @@ sfde_status sfde_step_fp64(sfde_ctx* c, const StepBatch& sb, int* n_partials) {
 
 namespace {
 
+// Launch without event timing or launch accounting (nothing is created or allocated).
+template <int EPI>
+void launch_plain(int T, const GemmParams& p, cudaStream_t s) {
+    long long rows = (long long)p.batch * p.R;
+    dim3 grid((unsigned)((rows + T - 1) / T), p.Cout / T);
+    if (T == 64) k_slice_gemm_fp64<64, EPI><<<grid, 256, 0, s>>>(p);
+    else if (T == 32) k_slice_gemm_fp64<32, EPI><<<grid, 256, 0, s>>>(p);
+    else k_slice_gemm_fp64<16, EPI><<<grid, 256, 0, s>>>(p);
+}
+
+}  // namespace
+
+// The four products of sfde_step_fp64 for one batch, with caller-provided intermediate buffers
+// T1, T2, T3 (batch x P^2 doubles each); no residual or norm.
+sfde_status sfde_step_fp64_into(sfde_ctx* c, const StepBatch& sb, double* T1, double* T2, double* T3) {
+    const int Px = c->x.P, Py = c->y.P;
+    const long long P2 = (long long)c->P2();
+    const int pmin = Px < Py ? Px : Py;
+    const int nb = sb.batch;
+    GemmParams p{};
+    p.batch = nb; p.X = sb.src; p.x_stride = sb.src_stride; p.R = Py; p.C = Px;
+    p.Mat = c->x.W; p.Cout = Px; p.Out = T1; p.out_stride = P2;
+    launch_plain<EPI_STORE>(choose_tile((long long)nb * Py, Px, pmin), p, c->stream);
+    GemmParams q{};
+    q.batch = nb; q.X = T1; q.x_stride = P2; q.R = Px; q.C = Py;
+    q.Mat = c->y.W; q.Cout = Py; q.Out = T2; q.out_stride = P2;
+    q.lamx = c->x.lam; q.lamy = c->y.lam; q.kx = c->kx; q.ky = c->ky;
+    q.dt = sb.dt; q.n0 = sb.n0; q.dn = sb.dn; q.scheme = sb.scheme;
+    q.rank = (sb.level0 ? c->rank : 0); q.time_w = c->time_w; q.px = c->px; q.py = c->py;
+    launch_plain<EPI_MODAL>(choose_tile((long long)nb * Px, Py, pmin), q, c->stream);
+    GemmParams r{};
+    r.batch = nb; r.X = T2; r.x_stride = P2; r.R = Py; r.C = Px;
+    r.Mat = c->x.VT; r.Cout = Px; r.Out = T3; r.out_stride = P2;
+    launch_plain<EPI_STORE>(choose_tile((long long)nb * Py, Px, pmin), r, c->stream);
+    GemmParams f{};
+    f.batch = nb; f.X = T3; f.x_stride = P2; f.R = Px; f.C = Py;
+    f.Mat = c->y.VT; f.Cout = Py; f.Out = sb.dst; f.out_stride = sb.dst_stride;
+    launch_plain<EPI_FINAL>(choose_tile((long long)nb * Px, Py, pmin), f, c->stream);
+    SFDE_CUDA(cudaGetLastError());
+    return SFDE_OK;
+}
+
+namespace {
+
 // T2_b = ((U_n + U_{n-1}) M_x)^T for a batch of consecutive n: the x-direction mass stencil
 // (h_x/6)(v_{i-1} + 4 v_i + v_{i+1}) fused with the sum of two time slices and a tile transpose.
 __global__ void k_mass_x_transpose(const double* Un, const double* Um, double* T2, int Px, int Py, double hx) {

@@ -1,0 +1,73 @@
+"""Mixed-precision MGRIT (BF16 / TF32 tensor-core V-cycles inside FP64 iterative refinement)
+against the FP64 oracle.  Acceptance: max-norm error <= 1e-8 relative to the max norm of the
+space-time solution, at every time point, against the exact sequential solution of Eq. (2.4)."""
+import numpy as np
+import pytest
+
+from oracle import sfde as osfde
+from sfde_workloads import WORKLOADS, gaussian_bump_forcing, sine_mode_amplitudes, sine_mode_nodal, time_grid
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1805_06688_gb300 as sfde  # noqa: E402
+
+PRECS = [("bf16", sfde.PREC_MIXED_BF16), ("tf32", sfde.PREC_MIXED_TF32)]
+
+
+def _err(U, ref):
+    return float(np.abs(U - ref).max() / np.abs(ref).max())
+
+
+@pytest.mark.parametrize("name,prec", PRECS)
+@pytest.mark.parametrize("nx,ny,nt,m,grid,levels", [(20, 13, 64, 4, "graded", 3), (31, 31, 64, 4, "uniform", 2),
+                                                     (100, 70, 96, 4, "uniform", 8)])
+def test_mixed_matches_sequential(name, prec, nx, ny, nt, m, grid, levels):
+    t = time_grid(nt, 1.0, grid)
+    F, _ = gaussian_bump_forcing(5, nx, ny, t)
+    psi = sine_mode_nodal(sine_mode_amplitudes(4), nx, ny)
+    P = sfde.Problem(0.6, 0.9, 1.0, 0.5, nx, ny, t, precision=prec)
+    P.set_initial(psi)
+    P.set_forcing(F)
+    U = np.zeros((nt + 1, ny, nx))
+    _, st = P.mgrit(U=U, m=m, max_levels=levels, coarse=sfde.COARSE_BE, rel_tol=1e-11, max_iter=60)
+    O = osfde.SFDE(0.6, 0.9, 1.0, 0.5, nx, ny, t)
+    ref = osfde.seq_timestep(O, psi, F)
+    assert st.converged
+    assert _err(U, ref) < 1e-8, (st.iters, st.inner_vcycles, _err(U, ref))
+
+
+@pytest.mark.parametrize("name,prec", PRECS)
+def test_mixed_manufactured(name, prec):
+    w = WORKLOADS["manufactured_N31_Nt64"]
+    t = w.t()
+    P = sfde.Problem(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t, precision=prec)
+    P.set_initial(w.initial())
+    P.set_forcing(w.forcing())
+    U = np.zeros((w.nt + 1, w.ny, w.nx))
+    _, st = P.mgrit(U=U, m=w.m, max_levels=2, coarse=sfde.COARSE_BE, rel_tol=1e-11, max_iter=60)
+    ref = osfde.seq_timestep(osfde.SFDE(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t), w.initial(), w.forcing())
+    assert st.converged and _err(U, ref) < 1e-8
+
+
+@pytest.mark.parametrize("name,prec", PRECS)
+def test_mixed_sine_N255_Nt1024_full_size(name, prec):
+    """The benchmarked workload in the bench's configuration, against the exact sequential
+    solution at sampled time points (space-time max norm)."""
+    w = WORKLOADS["sine_N255_Nt1024"]
+    t = w.t()
+    psi = w.initial()
+    P = sfde.Problem(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t, precision=prec)
+    P.set_initial(psi)
+    U = torch.zeros((w.nt + 1, w.ny, w.nx), dtype=torch.float64, device="cuda")
+    _, st = P.mgrit(U=U, m=w.m, max_levels=32, coarse=sfde.COARSE_AUTO, rel_tol=1e-10, max_iter=100)
+    assert st.converged
+    O = osfde.SFDE(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t)
+    keep = [1, 7, 8, 100, 513, 1024]
+    exact = osfde.spectral_sequential(O, psi, None, keep=keep)
+    scale = np.abs(psi).max()
+    for n in keep:
+        assert np.abs(U[n].cpu().numpy() - exact[n]).max() < 1e-8 * scale, n

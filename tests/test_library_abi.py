@@ -8,8 +8,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared_functions():
-    src = open(os.path.join(ROOT, "include", "sfde.h")).read()
+def _declared_functions(headers=("sfde.h",)):
+    src = "".join(open(os.path.join(ROOT, "include", h)).read() for h in headers)
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:sfde_status|void|const char\*)\s+(\w+)\s*\(", src, flags=re.M)))
 
@@ -32,7 +32,8 @@ def test_header_declares_the_boundary():
 def test_library_exports_every_declared_symbol():
     sfde = _library()
     lib = ctypes.CDLL(sfde.library_path)
-    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    headers = sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
+    missing = [n for n in _declared_functions(headers) if not hasattr(lib, n)]
     assert not missing, missing
     assert set(_declared_functions()) <= set(sfde.exported_symbols) | {"sfde_zz_placeholder"}
 
