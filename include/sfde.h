@@ -41,7 +41,8 @@ typedef enum {
     SFDE_ECUDA = 3,         /* a CUDA runtime call or kernel failed; context unusable    */
     SFDE_ENOCONV = 4,       /* no convergence within max_iter, or a non-finite residual  */
     SFDE_ETIMEOUT = 5,      /* a bounded device wait ran out                             */
-    SFDE_EUNSUPPORTED = 6   /* option not available in this build                        */
+    SFDE_EUNSUPPORTED = 6,  /* option not available in this build                        */
+    SFDE_ESCRATCH = 7       /* request larger than the fixed scratch of sfde_step_batch_noalloc */
 } sfde_status;
 
 typedef struct sfde_ctx sfde_ctx;
@@ -154,6 +155,32 @@ sfde_status seq_timestep(sfde_ctx* ctx, double* U, double* U_T, double* seconds)
  */
 sfde_status sfde_step_batch(sfde_ctx* ctx, int n0, int dn, int batch, const double* in,
                             double* out);
+
+/*
+ * sfde_step_batch_noalloc -- the same computation as sfde_step_batch, without allocating any device
+ * memory (no counterpart in the paper: this exists for callers of the library).
+ *
+ * Some callers cannot let a library call cudaMalloc or cudaFree: an application whose device memory
+ * is held by another allocator (a framework's caching allocator owns the pool, so a new cudaMalloc
+ * may fail or force that allocator to give memory back), or a latency-critical loop in which
+ * cudaFree would synchronise the whole device.  This entry point keeps its padded staging buffers
+ * and step intermediates in one fixed device array of SFDE_NOALLOC_SCRATCH_DOUBLES doubles (10 MiB)
+ * that is part of the library image: every GPU that loads the library holds it until exit.
+ *
+ *   in, out : DEVICE pointers, batch x N_y x N_x doubles each (host pointers -> SFDE_EINVAL).
+ *   limit   : 5 * batch * P_x * P_y <= SFDE_NOALLOC_SCRATCH_DOUBLES, where P is the padded extent
+ *             of a direction (32 for N <= 32, 64 for N <= 64, else N rounded up to a multiple of 128);
+ *             larger requests return SFDE_ESCRATCH before any work is queued.
+ * The work is queued on the context's stream and the call returns without waiting: synchronise that
+ * stream before reading `out`.  All calls, from every context on a device, share the one array:
+ * calls whose work overlaps on the GPU (different streams, or different host threads) race and must
+ * be serialised by the caller.  Each call writes every scratch element it reads, so no clearing is
+ * needed between calls.  On the first call for a device (with that device current) the library looks
+ * up the array's device address once and caches it; make that first call before any stream capture.
+ */
+#define SFDE_NOALLOC_SCRATCH_DOUBLES (5u * 262144u)
+sfde_status sfde_step_batch_noalloc(sfde_ctx* ctx, int n0, int dn, int batch, const double* in,
+                                    double* out);
 
 /* Read back setup data (for verification).  dir = 0 for x, 1 for y.
  *   coeffs : N doubles a_0..a_{N-1} of the Toeplitz stiffness (may be NULL)

@@ -9,7 +9,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(HERE, "libsfde.so")
 
-SFDE_OK, SFDE_EINVAL, SFDE_ENOMEM, SFDE_ECUDA, SFDE_ENOCONV, SFDE_ETIMEOUT, SFDE_EUNSUPPORTED = range(7)
+(SFDE_OK, SFDE_EINVAL, SFDE_ENOMEM, SFDE_ECUDA, SFDE_ENOCONV, SFDE_ETIMEOUT, SFDE_EUNSUPPORTED,
+ SFDE_ESCRATCH) = range(8)
+NOALLOC_SCRATCH_DOUBLES = 5 * 262144
 PREC_FP64, PREC_MIXED_BF16, PREC_MIXED_TF32 = 0, 1, 2
 RELAX_FCF, RELAX_F = 0, 1
 COARSE_CN, COARSE_BE, COARSE_AUTO = 0, 1, 2
@@ -18,7 +20,7 @@ HISTORY_MAX = 512
 # every entry point declared in include/sfde.h (checked by the tests)
 exported_symbols = (
     "sfde_setup", "sfde_set_initial", "sfde_set_forcing", "mgrit_solve", "seq_timestep",
-    "sfde_step_batch", "sfde_get_operator", "sfde_profile_enable", "sfde_profile_read",
+    "sfde_step_batch", "sfde_step_batch_noalloc", "sfde_get_operator", "sfde_profile_enable", "sfde_profile_read",
     "sfde_destroy", "sfde_strerror",
 )
 
@@ -74,6 +76,7 @@ def lib() -> C.CDLL:
         L.mgrit_solve.argtypes = [vp, C.POINTER(MgritOpts), vp, vp, C.POINTER(MgritStats)]
         L.seq_timestep.argtypes = [vp, vp, vp, dp]
         L.sfde_step_batch.argtypes = [vp, ip, ip, ip, vp, vp]
+        L.sfde_step_batch_noalloc.argtypes = [vp, ip, ip, ip, vp, vp]
         L.sfde_get_operator.argtypes = [vp, ip, vp, vp, vp]
         L.sfde_profile_enable.argtypes = [vp, ip]
         L.sfde_profile_read.argtypes = [vp, C.POINTER(SfdeProfile)]
@@ -154,6 +157,12 @@ def seq_timestep(ctx, U=None, U_T=None):
 def sfde_step_batch(ctx, n0, dn, batch, src, dst):
     return _check(lib().sfde_step_batch(ctx, int(n0), int(dn), int(batch), _ptr(src), _ptr(dst)),
                   "sfde_step_batch")
+
+
+def sfde_step_batch_noalloc(ctx, n0, dn, batch, src, dst):
+    """Queue the batched step on the context's stream using the library's fixed device scratch
+    (no device allocation); src and dst must be device tensors.  Returns the raw status."""
+    return lib().sfde_step_batch_noalloc(ctx, int(n0), int(dn), int(batch), _ptr(src), _ptr(dst))
 
 
 def sfde_get_operator(ctx, direction, n):

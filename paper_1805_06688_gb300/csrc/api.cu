@@ -109,6 +109,7 @@ const char* sfde_strerror(sfde_status s) {
         case SFDE_ENOCONV: return "no convergence";
         case SFDE_ETIMEOUT: return "device wait timed out";
         case SFDE_EUNSUPPORTED: return "unsupported option";
+        case SFDE_ESCRATCH: return "request exceeds the fixed scratch of sfde_step_batch_noalloc";
     }
     return "unknown status";
 }
