@@ -177,6 +177,64 @@ def run_reference(args, w):
     return 0
 
 
+# ----------------------------------------------------------------------------- roofline
+
+KERNEL_CLASSES = (
+    ("k_slice_gemm_fp64", "FP64 slice GEMM of the spectral step"),
+    ("k_slice_gemm_fp64", "FP64 slice GEMM of the space-time residual"),
+    ("k_tc_slice_gemm", "tcgen05 slice GEMM (BF16/TF32 operands, FP32 accumulate)"),
+)
+
+
+def roofline_from_profile(prof, precision: str):
+    """Roofline of the kernel class with the largest device time, plus a per-class breakdown.
+
+    FP64 GEMMs are bound by the FP64 pipe (peak = measured BF16 x nominal FP64/BF16 ratio); the
+    tensor-core GEMM is placed by its algorithmic intensity against the ridge point: below it the
+    bound is HBM bandwidth (algorithmic bytes / time), above it the tensor pipe of its dtype."""
+    pk, src = peaks()
+    fp64_peak = pk["bf16_tflops"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
+    tc_peak = pk["bf16_tflops"] * (0.5 if precision == "mixed-tf32" else 1.0)
+    kernels = []
+    for k, (name, what) in enumerate(KERNEL_CLASSES):
+        n, ms, fl, by = prof.launches[k], prof.ms[k], prof.flops[k], prof.bytes[k]
+        if n == 0 or ms <= 0:
+            continue
+        tfs = fl / (ms * 1e-3) / 1e12
+        gbs = by / (ms * 1e-3) / 1e9
+        if k < 2:
+            bound, ach, peak, unit = "alu", tfs, fp64_peak, "TFLOP/s"
+            psrc = f"{src} BF16 {pk['bf16_tflops']} TFLOP/s x nominal FP64/BF16 {NOMINAL_FP64_TFLOPS}/{NOMINAL_BF16_TFLOPS}"
+        elif fl / by < tc_peak * 1e12 / (pk["hbm_gbs"] * 1e9):
+            bound, ach, peak, unit = "hbm", gbs, pk["hbm_gbs"], "GB/s"
+            psrc = f"{src} HBM copy bandwidth"
+        else:
+            bound, ach, peak, unit = "tensor", tfs, tc_peak, "TFLOP/s"
+            psrc = f"{src} BF16 dense" + (" x 1/2 (TF32 nominal ratio)" if precision == "mixed-tf32" else "")
+        kernels.append({
+            "kernel": name, "what": what, "launches": int(n), "ms": ms, "share": None,
+            "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+            "peak_source": psrc, "avg_launch_us": 1e3 * ms / n,
+            "algorithmic_flops_per_launch": fl / n, "algorithmic_bytes_per_launch": by / n,
+            "tflops": tfs, "gbs": gbs,
+        })
+    tot = sum(k["ms"] for k in kernels) or 1.0
+    for k in kernels:
+        k["share"] = k["ms"] / tot
+    dom = max(kernels, key=lambda k: k["ms"])
+    roofline = {
+        "bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"], "unit": dom["unit"],
+        "frac": dom["frac"],
+        "traffic": traffic_from_profile(dom["kernel"], dom["algorithmic_flops_per_launch"]),
+        "kernel": f"{dom['kernel']} ({dom['what']})", "peak_source": dom["peak_source"],
+        "launches": dom["launches"], "avg_launch_us": dom["avg_launch_us"],
+        "algorithmic_flops_per_launch": dom["algorithmic_flops_per_launch"],
+        "algorithmic_bytes_per_launch": dom["algorithmic_bytes_per_launch"],
+        "share_of_gemm_time": dom["share"],
+    }
+    return roofline, kernels
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def run_ours(args, w):
@@ -241,19 +299,7 @@ def run_ours(args, w):
     P.mgrit(U_T=UT, **kw)
     prof = P.profile_read()
     P.profile_enable(False)
-    pk, src = peaks()
-    fp64_peak = pk["bf16_tflops"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
-    achieved = prof.gemm_flops / (prof.gemm_ms * 1e-3) / 1e12 if prof.gemm_ms > 0 else 0.0
-    flops_per_launch = prof.gemm_flops / max(prof.gemm_launches, 1)
-    roofline = {
-        "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-        "frac": achieved / fp64_peak if fp64_peak else None,
-        "traffic": traffic_from_profile("k_slice_gemm_fp64", flops_per_launch),
-        "kernel": "k_slice_gemm_fp64 (FP64 slice GEMM of the spectral step)",
-        "peak_source": f"{src} BF16 {pk['bf16_tflops']} TFLOP/s x nominal FP64/BF16 {NOMINAL_FP64_TFLOPS}/{NOMINAL_BF16_TFLOPS}",
-        "launches": prof.gemm_launches, "avg_launch_us": 1e3 * prof.gemm_ms / max(prof.gemm_launches, 1),
-        "algorithmic_flops_per_launch": flops_per_launch,
-    }
+    roofline, kernels = roofline_from_profile(prof, args.precision)
 
     # end to end through the C ABI with host buffers: psi_0 host -> device, u(T) device -> host
     psi_host = torch.from_numpy(psi).pin_memory()
@@ -287,6 +333,7 @@ def run_ours(args, w):
                    "l2": "space-time iterate (537 MB) larger than L2; no flush needed",
                    "parallelism": f"replicas x{world} (independent instances per GPU)"},
         "roofline": roofline,
+        "kernels": kernels,
         "e2e": e2e,
         "clocks": clk.summary(),
         "gpu_launches": launches,

@@ -111,6 +111,8 @@ typedef struct {
     double abs_tol;      /* C-point residual Phi_{km}(u_{km-1}) - u_{km} over all level-0 C-points */
     uint64_t init_seed;  /* 0: zero initial guess; else SplitMix64 uniform[-1,1) values at
                             t_1..t_N, value index (n*N_y + j)*N_x + i (Sec. 3.2)              */
+    int inner_cycles;    /* mixed precision only: low-precision V-cycles per FP64 refinement step
+                            (0 = default: 4 for BF16, 5 for TF32)                             */
 } mgrit_opts;
 
 #define SFDE_HISTORY_MAX 512
@@ -191,17 +193,20 @@ sfde_status sfde_get_operator(sfde_ctx* ctx, int dir, double* coeffs, double* la
 
 /*
  * Kernel accounting for roofline reports (no counterpart in the paper).
- * sfde_profile_enable resets the counters; with enable != 0 every launch of the step GEMM kernel
- * is additionally bracketed by CUDA events on the context's stream and its device time and
- * algorithmic work (2 n_R n_C n_out flops, unpadded sizes; X read + Mat read + Out written, bytes)
- * are accumulated.  kernel_launches counts every kernel this library launched on the context.
+ * sfde_profile_enable resets the counters; with enable != 0 every launch of the slice-GEMM kernels
+ * is additionally bracketed by CUDA events on the context's stream, and its device time and
+ * algorithmic work (2 n_R n_C n_out flops with unpadded sizes; bytes = X read + Mat read + Out
+ * written, plus the extra slices an epilogue reads) are accumulated per kernel class:
+ *   0 = FP64 step GEMM, 1 = FP64 space-time residual GEMM, 2 = tensor-core (BF16/TF32) GEMM.
+ * kernel_launches counts every kernel this library launched on the context.
  */
+#define SFDE_PROF_CLASSES 3
 typedef struct {
     long long kernel_launches;
-    long long gemm_launches;
-    double gemm_ms;
-    double gemm_flops;
-    double gemm_bytes;
+    long long launches[SFDE_PROF_CLASSES];
+    double ms[SFDE_PROF_CLASSES];
+    double flops[SFDE_PROF_CLASSES];
+    double bytes[SFDE_PROF_CLASSES];
 } sfde_profile;
 
 sfde_status sfde_profile_enable(sfde_ctx* ctx, int enable);

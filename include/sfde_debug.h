@@ -17,9 +17,12 @@ extern "C" {
  * output (tcgen05 kind::f16), kind 1: FP32 storage with TF32 products (kind::tf32); FP32
  * accumulation.  All pointers are device pointers, 16-byte aligned.  Synchronous.  *err_out (may be
  * NULL) receives the kernel's error word (non-zero if a bounded wait ran out -> SFDE_ETIMEOUT).
+ * If reps > 0 and ms_out != NULL, the product is then repeated `reps` times back to back on the
+ * legacy default stream and the average device time per launch (CUDA events) is stored in *ms_out.
  */
 sfde_status sfde_debug_tc_gemm(int kind, const void* X, long long nslices, int s0, int ds, int batch,
-                               int R, int C, const void* MatT, int Cout, void* Out, int* err_out);
+                               int R, int C, const void* MatT, int Cout, void* Out, int* err_out,
+                               int reps, float* ms_out);
 
 #ifdef __cplusplus
 }

@@ -25,9 +25,13 @@ exported_symbols = (
 )
 
 
+PROF_CLASSES = 3  # 0: FP64 step GEMM, 1: FP64 residual GEMM, 2: tensor-core GEMM
+
+
 class SfdeProfile(C.Structure):
-    _fields_ = [("kernel_launches", C.c_longlong), ("gemm_launches", C.c_longlong),
-                ("gemm_ms", C.c_double), ("gemm_flops", C.c_double), ("gemm_bytes", C.c_double)]
+    _fields_ = [("kernel_launches", C.c_longlong), ("launches", C.c_longlong * PROF_CLASSES),
+                ("ms", C.c_double * PROF_CLASSES), ("flops", C.c_double * PROF_CLASSES),
+                ("bytes", C.c_double * PROF_CLASSES)]
 
 
 class SfdeError(RuntimeError):
@@ -43,7 +47,8 @@ class SfdeOpts(C.Structure):
 class MgritOpts(C.Structure):
     _fields_ = [("m", C.c_int), ("max_levels", C.c_int), ("min_coarse", C.c_int),
                 ("relax", C.c_int), ("coarse", C.c_int), ("max_iter", C.c_int),
-                ("rel_tol", C.c_double), ("abs_tol", C.c_double), ("init_seed", C.c_uint64)]
+                ("rel_tol", C.c_double), ("abs_tol", C.c_double), ("init_seed", C.c_uint64),
+                ("inner_cycles", C.c_int)]
 
 
 class MgritStats(C.Structure):
@@ -190,9 +195,9 @@ def sfde_destroy(ctx):
 
 
 def make_opts(m=2, max_levels=64, min_coarse=2, relax=RELAX_FCF, coarse=COARSE_AUTO, max_iter=100,
-              rel_tol=1e-10, abs_tol=0.0, init_seed=0) -> MgritOpts:
+              rel_tol=1e-10, abs_tol=0.0, init_seed=0, inner_cycles=0) -> MgritOpts:
     return MgritOpts(int(m), int(max_levels), int(min_coarse), int(relax), int(coarse),
-                     int(max_iter), float(rel_tol), float(abs_tol), int(init_seed))
+                     int(max_iter), float(rel_tol), float(abs_tol), int(init_seed), int(inner_cycles))
 
 
 class Problem:

@@ -43,10 +43,14 @@ static void prof_flush_one(sfde_ctx* c, int slot) {
     SfdeProf& P = c->prof;
     cudaEventSynchronize(P.ev[2 * slot + 1]);
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, P.ev[2 * slot], P.ev[2 * slot + 1]) == cudaSuccess) P.ms += ms;
-    P.tot_flops += P.flops[slot];
-    P.tot_bytes += P.bytes[slot];
-    P.gemm_launches += 1;
+    if (cudaEventElapsedTime(&ms, P.ev[2 * slot], P.ev[2 * slot + 1]) != cudaSuccess) ms = 0.f;
+    const int k = P.cls[slot];
+    if (k >= 0 && k < SfdeProf::NCLS) {
+        P.ms[k] += ms;
+        P.tot_flops[k] += P.flops[slot];
+        P.tot_bytes[k] += P.bytes[slot];
+        P.n[k] += 1;
+    }
 }
 
 int sfde_prof_begin(sfde_ctx* c) {
@@ -63,10 +67,11 @@ int sfde_prof_begin(sfde_ctx* c) {
     return slot;
 }
 
-void sfde_prof_end(sfde_ctx* c, int slot, double flops, double bytes) {
+void sfde_prof_end(sfde_ctx* c, int slot, int cls, double flops, double bytes) {
     if (slot < 0) return;
     SfdeProf& P = c->prof;
     cudaEventRecord(P.ev[2 * slot + 1], c->stream);
+    P.cls[slot] = cls;
     P.flops[slot] = flops;
     P.bytes[slot] = bytes;
     P.head = (P.head + 1) % SfdeProf::CAP;
@@ -262,11 +267,12 @@ sfde_status mgrit_solve(sfde_ctx* c, const mgrit_opts* opts, double* U, double* 
     } else {
         o.m = 2; o.max_levels = 64; o.min_coarse = 2; o.relax = SFDE_RELAX_FCF;
         o.coarse = SFDE_COARSE_AUTO; o.max_iter = 100; o.rel_tol = 1e-10; o.abs_tol = 0.0; o.init_seed = 0;
+        o.inner_cycles = 0;
     }
     if (o.m < 2 || o.max_levels < 1 || o.min_coarse < 1 || o.max_iter < 1) return SFDE_EINVAL;
     if (o.relax != SFDE_RELAX_FCF && o.relax != SFDE_RELAX_F) return SFDE_EINVAL;
     if (o.coarse < SFDE_COARSE_CN || o.coarse > SFDE_COARSE_AUTO) return SFDE_EINVAL;
-    if (!(o.rel_tol >= 0.0) || !(o.abs_tol >= 0.0)) return SFDE_EINVAL;
+    if (!(o.rel_tol >= 0.0) || !(o.abs_tol >= 0.0) || o.inner_cycles < 0) return SFDE_EINVAL;
     sfde_status st;
     if (c->precision == SFDE_PREC_FP64)
         st = sfde_mgrit_fp64(c, &o, stats);
@@ -334,8 +340,8 @@ sfde_status sfde_profile_enable(sfde_ctx* c, int enable) {
     SfdeProf& P = c->prof;
     P.on = enable != 0;
     P.head = P.count = 0;
-    P.launches = P.gemm_launches = 0;
-    P.ms = P.tot_flops = P.tot_bytes = 0.0;
+    P.launches = 0;
+    for (int k = 0; k < SfdeProf::NCLS; ++k) { P.n[k] = 0; P.ms[k] = P.tot_flops[k] = P.tot_bytes[k] = 0.0; }
     return SFDE_OK;
 }
 
@@ -345,10 +351,12 @@ sfde_status sfde_profile_read(sfde_ctx* c, sfde_profile* out) {
     prof_flush_all(c);
     const SfdeProf& P = c->prof;
     out->kernel_launches = P.launches;
-    out->gemm_launches = P.gemm_launches;
-    out->gemm_ms = P.ms;
-    out->gemm_flops = P.tot_flops;
-    out->gemm_bytes = P.tot_bytes;
+    for (int k = 0; k < SfdeProf::NCLS; ++k) {
+        out->launches[k] = P.n[k];
+        out->ms[k] = P.ms[k];
+        out->flops[k] = P.tot_flops[k];
+        out->bytes[k] = P.tot_bytes[k];
+    }
     return SFDE_OK;
 }
 

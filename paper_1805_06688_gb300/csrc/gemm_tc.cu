@@ -108,8 +108,9 @@ k_tc_slice_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     }
 
     // ---- epilogue (all 128 threads)
-    const bool acc_ok = tc::mbar_wait(accf, 0, p.err, tc::ERR_WAIT_ACC);
-    __syncwarp();
+    // tcgen05.ld is warp-collective (.sync.aligned): the whole warp reads the accumulator or none of
+    // it, so a lane whose bounded wait ran out makes its warp skip the epilogue.
+    const bool acc_ok = __all_sync(0xffffffffu, tc::mbar_wait(accf, 0, p.err, tc::ERR_WAIT_ACC));
     tc::tc_fence_after();
     double sq = 0.0;
     if (acc_ok) {
@@ -117,39 +118,51 @@ k_tc_slice_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         const bool valid = m < Mtot;
         const long long b = valid ? m / p.R : 0;
         const int r = valid ? (int)(m % p.R) : 0;
-        T* out = (T*)p.out + b * p.out_stride;
+        T* __restrict__ out = (T*)p.out + b * p.out_stride;
         float lx = 0.f;
-        double dt = 0.0;
+        float dtf = 0.f;
         if (EPI == TC_EPI_SCALE && valid) {
             lx = p.e.kx * p.e.lamx[r];
-            dt = p.e.dt[p.e.n0 + (int)b * p.e.dn - 1];
+            dtf = (float)p.e.dt[p.e.n0 + (int)b * p.e.dn - 1];
         }
-        const T* g = (EPI == TC_EPI_FINAL && p.e.g) ? (const T*)p.e.g + b * p.e.g_stride : nullptr;
-        const T* ut = (EPI == TC_EPI_FINAL && p.e.utgt) ? (const T*)p.e.utgt + b * p.e.utgt_stride : nullptr;
+        const T* __restrict__ g = (EPI == TC_EPI_FINAL && p.e.g) ? (const T*)p.e.g + b * p.e.g_stride : nullptr;
+        const T* __restrict__ ut = (EPI == TC_EPI_FINAL && p.e.utgt) ? (const T*)p.e.utgt + b * p.e.utgt_stride : nullptr;
         for (int c0 = 0; c0 < BN; c0 += 32) {
             uint32_t v[32];
             tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
             if (!valid) continue;
+            const T* gcol = g ? g + (long long)(n0 + c0) * p.R + r : nullptr;
+            const T* ucol = ut ? ut + (long long)(n0 + c0) * p.R + r : nullptr;
+            T* ocol = out + (long long)(n0 + c0) * p.R + r;
+            // all operand loads of the 32-column chunk are issued before any store: they are
+            // independent, so their latencies overlap instead of adding up element by element
+            float add[32];
+            if (EPI == TC_EPI_SCALE) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) add[j] = __ldg(p.e.lamy + n0 + c0 + j);
+            } else if (EPI == TC_EPI_FINAL) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) add[j] = gcol ? StoreT<T>::to(gcol[(long long)j * p.R]) : 0.f;
+                if (ucol) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) add[j] -= StoreT<T>::to(ucol[(long long)j * p.R]);
+                }
+            }
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-                const int n = n0 + c0 + j;
                 float x = __uint_as_float(v[j]);
-                const long long o = (long long)n * p.R + r;
                 if (EPI == TC_EPI_SCALE) {
-                    const float z = (float)dt * (lx + p.e.ky * p.e.lamy[n]);
+                    const float z = dtf * (lx + p.e.ky * add[j]);
                     float f;
                     if (p.e.scheme == SCHEME_CN) f = (1.f - 0.5f * z) / (1.f + 0.5f * z);
                     else if (p.e.scheme == SCHEME_BE) f = 1.f / (1.f + z);
                     else f = 1.f / (1.f + 0.5f * z);  // solve: 1 / (1 + tau sigma)
                     x *= f;
                 } else if (EPI == TC_EPI_FINAL) {
-                    if (g) x += StoreT<T>::to(g[o]);
-                    if (ut) {
-                        x -= StoreT<T>::to(ut[o]);
-                        sq += (double)x * (double)x;
-                    }
+                    x += add[j];
+                    if (ucol) sq += (double)x * (double)x;
                 }
-                out[o] = StoreT<T>::from(x);
+                ocol[(long long)j * p.R] = StoreT<T>::from(x);
             }
         }
     }
@@ -183,7 +196,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 size_t smem_bytes(int BN) { return 1024 + (size_t)STAGES * (A_STAGE_BYTES + (size_t)BN * 128) + 256; }
 
 template <int KIND, typename T, int EPI>
-sfde_status launch(const CUtensorMap& A, const CUtensorMap& B, const TcArgs& p, cudaStream_t s) {
+sfde_status launch(sfde_ctx* c, const CUtensorMap& A, const CUtensorMap& B, const TcArgs& p, cudaStream_t s,
+                   int nr, int nc, int nout) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_tc_slice_gemm<KIND, T, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -192,7 +206,15 @@ sfde_status launch(const CUtensorMap& A, const CUtensorMap& B, const TcArgs& p, 
     }
     const long long rows = (long long)p.batch * p.R;
     dim3 grid((unsigned)((rows + BM - 1) / BM), p.Cout / p.BN);
+    const int slot = c ? sfde_prof_begin(c) : -1;
     k_tc_slice_gemm<KIND, T, EPI><<<grid, 128, smem_bytes(p.BN), s>>>(A, B, p);
+    if (c) {
+        const double b = p.batch, esz = sizeof(T);
+        const double extra = EPI == TC_EPI_FINAL ? ((p.e.g ? 1.0 : 0.0) + (p.e.utgt ? 1.0 : 0.0)) * b * nr * nout : 0.0;
+        sfde_prof_end(c, slot, 2, 2.0 * b * nr * nc * nout,
+                      esz * (b * nr * nc + b * nr * nout + (double)nc * nout + extra));
+        sfde_count_launch(c);
+    }
     SFDE_CUDA(cudaGetLastError());
     return SFDE_OK;
 }
@@ -200,6 +222,18 @@ sfde_status launch(const CUtensorMap& A, const CUtensorMap& B, const TcArgs& p, 
 }  // namespace
 
 int sfde_tc_tile_n(int cout) { return cout <= 256 ? cout : (cout % 256 == 0 ? 256 : 128); }
+
+// Raise the dynamic shared-memory limit of every instantiation up front (outside any stream capture).
+sfde_status sfde_tc_prepare() {
+    const int bytes = (int)smem_bytes(256);
+    SFDE_CUDA(cudaFuncSetAttribute(k_tc_slice_gemm<0, __nv_bfloat16, TC_EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SFDE_CUDA(cudaFuncSetAttribute(k_tc_slice_gemm<0, __nv_bfloat16, TC_EPI_SCALE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SFDE_CUDA(cudaFuncSetAttribute(k_tc_slice_gemm<0, __nv_bfloat16, TC_EPI_FINAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SFDE_CUDA(cudaFuncSetAttribute(k_tc_slice_gemm<1, float, TC_EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SFDE_CUDA(cudaFuncSetAttribute(k_tc_slice_gemm<1, float, TC_EPI_SCALE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SFDE_CUDA(cudaFuncSetAttribute(k_tc_slice_gemm<1, float, TC_EPI_FINAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    return SFDE_OK;
+}
 
 sfde_status sfde_tc_map_slices(CUtensorMap* map, const void* base, int esz, int K, int R, int ds,
                                long long nslices) {
@@ -229,20 +263,21 @@ sfde_status sfde_tc_map_matrix(CUtensorMap* map, const void* matT, int esz, int 
     return r == CUDA_SUCCESS ? SFDE_OK : SFDE_EINVAL;
 }
 
-sfde_status sfde_tc_gemm(int kind, int epi, const CUtensorMap& A, const CUtensorMap& B, const TcArgs& p,
-                         cudaStream_t s) {
+sfde_status sfde_tc_gemm(sfde_ctx* c, int kind, int epi, const CUtensorMap& A, const CUtensorMap& B, const TcArgs& p,
+                         cudaStream_t s, int nr, int nc, int nout) {
     if (kind == 0) {
-        if (epi == TC_EPI_STORE) return launch<0, __nv_bfloat16, TC_EPI_STORE>(A, B, p, s);
-        if (epi == TC_EPI_SCALE) return launch<0, __nv_bfloat16, TC_EPI_SCALE>(A, B, p, s);
-        return launch<0, __nv_bfloat16, TC_EPI_FINAL>(A, B, p, s);
+        if (epi == TC_EPI_STORE) return launch<0, __nv_bfloat16, TC_EPI_STORE>(c, A, B, p, s, nr, nc, nout);
+        if (epi == TC_EPI_SCALE) return launch<0, __nv_bfloat16, TC_EPI_SCALE>(c, A, B, p, s, nr, nc, nout);
+        return launch<0, __nv_bfloat16, TC_EPI_FINAL>(c, A, B, p, s, nr, nc, nout);
     }
-    if (epi == TC_EPI_STORE) return launch<1, float, TC_EPI_STORE>(A, B, p, s);
-    if (epi == TC_EPI_SCALE) return launch<1, float, TC_EPI_SCALE>(A, B, p, s);
-    return launch<1, float, TC_EPI_FINAL>(A, B, p, s);
+    if (epi == TC_EPI_STORE) return launch<1, float, TC_EPI_STORE>(c, A, B, p, s, nr, nc, nout);
+    if (epi == TC_EPI_SCALE) return launch<1, float, TC_EPI_SCALE>(c, A, B, p, s, nr, nc, nout);
+    return launch<1, float, TC_EPI_FINAL>(c, A, B, p, s, nr, nc, nout);
 }
 
 extern "C" sfde_status sfde_debug_tc_gemm(int kind, const void* X, long long nslices, int s0, int ds, int batch,
-                                         int R, int C, const void* MatT, int Cout, void* Out, int* err_out) {
+                                         int R, int C, const void* MatT, int Cout, void* Out, int* err_out,
+                                         int reps, float* ms_out) {
     if ((kind != 0 && kind != 1) || !X || !MatT || !Out || batch < 1 || R < 32 || R % 32 || C < 1 ||
         Cout < 32 || Cout % 32 || ds < 1 || s0 < 0 || s0 + (long long)(batch - 1) * ds >= nslices)
         return SFDE_EINVAL;
@@ -258,8 +293,22 @@ extern "C" sfde_status sfde_debug_tc_gemm(int kind, const void* X, long long nsl
     p.R = R; p.C = C; p.Cout = Cout; p.batch = batch; p.BN = sfde_tc_tile_n(Cout); p.s0 = s0; p.ds = ds;
     p.out = Out; p.out_stride = (long long)Cout * R;
     p.err = err;
-    sfde_status st = sfde_tc_gemm(kind, TC_EPI_STORE, A, B, p, nullptr);
+    sfde_status st = sfde_tc_gemm(nullptr, kind, TC_EPI_STORE, A, B, p, nullptr);
     cudaError_t e = cudaDeviceSynchronize();
+    if (st == SFDE_OK && e == cudaSuccess && ms_out && reps > 0) {
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, nullptr);
+        for (int i = 0; i < reps && st == SFDE_OK; ++i) st = sfde_tc_gemm(nullptr, kind, TC_EPI_STORE, A, B, p, nullptr);
+        cudaEventRecord(e1, nullptr);
+        e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *ms_out = ms / reps;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
     int herr = 0;
     cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
     cudaFree(err);

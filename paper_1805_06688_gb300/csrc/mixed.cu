@@ -99,6 +99,10 @@ struct SfdeMixed {
     size_t ws = 0;
     int* err = nullptr;
     std::vector<MapEntry> maps;
+    // captured inner solve (CUDA graph) and what it contains
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t inner_exec = nullptr;
+    long long inner_key = -1, inner_launches = 0, inner_steps = 0;
 };
 
 void sfde_free_mixed(sfde_ctx* c) {
@@ -111,6 +115,8 @@ void sfde_free_mixed(sfde_ctx* c) {
         cudaFree(L.u); cudaFree(L.g);
     }
     cudaFree(M->T1); cudaFree(M->T2); cudaFree(M->T3); cudaFree(M->err);
+    if (M->inner_exec) cudaGraphExecDestroy(M->inner_exec);
+    if (M->cap) cudaStreamDestroy(M->cap);
     delete M;
     c->mixed = nullptr;
 }
@@ -127,13 +133,14 @@ sfde_status lp_copy(sfde_ctx* c, const double* src, void** dst, size_t n, int ki
     return SFDE_OK;
 }
 
-sfde_status map_for(SfdeMixed* M, const void* ptr, int R, int C, int ds, long long ns, const CUtensorMap** out) {
-    for (auto& e : M->maps)
-        if (e.ptr == ptr && e.R == R && e.C == C && e.ds == ds && e.ns == ns) { *out = &e.map; return SFDE_OK; }
+// Returns a copy: the cache vector may grow (and move its elements) on a later lookup.
+sfde_status map_for(SfdeMixed* M, const void* ptr, int R, int C, int ds, long long ns, CUtensorMap* out) {
+    for (const auto& e : M->maps)
+        if (e.ptr == ptr && e.R == R && e.C == C && e.ds == ds && e.ns == ns) { *out = e.map; return SFDE_OK; }
     MapEntry e{ptr, R, C, ds, ns, {}};
     SFDE_TRY(sfde_tc_map_slices(&e.map, ptr, M->esz, C, R, ds, ns));
     M->maps.push_back(e);
-    *out = &M->maps.back().map;
+    *out = e.map;
     return SFDE_OK;
 }
 
@@ -145,6 +152,7 @@ sfde_status setup_mixed(sfde_ctx* c, int kind, int m, int max_levels, int min_co
     M = new SfdeMixed();
     c->mixed = M;
     M->kind = kind; M->esz = kind == 0 ? 2 : 4; M->m = m; M->max_levels = max_levels; M->min_coarse = min_coarse;
+    SFDE_TRY(sfde_tc_prepare());
     const int Px = c->x.P, Py = c->y.P;
     const size_t P2 = c->P2();
     SFDE_TRY(lp_copy(c, c->x.WT, &M->WTx, (size_t)Px * Px, kind));
@@ -227,7 +235,7 @@ struct LpEngine {
         int total = 0;
         for (int b0 = 0; b0 < batch; b0 += (int)M->ws) {
             const int nb = std::min<int>(batch - b0, (int)M->ws);
-            const CUtensorMap *a1, *a2, *a3, *a4;
+            CUtensorMap a1, a2, a3, a4;
             SFDE_TRY(map_for(M, src, Py, Px, ds, ns, &a1));
             SFDE_TRY(map_for(M, M->T1, Px, Py, 1, (long long)M->ws, &a2));
             SFDE_TRY(map_for(M, M->T2, Py, Px, 1, (long long)M->ws, &a3));
@@ -237,7 +245,7 @@ struct LpEngine {
             // G1: (X W_x)^T  or  (X V_x)^T
             p.R = Py; p.C = Px; p.Cout = Px; p.BN = sfde_tc_tile_n(Px); p.s0 = src0 + b0 * ds; p.ds = ds;
             p.out = M->T1; p.out_stride = P2l;
-            SFDE_TRY(sfde_tc_gemm(M->kind, TC_EPI_STORE, *a1, solve ? M->mVTx : M->mWTx, p, c->stream));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a1, solve ? M->mVTx : M->mWTx, p, c->stream, c->y.n, c->x.n, c->x.n));
             // G2: modal scaling
             TcArgs q{};
             q.batch = nb; q.err = M->err;
@@ -245,13 +253,13 @@ struct LpEngine {
             q.out = M->T2; q.out_stride = P2l;
             q.e.lamx = M->lamx; q.e.lamy = M->lamy; q.e.kx = (float)c->kx; q.e.ky = (float)c->ky;
             q.e.dt = dt; q.e.n0 = n0 + b0 * dn; q.e.dn = dn; q.e.scheme = solve ? SCHEME_SOLVE : sch;
-            SFDE_TRY(sfde_tc_gemm(M->kind, TC_EPI_SCALE, *a2, solve ? M->mVTy : M->mWTy, q, c->stream));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_SCALE, a2, solve ? M->mVTy : M->mWTy, q, c->stream, c->x.n, c->y.n, c->y.n));
             // G3: (C V_x^T)^T
             TcArgs r{};
             r.batch = nb; r.err = M->err;
             r.R = Py; r.C = Px; r.Cout = Px; r.BN = sfde_tc_tile_n(Px); r.s0 = 0; r.ds = 1;
             r.out = M->T3; r.out_stride = P2l;
-            SFDE_TRY(sfde_tc_gemm(M->kind, TC_EPI_STORE, *a3, M->mVx, r, c->stream));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a3, M->mVx, r, c->stream, c->y.n, c->x.n, c->x.n));
             // G4: (T3 V_y^T)^T + g - u_target
             TcArgs f{};
             f.batch = nb; f.err = M->err;
@@ -264,9 +272,8 @@ struct LpEngine {
             const int gx = (int)(((long long)nb * Px + 127) / 128), gy = Py / f.BN;
             if (partial && (size_t)(total + gx * gy) > c->partial_cap) return SFDE_EINVAL;
             f.e.partial = partial ? partial + total : nullptr;
-            SFDE_TRY(sfde_tc_gemm(M->kind, TC_EPI_FINAL, *a4, M->mVy, f, c->stream));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_FINAL, a4, M->mVy, f, c->stream, c->x.n, c->y.n, c->y.n));
             total += gx * gy;
-            sfde_count_launch(c, 4);
         }
         steps += batch;
         if (npart) *npart = total;
@@ -345,6 +352,38 @@ struct LpEngine {
     }
 };
 
+// Steps 2-4 of one outer iteration, queued on c->stream without any host synchronisation:
+// g_n = S_n^{-1} rho_n (rho already in g_0[1..N]), K V-cycles on E_n = Psi_n E_{n-1} + g_n from
+// E = 0 (the last one ends after its relaxation, so E is F-consistent), then U += E in FP64.
+sfde_status enqueue_inner(sfde_ctx* c, SfdeMixed* M, LpEngine& E, double* U, int kind, int K) {
+    LpLevel& L0 = M->lev[0];
+    const size_t P2 = c->P2();
+    SFDE_CUDA(cudaMemsetAsync(L0.g, 0, P2 * M->esz, c->stream));
+    SFDE_TRY(E.step(L0.g, L0.nalloc, 1, 1, c->nt, true, SCHEME_SOLVE, c->dt0, 1, 1, E.slice(L0.g, 1), 1,
+                    nullptr, nullptr, nullptr, nullptr));
+    SFDE_CUDA(cudaMemsetAsync(L0.u, 0, P2 * M->esz * L0.nalloc, c->stream));
+    if (E.L == 1) {
+        SFDE_TRY(E.coarsest(0));
+    } else {
+        for (int k = 1; k <= K; ++k) {
+            SFDE_TRY(E.relaxation(0));
+            if (k == K) break;
+            SFDE_TRY(E.residual(0, nullptr, nullptr));
+            SFDE_CUDA(cudaMemsetAsync(M->lev[1].u, 0, P2 * M->esz * (M->lev[1].N + 1), c->stream));
+            SFDE_TRY(E.solve(1));
+            SFDE_TRY(E.correct(0));
+        }
+    }
+    const size_t n = P2 * (size_t)c->nt;
+    if (kind == 0)
+        k_add_correction<__nv_bfloat16><<<grid_for(n), 256, 0, c->stream>>>(U + P2, (const __nv_bfloat16*)E.slice(L0.u, 1), n);
+    else
+        k_add_correction<float><<<grid_for(n), 256, 0, c->stream>>>(U + P2, (const float*)E.slice(L0.u, 1), n);
+    sfde_count_launch(c);
+    SFDE_CUDA(cudaGetLastError());
+    return SFDE_OK;
+}
+
 sfde_status check_err(SfdeMixed* M, cudaStream_t s) {
     int h = 0;
     SFDE_CUDA(cudaMemcpyAsync(&h, M->err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -362,15 +401,22 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
     double* U = nullptr;
     SFDE_TRY(sfde_level0(c, &U));
     const size_t P2 = c->P2();
-    const int coarse = (o->coarse == SFDE_COARSE_CN) ? SFDE_COARSE_CN : SFDE_COARSE_BE;
+    int coarse = SFDE_COARSE_BE;
+    double tub = 0.0;
+    SFDE_TRY(sfde_choose_coarse(c, o->m, o->coarse, &coarse, &tub));
     LpEngine E{c, M, o->m, L, o->relax, coarse == SFDE_COARSE_CN ? SCHEME_CN : SCHEME_BE};
-    const double inner_tol = kind == 0 ? 2e-2 : 5e-3;
-    const int max_inner = 30;
+    // inner V-cycles per refinement step: enough for the inner error to reach the low-precision
+    // floor (about 2e-2 BF16, 3e-3 TF32) at MGRIT contraction ~0.3 per V-cycle
+    const int K = o->inner_cycles > 0 ? o->inner_cycles : (kind == 0 ? 4 : 5);
+    // the inner solve is captured once as a CUDA graph and replayed; eager while kernels are timed
+    const bool use_graph = !c->prof.on;
+    const long long key = ((long long)K << 8) | ((long long)E.scheme << 4) | (long long)o->relax;
+    long long graph_steps = 0;
 
     mgrit_stats S{};
     S.levels = L;
     S.coarse_used = coarse;
-    S.tub = NAN;
+    S.tub = tub;
     SFDE_CUDA(cudaEventRecord(c->ev0, c->stream));
     SFDE_CUDA(cudaMemcpyAsync(U, c->U0, sizeof(double) * P2, cudaMemcpyDeviceToDevice, c->stream));
     if (o->init_seed) {
@@ -396,41 +442,39 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
         S.iters = it;
         if (!isfinite(nrm)) { rc = SFDE_ENOCONV; break; }
         if (nrm <= std::max(o->rel_tol * S.res0, o->abs_tol)) { S.converged = 1; break; }
-        // 2. g_n = S_n^{-1} rho_n in place (four tensor-core products per time point)
-        SFDE_CUDA(cudaMemsetAsync(L0.g, 0, P2 * M->esz, c->stream));
-        SFDE_TRY(E.step(L0.g, L0.nalloc, 1, 1, c->nt, true, SCHEME_SOLVE, c->dt0, 1, 1, E.slice(L0.g, 1), 1,
-                        nullptr, nullptr, nullptr, nullptr));
-        // 3. inner V-cycles on E_n = Psi_n E_{n-1} + g_n, E = 0 initially
-        SFDE_CUDA(cudaMemsetAsync(L0.u, 0, P2 * M->esz * L0.nalloc, c->stream));
-        if (L == 1) {
-            SFDE_TRY(E.coarsest(0));
-            ++inner_total;
-        } else {
-            double first = -1.0;
-            for (int k = 1; k <= max_inner; ++k) {
-                SFDE_TRY(E.relaxation(0));
-                int npi = 0;
-                SFDE_TRY(E.residual(0, c->partial, &npi));
-                double q2 = 0.0;
-                SFDE_TRY(sfde_reduce_partials(c, npi, &q2));
-                ++inner_total;
-                const double q = sqrt(q2);
-                if (first < 0) first = q;
-                if (!(q > inner_tol * first) || !isfinite(q) || k == max_inner) break;
-                SFDE_CUDA(cudaMemsetAsync(M->lev[1].u, 0, P2 * M->esz * (M->lev[1].N + 1), c->stream));
-                SFDE_TRY(E.solve(1));
-                SFDE_TRY(E.correct(0));
+        // 2-4: correction right-hand side, inner V-cycles, U += E (no host synchronisation inside)
+        if (use_graph) {
+            if (!M->inner_exec || M->inner_key != key) {
+                if (M->inner_exec) { cudaGraphExecDestroy(M->inner_exec); M->inner_exec = nullptr; }
+                if (!M->cap) SFDE_CUDA(cudaStreamCreateWithFlags(&M->cap, cudaStreamNonBlocking));
+                cudaStream_t user = c->stream;
+                const long long before = c->prof.launches;
+                SFDE_CUDA(cudaStreamBeginCapture(M->cap, cudaStreamCaptureModeThreadLocal));
+                c->stream = M->cap;
+                const sfde_status cs = enqueue_inner(c, M, E, U, kind, K);
+                c->stream = user;
+                cudaGraph_t graph = nullptr;
+                const cudaError_t ce = cudaStreamEndCapture(M->cap, &graph);
+                if (cs != SFDE_OK) { if (graph) cudaGraphDestroy(graph); return cs; }
+                SFDE_CUDA(ce);
+                const cudaError_t ie = cudaGraphInstantiate(&M->inner_exec, graph, 0);
+                cudaGraphDestroy(graph);
+                SFDE_CUDA(ie);
+                M->inner_key = key;
+                M->inner_launches = c->prof.launches - before;
+                M->inner_steps = E.steps;
+                c->prof.launches = before;
+                E.steps = 0;
             }
+            SFDE_CUDA(cudaGraphLaunch(M->inner_exec, c->stream));
+            sfde_count_launch(c, (int)M->inner_launches);
+            graph_steps += M->inner_steps;
+        } else {
+            SFDE_TRY(enqueue_inner(c, M, E, U, kind, K));
         }
-        // 4. U += E (FP64)
-        const size_t n = P2 * (size_t)c->nt;
-        if (kind == 0)
-            k_add_correction<__nv_bfloat16><<<grid_for(n), 256, 0, c->stream>>>(U + P2, (const __nv_bfloat16*)E.slice(L0.u, 1), n);
-        else
-            k_add_correction<float><<<grid_for(n), 256, 0, c->stream>>>(U + P2, (const float*)E.slice(L0.u, 1), n);
-        sfde_count_launch(c);
-        SFDE_CUDA(cudaGetLastError());
+        inner_total += (L == 1) ? 1 : K;
     }
+    E.steps += graph_steps;
     if (!S.converged && rc == SFDE_OK) rc = SFDE_ENOCONV;
     SFDE_CUDA(cudaEventRecord(c->ev1, c->stream));
     SFDE_CUDA(cudaEventSynchronize(c->ev1));

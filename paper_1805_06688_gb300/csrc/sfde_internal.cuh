@@ -52,11 +52,14 @@ struct SfdeLevel {
 struct SfdeProf {
     bool on = false;
     static const int CAP = 512;
+    static const int NCLS = SFDE_PROF_CLASSES;
     cudaEvent_t ev[2 * CAP] = {};
     double flops[CAP] = {}, bytes[CAP] = {};
+    int cls[CAP] = {};
     int head = 0, count = 0;
-    long long launches = 0, gemm_launches = 0;
-    double ms = 0, tot_flops = 0, tot_bytes = 0;
+    long long launches = 0;
+    long long n[NCLS] = {};
+    double ms[NCLS] = {}, tot_flops[NCLS] = {}, tot_bytes[NCLS] = {};
 };
 
 struct sfde_ctx {
@@ -144,19 +147,22 @@ struct TcArgs {
 };
 
 int sfde_tc_tile_n(int cout);
+sfde_status sfde_tc_prepare();
 sfde_status sfde_tc_map_slices(CUtensorMap* map, const void* base, int esz, int K, int R, int ds, long long nslices);
 sfde_status sfde_tc_map_matrix(CUtensorMap* map, const void* matT, int esz, int K, int N);
-sfde_status sfde_tc_gemm(int kind, int epi, const CUtensorMap& A, const CUtensorMap& B, const TcArgs& p,
-                         cudaStream_t s);
+// c may be NULL (no accounting); nr, nc, nout: unpadded extents of one slice product
+sfde_status sfde_tc_gemm(sfde_ctx* c, int kind, int epi, const CUtensorMap& A, const CUtensorMap& B, const TcArgs& p,
+                         cudaStream_t s, int nr = 0, int nc = 0, int nout = 0);
 
 // ---- MGRIT engine (mgrit.cu)
 sfde_status sfde_mgrit_fp64(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st);
 sfde_status sfde_seq_fp64(sfde_ctx* c, double* seconds);
 sfde_status sfde_ensure_workspace(sfde_ctx* c, size_t slices);
+sfde_status sfde_choose_coarse(sfde_ctx* c, int m, int requested, int* coarse, double* tub);
 
 // ---- kernel accounting (api.cu)
 int sfde_prof_begin(sfde_ctx* c);                               // slot or -1 when timing is off
-void sfde_prof_end(sfde_ctx* c, int slot, double flops, double bytes);
+void sfde_prof_end(sfde_ctx* c, int slot, int cls, double flops, double bytes);
 inline void sfde_count_launch(sfde_ctx* c, int n = 1) { c->prof.launches += n; }
 
 // ---- helpers (api.cu)

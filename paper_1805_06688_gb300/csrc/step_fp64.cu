@@ -42,7 +42,7 @@ struct GemmParams {
     const double* U;           // FP64 iterate, slice n at U + n * P2
     const double* bxn; const double* byn;   // nodal load factors (padded)
     double hx, hy;
-    int Px, Py;
+    int Px, Py, nx, ny;
     void* rout;                // residual output (BF16 or FP32), slice b at rout + b * out_stride
 };
 
@@ -178,7 +178,9 @@ __global__ void __launch_bounds__(256) k_slice_gemm_fp64(GemmParams p) {
                 double f = 0.0;
                 for (int q = 0; q < p.rank; ++q)
                     f += p.time_w[(size_t)(tn - 1) * p.rank + q] * p.byn[(size_t)q * p.Py + j] * p.bxn[(size_t)q * p.Px + i];
-                const double rho = f + mass - tau * stiff;
+                // padded rows/columns are not unknowns: the stencils above reach one past the last
+                // interior node, so the residual is defined as zero there
+                const double rho = (i < p.nx && j < p.ny) ? f + mass - tau * stiff : 0.0;
                 sq += rho * rho;
                 using OT = typename ResidOut<EPI>::T;
                 store_as((OT*)p.rout + b * p.out_stride + o, rho);
@@ -229,7 +231,7 @@ void launch_T(sfde_ctx* c, int T, const GemmParams& p, int nr, int nc, int nout)
     else if (T == 32) k_slice_gemm_fp64<32, EPI><<<grid, 256, 0, c->stream>>>(p);
     else k_slice_gemm_fp64<16, EPI><<<grid, 256, 0, c->stream>>>(p);
     const double b = p.batch;
-    sfde_prof_end(c, slot, 2.0 * b * nr * nc * nout,
+    sfde_prof_end(c, slot, (EPI == EPI_RESID_BF16 || EPI == EPI_RESID_F32 || p.X2) ? 1 : 0, 2.0 * b * nr * nc * nout,
                   8.0 * (b * nr * nc + b * nr * nout + (double)nc * nout + (EPI == EPI_FINAL && p.utgt ? b * nr * nout : 0.0)));
     sfde_count_launch(c);
 }
@@ -395,6 +397,7 @@ sfde_status sfde_residual_fp64(sfde_ctx* c, const double* U, int n_first, int co
         q.kx = c->kx; q.ky = c->ky; q.dt = c->dt0; q.n0 = n0;
         q.rank = c->rank; q.time_w = c->time_w; q.bxn = c->bxn; q.byn = c->byn;
         q.t1 = c->T1; q.U = U; q.hx = c->x.h; q.hy = c->y.h; q.Px = Px; q.Py = Py;
+        q.nx = c->x.n; q.ny = c->y.n;
         q.rout = (char*)rout + (size_t)b0 * rout_stride * esz;
         const int T = choose_tile((long long)nb * Px, Py, pmin);
         const long long ctas = (((long long)nb * Px + T - 1) / T) * (Py / T);

@@ -26,9 +26,10 @@ def run(kind, X, s0, ds, batch, MatT):
     L = sfde.lib()
     L.sfde_debug_tc_gemm.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                     ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
+                                     ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
     st = L.sfde_debug_tc_gemm(kind, X.data_ptr(), nslices, s0, ds, batch, R, C, MatT.data_ptr(), Cout,
-                              out.data_ptr(), ctypes.byref(err))
+                              out.data_ptr(), ctypes.byref(err), 0, None)
     assert st == 0, (sfde.sfde_strerror(st), err.value)
     return out
 
