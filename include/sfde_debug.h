@@ -24,6 +24,27 @@ sfde_status sfde_debug_tc_gemm(int kind, const void* X, long long nslices, int s
                                int R, int C, const void* MatT, int Cout, void* Out, int* err_out,
                                int reps, float* ms_out);
 
+/*
+ * One FP64-accurate slice GEMM on the BF16 tensor cores (error-free digit splitting):
+ *   Out[b] = (X[b] * Mat)^T,  b = 0..batch-1,  X: batch x R x K doubles, Mat: K x N doubles (row-major),
+ *   Out: batch x N x R doubles; R = 32, 64 or a multiple of 128; K, N multiples of 32, K <= 256.
+ * Device pointers; synchronous; allocates its own scratch.  Error about 2^-47 of
+ * max|X row| * max|Mat column| * K per element, the accuracy of an FP64 GEMM.
+ */
+sfde_status sfde_debug_oz_gemm(const double* X, int batch, int R, int K, const double* Mat, int N,
+                               double* Out, int* err_out);
+
+/*
+ * The FP64 space-time residual of the mixed-precision solver for a given iterate (Eq. (2.4)):
+ *   rho_n = F_n + B_n U_{n-1} - S_n U_n,  n = 1..N_t,
+ * U: (N_t+1) x N_y x N_x doubles (host or device); rho: N_t x N_y x N_x floats (host or device),
+ * rounded to TF32 as the solver stores it; *norm2 = sum of rho_n^2 accumulated in FP64 before
+ * rounding.  use_tensor_cores = 1 forms the two dense products per time point on the BF16 tensor
+ * cores by digit splitting (P_x, P_y <= 256), 0 with FP64 arithmetic.  Synchronous; allocates scratch.
+ */
+sfde_status sfde_debug_residual(sfde_ctx* ctx, const double* U, int use_tensor_cores, float* rho,
+                                double* norm2);
+
 #ifdef __cplusplus
 }
 #endif

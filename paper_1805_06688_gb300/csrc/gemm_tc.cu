@@ -32,7 +32,7 @@ template <> struct StoreT<__nv_bfloat16> {
     static __device__ __forceinline__ float to(__nv_bfloat16 v) { return __bfloat162float(v); }
 };
 template <> struct StoreT<float> {
-    static __device__ __forceinline__ float from(float v) { return v; }
+    static __device__ __forceinline__ float from(float v) { return sfde_round_tf32(v); }
     static __device__ __forceinline__ float to(float v) { return v; }
 };
 

@@ -30,7 +30,7 @@ namespace {
 
 template <typename T> __device__ __forceinline__ T to_lp(double v);
 template <> __device__ __forceinline__ __nv_bfloat16 to_lp<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
-template <> __device__ __forceinline__ float to_lp<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ float to_lp<float>(double v) { return sfde_round_tf32((float)v); }
 __device__ __forceinline__ float lp_f(__nv_bfloat16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ float lp_f(float v) { return v; }
 
@@ -103,6 +103,11 @@ struct SfdeMixed {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t inner_exec = nullptr;
     long long inner_key = -1, inner_launches = 0, inner_steps = 0;
+    // FP64-accurate residual products on the tensor cores (P <= 256)
+    bool use_oz = false;
+    OzMatrix oAx, oAy;
+    void* oz_digits = nullptr;
+    int* oz_xe = nullptr;
 };
 
 void sfde_free_mixed(sfde_ctx* c) {
@@ -116,6 +121,10 @@ void sfde_free_mixed(sfde_ctx* c) {
     }
     cudaFree(M->T1); cudaFree(M->T2); cudaFree(M->T3); cudaFree(M->err);
     if (M->inner_exec) cudaGraphExecDestroy(M->inner_exec);
+    sfde_oz_free_matrix(&M->oAx);
+    sfde_oz_free_matrix(&M->oAy);
+    cudaFree(M->oz_digits);
+    cudaFree(M->oz_xe);
     if (M->cap) cudaStreamDestroy(M->cap);
     delete M;
     c->mixed = nullptr;
@@ -205,7 +214,16 @@ sfde_status setup_mixed(sfde_ctx* c, int kind, int m, int max_levels, int min_co
     SFDE_CUDA(cudaMalloc(&M->T3, M->esz * P2 * M->ws));
     // FP64 scratch for the residual: a chunk of time points at a time
     SFDE_TRY(sfde_ensure_workspace(c, std::min<size_t>(c->nt, 128)));
-    size_t need = (size_t)c->nt * ((size_t)(c->x.P + 127) / 128) * (c->y.P / 32) + 64;
+    // products of the residual on the tensor cores (error-free digit splitting) when K <= 256
+    M->use_oz = Px <= 256 && Py <= 256;
+    if (M->use_oz) {
+        SFDE_TRY(sfde_oz_split_matrix(c->x.A, Px, Px, &M->oAx, c->stream));
+        SFDE_TRY(sfde_oz_split_matrix(c->y.A, Py, Py, &M->oAy, c->stream));
+        const int Pm = std::max(Px, Py);
+        SFDE_CUDA(cudaMalloc(&M->oz_digits, sfde_oz_digit_bytes(Pm, Pm, (int)c->ws_slices)));
+        SFDE_CUDA(cudaMalloc(&M->oz_xe, sizeof(int) * (size_t)Pm * c->ws_slices));
+    }
+    size_t need = (size_t)c->nt * (size_t)(c->x.P / 16) * (c->y.P / 16) + 64;
     if (c->partial_cap < need) {
         cudaFree(c->partial);
         c->partial = nullptr;
@@ -431,7 +449,11 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
     for (int it = 1; it <= o->max_iter; ++it) {
         // 1. FP64 residual of Eq. (2.4) at n = 1..N_t, stored low precision in g_0[n]
         int np = 0;
-        SFDE_TRY(sfde_residual_fp64(c, U, 1, c->nt, E.slice(L0.g, 1), (long long)P2, kind, c->partial, &np));
+        if (M->use_oz)
+            SFDE_TRY(sfde_residual_oz(c, U, 1, c->nt, E.slice(L0.g, 1), (long long)P2, kind, c->partial, &np,
+                                      M->oAx, M->oAy, M->oz_digits, M->oz_xe, M->err));
+        else
+            SFDE_TRY(sfde_residual_fp64(c, U, 1, c->nt, E.slice(L0.g, 1), (long long)P2, kind, c->partial, &np));
         double r2 = 0.0;
         SFDE_TRY(sfde_reduce_partials(c, np, &r2));
         SFDE_TRY(check_err(M, c->stream));

@@ -1,0 +1,509 @@
+// FP64-accurate slice GEMM on the BF16 tensor cores by error-free operand splitting (the splitting
+// scheme of Ozaki, Ogita, Oishi and Rump, restated here for tcgen05).
+//
+// Out_b = (X_b Mat)^T with FP64 X_b (R x K, row-major) and a fixed FP64 Mat (K x N), as the other
+// slice GEMMs.  Each row r of X_b is scaled by 2^{-e_r} (e_r from frexp of the row's max |x|) and
+// written as six signed base-256 digits:  x = 2^{e_r} sum_{p=1..6} d_p 2^{-8p} + O(2^{e_r - 49}),
+// |d_1| <= 256, |d_p| <= 128 (p >= 2), all exact in BF16.  Mat is split the same way per column n.
+// Then  (X Mat)[r][n] = 2^{e_r + e_n} sum_{p,q} 2^{-8(p+q)} sum_k d_p[r][k] d_q[k][n],  and the
+// terms with p + q <= 7 (21 digit products) are kept: the dropped ones and the digit truncation are
+// below 2^{-47} of 2^{e_r + e_n} K, the accuracy of an FP64 GEMM.
+//
+// Every digit product is an integer matrix product.  With K <= 256 a single product is at most
+// 256 * 2^16 = 2^24 in magnitude, and the products are grouped into 12 FP32 TMEM accumulators so
+// that every partial sum stays an integer of magnitude <= 2^24: FP32 accumulation is then exact.
+// The epilogue converts the 12 accumulators to integers, combines them in two int64 words
+// (digit weights 2^{-16..-40} and 2^{-48..-56}) and converts to FP64 once per output.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include <cudaTypedefs.h>
+
+#include "sfde_internal.cuh"
+#include "tc_common.cuh"
+
+namespace {
+
+constexpr int S = SFDE_OZ_DIGITS;      // 6 digits per operand
+constexpr int BM = 128, BN = 32, KC = 64;
+constexpr int XTILE = BM * KC * 2;     // 16 KB: one digit plane of the 128-row tile, one K chunk
+constexpr int MTILE = BN * KC * 2;     // 4 KB
+constexpr int STAGE = S * (XTILE + MTILE);
+constexpr int NACC = 12;
+constexpr int TMEM_COLS = 512;
+
+// accumulator a -> digit sum d = p + q of its products, and the product list (p, q, a)
+__constant__ int c_acc_d[NACC] = {2, 3, 4, 4, 5, 5, 6, 6, 6, 7, 7, 7};
+constexpr int NPROD = 21;
+__constant__ int c_prod[NPROD][3] = {
+    {1, 1, 0},
+    {1, 2, 1}, {2, 1, 1},
+    {1, 3, 2}, {2, 2, 2}, {3, 1, 3},
+    {1, 4, 4}, {2, 3, 4}, {3, 2, 5}, {4, 1, 5},
+    {1, 5, 6}, {2, 4, 6}, {3, 3, 7}, {4, 2, 7}, {5, 1, 8},
+    {1, 6, 9}, {2, 5, 9}, {3, 4, 10}, {4, 3, 10}, {5, 2, 11}, {6, 1, 11},
+};
+
+struct OzArgs {
+    int R, K, N, batch;          // X slice R x K (digits in planes of nslices x R x K), Mat K x N
+    const int* xe;               // row exponents, batch x R
+    const int* me;               // column exponents, N
+    double* out; long long out_stride;   // Out_b = (X_b Mat)^T, N x R per slice
+    int* err;
+};
+
+__device__ __forceinline__ double pow2(int e) {  // exact 2^e for normal range
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+__global__ void __launch_bounds__(128, 1)
+k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapM, OzArgs p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sX = smem;                       // S planes x 16 KB
+    uint8_t* sM = smem + S * XTILE;           // S planes x 4 KB
+    uint64_t* full = (uint64_t*)(smem + STAGE);
+    uint64_t* empty = full + 1;
+    uint64_t* accf = full + 2;
+    uint32_t* tmem_slot = (uint32_t*)(full + 3);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long m0 = (long long)blockIdx.x * BM;
+    const int n0 = blockIdx.y * BN;
+    const long long Mtot = (long long)p.batch * p.R;
+    const int nchunks = (p.K + KC - 1) / KC;
+
+    if (threadIdx.x == 0) {
+        tc::mbar_init(full, 1);
+        tc::mbar_init(empty, 1);
+        tc::mbar_init(accf, 1);
+        tc::mbar_fence_init();
+        tc::prefetch_tmap(&mapX);
+        tc::prefetch_tmap(&mapM);
+    }
+    if (warp == 0) tc::tmem_alloc(tmem_slot, TMEM_COLS);
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int b0 = (int)(m0 / p.R), r0 = (int)(m0 % p.R);
+    bool ok = true;
+    if (warp == 0 && lane == 0) {
+        for (int c = 0; c < nchunks && ok; ++c) {
+            if (c > 0) ok = tc::mbar_wait(empty, (uint32_t)(c - 1) & 1u, p.err, tc::ERR_WAIT_EMPTY);
+            if (!ok) break;
+            tc::mbar_arrive_expect_tx(full, (uint32_t)STAGE);
+            for (int d = 0; d < S; ++d) {
+                tc::tma_load_4d(sX + d * XTILE, &mapX, full, c * KC, r0, b0, d);
+                tc::tma_load_3d(sM + d * MTILE, &mapM, full, c * KC, n0, d);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t idesc = tc::idesc_f32acc(1u, BM, BN);
+        for (int c = 0; c < nchunks && ok; ++c) {
+            ok = tc::mbar_wait(full, (uint32_t)c & 1u, p.err, tc::ERR_WAIT_FULL);
+            if (!ok) break;
+            tc::tc_fence_after();
+            for (int i = 0; i < NPROD; ++i) {
+                const int dp = c_prod[i][0] - 1, dq = c_prod[i][1] - 1, a = c_prod[i][2];
+                // the first product of an accumulator in the first chunk overwrites it
+                const bool first = (c == 0) && (i == 0 || c_prod[i - 1][2] != a);
+#pragma unroll
+                for (int kk = 0; kk < KC / 16; ++kk) {
+                    const uint64_t ad = tc::smem_desc_sw128(sX + dp * XTILE + kk * 32);
+                    const uint64_t bd = tc::smem_desc_sw128(sM + dq * MTILE + kk * 32);
+                    tc::mma<0>(tmem + (uint32_t)(a * BN), ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+                }
+            }
+            tc::mma_commit(empty);
+        }
+        if (ok) tc::mma_commit(accf);
+    }
+
+    const bool acc_ok = __all_sync(0xffffffffu, tc::mbar_wait(accf, 0, p.err, tc::ERR_WAIT_ACC));
+    tc::tc_fence_after();
+    if (acc_ok) {
+        const long long m = m0 + warp * 32 + lane;
+        const bool valid = m < Mtot;
+        // z_hi in units of 2^-40 (digit sums d = 2..5), z_lo in units of 2^-56 (d = 6, 7)
+        long long zhi[BN], zlo[BN];
+#pragma unroll
+        for (int j = 0; j < BN; ++j) { zhi[j] = 0; zlo[j] = 0; }
+#pragma unroll 1
+        for (int a = 0; a < NACC; ++a) {
+            uint32_t v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * BN), v);
+            const int d = c_acc_d[a];
+#pragma unroll
+            for (int j = 0; j < BN; ++j) {
+                const long long s = (long long)__float2ll_rn(__uint_as_float(v[j]));  // exact integer
+                if (d <= 5) zhi[j] += s * (1ll << (8 * (5 - d)));
+                else zlo[j] += s * (1ll << (8 * (7 - d)));
+            }
+        }
+        if (valid) {
+            const long long b = m / p.R;
+            const int r = (int)(m % p.R);
+            const int er = p.xe[b * p.R + r];
+            double* out = p.out + b * p.out_stride + r;
+#pragma unroll
+            for (int j = 0; j < BN; ++j) {
+                const int n = n0 + j;
+                const int e = er + p.me[n];
+                const double y = (double)zhi[j] * pow2(e - 40) + (double)zlo[j] * pow2(e - 56);
+                out[(long long)n * p.R] = y;
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// Row splitting: X_b (+ X2_b) -> S digit planes (BF16) and one exponent per row.  One warp per row.
+__global__ void k_oz_split_rows(const double* X, const double* X2, long long x_stride, int R, int K, int nrows,
+                                __nv_bfloat16* digits, long long plane, int* xe) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= nrows) return;
+    const long long b = w / R, r = w % R;
+    const double* x = X + b * x_stride + r * K;
+    const double* x2 = X2 ? X2 + b * x_stride + r * K : nullptr;
+    double mx = 0.0;
+    for (int k = lane; k < K; k += 32) {
+        const double v = x2 ? x[k] + x2[k] : x[k];
+        mx = fmax(mx, fabs(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);          // mx = f 2^e, f in [0.5, 1)
+    if (lane == 0) xe[w] = e;
+    const double sc = pow2(-e);
+    __nv_bfloat16* out = digits + (long long)w * K;
+    for (int k = lane; k < K; k += 32) {
+        double v = (x2 ? x[k] + x2[k] : x[k]) * sc;  // in (-1, 1), exact scaling
+#pragma unroll
+        for (int d = 0; d < S; ++d) {
+            v *= 256.0;
+            const double q = rint(v);
+            v -= q;                                   // exact: |v| <= 1/2
+            out[(long long)d * plane + k] = __float2bfloat16_rn((float)q);   // |q| <= 256, exact
+        }
+    }
+}
+
+// Column splitting of the fixed matrix Mat (K x N, row-major) -> digits stored K-major per column
+// (planes of N x K) and one exponent per column.  One warp per column.
+__global__ void k_oz_split_cols(const double* Mat, int K, int N, __nv_bfloat16* digits, int* me) {
+    const int n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (n >= N) return;
+    double mx = 0.0;
+    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(Mat[(size_t)k * N + n]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);
+    if (lane == 0) me[n] = e;
+    const double sc = pow2(-e);
+    for (int k = lane; k < K; k += 32) {
+        double v = Mat[(size_t)k * N + n] * sc;
+#pragma unroll
+        for (int d = 0; d < S; ++d) {
+            v *= 256.0;
+            const double q = rint(v);
+            v -= q;
+            digits[(size_t)d * N * K + (size_t)n * K + k] = __float2bfloat16_rn((float)q);
+        }
+    }
+}
+
+// rho for one 32 x 32 tile of slice b (time n = n0 + b):
+//   rho = F_n + M_h (U_{n-1} - U_n) - tau_n (K_x M_y Y1 + K_y Y2'),  Y1 = V A_x given transposed in T1,
+//   Y2' = A_y V M_x given in T3 (row j, column i), V = U_{n-1} + U_n;  zero outside the interior nodes.
+// Writes rho in BF16/FP32 (kind 0/1) and one sum of rho^2 per block.
+template <typename OT>
+__global__ void k_resid_combine(const double* __restrict__ T1, const double* __restrict__ T3,
+                                const double* __restrict__ U, int n0, int Px, int Py, int nx, int ny, double hx,
+                                double hy, double kx, double ky, const double* __restrict__ dt, int rank,
+                                const double* __restrict__ time_w, const double* __restrict__ bxn,
+                                const double* __restrict__ byn, OT* __restrict__ rout, long long rout_stride,
+                                double* __restrict__ partial) {
+    __shared__ double t1[32][35];
+    __shared__ double red[256];
+    const size_t P2 = (size_t)Px * Py;
+    const int b = blockIdx.z, tn = n0 + b;
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    const double* T1b = T1 + (size_t)b * P2;
+    for (int ii = threadIdx.y; ii < 32; ii += blockDim.y)
+        for (int jj = threadIdx.x; jj < 34; jj += 32) {
+            const int j = j0 + jj - 1;
+            t1[ii][jj] = (j >= 0 && j < Py) ? T1b[(size_t)(i0 + ii) * Py + j] : 0.0;
+        }
+    __syncthreads();
+    const double tau = 0.5 * dt[tn - 1];
+    const double my = hy / 6.0, mx = hx / 6.0;
+    const double* Ua = U + (size_t)(tn - 1) * P2;
+    const double* Ub = U + (size_t)tn * P2;
+    const int ii = threadIdx.x, i = i0 + ii;
+    double sq = 0.0;
+    for (int jj = threadIdx.y; jj < 32; jj += blockDim.y) {
+        const int j = j0 + jj;
+        double rho = 0.0;
+        if (i < nx && j < ny) {
+            const double y1 = my * (t1[ii][jj] + 4.0 * t1[ii][jj + 1] + t1[ii][jj + 2]);
+            const double stiff = kx * y1 + ky * T3[(size_t)b * P2 + (size_t)j * Px + i];
+            double mass = 0.0;
+#pragma unroll
+            for (int a = -1; a <= 1; ++a) {
+                const int jy = j + a;
+                if (jy < 0 || jy >= ny) continue;
+                double row = 0.0;
+#pragma unroll
+                for (int cc = -1; cc <= 1; ++cc) {
+                    const int ix = i + cc;
+                    if (ix < 0 || ix >= nx) continue;
+                    const size_t e = (size_t)jy * Px + ix;
+                    row += (cc == 0 ? 4.0 : 1.0) * (Ua[e] - Ub[e]);
+                }
+                mass += (a == 0 ? 4.0 : 1.0) * row;
+            }
+            mass *= mx * my;
+            double f = 0.0;
+            for (int q = 0; q < rank; ++q)
+                f += time_w[(size_t)(tn - 1) * rank + q] * byn[(size_t)q * Py + j] * bxn[(size_t)q * Px + i];
+            rho = f + mass - tau * stiff;
+        }
+        sq += rho * rho;
+        OT* o = rout + (size_t)b * rout_stride + (size_t)j * Px + i;
+        if (sizeof(OT) == 2) *o = (OT)__float2bfloat16_rn((float)rho);
+        else *o = (OT)sfde_round_tf32((float)rho);
+    }
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    red[t] = sq;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (t < s) red[t] += red[t + s];
+        __syncthreads();
+    }
+    if (t == 0) partial[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = red[0];
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }
+    return fn;
+}
+
+constexpr size_t SMEM_BYTES = 1024 + STAGE + 256;
+
+}  // namespace
+
+sfde_status sfde_oz_split_matrix(const double* Mat, int K, int N, OzMatrix* out, cudaStream_t s) {
+    if (K > 256 || K % 32 || N % BN) return SFDE_EUNSUPPORTED;
+    out->K = K; out->N = N;
+    SFDE_CUDA(cudaMalloc(&out->digits, sizeof(__nv_bfloat16) * (size_t)S * N * K));
+    SFDE_CUDA(cudaMalloc(&out->exps, sizeof(int) * N));
+    k_oz_split_cols<<<(N * 32 + 255) / 256, 256, 0, s>>>(Mat, K, N, (__nv_bfloat16*)out->digits, out->exps);
+    SFDE_CUDA(cudaGetLastError());
+    auto fn = encode();
+    if (!fn) return SFDE_EUNSUPPORTED;
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)N, (cuuint64_t)S};
+    cuuint64_t strides[2] = {(cuuint64_t)K * 2, (cuuint64_t)N * K * 2};
+    cuuint32_t box[3] = {KC, BN, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(&out->map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, out->digits, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return SFDE_EINVAL;
+    SFDE_CUDA(cudaFuncSetAttribute(k_ozaki_slice_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    return SFDE_OK;
+}
+
+void sfde_oz_free_matrix(OzMatrix* m) {
+    cudaFree(m->digits);
+    cudaFree(m->exps);
+    m->digits = nullptr;
+    m->exps = nullptr;
+}
+
+size_t sfde_oz_digit_bytes(int R, int K, int batch) { return (size_t)S * R * K * batch * 2; }
+
+sfde_status sfde_oz_gemm(sfde_ctx* c, const double* X, const double* X2, long long x_stride, int R, int K,
+                         int batch, const OzMatrix& M, void* digits, int* xe, double* out, long long out_stride,
+                         int* err, int nr, int nc, int nout) {
+    if (K != M.K || K > 256 || R % 32 || (R > 128 && R % 128)) return SFDE_EUNSUPPORTED;
+    const long long plane = (long long)batch * R * K;
+    const int nrows = batch * R;
+    k_oz_split_rows<<<(nrows * 32 + 255) / 256, 256, 0, c->stream>>>(X, X2, x_stride, R, K, nrows,
+                                                                      (__nv_bfloat16*)digits, plane, xe);
+    sfde_count_launch(c);
+    SFDE_CUDA(cudaGetLastError());
+    auto fn = encode();
+    if (!fn) return SFDE_EUNSUPPORTED;
+    CUtensorMap mapX;
+    cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)R, (cuuint64_t)batch, (cuuint64_t)S};
+    cuuint64_t strides[3] = {(cuuint64_t)K * 2, (cuuint64_t)R * K * 2, (cuuint64_t)plane * 2};
+    cuuint32_t box[4] = {KC, (cuuint32_t)(R < BM ? R : BM), (cuuint32_t)(R < BM ? BM / R : 1), 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = fn(&mapX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, digits, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return SFDE_EINVAL;
+    OzArgs a{};
+    a.R = R; a.K = K; a.N = M.N; a.batch = batch; a.xe = xe; a.me = M.exps;
+    a.out = out; a.out_stride = out_stride; a.err = err;
+    dim3 grid((unsigned)(((long long)batch * R + BM - 1) / BM), M.N / BN);
+    const int slot = sfde_prof_begin(c);
+    k_ozaki_slice_gemm<<<grid, 128, SMEM_BYTES, c->stream>>>(mapX, M.map, a);
+    // tensor work: 21 digit products of 2 R K N flops each (counted as the FP64 product it replaces)
+    sfde_prof_end(c, slot, 1, 2.0 * batch * nr * nc * nout, 8.0 * ((double)batch * nr * nc + (double)batch * nr * nout));
+    sfde_count_launch(c);
+    SFDE_CUDA(cudaGetLastError());
+    return SFDE_OK;
+}
+
+sfde_status sfde_residual_oz(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
+                             long long rout_stride, int out_kind, double* partial, int* n_partials,
+                             const OzMatrix& Ax, const OzMatrix& Ay, void* digits, int* xe, int* err) {
+    const int Px = c->x.P, Py = c->y.P;
+    const size_t P2 = c->P2();
+    const size_t esz = out_kind == 0 ? 2 : 4;
+    int total = 0;
+    for (int b0 = 0; b0 < count; b0 += (int)c->ws_slices) {
+        const int nb = count - b0 < (int)c->ws_slices ? count - b0 : (int)c->ws_slices;
+        const int n0 = n_first + b0;
+        const double* Un = U + (size_t)n0 * P2;
+        const double* Um = U + (size_t)(n0 - 1) * P2;
+        // T1 = (V A_x)^T, V = U_n + U_{n-1} formed while splitting
+        SFDE_TRY(sfde_oz_gemm(c, Un, Um, (long long)P2, Py, Px, nb, Ax, digits, xe, c->T1, (long long)P2, err,
+                              c->y.n, c->x.n, c->x.n));
+        // T2 = (V M_x)^T, then T3 = A_y (V M_x) in row-j, column-i layout
+        sfde_launch_mass_x_transpose(Un, Um, c->T2, Px, Py, c->x.h, nb, c->stream);
+        sfde_count_launch(c);
+        SFDE_TRY(sfde_oz_gemm(c, c->T2, nullptr, (long long)P2, Px, Py, nb, Ay, digits, xe, c->T3, (long long)P2,
+                              err, c->x.n, c->y.n, c->y.n));
+        const int blocks = (Px / 32) * (Py / 32) * nb;
+        if ((size_t)(total + blocks) > c->partial_cap) return SFDE_EINVAL;
+        dim3 grid(Px / 32, Py / 32, nb), block(32, 8);
+        char* ro = (char*)rout + (size_t)b0 * rout_stride * esz;
+        if (out_kind == 0)
+            k_resid_combine<__nv_bfloat16><<<grid, block, 0, c->stream>>>(
+                c->T1, c->T3, U, n0, Px, Py, c->x.n, c->y.n, c->x.h, c->y.h, c->kx, c->ky, c->dt0, c->rank,
+                c->time_w, c->bxn, c->byn, (__nv_bfloat16*)ro, rout_stride, partial + total);
+        else
+            k_resid_combine<float><<<grid, block, 0, c->stream>>>(
+                c->T1, c->T3, U, n0, Px, Py, c->x.n, c->y.n, c->x.h, c->y.h, c->kx, c->ky, c->dt0, c->rank,
+                c->time_w, c->bxn, c->byn, (float*)ro, rout_stride, partial + total);
+        sfde_count_launch(c);
+        total += blocks;
+    }
+    SFDE_CUDA(cudaGetLastError());
+    if (n_partials) *n_partials = total;
+    return SFDE_OK;
+}
+
+extern "C" sfde_status sfde_debug_residual(sfde_ctx* c, const double* U, int use_tensor_cores, float* rho,
+                                          double* norm2) {
+    if (!c || !U || !rho || !norm2) return SFDE_EINVAL;
+    const int Px = c->x.P, Py = c->y.P;
+    if (use_tensor_cores && (Px > 256 || Py > 256)) return SFDE_EUNSUPPORTED;
+    const size_t P2 = c->P2(), n2 = (size_t)c->x.n * c->y.n;
+    double* u = nullptr;
+    SFDE_TRY(sfde_level0(c, &u));
+    SFDE_TRY(sfde_ensure_workspace(c, std::min<size_t>(c->nt, 128)));
+    const size_t need = (size_t)c->nt * (Px / 16) * (Py / 16) + 64;
+    if (c->partial_cap < need) {
+        cudaFree(c->partial);
+        c->partial = nullptr;
+        SFDE_CUDA(cudaMalloc(&c->partial, sizeof(double) * need));
+        c->partial_cap = need;
+    }
+    double* tmp = nullptr;
+    float *rp = nullptr, *ru = nullptr;
+    OzMatrix Ax, Ay;
+    void* digits = nullptr;
+    int *xe = nullptr, *err = nullptr;
+    sfde_status st = SFDE_OK;
+    int np = 0;
+    cudaError_t e;
+#define DC(x) if ((e = (x)) != cudaSuccess) { sfde_set_last_cuda_error(e, #x, __FILE__, __LINE__); st = SFDE_ECUDA; goto done; }
+    DC(cudaMalloc(&tmp, sizeof(double) * n2 * (c->nt + 1)));
+    DC(cudaMalloc(&rp, sizeof(float) * P2 * c->nt));
+    DC(cudaMalloc(&ru, sizeof(float) * n2 * c->nt));
+    DC(cudaMalloc(&err, sizeof(int)));
+    DC(cudaMemset(err, 0, sizeof(int)));
+    if ((st = sfde_copy_in(tmp, U, sizeof(double) * n2 * (c->nt + 1), c->stream)) != SFDE_OK) goto done;
+    sfde_launch_pad(tmp, u, c->y.n, c->x.n, Py, Px, c->nt + 1, c->stream);
+    if (use_tensor_cores) {
+        if ((st = sfde_oz_split_matrix(c->x.A, Px, Px, &Ax, c->stream)) != SFDE_OK) goto done;
+        if ((st = sfde_oz_split_matrix(c->y.A, Py, Py, &Ay, c->stream)) != SFDE_OK) goto done;
+        DC(cudaMalloc(&digits, sfde_oz_digit_bytes(std::max(Px, Py), std::max(Px, Py), (int)c->ws_slices)));
+        DC(cudaMalloc(&xe, sizeof(int) * (size_t)std::max(Px, Py) * c->ws_slices));
+        st = sfde_residual_oz(c, u, 1, c->nt, rp, (long long)P2, 1, c->partial, &np, Ax, Ay, digits, xe, err);
+    } else {
+        st = sfde_residual_fp64(c, u, 1, c->nt, rp, (long long)P2, 1, c->partial, &np);
+    }
+    if (st != SFDE_OK) goto done;
+    if ((st = sfde_reduce_partials(c, np, norm2)) != SFDE_OK) goto done;
+    sfde_launch_unpad_f32(rp, ru, c->y.n, c->x.n, Py, Px, c->nt, c->stream);  // one float per interior node
+    if ((st = sfde_copy_out(rho, ru, sizeof(float) * n2 * c->nt, c->stream)) != SFDE_OK) goto done;
+    DC(cudaStreamSynchronize(c->stream));
+    {
+        int herr = 0;
+        DC(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (herr) st = SFDE_ETIMEOUT;
+    }
+done:
+#undef DC
+    sfde_oz_free_matrix(&Ax);
+    sfde_oz_free_matrix(&Ay);
+    cudaFree(tmp); cudaFree(rp); cudaFree(ru); cudaFree(digits); cudaFree(xe); cudaFree(err);
+    return st;
+}
+
+extern "C" sfde_status sfde_debug_oz_gemm(const double* X, int batch, int R, int K, const double* Mat, int N,
+                                         double* Out, int* err_out) {
+    if (!X || !Mat || !Out || batch < 1 || R < 32 || R % 32 || (R > 128 && R % 128) || K < 32 || K % 32 ||
+        K > 256 || N < 32 || N % 32)
+        return SFDE_EINVAL;
+    sfde_ctx* c = new sfde_ctx();
+    OzMatrix M;
+    void* digits = nullptr;
+    int* xe = nullptr;
+    int* err = nullptr;
+    sfde_status st = SFDE_OK;
+    cudaError_t e = cudaSuccess;
+    int herr = 0;
+    st = sfde_oz_split_matrix(Mat, K, N, &M, nullptr);
+    if (st == SFDE_OK) {
+        if ((e = cudaMalloc(&digits, sfde_oz_digit_bytes(R, K, batch))) != cudaSuccess ||
+            (e = cudaMalloc(&xe, sizeof(int) * (size_t)batch * R)) != cudaSuccess ||
+            (e = cudaMalloc(&err, sizeof(int))) != cudaSuccess || (e = cudaMemset(err, 0, sizeof(int))) != cudaSuccess) {
+            sfde_set_last_cuda_error(e, "debug oz gemm alloc", __FILE__, __LINE__);
+            st = SFDE_ECUDA;
+        }
+    }
+    if (st == SFDE_OK)
+        st = sfde_oz_gemm(c, X, nullptr, (long long)R * K, R, K, batch, M, digits, xe, Out, (long long)N * R, err,
+                          R, K, N);
+    if (st == SFDE_OK) {
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) { sfde_set_last_cuda_error(e, "debug oz gemm", __FILE__, __LINE__); st = SFDE_ECUDA; }
+        else cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+    }
+    if (err_out) *err_out = herr;
+    if (st == SFDE_OK && herr) st = SFDE_ETIMEOUT;
+    sfde_oz_free_matrix(&M);
+    cudaFree(digits); cudaFree(xe); cudaFree(err);
+    delete c;
+    return st;
+}

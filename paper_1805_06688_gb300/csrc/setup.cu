@@ -260,7 +260,8 @@ __global__ void k_pad(const double* src, double* dst, int ny, int nx, int Py, in
     dst[sl * (size_t)Py * Px + (size_t)j * Px + i] = v;
 }
 
-__global__ void k_unpad(const double* src, double* dst, int ny, int nx, int Py, int Px) {
+template <typename T>
+__global__ void k_unpad(const T* src, T* dst, int ny, int nx, int Py, int Px) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     size_t sl = blockIdx.z;
@@ -307,7 +308,13 @@ void sfde_launch_pad(const double* src, double* dst, int ny, int nx, int Py, int
 void sfde_launch_unpad(const double* src, double* dst, int ny, int nx, int Py, int Px, int slices,
                        cudaStream_t s) {
     dim3 grid((nx + 127) / 128, ny, slices);
-    k_unpad<<<grid, 128, 0, s>>>(src, dst, ny, nx, Py, Px);
+    k_unpad<double><<<grid, 128, 0, s>>>(src, dst, ny, nx, Py, Px);
+}
+
+void sfde_launch_unpad_f32(const float* src, float* dst, int ny, int nx, int Py, int Px, int slices,
+                           cudaStream_t s) {
+    dim3 grid((nx + 127) / 128, ny, slices);
+    k_unpad<float><<<grid, 128, 0, s>>>(src, dst, ny, nx, Py, Px);
 }
 
 void sfde_launch_fill_random(double* u, int nt, int ny, int nx, int Py, int Px, uint64_t seed,

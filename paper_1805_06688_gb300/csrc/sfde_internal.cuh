@@ -9,6 +9,15 @@
 
 #define SFDE_MAX_RANK 4
 
+// Round an FP32 value to the nearest TF32 value (10 explicit mantissa bits).  The tensor cores read
+// FP32 storage as TF32 by dropping the low 13 bits, a biased truncation that accumulates coherently
+// over many time steps; values written for TF32 products are therefore rounded first.
+__device__ __forceinline__ float sfde_round_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
 // Return SFDE_ECUDA from the enclosing function on any CUDA error.
 #define SFDE_CUDA(call)                                   \
     do {                                                  \
@@ -154,6 +163,31 @@ sfde_status sfde_tc_map_matrix(CUtensorMap* map, const void* matT, int esz, int 
 sfde_status sfde_tc_gemm(sfde_ctx* c, int kind, int epi, const CUtensorMap& A, const CUtensorMap& B, const TcArgs& p,
                          cudaStream_t s, int nr = 0, int nc = 0, int nout = 0);
 
+// ---- FP64-accurate slice GEMM on the BF16 tensor cores (ozaki.cu)
+#define SFDE_OZ_DIGITS 6
+struct OzMatrix {            // a fixed K x N FP64 matrix split into SFDE_OZ_DIGITS BF16 digit planes
+    int K = 0, N = 0;
+    void* digits = nullptr;  // planes of N x K (K-major)
+    int* exps = nullptr;     // one exponent per column
+    CUtensorMap map;
+};
+sfde_status sfde_oz_split_matrix(const double* Mat, int K, int N, OzMatrix* out, cudaStream_t s);
+void sfde_oz_free_matrix(OzMatrix* m);
+size_t sfde_oz_digit_bytes(int R, int K, int batch);
+// Out_b = ((X_b [+ X2_b]) Mat)^T in FP64 accuracy; digits (sfde_oz_digit_bytes) and xe (batch x R ints)
+// are scratch.  K <= 256.
+sfde_status sfde_oz_gemm(sfde_ctx* c, const double* X, const double* X2, long long x_stride, int R, int K,
+                         int batch, const OzMatrix& M, void* digits, int* xe, double* out, long long out_stride,
+                         int* err, int nr, int nc, int nout);
+
+// The space-time residual of sfde_residual_fp64 with both dense products on the tensor cores
+// (Px, Py <= 256); digits / xe / err: scratch for sfde_oz_gemm.
+sfde_status sfde_residual_oz(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
+                             long long rout_stride, int out_kind, double* partial, int* n_partials,
+                             const OzMatrix& Ax, const OzMatrix& Ay, void* digits, int* xe, int* err);
+void sfde_launch_mass_x_transpose(const double* Un, const double* Um, double* T2, int Px, int Py, double hx,
+                                  int nb, cudaStream_t s);
+
 // ---- MGRIT engine (mgrit.cu)
 sfde_status sfde_mgrit_fp64(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st);
 sfde_status sfde_seq_fp64(sfde_ctx* c, double* seconds);
@@ -175,6 +209,9 @@ void sfde_launch_pad(const double* src, double* dst, int ny, int nx, int Py, int
                      cudaStream_t s);
 void sfde_launch_unpad(const double* src, double* dst, int ny, int nx, int Py, int Px, int slices,
                        cudaStream_t s);
+void sfde_launch_unpad_f32(const float* src, float* dst, int ny, int nx, int Py, int Px, int slices,
+                           cudaStream_t s);
+sfde_status sfde_level0(sfde_ctx* c, double** u);
 void sfde_launch_fill_random(double* u, int nt, int ny, int nx, int Py, int Px, uint64_t seed,
                              cudaStream_t s);
 void sfde_launch_axpy_strided(double* y, long long y_stride, const double* x, long long x_stride,

@@ -53,7 +53,7 @@ template <> struct ResidOut<EPI_RESID_BF16> { using T = __nv_bfloat16; };
 template <> struct ResidOut<EPI_RESID_F32> { using T = float; };
 
 __device__ __forceinline__ void store_as(__nv_bfloat16* p, double v) { *p = __float2bfloat16_rn((float)v); }
-__device__ __forceinline__ void store_as(float* p, double v) { *p = (float)v; }
+__device__ __forceinline__ void store_as(float* p, double v) { *p = sfde_round_tf32((float)v); }
 __device__ __forceinline__ void store_as(double* p, double v) { *p = v; }
 
 template <int T, int EPI>
@@ -369,6 +369,11 @@ __global__ void k_mass_x_transpose(const double* Un, const double* Um, double* T
 }
 
 }  // namespace
+
+void sfde_launch_mass_x_transpose(const double* Un, const double* Um, double* T2, int Px, int Py, double hx,
+                                  int nb, cudaStream_t s) {
+    k_mass_x_transpose<<<dim3(Px / 32, Py / 32, nb), dim3(32, 8), 0, s>>>(Un, Um, T2, Px, Py, hx);
+}
 
 sfde_status sfde_residual_fp64(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
                                long long rout_stride, int out_kind, double* partial, int* n_partials) {

@@ -1,0 +1,69 @@
+"""The FP64 space-time residual of the mixed-precision solver against the oracle's definition
+rho_n = F_n + B_n U_{n-1} - S_n U_n (Eq. (2.4)), for both ways of forming the dense products:
+FP64 arithmetic and the digit-split BF16 tensor-core product.
+
+The norm is accumulated in FP64 before the values are rounded for the low-precision solver, so
+||rho|| must agree to FP64-product accuracy: 1e-11 relative to ||S U|| (the scale that cancels
+when U nearly solves the system); the stored values are TF32 (10-bit mantissa), checked to 2^-10.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import sfde as osfde
+from sfde_workloads import gaussian_bump_forcing, sine_mode_amplitudes, sine_mode_nodal, time_grid
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1805_06688_gb300 as sfde  # noqa: E402
+
+
+def gpu_residual(P, U, use_tc):
+    L = sfde.lib()
+    L.sfde_debug_residual.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.POINTER(ctypes.c_double)]
+    nt = U.shape[0] - 1
+    rho = np.zeros((nt,) + U.shape[1:], dtype=np.float32)
+    n2 = ctypes.c_double(0)
+    st = L.sfde_debug_residual(P.ctx, U.ctypes.data, int(use_tc), rho.ctypes.data, ctypes.byref(n2))
+    assert st == 0, sfde.sfde_strerror(st)
+    return rho, np.sqrt(n2.value)
+
+
+def oracle_residual(O, U, F):
+    rho, su = [], []
+    for n in range(1, O.nt + 1):
+        tau = 0.5 * (O.t[n] - O.t[n - 1])
+        r = O.apply_B(U[n - 1], tau) - O.apply_S(U[n], tau)
+        if F is not None:
+            r = r + F.dense(n)
+        rho.append(r)
+        su.append(np.sum(O.apply_S(U[n], tau) ** 2))
+    return np.stack(rho), np.sqrt(sum(su))
+
+
+@pytest.mark.parametrize("use_tc", [0, 1])
+@pytest.mark.parametrize("nx,ny,nt,near", [(50, 70, 16, False), (255, 200, 6, False), (31, 31, 12, True)])
+def test_residual_matches_oracle(use_tc, nx, ny, nt, near):
+    t = time_grid(nt, 1.0, "graded")
+    F, _ = gaussian_bump_forcing(8, nx, ny, t)
+    psi = sine_mode_nodal(sine_mode_amplitudes(6), nx, ny)
+    O = osfde.SFDE(0.65, 0.85, 1.2, 0.6, nx, ny, t)
+    rng = np.random.default_rng(nx + nt)
+    if near:   # an iterate that almost solves the system: the residual is a small difference
+        U = osfde.seq_timestep(O, psi, F) + 1e-9 * rng.standard_normal((nt + 1, ny, nx))
+        U[0] = psi
+    else:
+        U = rng.standard_normal((nt + 1, ny, nx))
+    P = sfde.Problem(0.65, 0.85, 1.2, 0.6, nx, ny, t, precision=sfde.PREC_MIXED_TF32)
+    P.set_forcing(F)
+    rho, nrm = gpu_residual(P, np.ascontiguousarray(U), use_tc)
+    ref, scale = oracle_residual(O, U, F)
+    assert abs(nrm - np.sqrt(np.sum(ref ** 2))) <= 1e-11 * scale, (nrm, np.sqrt(np.sum(ref ** 2)), scale)
+    tol = 2.0 ** -10 * np.abs(ref).max(axis=(1, 2), keepdims=True) + 1e-13 * scale
+    assert np.all(np.abs(rho - ref) <= tol)
