@@ -45,6 +45,30 @@ sfde_status sfde_debug_oz_gemm(const double* X, int batch, int R, int K, const d
 sfde_status sfde_debug_residual(sfde_ctx* ctx, const double* U, int use_tensor_cores, float* rho,
                                 double* norm2);
 
+/*
+ * Whether the BF16 mixed-precision solver runs each spectral step as one fused kernel (the four
+ * products of Sec. 2's fast diagonalisation chained on chip; P_x = P_y in {128, 256}) or as four
+ * tensor-core slice GEMMs.  Default 1; the two give the same arithmetic up to the order of FP32
+ * accumulation.  Takes effect at the next mgrit_solve.
+ */
+sfde_status sfde_debug_set_fused_step(sfde_ctx* ctx, int enable);
+
+/*
+ * One batched low-precision step of the mixed-precision solver (ctx precision must be MIXED_BF16
+ * or MIXED_TF32):  out[b] = Phi(U[b]) + g[b] - ut[b],  b = 0..batch-1, slice b stepped from
+ * t_{n0+b-1} to t_{n0+b} (1 <= n0, n0 + batch - 1 <= N_t).
+ *   scheme 0: Crank-Nicolson step (Eq. (2.4) with F = 0), 1: backward Euler step (coarse
+ *   propagator of Sec. 3), 2: the solve S_{n}^{-1} U alone.
+ *   fused  1: the fused kernel (BF16, P_x = P_y in {128, 256}; SFDE_EUNSUPPORTED otherwise),
+ *          0: four tensor-core slice GEMMs.
+ * U, g, ut, out: batch x N_y x N_x doubles (host or device; g, ut may be NULL), rounded to the
+ * operand type on input; *norm2 (may be NULL; used only with ut) = sum over the batch of the squared
+ * outputs, formed from the FP32 values before they are rounded (FP32 partial sums of at most 256
+ * squares, added in FP64).  Synchronous; allocates scratch.
+ */
+sfde_status sfde_debug_lp_step(sfde_ctx* ctx, int fused, int scheme, const double* U, int batch, int n0,
+                               const double* g, const double* ut, double* out, double* norm2);
+
 #ifdef __cplusplus
 }
 #endif

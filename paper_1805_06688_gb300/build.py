@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsfde.so")
-SOURCES = ["api.cu", "setup.cu", "step_fp64.cu", "mgrit.cu", "mixed.cu", "gemm_tc.cu", "noalloc.cu", "ozaki.cu"]
+SOURCES = ["api.cu", "setup.cu", "step_fp64.cu", "mgrit.cu", "mixed.cu", "gemm_tc.cu", "noalloc.cu", "ozaki.cu",
+           "fused_step.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-v"]

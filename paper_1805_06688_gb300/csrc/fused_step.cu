@@ -1,0 +1,359 @@
+// One spectral step per CTA with all four products on chip (BF16 operands, FP32 accumulation,
+// P_x = P_y = P in {128, 256}).
+//
+// For a time slice U (P x P, row j = y node, column i = x node) the step
+//     X = V_y [ f o (W_y^T U W_x) ] V_x^T  (+ g - u_target)
+// is four tcgen05 products D = Op Data^T, Op (M x K) the fixed matrix, Data (N x K) the slice
+// operand, both K-major in shared memory.  Each accumulator row is the next product's Data row, so
+// the accumulator goes back to shared memory untransposed, in 16-byte vectors:
+//   phase 1  D1[a][j] = sum_i Wt_x[a][i] U[j][i]    = (U W_x)[j][a]
+//   phase 2  D2[q][a] = sum_j Wt_y[q][j] D1[a][j]   = (W_y^T U W_x)[q][a], then times f(sigma_qa)
+//   phase 3  D3[i][q] = sum_a V_x[i][a]  D2[q][a]   = (C V_x^T)[q][i]
+//   phase 4  D4[j][i] = sum_q V_y[j][q]  D3[i][q]   = X[j][i]
+// (the fast-diagonalisation solve S^{-1} uses V in place of W and f = 1/(1 + tau sigma)).  The
+// intermediates are rounded to BF16 exactly as the four-launch chain stores them, so the two forms
+// differ only in the order of FP32 accumulation and in how the modal factor is divided out (here
+// an approximate reciprocal shared by two modes).  A P x P FP32 accumulator takes P/128 x P TMEM columns (all 512 for
+// P = 256); the slice operand (P^2 BF16) stays in shared memory and the fixed matrices stream from
+// L2 in 64-wide K-atoms through a two-stage ring.  Per step HBM sees U read once and X written once
+// (plus g and u_target), and one launch does what four did.
+//
+// Roles: warps 0-3 drain the accumulator (TMEM lanes 32w..32w+31 of every 128-row half); warp 4
+// issues TMA (lane 0) and prefetches g / u_target into L2 (all lanes); warp 5 issues the MMAs.
+// Every wait is bounded; on a timeout the kernel records the error, lets its own copies and
+// products finish (bounded), frees TMEM and returns.
+#include <cuda_bf16.h>
+
+#include "sfde_internal.cuh"
+#include "tc_common.cuh"
+
+namespace {
+
+constexpr int THREADS = 192;
+constexpr int HALF_BYTES = 128 * 128;  // 128 rows x 128 bytes: one M-half of a K-atom
+
+template <int P> struct Geo {
+    static constexpr int NH = P / 128;             // 128-row halves of M
+    static constexpr int NATOM = P / 64;           // K-atoms of 64 BF16
+    static constexpr int ATOM = P * 128;           // bytes of one K-atom of a P-row operand
+    static constexpr int DATA = NATOM * ATOM;      // the slice operand, P^2 BF16
+    static constexpr int RING = 2 * ATOM;
+    static constexpr int TMEM_COLS = NH * P;       // 128 or 512
+    static constexpr int STAGE_ROW = P * 4;        // FP32 output staging: bytes per row
+    static constexpr int SMEM = 1024 + DATA + RING + 128 + 2 * P * 4 + 64;
+    static_assert(4 * 32 * STAGE_ROW <= DATA + RING, "output staging must fit in the operand space");
+};
+
+// byte offset of element (row r, column k) in a K-major, 128-byte-swizzled P-row operand:
+// K-atom k/64 is P rows x 128 bytes, rows in 1024-byte groups of 8, 16-byte chunks XOR (r % 8)
+template <int P>
+__device__ __forceinline__ uint32_t sw128(int r, int k) {
+    return (uint32_t)((k >> 6) * Geo<P>::ATOM + (r >> 3) * 1024 + (r & 7) * 128 +
+                      ((((k & 63) >> 3) ^ (r & 7)) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *(const uint32_t*)&v;
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+__device__ __forceinline__ float4 ld_shared_f4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr) : "memory");
+    return v;
+}
+
+// approximate reciprocal (PTX rcp.approx, about 1 ulp); the result is rounded to BF16 afterwards
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+__device__ __forceinline__ void bf16x8_to_f32(const uint4& u, float (&f)[8]) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        f[2 * i] = __uint_as_float(w[i] << 16);
+        f[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(THREADS, 1)
+k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ CUtensorMap mO1,
+             const __grid_constant__ CUtensorMap mO2, const __grid_constant__ CUtensorMap mO3,
+             const __grid_constant__ CUtensorMap mO4, FusedStepArgs p) {
+    using G = Geo<P>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sD = smem;                                  // slice operand (Data)
+    uint8_t* sO = smem + G::DATA;                        // ring of fixed-matrix K-atoms (Op)
+    uint64_t* bar = (uint64_t*)(sO + G::RING);
+    uint64_t* ofull = bar;                               // [2] Op atom landed
+    uint64_t* oempty = bar + 2;                          // [2] Op atom consumed
+    uint64_t* dfull = bar + 4;                           // U landed
+    uint64_t* dready = bar + 5;                          // the next Data written by the drain warps
+    uint64_t* accf = bar + 6;                            // a phase's products complete
+    uint64_t* fin = bar + 7;                             // error path: outstanding products complete
+    uint32_t* tmem_slot = (uint32_t*)(bar + 8);
+    float* s_A = (float*)(bar + 16);                     // c K_x lambda_x[a], P floats
+    float* s_B = s_A + P;                                // 1 + c K_y lambda_y[q]
+    double* red = (double*)(s_B + P);                    // 4 partial sums
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s) { tc::mbar_init(&ofull[s], 1); tc::mbar_init(&oempty[s], 1); }
+        tc::mbar_init(dfull, 1);
+        tc::mbar_init(dready, 128);
+        tc::mbar_init(accf, 1);
+        tc::mbar_init(fin, 1);
+        tc::mbar_fence_init();
+    }
+    {
+        // modal factor of this slice's step: d_qa = 1 + c sigma_qa = s_A[a] + s_B[q] with
+        // sigma_qa = K_x lambda_x[a] + K_y lambda_y[q], c = tau = dt/2 (Crank-Nicolson, solve) or dt
+        // (backward Euler); f = 1/d, and 2/d - 1 = (1 - tau sigma)/(1 + tau sigma) for Crank-Nicolson
+        const float dtb = (float)p.dt[p.n0 + b * p.dn - 1];
+        const float cst = p.scheme == SCHEME_BE ? dtb : 0.5f * dtb;
+        for (int i = threadIdx.x; i < P; i += THREADS) {
+            s_A[i] = cst * (p.kx * p.lamx[i]);
+            s_B[i] = fmaf(cst, p.ky * p.lamy[i], 1.f);
+        }
+    }
+    if (threadIdx.x < 4) red[threadIdx.x] = 0.0;
+    if (warp == 0) tc::tmem_alloc(tmem_slot, G::TMEM_COLS);
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const __nv_bfloat16* __restrict__ g = p.g ? (const __nv_bfloat16*)p.g + (long long)b * p.g_stride : nullptr;
+    const __nv_bfloat16* __restrict__ ut = p.ut ? (const __nv_bfloat16*)p.ut + (long long)b * p.ut_stride : nullptr;
+
+    if (warp == 4) {
+        const int s = p.s0 + b * p.ds;
+        if (lane == 0) {
+            tc::prefetch_tmap(&mapU);
+            tc::mbar_arrive_expect_tx(dfull, (uint32_t)G::DATA);
+            for (int t = 0; t < G::NATOM; ++t)
+                for (int h = 0; h < G::NH; ++h)
+                    tc::tma_load_4d(sD + t * G::ATOM + h * HALF_BYTES, &mapU, dfull, t * 64, h * 128, p.s0 % p.ds,
+                                    s / p.ds);
+        }
+        __syncwarp();
+        // g and u_target are read only by the last drain: bring them into L2 now
+        for (int e = lane; e < P * P * 2 / 128; e += 32) {
+            if (g) prefetch_l2((const char*)g + (size_t)e * 128);
+            if (ut) prefetch_l2((const char*)ut + (size_t)e * 128);
+        }
+        if (lane == 0) {
+            const CUtensorMap* maps[4] = {&mO1, &mO2, &mO3, &mO4};
+            bool ok = true;
+            int issued = 0;
+            for (int gi = 0; gi < 4 * G::NATOM && ok; ++gi) {
+                const int st = gi & 1;
+                if (gi >= 2) ok = tc::mbar_wait(&oempty[st], (uint32_t)((gi >> 1) - 1) & 1u, p.err, tc::ERR_WAIT_EMPTY);
+                if (!ok) break;
+                tc::mbar_arrive_expect_tx(&ofull[st], (uint32_t)G::ATOM);
+                tc::tma_load_2d(sO + st * G::ATOM, maps[gi / G::NATOM], &ofull[st], (gi % G::NATOM) * 64, 0);
+                ++issued;
+            }
+            // own copies in flight must land before the CTA's shared memory goes away
+            tc::mbar_wait(dfull, 0, p.err, tc::ERR_WAIT_FULL);
+            for (int gi = issued - 2 < 0 ? 0 : issued - 2; gi < issued; ++gi)
+                tc::mbar_wait(&ofull[gi & 1], (uint32_t)(gi >> 1) & 1u, p.err, tc::ERR_WAIT_FULL);
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_f32acc(1u, 128, P);
+            bool ok = tc::mbar_wait(dfull, 0, p.err, tc::ERR_WAIT_FULL);
+            bool any = false;
+            for (int ph = 0; ph < 4 && ok; ++ph) {
+                if (ph > 0) ok = tc::mbar_wait(dready, (uint32_t)(ph - 1) & 1u, p.err, tc::ERR_WAIT_FULL);
+                if (!ok) break;
+                tc::tc_fence_after();
+                for (int t = 0; t < G::NATOM && ok; ++t) {
+                    const int gi = ph * G::NATOM + t, st = gi & 1;
+                    ok = tc::mbar_wait(&ofull[st], (uint32_t)(gi >> 1) & 1u, p.err, tc::ERR_WAIT_FULL);
+                    if (!ok) break;
+                    tc::tc_fence_after();
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t bd = tc::smem_desc_sw128(sD + t * G::ATOM + kk * 32);
+#pragma unroll
+                        for (int h = 0; h < G::NH; ++h) {
+                            const uint64_t ad = tc::smem_desc_sw128(sO + st * G::ATOM + h * HALF_BYTES + kk * 32);
+                            tc::mma<0>(tmem + (uint32_t)(h * P), ad, bd, idesc, (t > 0 || kk > 0) ? 1u : 0u);
+                        }
+                    }
+                    any = true;
+                    tc::mma_commit(&oempty[st]);
+                }
+                if (ok) tc::mma_commit(accf);
+            }
+            if (!ok && any) {  // products still running must finish before TMEM is freed
+                tc::mma_commit(fin);
+                tc::mbar_wait(fin, 0, p.err, tc::ERR_WAIT_ACC);
+            }
+        }
+    } else {
+        // ---- warps 0-3: accumulator -> next Data operand (phases 1-3) or output (phase 4)
+        const bool cn = p.scheme == SCHEME_CN;
+        double sq = 0.0;
+        bool ok = true;
+        const uint32_t sD_u = tc::smem_u32(sD);
+        for (int ph = 0; ph < 4; ++ph) {
+            ok = ok && __all_sync(0xffffffffu, tc::mbar_wait(accf, (uint32_t)ph & 1u, p.err, tc::ERR_WAIT_ACC));
+            tc::tc_fence_after();
+            if (!ok) break;
+            for (int h = 0; h < G::NH; ++h) {
+                const int row = h * 128 + warp * 32 + lane;  // M index held by this thread
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * P);
+                if (ph < 3) {
+                    const float Bq = s_B[row];
+                    for (int c0 = 0; c0 < P; c0 += 64) {
+                        uint32_t v[64];
+                        tc::tmem_ld64(taddr + (uint32_t)c0, v);
+                        float x[64];
+#pragma unroll
+                        for (int j = 0; j < 64; ++j) x[j] = __uint_as_float(v[j]);
+                        if (ph == 1) {  // D2[q = row][a = c0 + j] times f(sigma_qa)
+#pragma unroll
+                            for (int j = 0; j < 64; j += 2) {
+                                // one reciprocal for two modes: 1/d0 = d1 / (d0 d1), 1/d1 = d0 / (d0 d1)
+                                const float d0 = s_A[c0 + j] + Bq, d1 = s_A[c0 + j + 1] + Bq;
+                                const float r = rcp_approx(d0 * d1);
+                                float f0 = d1 * r, f1 = d0 * r;
+                                if (cn) { f0 = fmaf(2.f, f0, -1.f); f1 = fmaf(2.f, f1, -1.f); }
+                                x[j] *= f0;
+                                x[j + 1] *= f1;
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            st_shared_v4(sD_u + sw128<P>(row, c0 + 8 * u), pack_bf16x2(x[8 * u], x[8 * u + 1]),
+                                         pack_bf16x2(x[8 * u + 2], x[8 * u + 3]), pack_bf16x2(x[8 * u + 4], x[8 * u + 5]),
+                                         pack_bf16x2(x[8 * u + 6], x[8 * u + 7]));
+                    }
+                } else {
+                    // stage this warp's 32 rows (j) in FP32, 16-byte chunks XOR (row % 8), then write
+                    // X + g - u_target with whole-row coalesced accesses
+                    const uint32_t stg = sD_u + (uint32_t)(warp * 32 * G::STAGE_ROW);
+                    for (int c0 = 0; c0 < P; c0 += 64) {
+                        uint32_t v[64];
+                        tc::tmem_ld64(taddr + (uint32_t)c0, v);
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            const int ch = (c0 >> 2) + u;
+                            st_shared_v4(stg + (uint32_t)(lane * G::STAGE_ROW + ((ch ^ (lane & 7)) << 4)), v[4 * u],
+                                         v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+                        }
+                    }
+                    __syncwarp();
+                    constexpr int CPR = P / 8;              // 8-column chunks per row
+                    constexpr int ITER = CPR;               // 32 rows x CPR chunks over 32 lanes
+                    constexpr int UNR = 8;
+                    __nv_bfloat16* __restrict__ dst = (__nv_bfloat16*)p.dst + (long long)b * p.dst_stride;
+                    const int rbase = h * 128 + warp * 32;
+                    const bool want_sq = ut && p.partial;
+                    float sqf = 0.f;   // FP32 over this lane's 8 x ITER values (the FP64 pipe is ~1/64 rate)
+                    for (int i0 = 0; i0 < ITER; i0 += UNR) {
+                        uint4 gv[UNR], uv[UNR];
+#pragma unroll
+                        for (int k = 0; k < UNR; ++k) {
+                            const int e = (i0 + k) * 32 + lane, rr = e / CPR, cc = e % CPR;
+                            const size_t off = (size_t)(rbase + rr) * P + cc * 8;
+                            gv[k] = g ? __ldg((const uint4*)(g + off)) : make_uint4(0, 0, 0, 0);
+                            uv[k] = ut ? __ldg((const uint4*)(ut + off)) : make_uint4(0, 0, 0, 0);
+                        }
+#pragma unroll
+                        for (int k = 0; k < UNR; ++k) {
+                            const int e = (i0 + k) * 32 + lane, rr = e / CPR, cc = e % CPR;
+                            const float4 x0 = ld_shared_f4(stg + (uint32_t)(rr * G::STAGE_ROW + (((2 * cc) ^ (rr & 7)) << 4)));
+                            const float4 x1 = ld_shared_f4(stg + (uint32_t)(rr * G::STAGE_ROW + (((2 * cc + 1) ^ (rr & 7)) << 4)));
+                            float xf[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                            float gf[8], uf[8];
+                            bf16x8_to_f32(gv[k], gf);
+                            bf16x8_to_f32(uv[k], uf);
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) xf[q] += gf[q] - uf[q];
+                            if (want_sq) {
+#pragma unroll
+                                for (int q = 0; q < 8; ++q) sqf = fmaf(xf[q], xf[q], sqf);
+                            }
+                            uint4 o;
+                            o.x = pack_bf16x2(xf[0], xf[1]);
+                            o.y = pack_bf16x2(xf[2], xf[3]);
+                            o.z = pack_bf16x2(xf[4], xf[5]);
+                            o.w = pack_bf16x2(xf[6], xf[7]);
+                            *(uint4*)(dst + (size_t)(rbase + rr) * P + cc * 8) = o;
+                        }
+                    }
+                    sq += (double)sqf;
+                    __syncwarp();
+                }
+            }
+            if (ph < 3) {
+                // generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tc::tc_fence_before();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(dready)) : "memory");
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (lane == 0) red[warp] = sq;
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (p.partial && threadIdx.x == 0) p.partial[b] = red[0] + red[1] + red[2] + red[3];
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, G::TMEM_COLS);
+    }
+}
+
+template <int P>
+sfde_status launch(sfde_ctx* c, const CUtensorMap& U, const CUtensorMap& O1, const CUtensorMap& O2,
+                   const CUtensorMap& O3, const CUtensorMap& O4, const FusedStepArgs& a, cudaStream_t s) {
+    const int slot = c ? sfde_prof_begin(c) : -1;
+    k_fused_step<P><<<a.batch, THREADS, Geo<P>::SMEM, s>>>(U, O1, O2, O3, O4, a);
+    if (c) {
+        const double nb = a.batch, nx = c->x.n, ny = c->y.n;
+        const double slice = nx * ny;
+        const double io = (2.0 + (a.g ? 1.0 : 0.0) + (a.ut ? 1.0 : 0.0)) * nb * slice;
+        sfde_prof_end(c, slot, 2, nb * 4.0 * slice * (nx + ny), 2.0 * (io + 2.0 * nx * nx + 2.0 * ny * ny));
+        sfde_count_launch(c);
+    }
+    SFDE_CUDA(cudaGetLastError());
+    return SFDE_OK;
+}
+
+}  // namespace
+
+bool sfde_fused_supported(int kind, int Px, int Py) { return kind == 0 && Px == Py && (Px == 128 || Px == 256); }
+
+sfde_status sfde_fused_prepare() {
+    SFDE_CUDA(cudaFuncSetAttribute(k_fused_step<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<128>::SMEM));
+    SFDE_CUDA(cudaFuncSetAttribute(k_fused_step<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<256>::SMEM));
+    return SFDE_OK;
+}
+
+sfde_status sfde_fused_step(sfde_ctx* c, int P, const CUtensorMap& U, const CUtensorMap& O1, const CUtensorMap& O2,
+                            const CUtensorMap& O3, const CUtensorMap& O4, const FusedStepArgs& a, cudaStream_t s) {
+    if (a.batch < 1) return SFDE_OK;
+    if (a.batch > 2147483647 || !a.dst || !a.dt || !a.lamx || !a.lamy || !a.err) return SFDE_EINVAL;
+    if (((uintptr_t)a.dst | (uintptr_t)a.g | (uintptr_t)a.ut) & 15) return SFDE_EINVAL;
+    if (P == 128) return launch<128>(c, U, O1, O2, O3, O4, a, s);
+    if (P == 256) return launch<256>(c, U, O1, O2, O3, O4, a, s);
+    return SFDE_EINVAL;
+}

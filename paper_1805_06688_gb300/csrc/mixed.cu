@@ -108,6 +108,8 @@ struct SfdeMixed {
     OzMatrix oAx, oAy;
     void* oz_digits = nullptr;
     int* oz_xe = nullptr;
+    // each BF16 step as one fused four-product kernel (P_x = P_y in {128, 256})
+    bool fused = false;
 };
 
 void sfde_free_mixed(sfde_ctx* c) {
@@ -162,6 +164,7 @@ sfde_status setup_mixed(sfde_ctx* c, int kind, int m, int max_levels, int min_co
     c->mixed = M;
     M->kind = kind; M->esz = kind == 0 ? 2 : 4; M->m = m; M->max_levels = max_levels; M->min_coarse = min_coarse;
     SFDE_TRY(sfde_tc_prepare());
+    SFDE_TRY(sfde_fused_prepare());
     const int Px = c->x.P, Py = c->y.P;
     const size_t P2 = c->P2();
     SFDE_TRY(lp_copy(c, c->x.WT, &M->WTx, (size_t)Px * Px, kind));
@@ -250,6 +253,25 @@ struct LpEngine {
                      double* partial, int* npart) {
         const int Px = c->x.P, Py = c->y.P;
         const long long P2l = (long long)P2();
+        if (M->fused) {
+            CUtensorMap a1;
+            SFDE_TRY(map_for(M, src, Py, Px, ds, ns, &a1));
+            if (partial && (size_t)batch > c->partial_cap) return SFDE_EINVAL;
+            FusedStepArgs a{};
+            a.s0 = src0; a.ds = ds; a.batch = batch;
+            a.dst = dst; a.dst_stride = (long long)dst_ds * P2l;
+            a.g = g; a.g_stride = (long long)dn * P2l;
+            a.ut = ut; a.ut_stride = (long long)dn * P2l;
+            a.partial = partial;
+            a.lamx = M->lamx; a.lamy = M->lamy; a.kx = (float)c->kx; a.ky = (float)c->ky;
+            a.dt = dt; a.n0 = n0; a.dn = dn; a.scheme = solve ? SCHEME_SOLVE : sch;
+            a.err = M->err;
+            SFDE_TRY(sfde_fused_step(c, Px, a1, solve ? M->mVTx : M->mWTx, solve ? M->mVTy : M->mWTy, M->mVx,
+                                     M->mVy, a, c->stream));
+            steps += batch;
+            if (npart) *npart = batch;
+            return SFDE_OK;
+        }
         int total = 0;
         for (int b0 = 0; b0 < batch; b0 += (int)M->ws) {
             const int nb = std::min<int>(batch - b0, (int)M->ws);
@@ -415,6 +437,7 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
     const int kind = c->precision == SFDE_PREC_MIXED_BF16 ? 0 : 1;
     SFDE_TRY(setup_mixed(c, kind, o->m, o->max_levels, o->min_coarse));
     SfdeMixed* M = c->mixed;
+    M->fused = c->fused_step && sfde_fused_supported(kind, c->x.P, c->y.P);
     const int L = (int)M->lev.size();
     double* U = nullptr;
     SFDE_TRY(sfde_level0(c, &U));
@@ -428,7 +451,8 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
     const int K = o->inner_cycles > 0 ? o->inner_cycles : (kind == 0 ? 4 : 5);
     // the inner solve is captured once as a CUDA graph and replayed; eager while kernels are timed
     const bool use_graph = !c->prof.on;
-    const long long key = ((long long)K << 8) | ((long long)E.scheme << 4) | (long long)o->relax;
+    const long long key = ((long long)M->fused << 20) | ((long long)K << 8) | ((long long)E.scheme << 4) |
+                          (long long)o->relax;
     long long graph_steps = 0;
 
     mgrit_stats S{};
@@ -517,4 +541,78 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
     }
     if (st) *st = S;
     return rc;
+}
+
+// ---- verification hooks (sfde_debug.h)
+
+namespace {
+template <typename T>
+__global__ void k_lp_to_f64(const T* src, double* dst, size_t n) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        dst[e] = (double)lp_f(src[e]);
+}
+
+// unpadded FP64 slices (host or device) -> padded low-precision device slices
+sfde_status load_lp(sfde_ctx* c, const double* in, int batch, double* tmp_unp, double* tmp_pad, void* out, int kind) {
+    const size_t n2 = (size_t)c->x.n * c->y.n, P2 = c->P2();
+    SFDE_TRY(sfde_copy_in(tmp_unp, in, sizeof(double) * n2 * batch, c->stream));
+    SFDE_CUDA(cudaMemsetAsync(tmp_pad, 0, sizeof(double) * P2 * batch, c->stream));
+    sfde_launch_pad(tmp_unp, tmp_pad, c->y.n, c->x.n, c->y.P, c->x.P, batch, c->stream);
+    const size_t n = P2 * batch;
+    if (kind == 0) k_to_lp<__nv_bfloat16><<<grid_for(n), 256, 0, c->stream>>>(tmp_pad, (__nv_bfloat16*)out, n);
+    else k_to_lp<float><<<grid_for(n), 256, 0, c->stream>>>(tmp_pad, (float*)out, n);
+    SFDE_CUDA(cudaGetLastError());
+    return SFDE_OK;
+}
+}  // namespace
+
+extern "C" sfde_status sfde_debug_set_fused_step(sfde_ctx* c, int enable) {
+    if (!c) return SFDE_EINVAL;
+    c->fused_step = enable ? 1 : 0;
+    return SFDE_OK;
+}
+
+extern "C" sfde_status sfde_debug_lp_step(sfde_ctx* c, int fused, int scheme, const double* U, int batch, int n0,
+                                         const double* g, const double* ut, double* out, double* norm2) {
+    if (!c || !U || !out || batch < 1 || n0 < 1 || (long long)n0 + batch - 1 > c->nt || scheme < 0 || scheme > 2)
+        return SFDE_EINVAL;
+    if (c->precision != SFDE_PREC_MIXED_BF16 && c->precision != SFDE_PREC_MIXED_TF32) return SFDE_EINVAL;
+    const int kind = c->precision == SFDE_PREC_MIXED_BF16 ? 0 : 1;
+    if (fused && !sfde_fused_supported(kind, c->x.P, c->y.P)) return SFDE_EUNSUPPORTED;
+    if (!c->mixed || c->mixed->kind != kind) SFDE_TRY(setup_mixed(c, kind, 2, 1, 1));
+    SfdeMixed* M = c->mixed;
+    const size_t P2 = c->P2(), n2 = (size_t)c->x.n * c->y.n, lp = P2 * M->esz * batch;
+    double *tu = nullptr, *tp = nullptr;
+    void *src = nullptr, *dst = nullptr, *dg = nullptr, *du = nullptr;
+    sfde_status st = SFDE_OK;
+    const bool saved = M->fused;
+    M->fused = fused != 0;
+    if (cudaMalloc(&tu, sizeof(double) * n2 * batch) != cudaSuccess ||
+        cudaMalloc(&tp, sizeof(double) * P2 * batch) != cudaSuccess || cudaMalloc(&src, lp) != cudaSuccess ||
+        cudaMalloc(&dst, lp) != cudaSuccess || cudaMalloc(&dg, lp) != cudaSuccess || cudaMalloc(&du, lp) != cudaSuccess)
+        st = SFDE_ENOMEM;
+    if (st == SFDE_OK) st = load_lp(c, U, batch, tu, tp, src, kind);
+    if (st == SFDE_OK && g) st = load_lp(c, g, batch, tu, tp, dg, kind);
+    if (st == SFDE_OK && ut) st = load_lp(c, ut, batch, tu, tp, du, kind);
+    if (st == SFDE_OK) {
+        LpEngine E{c, M, 2, 1, SFDE_RELAX_FCF, SCHEME_CN};
+        int np = 0;
+        const int sch = scheme == 0 ? SCHEME_CN : (scheme == 1 ? SCHEME_BE : SCHEME_SOLVE);
+        st = E.step(src, batch, 0, 1, batch, scheme == 2, sch, c->dt0, n0, 1, dst, 1, g ? dg : nullptr,
+                    ut ? du : nullptr, ut ? c->partial : nullptr, &np);
+        if (st == SFDE_OK && ut && norm2) st = sfde_reduce_partials(c, np, norm2);
+    }
+    if (st == SFDE_OK) {
+        const size_t n = P2 * batch;
+        if (kind == 0) k_lp_to_f64<__nv_bfloat16><<<grid_for(n), 256, 0, c->stream>>>((const __nv_bfloat16*)dst, tp, n);
+        else k_lp_to_f64<float><<<grid_for(n), 256, 0, c->stream>>>((const float*)dst, tp, n);
+        sfde_launch_unpad(tp, tu, c->y.n, c->x.n, c->y.P, c->x.P, batch, c->stream);
+        st = sfde_copy_out(out, tu, sizeof(double) * n2 * batch, c->stream);
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (st == SFDE_OK && e != cudaSuccess) { sfde_set_last_cuda_error(e, "debug lp step", __FILE__, __LINE__); st = SFDE_ECUDA; }
+    if (st == SFDE_OK) st = check_err(M, c->stream);
+    M->fused = saved;
+    cudaFree(tu); cudaFree(tp); cudaFree(src); cudaFree(dst); cudaFree(dg); cudaFree(du);
+    return st;
 }

@@ -102,6 +102,7 @@ struct sfde_ctx {
     int lev_m = 0, lev_max = 0, lev_min = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     struct SfdeMixed* mixed = nullptr;  // tensor-core operands and inner hierarchy (mixed.cu)
+    int fused_step = 1;         // BF16 steps as one fused kernel where the padded sizes allow it
     SfdeProf prof;
     size_t P2() const { return (size_t)x.P * (size_t)y.P; }
 };
@@ -162,6 +163,23 @@ sfde_status sfde_tc_map_matrix(CUtensorMap* map, const void* matT, int esz, int 
 // c may be NULL (no accounting); nr, nc, nout: unpadded extents of one slice product
 sfde_status sfde_tc_gemm(sfde_ctx* c, int kind, int epi, const CUtensorMap& A, const CUtensorMap& B, const TcArgs& p,
                          cudaStream_t s, int nr = 0, int nc = 0, int nout = 0);
+
+// ---- one whole spectral step per CTA, four chained BF16 products on chip (fused_step.cu)
+struct FusedStepArgs {
+    int s0, ds, batch;                    // source slices s0 + b*ds (through the slice tensor map)
+    void* dst; long long dst_stride;      // output slice b at dst + b*dst_stride (elements)
+    const void* g; long long g_stride;    // added to the output (or nullptr)
+    const void* ut; long long ut_stride;  // subtracted; sum of squares per slice into partial[b]
+    double* partial;                      // batch entries (or nullptr)
+    const float* lamx; const float* lamy; float kx, ky;
+    const double* dt; int n0, dn, scheme; // step size of slice b: dt[n0 + b*dn - 1]; SfdeScheme / SCHEME_SOLVE
+    int* err;                             // device error word (bounded waits)
+};
+bool sfde_fused_supported(int kind, int Px, int Py);
+sfde_status sfde_fused_prepare();
+// O1, O2: W_x^T, W_y^T (V_x^T, V_y^T for the solve); O3, O4: V_x, V_y -- K-major P x P BF16 maps.
+sfde_status sfde_fused_step(sfde_ctx* c, int P, const CUtensorMap& U, const CUtensorMap& O1, const CUtensorMap& O2,
+                            const CUtensorMap& O3, const CUtensorMap& O4, const FusedStepArgs& a, cudaStream_t s);
 
 // ---- FP64-accurate slice GEMM on the BF16 tensor cores (ozaki.cu)
 #define SFDE_OZ_DIGITS 6

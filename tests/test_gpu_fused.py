@@ -1,0 +1,153 @@
+"""One low-precision spectral step of the mixed-precision solver, fused (one kernel, four products
+chained on chip) and as four tensor-core slice GEMMs, against the oracle's FP64 step.
+
+Tolerances follow from the operand rounding: with unit roundoff u (2^-9 for BF16, 2^-11 for TF32),
+the input, the four fixed matrices, the three intermediates and the output are each rounded once,
+about nine independent relative perturbations of size <= u, so the relative Frobenius error of a
+slice is about 2u; the bound is 5u.  The fused kernel and the chain round the same quantities and
+differ only in the order of FP32 accumulation (and the modal factor's reciprocal), so they agree to
+well below one rounding: relative Frobenius <= u/2, elementwise <= 4u of the slice maximum.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import sfde as osfde
+from sfde_workloads import sine_mode_amplitudes, sine_mode_nodal, time_grid
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1805_06688_gb300 as sfde  # noqa: E402
+
+PD = ctypes.POINTER(ctypes.c_double)
+
+
+def lp_step(P, fused, scheme, U, n0, g=None, ut=None):
+    L = sfde.lib()
+    L.sfde_debug_lp_step.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, PD]
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    out = np.zeros_like(U)
+    n2 = ctypes.c_double(-1.0)
+    st = L.sfde_debug_lp_step(P.ctx, fused, scheme, U.ctypes.data, U.shape[0], n0,
+                              None if g is None else np.ascontiguousarray(g).ctypes.data,
+                              None if ut is None else np.ascontiguousarray(ut).ctypes.data,
+                              out.ctypes.data, ctypes.byref(n2))
+    return st, out, n2.value
+
+
+def oracle_step(O, scheme, U, n0, g=None, ut=None):
+    out = []
+    for b in range(U.shape[0]):
+        n = n0 + b
+        dt = O.t[n] - O.t[n - 1]
+        if scheme == 0:
+            x = O.propagate(U[b], dt, "cn")
+        elif scheme == 1:
+            x = O.propagate(U[b], dt, "be")
+        else:
+            x = O.solve_S_fdm(U[b], 0.5 * dt)
+        if g is not None:
+            x = x + g[b]
+        if ut is not None:
+            x = x - ut[b]
+        out.append(x)
+    return np.stack(out)
+
+
+def rel_fro(a, b):
+    return np.sqrt(np.sum((a - b) ** 2, axis=(1, 2)) / np.sum(b ** 2, axis=(1, 2)))
+
+
+CASES = [(255, 255, 160, 30), (200, 230, 6, 1), (100, 127, 40, 3)]
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+@pytest.mark.parametrize("nx,ny,batch,n0", CASES)
+def test_fused_step_matches_chain_and_oracle(scheme, nx, ny, batch, n0):
+    nt = n0 + batch + 3
+    t = time_grid(nt, 1.0, "graded")
+    O = osfde.SFDE(0.7, 0.8, 1.0, 0.5, nx, ny, t)
+    P = sfde.Problem(0.7, 0.8, 1.0, 0.5, nx, ny, t, precision=sfde.PREC_MIXED_BF16)
+    rng = np.random.default_rng(nx * 7 + scheme)
+    U = rng.standard_normal((batch, ny, nx))
+    ref = oracle_step(O, scheme, U, n0)
+    st_f, xf, _ = lp_step(P, 1, scheme, U, n0)
+    st_c, xc, _ = lp_step(P, 0, scheme, U, n0)
+    assert st_f == 0 and st_c == 0, (sfde.sfde_strerror(st_f), sfde.sfde_strerror(st_c))
+    u = 2.0 ** -9
+    assert rel_fro(xf, ref).max() <= 5 * u, rel_fro(xf, ref).max()
+    assert rel_fro(xc, ref).max() <= 5 * u, rel_fro(xc, ref).max()
+    assert rel_fro(xf, xc).max() <= u / 2, rel_fro(xf, xc).max()
+    scale = np.abs(xc).max(axis=(1, 2), keepdims=True)
+    assert np.all(np.abs(xf - xc) <= 4 * u * scale)
+
+
+@pytest.mark.parametrize("nx,ny,batch,n0", CASES[:1] + CASES[2:])
+def test_fused_step_with_rhs_and_residual(nx, ny, batch, n0):
+    """The residual form of Algorithm 1: Phi(u) + g - u_target, and its FP64 sum of squares."""
+    nt = n0 + batch
+    t = time_grid(nt, 2.0, "uniform")
+    O = osfde.SFDE(0.6, 0.9, 1.5, 0.7, nx, ny, t)
+    P = sfde.Problem(0.6, 0.9, 1.5, 0.7, nx, ny, t, precision=sfde.PREC_MIXED_BF16)
+    rng = np.random.default_rng(nx + ny)
+    U = rng.standard_normal((batch, ny, nx))
+    g = 0.3 * rng.standard_normal((batch, ny, nx))
+    ref0 = oracle_step(O, 0, U, n0, g)
+    ut = ref0 + 0.05 * rng.standard_normal((batch, ny, nx))   # a near-solution: small differences
+    ref = ref0 - ut
+    for fused in (1, 0):
+        st, x, n2 = lp_step(P, fused, 0, U, n0, g, ut)
+        assert st == 0, sfde.sfde_strerror(st)
+        # the difference is ~0.05 of the terms it is formed from: errors relative to the terms
+        err = np.sqrt(np.sum((x - ref) ** 2, axis=(1, 2)) / np.sum(ref0 ** 2, axis=(1, 2)))
+        assert err.max() <= 5 * 2.0 ** -9, err.max()
+        assert abs(n2 - np.sum(x ** 2)) <= 2.0 ** -7 * np.sum(x ** 2)
+
+
+def test_tf32_chain_step_and_fused_unsupported():
+    nx = ny = 100
+    t = time_grid(12, 1.0, "graded")
+    O = osfde.SFDE(0.7, 0.8, 1.0, 0.5, nx, ny, t)
+    P = sfde.Problem(0.7, 0.8, 1.0, 0.5, nx, ny, t, precision=sfde.PREC_MIXED_TF32)
+    U = np.random.default_rng(3).standard_normal((5, ny, nx))
+    st, _, _ = lp_step(P, 1, 0, U, 2)
+    assert st == sfde.SFDE_EUNSUPPORTED
+    st, x, _ = lp_step(P, 0, 0, U, 2)
+    assert st == 0
+    assert rel_fro(x, oracle_step(O, 0, U, 2)).max() <= 5 * 2.0 ** -11
+
+
+def test_lp_step_argument_errors():
+    t = time_grid(8, 1.0, "uniform")
+    P = sfde.Problem(0.7, 0.8, 1.0, 0.5, 40, 40, t, precision=sfde.PREC_MIXED_BF16)
+    U = np.zeros((4, 40, 40))
+    assert lp_step(P, 0, 0, U, 6)[0] == sfde.SFDE_EINVAL      # n0 + batch - 1 > N_t
+    assert lp_step(P, 0, 3, U, 1)[0] == sfde.SFDE_EINVAL      # unknown scheme
+    assert lp_step(P, 1, 0, U, 1)[0] == sfde.SFDE_EUNSUPPORTED  # P = 64: no fused form
+    Q = sfde.Problem(0.7, 0.8, 1.0, 0.5, 40, 40, t)
+    assert lp_step(Q, 0, 0, U, 1)[0] == sfde.SFDE_EINVAL      # FP64 context
+
+
+def test_mixed_bf16_solve_with_and_without_fused_step():
+    """The whole mixed-precision solve reaches the FP64 answer either way (P = 128)."""
+    nx, ny, nt = 100, 120, 128
+    t = time_grid(nt, 1.0, "uniform")
+    psi = sine_mode_nodal(sine_mode_amplitudes(5), nx, ny)
+    O = osfde.SFDE(0.75, 0.85, 1.0, 1.0, nx, ny, t)
+    ref = osfde.seq_timestep(O, psi)
+    L = sfde.lib()
+    L.sfde_debug_set_fused_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    for fused in (1, 0):
+        P = sfde.Problem(0.75, 0.85, 1.0, 1.0, nx, ny, t, precision=sfde.PREC_MIXED_BF16)
+        P.set_initial(psi)
+        assert L.sfde_debug_set_fused_step(P.ctx, fused) == 0
+        U = np.zeros((nt + 1, ny, nx))
+        _, stats = P.mgrit(U=U, m=4, max_levels=8, coarse=sfde.COARSE_BE, rel_tol=1e-11, max_iter=60)
+        assert stats.converged
+        assert np.abs(U - ref).max() <= 1e-8 * np.abs(ref).max(), fused
