@@ -1,9 +1,10 @@
 // Mixed-precision MGRIT: FP64 iterative refinement around low-precision tensor-core V-cycles.
 //
 // The iterate U (all time points) is FP64.  One outer iteration
-//   1. forms the space-time residual of Eq. (2.4) in FP64,
+//   1. forms the space-time residual of Eq. (2.4) to FP64 accuracy,
 //          rho_n = F_n + B_n U_{n-1} - S_n U_n = F_n + M_h (U_{n-1} - U_n) - tau_n K (U_{n-1} + U_n),
-//      (two FP64 slice GEMMs per time point) and its norm, and stores rho in BF16/FP32;
+//      (P <= 256: exact integer arithmetic around two digit-split tensor-core products per time
+//      point, resid_int.cu; larger P: FP64 slice GEMMs) and its norm, and stores rho in BF16/FP32;
 //   2. turns it into the right-hand side of the correction system in Psi form, g_n = S_n^{-1} rho_n
 //      (the fast-diagonalisation solve, four tensor-core slice GEMMs per time point), so that the
 //      correction E solves E_n = Psi_n E_{n-1} + g_n, E_0 = 0 -- the system of Eq. (3.1) again;
@@ -103,11 +104,11 @@ struct SfdeMixed {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t inner_exec = nullptr;
     long long inner_key = -1, inner_launches = 0, inner_steps = 0;
-    // FP64-accurate residual products on the tensor cores (P <= 256)
+    // FP64-accurate residual in integer arithmetic around tensor-core products (P <= 256)
     bool use_oz = false;
     OzMatrix oAx, oAy;
-    void* oz_digits = nullptr;
-    int* oz_xe = nullptr;
+    void *oz_dV = nullptr, *oz_dW = nullptr;
+    int* oz_E = nullptr;
     // each BF16 step as one fused four-product kernel (P_x = P_y in {128, 256})
     bool fused = false;
 };
@@ -125,8 +126,9 @@ void sfde_free_mixed(sfde_ctx* c) {
     if (M->inner_exec) cudaGraphExecDestroy(M->inner_exec);
     sfde_oz_free_matrix(&M->oAx);
     sfde_oz_free_matrix(&M->oAy);
-    cudaFree(M->oz_digits);
-    cudaFree(M->oz_xe);
+    cudaFree(M->oz_dV);
+    cudaFree(M->oz_dW);
+    cudaFree(M->oz_E);
     if (M->cap) cudaStreamDestroy(M->cap);
     delete M;
     c->mixed = nullptr;
@@ -220,11 +222,10 @@ sfde_status setup_mixed(sfde_ctx* c, int kind, int m, int max_levels, int min_co
     // products of the residual on the tensor cores (error-free digit splitting) when K <= 256
     M->use_oz = Px <= 256 && Py <= 256;
     if (M->use_oz) {
-        SFDE_TRY(sfde_oz_split_matrix(c->x.A, Px, Px, &M->oAx, c->stream));
-        SFDE_TRY(sfde_oz_split_matrix(c->y.A, Py, Py, &M->oAy, c->stream));
-        const int Pm = std::max(Px, Py);
-        SFDE_CUDA(cudaMalloc(&M->oz_digits, sfde_oz_digit_bytes(Pm, Pm, (int)c->ws_slices)));
-        SFDE_CUDA(cudaMalloc(&M->oz_xe, sizeof(int) * (size_t)Pm * c->ws_slices));
+        SFDE_TRY(sfde_resid_int_matrices(c, &M->oAx, &M->oAy));
+        SFDE_CUDA(cudaMalloc(&M->oz_dV, sfde_resid_int_digit_bytes(Px, Py, (int)c->ws_slices)));
+        SFDE_CUDA(cudaMalloc(&M->oz_dW, sfde_resid_int_digit_bytes(Px, Py, (int)c->ws_slices)));
+        SFDE_CUDA(cudaMalloc(&M->oz_E, sizeof(int) * ((size_t)c->nt + 1)));
     }
     size_t need = (size_t)c->nt * (size_t)(c->x.P / 16) * (c->y.P / 16) + 64;
     if (c->partial_cap < need) {
@@ -474,8 +475,8 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
         // 1. FP64 residual of Eq. (2.4) at n = 1..N_t, stored low precision in g_0[n]
         int np = 0;
         if (M->use_oz)
-            SFDE_TRY(sfde_residual_oz(c, U, 1, c->nt, E.slice(L0.g, 1), (long long)P2, kind, c->partial, &np,
-                                      M->oAx, M->oAy, M->oz_digits, M->oz_xe, M->err));
+            SFDE_TRY(sfde_residual_int(c, U, 1, c->nt, E.slice(L0.g, 1), (long long)P2, kind, c->partial, &np,
+                                       M->oAx, M->oAy, M->oz_dV, M->oz_dW, M->oz_E, M->err));
         else
             SFDE_TRY(sfde_residual_fp64(c, U, 1, c->nt, E.slice(L0.g, 1), (long long)P2, kind, c->partial, &np));
         double r2 = 0.0;

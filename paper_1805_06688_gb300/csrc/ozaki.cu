@@ -13,7 +13,10 @@
 // 256 * 2^16 = 2^24 in magnitude, and the products are grouped into 12 FP32 TMEM accumulators so
 // that every partial sum stays an integer of magnitude <= 2^24: FP32 accumulation is then exact.
 // The epilogue converts the 12 accumulators to integers, combines them in two int64 words
-// (digit weights 2^{-16..-40} and 2^{-48..-56}) and converts to FP64 once per output.
+// (digit weights 2^{-16..-40} and 2^{-48..-56}) and converts to FP64 once per output -- or, for the
+// space-time residual (resid_int.cu), leaves the product as one exact int64 in units of 2^-48 of the
+// operands' scales, so that the residual is assembled in integer arithmetic (the FP64 pipe of this
+// GPU runs at about 1/64 of the FP32 rate).
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -26,18 +29,23 @@
 
 namespace {
 
-constexpr int S = SFDE_OZ_DIGITS;      // 6 digits per operand
 constexpr int BM = 128, BN = 32, KC = 64;
 constexpr int XTILE = BM * KC * 2;     // 16 KB: one digit plane of the 128-row tile, one K chunk
 constexpr int MTILE = BN * KC * 2;     // 4 KB
-constexpr int STAGE = S * (XTILE + MTILE);
-constexpr int NACC = 12;
 constexpr int TMEM_COLS = 512;
 
-// accumulator a -> digit sum d = p + q of its products, and the product list (p, q, a)
-__constant__ int c_acc_d[NACC] = {2, 3, 4, 4, 5, 5, 6, 6, 6, 7, 7, 7};
-constexpr int NPROD = 21;
-__constant__ int c_prod[NPROD][3] = {
+// Digit plans.  Partial sums of an accumulator must stay integers of magnitude <= 2^24 (exact in
+// FP32): with K <= 256, |d_1| <= 256 and |d_p| <= 128 (p >= 2), one (1,1) product, two (1,q)/(p,1)
+// products or four products with p, q >= 2 fit in one accumulator.
+//   FP64 output: 6 digits per operand, the 21 products with p + q <= 7 in 12 accumulators;
+//   integer output: 7 digits, the 28 products with p + q <= 8 in 13 accumulators.
+template <bool INT_OUT> struct Plan;
+template <> struct Plan<false> { static constexpr int S = 6, NPROD = 21, NACC = 12; };
+template <> struct Plan<true> { static constexpr int S = 7, NPROD = 28, NACC = 13; };
+
+// accumulator a -> digit sum d = p + q of its products, and the product list (p, q, a), grouped by a
+__constant__ int c6_acc_d[12] = {2, 3, 4, 4, 5, 5, 6, 6, 6, 7, 7, 7};
+__constant__ int c6_prod[21][3] = {
     {1, 1, 0},
     {1, 2, 1}, {2, 1, 1},
     {1, 3, 2}, {2, 2, 2}, {3, 1, 3},
@@ -45,12 +53,25 @@ __constant__ int c_prod[NPROD][3] = {
     {1, 5, 6}, {2, 4, 6}, {3, 3, 7}, {4, 2, 7}, {5, 1, 8},
     {1, 6, 9}, {2, 5, 9}, {3, 4, 10}, {4, 3, 10}, {5, 2, 11}, {6, 1, 11},
 };
+__constant__ int c7_acc_d[13] = {2, 3, 4, 4, 5, 5, 6, 6, 7, 7, 8, 8, 8};
+__constant__ int c7_prod[28][3] = {
+    {1, 1, 0},
+    {1, 2, 1}, {2, 1, 1},
+    {1, 3, 2}, {3, 1, 2}, {2, 2, 3},
+    {1, 4, 4}, {4, 1, 4}, {2, 3, 5}, {3, 2, 5},
+    {1, 5, 6}, {5, 1, 6}, {2, 4, 7}, {3, 3, 7}, {4, 2, 7},
+    {1, 6, 8}, {6, 1, 8}, {2, 5, 9}, {3, 4, 9}, {4, 3, 9}, {5, 2, 9},
+    {1, 7, 10}, {7, 1, 10}, {2, 6, 11}, {3, 5, 11}, {4, 4, 11}, {5, 3, 11}, {6, 2, 12},
+};
+
+template <bool INT_OUT>
+constexpr size_t smem_bytes() { return 1024 + (size_t)Plan<INT_OUT>::S * (XTILE + MTILE) + 256; }
 
 struct OzArgs {
     int R, K, N, batch;          // X slice R x K (digits in planes of nslices x R x K), Mat K x N
-    const int* xe;               // row exponents, batch x R
-    const int* me;               // column exponents, N
-    double* out; long long out_stride;   // Out_b = (X_b Mat)^T, N x R per slice
+    const int* xe;               // row exponents, batch x R (FP64 output only)
+    const int* me;               // column exponents, N (FP64 output only)
+    void* out; long long out_stride;     // Out_b = (X_b Mat)^T, N x R per slice: double or int64
     int* err;
 };
 
@@ -58,8 +79,16 @@ __device__ __forceinline__ double pow2(int e) {  // exact 2^e for normal range
     return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
+// INT_OUT: write sum_{p+q<=8} 2^{-8(p+q)} sum_k d_p c_q as one int64 in units of 2^-52 (exact up to
+// the rounding of the p + q >= 7 terms to that unit; |value| <= K 2^52 <= 2^60); otherwise FP64
+// scaled by the row and column exponents (p + q <= 7).
+template <bool INT_OUT>
 __global__ void __launch_bounds__(128, 1)
 k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapM, OzArgs p) {
+    constexpr int S = Plan<INT_OUT>::S, NPROD = Plan<INT_OUT>::NPROD, NACC = Plan<INT_OUT>::NACC;
+    constexpr int STAGE = S * (XTILE + MTILE);
+    const int (*c_prod)[3] = INT_OUT ? c7_prod : c6_prod;
+    const int* c_acc_d = INT_OUT ? c7_acc_d : c6_acc_d;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sX = smem;                       // S planes x 16 KB
@@ -124,7 +153,33 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
 
     const bool acc_ok = __all_sync(0xffffffffu, tc::mbar_wait(accf, 0, p.err, tc::ERR_WAIT_ACC));
     tc::tc_fence_after();
-    if (acc_ok) {
+    if (acc_ok && INT_OUT) {
+        const long long m = m0 + warp * 32 + lane;
+        // z: digit sums d <= 6 in units of 2^-52 (exact); zl: d = 7, 8 in units of 2^-64 (exact)
+        long long z[BN], zl[BN];
+#pragma unroll
+        for (int j = 0; j < BN; ++j) { z[j] = 0; zl[j] = 0; }
+#pragma unroll 1
+        for (int a = 0; a < NACC; ++a) {
+            uint32_t v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * BN), v);
+            const int d = c_acc_d[a];
+            const int sh = d <= 6 ? 52 - 8 * d : 8 * (8 - d);
+#pragma unroll
+            for (int j = 0; j < BN; ++j) {
+                const long long s = (long long)__float2int_rn(__uint_as_float(v[j]));  // exact, |s| <= 2^24
+                if (d <= 6) z[j] += s << sh;
+                else zl[j] += s << sh;
+            }
+        }
+        if (m < Mtot) {
+            const long long b = m / p.R;
+            const int r = (int)(m % p.R);
+            long long* out = (long long*)p.out + b * p.out_stride + r;
+#pragma unroll
+            for (int j = 0; j < BN; ++j) out[(long long)(n0 + j) * p.R] = z[j] + ((zl[j] + 2048) >> 12);
+        }
+    } else if (acc_ok) {
         const long long m = m0 + warp * 32 + lane;
         const bool valid = m < Mtot;
         // z_hi in units of 2^-40 (digit sums d = 2..5), z_lo in units of 2^-56 (d = 6, 7)
@@ -147,7 +202,7 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
             const long long b = m / p.R;
             const int r = (int)(m % p.R);
             const int er = p.xe[b * p.R + r];
-            double* out = p.out + b * p.out_stride + r;
+            double* out = (double*)p.out + b * p.out_stride + r;
 #pragma unroll
             for (int j = 0; j < BN; ++j) {
                 const int n = n0 + j;
@@ -187,7 +242,7 @@ __global__ void k_oz_split_rows(const double* X, const double* X2, long long x_s
     for (int k = lane; k < K; k += 32) {
         double v = (x2 ? x[k] + x2[k] : x[k]) * sc;  // in (-1, 1), exact scaling
 #pragma unroll
-        for (int d = 0; d < S; ++d) {
+        for (int d = 0; d < Plan<false>::S; ++d) {
             v *= 256.0;
             const double q = rint(v);
             v -= q;                                   // exact: |v| <= 1/2
@@ -196,22 +251,42 @@ __global__ void k_oz_split_rows(const double* X, const double* X2, long long x_s
     }
 }
 
-// Column splitting of the fixed matrix Mat (K x N, row-major) -> digits stored K-major per column
-// (planes of N x K) and one exponent per column.  One warp per column.
-__global__ void k_oz_split_cols(const double* Mat, int K, int N, __nv_bfloat16* digits, int* me) {
+// Column splitting of the fixed matrix alpha Mat (K x N, row-major) -> digits stored K-major per
+// column (planes of N x K).  k_oz_col_exps: one exponent per column (max_k |alpha m_kn| < 2^e_n);
+// k_oz_uniform_exp optionally replaces them by their maximum (one scale for the whole matrix);
+// k_oz_split_cols writes the digits with those exponents.  One warp per column; setup time only.
+__global__ void k_oz_col_exps(const double* Mat, double alpha, int K, int N, int* me) {
     const int n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (n >= N) return;
     double mx = 0.0;
-    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(Mat[(size_t)k * N + n]));
+    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(alpha * Mat[(size_t)k * N + n]));
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     int e = 0;
     if (mx > 0.0) frexp(mx, &e);
     if (lane == 0) me[n] = e;
-    const double sc = pow2(-e);
+}
+
+__global__ void k_oz_uniform_exp(int* me, int N) {
+    __shared__ int red[256];
+    int e = -1074;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) e = max(e, me[n]);
+    red[threadIdx.x] = e;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    for (int n = threadIdx.x; n < N; n += blockDim.x) me[n] = red[0];
+}
+
+__global__ void k_oz_split_cols(const double* Mat, double alpha, int K, int N, int nd, __nv_bfloat16* digits,
+                                const int* me) {
+    const int n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (n >= N) return;
+    const double sc = pow2(-me[n]);
     for (int k = lane; k < K; k += 32) {
-        double v = Mat[(size_t)k * N + n] * sc;
-#pragma unroll
-        for (int d = 0; d < S; ++d) {
+        double v = alpha * Mat[(size_t)k * N + n] * sc;
+        for (int d = 0; d < nd; ++d) {
             v *= 256.0;
             const double q = rint(v);
             v -= q;
@@ -303,17 +378,25 @@ PFN_cuTensorMapEncodeTiled_v12000 encode() {
     return fn;
 }
 
-constexpr size_t SMEM_BYTES = 1024 + STAGE + 256;
 
 }  // namespace
 
-sfde_status sfde_oz_split_matrix(const double* Mat, int K, int N, OzMatrix* out, cudaStream_t s) {
+sfde_status sfde_oz_split_matrix(const double* Mat, int K, int N, OzMatrix* out, cudaStream_t s, double alpha,
+                                 bool uniform) {
     if (K > 256 || K % 32 || N % BN) return SFDE_EUNSUPPORTED;
-    out->K = K; out->N = N;
+    // uniform scale: the integer-output product (7 digits); per-column scales: FP64 output (6)
+    const int S = uniform ? Plan<true>::S : Plan<false>::S;
+    out->K = K; out->N = N; out->nd = S;
     SFDE_CUDA(cudaMalloc(&out->digits, sizeof(__nv_bfloat16) * (size_t)S * N * K));
     SFDE_CUDA(cudaMalloc(&out->exps, sizeof(int) * N));
-    k_oz_split_cols<<<(N * 32 + 255) / 256, 256, 0, s>>>(Mat, K, N, (__nv_bfloat16*)out->digits, out->exps);
+    const unsigned g = (unsigned)((N * 32 + 255) / 256);
+    k_oz_col_exps<<<g, 256, 0, s>>>(Mat, alpha, K, N, out->exps);
+    if (uniform) k_oz_uniform_exp<<<1, 256, 0, s>>>(out->exps, N);
+    k_oz_split_cols<<<g, 256, 0, s>>>(Mat, alpha, K, N, S, (__nv_bfloat16*)out->digits, out->exps);
     SFDE_CUDA(cudaGetLastError());
+    out->e_uniform = 0;
+    if (uniform) SFDE_CUDA(cudaMemcpyAsync(&out->e_uniform, out->exps, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SFDE_CUDA(cudaStreamSynchronize(s));
     auto fn = encode();
     if (!fn) return SFDE_EUNSUPPORTED;
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)N, (cuuint64_t)S};
@@ -324,7 +407,10 @@ sfde_status sfde_oz_split_matrix(const double* Mat, int K, int N, OzMatrix* out,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return SFDE_EINVAL;
-    SFDE_CUDA(cudaFuncSetAttribute(k_ozaki_slice_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    SFDE_CUDA(cudaFuncSetAttribute(k_ozaki_slice_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem_bytes<false>()));
+    SFDE_CUDA(cudaFuncSetAttribute(k_ozaki_slice_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem_bytes<true>()));
     return SFDE_OK;
 }
 
@@ -335,139 +421,68 @@ void sfde_oz_free_matrix(OzMatrix* m) {
     m->exps = nullptr;
 }
 
-size_t sfde_oz_digit_bytes(int R, int K, int batch) { return (size_t)S * R * K * batch * 2; }
+size_t sfde_oz_digit_bytes(int R, int K, int batch) { return (size_t)Plan<false>::S * R * K * batch * 2; }
+
+namespace {
+// 4-D map over S digit planes of batch x R x K BF16 values: {K, R, batch, plane}
+sfde_status map_digit_planes(CUtensorMap* map, void* digits, int R, int K, int batch, long long plane, int S) {
+    auto fn = encode();
+    if (!fn) return SFDE_EUNSUPPORTED;
+    cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)R, (cuuint64_t)batch, (cuuint64_t)S};
+    cuuint64_t strides[3] = {(cuuint64_t)K * 2, (cuuint64_t)R * K * 2, (cuuint64_t)plane * 2};
+    cuuint32_t box[4] = {KC, (cuuint32_t)(R < BM ? R : BM), (cuuint32_t)(R < BM ? BM / R : 1), 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, digits, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? SFDE_OK : SFDE_EINVAL;
+}
+
+template <bool INT_OUT>
+sfde_status launch_oz(sfde_ctx* c, const CUtensorMap& mapX, const OzMatrix& M, const OzArgs& a, cudaStream_t s,
+                      int nr, int nc, int nout) {
+    dim3 grid((unsigned)(((long long)a.batch * a.R + BM - 1) / BM), M.N / BN);
+    const int slot = sfde_prof_begin(c);
+    k_ozaki_slice_gemm<INT_OUT><<<grid, 128, smem_bytes<INT_OUT>(), s>>>(mapX, M.map, a);
+    // tensor work: 21 digit products of 2 R K N flops each (counted as the FP64 product it replaces)
+    sfde_prof_end(c, slot, 1, 2.0 * a.batch * nr * nc * nout,
+                  8.0 * ((double)a.batch * nr * nc + (double)a.batch * nr * nout));
+    sfde_count_launch(c);
+    SFDE_CUDA(cudaGetLastError());
+    return SFDE_OK;
+}
+}  // namespace
 
 sfde_status sfde_oz_gemm(sfde_ctx* c, const double* X, const double* X2, long long x_stride, int R, int K,
                          int batch, const OzMatrix& M, void* digits, int* xe, double* out, long long out_stride,
                          int* err, int nr, int nc, int nout) {
-    if (K != M.K || K > 256 || R % 32 || (R > 128 && R % 128)) return SFDE_EUNSUPPORTED;
+    if (K != M.K || K > 256 || R % 32 || (R > 128 && R % 128) || M.nd != Plan<false>::S) return SFDE_EUNSUPPORTED;
     const long long plane = (long long)batch * R * K;
     const int nrows = batch * R;
     k_oz_split_rows<<<(nrows * 32 + 255) / 256, 256, 0, c->stream>>>(X, X2, x_stride, R, K, nrows,
                                                                       (__nv_bfloat16*)digits, plane, xe);
     sfde_count_launch(c);
     SFDE_CUDA(cudaGetLastError());
-    auto fn = encode();
-    if (!fn) return SFDE_EUNSUPPORTED;
     CUtensorMap mapX;
-    cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)R, (cuuint64_t)batch, (cuuint64_t)S};
-    cuuint64_t strides[3] = {(cuuint64_t)K * 2, (cuuint64_t)R * K * 2, (cuuint64_t)plane * 2};
-    cuuint32_t box[4] = {KC, (cuuint32_t)(R < BM ? R : BM), (cuuint32_t)(R < BM ? BM / R : 1), 1};
-    cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = fn(&mapX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, digits, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return SFDE_EINVAL;
+    SFDE_TRY(map_digit_planes(&mapX, digits, R, K, batch, plane, Plan<false>::S));
     OzArgs a{};
     a.R = R; a.K = K; a.N = M.N; a.batch = batch; a.xe = xe; a.me = M.exps;
     a.out = out; a.out_stride = out_stride; a.err = err;
-    dim3 grid((unsigned)(((long long)batch * R + BM - 1) / BM), M.N / BN);
-    const int slot = sfde_prof_begin(c);
-    k_ozaki_slice_gemm<<<grid, 128, SMEM_BYTES, c->stream>>>(mapX, M.map, a);
-    // tensor work: 21 digit products of 2 R K N flops each (counted as the FP64 product it replaces)
-    sfde_prof_end(c, slot, 1, 2.0 * batch * nr * nc * nout, 8.0 * ((double)batch * nr * nc + (double)batch * nr * nout));
-    sfde_count_launch(c);
-    SFDE_CUDA(cudaGetLastError());
-    return SFDE_OK;
+    return launch_oz<false>(c, mapX, M, a, c->stream, nr, nc, nout);
 }
 
-sfde_status sfde_residual_oz(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
-                             long long rout_stride, int out_kind, double* partial, int* n_partials,
-                             const OzMatrix& Ax, const OzMatrix& Ay, void* digits, int* xe, int* err) {
-    const int Px = c->x.P, Py = c->y.P;
-    const size_t P2 = c->P2();
-    const size_t esz = out_kind == 0 ? 2 : 4;
-    int total = 0;
-    for (int b0 = 0; b0 < count; b0 += (int)c->ws_slices) {
-        const int nb = count - b0 < (int)c->ws_slices ? count - b0 : (int)c->ws_slices;
-        const int n0 = n_first + b0;
-        const double* Un = U + (size_t)n0 * P2;
-        const double* Um = U + (size_t)(n0 - 1) * P2;
-        // T1 = (V A_x)^T, V = U_n + U_{n-1} formed while splitting
-        SFDE_TRY(sfde_oz_gemm(c, Un, Um, (long long)P2, Py, Px, nb, Ax, digits, xe, c->T1, (long long)P2, err,
-                              c->y.n, c->x.n, c->x.n));
-        // T2 = (V M_x)^T, then T3 = A_y (V M_x) in row-j, column-i layout
-        sfde_launch_mass_x_transpose(Un, Um, c->T2, Px, Py, c->x.h, nb, c->stream);
-        sfde_count_launch(c);
-        SFDE_TRY(sfde_oz_gemm(c, c->T2, nullptr, (long long)P2, Px, Py, nb, Ay, digits, xe, c->T3, (long long)P2,
-                              err, c->x.n, c->y.n, c->y.n));
-        const int blocks = (Px / 32) * (Py / 32) * nb;
-        if ((size_t)(total + blocks) > c->partial_cap) return SFDE_EINVAL;
-        dim3 grid(Px / 32, Py / 32, nb), block(32, 8);
-        char* ro = (char*)rout + (size_t)b0 * rout_stride * esz;
-        if (out_kind == 0)
-            k_resid_combine<__nv_bfloat16><<<grid, block, 0, c->stream>>>(
-                c->T1, c->T3, U, n0, Px, Py, c->x.n, c->y.n, c->x.h, c->y.h, c->kx, c->ky, c->dt0, c->rank,
-                c->time_w, c->bxn, c->byn, (__nv_bfloat16*)ro, rout_stride, partial + total);
-        else
-            k_resid_combine<float><<<grid, block, 0, c->stream>>>(
-                c->T1, c->T3, U, n0, Px, Py, c->x.n, c->y.n, c->x.h, c->y.h, c->kx, c->ky, c->dt0, c->rank,
-                c->time_w, c->bxn, c->byn, (float*)ro, rout_stride, partial + total);
-        sfde_count_launch(c);
-        total += blocks;
-    }
-    SFDE_CUDA(cudaGetLastError());
-    if (n_partials) *n_partials = total;
-    return SFDE_OK;
-}
-
-extern "C" sfde_status sfde_debug_residual(sfde_ctx* c, const double* U, int use_tensor_cores, float* rho,
-                                          double* norm2) {
-    if (!c || !U || !rho || !norm2) return SFDE_EINVAL;
-    const int Px = c->x.P, Py = c->y.P;
-    if (use_tensor_cores && (Px > 256 || Py > 256)) return SFDE_EUNSUPPORTED;
-    const size_t P2 = c->P2(), n2 = (size_t)c->x.n * c->y.n;
-    double* u = nullptr;
-    SFDE_TRY(sfde_level0(c, &u));
-    SFDE_TRY(sfde_ensure_workspace(c, std::min<size_t>(c->nt, 128)));
-    const size_t need = (size_t)c->nt * (Px / 16) * (Py / 16) + 64;
-    if (c->partial_cap < need) {
-        cudaFree(c->partial);
-        c->partial = nullptr;
-        SFDE_CUDA(cudaMalloc(&c->partial, sizeof(double) * need));
-        c->partial_cap = need;
-    }
-    double* tmp = nullptr;
-    float *rp = nullptr, *ru = nullptr;
-    OzMatrix Ax, Ay;
-    void* digits = nullptr;
-    int *xe = nullptr, *err = nullptr;
-    sfde_status st = SFDE_OK;
-    int np = 0;
-    cudaError_t e;
-#define DC(x) if ((e = (x)) != cudaSuccess) { sfde_set_last_cuda_error(e, #x, __FILE__, __LINE__); st = SFDE_ECUDA; goto done; }
-    DC(cudaMalloc(&tmp, sizeof(double) * n2 * (c->nt + 1)));
-    DC(cudaMalloc(&rp, sizeof(float) * P2 * c->nt));
-    DC(cudaMalloc(&ru, sizeof(float) * n2 * c->nt));
-    DC(cudaMalloc(&err, sizeof(int)));
-    DC(cudaMemset(err, 0, sizeof(int)));
-    if ((st = sfde_copy_in(tmp, U, sizeof(double) * n2 * (c->nt + 1), c->stream)) != SFDE_OK) goto done;
-    sfde_launch_pad(tmp, u, c->y.n, c->x.n, Py, Px, c->nt + 1, c->stream);
-    if (use_tensor_cores) {
-        if ((st = sfde_oz_split_matrix(c->x.A, Px, Px, &Ax, c->stream)) != SFDE_OK) goto done;
-        if ((st = sfde_oz_split_matrix(c->y.A, Py, Py, &Ay, c->stream)) != SFDE_OK) goto done;
-        DC(cudaMalloc(&digits, sfde_oz_digit_bytes(std::max(Px, Py), std::max(Px, Py), (int)c->ws_slices)));
-        DC(cudaMalloc(&xe, sizeof(int) * (size_t)std::max(Px, Py) * c->ws_slices));
-        st = sfde_residual_oz(c, u, 1, c->nt, rp, (long long)P2, 1, c->partial, &np, Ax, Ay, digits, xe, err);
-    } else {
-        st = sfde_residual_fp64(c, u, 1, c->nt, rp, (long long)P2, 1, c->partial, &np);
-    }
-    if (st != SFDE_OK) goto done;
-    if ((st = sfde_reduce_partials(c, np, norm2)) != SFDE_OK) goto done;
-    sfde_launch_unpad_f32(rp, ru, c->y.n, c->x.n, Py, Px, c->nt, c->stream);  // one float per interior node
-    if ((st = sfde_copy_out(rho, ru, sizeof(float) * n2 * c->nt, c->stream)) != SFDE_OK) goto done;
-    DC(cudaStreamSynchronize(c->stream));
-    {
-        int herr = 0;
-        DC(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (herr) st = SFDE_ETIMEOUT;
-    }
-done:
-#undef DC
-    sfde_oz_free_matrix(&Ax);
-    sfde_oz_free_matrix(&Ay);
-    cudaFree(tmp); cudaFree(rp); cudaFree(ru); cudaFree(digits); cudaFree(xe); cudaFree(err);
-    return st;
+sfde_status sfde_oz_gemm_int(sfde_ctx* c, void* xdigits, long long plane, int R, int K, int batch,
+                             const OzMatrix& M, long long* out, long long out_stride, int* err, int nr, int nc,
+                             int nout) {
+    if (K != M.K || K > 256 || R % 32 || (R > 128 && R % 128) || plane < (long long)batch * R * K ||
+        M.nd != Plan<true>::S)
+        return SFDE_EUNSUPPORTED;
+    CUtensorMap mapX;
+    SFDE_TRY(map_digit_planes(&mapX, xdigits, R, K, batch, plane, Plan<true>::S));
+    OzArgs a{};
+    a.R = R; a.K = K; a.N = M.N; a.batch = batch;
+    a.out = out; a.out_stride = out_stride; a.err = err;
+    return launch_oz<true>(c, mapX, M, a, c->stream, nr, nc, nout);
 }
 
 extern "C" sfde_status sfde_debug_oz_gemm(const double* X, int batch, int R, int K, const double* Mat, int N,
@@ -483,7 +498,7 @@ extern "C" sfde_status sfde_debug_oz_gemm(const double* X, int batch, int R, int
     sfde_status st = SFDE_OK;
     cudaError_t e = cudaSuccess;
     int herr = 0;
-    st = sfde_oz_split_matrix(Mat, K, N, &M, nullptr);
+    st = sfde_oz_split_matrix(Mat, K, N, &M, nullptr, 1.0, false);
     if (st == SFDE_OK) {
         if ((e = cudaMalloc(&digits, sfde_oz_digit_bytes(R, K, batch))) != cudaSuccess ||
             (e = cudaMalloc(&xe, sizeof(int) * (size_t)batch * R)) != cudaSuccess ||

@@ -1,0 +1,325 @@
+// The FP64-accurate space-time residual of Eq. (2.4),
+//     rho_n = F_n + M_h (U_{n-1} - U_n) - tau_n K (U_{n-1} + U_n),   n = 1..N_t,
+// assembled in integer arithmetic around two digit-split BF16 tensor-core products.
+//
+// The FP64 pipe of this GPU runs at about 1/64 of the FP32 rate, so every FP64 operation per
+// element of the space-time grid costs about as much as a whole tensor-core product.  Here the
+// iterate is read once as FP64 bit patterns and everything up to the final combination is exact
+// integer work:
+//   1. per time point, E_n with max |U_n| < 2^{E_n} (an integer max over the bit patterns);
+//   2. per pair (n-1, n) with E = max(E_{n-1}, E_n): the fixed-point values fix(u) = round(u 2^{54-E})
+//      (|fix| <= 2^54), V = fix(U_{n-1}) + fix(U_n) and W = V (1, 4, 1) along x, both exact, written
+//      as seven balanced base-256 digits each (BF16-exact; 2V exactly, W to 2^-57 of 2^58);
+//   3. Z1 = V (K_x h_y/6 A_x) and Z2 = (K_y h_x/6 A_y) W on the tensor cores (ozaki.cu, 28 digit
+//      products), each an int64 in units of 2^{-52} of the operands' scales;
+//   4. with the mass matrices M = (h/6) tridiag(1, 4, 1) in both directions,
+//          K V = (1,4,1)_y Z1 + Z2      (integer, aligned to a common power of two),
+//          M_h (U_{n-1} - U_n) = (h_x h_y / 36) (1,4,1)_y (1,4,1)_x (fix(U_{n-1}) - fix(U_n)),
+//      and rho = F + c_m S9 - tau c_s S in FP64: two conversions and two FMAs per element.
+// The fixed-point grid of a pair is 2^{E-54}: values far below the slice maximum keep an absolute
+// accuracy of 2^{-55} max|U|, the scale at which an FP64 product's rounding errors enter the residual.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "sfde_internal.cuh"
+
+namespace {
+
+// max over one slice of |u| as a bit pattern -> E with max|u| < 2^E (2047 exponent: not finite)
+__global__ void __launch_bounds__(256) k_slice_maxexp(const double* __restrict__ U, size_t P2, int* __restrict__ E) {
+    const unsigned long long* u = (const unsigned long long*)(U + (size_t)blockIdx.x * P2);
+    unsigned long long mx = 0;
+    for (size_t e = threadIdx.x * 2; e < P2; e += blockDim.x * 2) {
+        const ulonglong2 v = *(const ulonglong2*)(u + e);
+        mx = max(mx, max(v.x & 0x7FFFFFFFFFFFFFFFull, v.y & 0x7FFFFFFFFFFFFFFFull));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __shared__ unsigned long long red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, red[w]);
+        mx = max(mx, red[0]);
+        E[blockIdx.x] = (int)(mx >> 52) - 1022;   // 1.f 2^{ex-1023} < 2^{ex-1022}
+    }
+}
+
+// round(u 2^{54-E}) for |u| < 2^E from the bit pattern (integer operations only); |result| <= 2^54
+__device__ __forceinline__ long long fixp(unsigned long long bits, int E) {
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    if (ex == 0) return 0;                                    // zero or below 2^-1022
+    const long long m = (long long)((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+    const int sh = E + 1021 - ex;                             // >= -1 because |u| < 2^E
+    long long r;
+    if (sh <= 0) r = m << (-sh);
+    else if (sh >= 62) r = 0;
+    else r = (m + (1ll << (sh - 1))) >> sh;
+    return (bits >> 63) ? -r : r;
+}
+
+// BF16 bit pattern of a small integer |d| <= 256 (exact): 1.5 2^23 + d is exact in FP32
+__device__ __forceinline__ uint16_t bf16_of_int(int d) {
+    const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+    return (uint16_t)(__float_as_uint(f) >> 16);
+}
+
+constexpr int ND = 7;  // digits per operand
+
+// Balanced base-256 digits of x (|x| <= 2^T, T >= 56): x = d_1 2^{T-8} + sum_{p=2..7} d_p 2^{T-8p} + r
+// with d_1 in [-256, 256], d_p in [-128, 127] and |r| <= 2^{T-57} (r = 0 for T = 56).  Adding
+// C = sum_{p>=2} 128 2^{T-8p} (+ 2^{T-57} to round) turns every lower digit into an unsigned byte, so
+// each digit is one shift and mask.
+template <int T>
+__device__ __forceinline__ void split7(long long x, uint16_t (&bf)[ND]) {
+    static_assert(T >= 56 && T <= 61, "digit frame");
+    constexpr unsigned long long C = 128ull * ((1ull << (T - 16)) + (1ull << (T - 24)) + (1ull << (T - 32)) +
+                                               (1ull << (T - 40)) + (1ull << (T - 48)) + (1ull << (T - 56))) +
+                                     (T > 56 ? (1ull << (T > 56 ? T - 57 : 0)) : 0ull);
+    const long long xp = x + (long long)C;
+    bf[0] = bf16_of_int((int)(xp >> (T - 8)));
+#pragma unroll
+    for (int p = 1; p < ND; ++p) bf[p] = bf16_of_int((int)((unsigned long long)(xp >> (T - 8 * (p + 1))) & 255u) - 128);
+}
+
+// V = fix(U_{n-1}) + fix(U_n) and W = V (1,4,1)_x for one 32 x 32 tile of pair b (n = n0 + b):
+// V's digits row-major [b][j][i] (rows of the A_x product), W's digits transposed [b][i][j].
+__global__ void __launch_bounds__(256) k_split_pair(const double* __restrict__ U, const int* __restrict__ En, int n0,
+                                                    int Px, int Py, uint16_t* __restrict__ dV, long long planeV,
+                                                    uint16_t* __restrict__ dW, long long planeW) {
+    __shared__ long long vs[32][35];      // rows j0.., columns i0-1 .. i0+32
+    __shared__ uint16_t wd[ND][32][34];   // W digits, [p][i][j]
+    const int b = blockIdx.z, n = n0 + b;
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int E = max(En[n - 1], En[n]);
+    const size_t P2 = (size_t)Px * Py;
+    const unsigned long long* Un = (const unsigned long long*)(U + (size_t)n * P2);
+    const unsigned long long* Um = (const unsigned long long*)(U + (size_t)(n - 1) * P2);
+    for (int jj = ty; jj < 32; jj += 8) {
+        const size_t row = (size_t)(j0 + jj) * Px;
+        for (int c = tx; c < 34; c += 32) {
+            const int i = i0 + c - 1;
+            long long v = 0;
+            if (i >= 0 && i < Px) v = fixp(Un[row + i], E) + fixp(Um[row + i], E);
+            vs[jj][c] = v;
+        }
+    }
+    __syncthreads();
+    for (int jj = ty; jj < 32; jj += 8) {
+        uint16_t bf[ND];
+        split7<56>(2 * vs[jj][tx + 1], bf);          // 2V: |2V| <= 2^56, represented exactly
+        const size_t o = ((size_t)b * Py + j0 + jj) * Px + i0 + tx;
+#pragma unroll
+        for (int p = 0; p < ND; ++p) dV[p * planeV + o] = bf[p];
+        split7<58>(vs[jj][tx] + 4 * vs[jj][tx + 1] + vs[jj][tx + 2], bf);   // |W| <= 6 2^55 < 2^58
+#pragma unroll
+        for (int p = 0; p < ND; ++p) wd[p][tx][jj] = bf[p];
+    }
+    __syncthreads();
+    for (int ii = ty; ii < 32; ii += 8) {
+        const size_t o = ((size_t)b * Px + i0 + ii) * Py + j0 + tx;
+#pragma unroll
+        for (int p = 0; p < ND; ++p) dW[p * planeW + o] = wd[p][ii][tx];
+    }
+}
+
+// rounding arithmetic right shift (k >= 0)
+__device__ __forceinline__ long long rshr(long long x, int k) {
+    if (k <= 0) return x;
+    if (k >= 62) return 0;
+    return (x + (1ll << (k - 1))) >> k;
+}
+
+// rho for one 32 x 32 tile of pair b.  Z1 = T1[b][i][j] counts 2^{E+ex-51} (2V / 2^56 times the
+// matrix over 2^ex, in units of 2^-52), Z2 = T3[b][j][i] counts 2^{E+ey-48} (W / 2^58), fixed-point
+// values count 2^{E-54}.  |Z| <= K 2^52 = 2^60, so (1,4,1) Z1 stays below 2^63 and both terms are
+// halved at least once before they are added.  Writes rho (BF16 or TF32-rounded FP32), zero
+// outside the interior nodes, and one FP64 sum of rho^2 per block.
+template <typename OT>
+__global__ void __launch_bounds__(256) k_combine_int(
+    const long long* __restrict__ T1, const long long* __restrict__ T3, const double* __restrict__ U,
+    const int* __restrict__ En, int n0, int Px, int Py, int nx, int ny, double cmass, int ex, int ey,
+    const double* __restrict__ dt, int rank, const double* __restrict__ time_w, const double* __restrict__ bxn,
+    const double* __restrict__ byn, OT* __restrict__ rout, long long rout_stride, double* __restrict__ partial) {
+    __shared__ long long t1[32][35];      // Z1 rows i0.., columns j0-1 .. j0+32
+    __shared__ long long du[34][35];      // fix(U_{n-1}) - fix(U_n), rows j0-1.., columns i0-1..
+    __shared__ double red[8];
+    const int b = blockIdx.z, n = n0 + b;
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int E = max(En[n - 1], En[n]);
+    const size_t P2 = (size_t)Px * Py;
+    const long long* T1b = T1 + (size_t)b * P2;
+    for (int ii = ty; ii < 32; ii += 8)
+        for (int c = tx; c < 34; c += 32) {
+            const int j = j0 + c - 1;
+            t1[ii][c] = (j >= 0 && j < Py) ? T1b[(size_t)(i0 + ii) * Py + j] : 0;
+        }
+    const unsigned long long* Un = (const unsigned long long*)(U + (size_t)n * P2);
+    const unsigned long long* Um = (const unsigned long long*)(U + (size_t)(n - 1) * P2);
+    for (int r = ty; r < 34; r += 8)
+        for (int c = tx; c < 34; c += 32) {
+            const int j = j0 + r - 1, i = i0 + c - 1;
+            long long v = 0;
+            if (j >= 0 && j < Py && i >= 0 && i < Px) {
+                const size_t e = (size_t)j * Px + i;
+                v = fixp(Um[e], E) - fixp(Un[e], E);
+            }
+            du[r][c] = v;
+        }
+    __syncthreads();
+    const int u1 = E + ex - 51, u2 = E + ey - 48, u = max(u1, u2) + 1;
+    const double tau = 0.5 * dt[n - 1];
+    const double cs = -tau * ldexp(1.0, u);
+    const double cm = cmass * ldexp(1.0, E - 54);
+    const bool finite = E < 1024;
+    const int i = i0 + tx;
+    double sq = 0.0;
+    for (int jj = ty; jj < 32; jj += 8) {
+        const int j = j0 + jj;
+        double rho = 0.0;
+        if (i < nx && j < ny) {
+            const long long k1 = t1[tx][jj] + 4 * t1[tx][jj + 1] + t1[tx][jj + 2];
+            const long long st = rshr(k1, u - u1) + rshr(T3[(size_t)b * P2 + (size_t)j * Px + i], u - u2);
+            long long s9 = 0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const long long row = du[jj + a][tx] + 4 * du[jj + a][tx + 1] + du[jj + a][tx + 2];
+                s9 += a == 1 ? 4 * row : row;
+            }
+            double f = 0.0;
+            for (int q = 0; q < rank; ++q)
+                f += time_w[(size_t)(n - 1) * rank + q] * byn[(size_t)q * Py + j] * bxn[(size_t)q * Px + i];
+            rho = fma(cm, (double)s9, fma(cs, (double)st, f));
+            if (!finite) rho = __longlong_as_double(0x7FF8000000000000ll);
+        }
+        sq = fma(rho, rho, sq);
+        OT* o = rout + (size_t)b * rout_stride + (size_t)j * Px + i;
+        if (sizeof(OT) == 2) *o = (OT)__float2bfloat16_rn((float)rho);
+        else *o = (OT)sfde_round_tf32((float)rho);
+    }
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    const int w = (ty * 32 + tx) >> 5;
+    if ((tx & 31) == 0) red[w] = sq;
+    __syncthreads();
+    if (tx == 0 && ty == 0) {
+        double s = 0.0;
+        for (int k = 0; k < 8; ++k) s += red[k];
+        partial[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+}  // namespace
+
+size_t sfde_resid_int_digit_bytes(int Px, int Py, int batch) { return (size_t)ND * Px * Py * batch * 2; }
+
+sfde_status sfde_resid_int_matrices(sfde_ctx* c, OzMatrix* Ax, OzMatrix* Ay) {
+    // K_x M_y (x) A_x = (1,4,1)_y (x) (K_x h_y / 6) A_x and K_y A_y (x) M_x = (K_y h_x / 6) A_y (x) (1,4,1)_x
+    SFDE_TRY(sfde_oz_split_matrix(c->x.A, c->x.P, c->x.P, Ax, c->stream, c->kx * c->y.h / 6.0, true));
+    SFDE_TRY(sfde_oz_split_matrix(c->y.A, c->y.P, c->y.P, Ay, c->stream, c->ky * c->x.h / 6.0, true));
+    return SFDE_OK;
+}
+
+sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
+                              long long rout_stride, int out_kind, double* partial, int* n_partials,
+                              const OzMatrix& Ax, const OzMatrix& Ay, void* dV, void* dW, int* En, int* err) {
+    const int Px = c->x.P, Py = c->y.P;
+    const size_t P2 = c->P2();
+    const size_t esz = out_kind == 0 ? 2 : 4;
+    if (Px > 256 || Py > 256 || n_first < 1 || count < 1) return SFDE_EINVAL;
+    k_slice_maxexp<<<count + 1, 256, 0, c->stream>>>(U + (size_t)(n_first - 1) * P2, P2, En + (n_first - 1));
+    sfde_count_launch(c);
+    int total = 0;
+    for (int b0 = 0; b0 < count; b0 += (int)c->ws_slices) {
+        const int nb = std::min(count - b0, (int)c->ws_slices);
+        const int n0 = n_first + b0;
+        const long long plane = (long long)nb * Px * Py;
+        dim3 grid(Px / 32, Py / 32, nb), block(32, 8);
+        k_split_pair<<<grid, block, 0, c->stream>>>(U, En, n0, Px, Py, (uint16_t*)dV, plane, (uint16_t*)dW, plane);
+        sfde_count_launch(c);
+        SFDE_TRY(sfde_oz_gemm_int(c, dV, plane, Py, Px, nb, Ax, (long long*)c->T1, (long long)P2, err, c->y.n,
+                                  c->x.n, c->x.n));
+        SFDE_TRY(sfde_oz_gemm_int(c, dW, plane, Px, Py, nb, Ay, (long long*)c->T3, (long long)P2, err, c->x.n,
+                                  c->y.n, c->y.n));
+        const int blocks = (Px / 32) * (Py / 32) * nb;
+        if ((size_t)(total + blocks) > c->partial_cap) return SFDE_EINVAL;
+        char* ro = (char*)rout + (size_t)b0 * rout_stride * esz;
+        const double cmass = c->x.h * c->y.h / 36.0;
+        if (out_kind == 0)
+            k_combine_int<__nv_bfloat16><<<grid, block, 0, c->stream>>>(
+                (const long long*)c->T1, (const long long*)c->T3, U, En, n0, Px, Py, c->x.n, c->y.n, cmass,
+                Ax.e_uniform, Ay.e_uniform, c->dt0, c->rank, c->time_w, c->bxn, c->byn, (__nv_bfloat16*)ro,
+                rout_stride, partial + total);
+        else
+            k_combine_int<float><<<grid, block, 0, c->stream>>>(
+                (const long long*)c->T1, (const long long*)c->T3, U, En, n0, Px, Py, c->x.n, c->y.n, cmass,
+                Ax.e_uniform, Ay.e_uniform, c->dt0, c->rank, c->time_w, c->bxn, c->byn, (float*)ro, rout_stride,
+                partial + total);
+        sfde_count_launch(c);
+        total += blocks;
+    }
+    SFDE_CUDA(cudaGetLastError());
+    if (n_partials) *n_partials = total;
+    return SFDE_OK;
+}
+
+extern "C" sfde_status sfde_debug_residual(sfde_ctx* c, const double* U, int use_tensor_cores, float* rho,
+                                          double* norm2) {
+    if (!c || !U || !rho || !norm2) return SFDE_EINVAL;
+    const int Px = c->x.P, Py = c->y.P;
+    if (use_tensor_cores && (Px > 256 || Py > 256)) return SFDE_EUNSUPPORTED;
+    const size_t P2 = c->P2(), n2 = (size_t)c->x.n * c->y.n;
+    double* u = nullptr;
+    SFDE_TRY(sfde_level0(c, &u));
+    SFDE_TRY(sfde_ensure_workspace(c, std::min<size_t>(c->nt, 128)));
+    const size_t need = (size_t)c->nt * (Px / 16) * (Py / 16) + 64;
+    if (c->partial_cap < need) {
+        cudaFree(c->partial);
+        c->partial = nullptr;
+        SFDE_CUDA(cudaMalloc(&c->partial, sizeof(double) * need));
+        c->partial_cap = need;
+    }
+    double* tmp = nullptr;
+    float *rp = nullptr, *ru = nullptr;
+    OzMatrix Ax, Ay;
+    void *dV = nullptr, *dW = nullptr;
+    int *En = nullptr, *err = nullptr;
+    sfde_status st = SFDE_OK;
+    int np = 0;
+    cudaError_t e;
+#define DC(x) if ((e = (x)) != cudaSuccess) { sfde_set_last_cuda_error(e, #x, __FILE__, __LINE__); st = SFDE_ECUDA; goto done; }
+    DC(cudaMalloc(&tmp, sizeof(double) * n2 * (c->nt + 1)));
+    DC(cudaMalloc(&rp, sizeof(float) * P2 * c->nt));
+    DC(cudaMalloc(&ru, sizeof(float) * n2 * c->nt));
+    DC(cudaMalloc(&err, sizeof(int)));
+    DC(cudaMemset(err, 0, sizeof(int)));
+    if ((st = sfde_copy_in(tmp, U, sizeof(double) * n2 * (c->nt + 1), c->stream)) != SFDE_OK) goto done;
+    sfde_launch_pad(tmp, u, c->y.n, c->x.n, Py, Px, c->nt + 1, c->stream);
+    if (use_tensor_cores) {
+        if ((st = sfde_resid_int_matrices(c, &Ax, &Ay)) != SFDE_OK) goto done;
+        DC(cudaMalloc(&dV, sfde_resid_int_digit_bytes(Px, Py, (int)c->ws_slices)));
+        DC(cudaMalloc(&dW, sfde_resid_int_digit_bytes(Px, Py, (int)c->ws_slices)));
+        DC(cudaMalloc(&En, sizeof(int) * (c->nt + 1)));
+        st = sfde_residual_int(c, u, 1, c->nt, rp, (long long)P2, 1, c->partial, &np, Ax, Ay, dV, dW, En, err);
+    } else {
+        st = sfde_residual_fp64(c, u, 1, c->nt, rp, (long long)P2, 1, c->partial, &np);
+    }
+    if (st != SFDE_OK) goto done;
+    if ((st = sfde_reduce_partials(c, np, norm2)) != SFDE_OK) goto done;
+    sfde_launch_unpad_f32(rp, ru, c->y.n, c->x.n, Py, Px, c->nt, c->stream);  // one float per interior node
+    if ((st = sfde_copy_out(rho, ru, sizeof(float) * n2 * c->nt, c->stream)) != SFDE_OK) goto done;
+    DC(cudaStreamSynchronize(c->stream));
+    {
+        int herr = 0;
+        DC(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (herr) st = SFDE_ETIMEOUT;
+    }
+done:
+#undef DC
+    sfde_oz_free_matrix(&Ax);
+    sfde_oz_free_matrix(&Ay);
+    cudaFree(tmp); cudaFree(rp); cudaFree(ru); cudaFree(dV); cudaFree(dW); cudaFree(En); cudaFree(err);
+    return st;
+}

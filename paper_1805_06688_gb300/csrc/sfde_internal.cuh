@@ -186,10 +186,15 @@ sfde_status sfde_fused_step(sfde_ctx* c, int P, const CUtensorMap& U, const CUte
 struct OzMatrix {            // a fixed K x N FP64 matrix split into SFDE_OZ_DIGITS BF16 digit planes
     int K = 0, N = 0;
     void* digits = nullptr;  // planes of N x K (K-major)
-    int* exps = nullptr;     // one exponent per column
+    int* exps = nullptr;     // one exponent per column (device)
+    int e_uniform = 0;       // the common exponent when split with one scale for the whole matrix
+    int nd = 0;              // digit planes: 7 with one scale (integer-output product), else 6
     CUtensorMap map;
 };
-sfde_status sfde_oz_split_matrix(const double* Mat, int K, int N, OzMatrix* out, cudaStream_t s);
+// digits of alpha * Mat; uniform: one exponent (max_kn |alpha m_kn| < 2^e) for all columns and seven
+// digits (for sfde_oz_gemm_int), else one exponent per column and six digits (for sfde_oz_gemm)
+sfde_status sfde_oz_split_matrix(const double* Mat, int K, int N, OzMatrix* out, cudaStream_t s, double alpha,
+                                 bool uniform);
 void sfde_oz_free_matrix(OzMatrix* m);
 size_t sfde_oz_digit_bytes(int R, int K, int batch);
 // Out_b = ((X_b [+ X2_b]) Mat)^T in FP64 accuracy; digits (sfde_oz_digit_bytes) and xe (batch x R ints)
@@ -198,11 +203,21 @@ sfde_status sfde_oz_gemm(sfde_ctx* c, const double* X, const double* X2, long lo
                          int batch, const OzMatrix& M, void* digits, int* xe, double* out, long long out_stride,
                          int* err, int nr, int nc, int nout);
 
-// The space-time residual of sfde_residual_fp64 with both dense products on the tensor cores
-// (Px, Py <= 256); digits / xe / err: scratch for sfde_oz_gemm.
-sfde_status sfde_residual_oz(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
-                             long long rout_stride, int out_kind, double* partial, int* n_partials,
-                             const OzMatrix& Ax, const OzMatrix& Ay, void* digits, int* xe, int* err);
+// The same product on pre-split operand digits (seven planes `plane` elements apart) with the 28 digit
+// products p + q <= 8, written as int64 in units of 2^-52 of the operand scales (uniform-exponent
+// matrix); exact up to rounding the p + q >= 7 terms to that unit.
+sfde_status sfde_oz_gemm_int(sfde_ctx* c, void* xdigits, long long plane, int R, int K, int batch,
+                             const OzMatrix& M, long long* out, long long out_stride, int* err, int nr, int nc,
+                             int nout);
+
+// ---- the space-time residual of sfde_residual_fp64 in integer arithmetic around two digit-split
+// tensor-core products (resid_int.cu), Px, Py <= 256.  Ax, Ay from sfde_resid_int_matrices; dV, dW:
+// sfde_resid_int_digit_bytes(Px, Py, ws_slices) each; En: N_t + 1 ints; err: device error word.
+size_t sfde_resid_int_digit_bytes(int Px, int Py, int batch);
+sfde_status sfde_resid_int_matrices(sfde_ctx* c, OzMatrix* Ax, OzMatrix* Ay);
+sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
+                              long long rout_stride, int out_kind, double* partial, int* n_partials,
+                              const OzMatrix& Ax, const OzMatrix& Ay, void* dV, void* dW, int* En, int* err);
 void sfde_launch_mass_x_transpose(const double* Un, const double* Um, double* T2, int Px, int Py, double hx,
                                   int nb, cudaStream_t s);
 

@@ -1,6 +1,7 @@
 """The FP64 space-time residual of the mixed-precision solver against the oracle's definition
-rho_n = F_n + B_n U_{n-1} - S_n U_n (Eq. (2.4)), for both ways of forming the dense products:
-FP64 arithmetic and the digit-split BF16 tensor-core product.
+rho_n = F_n + B_n U_{n-1} - S_n U_n (Eq. (2.4)), for both ways of forming it: FP64 arithmetic,
+and exact integer arithmetic around digit-split BF16 tensor-core products (fixed point on a grid
+of 2^-54 of each pair of time slices' maximum).
 
 The norm is accumulated in FP64 before the values are rounded for the low-precision solver, so
 ||rho|| must agree to FP64-product accuracy: 1e-11 relative to ||S U|| (the scale that cancels
@@ -67,3 +68,37 @@ def test_residual_matches_oracle(use_tc, nx, ny, nt, near):
     assert abs(nrm - np.sqrt(np.sum(ref ** 2))) <= 1e-11 * scale, (nrm, np.sqrt(np.sum(ref ** 2)), scale)
     tol = 2.0 ** -10 * np.abs(ref).max(axis=(1, 2), keepdims=True) + 1e-13 * scale
     assert np.all(np.abs(rho - ref) <= tol)
+
+
+@pytest.mark.parametrize("use_tc", [0, 1])
+def test_residual_wide_dynamic_range(use_tc):
+    """Values spread over eight decades inside each slice, slices of very different size (and one
+    exactly zero): the fixed-point grid follows each pair of slices, so the residual still agrees
+    with the oracle to FP64-product accuracy."""
+    nx, ny, nt = 60, 45, 10
+    t = time_grid(nt, 1.0, "uniform")
+    O = osfde.SFDE(0.8, 0.7, 1.0, 2.0, nx, ny, t)
+    rng = np.random.default_rng(7)
+    U = rng.standard_normal((nt + 1, ny, nx)) * 10.0 ** rng.uniform(-8, 0, (nt + 1, ny, nx))
+    U *= 10.0 ** rng.uniform(-20, 20, (nt + 1, 1, 1))
+    U[4] = 0.0
+    P = sfde.Problem(0.8, 0.7, 1.0, 2.0, nx, ny, t, precision=sfde.PREC_MIXED_TF32)
+    rho, nrm = gpu_residual(P, np.ascontiguousarray(U), use_tc)
+    ref, scale = oracle_residual(O, U, None)
+    assert abs(nrm - np.sqrt(np.sum(ref ** 2))) <= 1e-11 * scale
+    # per time point: error relative to that step's own terms
+    for n in range(nt):
+        tau = 0.5 * (t[n + 1] - t[n])
+        terms = np.sqrt(np.sum(O.apply_B(U[n], tau) ** 2) + np.sum(O.apply_S(U[n + 1], tau) ** 2))
+        assert np.sqrt(np.sum((rho[n] - ref[n]) ** 2)) <= 2.0 ** -10 * np.sqrt(np.sum(ref[n] ** 2)) + 1e-12 * terms
+
+
+def test_residual_not_finite():
+    """A non-finite iterate gives a non-finite residual norm (the solver's divergence check)."""
+    nx, ny, nt = 40, 40, 6
+    t = time_grid(nt, 1.0, "uniform")
+    U = np.random.default_rng(1).standard_normal((nt + 1, ny, nx))
+    U[3, 5, 7] = np.inf
+    P = sfde.Problem(0.8, 0.7, 1.0, 2.0, nx, ny, t, precision=sfde.PREC_MIXED_TF32)
+    _, nrm = gpu_residual(P, U, 1)
+    assert not np.isfinite(nrm)
