@@ -103,7 +103,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-KERNEL_SOURCES = {"k_slice_gemm_fp64": ("step_fp64.cu",), "k_tc_slice_gemm": ("gemm_tc.cu", "tc_common.cuh")}
+KERNEL_SOURCES = {
+    "k_slice_gemm_fp64": ("step_fp64.cu",),
+    "k_tc_slice_gemm": ("gemm_tc.cu", "tc_common.cuh"),
+    "k_fused_step": ("fused_step.cu", "tc_common.cuh"),
+    "k_ozaki_slice_gemm": ("ozaki.cu", "tc_common.cuh"),
+    "k_split_pair+k_combine_int": ("resid_int.cu",),
+}
 
 
 def kernel_source_sha(kernel: str):
@@ -113,9 +119,10 @@ def kernel_source_sha(kernel: str):
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(kernel: str, flops_per_launch: float):
+def traffic_from_profile(kernel: str, flops_per_launch: float, bytes_per_launch: float):
     """DRAM bytes per launch from a committed ncu summary (profiles/traffic.json), scaled by the
-    algorithmic work of the launch, if the counters were taken on the current kernel source."""
+    algorithmic work of the launch (flops, or bytes for a kernel without flops), if the counters
+    were taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(path))[kernel]
@@ -123,7 +130,9 @@ def traffic_from_profile(kernel: str, flops_per_launch: float):
         return None
     if d.get("source_sha") != kernel_source_sha(kernel):
         return None
-    return d["dram_bytes_per_flop"] * flops_per_launch
+    if "dram_bytes_per_flop" in d:
+        return d["dram_bytes_per_flop"] * flops_per_launch
+    return d["dram_bytes_per_alg_byte"] * bytes_per_launch
 
 
 # ----------------------------------------------------------------------------- oracle timing
@@ -183,38 +192,46 @@ def run_reference(args, w):
 
 # ----------------------------------------------------------------------------- roofline
 
-KERNEL_CLASSES = (
-    ("k_slice_gemm_fp64", "FP64 slice GEMM of the spectral step"),
-    ("k_slice_gemm_fp64", "FP64 slice GEMM of the space-time residual"),
-    ("k_tc_slice_gemm", "tcgen05 slice GEMM (BF16/TF32 operands, FP32 accumulate)"),
+KERNEL_CLASSES = (  # the library's accounting classes (include/sfde.h, sfde_profile)
+    ("k_slice_gemm_fp64", "FP64 slice GEMM of a step", "alu"),
+    ("k_slice_gemm_fp64", "FP64 slice GEMM of the space-time residual", "alu"),
+    ("k_tc_slice_gemm", "tcgen05 slice GEMM of a low-precision step (BF16/TF32)", "tc"),
+    ("k_fused_step", "fused BF16 spectral step: four tcgen05 products per slice on chip", "tc"),
+    ("k_ozaki_slice_gemm", "digit-split residual products: 28 BF16 tcgen05 products, exact int64", "tc"),
+    ("k_split_pair+k_combine_int", "integer residual assembly (exponents, digits, combination)", "hbm"),
 )
 
 
 def roofline_from_profile(prof, precision: str):
     """Roofline of the kernel class with the largest device time, plus a per-class breakdown.
 
-    FP64 GEMMs are bound by the FP64 pipe (peak = measured BF16 x nominal FP64/BF16 ratio); the
-    tensor-core GEMM is placed by its algorithmic intensity against the ridge point: below it the
-    bound is HBM bandwidth (algorithmic bytes / time), above it the tensor pipe of its dtype."""
+    Each class's launches are timed with CUDA events inside the solve (a long step), so the
+    denominators are the sustained measured rates.  FP64 SIMT GEMMs are bound by the FP64 pipe
+    (measured BF16 x nominal FP64/BF16); tensor-core kernels are placed by algorithmic intensity
+    against the ridge point (below it: HBM bandwidth, above it: the tensor pipe of their dtype);
+    the integer assembly kernels move bytes only."""
     pk, src = peaks()
-    fp64_peak = pk["bf16_tflops"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
-    tc_peak = pk["bf16_tflops"] * (0.5 if precision == "mixed-tf32" else 1.0)
+    bf16 = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    fp64_peak = bf16 * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
     kernels = []
-    for k, (name, what) in enumerate(KERNEL_CLASSES):
+    for k, (name, what, kind) in enumerate(KERNEL_CLASSES):
+        if k >= len(prof.launches):
+            break
         n, ms, fl, by = prof.launches[k], prof.ms[k], prof.flops[k], prof.bytes[k]
         if n == 0 or ms <= 0:
             continue
         tfs = fl / (ms * 1e-3) / 1e12
         gbs = by / (ms * 1e-3) / 1e9
-        if k < 2:
+        tc_peak = bf16 * (0.5 if (k == 2 and precision == "mixed-tf32") else 1.0)
+        if kind == "alu":
             bound, ach, peak, unit = "alu", tfs, fp64_peak, "TFLOP/s"
-            psrc = f"{src} BF16 {pk['bf16_tflops']} TFLOP/s x nominal FP64/BF16 {NOMINAL_FP64_TFLOPS}/{NOMINAL_BF16_TFLOPS}"
-        elif fl / by < tc_peak * 1e12 / (pk["hbm_gbs"] * 1e9):
+            psrc = f"{src} sustained BF16 {bf16} TFLOP/s x nominal FP64/BF16 {NOMINAL_FP64_TFLOPS}/{NOMINAL_BF16_TFLOPS}"
+        elif kind == "hbm" or fl / by < tc_peak * 1e12 / (pk["hbm_gbs"] * 1e9):
             bound, ach, peak, unit = "hbm", gbs, pk["hbm_gbs"], "GB/s"
             psrc = f"{src} HBM copy bandwidth"
         else:
             bound, ach, peak, unit = "tensor", tfs, tc_peak, "TFLOP/s"
-            psrc = f"{src} BF16 dense" + (" x 1/2 (TF32 nominal ratio)" if precision == "mixed-tf32" else "")
+            psrc = f"{src} sustained BF16 dense" + (" x 1/2 (TF32 nominal ratio)" if tc_peak < bf16 else "")
         kernels.append({
             "kernel": name, "what": what, "launches": int(n), "ms": ms, "share": None,
             "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
@@ -229,12 +246,13 @@ def roofline_from_profile(prof, precision: str):
     roofline = {
         "bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"], "unit": dom["unit"],
         "frac": dom["frac"],
-        "traffic": traffic_from_profile(dom["kernel"], dom["algorithmic_flops_per_launch"]),
+        "traffic": traffic_from_profile(dom["kernel"], dom["algorithmic_flops_per_launch"],
+                                        dom["algorithmic_bytes_per_launch"]),
         "kernel": f"{dom['kernel']} ({dom['what']})", "peak_source": dom["peak_source"],
         "launches": dom["launches"], "avg_launch_us": dom["avg_launch_us"],
         "algorithmic_flops_per_launch": dom["algorithmic_flops_per_launch"],
         "algorithmic_bytes_per_launch": dom["algorithmic_bytes_per_launch"],
-        "share_of_gemm_time": dom["share"],
+        "share_of_accounted_time": dom["share"],
     }
     return roofline, kernels
 

@@ -193,14 +193,20 @@ sfde_status sfde_get_operator(sfde_ctx* ctx, int dir, double* coeffs, double* la
 
 /*
  * Kernel accounting for roofline reports (no counterpart in the paper).
- * sfde_profile_enable resets the counters; with enable != 0 every launch of the slice-GEMM kernels
+ * sfde_profile_enable resets the counters; with enable != 0 every launch of the accounted kernels
  * is additionally bracketed by CUDA events on the context's stream, and its device time and
- * algorithmic work (2 n_R n_C n_out flops with unpadded sizes; bytes = X read + Mat read + Out
- * written, plus the extra slices an epilogue reads) are accumulated per kernel class:
- *   0 = FP64 step GEMM, 1 = FP64 space-time residual GEMM, 2 = tensor-core (BF16/TF32) GEMM.
+ * algorithmic work (flops of the products with unpadded sizes; bytes each launch must move at
+ * least once) are accumulated per kernel class:
+ *   0 = FP64 slice GEMM of a step (2 n_R n_C n_out flops per product),
+ *   1 = FP64 slice GEMM of the space-time residual (P > 256),
+ *   2 = tensor-core slice GEMM of a low-precision step (BF16/TF32; four per step),
+ *   3 = fused low-precision step (BF16; 4 n_x n_y (n_x + n_y) flops per slice),
+ *   4 = digit-split tensor-core product of the residual (BF16 digit products actually computed:
+ *       28 (integer output) or 21 (FP64 output) times 2 n_R n_C n_out),
+ *   5 = integer residual assembly (exponents, digit splitting, combination; bytes only).
  * kernel_launches counts every kernel this library launched on the context.
  */
-#define SFDE_PROF_CLASSES 3
+#define SFDE_PROF_CLASSES 6
 typedef struct {
     long long kernel_launches;
     long long launches[SFDE_PROF_CLASSES];

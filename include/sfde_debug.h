@@ -38,9 +38,10 @@ sfde_status sfde_debug_oz_gemm(const double* X, int batch, int R, int K, const d
  * The FP64 space-time residual of the mixed-precision solver for a given iterate (Eq. (2.4)):
  *   rho_n = F_n + B_n U_{n-1} - S_n U_n,  n = 1..N_t,
  * U: (N_t+1) x N_y x N_x doubles (host or device); rho: N_t x N_y x N_x floats (host or device),
- * rounded to TF32 as the solver stores it; *norm2 = sum of rho_n^2 accumulated in FP64 before
- * rounding.  use_tensor_cores = 1 forms the two dense products per time point on the BF16 tensor
- * cores by digit splitting (P_x, P_y <= 256), 0 with FP64 arithmetic.  Synchronous; allocates scratch.
+ * rounded to TF32 as the solver stores it; *norm2 = sum of rho_n^2.  use_tensor_cores = 1 assembles
+ * rho in integer arithmetic around digit-split BF16 tensor-core products (P_x, P_y <= 256; *norm2
+ * from the stored FP32 values, relative accuracy about 2^-22), 0 with FP64 arithmetic (*norm2 of
+ * the FP64 values).  Synchronous; allocates scratch.
  */
 sfde_status sfde_debug_residual(sfde_ctx* ctx, const double* U, int use_tensor_cores, float* rho,
                                 double* norm2);

@@ -25,7 +25,7 @@ exported_symbols = (
 )
 
 
-PROF_CLASSES = 3  # 0: FP64 step GEMM, 1: FP64 residual GEMM, 2: tensor-core GEMM
+PROF_CLASSES = 6  # see include/sfde.h: FP64 step, FP64 residual, TC GEMM, fused step, digit products, int assembly
 
 
 class SfdeProfile(C.Structure):

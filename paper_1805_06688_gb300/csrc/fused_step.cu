@@ -331,7 +331,7 @@ sfde_status launch(sfde_ctx* c, const CUtensorMap& U, const CUtensorMap& O1, con
         const double nb = a.batch, nx = c->x.n, ny = c->y.n;
         const double slice = nx * ny;
         const double io = (2.0 + (a.g ? 1.0 : 0.0) + (a.ut ? 1.0 : 0.0)) * nb * slice;
-        sfde_prof_end(c, slot, 2, nb * 4.0 * slice * (nx + ny), 2.0 * (io + 2.0 * nx * nx + 2.0 * ny * ny));
+        sfde_prof_end(c, slot, 3, nb * 4.0 * slice * (nx + ny), 2.0 * (io + 2.0 * nx * nx + 2.0 * ny * ny));
         sfde_count_launch(c);
     }
     SFDE_CUDA(cudaGetLastError());

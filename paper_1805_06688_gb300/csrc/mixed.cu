@@ -107,7 +107,7 @@ struct SfdeMixed {
     // FP64-accurate residual in integer arithmetic around tensor-core products (P <= 256)
     bool use_oz = false;
     OzMatrix oAx, oAy;
-    void *oz_dV = nullptr, *oz_dW = nullptr;
+    void *oz_dV = nullptr, *oz_dVt = nullptr;
     int* oz_E = nullptr;
     // each BF16 step as one fused four-product kernel (P_x = P_y in {128, 256})
     bool fused = false;
@@ -127,7 +127,7 @@ void sfde_free_mixed(sfde_ctx* c) {
     sfde_oz_free_matrix(&M->oAx);
     sfde_oz_free_matrix(&M->oAy);
     cudaFree(M->oz_dV);
-    cudaFree(M->oz_dW);
+    cudaFree(M->oz_dVt);
     cudaFree(M->oz_E);
     if (M->cap) cudaStreamDestroy(M->cap);
     delete M;
@@ -224,7 +224,7 @@ sfde_status setup_mixed(sfde_ctx* c, int kind, int m, int max_levels, int min_co
     if (M->use_oz) {
         SFDE_TRY(sfde_resid_int_matrices(c, &M->oAx, &M->oAy));
         SFDE_CUDA(cudaMalloc(&M->oz_dV, sfde_resid_int_digit_bytes(Px, Py, (int)c->ws_slices)));
-        SFDE_CUDA(cudaMalloc(&M->oz_dW, sfde_resid_int_digit_bytes(Px, Py, (int)c->ws_slices)));
+        SFDE_CUDA(cudaMalloc(&M->oz_dVt, sfde_resid_int_digit_bytes(Px, Py, (int)c->ws_slices)));
         SFDE_CUDA(cudaMalloc(&M->oz_E, sizeof(int) * ((size_t)c->nt + 1)));
     }
     size_t need = (size_t)c->nt * (size_t)(c->x.P / 16) * (c->y.P / 16) + 64;
@@ -476,7 +476,7 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
         int np = 0;
         if (M->use_oz)
             SFDE_TRY(sfde_residual_int(c, U, 1, c->nt, E.slice(L0.g, 1), (long long)P2, kind, c->partial, &np,
-                                       M->oAx, M->oAy, M->oz_dV, M->oz_dW, M->oz_E, M->err));
+                                       M->oAx, M->oAy, M->oz_dV, M->oz_dVt, M->oz_E, M->err));
         else
             SFDE_TRY(sfde_residual_fp64(c, U, 1, c->nt, E.slice(L0.g, 1), (long long)P2, kind, c->partial, &np));
         double r2 = 0.0;

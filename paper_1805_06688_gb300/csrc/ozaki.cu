@@ -29,9 +29,11 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 32, KC = 64;
-constexpr int XTILE = BM * KC * 2;     // 16 KB: one digit plane of the 128-row tile, one K chunk
-constexpr int MTILE = BN * KC * 2;     // 4 KB
+// K chunks of 32 BF16 (64-byte rows, 64-byte swizzle) in a three-stage ring: a stage holds every
+// digit plane of one chunk of both operands (7 x 10 KB), so loads overlap the products.
+constexpr int BM = 128, BN = 32, KC = 32, STAGES = 3;
+constexpr int XTILE = BM * KC * 2;     // 8 KB: one digit plane of the 128-row tile, one K chunk
+constexpr int MTILE = BN * KC * 2;     // 2 KB
 constexpr int TMEM_COLS = 512;
 
 // Digit plans.  Partial sums of an accumulator must stay integers of magnitude <= 2^24 (exact in
@@ -64,8 +66,20 @@ __constant__ int c7_prod[28][3] = {
     {1, 7, 10}, {7, 1, 10}, {2, 6, 11}, {3, 5, 11}, {4, 4, 11}, {5, 3, 11}, {6, 2, 12},
 };
 
+// table entries with the plan chosen at compile time (direct constant-bank reads, no generic loads)
 template <bool INT_OUT>
-constexpr size_t smem_bytes() { return 1024 + (size_t)Plan<INT_OUT>::S * (XTILE + MTILE) + 256; }
+__device__ __forceinline__ int prod_entry(int i, int k) {
+    if constexpr (INT_OUT) return c7_prod[i][k];
+    else return c6_prod[i][k];
+}
+template <bool INT_OUT>
+__device__ __forceinline__ int acc_digit_sum(int a) {
+    if constexpr (INT_OUT) return c7_acc_d[a];
+    else return c6_acc_d[a];
+}
+
+template <bool INT_OUT>
+constexpr size_t smem_bytes() { return 1024 + (size_t)STAGES * Plan<INT_OUT>::S * (XTILE + MTILE) + 256; }
 
 struct OzArgs {
     int R, K, N, batch;          // X slice R x K (digits in planes of nslices x R x K), Mat K x N
@@ -87,27 +101,26 @@ __global__ void __launch_bounds__(128, 1)
 k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapM, OzArgs p) {
     constexpr int S = Plan<INT_OUT>::S, NPROD = Plan<INT_OUT>::NPROD, NACC = Plan<INT_OUT>::NACC;
     constexpr int STAGE = S * (XTILE + MTILE);
-    const int (*c_prod)[3] = INT_OUT ? c7_prod : c6_prod;
-    const int* c_acc_d = INT_OUT ? c7_acc_d : c6_acc_d;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* sX = smem;                       // S planes x 16 KB
-    uint8_t* sM = smem + S * XTILE;           // S planes x 4 KB
-    uint64_t* full = (uint64_t*)(smem + STAGE);
-    uint64_t* empty = full + 1;
-    uint64_t* accf = full + 2;
-    uint32_t* tmem_slot = (uint32_t*)(full + 3);
+    // stage st: S X planes (8 KB each) then S matrix planes (2 KB each)
+    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accf = empty + STAGES;
+    uint64_t* fin = accf + 1;
+    uint32_t* tmem_slot = (uint32_t*)(fin + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long m0 = (long long)blockIdx.x * BM;
-    const int n0 = blockIdx.y * BN;
+    // the N tiles of one M tile are neighbours in launch order: they share the X digit planes in L2
+    const long long m0 = (long long)blockIdx.y * BM;
+    const int n0 = blockIdx.x * BN;
     const long long Mtot = (long long)p.batch * p.R;
     const int nchunks = (p.K + KC - 1) / KC;
 
     if (threadIdx.x == 0) {
-        tc::mbar_init(full, 1);
-        tc::mbar_init(empty, 1);
+        for (int st = 0; st < STAGES; ++st) { tc::mbar_init(&full[st], 1); tc::mbar_init(&empty[st], 1); }
         tc::mbar_init(accf, 1);
+        tc::mbar_init(fin, 1);
         tc::mbar_fence_init();
         tc::prefetch_tmap(&mapX);
         tc::prefetch_tmap(&mapM);
@@ -120,35 +133,54 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
     const int b0 = (int)(m0 / p.R), r0 = (int)(m0 % p.R);
     bool ok = true;
     if (warp == 0 && lane == 0) {
+        int issued = 0;
         for (int c = 0; c < nchunks && ok; ++c) {
-            if (c > 0) ok = tc::mbar_wait(empty, (uint32_t)(c - 1) & 1u, p.err, tc::ERR_WAIT_EMPTY);
+            const int st = c % STAGES;
+            if (c >= STAGES) ok = tc::mbar_wait(&empty[st], (uint32_t)(c / STAGES - 1) & 1u, p.err, tc::ERR_WAIT_EMPTY);
             if (!ok) break;
-            tc::mbar_arrive_expect_tx(full, (uint32_t)STAGE);
+            uint8_t* sX = smem + st * STAGE;
+            uint8_t* sM = sX + S * XTILE;
+            tc::mbar_arrive_expect_tx(&full[st], (uint32_t)STAGE);
             for (int d = 0; d < S; ++d) {
-                tc::tma_load_4d(sX + d * XTILE, &mapX, full, c * KC, r0, b0, d);
-                tc::tma_load_3d(sM + d * MTILE, &mapM, full, c * KC, n0, d);
+                tc::tma_load_4d(sX + d * XTILE, &mapX, &full[st], c * KC, r0, b0, d);
+                tc::tma_load_3d(sM + d * MTILE, &mapM, &full[st], c * KC, n0, d);
             }
+            ++issued;
         }
+        // own copies in flight must land before the CTA's shared memory goes away
+        for (int c = issued - STAGES < 0 ? 0 : issued - STAGES; c < issued; ++c)
+            tc::mbar_wait(&full[c % STAGES], (uint32_t)(c / STAGES) & 1u, p.err, tc::ERR_WAIT_FULL);
     } else if (warp == 1 && lane == 0) {
         const uint32_t idesc = tc::idesc_f32acc(1u, BM, BN);
+        bool any = false;
         for (int c = 0; c < nchunks && ok; ++c) {
-            ok = tc::mbar_wait(full, (uint32_t)c & 1u, p.err, tc::ERR_WAIT_FULL);
+            const int st = c % STAGES;
+            ok = tc::mbar_wait(&full[st], (uint32_t)(c / STAGES) & 1u, p.err, tc::ERR_WAIT_FULL);
             if (!ok) break;
             tc::tc_fence_after();
+            const uint8_t* sX = smem + st * STAGE;
+            const uint8_t* sM = sX + S * XTILE;
+#pragma unroll
             for (int i = 0; i < NPROD; ++i) {
-                const int dp = c_prod[i][0] - 1, dq = c_prod[i][1] - 1, a = c_prod[i][2];
+                const int dp = prod_entry<INT_OUT>(i, 0) - 1, dq = prod_entry<INT_OUT>(i, 1) - 1;
+                const int a = prod_entry<INT_OUT>(i, 2);
                 // the first product of an accumulator in the first chunk overwrites it
-                const bool first = (c == 0) && (i == 0 || c_prod[i - 1][2] != a);
+                const bool first = (c == 0) && (i == 0 || prod_entry<INT_OUT>(i - 1, 2) != a);
 #pragma unroll
                 for (int kk = 0; kk < KC / 16; ++kk) {
-                    const uint64_t ad = tc::smem_desc_sw128(sX + dp * XTILE + kk * 32);
-                    const uint64_t bd = tc::smem_desc_sw128(sM + dq * MTILE + kk * 32);
+                    const uint64_t ad = tc::smem_desc_sw64(sX + dp * XTILE + kk * 32);
+                    const uint64_t bd = tc::smem_desc_sw64(sM + dq * MTILE + kk * 32);
                     tc::mma<0>(tmem + (uint32_t)(a * BN), ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
                 }
             }
-            tc::mma_commit(empty);
+            any = true;
+            tc::mma_commit(&empty[st]);
         }
         if (ok) tc::mma_commit(accf);
+        else if (any) {  // products still running must finish before TMEM is freed
+            tc::mma_commit(fin);
+            tc::mbar_wait(fin, 0, p.err, tc::ERR_WAIT_ACC);
+        }
     }
 
     const bool acc_ok = __all_sync(0xffffffffu, tc::mbar_wait(accf, 0, p.err, tc::ERR_WAIT_ACC));
@@ -163,7 +195,7 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
         for (int a = 0; a < NACC; ++a) {
             uint32_t v[32];
             tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * BN), v);
-            const int d = c_acc_d[a];
+            const int d = acc_digit_sum<INT_OUT>(a);
             const int sh = d <= 6 ? 52 - 8 * d : 8 * (8 - d);
 #pragma unroll
             for (int j = 0; j < BN; ++j) {
@@ -190,7 +222,7 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
         for (int a = 0; a < NACC; ++a) {
             uint32_t v[32];
             tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * BN), v);
-            const int d = c_acc_d[a];
+            const int d = acc_digit_sum<INT_OUT>(a);
 #pragma unroll
             for (int j = 0; j < BN; ++j) {
                 const long long s = (long long)__float2ll_rn(__uint_as_float(v[j]));  // exact integer
@@ -404,7 +436,7 @@ sfde_status sfde_oz_split_matrix(const double* Mat, int K, int N, OzMatrix* out,
     cuuint32_t box[3] = {KC, BN, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(&out->map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, out->digits, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return SFDE_EINVAL;
     SFDE_CUDA(cudaFuncSetAttribute(k_ozaki_slice_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -433,7 +465,7 @@ sfde_status map_digit_planes(CUtensorMap* map, void* digits, int R, int K, int b
     cuuint32_t box[4] = {KC, (cuuint32_t)(R < BM ? R : BM), (cuuint32_t)(R < BM ? BM / R : 1), 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, digits, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? SFDE_OK : SFDE_EINVAL;
 }
@@ -441,12 +473,16 @@ sfde_status map_digit_planes(CUtensorMap* map, void* digits, int R, int K, int b
 template <bool INT_OUT>
 sfde_status launch_oz(sfde_ctx* c, const CUtensorMap& mapX, const OzMatrix& M, const OzArgs& a, cudaStream_t s,
                       int nr, int nc, int nout) {
-    dim3 grid((unsigned)(((long long)a.batch * a.R + BM - 1) / BM), M.N / BN);
+    const long long mt = ((long long)a.batch * a.R + BM - 1) / BM;
+    if (mt > 65535) return SFDE_EINVAL;
+    dim3 grid(M.N / BN, (unsigned)mt);
     const int slot = sfde_prof_begin(c);
     k_ozaki_slice_gemm<INT_OUT><<<grid, 128, smem_bytes<INT_OUT>(), s>>>(mapX, M.map, a);
-    // tensor work: 21 digit products of 2 R K N flops each (counted as the FP64 product it replaces)
-    sfde_prof_end(c, slot, 1, 2.0 * a.batch * nr * nc * nout,
-                  8.0 * ((double)a.batch * nr * nc + (double)a.batch * nr * nout));
+    // tensor work: NPROD digit products of 2 R K N flops each; bytes: the digit planes of X, the
+    // matrix digits and the output (8 bytes per element) once
+    constexpr int S = Plan<INT_OUT>::S, NPROD = Plan<INT_OUT>::NPROD;
+    sfde_prof_end(c, slot, 4, (double)NPROD * 2.0 * a.batch * nr * nc * nout,
+                  2.0 * S * ((double)a.batch * nr * nc + (double)nc * nout) + 8.0 * a.batch * nr * nout);
     sfde_count_launch(c);
     SFDE_CUDA(cudaGetLastError());
     return SFDE_OK;

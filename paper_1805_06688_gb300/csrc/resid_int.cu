@@ -8,14 +8,16 @@
 // integer work:
 //   1. per time point, E_n with max |U_n| < 2^{E_n} (an integer max over the bit patterns);
 //   2. per pair (n-1, n) with E = max(E_{n-1}, E_n): the fixed-point values fix(u) = round(u 2^{54-E})
-//      (|fix| <= 2^54), V = fix(U_{n-1}) + fix(U_n) and W = V (1, 4, 1) along x, both exact, written
-//      as seven balanced base-256 digits each (BF16-exact; 2V exactly, W to 2^-57 of 2^58);
-//   3. Z1 = V (K_x h_y/6 A_x) and Z2 = (K_y h_x/6 A_y) W on the tensor cores (ozaki.cu, 28 digit
+//      (|fix| <= 2^54) and V = fix(U_{n-1}) + fix(U_n), exact, written as seven balanced base-256
+//      digits of 2V (BF16-exact, no remainder) in row-major and in transposed order;
+//   3. Z1 = V (K_x h_y/6 A_x) and Z2 = (K_y h_x/6 A_y) V on the tensor cores (ozaki.cu, 28 digit
 //      products), each an int64 in units of 2^{-52} of the operands' scales;
-//   4. with the mass matrices M = (h/6) tridiag(1, 4, 1) in both directions,
-//          K V = (1,4,1)_y Z1 + Z2      (integer, aligned to a common power of two),
+//   4. with the mass matrices M = (h/6) tridiag(1, 4, 1) in both directions (they commute with the
+//      products: A_y (V M_x) = (A_y V) M_x),
+//          K V = (1,4,1)_y Z1 + (1,4,1)_x Z2      (integer, aligned to a common power of two),
 //          M_h (U_{n-1} - U_n) = (h_x h_y / 36) (1,4,1)_y (1,4,1)_x (fix(U_{n-1}) - fix(U_n)),
-//      and rho = F + c_m S9 - tau c_s S in FP64: two conversions and two FMAs per element.
+//      and rho = F + c_m S9 - tau c_s S in FP64: two FMAs per element (the int64 -> FP64
+//      conversions are built from bits); the sum of rho^2 is taken over the stored FP32 values.
 // The fixed-point grid of a pair is 2^{E-54}: values far below the slice maximum keep an absolute
 // accuracy of 2^{-55} max|U|, the scale at which an FP64 product's rounding errors enter the residual.
 #include <cuda_bf16.h>
@@ -83,13 +85,12 @@ __device__ __forceinline__ void split7(long long x, uint16_t (&bf)[ND]) {
     for (int p = 1; p < ND; ++p) bf[p] = bf16_of_int((int)((unsigned long long)(xp >> (T - 8 * (p + 1))) & 255u) - 128);
 }
 
-// V = fix(U_{n-1}) + fix(U_n) and W = V (1,4,1)_x for one 32 x 32 tile of pair b (n = n0 + b):
-// V's digits row-major [b][j][i] (rows of the A_x product), W's digits transposed [b][i][j].
+// V = fix(U_{n-1}) + fix(U_n) for one 32 x 32 tile of pair b (n = n0 + b): the digits of 2V
+// row-major [b][j][i] (rows of the A_x product) and transposed [b][i][j] (rows of the A_y product).
 __global__ void __launch_bounds__(256) k_split_pair(const double* __restrict__ U, const int* __restrict__ En, int n0,
-                                                    int Px, int Py, uint16_t* __restrict__ dV, long long planeV,
-                                                    uint16_t* __restrict__ dW, long long planeW) {
-    __shared__ long long vs[32][35];      // rows j0.., columns i0-1 .. i0+32
-    __shared__ uint16_t wd[ND][32][34];   // W digits, [p][i][j]
+                                                    int Px, int Py, uint16_t* __restrict__ dV, uint16_t* __restrict__ dVt,
+                                                    long long plane) {
+    __shared__ uint16_t dt[ND][32][34];   // digits, [p][i][j]
     const int b = blockIdx.z, n = n0 + b;
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -98,31 +99,42 @@ __global__ void __launch_bounds__(256) k_split_pair(const double* __restrict__ U
     const unsigned long long* Un = (const unsigned long long*)(U + (size_t)n * P2);
     const unsigned long long* Um = (const unsigned long long*)(U + (size_t)(n - 1) * P2);
     for (int jj = ty; jj < 32; jj += 8) {
-        const size_t row = (size_t)(j0 + jj) * Px;
-        for (int c = tx; c < 34; c += 32) {
-            const int i = i0 + c - 1;
-            long long v = 0;
-            if (i >= 0 && i < Px) v = fixp(Un[row + i], E) + fixp(Um[row + i], E);
-            vs[jj][c] = v;
-        }
-    }
-    __syncthreads();
-    for (int jj = ty; jj < 32; jj += 8) {
+        const size_t e = (size_t)(j0 + jj) * Px + i0 + tx;
         uint16_t bf[ND];
-        split7<56>(2 * vs[jj][tx + 1], bf);          // 2V: |2V| <= 2^56, represented exactly
-        const size_t o = ((size_t)b * Py + j0 + jj) * Px + i0 + tx;
+        split7<56>(2 * (fixp(Un[e], E) + fixp(Um[e], E)), bf);     // |2V| <= 2^56, represented exactly
+        const size_t o = (size_t)b * P2 + e;
 #pragma unroll
-        for (int p = 0; p < ND; ++p) dV[p * planeV + o] = bf[p];
-        split7<58>(vs[jj][tx] + 4 * vs[jj][tx + 1] + vs[jj][tx + 2], bf);   // |W| <= 6 2^55 < 2^58
-#pragma unroll
-        for (int p = 0; p < ND; ++p) wd[p][tx][jj] = bf[p];
+        for (int p = 0; p < ND; ++p) {
+            dV[p * plane + o] = bf[p];
+            dt[p][tx][jj] = bf[p];
+        }
     }
     __syncthreads();
     for (int ii = ty; ii < 32; ii += 8) {
         const size_t o = ((size_t)b * Px + i0 + ii) * Py + j0 + tx;
 #pragma unroll
-        for (int p = 0; p < ND; ++p) dW[p * planeW + o] = wd[p][ii][tx];
+        for (int p = 0; p < ND; ++p) dVt[p * plane + o] = dt[p][ii][tx];
     }
+}
+
+// Exact int64 -> FP64 conversion, round to nearest even, from integer operations (the conversion
+// instruction runs on the slow FP64 pipe).
+__device__ __forceinline__ double i64_to_f64(long long x) {
+    if (x == 0) return 0.0;
+    const unsigned long long sgn = (unsigned long long)x & 0x8000000000000000ull;
+    const unsigned long long a = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+    int e = 63 - __clzll((long long)a);                   // a in [2^e, 2^{e+1})
+    unsigned long long m;
+    if (e <= 52) {
+        m = a << (52 - e);
+    } else {
+        const int sh = e - 52;
+        const unsigned long long rem = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        m = a >> sh;
+        if (rem > half || (rem == half && (m & 1ull))) ++m;
+        if (m == (1ull << 53)) { m >>= 1; ++e; }
+    }
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 1023) << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 
 // rounding arithmetic right shift (k >= 0)
@@ -132,20 +144,22 @@ __device__ __forceinline__ long long rshr(long long x, int k) {
     return (x + (1ll << (k - 1))) >> k;
 }
 
-// rho for one 32 x 32 tile of pair b.  Z1 = T1[b][i][j] counts 2^{E+ex-51} (2V / 2^56 times the
-// matrix over 2^ex, in units of 2^-52), Z2 = T3[b][j][i] counts 2^{E+ey-48} (W / 2^58), fixed-point
-// values count 2^{E-54}.  |Z| <= K 2^52 = 2^60, so (1,4,1) Z1 stays below 2^63 and both terms are
-// halved at least once before they are added.  Writes rho (BF16 or TF32-rounded FP32), zero
+// rho for one 32 x 32 tile of pair b.  Z1 = T1[b][i][j] counts 2^{E+ex-51} and Z2 = T3[b][j][i]
+// counts 2^{E+ey-51} (2V / 2^56 times the matrix over 2^e, in units of 2^-52), fixed-point values
+// count 2^{E-54}.  |Z| <= K 2^52 = 2^60, so (1,4,1) Z stays below 2^63, and both terms are halved
+// at least once before they are added.  Writes rho (BF16 or TF32-rounded FP32), zero
 // outside the interior nodes, and one FP64 sum of rho^2 per block.
 template <typename OT>
-__global__ void __launch_bounds__(256) k_combine_int(
+__global__ void __launch_bounds__(256, 4) k_combine_int(
     const long long* __restrict__ T1, const long long* __restrict__ T3, const double* __restrict__ U,
     const int* __restrict__ En, int n0, int Px, int Py, int nx, int ny, double cmass, int ex, int ey,
     const double* __restrict__ dt, int rank, const double* __restrict__ time_w, const double* __restrict__ bxn,
     const double* __restrict__ byn, OT* __restrict__ rout, long long rout_stride, double* __restrict__ partial) {
     __shared__ long long t1[32][35];      // Z1 rows i0.., columns j0-1 .. j0+32
+    __shared__ long long t3[32][35];      // Z2 rows j0.., columns i0-1 .. i0+32
     __shared__ long long du[34][35];      // fix(U_{n-1}) - fix(U_n), rows j0-1.., columns i0-1..
     __shared__ double red[8];
+    __shared__ double cst[2];             // c_m 2^{E-54}, -tau 2^u
     const int b = blockIdx.z, n = n0 + b;
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -156,6 +170,12 @@ __global__ void __launch_bounds__(256) k_combine_int(
         for (int c = tx; c < 34; c += 32) {
             const int j = j0 + c - 1;
             t1[ii][c] = (j >= 0 && j < Py) ? T1b[(size_t)(i0 + ii) * Py + j] : 0;
+        }
+    const long long* T3b = T3 + (size_t)b * P2;
+    for (int jj = ty; jj < 32; jj += 8)
+        for (int c = tx; c < 34; c += 32) {
+            const int i = i0 + c - 1;
+            t3[jj][c] = (i >= 0 && i < Px) ? T3b[(size_t)(j0 + jj) * Px + i] : 0;
         }
     const unsigned long long* Un = (const unsigned long long*)(U + (size_t)n * P2);
     const unsigned long long* Um = (const unsigned long long*)(U + (size_t)(n - 1) * P2);
@@ -169,20 +189,23 @@ __global__ void __launch_bounds__(256) k_combine_int(
             }
             du[r][c] = v;
         }
+    const int u1 = E + ex - 51, u2 = E + ey - 51, u = max(u1, u2) + 1;
+    if (tx == 0 && ty == 0) {
+        cst[0] = ldexp(cmass, E - 54);
+        cst[1] = ldexp(-0.5 * dt[n - 1], u);
+    }
     __syncthreads();
-    const int u1 = E + ex - 51, u2 = E + ey - 48, u = max(u1, u2) + 1;
-    const double tau = 0.5 * dt[n - 1];
-    const double cs = -tau * ldexp(1.0, u);
-    const double cm = cmass * ldexp(1.0, E - 54);
+    const double cm = cst[0], cs = cst[1];
     const bool finite = E < 1024;
     const int i = i0 + tx;
-    double sq = 0.0;
+    float sq = 0.f;   // of the stored values; the norm only decides when the iteration stops
     for (int jj = ty; jj < 32; jj += 8) {
         const int j = j0 + jj;
         double rho = 0.0;
         if (i < nx && j < ny) {
             const long long k1 = t1[tx][jj] + 4 * t1[tx][jj + 1] + t1[tx][jj + 2];
-            const long long st = rshr(k1, u - u1) + rshr(T3[(size_t)b * P2 + (size_t)j * Px + i], u - u2);
+            const long long k2 = t3[jj][tx] + 4 * t3[jj][tx + 1] + t3[jj][tx + 2];
+            const long long st = rshr(k1, u - u1) + rshr(k2, u - u2);
             long long s9 = 0;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -192,17 +215,19 @@ __global__ void __launch_bounds__(256) k_combine_int(
             double f = 0.0;
             for (int q = 0; q < rank; ++q)
                 f += time_w[(size_t)(n - 1) * rank + q] * byn[(size_t)q * Py + j] * bxn[(size_t)q * Px + i];
-            rho = fma(cm, (double)s9, fma(cs, (double)st, f));
+            rho = fma(cm, i64_to_f64(s9), rank > 0 ? fma(cs, i64_to_f64(st), f) : cs * i64_to_f64(st));
             if (!finite) rho = __longlong_as_double(0x7FF8000000000000ll);
         }
-        sq = fma(rho, rho, sq);
+        const float rf = (float)rho;
+        sq = fmaf(rf, rf, sq);
         OT* o = rout + (size_t)b * rout_stride + (size_t)j * Px + i;
-        if (sizeof(OT) == 2) *o = (OT)__float2bfloat16_rn((float)rho);
-        else *o = (OT)sfde_round_tf32((float)rho);
+        if (sizeof(OT) == 2) *o = (OT)__float2bfloat16_rn(rf);
+        else *o = (OT)sfde_round_tf32(rf);
     }
-    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    double sqd = sq;
+    for (int o = 16; o > 0; o >>= 1) sqd += __shfl_xor_sync(0xffffffffu, sqd, o);
     const int w = (ty * 32 + tx) >> 5;
-    if ((tx & 31) == 0) red[w] = sq;
+    if ((tx & 31) == 0) red[w] = sqd;
     __syncthreads();
     if (tx == 0 && ty == 0) {
         double s = 0.0;
@@ -216,7 +241,8 @@ __global__ void __launch_bounds__(256) k_combine_int(
 size_t sfde_resid_int_digit_bytes(int Px, int Py, int batch) { return (size_t)ND * Px * Py * batch * 2; }
 
 sfde_status sfde_resid_int_matrices(sfde_ctx* c, OzMatrix* Ax, OzMatrix* Ay) {
-    // K_x M_y (x) A_x = (1,4,1)_y (x) (K_x h_y / 6) A_x and K_y A_y (x) M_x = (K_y h_x / 6) A_y (x) (1,4,1)_x
+    // K_x M_y (x) A_x = (1,4,1)_y (x) (K_x h_y / 6) A_x and K_y A_y (x) M_x = (K_y h_x / 6) A_y (x) (1,4,1)_x:
+    // the (1,4,1) stencils are applied to the exact integer products
     SFDE_TRY(sfde_oz_split_matrix(c->x.A, c->x.P, c->x.P, Ax, c->stream, c->kx * c->y.h / 6.0, true));
     SFDE_TRY(sfde_oz_split_matrix(c->y.A, c->y.P, c->y.P, Ay, c->stream, c->ky * c->x.h / 6.0, true));
     return SFDE_OK;
@@ -224,12 +250,16 @@ sfde_status sfde_resid_int_matrices(sfde_ctx* c, OzMatrix* Ax, OzMatrix* Ay) {
 
 sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
                               long long rout_stride, int out_kind, double* partial, int* n_partials,
-                              const OzMatrix& Ax, const OzMatrix& Ay, void* dV, void* dW, int* En, int* err) {
+                              const OzMatrix& Ax, const OzMatrix& Ay, void* dV, void* dVt, int* En, int* err) {
     const int Px = c->x.P, Py = c->y.P;
     const size_t P2 = c->P2();
     const size_t esz = out_kind == 0 ? 2 : 4;
     if (Px > 256 || Py > 256 || n_first < 1 || count < 1) return SFDE_EINVAL;
+    // accounting (class 5): bytes each kernel must move once, unpadded
+    const double nxy = (double)c->x.n * c->y.n;
+    int slot = sfde_prof_begin(c);
     k_slice_maxexp<<<count + 1, 256, 0, c->stream>>>(U + (size_t)(n_first - 1) * P2, P2, En + (n_first - 1));
+    sfde_prof_end(c, slot, 5, 0.0, 8.0 * nxy * (count + 1));
     sfde_count_launch(c);
     int total = 0;
     for (int b0 = 0; b0 < count; b0 += (int)c->ws_slices) {
@@ -237,16 +267,19 @@ sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int cou
         const int n0 = n_first + b0;
         const long long plane = (long long)nb * Px * Py;
         dim3 grid(Px / 32, Py / 32, nb), block(32, 8);
-        k_split_pair<<<grid, block, 0, c->stream>>>(U, En, n0, Px, Py, (uint16_t*)dV, plane, (uint16_t*)dW, plane);
+        slot = sfde_prof_begin(c);
+        k_split_pair<<<grid, block, 0, c->stream>>>(U, En, n0, Px, Py, (uint16_t*)dV, (uint16_t*)dVt, plane);
+        sfde_prof_end(c, slot, 5, 0.0, (16.0 + 4.0 * ND) * nxy * nb);   // U pair in, 2 x 7 digit planes out
         sfde_count_launch(c);
         SFDE_TRY(sfde_oz_gemm_int(c, dV, plane, Py, Px, nb, Ax, (long long*)c->T1, (long long)P2, err, c->y.n,
                                   c->x.n, c->x.n));
-        SFDE_TRY(sfde_oz_gemm_int(c, dW, plane, Px, Py, nb, Ay, (long long*)c->T3, (long long)P2, err, c->x.n,
+        SFDE_TRY(sfde_oz_gemm_int(c, dVt, plane, Px, Py, nb, Ay, (long long*)c->T3, (long long)P2, err, c->x.n,
                                   c->y.n, c->y.n));
         const int blocks = (Px / 32) * (Py / 32) * nb;
         if ((size_t)(total + blocks) > c->partial_cap) return SFDE_EINVAL;
         char* ro = (char*)rout + (size_t)b0 * rout_stride * esz;
         const double cmass = c->x.h * c->y.h / 36.0;
+        slot = sfde_prof_begin(c);
         if (out_kind == 0)
             k_combine_int<__nv_bfloat16><<<grid, block, 0, c->stream>>>(
                 (const long long*)c->T1, (const long long*)c->T3, U, En, n0, Px, Py, c->x.n, c->y.n, cmass,
@@ -257,6 +290,7 @@ sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int cou
                 (const long long*)c->T1, (const long long*)c->T3, U, En, n0, Px, Py, c->x.n, c->y.n, cmass,
                 Ax.e_uniform, Ay.e_uniform, c->dt0, c->rank, c->time_w, c->bxn, c->byn, (float*)ro, rout_stride,
                 partial + total);
+        sfde_prof_end(c, slot, 5, 0.0, (16.0 + 16.0 + (double)esz) * nxy * nb);   // Z1, Z2, U pair in, rho out
         sfde_count_launch(c);
         total += blocks;
     }
@@ -284,7 +318,7 @@ extern "C" sfde_status sfde_debug_residual(sfde_ctx* c, const double* U, int use
     double* tmp = nullptr;
     float *rp = nullptr, *ru = nullptr;
     OzMatrix Ax, Ay;
-    void *dV = nullptr, *dW = nullptr;
+    void *dV = nullptr, *dVt = nullptr;
     int *En = nullptr, *err = nullptr;
     sfde_status st = SFDE_OK;
     int np = 0;
@@ -300,9 +334,9 @@ extern "C" sfde_status sfde_debug_residual(sfde_ctx* c, const double* U, int use
     if (use_tensor_cores) {
         if ((st = sfde_resid_int_matrices(c, &Ax, &Ay)) != SFDE_OK) goto done;
         DC(cudaMalloc(&dV, sfde_resid_int_digit_bytes(Px, Py, (int)c->ws_slices)));
-        DC(cudaMalloc(&dW, sfde_resid_int_digit_bytes(Px, Py, (int)c->ws_slices)));
+        DC(cudaMalloc(&dVt, sfde_resid_int_digit_bytes(Px, Py, (int)c->ws_slices)));
         DC(cudaMalloc(&En, sizeof(int) * (c->nt + 1)));
-        st = sfde_residual_int(c, u, 1, c->nt, rp, (long long)P2, 1, c->partial, &np, Ax, Ay, dV, dW, En, err);
+        st = sfde_residual_int(c, u, 1, c->nt, rp, (long long)P2, 1, c->partial, &np, Ax, Ay, dV, dVt, En, err);
     } else {
         st = sfde_residual_fp64(c, u, 1, c->nt, rp, (long long)P2, 1, c->partial, &np);
     }
@@ -320,6 +354,6 @@ done:
 #undef DC
     sfde_oz_free_matrix(&Ax);
     sfde_oz_free_matrix(&Ay);
-    cudaFree(tmp); cudaFree(rp); cudaFree(ru); cudaFree(dV); cudaFree(dW); cudaFree(En); cudaFree(err);
+    cudaFree(tmp); cudaFree(rp); cudaFree(ru); cudaFree(dV); cudaFree(dVt); cudaFree(En); cudaFree(err);
     return st;
 }

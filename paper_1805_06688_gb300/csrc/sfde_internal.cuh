@@ -211,13 +211,14 @@ sfde_status sfde_oz_gemm_int(sfde_ctx* c, void* xdigits, long long plane, int R,
                              int nout);
 
 // ---- the space-time residual of sfde_residual_fp64 in integer arithmetic around two digit-split
-// tensor-core products (resid_int.cu), Px, Py <= 256.  Ax, Ay from sfde_resid_int_matrices; dV, dW:
-// sfde_resid_int_digit_bytes(Px, Py, ws_slices) each; En: N_t + 1 ints; err: device error word.
+// tensor-core products (resid_int.cu), Px, Py <= 256.  Ax, Ay from sfde_resid_int_matrices; dV, dVt:
+// sfde_resid_int_digit_bytes(Px, Py, ws_slices) each (digits of 2V row-major and transposed); En:
+// N_t + 1 ints; err: device error word.
 size_t sfde_resid_int_digit_bytes(int Px, int Py, int batch);
 sfde_status sfde_resid_int_matrices(sfde_ctx* c, OzMatrix* Ax, OzMatrix* Ay);
 sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
                               long long rout_stride, int out_kind, double* partial, int* n_partials,
-                              const OzMatrix& Ax, const OzMatrix& Ay, void* dV, void* dW, int* En, int* err);
+                              const OzMatrix& Ax, const OzMatrix& Ay, void* dV, void* dVt, int* En, int* err);
 void sfde_launch_mass_x_transpose(const double* Un, const double* Um, double* T2, int Px, int Py, double hx,
                                   int nb, cudaStream_t s);
 

@@ -111,6 +111,12 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(const void* p) {
     return ((a & 0x3FFFFull) >> 4) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
 }
 
+// The same for 64-byte rows with 64-byte swizzle (layout 4): 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw64(const void* p) {
+    const uint64_t a = smem_u32(p);
+    return ((a & 0x3FFFFull) >> 4) | (1ull << 16) | ((uint64_t)(512 >> 4) << 32) | (1ull << 46) | (4ull << 61);
+}
+
 // Instruction descriptor, dense MMA with FP32 accumulation, both operands K-major:
 //   bits 4-5 D format (1 = F32), 7-9 A format, 10-12 B format (1 = BF16 for kind::f16, 2 = TF32 for
 //   kind::tf32), 17-22 N >> 3, 24-28 M >> 4.
