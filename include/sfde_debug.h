@@ -70,6 +70,21 @@ sfde_status sfde_debug_set_fused_step(sfde_ctx* ctx, int enable);
 sfde_status sfde_debug_lp_step(sfde_ctx* ctx, int fused, int scheme, const double* U, int batch, int n0,
                                const double* g, const double* ut, double* out, double* norm2);
 
+/*
+ * nchain consecutive low-precision steps from each of `batch` slices (ctx precision MIXED_BF16 or
+ * MIXED_TF32), as in the F-relaxation of Algorithm 1:
+ *   x_0 = U[b],  x_{k+1} = Phi(x_k) + g[b][k],  out[b][k] = x_{k+1},  k = 0..nchain-1,
+ * step k of slice b going from t_{n0 + b*nchain + k - 1} to t_{n0 + b*nchain + k}
+ * (n0 >= 1, n0 + batch*nchain - 1 <= N_t); scheme 0 Crank-Nicolson, 1 backward Euler.
+ *   mode 1: one launch of the fused kernel, each CTA chaining the steps of its slice on chip;
+ *   mode 2: nchain launches of the fused kernel (single steps);  mode 0: four slice GEMMs per step.
+ * Modes 1 and 2 need BF16 and P_x = P_y in {128, 256} (else SFDE_EUNSUPPORTED) and give identical
+ * results.  U: batch x N_y x N_x, g (may be NULL) and out: batch x nchain x N_y x N_x doubles (host
+ * or device), rounded to the operand type on input.  Synchronous; allocates scratch.
+ */
+sfde_status sfde_debug_lp_chain(sfde_ctx* ctx, int mode, int scheme, const double* U, int batch, int nchain,
+                                int n0, const double* g, double* out);
+
 #ifdef __cplusplus
 }
 #endif

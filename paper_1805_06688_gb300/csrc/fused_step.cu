@@ -105,12 +105,14 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
     uint64_t* accf = bar + 6;                            // a phase's products complete
     uint64_t* fin = bar + 7;                             // error path: outstanding products complete
     uint32_t* tmem_slot = (uint32_t*)(bar + 8);
-    float* s_A = (float*)(bar + 16);                     // c K_x lambda_x[a], P floats
-    float* s_B = s_A + P;                                // 1 + c K_y lambda_y[q]
-    double* red = (double*)(s_B + P);                    // 4 partial sums
+    float* s_lx = (float*)(bar + 16);                    // K_x lambda_x[a], P floats
+    float* s_ly = s_lx + P;                              // K_y lambda_y[q]
+    double* red = (double*)(s_ly + P);                   // 4 partial sums
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x;
+    const int nchain = p.nchain;
+    const int nphase = 4 * nchain;                       // phases of all chained steps
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2; ++s) { tc::mbar_init(&ofull[s], 1); tc::mbar_init(&oempty[s], 1); }
@@ -120,16 +122,9 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
         tc::mbar_init(fin, 1);
         tc::mbar_fence_init();
     }
-    {
-        // modal factor of this slice's step: d_qa = 1 + c sigma_qa = s_A[a] + s_B[q] with
-        // sigma_qa = K_x lambda_x[a] + K_y lambda_y[q], c = tau = dt/2 (Crank-Nicolson, solve) or dt
-        // (backward Euler); f = 1/d, and 2/d - 1 = (1 - tau sigma)/(1 + tau sigma) for Crank-Nicolson
-        const float dtb = (float)p.dt[p.n0 + b * p.dn - 1];
-        const float cst = p.scheme == SCHEME_BE ? dtb : 0.5f * dtb;
-        for (int i = threadIdx.x; i < P; i += THREADS) {
-            s_A[i] = cst * (p.kx * p.lamx[i]);
-            s_B[i] = fmaf(cst, p.ky * p.lamy[i], 1.f);
-        }
+    for (int i = threadIdx.x; i < P; i += THREADS) {
+        s_lx[i] = p.kx * p.lamx[i];
+        s_ly[i] = p.ky * p.lamy[i];
     }
     if (threadIdx.x < 4) red[threadIdx.x] = 0.0;
     if (warp == 0) tc::tmem_alloc(tmem_slot, G::TMEM_COLS);
@@ -137,8 +132,10 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const __nv_bfloat16* __restrict__ g = p.g ? (const __nv_bfloat16*)p.g + (long long)b * p.g_stride : nullptr;
+    // step k of the chain: output slice dst_k, right-hand side g_k, step size dt[n0 + b dn - 1 + k]
+    const __nv_bfloat16* __restrict__ g0 = p.g ? (const __nv_bfloat16*)p.g + (long long)b * p.g_stride : nullptr;
     const __nv_bfloat16* __restrict__ ut = p.ut ? (const __nv_bfloat16*)p.ut + (long long)b * p.ut_stride : nullptr;
+    __nv_bfloat16* __restrict__ dst0 = (__nv_bfloat16*)p.dst + (long long)b * p.dst_stride;
 
     if (warp == 4) {
         const int s = p.s0 + b * p.ds;
@@ -151,21 +148,23 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                                     s / p.ds);
         }
         __syncwarp();
-        // g and u_target are read only by the last drain: bring them into L2 now
+        // the right-hand sides of the first two steps and u_target are read only by late drains:
+        // bring them into L2 now (the drains prefetch the later steps')
         for (int e = lane; e < P * P * 2 / 128; e += 32) {
-            if (g) prefetch_l2((const char*)g + (size_t)e * 128);
+            if (g0) prefetch_l2((const char*)g0 + (size_t)e * 128);
+            if (g0 && nchain > 1) prefetch_l2((const char*)(g0 + p.g_kstride) + (size_t)e * 128);
             if (ut) prefetch_l2((const char*)ut + (size_t)e * 128);
         }
         if (lane == 0) {
             const CUtensorMap* maps[4] = {&mO1, &mO2, &mO3, &mO4};
             bool ok = true;
             int issued = 0;
-            for (int gi = 0; gi < 4 * G::NATOM && ok; ++gi) {
+            for (int gi = 0; gi < nphase * G::NATOM && ok; ++gi) {
                 const int st = gi & 1;
                 if (gi >= 2) ok = tc::mbar_wait(&oempty[st], (uint32_t)((gi >> 1) - 1) & 1u, p.err, tc::ERR_WAIT_EMPTY);
                 if (!ok) break;
                 tc::mbar_arrive_expect_tx(&ofull[st], (uint32_t)G::ATOM);
-                tc::tma_load_2d(sO + st * G::ATOM, maps[gi / G::NATOM], &ofull[st], (gi % G::NATOM) * 64, 0);
+                tc::tma_load_2d(sO + st * G::ATOM, maps[(gi / G::NATOM) & 3], &ofull[st], (gi % G::NATOM) * 64, 0);
                 ++issued;
             }
             // own copies in flight must land before the CTA's shared memory goes away
@@ -178,7 +177,8 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
             const uint32_t idesc = tc::idesc_f32acc(1u, 128, P);
             bool ok = tc::mbar_wait(dfull, 0, p.err, tc::ERR_WAIT_FULL);
             bool any = false;
-            for (int ph = 0; ph < 4 && ok; ++ph) {
+            for (int ph = 0; ph < nphase && ok; ++ph) {
+                // the Data of phase ph > 0 is written by the drain of phase ph - 1
                 if (ph > 0) ok = tc::mbar_wait(dready, (uint32_t)(ph - 1) & 1u, p.err, tc::ERR_WAIT_FULL);
                 if (!ok) break;
                 tc::tc_fence_after();
@@ -207,20 +207,29 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
             }
         }
     } else {
-        // ---- warps 0-3: accumulator -> next Data operand (phases 1-3) or output (phase 4)
+        // ---- warps 0-3: accumulator -> next Data operand (phases 1-3 of a step, and phase 4 of a
+        // step followed by another) or output (phase 4 of the last step)
         const bool cn = p.scheme == SCHEME_CN;
         double sq = 0.0;
         bool ok = true;
         const uint32_t sD_u = tc::smem_u32(sD);
-        for (int ph = 0; ph < 4; ++ph) {
-            ok = ok && __all_sync(0xffffffffu, tc::mbar_wait(accf, (uint32_t)ph & 1u, p.err, tc::ERR_WAIT_ACC));
+        for (int gph = 0; gph < nphase; ++gph) {
+            const int ph = gph & 3, k = gph >> 2;
+            ok = ok && __all_sync(0xffffffffu, tc::mbar_wait(accf, (uint32_t)gph & 1u, p.err, tc::ERR_WAIT_ACC));
             tc::tc_fence_after();
             if (!ok) break;
+            const bool last = k == nchain - 1;
+            const __nv_bfloat16* __restrict__ g = g0 ? g0 + (long long)k * p.g_kstride : nullptr;
+            // modal factor of this step: d_qa = 1 + c sigma_qa, sigma_qa = K_x lambda_x[a] + K_y lambda_y[q],
+            // c = tau = dt/2 (Crank-Nicolson, solve) or dt (backward Euler); f = 1/d, and
+            // 2/d - 1 = (1 - tau sigma)/(1 + tau sigma) for Crank-Nicolson
+            const float dtb = (float)p.dt[p.n0 + b * p.dn - 1 + k];
+            const float cst = p.scheme == SCHEME_BE ? dtb : 0.5f * dtb;
             for (int h = 0; h < G::NH; ++h) {
                 const int row = h * 128 + warp * 32 + lane;  // M index held by this thread
                 const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * P);
                 if (ph < 3) {
-                    const float Bq = s_B[row];
+                    const float Bq = fmaf(cst, s_ly[row], 1.f);
                     for (int c0 = 0; c0 < P; c0 += 64) {
                         uint32_t v[64];
                         tc::tmem_ld64(taddr + (uint32_t)c0, v);
@@ -231,7 +240,7 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
 #pragma unroll
                             for (int j = 0; j < 64; j += 2) {
                                 // one reciprocal for two modes: 1/d0 = d1 / (d0 d1), 1/d1 = d0 / (d0 d1)
-                                const float d0 = s_A[c0 + j] + Bq, d1 = s_A[c0 + j + 1] + Bq;
+                                const float d0 = fmaf(cst, s_lx[c0 + j], Bq), d1 = fmaf(cst, s_lx[c0 + j + 1], Bq);
                                 const float r = rcp_approx(d0 * d1);
                                 float f0 = d1 * r, f1 = d0 * r;
                                 if (cn) { f0 = fmaf(2.f, f0, -1.f); f1 = fmaf(2.f, f1, -1.f); }
@@ -244,6 +253,28 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                             st_shared_v4(sD_u + sw128<P>(row, c0 + 8 * u), pack_bf16x2(x[8 * u], x[8 * u + 1]),
                                          pack_bf16x2(x[8 * u + 2], x[8 * u + 3]), pack_bf16x2(x[8 * u + 4], x[8 * u + 5]),
                                          pack_bf16x2(x[8 * u + 6], x[8 * u + 7]));
+                    }
+                } else if (!last) {
+                    // chained: X[j = row][i] + g -> BF16, the next step's Data (row j, K = i) and this
+                    // step's output; the output is copied to global memory after the next step starts
+                    const __nv_bfloat16* grow = g ? g + (size_t)row * P : nullptr;
+                    for (int c0 = 0; c0 < P; c0 += 64) {
+                        uint4 gv[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            gv[u] = grow ? __ldg((const uint4*)(grow + c0 + 8 * u)) : make_uint4(0, 0, 0, 0);
+                        uint32_t v[64];
+                        tc::tmem_ld64(taddr + (uint32_t)c0, v);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            float gf[8];
+                            bf16x8_to_f32(gv[u], gf);
+                            float x[8];
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) x[q] = __uint_as_float(v[8 * u + q]) + gf[q];
+                            st_shared_v4(sD_u + sw128<P>(row, c0 + 8 * u), pack_bf16x2(x[0], x[1]), pack_bf16x2(x[2], x[3]),
+                                         pack_bf16x2(x[4], x[5]), pack_bf16x2(x[6], x[7]));
+                        }
                     }
                 } else {
                     // stage this warp's 32 rows (j) in FP32, 16-byte chunks XOR (row % 8), then write
@@ -263,28 +294,28 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                     constexpr int CPR = P / 8;              // 8-column chunks per row
                     constexpr int ITER = CPR;               // 32 rows x CPR chunks over 32 lanes
                     constexpr int UNR = 8;
-                    __nv_bfloat16* __restrict__ dst = (__nv_bfloat16*)p.dst + (long long)b * p.dst_stride;
+                    __nv_bfloat16* __restrict__ dst = dst0 + (long long)k * p.dst_kstride;
                     const int rbase = h * 128 + warp * 32;
                     const bool want_sq = ut && p.partial;
                     float sqf = 0.f;   // FP32 over this lane's 8 x ITER values (the FP64 pipe is ~1/64 rate)
                     for (int i0 = 0; i0 < ITER; i0 += UNR) {
                         uint4 gv[UNR], uv[UNR];
 #pragma unroll
-                        for (int k = 0; k < UNR; ++k) {
-                            const int e = (i0 + k) * 32 + lane, rr = e / CPR, cc = e % CPR;
+                        for (int kk = 0; kk < UNR; ++kk) {
+                            const int e = (i0 + kk) * 32 + lane, rr = e / CPR, cc = e % CPR;
                             const size_t off = (size_t)(rbase + rr) * P + cc * 8;
-                            gv[k] = g ? __ldg((const uint4*)(g + off)) : make_uint4(0, 0, 0, 0);
-                            uv[k] = ut ? __ldg((const uint4*)(ut + off)) : make_uint4(0, 0, 0, 0);
+                            gv[kk] = g ? __ldg((const uint4*)(g + off)) : make_uint4(0, 0, 0, 0);
+                            uv[kk] = ut ? __ldg((const uint4*)(ut + off)) : make_uint4(0, 0, 0, 0);
                         }
 #pragma unroll
-                        for (int k = 0; k < UNR; ++k) {
-                            const int e = (i0 + k) * 32 + lane, rr = e / CPR, cc = e % CPR;
+                        for (int kk = 0; kk < UNR; ++kk) {
+                            const int e = (i0 + kk) * 32 + lane, rr = e / CPR, cc = e % CPR;
                             const float4 x0 = ld_shared_f4(stg + (uint32_t)(rr * G::STAGE_ROW + (((2 * cc) ^ (rr & 7)) << 4)));
                             const float4 x1 = ld_shared_f4(stg + (uint32_t)(rr * G::STAGE_ROW + (((2 * cc + 1) ^ (rr & 7)) << 4)));
                             float xf[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
                             float gf[8], uf[8];
-                            bf16x8_to_f32(gv[k], gf);
-                            bf16x8_to_f32(uv[k], uf);
+                            bf16x8_to_f32(gv[kk], gf);
+                            bf16x8_to_f32(uv[kk], uf);
 #pragma unroll
                             for (int q = 0; q < 8; ++q) xf[q] += gf[q] - uf[q];
                             if (want_sq) {
@@ -303,11 +334,32 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                     __syncwarp();
                 }
             }
-            if (ph < 3) {
+            if (ph < 3 || !last) {
                 // generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 tc::tc_fence_before();
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(dready)) : "memory");
+            }
+            if (ph == 3 && !last) {
+                // while the next step's first product runs: copy this warp's rows of the new Data
+                // (exactly this step's BF16 output) to global memory, one row per warp instruction,
+                // and bring the right-hand side two steps ahead into L2
+                __nv_bfloat16* __restrict__ dst = dst0 + (long long)k * p.dst_kstride;
+                for (int h = 0; h < G::NH; ++h)
+                    for (int r = 0; r < 32; ++r) {
+                        const int row = h * 128 + warp * 32 + r;
+                        for (int c = lane; c < P / 8; c += 32) {
+                            uint4 o;
+                            asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                                         : "=r"(o.x), "=r"(o.y), "=r"(o.z), "=r"(o.w)
+                                         : "r"(sD_u + sw128<P>(row, 8 * c)) : "memory");
+                            *(uint4*)(dst + (size_t)row * P + 8 * c) = o;
+                        }
+                    }
+                if (g0 && k + 2 < nchain) {
+                    const char* gn = (const char*)(g0 + (long long)(k + 2) * p.g_kstride);
+                    for (int e = warp * 32 + lane; e < P * P * 2 / 128; e += 128) prefetch_l2(gn + (size_t)e * 128);
+                }
             }
         }
         for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
@@ -328,10 +380,11 @@ sfde_status launch(sfde_ctx* c, const CUtensorMap& U, const CUtensorMap& O1, con
     const int slot = c ? sfde_prof_begin(c) : -1;
     k_fused_step<P><<<a.batch, THREADS, Geo<P>::SMEM, s>>>(U, O1, O2, O3, O4, a);
     if (c) {
-        const double nb = a.batch, nx = c->x.n, ny = c->y.n;
+        // per slice: the input once, the output and right-hand side of every chained step
+        const double nb = a.batch, nx = c->x.n, ny = c->y.n, nk = a.nchain;
         const double slice = nx * ny;
-        const double io = (2.0 + (a.g ? 1.0 : 0.0) + (a.ut ? 1.0 : 0.0)) * nb * slice;
-        sfde_prof_end(c, slot, 3, nb * 4.0 * slice * (nx + ny), 2.0 * (io + 2.0 * nx * nx + 2.0 * ny * ny));
+        const double io = (1.0 + nk * (1.0 + (a.g ? 1.0 : 0.0)) + (a.ut ? 1.0 : 0.0)) * nb * slice;
+        sfde_prof_end(c, slot, 3, nk * nb * 4.0 * slice * (nx + ny), 2.0 * (io + 2.0 * nx * nx + 2.0 * ny * ny));
         sfde_count_launch(c);
     }
     SFDE_CUDA(cudaGetLastError());
@@ -351,7 +404,9 @@ sfde_status sfde_fused_prepare() {
 sfde_status sfde_fused_step(sfde_ctx* c, int P, const CUtensorMap& U, const CUtensorMap& O1, const CUtensorMap& O2,
                             const CUtensorMap& O3, const CUtensorMap& O4, const FusedStepArgs& a, cudaStream_t s) {
     if (a.batch < 1) return SFDE_OK;
-    if (a.batch > 2147483647 || !a.dst || !a.dt || !a.lamx || !a.lamy || !a.err) return SFDE_EINVAL;
+    if (!a.dst || !a.dt || !a.lamx || !a.lamy || !a.err || a.nchain < 1 || (a.ut && a.nchain != 1) ||
+        a.batch > 65535 * 1024)
+        return SFDE_EINVAL;
     if (((uintptr_t)a.dst | (uintptr_t)a.g | (uintptr_t)a.ut) & 15) return SFDE_EINVAL;
     if (P == 128) return launch<128>(c, U, O1, O2, O3, O4, a, s);
     if (P == 256) return launch<256>(c, U, O1, O2, O3, O4, a, s);

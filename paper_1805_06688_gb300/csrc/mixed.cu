@@ -251,7 +251,7 @@ struct LpEngine {
     // `ns` slices) -> dst slices (stride dst_ds slices); optional g and u-target (stride dn slices).
     sfde_status step(void* src, long long ns, int src0, int ds, int batch, bool solve, int sch,
                      const double* dt, int n0, int dn, void* dst, int dst_ds, const void* g, const void* ut,
-                     double* partial, int* npart) {
+                     double* partial, int* npart, int nchain = 1) {
         const int Px = c->x.P, Py = c->y.P;
         const long long P2l = (long long)P2();
         if (M->fused) {
@@ -259,8 +259,8 @@ struct LpEngine {
             SFDE_TRY(map_for(M, src, Py, Px, ds, ns, &a1));
             if (partial && (size_t)batch > c->partial_cap) return SFDE_EINVAL;
             FusedStepArgs a{};
-            a.s0 = src0; a.ds = ds; a.batch = batch;
-            a.dst = dst; a.dst_stride = (long long)dst_ds * P2l;
+            a.s0 = src0; a.ds = ds; a.batch = batch; a.nchain = nchain;
+            a.dst = dst; a.dst_stride = (long long)dst_ds * P2l; a.dst_kstride = P2l; a.g_kstride = P2l;
             a.g = g; a.g_stride = (long long)dn * P2l;
             a.ut = ut; a.ut_stride = (long long)dn * P2l;
             a.partial = partial;
@@ -269,10 +269,11 @@ struct LpEngine {
             a.err = M->err;
             SFDE_TRY(sfde_fused_step(c, Px, a1, solve ? M->mVTx : M->mWTx, solve ? M->mVTy : M->mWTy, M->mVx,
                                      M->mVy, a, c->stream));
-            steps += batch;
+            steps += (long long)batch * nchain;
             if (npart) *npart = batch;
             return SFDE_OK;
         }
+        if (nchain != 1) return SFDE_EINVAL;
         int total = 0;
         for (int b0 = 0; b0 < batch; b0 += (int)M->ws) {
             const int nb = std::min<int>(batch - b0, (int)M->ws);
@@ -328,9 +329,14 @@ struct LpEngine {
                     dst, dst_ds, slice(Lv.g, n0), ut, partial, npart);
     }
 
+    // F-relaxation: u_{im+j} = Phi(u_{im+j-1}) + g_{im+j}, j = 1..m-1, all intervals i at once; the
+    // fused kernel runs the m-1 steps of an interval in one CTA, each step starting from the last
     sfde_status frelax(int l) {
         LpLevel& Lv = M->lev[l];
         const int nc = Lv.N / m;
+        if (M->fused)
+            return step(Lv.u, Lv.nalloc, 0, m, nc, false, l == 0 ? SCHEME_CN : scheme, Lv.dt, 1, m, slice(Lv.u, 1), m,
+                        slice(Lv.g, 1), nullptr, nullptr, nullptr, m - 1);
         for (int j = 1; j < m; ++j)
             SFDE_TRY(lstep(l, nc, j - 1, m, j, m, slice(Lv.u, j), m, nullptr, nullptr, nullptr));
         return SFDE_OK;
@@ -615,5 +621,63 @@ extern "C" sfde_status sfde_debug_lp_step(sfde_ctx* c, int fused, int scheme, co
     if (st == SFDE_OK) st = check_err(M, c->stream);
     M->fused = saved;
     cudaFree(tu); cudaFree(tp); cudaFree(src); cudaFree(dst); cudaFree(dg); cudaFree(du);
+    return st;
+}
+
+extern "C" sfde_status sfde_debug_lp_chain(sfde_ctx* c, int mode, int scheme, const double* U, int batch, int nchain,
+                                          int n0, const double* g, double* out) {
+    if (!c || !U || !out || batch < 1 || nchain < 1 || n0 < 1 || scheme < 0 || scheme > 1 ||
+        (long long)n0 + (long long)batch * nchain - 1 > c->nt || mode < 0 || mode > 2)
+        return SFDE_EINVAL;
+    if (c->precision != SFDE_PREC_MIXED_BF16 && c->precision != SFDE_PREC_MIXED_TF32) return SFDE_EINVAL;
+    const int kind = c->precision == SFDE_PREC_MIXED_BF16 ? 0 : 1;
+    if (mode != 0 && !sfde_fused_supported(kind, c->x.P, c->y.P)) return SFDE_EUNSUPPORTED;
+    if (!c->mixed || c->mixed->kind != kind) SFDE_TRY(setup_mixed(c, kind, 2, 1, 1));
+    SfdeMixed* M = c->mixed;
+    const size_t P2 = c->P2(), n2 = (size_t)c->x.n * c->y.n;
+    const size_t nout = (size_t)batch * nchain, esz = M->esz;
+    double *tu = nullptr, *tp = nullptr;
+    void *src = nullptr, *dst = nullptr, *dg = nullptr;
+    sfde_status st = SFDE_OK;
+    const bool saved = M->fused;
+    if (cudaMalloc(&tu, sizeof(double) * n2 * nout) != cudaSuccess ||
+        cudaMalloc(&tp, sizeof(double) * P2 * nout) != cudaSuccess || cudaMalloc(&src, P2 * esz * batch) != cudaSuccess ||
+        cudaMalloc(&dst, P2 * esz * (nout + nchain)) != cudaSuccess || cudaMalloc(&dg, P2 * esz * nout) != cudaSuccess)
+        st = SFDE_ENOMEM;
+    if (st == SFDE_OK) st = load_lp(c, U, batch, tu, tp, src, kind);
+    if (st == SFDE_OK && g) st = load_lp(c, g, (int)nout, tu, tp, dg, kind);
+    if (st == SFDE_OK) {
+        LpEngine E{c, M, 2, 1, SFDE_RELAX_FCF, SCHEME_CN};
+        const int sch = scheme == 0 ? SCHEME_CN : SCHEME_BE;
+        const size_t sl = P2 * esz;
+        if (mode == 1) {   // one launch: each CTA runs the nchain steps of its slice
+            M->fused = true;
+            st = E.step(src, batch, 0, 1, batch, false, sch, c->dt0, n0, nchain, dst, nchain, g ? dg : nullptr,
+                        nullptr, nullptr, nullptr, nchain);
+        } else {           // nchain launches of single steps (fused kernel or four slice GEMMs)
+            M->fused = mode == 2;
+            for (int k = 0; k < nchain && st == SFDE_OK; ++k) {
+                // step k reads the outputs of step k-1: slices k-1 + b*nchain of dst (allocated with
+                // nchain spare slices, so the map over batch*nchain slices from there stays inside)
+                void* s = k == 0 ? src : (void*)((char*)dst + (k - 1) * sl);
+                const long long ns = k == 0 ? batch : (long long)nout;
+                st = E.step(s, ns, 0, k == 0 ? 1 : nchain, batch, false, sch, c->dt0, n0 + k, nchain,
+                            (char*)dst + k * sl, nchain, g ? (const void*)((const char*)dg + k * sl) : nullptr,
+                            nullptr, nullptr, nullptr);
+            }
+        }
+    }
+    if (st == SFDE_OK) {
+        const size_t n = P2 * nout;
+        if (kind == 0) k_lp_to_f64<__nv_bfloat16><<<grid_for(n), 256, 0, c->stream>>>((const __nv_bfloat16*)dst, tp, n);
+        else k_lp_to_f64<float><<<grid_for(n), 256, 0, c->stream>>>((const float*)dst, tp, n);
+        sfde_launch_unpad(tp, tu, c->y.n, c->x.n, c->y.P, c->x.P, (int)nout, c->stream);
+        st = sfde_copy_out(out, tu, sizeof(double) * n2 * nout, c->stream);
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (st == SFDE_OK && e != cudaSuccess) { sfde_set_last_cuda_error(e, "debug lp chain", __FILE__, __LINE__); st = SFDE_ECUDA; }
+    if (st == SFDE_OK) st = check_err(M, c->stream);
+    M->fused = saved;
+    cudaFree(tu); cudaFree(tp); cudaFree(src); cudaFree(dst); cudaFree(dg);
     return st;
 }

@@ -167,12 +167,15 @@ sfde_status sfde_tc_gemm(sfde_ctx* c, int kind, int epi, const CUtensorMap& A, c
 // ---- one whole spectral step per CTA, four chained BF16 products on chip (fused_step.cu)
 struct FusedStepArgs {
     int s0, ds, batch;                    // source slices s0 + b*ds (through the slice tensor map)
-    void* dst; long long dst_stride;      // output slice b at dst + b*dst_stride (elements)
-    const void* g; long long g_stride;    // added to the output (or nullptr)
+    int nchain;                           // steps per CTA: step k > 0 starts from step k-1's output
+    void* dst; long long dst_stride;      // output of step k for slice b at dst + b*dst_stride +
+    long long dst_kstride;                //   k*dst_kstride (elements)
+    const void* g; long long g_stride;    // added to the output (or nullptr); step k: + k*g_kstride
+    long long g_kstride;
     const void* ut; long long ut_stride;  // subtracted; sum of squares per slice into partial[b]
     double* partial;                      // batch entries (or nullptr)
     const float* lamx; const float* lamy; float kx, ky;
-    const double* dt; int n0, dn, scheme; // step size of slice b: dt[n0 + b*dn - 1]; SfdeScheme / SCHEME_SOLVE
+    const double* dt; int n0, dn, scheme; // step k of slice b: dt[n0 + b*dn - 1 + k]; SfdeScheme / SCHEME_SOLVE
     int* err;                             // device error word (bounded waits)
 };
 bool sfde_fused_supported(int kind, int Px, int Py);

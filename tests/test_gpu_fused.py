@@ -151,3 +151,56 @@ def test_mixed_bf16_solve_with_and_without_fused_step():
         _, stats = P.mgrit(U=U, m=4, max_levels=8, coarse=sfde.COARSE_BE, rel_tol=1e-11, max_iter=60)
         assert stats.converged
         assert np.abs(U - ref).max() <= 1e-8 * np.abs(ref).max(), fused
+
+
+def mnorm(O, v):
+    """||v||_{M_h} = (v, M_h v)^(1/2) with M_h = M_y (x) M_x (Sec. 2)."""
+    return np.sqrt(np.sum(v * O.apply_mass(v)))
+
+
+def lp_chain(P, mode, scheme, U, nchain, n0, g=None):
+    L = sfde.lib()
+    L.sfde_debug_lp_chain.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    out = np.zeros((U.shape[0], nchain) + U.shape[1:])
+    st = L.sfde_debug_lp_chain(P.ctx, mode, scheme, U.ctypes.data, U.shape[0], nchain, n0,
+                               None if g is None else np.ascontiguousarray(g).ctypes.data, out.ctypes.data)
+    return st, out
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("nx,ny,batch,nchain", [(255, 255, 150, 2), (100, 127, 3, 3), (200, 180, 2, 15)])
+def test_chained_steps(scheme, nx, ny, batch, nchain):
+    """The F-relaxation chain of one fused launch (each CTA keeps its slice on chip from step to
+    step) equals single fused launches bit for bit; it and the four-GEMM steps both follow the
+    oracle's FP64 steps.  Both propagators are contractions in the M_h-norm (Sec. 3: their modal
+    factors are at most 1 in modulus), so rounding errors introduced at each step add up in that
+    norm: after k + 1 steps at most 5u (k + 1).  The two low-precision paths agree to u/2 on the
+    first step, from identical BF16 input; after it their inputs differ slightly and their
+    roundings are no longer the same, so they are compared through the oracle."""
+    n0 = 2
+    nt = n0 + batch * nchain
+    t = time_grid(nt, 1.0, "graded")
+    O = osfde.SFDE(0.7, 0.8, 1.0, 0.5, nx, ny, t)
+    P = sfde.Problem(0.7, 0.8, 1.0, 0.5, nx, ny, t, precision=sfde.PREC_MIXED_BF16)
+    rng = np.random.default_rng(nx + nchain + scheme)
+    U = rng.standard_normal((batch, ny, nx))
+    g = 0.2 * rng.standard_normal((batch, nchain, ny, nx))
+    st1, x1 = lp_chain(P, 1, scheme, U, nchain, n0, g)
+    st2, x2 = lp_chain(P, 2, scheme, U, nchain, n0, g)
+    st0, x0 = lp_chain(P, 0, scheme, U, nchain, n0, g)
+    assert st1 == 0 and st2 == 0 and st0 == 0
+    assert np.array_equal(x1, x2)
+    u = 2.0 ** -9
+    for b in range(batch):
+        x = U[b]
+        for k in range(nchain):
+            n = n0 + b * nchain + k
+            x = O.propagate(x, O.t[n] - O.t[n - 1], "cn" if scheme == 0 else "be") + g[b, k]
+            mref = mnorm(O, x)
+            for xs in (x1, x0):
+                rel = mnorm(O, xs[b, k] - x) / mref
+                assert rel <= 5 * u * (k + 1), (b, k, rel)
+        d = np.sqrt(np.sum((x1[b, 0] - x0[b, 0]) ** 2) / np.sum(x0[b, 0] ** 2))
+        assert d <= u / 2, (b, d)
