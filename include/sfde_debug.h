@@ -39,9 +39,9 @@ sfde_status sfde_debug_oz_gemm(const double* X, int batch, int R, int K, const d
  *   rho_n = F_n + B_n U_{n-1} - S_n U_n,  n = 1..N_t,
  * U: (N_t+1) x N_y x N_x doubles (host or device); rho: N_t x N_y x N_x floats (host or device),
  * rounded to TF32 as the solver stores it; *norm2 = sum of rho_n^2.  use_tensor_cores = 1 assembles
- * rho in integer arithmetic around digit-split BF16 tensor-core products (P_x, P_y <= 256; *norm2
- * from the stored FP32 values, relative accuracy about 2^-22), 0 with FP64 arithmetic (*norm2 of
- * the FP64 values).  Synchronous; allocates scratch.
+ * rho in integer arithmetic around digit-split BF16 tensor-core products (padded P_x, P_y <= 256 or
+ * multiples of 256 up to 1024; *norm2 from the stored FP32 values, relative accuracy about 2^-22),
+ * 0 with FP64 arithmetic (*norm2 of the FP64 values).  Synchronous; allocates scratch.
  */
 sfde_status sfde_debug_residual(sfde_ctx* ctx, const double* U, int use_tensor_cores, float* rho,
                                 double* norm2);

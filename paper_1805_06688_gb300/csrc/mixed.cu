@@ -104,7 +104,8 @@ struct SfdeMixed {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t inner_exec = nullptr;
     long long inner_key = -1, inner_launches = 0, inner_steps = 0;
-    // FP64-accurate residual in integer arithmetic around tensor-core products (P <= 256)
+    // FP64-accurate residual in integer arithmetic around tensor-core products (P <= 256 or a
+    // multiple of 256 up to 1024)
     bool use_oz = false;
     OzMatrix oAx, oAy;
     void *oz_dV = nullptr, *oz_dVt = nullptr;
@@ -220,7 +221,7 @@ sfde_status setup_mixed(sfde_ctx* c, int kind, int m, int max_levels, int min_co
     // FP64 scratch for the residual: a chunk of time points at a time
     SFDE_TRY(sfde_ensure_workspace(c, std::min<size_t>(c->nt, 128)));
     // products of the residual on the tensor cores (error-free digit splitting) when K <= 256
-    M->use_oz = Px <= 256 && Py <= 256;
+    M->use_oz = sfde_resid_int_supported(Px, Py);
     if (M->use_oz) {
         SFDE_TRY(sfde_resid_int_matrices(c, &M->oAx, &M->oAy));
         SFDE_CUDA(cudaMalloc(&M->oz_dV, sfde_resid_int_digit_bytes(Px, Py, (int)c->ws_slices)));
@@ -604,7 +605,7 @@ extern "C" sfde_status sfde_debug_lp_step(sfde_ctx* c, int fused, int scheme, co
     if (st == SFDE_OK) {
         LpEngine E{c, M, 2, 1, SFDE_RELAX_FCF, SCHEME_CN};
         int np = 0;
-        const int sch = scheme == 0 ? SCHEME_CN : (scheme == 1 ? SCHEME_BE : SCHEME_SOLVE);
+        const int sch = scheme == 0 ? (int)SCHEME_CN : (scheme == 1 ? (int)SCHEME_BE : (int)SCHEME_SOLVE);
         st = E.step(src, batch, 0, 1, batch, scheme == 2, sch, c->dt0, n0, 1, dst, 1, g ? dg : nullptr,
                     ut ? du : nullptr, ut ? c->partial : nullptr, &np);
         if (st == SFDE_OK && ut && norm2) st = sfde_reduce_partials(c, np, norm2);

@@ -86,18 +86,27 @@ struct OzArgs {
     const int* xe;               // row exponents, batch x R (FP64 output only)
     const int* me;               // column exponents, N (FP64 output only)
     void* out; long long out_stride;     // Out_b = (X_b Mat)^T, N x R per slice: double or int64
+    int zshift;                  // integer output: final right shift (units 2^{zshift-52})
     int* err;
 };
+
+// Partial sums stay exact integers below 2^24 over K <= 256: longer K is summed in groups of 256,
+// each group drained from TMEM into int64 registers before the next one starts.
+constexpr int KGROUP = 256;
 
 __device__ __forceinline__ double pow2(int e) {  // exact 2^e for normal range
     return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-// INT_OUT: write sum_{p+q<=8} 2^{-8(p+q)} sum_k d_p c_q as one int64 in units of 2^-52 (exact up to
-// the rounding of the p + q >= 7 terms to that unit; |value| <= K 2^52 <= 2^60); otherwise FP64
+// INT_OUT: write sum_{p+q<=8} 2^{-8(p+q)} sum_k d_p c_q as one int64 in units of 2^{zshift-52}
+// (exact up to the rounding of the p + q >= 7 terms to that unit; |value| <= 2^60); otherwise FP64
 // scaled by the row and column exponents (p + q <= 7).
+// Roles: warp 4 lane 0 issues TMA, warp 5 lane 0 issues the MMAs, warps 0-3 drain the
+// accumulators (TMEM lanes 32w..32w+31), also between K groups while the other two roles run on.
+constexpr int OZ_THREADS = 192;
+
 template <bool INT_OUT>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(OZ_THREADS, 1)
 k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapM, OzArgs p) {
     constexpr int S = Plan<INT_OUT>::S, NPROD = Plan<INT_OUT>::NPROD, NACC = Plan<INT_OUT>::NACC;
     constexpr int STAGE = S * (XTILE + MTILE);
@@ -108,7 +117,8 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
     uint64_t* empty = full + STAGES;
     uint64_t* accf = empty + STAGES;
     uint64_t* fin = accf + 1;
-    uint32_t* tmem_slot = (uint32_t*)(fin + 1);
+    uint64_t* tfree = fin + 1;                // a K group's accumulators have been drained
+    uint32_t* tmem_slot = (uint32_t*)(tfree + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // the N tiles of one M tile are neighbours in launch order: they share the X digit planes in L2
@@ -116,11 +126,14 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
     const int n0 = blockIdx.x * BN;
     const long long Mtot = (long long)p.batch * p.R;
     const int nchunks = (p.K + KC - 1) / KC;
+    constexpr int CPG = KGROUP / KC;          // chunks per K group
+    const int ngroups = (nchunks + CPG - 1) / CPG;
 
     if (threadIdx.x == 0) {
         for (int st = 0; st < STAGES; ++st) { tc::mbar_init(&full[st], 1); tc::mbar_init(&empty[st], 1); }
         tc::mbar_init(accf, 1);
         tc::mbar_init(fin, 1);
+        tc::mbar_init(tfree, 128);
         tc::mbar_fence_init();
         tc::prefetch_tmap(&mapX);
         tc::prefetch_tmap(&mapM);
@@ -132,7 +145,7 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
 
     const int b0 = (int)(m0 / p.R), r0 = (int)(m0 % p.R);
     bool ok = true;
-    if (warp == 0 && lane == 0) {
+    if (warp == 4 && lane == 0) {
         int issued = 0;
         for (int c = 0; c < nchunks && ok; ++c) {
             const int st = c % STAGES;
@@ -150,11 +163,15 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
         // own copies in flight must land before the CTA's shared memory goes away
         for (int c = issued - STAGES < 0 ? 0 : issued - STAGES; c < issued; ++c)
             tc::mbar_wait(&full[c % STAGES], (uint32_t)(c / STAGES) & 1u, p.err, tc::ERR_WAIT_FULL);
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp == 5 && lane == 0) {
         const uint32_t idesc = tc::idesc_f32acc(1u, BM, BN);
         bool any = false;
         for (int c = 0; c < nchunks && ok; ++c) {
-            const int st = c % STAGES;
+            const int st = c % STAGES, grp = c / CPG;
+            const bool group_start = c % CPG == 0;
+            // a new K group overwrites the accumulators once the drain warps have read them
+            if (group_start && grp > 0) ok = tc::mbar_wait(tfree, (uint32_t)(grp - 1) & 1u, p.err, tc::ERR_WAIT_ACC);
+            if (!ok) break;
             ok = tc::mbar_wait(&full[st], (uint32_t)(c / STAGES) & 1u, p.err, tc::ERR_WAIT_FULL);
             if (!ok) break;
             tc::tc_fence_after();
@@ -164,8 +181,8 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
             for (int i = 0; i < NPROD; ++i) {
                 const int dp = prod_entry<INT_OUT>(i, 0) - 1, dq = prod_entry<INT_OUT>(i, 1) - 1;
                 const int a = prod_entry<INT_OUT>(i, 2);
-                // the first product of an accumulator in the first chunk overwrites it
-                const bool first = (c == 0) && (i == 0 || prod_entry<INT_OUT>(i - 1, 2) != a);
+                // the first product of an accumulator in a group's first chunk overwrites it
+                const bool first = group_start && (i == 0 || prod_entry<INT_OUT>(i - 1, 2) != a);
 #pragma unroll
                 for (int kk = 0; kk < KC / 16; ++kk) {
                     const uint64_t ad = tc::smem_desc_sw64(sX + dp * XTILE + kk * 32);
@@ -175,43 +192,60 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
             }
             any = true;
             tc::mma_commit(&empty[st]);
+            if (c % CPG == CPG - 1 || c == nchunks - 1) tc::mma_commit(accf);   // group complete
         }
-        if (ok) tc::mma_commit(accf);
-        else if (any) {  // products still running must finish before TMEM is freed
+        if (!ok && any) {  // products still running must finish before TMEM is freed
             tc::mma_commit(fin);
             tc::mbar_wait(fin, 0, p.err, tc::ERR_WAIT_ACC);
         }
     }
 
-    const bool acc_ok = __all_sync(0xffffffffu, tc::mbar_wait(accf, 0, p.err, tc::ERR_WAIT_ACC));
-    tc::tc_fence_after();
-    if (acc_ok && INT_OUT) {
+    if (warp >= 4) {
+        // producer and MMA warps: nothing to drain
+    } else if constexpr (INT_OUT) {
         const long long m = m0 + warp * 32 + lane;
         // z: digit sums d <= 6 in units of 2^-52 (exact); zl: d = 7, 8 in units of 2^-64 (exact)
         long long z[BN], zl[BN];
 #pragma unroll
         for (int j = 0; j < BN; ++j) { z[j] = 0; zl[j] = 0; }
+        bool acc_ok = true;
+        for (int grp = 0; grp < ngroups; ++grp) {
+            acc_ok = __all_sync(0xffffffffu, tc::mbar_wait(accf, (uint32_t)grp & 1u, p.err, tc::ERR_WAIT_ACC));
+            tc::tc_fence_after();
+            if (!acc_ok) break;
 #pragma unroll 1
-        for (int a = 0; a < NACC; ++a) {
-            uint32_t v[32];
-            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * BN), v);
-            const int d = acc_digit_sum<INT_OUT>(a);
-            const int sh = d <= 6 ? 52 - 8 * d : 8 * (8 - d);
+            for (int a = 0; a < NACC; ++a) {
+                uint32_t v[32];
+                tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * BN), v);
+                const int d = acc_digit_sum<INT_OUT>(a);
+                const int sh = d <= 6 ? 52 - 8 * d : 8 * (8 - d);
 #pragma unroll
-            for (int j = 0; j < BN; ++j) {
-                const long long s = (long long)__float2int_rn(__uint_as_float(v[j]));  // exact, |s| <= 2^24
-                if (d <= 6) z[j] += s << sh;
-                else zl[j] += s << sh;
+                for (int j = 0; j < BN; ++j) {
+                    const long long s = (long long)__float2int_rn(__uint_as_float(v[j]));  // exact, |s| <= 2^24
+                    if (d <= 6) z[j] += s << sh;
+                    else zl[j] += s << sh;
+                }
+            }
+            if (grp + 1 < ngroups) {
+                tc::tc_fence_before();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(tfree)) : "memory");
             }
         }
-        if (m < Mtot) {
+        if (acc_ok && m < Mtot) {
             const long long b = m / p.R;
             const int r = (int)(m % p.R);
             long long* out = (long long*)p.out + b * p.out_stride + r;
+            const int zs = p.zshift;
 #pragma unroll
-            for (int j = 0; j < BN; ++j) out[(long long)(n0 + j) * p.R] = z[j] + ((zl[j] + 2048) >> 12);
+            for (int j = 0; j < BN; ++j) {
+                long long y = z[j] + ((zl[j] + 2048) >> 12);
+                if (zs > 0) y = (y + (1ll << (zs - 1))) >> zs;
+                out[(long long)(n0 + j) * p.R] = y;
+            }
         }
-    } else if (acc_ok) {
+    } else if (__all_sync(0xffffffffu, tc::mbar_wait(accf, 0, p.err, tc::ERR_WAIT_ACC))) {
+        // FP64 output (K <= 256: one group)
+        tc::tc_fence_after();
         const long long m = m0 + warp * 32 + lane;
         const bool valid = m < Mtot;
         // z_hi in units of 2^-40 (digit sums d = 2..5), z_lo in units of 2^-56 (d = 6, 7)
@@ -415,7 +449,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode() {
 
 sfde_status sfde_oz_split_matrix(const double* Mat, int K, int N, OzMatrix* out, cudaStream_t s, double alpha,
                                  bool uniform) {
-    if (K > 256 || K % 32 || N % BN) return SFDE_EUNSUPPORTED;
+    if (K > (uniform ? 1024 : 256) || K % 32 || N % BN) return SFDE_EUNSUPPORTED;
     // uniform scale: the integer-output product (7 digits); per-column scales: FP64 output (6)
     const int S = uniform ? Plan<true>::S : Plan<false>::S;
     out->K = K; out->N = N; out->nd = S;
@@ -477,7 +511,7 @@ sfde_status launch_oz(sfde_ctx* c, const CUtensorMap& mapX, const OzMatrix& M, c
     if (mt > 65535) return SFDE_EINVAL;
     dim3 grid(M.N / BN, (unsigned)mt);
     const int slot = sfde_prof_begin(c);
-    k_ozaki_slice_gemm<INT_OUT><<<grid, 128, smem_bytes<INT_OUT>(), s>>>(mapX, M.map, a);
+    k_ozaki_slice_gemm<INT_OUT><<<grid, OZ_THREADS, smem_bytes<INT_OUT>(), s>>>(mapX, M.map, a);
     // tensor work: NPROD digit products of 2 R K N flops each; bytes: the digit planes of X, the
     // matrix digits and the output (8 bytes per element) once
     constexpr int S = Plan<INT_OUT>::S, NPROD = Plan<INT_OUT>::NPROD;
@@ -507,17 +541,26 @@ sfde_status sfde_oz_gemm(sfde_ctx* c, const double* X, const double* X2, long lo
     return launch_oz<false>(c, mapX, M, a, c->stream, nr, nc, nout);
 }
 
+// |sum_k x_k m_k| <= K for |x|, |m| <= 1 (units 2^-52): beyond K = 256 the product is scaled down
+// by K/256 so that it keeps 3 bits of int64 headroom for the (1,4,1) stencils
+int sfde_oz_int_shift(int K) {
+    int s = 0;
+    while ((KGROUP << s) < K) ++s;
+    return s;
+}
+
 sfde_status sfde_oz_gemm_int(sfde_ctx* c, void* xdigits, long long plane, int R, int K, int batch,
                              const OzMatrix& M, long long* out, long long out_stride, int* err, int nr, int nc,
                              int nout) {
-    if (K != M.K || K > 256 || R % 32 || (R > 128 && R % 128) || plane < (long long)batch * R * K ||
-        M.nd != Plan<true>::S)
+    if (K != M.K || K > 1024 || (K > KGROUP && K % KGROUP) || R % 32 || (R > 128 && R % 128) ||
+        plane < (long long)batch * R * K || M.nd != Plan<true>::S)
         return SFDE_EUNSUPPORTED;
     CUtensorMap mapX;
     SFDE_TRY(map_digit_planes(&mapX, xdigits, R, K, batch, plane, Plan<true>::S));
     OzArgs a{};
     a.R = R; a.K = K; a.N = M.N; a.batch = batch;
     a.out = out; a.out_stride = out_stride; a.err = err;
+    a.zshift = sfde_oz_int_shift(K);
     return launch_oz<true>(c, mapX, M, a, c->stream, nr, nc, nout);
 }
 

@@ -144,15 +144,15 @@ __device__ __forceinline__ long long rshr(long long x, int k) {
     return (x + (1ll << (k - 1))) >> k;
 }
 
-// rho for one 32 x 32 tile of pair b.  Z1 = T1[b][i][j] counts 2^{E+ex-51} and Z2 = T3[b][j][i]
-// counts 2^{E+ey-51} (2V / 2^56 times the matrix over 2^e, in units of 2^-52), fixed-point values
-// count 2^{E-54}.  |Z| <= K 2^52 = 2^60, so (1,4,1) Z stays below 2^63, and both terms are halved
+// rho for one 32 x 32 tile of pair b.  Z1 = T1[b][i][j] counts 2^{E+ex-51+zsx} and Z2 = T3[b][j][i]
+// counts 2^{E+ey-51+zsy} (2V / 2^56 times the matrix over 2^e, in units of 2^{zs-52} with zs the
+// product's shift for its contraction length), fixed-point values count 2^{E-54}.  |Z| <= K 2^52 = 2^60, so (1,4,1) Z stays below 2^63, and both terms are halved
 // at least once before they are added.  Writes rho (BF16 or TF32-rounded FP32), zero
 // outside the interior nodes, and one FP64 sum of rho^2 per block.
 template <typename OT>
 __global__ void __launch_bounds__(256, 4) k_combine_int(
     const long long* __restrict__ T1, const long long* __restrict__ T3, const double* __restrict__ U,
-    const int* __restrict__ En, int n0, int Px, int Py, int nx, int ny, double cmass, int ex, int ey,
+    const int* __restrict__ En, int n0, int Px, int Py, int nx, int ny, double cmass, int ex, int ey, int zsx, int zsy,
     const double* __restrict__ dt, int rank, const double* __restrict__ time_w, const double* __restrict__ bxn,
     const double* __restrict__ byn, OT* __restrict__ rout, long long rout_stride, double* __restrict__ partial) {
     __shared__ long long t1[32][35];      // Z1 rows i0.., columns j0-1 .. j0+32
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
             }
             du[r][c] = v;
         }
-    const int u1 = E + ex - 51, u2 = E + ey - 51, u = max(u1, u2) + 1;
+    const int u1 = E + ex - 51 + zsx, u2 = E + ey - 51 + zsy, u = max(u1, u2) + 1;
     if (tx == 0 && ty == 0) {
         cst[0] = ldexp(cmass, E - 54);
         cst[1] = ldexp(-0.5 * dt[n - 1], u);
@@ -238,6 +238,12 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
 
 }  // namespace
 
+// contraction lengths up to 256, or multiples of 256 up to 1024 (the digit product's K groups)
+bool sfde_resid_int_supported(int Px, int Py) {
+    auto ok = [](int P) { return P <= 256 || (P <= 1024 && P % 256 == 0); };
+    return ok(Px) && ok(Py);
+}
+
 size_t sfde_resid_int_digit_bytes(int Px, int Py, int batch) { return (size_t)ND * Px * Py * batch * 2; }
 
 sfde_status sfde_resid_int_matrices(sfde_ctx* c, OzMatrix* Ax, OzMatrix* Ay) {
@@ -254,7 +260,7 @@ sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int cou
     const int Px = c->x.P, Py = c->y.P;
     const size_t P2 = c->P2();
     const size_t esz = out_kind == 0 ? 2 : 4;
-    if (Px > 256 || Py > 256 || n_first < 1 || count < 1) return SFDE_EINVAL;
+    if (!sfde_resid_int_supported(Px, Py) || n_first < 1 || count < 1) return SFDE_EINVAL;
     // accounting (class 5): bytes each kernel must move once, unpadded
     const double nxy = (double)c->x.n * c->y.n;
     int slot = sfde_prof_begin(c);
@@ -283,12 +289,14 @@ sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int cou
         if (out_kind == 0)
             k_combine_int<__nv_bfloat16><<<grid, block, 0, c->stream>>>(
                 (const long long*)c->T1, (const long long*)c->T3, U, En, n0, Px, Py, c->x.n, c->y.n, cmass,
-                Ax.e_uniform, Ay.e_uniform, c->dt0, c->rank, c->time_w, c->bxn, c->byn, (__nv_bfloat16*)ro,
+                Ax.e_uniform, Ay.e_uniform, sfde_oz_int_shift(Px), sfde_oz_int_shift(Py), c->dt0, c->rank,
+                c->time_w, c->bxn, c->byn, (__nv_bfloat16*)ro,
                 rout_stride, partial + total);
         else
             k_combine_int<float><<<grid, block, 0, c->stream>>>(
                 (const long long*)c->T1, (const long long*)c->T3, U, En, n0, Px, Py, c->x.n, c->y.n, cmass,
-                Ax.e_uniform, Ay.e_uniform, c->dt0, c->rank, c->time_w, c->bxn, c->byn, (float*)ro, rout_stride,
+                Ax.e_uniform, Ay.e_uniform, sfde_oz_int_shift(Px), sfde_oz_int_shift(Py), c->dt0, c->rank,
+                c->time_w, c->bxn, c->byn, (float*)ro, rout_stride,
                 partial + total);
         sfde_prof_end(c, slot, 5, 0.0, (16.0 + 16.0 + (double)esz) * nxy * nb);   // Z1, Z2, U pair in, rho out
         sfde_count_launch(c);
@@ -303,7 +311,7 @@ extern "C" sfde_status sfde_debug_residual(sfde_ctx* c, const double* U, int use
                                           double* norm2) {
     if (!c || !U || !rho || !norm2) return SFDE_EINVAL;
     const int Px = c->x.P, Py = c->y.P;
-    if (use_tensor_cores && (Px > 256 || Py > 256)) return SFDE_EUNSUPPORTED;
+    if (use_tensor_cores && !sfde_resid_int_supported(Px, Py)) return SFDE_EUNSUPPORTED;
     const size_t P2 = c->P2(), n2 = (size_t)c->x.n * c->y.n;
     double* u = nullptr;
     SFDE_TRY(sfde_level0(c, &u));

@@ -209,14 +209,16 @@ sfde_status sfde_oz_gemm(sfde_ctx* c, const double* X, const double* X2, long lo
 // The same product on pre-split operand digits (seven planes `plane` elements apart) with the 28 digit
 // products p + q <= 8, written as int64 in units of 2^-52 of the operand scales (uniform-exponent
 // matrix); exact up to rounding the p + q >= 7 terms to that unit.
+int sfde_oz_int_shift(int K);  // the integer product's extra right shift for contraction length K
 sfde_status sfde_oz_gemm_int(sfde_ctx* c, void* xdigits, long long plane, int R, int K, int batch,
                              const OzMatrix& M, long long* out, long long out_stride, int* err, int nr, int nc,
                              int nout);
 
 // ---- the space-time residual of sfde_residual_fp64 in integer arithmetic around two digit-split
-// tensor-core products (resid_int.cu), Px, Py <= 256.  Ax, Ay from sfde_resid_int_matrices; dV, dVt:
+// tensor-core products (resid_int.cu), Px, Py <= 1024.  Ax, Ay from sfde_resid_int_matrices; dV, dVt:
 // sfde_resid_int_digit_bytes(Px, Py, ws_slices) each (digits of 2V row-major and transposed); En:
 // N_t + 1 ints; err: device error word.
+bool sfde_resid_int_supported(int Px, int Py);
 size_t sfde_resid_int_digit_bytes(int Px, int Py, int batch);
 sfde_status sfde_resid_int_matrices(sfde_ctx* c, OzMatrix* Ax, OzMatrix* Ay);
 sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int count, void* rout,

@@ -71,3 +71,23 @@ def test_mixed_sine_N255_Nt1024_full_size(name, prec):
     scale = np.abs(psi).max()
     for n in keep:
         assert np.abs(U[n].cpu().numpy() - exact[n]).max() < 1e-8 * scale, n
+
+
+def test_mixed_bump_N511_Nt2048_full_size():
+    """The N = 511 workload (padded P = 512: four-GEMM tensor-core steps and the K-grouped integer
+    residual), mixed BF16 to 1e-8, against the exact sequential solution at sampled time points."""
+    w = WORKLOADS["bump_N511_Nt2048"]
+    t = w.t()
+    psi, F = w.initial(), w.forcing()
+    P = sfde.Problem(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t, precision=sfde.PREC_MIXED_BF16)
+    P.set_initial(psi)
+    P.set_forcing(F)
+    U = torch.zeros((w.nt + 1, w.ny, w.nx), dtype=torch.float64, device="cuda")
+    _, st = P.mgrit(U=U, m=w.m, max_levels=32, coarse=sfde.COARSE_AUTO, rel_tol=w.rel_tol, max_iter=100)
+    assert st.converged
+    O = osfde.SFDE(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t)
+    keep = [1, 9, 512, 1500, 2048]
+    exact = osfde.spectral_sequential(O, psi, F, keep=keep)
+    scale = max(np.abs(exact[n]).max() for n in keep)
+    for n in keep:
+        assert np.abs(U[n].cpu().numpy() - exact[n]).max() < 1e-8 * scale, n

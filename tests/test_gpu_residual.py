@@ -1,7 +1,7 @@
 """The FP64 space-time residual of the mixed-precision solver against the oracle's definition
 rho_n = F_n + B_n U_{n-1} - S_n U_n (Eq. (2.4)), for both ways of forming it: FP64 arithmetic,
 and exact integer arithmetic around digit-split BF16 tensor-core products (fixed point on a grid
-of 2^-54 of each pair of time slices' maximum).
+of 2^-54 of each pair of time slices' maximum; contractions longer than 256 in groups of 256).
 
 The residual is formed to FP64-product accuracy: where U nearly solves the system its norm is a
 small difference of terms of size ||S U||, and must still agree with the oracle to 1e-11 ||S U||.
@@ -51,7 +51,8 @@ def oracle_residual(O, U, F):
 
 
 @pytest.mark.parametrize("use_tc", [0, 1])
-@pytest.mark.parametrize("nx,ny,nt,near", [(50, 70, 16, False), (255, 200, 6, False), (31, 31, 12, True)])
+@pytest.mark.parametrize("nx,ny,nt,near", [(50, 70, 16, False), (255, 200, 6, False), (31, 31, 12, True),
+                                           (450, 500, 3, True), (1000, 700, 2, False)])
 def test_residual_matches_oracle(use_tc, nx, ny, nt, near):
     t = time_grid(nt, 1.0, "graded")
     F, _ = gaussian_bump_forcing(8, nx, ny, t)
