@@ -391,6 +391,53 @@ def run_ours(args, w):
     return 0
 
 
+def run_batch(args):
+    """The batched form: the 64 uneven instances of batch_workloads(0) (N in {63..511}, N_t in
+    {256..4096}, random beta, gamma, K), mixed BF16 to 1e-8, solved by sfde_batch_solve.  value =
+    sum of N_x N_y N_t over the instances / seconds per batch solve (host clock with the device
+    synchronised on both sides: the instances run on 64 streams)."""
+    import torch
+    from sfde_workloads.generate import batch_workloads
+    import paper_1805_06688_gb300 as sfde
+    if not os.path.exists(sfde.library_path):
+        from paper_1805_06688_gb300.build import build
+        build()
+    ws = batch_workloads(0, 64)
+    t0 = time.perf_counter()
+    probs = []
+    for w in ws:
+        P = sfde.Problem(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, w.t(), w.omega, precision=sfde.PREC_MIXED_BF16)
+        P.set_initial(w.initial())
+        probs.append(P)
+    setup_s = time.perf_counter() - t0
+    kw = dict(m=8, max_levels=32, coarse=sfde.COARSE_AUTO, rel_tol=1e-8, max_iter=400)
+    dofs = sum(w.space_time_updates for w in ws)
+    for _ in range(args.warmup):
+        sfde.batch_solve(probs, **kw)
+    secs = []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, status, stats = sfde.batch_solve(probs, **kw)
+            torch.cuda.synchronize()
+            secs.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.median(secs)
+    line = {
+        "metric": METRIC, "value": dofs / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16+f64", "data": "synthetic",
+        "config": {"workload": "batch64 (batch_workloads seed 0)", "instances": len(ws), "space_time_updates": dofs,
+                   "m": 8, "rel_tol": 1e-8, "precision": "mixed-bf16", "setup_s": setup_s,
+                   "converged": sum(1 for s in stats if s.converged),
+                   "iters_max": max(s.iters for s in stats), "timer": "host, device synchronised",
+                   "l2": "space-time iterates far larger than L2"},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -402,6 +449,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-comparator", action="store_true")
     args = ap.parse_args()
+    if args.workload == "batch64":
+        return run_batch(args)
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)

@@ -145,6 +145,25 @@ typedef struct {
 sfde_status mgrit_solve(sfde_ctx* ctx, const mgrit_opts* opts, double* U, double* U_T,
                         mgrit_stats* stats);
 
+/*
+ * sfde_batch_solve -- the batched form: n independent instances (distinct contexts from
+ * sfde_setup, any sizes and precisions) solved by Algorithm 1 concurrently on the current GPU.
+ * Each instance runs exactly the arithmetic of mgrit_solve on its own stream (a context created
+ * with the legacy default stream gets a private non-blocking stream for the call), driven by up to
+ * 16 host threads, so results equal those of separate mgrit_solve calls.  No counterpart in the
+ * paper (its parallelism is across time on a CPU cluster); it fills the GPU where one instance's
+ * coarse levels cannot.
+ *   opts   : shared by all instances (NULL: the mgrit_solve defaults).
+ *   U_T    : NULL, or n pointers (entries may be NULL) to N_y x N_x doubles receiving u(t_N),
+ *            host or device.
+ *   stats  : NULL or n entries;  status : NULL or n entries receiving each instance's status.
+ * Returns SFDE_EINVAL for n < 1 or NULL / repeated contexts (nothing runs), else the first
+ * non-OK instance status (SFDE_OK if all converged).  Synchronous: all instances have finished,
+ * outputs written, on return.  Contexts must not be used by other threads during the call.
+ */
+sfde_status sfde_batch_solve(int n, sfde_ctx* const* ctxs, const mgrit_opts* opts, double* const* U_T,
+                             mgrit_stats* stats, sfde_status* status);
+
 /* Sequential time stepping U_n = S_n^{-1}(B_n U_{n-1} + F_n), n = 1..N_t (Eq. (2.4)), one step
  * after another.  U and U_T as in mgrit_solve; seconds (may be NULL) = device time. */
 sfde_status seq_timestep(sfde_ctx* ctx, double* U, double* U_T, double* seconds);

@@ -21,7 +21,7 @@ HISTORY_MAX = 512
 exported_symbols = (
     "sfde_setup", "sfde_set_initial", "sfde_set_forcing", "mgrit_solve", "seq_timestep",
     "sfde_step_batch", "sfde_step_batch_noalloc", "sfde_get_operator", "sfde_profile_enable", "sfde_profile_read",
-    "sfde_destroy", "sfde_strerror",
+    "sfde_destroy", "sfde_strerror", "sfde_batch_solve",
 )
 
 
@@ -85,6 +85,8 @@ def lib() -> C.CDLL:
         L.sfde_get_operator.argtypes = [vp, ip, vp, vp, vp]
         L.sfde_profile_enable.argtypes = [vp, ip]
         L.sfde_profile_read.argtypes = [vp, C.POINTER(SfdeProfile)]
+        L.sfde_batch_solve.argtypes = [ip, C.POINTER(vp), C.POINTER(MgritOpts), C.POINTER(vp),
+                                       C.POINTER(MgritStats), C.POINTER(ip)]
         L.sfde_destroy.argtypes = [vp]
         L.sfde_destroy.restype = None
         L.sfde_strerror.argtypes = [ip]
@@ -159,6 +161,21 @@ def seq_timestep(ctx, U=None, U_T=None):
     return sec.value
 
 
+def sfde_batch_solve(ctxs, opts: MgritOpts | None, U_T=None, check=True):
+    """Solve independent instances concurrently; returns (status, per-instance statuses, stats)."""
+    n = len(ctxs)
+    carr = (C.c_void_p * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    uarr = None
+    if U_T is not None:
+        uarr = (C.c_void_p * n)(*[_ptr(u) for u in U_T])
+    stats = (MgritStats * n)()
+    status = (C.c_int * n)()
+    st = lib().sfde_batch_solve(n, carr, C.byref(opts) if opts is not None else None, uarr, stats, status)
+    if check:
+        _check(st, "sfde_batch_solve", allow=(SFDE_OK, SFDE_ENOCONV))
+    return st, list(status), list(stats)
+
+
 def sfde_step_batch(ctx, n0, dn, batch, src, dst):
     return _check(lib().sfde_step_batch(ctx, int(n0), int(dn), int(batch), _ptr(src), _ptr(dst)),
                   "sfde_step_batch")
@@ -192,6 +209,11 @@ def sfde_profile_read(ctx) -> SfdeProfile:
 def sfde_destroy(ctx):
     if ctx:
         lib().sfde_destroy(ctx)
+
+
+def batch_solve(problems, U_T=None, check=True, **kw):
+    """sfde_batch_solve over a list of Problem objects (shared options as for Problem.mgrit)."""
+    return sfde_batch_solve([p.ctx for p in problems], make_opts(**kw), U_T, check=check)
 
 
 def make_opts(m=2, max_levels=64, min_coarse=2, relax=RELAX_FCF, coarse=COARSE_AUTO, max_iter=100,

@@ -243,12 +243,15 @@ static sfde_status write_outputs(sfde_ctx* c, double* U, double* U_T) {
         if (sfde_is_device_ptr(U_T)) {
             sfde_launch_unpad(last, U_T, c->y.n, c->x.n, c->y.P, c->x.P, 1, c->stream);
         } else {
-            double* tmp = nullptr;
-            SFDE_CUDA(cudaMalloc(&tmp, sizeof(double) * n2));
+            // staged in the step workspace when there is one: cudaFree would synchronise the whole
+            // device, stalling instances that run concurrently (sfde_batch_solve)
+            const bool ws = c->T1 && c->ws_slices >= 1;
+            double* tmp = ws ? c->T1 : nullptr;
+            if (!ws) SFDE_CUDA(cudaMalloc(&tmp, sizeof(double) * n2));
             sfde_launch_unpad(last, tmp, c->y.n, c->x.n, c->y.P, c->x.P, 1, c->stream);
             cudaError_t e = cudaMemcpyAsync(U_T, tmp, sizeof(double) * n2, cudaMemcpyDeviceToHost, c->stream);
             cudaError_t e2 = cudaStreamSynchronize(c->stream);
-            cudaFree(tmp);
+            if (!ws) cudaFree(tmp);
             SFDE_CUDA(e);
             SFDE_CUDA(e2);
         }

@@ -1,0 +1,62 @@
+// The batched form: independent problem instances solved concurrently on one GPU.
+//
+// A single MGRIT solve is latency-bound on its coarse levels (few slices per launch, long chains of
+// dependent steps), so one instance leaves most of the GPU idle there.  Independent instances have
+// no data dependence at all: each one runs its own solve (inner V-cycles replayed as its own CUDA
+// graph) on its own stream, driven by a pool of host threads, and the hardware interleaves their
+// launches.  A context created on the legacy default stream gets a private non-blocking stream for
+// the duration of the call.
+#include <algorithm>
+#include <atomic>
+#include <thread>
+#include <unordered_set>
+#include <vector>
+
+#include "sfde_internal.cuh"
+
+extern "C" sfde_status sfde_batch_solve(int n, sfde_ctx* const* ctxs, const mgrit_opts* opts, double* const* U_T,
+                                       mgrit_stats* stats, sfde_status* status) {
+    if (n < 1 || !ctxs) return SFDE_EINVAL;
+    std::unordered_set<const sfde_ctx*> seen;
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i] || !seen.insert(ctxs[i]).second) return SFDE_EINVAL;   // distinct contexts only
+    int dev = 0;
+    SFDE_CUDA(cudaGetDevice(&dev));
+    std::vector<cudaStream_t> own(n, nullptr);
+    sfde_status first = SFDE_OK;
+    for (int i = 0; i < n && first == SFDE_OK; ++i)
+        if (!ctxs[i]->stream) {
+            if (cudaStreamCreateWithFlags(&own[i], cudaStreamNonBlocking) != cudaSuccess) first = SFDE_ECUDA;
+            else ctxs[i]->stream = own[i];
+        }
+    std::vector<sfde_status> st(n, SFDE_OK);
+    if (first == SFDE_OK) {
+        std::atomic<int> next{0};
+        auto work = [&]() {
+            cudaSetDevice(dev);   // a new host thread starts on device 0
+            for (int i; (i = next.fetch_add(1)) < n;) {
+                st[i] = mgrit_solve(ctxs[i], opts, nullptr, U_T ? U_T[i] : nullptr, stats ? &stats[i] : nullptr);
+                if (st[i] == SFDE_OK || st[i] == SFDE_ENOCONV) {
+                    const cudaError_t e = cudaStreamSynchronize(ctxs[i]->stream);
+                    if (e != cudaSuccess) { sfde_set_last_cuda_error(e, "batch solve", __FILE__, __LINE__); st[i] = SFDE_ECUDA; }
+                }
+            }
+        };
+        const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+        const int nth = std::max(1, std::min({n, 16, hw}));
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nth; ++t) pool.emplace_back(work);
+        work();
+        for (auto& t : pool) t.join();
+        for (int i = 0; i < n; ++i)
+            if (st[i] != SFDE_OK && first == SFDE_OK) first = st[i];
+    }
+    for (int i = 0; i < n; ++i)
+        if (own[i]) {
+            cudaStreamSynchronize(own[i]);
+            ctxs[i]->stream = nullptr;
+            cudaStreamDestroy(own[i]);
+        }
+    if (status) std::copy(st.begin(), st.end(), status);
+    return first;
+}

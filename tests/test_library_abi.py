@@ -60,3 +60,13 @@ def test_argument_validation_needs_no_gpu():
         assert st == sfde.SFDE_EINVAL
     assert L.mgrit_solve(None, None, None, None, None) == sfde.SFDE_EINVAL
     assert sfde.sfde_strerror(sfde.SFDE_ENOCONV) == "no convergence"
+
+
+def test_batch_solve_argument_validation_needs_no_gpu():
+    """sfde_batch_solve rejects an empty batch and NULL contexts before any CUDA call."""
+    import ctypes as C
+    sfde = _library()
+    L = sfde.lib()
+    assert L.sfde_batch_solve(0, None, None, None, None, None) == sfde.SFDE_EINVAL
+    arr = (C.c_void_p * 2)(None, None)
+    assert L.sfde_batch_solve(2, arr, None, None, None, None) == sfde.SFDE_EINVAL
