@@ -278,7 +278,7 @@ def run_ours(args, w):
 
     stream = torch.cuda.current_stream(dev)
     prec = {"fp64": sfde.PREC_FP64, "mixed-bf16": sfde.PREC_MIXED_BF16,
-            "mixed-tf32": sfde.PREC_MIXED_TF32}[args.precision]
+            "mixed-tf32": sfde.PREC_MIXED_TF32, "mixed-auto": sfde.PREC_MIXED_AUTO}[args.precision]
     t = w.t()
     psi = w.initial()
     P = sfde.Problem(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t, w.omega, precision=prec,
@@ -364,7 +364,8 @@ def run_ours(args, w):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if prec == sfde.PREC_FP64 else {"mixed-bf16": "bf16+f64", "mixed-tf32": "tf32+f64"}[args.precision],
+        "dtype": "f64" if prec == sfde.PREC_FP64 else {"mixed-bf16": "bf16+f64", "mixed-tf32": "tf32+f64",
+                                                        "mixed-auto": "bf16/tf32+f64"}[args.precision],
         "data": "synthetic",
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nt": w.nt, "beta": w.beta,
                    "gamma": w.gamma, "kx": w.kx, "ky": w.ky, "m": w.m, "rel_tol": tol,
@@ -393,7 +394,8 @@ def run_ours(args, w):
 
 def run_batch(args):
     """The batched form: the 64 uneven instances of batch_workloads(0) (N in {63..511}, N_t in
-    {256..4096}, random beta, gamma, K), mixed BF16 to 1e-8, solved by sfde_batch_solve.  value =
+    {256..4096}, random beta, gamma, K), mixed precision to 1e-8 with the operand type chosen per
+    instance (--precision, default mixed-auto), solved by sfde_batch_solve.  value =
     sum of N_x N_y N_t over the instances / seconds per batch solve (host clock with the device
     synchronised on both sides: the instances run on 64 streams)."""
     import torch
@@ -403,10 +405,13 @@ def run_batch(args):
         from paper_1805_06688_gb300.build import build
         build()
     ws = batch_workloads(0, 64)
+    pname = "mixed-auto" if args.precision == "mixed-bf16" else args.precision
+    prec = {"mixed-bf16": sfde.PREC_MIXED_BF16, "mixed-tf32": sfde.PREC_MIXED_TF32,
+            "mixed-auto": sfde.PREC_MIXED_AUTO}[pname]
     t0 = time.perf_counter()
     probs = []
     for w in ws:
-        P = sfde.Problem(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, w.t(), w.omega, precision=sfde.PREC_MIXED_BF16)
+        P = sfde.Problem(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, w.t(), w.omega, precision=prec)
         P.set_initial(w.initial())
         probs.append(P)
     setup_s = time.perf_counter() - t0
@@ -426,9 +431,9 @@ def run_batch(args):
     line = {
         "metric": METRIC, "value": dofs / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16+f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16/tf32+f64", "data": "synthetic",
         "config": {"workload": "batch64 (batch_workloads seed 0)", "instances": len(ws), "space_time_updates": dofs,
-                   "m": 8, "rel_tol": 1e-8, "precision": "mixed-bf16", "setup_s": setup_s,
+                   "m": 8, "rel_tol": 1e-8, "precision": pname, "setup_s": setup_s,
                    "converged": sum(1 for s in stats if s.converged),
                    "iters_max": max(s.iters for s in stats), "timer": "host, device synchronised",
                    "l2": "space-time iterates far larger than L2"},
@@ -444,7 +449,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed-bf16", "mixed-tf32"], default="mixed-bf16")
+    ap.add_argument("--precision", choices=["fp64", "mixed-bf16", "mixed-tf32", "mixed-auto"], default="mixed-bf16")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-comparator", action="store_true")

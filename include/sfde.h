@@ -52,7 +52,11 @@ typedef enum {
     SFDE_PREC_FP64 = 0,        /* every step in FP64                                              */
     SFDE_PREC_MIXED_BF16 = 1,  /* inner V-cycles on BF16 tensor cores (FP32 accumulate), FP64
                                   space-time residual and iterative refinement                    */
-    SFDE_PREC_MIXED_TF32 = 2   /* as above with TF32 operands                                     */
+    SFDE_PREC_MIXED_TF32 = 2,  /* as above with TF32 operands                                     */
+    SFDE_PREC_MIXED_AUTO = 3   /* BF16 where the fused BF16 step applies (padded P_x = P_y in
+                                  {128, 256}) and N_t <= 1024, else TF32: the low-precision fixed
+                                  point drifts with the rounding accumulated over N_t nearly undamped
+                                  steps, and TF32 rounds 4x finer (no counterpart in the paper) */
 } sfde_precision;
 
 typedef struct {
@@ -149,8 +153,9 @@ sfde_status mgrit_solve(sfde_ctx* ctx, const mgrit_opts* opts, double* U, double
  * sfde_batch_solve -- the batched form: n independent instances (distinct contexts from
  * sfde_setup, any sizes and precisions) solved by Algorithm 1 concurrently on the current GPU.
  * Each instance runs exactly the arithmetic of mgrit_solve on its own stream (a context created
- * with the legacy default stream gets a private non-blocking stream for the call), driven by up to
- * 16 host threads, so results equal those of separate mgrit_solve calls.  No counterpart in the
+ * with the legacy default stream gets a private non-blocking stream for the call, the quarter with
+ * the most work at the highest stream priority), driven by up to 16 host threads that start the
+ * instances in order of decreasing work, so results equal those of separate mgrit_solve calls.  No counterpart in the
  * paper (its parallelism is across time on a CPU cluster); it fills the GPU where one instance's
  * coarse levels cannot.
  *   opts   : shared by all instances (NULL: the mgrit_solve defaults).

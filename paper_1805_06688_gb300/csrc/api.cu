@@ -134,7 +134,7 @@ sfde_status sfde_setup(double beta, double gamma, double kx, double ky, const do
     for (int n = 1; n <= nt; ++n)
         if (!(t[n] > t[n - 1]) || !isfinite(t[n])) return SFDE_EINVAL;
     int prec = opts ? opts->precision : SFDE_PREC_FP64;
-    if (prec < SFDE_PREC_FP64 || prec > SFDE_PREC_MIXED_TF32) return SFDE_EINVAL;
+    if (prec < SFDE_PREC_FP64 || prec > SFDE_PREC_MIXED_AUTO) return SFDE_EINVAL;
 
     sfde_ctx* c = new (std::nothrow) sfde_ctx();
     if (!c) return SFDE_ENOMEM;

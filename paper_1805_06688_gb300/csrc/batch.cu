@@ -6,6 +6,11 @@
 // graph) on its own stream, driven by a pool of host threads, and the hardware interleaves their
 // launches.  A context created on the legacy default stream gets a private non-blocking stream for
 // the duration of the call.
+//
+// The batch ends with its slowest instance, so instances start in order of decreasing work per
+// step sweep, N_t P_x P_y (P_x + P_y), and the quarter with the most work gets the highest stream
+// priority: the long solves run at full speed from the start and the short ones fill in around
+// them (longest-processing-time-first scheduling).
 #include <algorithm>
 #include <atomic>
 #include <thread>
@@ -22,19 +27,33 @@ extern "C" sfde_status sfde_batch_solve(int n, sfde_ctx* const* ctxs, const mgri
         if (!ctxs[i] || !seen.insert(ctxs[i]).second) return SFDE_EINVAL;   // distinct contexts only
     int dev = 0;
     SFDE_CUDA(cudaGetDevice(&dev));
+    std::vector<int> order(n);
+    std::vector<double> cost(n);
+    for (int i = 0; i < n; ++i) {
+        order[i] = i;
+        const sfde_ctx* c = ctxs[i];
+        cost[i] = (double)c->nt * c->x.P * c->y.P * (double)(c->x.P + c->y.P);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    int prio_low = 0, prio_high = 0;
+    SFDE_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
     std::vector<cudaStream_t> own(n, nullptr);
     sfde_status first = SFDE_OK;
-    for (int i = 0; i < n && first == SFDE_OK; ++i)
+    for (int r = 0; r < n && first == SFDE_OK; ++r) {
+        const int i = order[r];
         if (!ctxs[i]->stream) {
-            if (cudaStreamCreateWithFlags(&own[i], cudaStreamNonBlocking) != cudaSuccess) first = SFDE_ECUDA;
+            const int prio = r < (n + 3) / 4 ? prio_high : prio_low;
+            if (cudaStreamCreateWithPriority(&own[i], cudaStreamNonBlocking, prio) != cudaSuccess) first = SFDE_ECUDA;
             else ctxs[i]->stream = own[i];
         }
+    }
     std::vector<sfde_status> st(n, SFDE_OK);
     if (first == SFDE_OK) {
         std::atomic<int> next{0};
         auto work = [&]() {
             cudaSetDevice(dev);   // a new host thread starts on device 0
-            for (int i; (i = next.fetch_add(1)) < n;) {
+            for (int r; (r = next.fetch_add(1)) < n;) {
+                const int i = order[r];
                 st[i] = mgrit_solve(ctxs[i], opts, nullptr, U_T ? U_T[i] : nullptr, stats ? &stats[i] : nullptr);
                 if (st[i] == SFDE_OK || st[i] == SFDE_ENOCONV) {
                     const cudaError_t e = cudaStreamSynchronize(ctxs[i]->stream);

@@ -102,8 +102,9 @@ struct SfdeMixed {
     std::vector<MapEntry> maps;
     // captured inner solve (CUDA graph) and what it contains
     cudaStream_t cap = nullptr;
-    cudaGraphExec_t inner_exec = nullptr;
-    long long inner_key = -1, inner_launches = 0, inner_steps = 0;
+    // the inner solve in three captured parts: prologue, one V-cycle (replayed K-1 times), epilogue
+    cudaGraphExec_t inner_exec[3] = {nullptr, nullptr, nullptr};
+    long long inner_key = -1, inner_launches[3] = {0, 0, 0}, inner_steps[3] = {0, 0, 0};
     // FP64-accurate residual in integer arithmetic around tensor-core products (P <= 256 or a
     // multiple of 256 up to 1024)
     bool use_oz = false;
@@ -124,7 +125,8 @@ void sfde_free_mixed(sfde_ctx* c) {
         cudaFree(L.u); cudaFree(L.g);
     }
     cudaFree(M->T1); cudaFree(M->T2); cudaFree(M->T3); cudaFree(M->err);
-    if (M->inner_exec) cudaGraphExecDestroy(M->inner_exec);
+    for (auto& g : M->inner_exec)
+        if (g) cudaGraphExecDestroy(g);
     sfde_oz_free_matrix(&M->oAx);
     sfde_oz_free_matrix(&M->oAy);
     cudaFree(M->oz_dV);
@@ -400,28 +402,30 @@ struct LpEngine {
     }
 };
 
-// Steps 2-4 of one outer iteration, queued on c->stream without any host synchronisation:
-// g_n = S_n^{-1} rho_n (rho already in g_0[1..N]), K V-cycles on E_n = Psi_n E_{n-1} + g_n from
-// E = 0 (the last one ends after its relaxation, so E is F-consistent), then U += E in FP64.
-sfde_status enqueue_inner(sfde_ctx* c, SfdeMixed* M, LpEngine& E, double* U, int kind, int K) {
+// Steps 2-4 of one outer iteration, queued on c->stream without any host synchronisation, in three
+// parts: (0) g_n = S_n^{-1} rho_n (rho already in g_0[1..N]) and E = 0; (1) one V-cycle on
+// E_n = Psi_n E_{n-1} + g_n up to the C-point correction; (2) the relaxation of the last V-cycle (so
+// E is F-consistent; the sequential solve when there is one level) and U += E in FP64.  K V-cycles
+// are part 0, K-1 times part 1, part 2.
+sfde_status enqueue_inner_part(sfde_ctx* c, SfdeMixed* M, LpEngine& E, double* U, int kind, int part) {
     LpLevel& L0 = M->lev[0];
     const size_t P2 = c->P2();
-    SFDE_CUDA(cudaMemsetAsync(L0.g, 0, P2 * M->esz, c->stream));
-    SFDE_TRY(E.step(L0.g, L0.nalloc, 1, 1, c->nt, true, SCHEME_SOLVE, c->dt0, 1, 1, E.slice(L0.g, 1), 1,
-                    nullptr, nullptr, nullptr, nullptr));
-    SFDE_CUDA(cudaMemsetAsync(L0.u, 0, P2 * M->esz * L0.nalloc, c->stream));
-    if (E.L == 1) {
-        SFDE_TRY(E.coarsest(0));
-    } else {
-        for (int k = 1; k <= K; ++k) {
-            SFDE_TRY(E.relaxation(0));
-            if (k == K) break;
-            SFDE_TRY(E.residual(0, nullptr, nullptr));
-            SFDE_CUDA(cudaMemsetAsync(M->lev[1].u, 0, P2 * M->esz * (M->lev[1].N + 1), c->stream));
-            SFDE_TRY(E.solve(1));
-            SFDE_TRY(E.correct(0));
-        }
+    if (part == 0) {
+        SFDE_CUDA(cudaMemsetAsync(L0.g, 0, P2 * M->esz, c->stream));
+        SFDE_TRY(E.step(L0.g, L0.nalloc, 1, 1, c->nt, true, SCHEME_SOLVE, c->dt0, 1, 1, E.slice(L0.g, 1), 1,
+                        nullptr, nullptr, nullptr, nullptr));
+        SFDE_CUDA(cudaMemsetAsync(L0.u, 0, P2 * M->esz * L0.nalloc, c->stream));
+        return SFDE_OK;
     }
+    if (part == 1) {
+        SFDE_TRY(E.relaxation(0));
+        SFDE_TRY(E.residual(0, nullptr, nullptr));
+        SFDE_CUDA(cudaMemsetAsync(M->lev[1].u, 0, P2 * M->esz * (M->lev[1].N + 1), c->stream));
+        SFDE_TRY(E.solve(1));
+        return E.correct(0);
+    }
+    if (E.L == 1) SFDE_TRY(E.coarsest(0));
+    else SFDE_TRY(E.relaxation(0));
     const size_t n = P2 * (size_t)c->nt;
     if (kind == 0)
         k_add_correction<__nv_bfloat16><<<grid_for(n), 256, 0, c->stream>>>(U + P2, (const __nv_bfloat16*)E.slice(L0.u, 1), n);
@@ -429,6 +433,29 @@ sfde_status enqueue_inner(sfde_ctx* c, SfdeMixed* M, LpEngine& E, double* U, int
         k_add_correction<float><<<grid_for(n), 256, 0, c->stream>>>(U + P2, (const float*)E.slice(L0.u, 1), n);
     sfde_count_launch(c);
     SFDE_CUDA(cudaGetLastError());
+    return SFDE_OK;
+}
+
+// Capture part `part` of the inner solve as a CUDA graph (once per configuration).
+sfde_status capture_inner_part(sfde_ctx* c, SfdeMixed* M, LpEngine& E, double* U, int kind, int part) {
+    if (!M->cap) SFDE_CUDA(cudaStreamCreateWithFlags(&M->cap, cudaStreamNonBlocking));
+    cudaStream_t user = c->stream;
+    const long long before = c->prof.launches, steps_before = E.steps;
+    SFDE_CUDA(cudaStreamBeginCapture(M->cap, cudaStreamCaptureModeThreadLocal));
+    c->stream = M->cap;
+    const sfde_status cs = enqueue_inner_part(c, M, E, U, kind, part);
+    c->stream = user;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(M->cap, &graph);
+    if (cs != SFDE_OK) { if (graph) cudaGraphDestroy(graph); return cs; }
+    SFDE_CUDA(ce);
+    const cudaError_t ie = cudaGraphInstantiate(&M->inner_exec[part], graph, 0);
+    cudaGraphDestroy(graph);
+    SFDE_CUDA(ie);
+    M->inner_launches[part] = c->prof.launches - before;
+    M->inner_steps[part] = E.steps - steps_before;
+    c->prof.launches = before;
+    E.steps = steps_before;
     return SFDE_OK;
 }
 
@@ -442,7 +469,7 @@ sfde_status check_err(SfdeMixed* M, cudaStream_t s) {
 }  // namespace
 
 sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) {
-    const int kind = c->precision == SFDE_PREC_MIXED_BF16 ? 0 : 1;
+    const int kind = sfde_mixed_kind(c);
     SFDE_TRY(setup_mixed(c, kind, o->m, o->max_levels, o->min_coarse));
     SfdeMixed* M = c->mixed;
     M->fused = c->fused_step && sfde_fused_supported(kind, c->x.P, c->y.P);
@@ -455,12 +482,13 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
     SFDE_TRY(sfde_choose_coarse(c, o->m, o->coarse, &coarse, &tub));
     LpEngine E{c, M, o->m, L, o->relax, coarse == SFDE_COARSE_CN ? SCHEME_CN : SCHEME_BE};
     // inner V-cycles per refinement step: enough for the inner error to reach the low-precision
-    // floor (about 2e-2 BF16, 3e-3 TF32) at MGRIT contraction ~0.3 per V-cycle
+    // floor (about 2e-2 BF16, 3e-3 TF32) at MGRIT contraction ~0.3 per V-cycle.  (Raising K when the
+    // refinement contracts slowly does not help: there the floor itself is high -- rounding
+    // accumulated over long stiff runs -- and more V-cycles only add time.)
     const int K = o->inner_cycles > 0 ? o->inner_cycles : (kind == 0 ? 4 : 5);
-    // the inner solve is captured once as a CUDA graph and replayed; eager while kernels are timed
+    // the inner solve is captured once as CUDA graphs and replayed; eager while kernels are timed
     const bool use_graph = !c->prof.on;
-    const long long key = ((long long)M->fused << 20) | ((long long)K << 8) | ((long long)E.scheme << 4) |
-                          (long long)o->relax;
+    const long long key = ((long long)M->fused << 20) | ((long long)E.scheme << 4) | (long long)o->relax;
     long long graph_steps = 0;
 
     mgrit_stats S{};
@@ -497,36 +525,27 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
         if (!isfinite(nrm)) { rc = SFDE_ENOCONV; break; }
         if (nrm <= std::max(o->rel_tol * S.res0, o->abs_tol)) { S.converged = 1; break; }
         // 2-4: correction right-hand side, inner V-cycles, U += E (no host synchronisation inside)
+        const int Kr = L == 1 ? 1 : K;
         if (use_graph) {
-            if (!M->inner_exec || M->inner_key != key) {
-                if (M->inner_exec) { cudaGraphExecDestroy(M->inner_exec); M->inner_exec = nullptr; }
-                if (!M->cap) SFDE_CUDA(cudaStreamCreateWithFlags(&M->cap, cudaStreamNonBlocking));
-                cudaStream_t user = c->stream;
-                const long long before = c->prof.launches;
-                SFDE_CUDA(cudaStreamBeginCapture(M->cap, cudaStreamCaptureModeThreadLocal));
-                c->stream = M->cap;
-                const sfde_status cs = enqueue_inner(c, M, E, U, kind, K);
-                c->stream = user;
-                cudaGraph_t graph = nullptr;
-                const cudaError_t ce = cudaStreamEndCapture(M->cap, &graph);
-                if (cs != SFDE_OK) { if (graph) cudaGraphDestroy(graph); return cs; }
-                SFDE_CUDA(ce);
-                const cudaError_t ie = cudaGraphInstantiate(&M->inner_exec, graph, 0);
-                cudaGraphDestroy(graph);
-                SFDE_CUDA(ie);
+            if (M->inner_key != key) {
+                for (auto& g : M->inner_exec)
+                    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+                for (int part = 0; part < 3; ++part)
+                    if (part != 1 || L > 1) SFDE_TRY(capture_inner_part(c, M, E, U, kind, part));
                 M->inner_key = key;
-                M->inner_launches = c->prof.launches - before;
-                M->inner_steps = E.steps;
-                c->prof.launches = before;
-                E.steps = 0;
             }
-            SFDE_CUDA(cudaGraphLaunch(M->inner_exec, c->stream));
-            sfde_count_launch(c, (int)M->inner_launches);
-            graph_steps += M->inner_steps;
+            for (int r = 0; r < Kr + 1; ++r) {
+                const int part = r == 0 ? 0 : (r == Kr ? 2 : 1);
+                SFDE_CUDA(cudaGraphLaunch(M->inner_exec[part], c->stream));
+                sfde_count_launch(c, (int)M->inner_launches[part]);
+                graph_steps += M->inner_steps[part];
+            }
         } else {
-            SFDE_TRY(enqueue_inner(c, M, E, U, kind, K));
+            SFDE_TRY(enqueue_inner_part(c, M, E, U, kind, 0));
+            for (int k = 1; k < Kr; ++k) SFDE_TRY(enqueue_inner_part(c, M, E, U, kind, 1));
+            SFDE_TRY(enqueue_inner_part(c, M, E, U, kind, 2));
         }
-        inner_total += (L == 1) ? 1 : K;
+        inner_total += Kr;
     }
     E.steps += graph_steps;
     if (!S.converged && rc == SFDE_OK) rc = SFDE_ENOCONV;
@@ -584,8 +603,8 @@ extern "C" sfde_status sfde_debug_lp_step(sfde_ctx* c, int fused, int scheme, co
                                          const double* g, const double* ut, double* out, double* norm2) {
     if (!c || !U || !out || batch < 1 || n0 < 1 || (long long)n0 + batch - 1 > c->nt || scheme < 0 || scheme > 2)
         return SFDE_EINVAL;
-    if (c->precision != SFDE_PREC_MIXED_BF16 && c->precision != SFDE_PREC_MIXED_TF32) return SFDE_EINVAL;
-    const int kind = c->precision == SFDE_PREC_MIXED_BF16 ? 0 : 1;
+    if (c->precision == SFDE_PREC_FP64) return SFDE_EINVAL;
+    const int kind = sfde_mixed_kind(c);
     if (fused && !sfde_fused_supported(kind, c->x.P, c->y.P)) return SFDE_EUNSUPPORTED;
     if (!c->mixed || c->mixed->kind != kind) SFDE_TRY(setup_mixed(c, kind, 2, 1, 1));
     SfdeMixed* M = c->mixed;
@@ -630,8 +649,8 @@ extern "C" sfde_status sfde_debug_lp_chain(sfde_ctx* c, int mode, int scheme, co
     if (!c || !U || !out || batch < 1 || nchain < 1 || n0 < 1 || scheme < 0 || scheme > 1 ||
         (long long)n0 + (long long)batch * nchain - 1 > c->nt || mode < 0 || mode > 2)
         return SFDE_EINVAL;
-    if (c->precision != SFDE_PREC_MIXED_BF16 && c->precision != SFDE_PREC_MIXED_TF32) return SFDE_EINVAL;
-    const int kind = c->precision == SFDE_PREC_MIXED_BF16 ? 0 : 1;
+    if (c->precision == SFDE_PREC_FP64) return SFDE_EINVAL;
+    const int kind = sfde_mixed_kind(c);
     if (mode != 0 && !sfde_fused_supported(kind, c->x.P, c->y.P)) return SFDE_EUNSUPPORTED;
     if (!c->mixed || c->mixed->kind != kind) SFDE_TRY(setup_mixed(c, kind, 2, 1, 1));
     SfdeMixed* M = c->mixed;

@@ -179,6 +179,13 @@ struct FusedStepArgs {
     int* err;                             // device error word (bounded waits)
 };
 bool sfde_fused_supported(int kind, int Px, int Py);
+// low-precision operand kind of a mixed-precision context: 0 BF16, 1 TF32 (SFDE_PREC_MIXED_AUTO
+// resolved by size and length, see include/sfde.h)
+inline int sfde_mixed_kind(const sfde_ctx* c) {
+    if (c->precision == SFDE_PREC_MIXED_BF16) return 0;
+    if (c->precision == SFDE_PREC_MIXED_TF32) return 1;
+    return (sfde_fused_supported(0, c->x.P, c->y.P) && c->nt <= 1024) ? 0 : 1;
+}
 sfde_status sfde_fused_prepare();
 // O1, O2: W_x^T, W_y^T (V_x^T, V_y^T for the solve); O3, O4: V_x, V_y -- K-major P x P BF16 maps.
 sfde_status sfde_fused_step(sfde_ctx* c, int P, const CUtensorMap& U, const CUtensorMap& O1, const CUtensorMap& O2,

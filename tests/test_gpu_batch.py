@@ -19,9 +19,9 @@ import paper_1805_06688_gb300 as sfde  # noqa: E402
 
 # (beta, gamma, kx, ky, nx, ny, nt, grid, precision, forcing seed or None)
 INSTANCES = [
-    (0.6, 0.9, 1.0, 0.5, 63, 63, 128, "uniform", sfde.PREC_MIXED_BF16, None),
+    (0.6, 0.9, 1.0, 0.5, 63, 63, 128, "uniform", sfde.PREC_MIXED_AUTO, None),
     (0.75, 0.8, 0.3, 1.7, 127, 100, 64, "graded", sfde.PREC_MIXED_BF16, 3),
-    (0.55, 0.95, 1.0, 0.1, 255, 255, 256, "uniform", sfde.PREC_MIXED_BF16, None),
+    (0.55, 0.95, 1.0, 0.1, 255, 255, 256, "uniform", sfde.PREC_MIXED_AUTO, None),
     (0.9, 0.6, 2.0, 0.2, 200, 150, 96, "uniform", sfde.PREC_MIXED_TF32, 5),
     (0.7, 0.7, 1.0, 1.0, 40, 31, 64, "graded", sfde.PREC_FP64, None),
     (0.65, 0.85, 1.5, 0.7, 300, 260, 64, "uniform", sfde.PREC_MIXED_BF16, None),
