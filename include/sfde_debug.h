@@ -38,13 +38,23 @@ sfde_status sfde_debug_oz_gemm(const double* X, int batch, int R, int K, const d
  * The FP64 space-time residual of the mixed-precision solver for a given iterate (Eq. (2.4)):
  *   rho_n = F_n + B_n U_{n-1} - S_n U_n,  n = 1..N_t,
  * U: (N_t+1) x N_y x N_x doubles (host or device); rho: N_t x N_y x N_x floats (host or device),
- * rounded to TF32 as the solver stores it; *norm2 = sum of rho_n^2.  use_tensor_cores = 1 assembles
- * rho in integer arithmetic around digit-split BF16 tensor-core products (padded P_x, P_y <= 256 or
- * multiples of 256 up to 1024; *norm2 from the stored FP32 values, relative accuracy about 2^-22),
- * 0 with FP64 arithmetic (*norm2 of the FP64 values).  Synchronous; allocates scratch.
+ * rounded to TF32 as the solver stores it; *norm2 = sum of rho_n^2.  use_tensor_cores = 1 (or 7)
+ * assembles rho in integer arithmetic around digit-split BF16 tensor-core products with seven
+ * digits per operand, 4..6 with that many (operands truncated at about 2^{9-8 nd} of their scales);
+ * padded P_x, P_y <= 256 or multiples of 256 up to 1024; *norm2 from the stored FP32 values,
+ * relative accuracy about 2^-22.  0 uses FP64 arithmetic (*norm2 of the FP64 values).
+ * Synchronous; allocates scratch.
  */
 sfde_status sfde_debug_residual(sfde_ctx* ctx, const double* U, int use_tensor_cores, float* rho,
                                 double* norm2);
+
+/*
+ * Digits per operand of the mixed-precision solver's tensor-core residual (Eq. (2.4)): 0 (default)
+ * chooses 4 to 7 per outer iteration from the residual's size relative to the first one, always
+ * confirming convergence with 7 (exact operands); 4..7 fixes the count.  Takes effect at the next
+ * mgrit_solve.
+ */
+sfde_status sfde_debug_set_residual_digits(sfde_ctx* ctx, int nd);
 
 /*
  * Whether the BF16 mixed-precision solver runs each spectral step as one fused kernel (the four

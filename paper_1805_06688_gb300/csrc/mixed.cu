@@ -506,18 +506,42 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
     LpLevel& L0 = M->lev[0];
     sfde_status rc = SFDE_OK;
     long long inner_total = 0;
+    // digits of the tensor-core residual: the refinement needs the residual to a fraction of its own
+    // size only, about 1e-5 ||rho_{k-1}|| (scale: the first residual, with a wide margin); the digit
+    // products of nd digits are accurate to about 2^{9-8 nd} of the operands' scale.  A residual
+    // that passes the stopping test with fewer than 7 digits is recomputed with all 7.
+    auto digits_for = [&](double prev) {
+        if (prev <= 0.0 || S.res0 <= 0.0) return 4;
+        const double need = 1e-5 * prev / S.res0;
+        int nd = 4;
+        while (nd < 7 && ldexp(1.0, 9 - 8 * nd) > need) ++nd;
+        return nd;
+    };
+    double prev_nrm = 0.0;
+    long long digit_products = 0;
     for (int it = 1; it <= o->max_iter; ++it) {
         // 1. FP64 residual of Eq. (2.4) at n = 1..N_t, stored low precision in g_0[n]
-        int np = 0;
-        if (M->use_oz)
-            SFDE_TRY(sfde_residual_int(c, U, 1, c->nt, E.slice(L0.g, 1), (long long)P2, kind, c->partial, &np,
-                                       M->oAx, M->oAy, M->oz_dV, M->oz_dVt, M->oz_E, M->err));
-        else
-            SFDE_TRY(sfde_residual_fp64(c, U, 1, c->nt, E.slice(L0.g, 1), (long long)P2, kind, c->partial, &np));
-        double r2 = 0.0;
-        SFDE_TRY(sfde_reduce_partials(c, np, &r2));
-        SFDE_TRY(check_err(M, c->stream));
-        const double nrm = sqrt(r2);
+        int nd = c->resid_digits ? c->resid_digits : digits_for(it == 1 ? 0.0 : prev_nrm);
+        double nrm = 0.0;
+        for (;;) {
+            int np = 0;
+            if (M->use_oz) {
+                SFDE_TRY(sfde_residual_int(c, U, 1, c->nt, E.slice(L0.g, 1), (long long)P2, kind, c->partial, &np,
+                                           M->oAx, M->oAy, M->oz_dV, M->oz_dVt, M->oz_E, M->err, nd));
+                digit_products += nd * (nd + 1) / 2;
+            } else {
+                SFDE_TRY(sfde_residual_fp64(c, U, 1, c->nt, E.slice(L0.g, 1), (long long)P2, kind, c->partial, &np));
+                nd = 7;
+            }
+            double r2 = 0.0;
+            SFDE_TRY(sfde_reduce_partials(c, np, &r2));
+            SFDE_TRY(check_err(M, c->stream));
+            nrm = sqrt(r2);
+            const double res0 = it == 1 ? nrm : S.res0;
+            if (nd == 7 || !(nrm <= std::max(o->rel_tol * res0, o->abs_tol))) break;
+            nd = 7;   // apparently converged: confirm with exact operands
+        }
+        prev_nrm = nrm;
         if (it - 1 < SFDE_HISTORY_MAX) S.history[it - 1] = nrm;
         if (it == 1) S.res0 = nrm;
         S.res_final = nrm;
@@ -592,6 +616,12 @@ sfde_status load_lp(sfde_ctx* c, const double* in, int batch, double* tmp_unp, d
     return SFDE_OK;
 }
 }  // namespace
+
+extern "C" sfde_status sfde_debug_set_residual_digits(sfde_ctx* c, int nd) {
+    if (!c || (nd != 0 && (nd < 4 || nd > 7))) return SFDE_EINVAL;
+    c->resid_digits = nd;
+    return SFDE_OK;
+}
 
 extern "C" sfde_status sfde_debug_set_fused_step(sfde_ctx* c, int enable) {
     if (!c) return SFDE_EINVAL;

@@ -87,6 +87,7 @@ struct OzArgs {
     const int* me;               // column exponents, N (FP64 output only)
     void* out; long long out_stride;     // Out_b = (X_b Mat)^T, N x R per slice: double or int64
     int zshift;                  // integer output: final right shift (units 2^{zshift-52})
+    int nd;                      // integer output: digits used per operand (4..7; p + q <= nd + 1)
     int* err;
 };
 
@@ -126,6 +127,11 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
     const int n0 = blockIdx.x * BN;
     const long long Mtot = (long long)p.batch * p.R;
     const int nchunks = (p.K + KC - 1) / KC;
+    // digits in use: the 7-digit plan's products and accumulators are ordered by digit sum, so the
+    // plan for nd digits (products with p + q <= nd + 1) is a prefix of both lists
+    const int nd = INT_OUT ? p.nd : S;
+    const int nprod = INT_OUT ? nd * (nd + 1) / 2 : NPROD;
+    const int nacc = INT_OUT ? (nd == 7 ? 13 : 2 * nd - 2) : NACC;
     constexpr int CPG = KGROUP / KC;          // chunks per K group
     const int ngroups = (nchunks + CPG - 1) / CPG;
 
@@ -153,8 +159,8 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
             if (!ok) break;
             uint8_t* sX = smem + st * STAGE;
             uint8_t* sM = sX + S * XTILE;
-            tc::mbar_arrive_expect_tx(&full[st], (uint32_t)STAGE);
-            for (int d = 0; d < S; ++d) {
+            tc::mbar_arrive_expect_tx(&full[st], (uint32_t)(nd * (XTILE + MTILE)));
+            for (int d = 0; d < nd; ++d) {
                 tc::tma_load_4d(sX + d * XTILE, &mapX, &full[st], c * KC, r0, b0, d);
                 tc::tma_load_3d(sM + d * MTILE, &mapM, &full[st], c * KC, n0, d);
             }
@@ -177,8 +183,7 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
             tc::tc_fence_after();
             const uint8_t* sX = smem + st * STAGE;
             const uint8_t* sM = sX + S * XTILE;
-#pragma unroll
-            for (int i = 0; i < NPROD; ++i) {
+            for (int i = 0; i < nprod; ++i) {
                 const int dp = prod_entry<INT_OUT>(i, 0) - 1, dq = prod_entry<INT_OUT>(i, 1) - 1;
                 const int a = prod_entry<INT_OUT>(i, 2);
                 // the first product of an accumulator in a group's first chunk overwrites it
@@ -214,7 +219,7 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
             tc::tc_fence_after();
             if (!acc_ok) break;
 #pragma unroll 1
-            for (int a = 0; a < NACC; ++a) {
+            for (int a = 0; a < nacc; ++a) {
                 uint32_t v[32];
                 tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * BN), v);
                 const int d = acc_digit_sum<INT_OUT>(a);
@@ -512,9 +517,10 @@ sfde_status launch_oz(sfde_ctx* c, const CUtensorMap& mapX, const OzMatrix& M, c
     dim3 grid(M.N / BN, (unsigned)mt);
     const int slot = sfde_prof_begin(c);
     k_ozaki_slice_gemm<INT_OUT><<<grid, OZ_THREADS, smem_bytes<INT_OUT>(), s>>>(mapX, M.map, a);
-    // tensor work: NPROD digit products of 2 R K N flops each; bytes: the digit planes of X, the
-    // matrix digits and the output (8 bytes per element) once
-    constexpr int S = Plan<INT_OUT>::S, NPROD = Plan<INT_OUT>::NPROD;
+    // tensor work: the digit products of 2 R K N flops each; bytes: the digit planes of X in use,
+    // the matrix digits and the output (8 bytes per element) once
+    const int S = INT_OUT ? a.nd : Plan<false>::S;
+    const int NPROD = INT_OUT ? a.nd * (a.nd + 1) / 2 : Plan<false>::NPROD;
     sfde_prof_end(c, slot, 4, (double)NPROD * 2.0 * a.batch * nr * nc * nout,
                   2.0 * S * ((double)a.batch * nr * nc + (double)nc * nout) + 8.0 * a.batch * nr * nout);
     sfde_count_launch(c);
@@ -551,9 +557,9 @@ int sfde_oz_int_shift(int K) {
 
 sfde_status sfde_oz_gemm_int(sfde_ctx* c, void* xdigits, long long plane, int R, int K, int batch,
                              const OzMatrix& M, long long* out, long long out_stride, int* err, int nr, int nc,
-                             int nout) {
+                             int nout, int nd) {
     if (K != M.K || K > 1024 || (K > KGROUP && K % KGROUP) || R % 32 || (R > 128 && R % 128) ||
-        plane < (long long)batch * R * K || M.nd != Plan<true>::S)
+        plane < (long long)batch * R * K || M.nd != Plan<true>::S || nd < 4 || nd > Plan<true>::S)
         return SFDE_EUNSUPPORTED;
     CUtensorMap mapX;
     SFDE_TRY(map_digit_planes(&mapX, xdigits, R, K, batch, plane, Plan<true>::S));
@@ -561,6 +567,7 @@ sfde_status sfde_oz_gemm_int(sfde_ctx* c, void* xdigits, long long plane, int R,
     a.R = R; a.K = K; a.N = M.N; a.batch = batch;
     a.out = out; a.out_stride = out_stride; a.err = err;
     a.zshift = sfde_oz_int_shift(K);
+    a.nd = nd;
     return launch_oz<true>(c, mapX, M, a, c->stream, nr, nc, nout);
 }
 

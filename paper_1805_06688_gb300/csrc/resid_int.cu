@@ -89,7 +89,7 @@ __device__ __forceinline__ void split7(long long x, uint16_t (&bf)[ND]) {
 // row-major [b][j][i] (rows of the A_x product) and transposed [b][i][j] (rows of the A_y product).
 __global__ void __launch_bounds__(256) k_split_pair(const double* __restrict__ U, const int* __restrict__ En, int n0,
                                                     int Px, int Py, uint16_t* __restrict__ dV, uint16_t* __restrict__ dVt,
-                                                    long long plane) {
+                                                    long long plane, int nd) {
     __shared__ uint16_t dt[ND][32][34];   // digits, [p][i][j]
     const int b = blockIdx.z, n = n0 + b;
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
@@ -104,16 +104,18 @@ __global__ void __launch_bounds__(256) k_split_pair(const double* __restrict__ U
         split7<56>(2 * (fixp(Un[e], E) + fixp(Um[e], E)), bf);     // |2V| <= 2^56, represented exactly
         const size_t o = (size_t)b * P2 + e;
 #pragma unroll
-        for (int p = 0; p < ND; ++p) {
-            dV[p * plane + o] = bf[p];
-            dt[p][tx][jj] = bf[p];
-        }
+        for (int p = 0; p < ND; ++p)
+            if (p < nd) {
+                dV[p * plane + o] = bf[p];
+                dt[p][tx][jj] = bf[p];
+            }
     }
     __syncthreads();
     for (int ii = ty; ii < 32; ii += 8) {
         const size_t o = ((size_t)b * Px + i0 + ii) * Py + j0 + tx;
 #pragma unroll
-        for (int p = 0; p < ND; ++p) dVt[p * plane + o] = dt[p][ii][tx];
+        for (int p = 0; p < ND; ++p)
+            if (p < nd) dVt[p * plane + o] = dt[p][ii][tx];
     }
 }
 
@@ -256,11 +258,12 @@ sfde_status sfde_resid_int_matrices(sfde_ctx* c, OzMatrix* Ax, OzMatrix* Ay) {
 
 sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
                               long long rout_stride, int out_kind, double* partial, int* n_partials,
-                              const OzMatrix& Ax, const OzMatrix& Ay, void* dV, void* dVt, int* En, int* err) {
+                              const OzMatrix& Ax, const OzMatrix& Ay, void* dV, void* dVt, int* En, int* err,
+                              int nd) {
     const int Px = c->x.P, Py = c->y.P;
     const size_t P2 = c->P2();
     const size_t esz = out_kind == 0 ? 2 : 4;
-    if (!sfde_resid_int_supported(Px, Py) || n_first < 1 || count < 1) return SFDE_EINVAL;
+    if (!sfde_resid_int_supported(Px, Py) || n_first < 1 || count < 1 || nd < 4 || nd > ND) return SFDE_EINVAL;
     // accounting (class 5): bytes each kernel must move once, unpadded
     const double nxy = (double)c->x.n * c->y.n;
     int slot = sfde_prof_begin(c);
@@ -274,13 +277,13 @@ sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int cou
         const long long plane = (long long)nb * Px * Py;
         dim3 grid(Px / 32, Py / 32, nb), block(32, 8);
         slot = sfde_prof_begin(c);
-        k_split_pair<<<grid, block, 0, c->stream>>>(U, En, n0, Px, Py, (uint16_t*)dV, (uint16_t*)dVt, plane);
-        sfde_prof_end(c, slot, 5, 0.0, (16.0 + 4.0 * ND) * nxy * nb);   // U pair in, 2 x 7 digit planes out
+        k_split_pair<<<grid, block, 0, c->stream>>>(U, En, n0, Px, Py, (uint16_t*)dV, (uint16_t*)dVt, plane, nd);
+        sfde_prof_end(c, slot, 5, 0.0, (16.0 + 4.0 * nd) * nxy * nb);   // U pair in, 2 x nd digit planes out
         sfde_count_launch(c);
         SFDE_TRY(sfde_oz_gemm_int(c, dV, plane, Py, Px, nb, Ax, (long long*)c->T1, (long long)P2, err, c->y.n,
-                                  c->x.n, c->x.n));
+                                  c->x.n, c->x.n, nd));
         SFDE_TRY(sfde_oz_gemm_int(c, dVt, plane, Px, Py, nb, Ay, (long long*)c->T3, (long long)P2, err, c->x.n,
-                                  c->y.n, c->y.n));
+                                  c->y.n, c->y.n, nd));
         const int blocks = (Px / 32) * (Py / 32) * nb;
         if ((size_t)(total + blocks) > c->partial_cap) return SFDE_EINVAL;
         char* ro = (char*)rout + (size_t)b0 * rout_stride * esz;
@@ -311,6 +314,8 @@ extern "C" sfde_status sfde_debug_residual(sfde_ctx* c, const double* U, int use
                                           double* norm2) {
     if (!c || !U || !rho || !norm2) return SFDE_EINVAL;
     const int Px = c->x.P, Py = c->y.P;
+    const int nd = use_tensor_cores == 1 ? ND : use_tensor_cores;
+    if (use_tensor_cores && (nd < 4 || nd > ND)) return SFDE_EINVAL;
     if (use_tensor_cores && !sfde_resid_int_supported(Px, Py)) return SFDE_EUNSUPPORTED;
     const size_t P2 = c->P2(), n2 = (size_t)c->x.n * c->y.n;
     double* u = nullptr;
@@ -344,7 +349,7 @@ extern "C" sfde_status sfde_debug_residual(sfde_ctx* c, const double* U, int use
         DC(cudaMalloc(&dV, sfde_resid_int_digit_bytes(Px, Py, (int)c->ws_slices)));
         DC(cudaMalloc(&dVt, sfde_resid_int_digit_bytes(Px, Py, (int)c->ws_slices)));
         DC(cudaMalloc(&En, sizeof(int) * (c->nt + 1)));
-        st = sfde_residual_int(c, u, 1, c->nt, rp, (long long)P2, 1, c->partial, &np, Ax, Ay, dV, dVt, En, err);
+        st = sfde_residual_int(c, u, 1, c->nt, rp, (long long)P2, 1, c->partial, &np, Ax, Ay, dV, dVt, En, err, nd);
     } else {
         st = sfde_residual_fp64(c, u, 1, c->nt, rp, (long long)P2, 1, c->partial, &np);
     }

@@ -103,6 +103,7 @@ struct sfde_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     struct SfdeMixed* mixed = nullptr;  // tensor-core operands and inner hierarchy (mixed.cu)
     int fused_step = 1;         // BF16 steps as one fused kernel where the padded sizes allow it
+    int resid_digits = 0;       // digits of the tensor-core residual: 0 per iteration, else 4..7 fixed
     SfdeProf prof;
     size_t P2() const { return (size_t)x.P * (size_t)y.P; }
 };
@@ -219,18 +220,20 @@ sfde_status sfde_oz_gemm(sfde_ctx* c, const double* X, const double* X2, long lo
 int sfde_oz_int_shift(int K);  // the integer product's extra right shift for contraction length K
 sfde_status sfde_oz_gemm_int(sfde_ctx* c, void* xdigits, long long plane, int R, int K, int batch,
                              const OzMatrix& M, long long* out, long long out_stride, int* err, int nr, int nc,
-                             int nout);
+                             int nout, int nd);
 
 // ---- the space-time residual of sfde_residual_fp64 in integer arithmetic around two digit-split
 // tensor-core products (resid_int.cu), Px, Py <= 1024.  Ax, Ay from sfde_resid_int_matrices; dV, dVt:
 // sfde_resid_int_digit_bytes(Px, Py, ws_slices) each (digits of 2V row-major and transposed); En:
-// N_t + 1 ints; err: device error word.
+// N_t + 1 ints; err: device error word; nd: digits per operand, 4..7 (7: exact operands; fewer
+// digits truncate V and the matrices at about 2^{9-8 nd} of their scales).
 bool sfde_resid_int_supported(int Px, int Py);
 size_t sfde_resid_int_digit_bytes(int Px, int Py, int batch);
 sfde_status sfde_resid_int_matrices(sfde_ctx* c, OzMatrix* Ax, OzMatrix* Ay);
 sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
                               long long rout_stride, int out_kind, double* partial, int* n_partials,
-                              const OzMatrix& Ax, const OzMatrix& Ay, void* dV, void* dVt, int* En, int* err);
+                              const OzMatrix& Ax, const OzMatrix& Ay, void* dV, void* dVt, int* En, int* err,
+                              int nd);
 void sfde_launch_mass_x_transpose(const double* Un, const double* Um, double* T2, int Px, int Py, double hx,
                                   int nb, cudaStream_t s);
 

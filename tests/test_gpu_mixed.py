@@ -91,3 +91,25 @@ def test_mixed_bump_N511_Nt2048_full_size():
     scale = max(np.abs(exact[n]).max() for n in keep)
     for n in keep:
         assert np.abs(U[n].cpu().numpy() - exact[n]).max() < 1e-8 * scale, n
+
+
+def test_mixed_adaptive_and_exact_residual_digits_agree():
+    """The refinement with per-iteration residual digits (4 to 7) and with 7 throughout both reach
+    the exact sequential solution to 1e-8; the stopping test always uses 7 digits."""
+    import ctypes
+    nx, ny, nt = 100, 70, 96
+    t = time_grid(nt, 1.0, "uniform")
+    F, _ = gaussian_bump_forcing(5, nx, ny, t)
+    psi = sine_mode_nodal(sine_mode_amplitudes(4), nx, ny)
+    ref = osfde.seq_timestep(osfde.SFDE(0.6, 0.9, 1.0, 0.5, nx, ny, t), psi, F)
+    L = sfde.lib()
+    L.sfde_debug_set_residual_digits.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    for nd in (0, 7):
+        P = sfde.Problem(0.6, 0.9, 1.0, 0.5, nx, ny, t, precision=sfde.PREC_MIXED_BF16)
+        P.set_initial(psi)
+        P.set_forcing(F)
+        assert L.sfde_debug_set_residual_digits(P.ctx, nd) == 0
+        U = np.zeros((nt + 1, ny, nx))
+        _, st = P.mgrit(U=U, m=4, max_levels=8, coarse=sfde.COARSE_BE, rel_tol=1e-11, max_iter=60)
+        assert st.converged
+        assert _err(U, ref) < 1e-8, (nd, st.iters, _err(U, ref))

@@ -107,3 +107,19 @@ def test_residual_not_finite():
     P = sfde.Problem(0.8, 0.7, 1.0, 2.0, nx, ny, t, precision=sfde.PREC_MIXED_TF32)
     _, nrm = gpu_residual(P, U, 1)
     assert not np.isfinite(nrm)
+
+
+@pytest.mark.parametrize("nd", [4, 5, 6])
+def test_residual_with_fewer_digits(nd):
+    """With nd digits per operand the products are truncated at about 2^(9 - 8 nd) of the operands'
+    scale (the refinement uses this while its residual is still large); the error against the
+    oracle is bounded by 2^(12 - 8 nd) of ||S U|| (a factor 8 of margin), and shrinks with nd."""
+    nx, ny, nt = 255, 200, 4
+    t = time_grid(nt, 1.0, "uniform")
+    O = osfde.SFDE(0.65, 0.85, 1.2, 0.6, nx, ny, t)
+    U = np.random.default_rng(nd).standard_normal((nt + 1, ny, nx))
+    P = sfde.Problem(0.65, 0.85, 1.2, 0.6, nx, ny, t, precision=sfde.PREC_MIXED_TF32)
+    rho, nrm = gpu_residual(P, U, nd)
+    ref, scale = oracle_residual(O, U, None)
+    rn = np.sqrt(np.sum(ref ** 2))
+    assert abs(nrm - rn) <= 2.0 ** (12 - 8 * nd) * scale + 2.0 ** -20 * rn
