@@ -98,10 +98,19 @@ __global__ void __launch_bounds__(256) k_split_pair(const double* __restrict__ U
     const size_t P2 = (size_t)Px * Py;
     const unsigned long long* Un = (const unsigned long long*)(U + (size_t)n * P2);
     const unsigned long long* Um = (const unsigned long long*)(U + (size_t)(n - 1) * P2);
-    for (int jj = ty; jj < 32; jj += 8) {
+    unsigned long long un[4], um[4];   // all loads first: their latencies overlap
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const size_t e = (size_t)(j0 + ty + 8 * k) * Px + i0 + tx;
+        un[k] = __ldg(Un + e);
+        um[k] = __ldg(Um + e);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int jj = ty + 8 * k;
         const size_t e = (size_t)(j0 + jj) * Px + i0 + tx;
         uint16_t bf[ND];
-        split7<56>(2 * (fixp(Un[e], E) + fixp(Um[e], E)), bf);     // |2V| <= 2^56, represented exactly
+        split7<56>(2 * (fixp(un[k], E) + fixp(um[k], E)), bf);     // |2V| <= 2^56, represented exactly
         const size_t o = (size_t)b * P2 + e;
 #pragma unroll
         for (int p = 0; p < ND; ++p)
@@ -152,7 +161,7 @@ __device__ __forceinline__ long long rshr(long long x, int k) {
 // at least once before they are added.  Writes rho (BF16 or TF32-rounded FP32), zero
 // outside the interior nodes, and one FP64 sum of rho^2 per block.
 template <typename OT>
-__global__ void __launch_bounds__(256, 4) k_combine_int(
+__global__ void __launch_bounds__(256, 3) k_combine_int(
     const long long* __restrict__ T1, const long long* __restrict__ T3, const double* __restrict__ U,
     const int* __restrict__ En, int n0, int Px, int Py, int nx, int ny, double cmass, int ex, int ey, int zsx, int zsy,
     const double* __restrict__ dt, int rank, const double* __restrict__ time_w, const double* __restrict__ bxn,
@@ -167,29 +176,48 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int E = max(En[n - 1], En[n]);
     const size_t P2 = (size_t)Px * Py;
+    // all global loads of the block are issued before any of them is used (compile-time trip
+    // counts, register staging), so their latencies overlap
     const long long* T1b = T1 + (size_t)b * P2;
-    for (int ii = ty; ii < 32; ii += 8)
-        for (int c = tx; c < 34; c += 32) {
-            const int j = j0 + c - 1;
-            t1[ii][c] = (j >= 0 && j < Py) ? T1b[(size_t)(i0 + ii) * Py + j] : 0;
-        }
     const long long* T3b = T3 + (size_t)b * P2;
-    for (int jj = ty; jj < 32; jj += 8)
-        for (int c = tx; c < 34; c += 32) {
-            const int i = i0 + c - 1;
-            t3[jj][c] = (i >= 0 && i < Px) ? T3b[(size_t)(j0 + jj) * Px + i] : 0;
-        }
     const unsigned long long* Un = (const unsigned long long*)(U + (size_t)n * P2);
     const unsigned long long* Um = (const unsigned long long*)(U + (size_t)(n - 1) * P2);
-    for (int r = ty; r < 34; r += 8)
-        for (int c = tx; c < 34; c += 32) {
+    long long a1[4][2], a3[4][2];
+    unsigned long long um[5][2], un[5][2];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = tx + 32 * h;
+            const int j = j0 + c - 1, i = i0 + c - 1;
+            a1[k][h] = (c < 34 && j >= 0 && j < Py) ? __ldg(T1b + (size_t)(i0 + ty + 8 * k) * Py + j) : 0;
+            a3[k][h] = (c < 34 && i >= 0 && i < Px) ? __ldg(T3b + (size_t)(j0 + ty + 8 * k) * Px + i) : 0;
+        }
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = ty + 8 * k, c = tx + 32 * h;
             const int j = j0 + r - 1, i = i0 + c - 1;
-            long long v = 0;
-            if (j >= 0 && j < Py && i >= 0 && i < Px) {
-                const size_t e = (size_t)j * Px + i;
-                v = fixp(Um[e], E) - fixp(Un[e], E);
+            const bool in = r < 34 && c < 34 && j >= 0 && j < Py && i >= 0 && i < Px;
+            const size_t e = in ? (size_t)j * Px + i : 0;
+            um[k][h] = in ? __ldg(Um + e) : 0ull;
+            un[k][h] = in ? __ldg(Un + e) : 0ull;
+        }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (tx + 32 * h < 34) {
+                t1[ty + 8 * k][tx + 32 * h] = a1[k][h];
+                t3[ty + 8 * k][tx + 32 * h] = a3[k][h];
             }
-            du[r][c] = v;
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = ty + 8 * k, c = tx + 32 * h;
+            if (r < 34 && c < 34) du[r][c] = fixp(um[k][h], E) - fixp(un[k][h], E);   // fix(0) = 0
         }
     const int u1 = E + ex - 51 + zsx, u2 = E + ey - 51 + zsy, u = max(u1, u2) + 1;
     if (tx == 0 && ty == 0) {
