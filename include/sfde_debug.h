@@ -41,7 +41,7 @@ sfde_status sfde_debug_oz_gemm(const double* X, int batch, int R, int K, const d
  * rounded to TF32 as the solver stores it; *norm2 = sum of rho_n^2.  use_tensor_cores = 1 (or 7)
  * assembles rho in integer arithmetic around digit-split BF16 tensor-core products with seven
  * digits per operand, 4..6 with that many (operands truncated at about 2^{9-8 nd} of their scales);
- * padded P_x, P_y <= 256 or multiples of 256 up to 1024; *norm2 from the stored FP32 values,
+ * padded 64 <= P_x, P_y <= 256 or multiples of 256 up to 1024; *norm2 from the stored FP32 values,
  * relative accuracy about 2^-22.  0 uses FP64 arithmetic (*norm2 of the FP64 values).
  * Synchronous; allocates scratch.
  */

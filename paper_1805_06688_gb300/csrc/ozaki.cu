@@ -9,14 +9,13 @@
 // terms with p + q <= 7 (21 digit products) are kept: the dropped ones and the digit truncation are
 // below 2^{-47} of 2^{e_r + e_n} K, the accuracy of an FP64 GEMM.
 //
-// Every digit product is an integer matrix product.  With K <= 256 a single product is at most
-// 256 * 2^16 = 2^24 in magnitude, and the products are grouped into 12 FP32 TMEM accumulators so
-// that every partial sum stays an integer of magnitude <= 2^24: FP32 accumulation is then exact.
-// The epilogue converts the 12 accumulators to integers, combines them in two int64 words
-// (digit weights 2^{-16..-40} and 2^{-48..-56}) and converts to FP64 once per output -- or, for the
-// space-time residual (resid_int.cu), leaves the product as one exact int64 in units of 2^-48 of the
-// operands' scales, so that the residual is assembled in integer arithmetic (the FP64 pipe of this
-// GPU runs at about 1/64 of the FP32 rate).
+// Every digit product is an integer matrix product, accumulated exactly in FP32 TMEM accumulators
+// as long as every partial sum stays an integer of magnitude <= 2^24 (the digit plans below).  For
+// FP64 output the epilogue combines the accumulators in two int64 words (digit weights
+// 2^{-16..-40} and 2^{-48..-56}) and converts to FP64 once per output; for the space-time residual
+// (resid_int.cu) it leaves the product as one int64 in units of 2^-52 of the operands' scales, so
+// that the residual is assembled in integer arithmetic (the FP64 pipe of this GPU runs at about
+// 1/64 of the FP32 rate).
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -29,21 +28,27 @@
 
 namespace {
 
-// K chunks of 32 BF16 (64-byte rows, 64-byte swizzle) in a three-stage ring: a stage holds every
-// digit plane of one chunk of both operands (7 x 10 KB), so loads overlap the products.
-constexpr int BM = 128, BN = 32, KC = 32, STAGES = 3;
+// K chunks of 32 BF16 (64-byte rows, 64-byte swizzle) in a ring of stages: a stage holds every
+// digit plane of one chunk of both operands, so loads overlap the products.
+constexpr int BM = 128, KC = 32;
 constexpr int XTILE = BM * KC * 2;     // 8 KB: one digit plane of the 128-row tile, one K chunk
-constexpr int MTILE = BN * KC * 2;     // 2 KB
 constexpr int TMEM_COLS = 512;
 
 // Digit plans.  Partial sums of an accumulator must stay integers of magnitude <= 2^24 (exact in
-// FP32): with K <= 256, |d_1| <= 256 and |d_p| <= 128 (p >= 2), one (1,1) product, two (1,q)/(p,1)
-// products or four products with p, q >= 2 fit in one accumulator.
-//   FP64 output: 6 digits per operand, the 21 products with p + q <= 7 in 12 accumulators;
-//   integer output: 7 digits, the 28 products with p + q <= 8 in 13 accumulators.
+// FP32).
+//   FP64 output: 6 digits per operand (|d_1| <= 256, |d_p| <= 128), K <= 256: one (1,1) product,
+//     two (1,q)/(p,1) products or four with p, q >= 2 per accumulator; the 21 products with
+//     p + q <= 7 in 12 accumulators; tiles of N = 32 columns, K summed in one group.
+//   Integer output: 7 digits per operand, all of magnitude <= 128, K summed in groups of 128: every
+//     product is at most 128^3 = 2^21 per group, so all (at most 7) products of one digit sum share
+//     an accumulator: the 28 products with p + q <= 8 in 7 accumulators, tiles of N = 64 columns.
 template <bool INT_OUT> struct Plan;
-template <> struct Plan<false> { static constexpr int S = 6, NPROD = 21, NACC = 12; };
-template <> struct Plan<true> { static constexpr int S = 7, NPROD = 28, NACC = 13; };
+template <> struct Plan<false> {
+    static constexpr int S = 6, NPROD = 21, NACC = 12, BN = 32, STAGES = 3, KGROUP = 256;
+};
+template <> struct Plan<true> {
+    static constexpr int S = 7, NPROD = 28, NACC = 7, BN = 64, STAGES = 2, KGROUP = 128;
+};
 
 // accumulator a -> digit sum d = p + q of its products, and the product list (p, q, a), grouped by a
 __constant__ int c6_acc_d[12] = {2, 3, 4, 4, 5, 5, 6, 6, 6, 7, 7, 7};
@@ -55,15 +60,15 @@ __constant__ int c6_prod[21][3] = {
     {1, 5, 6}, {2, 4, 6}, {3, 3, 7}, {4, 2, 7}, {5, 1, 8},
     {1, 6, 9}, {2, 5, 9}, {3, 4, 10}, {4, 3, 10}, {5, 2, 11}, {6, 1, 11},
 };
-__constant__ int c7_acc_d[13] = {2, 3, 4, 4, 5, 5, 6, 6, 7, 7, 8, 8, 8};
+__constant__ int c7_acc_d[7] = {2, 3, 4, 5, 6, 7, 8};
 __constant__ int c7_prod[28][3] = {
     {1, 1, 0},
     {1, 2, 1}, {2, 1, 1},
-    {1, 3, 2}, {3, 1, 2}, {2, 2, 3},
-    {1, 4, 4}, {4, 1, 4}, {2, 3, 5}, {3, 2, 5},
-    {1, 5, 6}, {5, 1, 6}, {2, 4, 7}, {3, 3, 7}, {4, 2, 7},
-    {1, 6, 8}, {6, 1, 8}, {2, 5, 9}, {3, 4, 9}, {4, 3, 9}, {5, 2, 9},
-    {1, 7, 10}, {7, 1, 10}, {2, 6, 11}, {3, 5, 11}, {4, 4, 11}, {5, 3, 11}, {6, 2, 12},
+    {1, 3, 2}, {2, 2, 2}, {3, 1, 2},
+    {1, 4, 3}, {2, 3, 3}, {3, 2, 3}, {4, 1, 3},
+    {1, 5, 4}, {2, 4, 4}, {3, 3, 4}, {4, 2, 4}, {5, 1, 4},
+    {1, 6, 5}, {2, 5, 5}, {3, 4, 5}, {4, 3, 5}, {5, 2, 5}, {6, 1, 5},
+    {1, 7, 6}, {2, 6, 6}, {3, 5, 6}, {4, 4, 6}, {5, 3, 6}, {6, 2, 6}, {7, 1, 6},
 };
 
 // table entries with the plan chosen at compile time (direct constant-bank reads, no generic loads)
@@ -79,7 +84,11 @@ __device__ __forceinline__ int acc_digit_sum(int a) {
 }
 
 template <bool INT_OUT>
-constexpr size_t smem_bytes() { return 1024 + (size_t)STAGES * Plan<INT_OUT>::S * (XTILE + MTILE) + 256; }
+constexpr int mtile() { return Plan<INT_OUT>::BN * KC * 2; }   // one digit plane of the matrix tile
+template <bool INT_OUT>
+constexpr size_t smem_bytes() {
+    return 1024 + (size_t)Plan<INT_OUT>::STAGES * Plan<INT_OUT>::S * (XTILE + mtile<INT_OUT>()) + 256;
+}
 
 struct OzArgs {
     int R, K, N, batch;          // X slice R x K (digits in planes of nslices x R x K), Mat K x N
@@ -91,16 +100,15 @@ struct OzArgs {
     int* err;
 };
 
-// Partial sums stay exact integers below 2^24 over K <= 256: longer K is summed in groups of 256,
-// each group drained from TMEM into int64 registers before the next one starts.
-constexpr int KGROUP = 256;
+// Longer K is summed in groups (Plan::KGROUP), each group drained from TMEM into int64 registers
+// before the next one starts.
 
 __device__ __forceinline__ double pow2(int e) {  // exact 2^e for normal range
     return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
 // INT_OUT: write sum_{p+q<=8} 2^{-8(p+q)} sum_k d_p c_q as one int64 in units of 2^{zshift-52}
-// (exact up to the rounding of the p + q >= 7 terms to that unit; |value| <= 2^60); otherwise FP64
+// (exact up to the rounding of the p + q >= 7 terms to that unit; |value| <= 2^58); otherwise FP64
 // scaled by the row and column exponents (p + q <= 7).
 // Roles: warp 4 lane 0 issues TMA, warp 5 lane 0 issues the MMAs, warps 0-3 drain the
 // accumulators (TMEM lanes 32w..32w+31), also between K groups while the other two roles run on.
@@ -110,10 +118,12 @@ template <bool INT_OUT>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapM, OzArgs p) {
     constexpr int S = Plan<INT_OUT>::S, NPROD = Plan<INT_OUT>::NPROD, NACC = Plan<INT_OUT>::NACC;
+    constexpr int BN = Plan<INT_OUT>::BN, STAGES = Plan<INT_OUT>::STAGES, KGROUP = Plan<INT_OUT>::KGROUP;
+    constexpr int MTILE = BN * KC * 2;
     constexpr int STAGE = S * (XTILE + MTILE);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    // stage st: S X planes (8 KB each) then S matrix planes (2 KB each)
+    // stage st: S X planes (8 KB each) then S matrix planes (BN x 64 bytes each)
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE);
     uint64_t* empty = full + STAGES;
     uint64_t* accf = empty + STAGES;
@@ -131,7 +141,7 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
     // plan for nd digits (products with p + q <= nd + 1) is a prefix of both lists
     const int nd = INT_OUT ? p.nd : S;
     const int nprod = INT_OUT ? nd * (nd + 1) / 2 : NPROD;
-    const int nacc = INT_OUT ? (nd == 7 ? 13 : 2 * nd - 2) : NACC;
+    const int nacc = INT_OUT ? nd : NACC;          // integer plan: one accumulator per digit sum
     constexpr int CPG = KGROUP / KC;          // chunks per K group
     const int ngroups = (nchunks + CPG - 1) / CPG;
 
@@ -209,27 +219,37 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
         // producer and MMA warps: nothing to drain
     } else if constexpr (INT_OUT) {
         const long long m = m0 + warp * 32 + lane;
-        // z: digit sums d <= 6 in units of 2^-52 (exact); zl: d = 7, 8 in units of 2^-64 (exact)
-        long long z[BN], zl[BN];
+        // zt: running sums over the K groups in units of 2^-52; per group and 16-column slice, z holds
+        // the digit sums d <= 6 (units 2^-52, exact) and zl d = 7, 8 (units 2^-64, exact), folded into
+        // zt with one rounding per group (at most half a unit each)
+        long long zt[BN];
 #pragma unroll
-        for (int j = 0; j < BN; ++j) { z[j] = 0; zl[j] = 0; }
+        for (int j = 0; j < BN; ++j) zt[j] = 0;
         bool acc_ok = true;
         for (int grp = 0; grp < ngroups; ++grp) {
             acc_ok = __all_sync(0xffffffffu, tc::mbar_wait(accf, (uint32_t)grp & 1u, p.err, tc::ERR_WAIT_ACC));
             tc::tc_fence_after();
             if (!acc_ok) break;
-#pragma unroll 1
-            for (int a = 0; a < nacc; ++a) {
-                uint32_t v[32];
-                tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * BN), v);
-                const int d = acc_digit_sum<INT_OUT>(a);
-                const int sh = d <= 6 ? 52 - 8 * d : 8 * (8 - d);
 #pragma unroll
-                for (int j = 0; j < BN; ++j) {
-                    const long long s = (long long)__float2int_rn(__uint_as_float(v[j]));  // exact, |s| <= 2^24
-                    if (d <= 6) z[j] += s << sh;
-                    else zl[j] += s << sh;
+            for (int qs = 0; qs < BN / 16; ++qs) {
+                long long z[16], zl[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) { z[j] = 0; zl[j] = 0; }
+#pragma unroll 1
+                for (int a = 0; a < nacc; ++a) {
+                    uint32_t v[16];
+                    tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * BN + qs * 16), v);
+                    const int d = acc_digit_sum<INT_OUT>(a);
+                    const int sh = d <= 6 ? 52 - 8 * d : 8 * (8 - d);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const long long sv = (long long)__float2int_rn(__uint_as_float(v[j]));  // exact, |sv| <= 2^24
+                        if (d <= 6) z[j] += sv << sh;
+                        else zl[j] += sv << sh;
+                    }
                 }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) zt[qs * 16 + j] += z[j] + ((zl[j] + 2048) >> 12);
             }
             if (grp + 1 < ngroups) {
                 tc::tc_fence_before();
@@ -243,9 +263,9 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
             const int zs = p.zshift;
 #pragma unroll
             for (int j = 0; j < BN; ++j) {
-                long long y = z[j] + ((zl[j] + 2048) >> 12);
+                long long y = zt[j];
                 if (zs > 0) y = (y + (1ll << (zs - 1))) >> zs;
-                out[(long long)(n0 + j) * p.R] = y;
+                if (n0 + j < p.N) out[(long long)(n0 + j) * p.R] = y;
             }
         }
     } else if (__all_sync(0xffffffffu, tc::mbar_wait(accf, 0, p.err, tc::ERR_WAIT_ACC))) {
@@ -337,6 +357,8 @@ __global__ void k_oz_col_exps(const double* Mat, double alpha, int K, int N, int
     if (lane == 0) me[n] = e;
 }
 
+// one exponent for the whole matrix, one above the largest column's: |alpha m / 2^e| < 1/2, so the
+// first digit, like every other, lies within [-128, 128] (the integer plan's accumulator bound)
 __global__ void k_oz_uniform_exp(int* me, int N) {
     __shared__ int red[256];
     int e = -1074;
@@ -347,7 +369,7 @@ __global__ void k_oz_uniform_exp(int* me, int N) {
         if ((int)threadIdx.x < s) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + s]);
         __syncthreads();
     }
-    for (int n = threadIdx.x; n < N; n += blockDim.x) me[n] = red[0];
+    for (int n = threadIdx.x; n < N; n += blockDim.x) me[n] = red[0] + 1;
 }
 
 __global__ void k_oz_split_cols(const double* Mat, double alpha, int K, int N, int nd, __nv_bfloat16* digits,
@@ -454,7 +476,10 @@ PFN_cuTensorMapEncodeTiled_v12000 encode() {
 
 sfde_status sfde_oz_split_matrix(const double* Mat, int K, int N, OzMatrix* out, cudaStream_t s, double alpha,
                                  bool uniform) {
-    if (K > (uniform ? 1024 : 256) || K % 32 || N % BN) return SFDE_EUNSUPPORTED;
+    // integer plan: tiles of 64 columns, a last tile of 32 reads zeros past N (N >= 64 keeps the
+    // box within the matrix)
+    const int BN = uniform ? Plan<true>::BN : Plan<false>::BN;
+    if (K > (uniform ? 1024 : 256) || K % 32 || N % 32 || N < BN) return SFDE_EUNSUPPORTED;
     // uniform scale: the integer-output product (7 digits); per-column scales: FP64 output (6)
     const int S = uniform ? Plan<true>::S : Plan<false>::S;
     out->K = K; out->N = N; out->nd = S;
@@ -472,7 +497,7 @@ sfde_status sfde_oz_split_matrix(const double* Mat, int K, int N, OzMatrix* out,
     if (!fn) return SFDE_EUNSUPPORTED;
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)N, (cuuint64_t)S};
     cuuint64_t strides[2] = {(cuuint64_t)K * 2, (cuuint64_t)N * K * 2};
-    cuuint32_t box[3] = {KC, BN, 1};
+    cuuint32_t box[3] = {(cuuint32_t)KC, (cuuint32_t)BN, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(&out->map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, out->digits, dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -514,7 +539,7 @@ sfde_status launch_oz(sfde_ctx* c, const CUtensorMap& mapX, const OzMatrix& M, c
                       int nr, int nc, int nout) {
     const long long mt = ((long long)a.batch * a.R + BM - 1) / BM;
     if (mt > 65535) return SFDE_EINVAL;
-    dim3 grid(M.N / BN, (unsigned)mt);
+    dim3 grid((M.N + Plan<INT_OUT>::BN - 1) / Plan<INT_OUT>::BN, (unsigned)mt);
     const int slot = sfde_prof_begin(c);
     k_ozaki_slice_gemm<INT_OUT><<<grid, OZ_THREADS, smem_bytes<INT_OUT>(), s>>>(mapX, M.map, a);
     // tensor work: the digit products of 2 R K N flops each; bytes: the digit planes of X in use,
@@ -547,18 +572,18 @@ sfde_status sfde_oz_gemm(sfde_ctx* c, const double* X, const double* X2, long lo
     return launch_oz<false>(c, mapX, M, a, c->stream, nr, nc, nout);
 }
 
-// |sum_k x_k m_k| <= K for |x|, |m| <= 1 (units 2^-52): beyond K = 256 the product is scaled down
-// by K/256 so that it keeps 3 bits of int64 headroom for the (1,4,1) stencils
+// |sum_k x_k m_k| <= K/4 for |x|, |m| <= 1/2 (units 2^-52): beyond K = 256 the product is scaled
+// down by K/256 so that it stays below 2^58, with headroom for the (1,4,1) stencils
 int sfde_oz_int_shift(int K) {
     int s = 0;
-    while ((KGROUP << s) < K) ++s;
+    while ((256 << s) < K) ++s;
     return s;
 }
 
 sfde_status sfde_oz_gemm_int(sfde_ctx* c, void* xdigits, long long plane, int R, int K, int batch,
                              const OzMatrix& M, long long* out, long long out_stride, int* err, int nr, int nc,
                              int nout, int nd) {
-    if (K != M.K || K > 1024 || (K > KGROUP && K % KGROUP) || R % 32 || (R > 128 && R % 128) ||
+    if (K != M.K || K > 1024 || (K > 256 && K % 256) || R % 32 || (R > 128 && R % 128) ||
         plane < (long long)batch * R * K || M.nd != Plan<true>::S || nd < 4 || nd > Plan<true>::S)
         return SFDE_EUNSUPPORTED;
     CUtensorMap mapX;

@@ -85,7 +85,7 @@ __device__ __forceinline__ void split7(long long x, uint16_t (&bf)[ND]) {
     for (int p = 1; p < ND; ++p) bf[p] = bf16_of_int((int)((unsigned long long)(xp >> (T - 8 * (p + 1))) & 255u) - 128);
 }
 
-// V = fix(U_{n-1}) + fix(U_n) for one 32 x 32 tile of pair b (n = n0 + b): the digits of 2V
+// V = fix(U_{n-1}) + fix(U_n) for one 32 x 32 tile of pair b (n = n0 + b): the digits of V
 // row-major [b][j][i] (rows of the A_x product) and transposed [b][i][j] (rows of the A_y product).
 __global__ void __launch_bounds__(256) k_split_pair(const double* __restrict__ U, const int* __restrict__ En, int n0,
                                                     int Px, int Py, uint16_t* __restrict__ dV, uint16_t* __restrict__ dVt,
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) k_split_pair(const double* __restrict__ U
         const int jj = ty + 8 * k;
         const size_t e = (size_t)(j0 + jj) * Px + i0 + tx;
         uint16_t bf[ND];
-        split7<56>(2 * (fixp(un[k], E) + fixp(um[k], E)), bf);     // |2V| <= 2^56, represented exactly
+        split7<56>(fixp(un[k], E) + fixp(um[k], E), bf);     // |V| <= 2^55: every digit within [-128, 128], exact
         const size_t o = (size_t)b * P2 + e;
 #pragma unroll
         for (int p = 0; p < ND; ++p)
@@ -155,10 +155,10 @@ __device__ __forceinline__ long long rshr(long long x, int k) {
     return (x + (1ll << (k - 1))) >> k;
 }
 
-// rho for one 32 x 32 tile of pair b.  Z1 = T1[b][i][j] counts 2^{E+ex-51+zsx} and Z2 = T3[b][j][i]
-// counts 2^{E+ey-51+zsy} (2V / 2^56 times the matrix over 2^e, in units of 2^{zs-52} with zs the
-// product's shift for its contraction length), fixed-point values count 2^{E-54}.  |Z| <= K 2^52 = 2^60, so (1,4,1) Z stays below 2^63, and both terms are halved
-// at least once before they are added.  Writes rho (BF16 or TF32-rounded FP32), zero
+// rho for one 32 x 32 tile of pair b.  Z1 = T1[b][i][j] counts 2^{E+ex-50+zsx} and Z2 = T3[b][j][i]
+// counts 2^{E+ey-50+zsy} (V / 2^56 times the matrix over 2^e, in units of 2^{zs-52} with zs the
+// product's shift for its contraction length), fixed-point values count 2^{E-54}.  |Z| <= 2^58, so
+// (1,4,1) Z stays below 2^61, and both terms are halved at least once before they are added.  Writes rho (BF16 or TF32-rounded FP32), zero
 // outside the interior nodes, and one FP64 sum of rho^2 per block.
 template <typename OT>
 __global__ void __launch_bounds__(256, 3) k_combine_int(
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(256, 3) k_combine_int(
             const int r = ty + 8 * k, c = tx + 32 * h;
             if (r < 34 && c < 34) du[r][c] = fixp(um[k][h], E) - fixp(un[k][h], E);   // fix(0) = 0
         }
-    const int u1 = E + ex - 51 + zsx, u2 = E + ey - 51 + zsy, u = max(u1, u2) + 1;
+    const int u1 = E + ex - 50 + zsx, u2 = E + ey - 50 + zsy, u = max(u1, u2) + 1;
     if (tx == 0 && ty == 0) {
         cst[0] = ldexp(cmass, E - 54);
         cst[1] = ldexp(-0.5 * dt[n - 1], u);
@@ -270,7 +270,9 @@ __global__ void __launch_bounds__(256, 3) k_combine_int(
 
 // contraction lengths up to 256, or multiples of 256 up to 1024 (the digit product's K groups)
 bool sfde_resid_int_supported(int Px, int Py) {
-    auto ok = [](int P) { return P <= 256 || (P <= 1024 && P % 256 == 0); };
+    // the digit products take tiles of 64 output columns (at least one whole tile) and sum K in
+    // groups of 128, up to 1024
+    auto ok = [](int P) { return P >= 64 && (P <= 256 || (P <= 1024 && P % 256 == 0)); };
     return ok(Px) && ok(Py);
 }
 
