@@ -65,6 +65,15 @@ sfde_status sfde_debug_set_residual_digits(sfde_ctx* ctx, int nd);
 sfde_status sfde_debug_set_fused_step(sfde_ctx* ctx, int enable);
 
 /*
+ * How the fused kernel spreads a slice over the GPU (P_x = P_y = 256): 0 one CTA per slice, 1
+ * (default) a cluster of two CTAs per slice -- each computing half the rows of every product and
+ * exchanging its half of each intermediate through distributed shared memory -- when twice the
+ * number of slices of a launch fits on the SMs, 2 always the pair.  The two forms give identical
+ * results.  Takes effect at the next mgrit_solve or debug step.
+ */
+sfde_status sfde_debug_set_fused_pair(sfde_ctx* ctx, int mode);
+
+/*
  * One batched low-precision step of the mixed-precision solver (ctx precision must be MIXED_BF16
  * or MIXED_TF32):  out[b] = Phi(U[b]) + g[b] - ut[b],  b = 0..batch-1, slice b stepped from
  * t_{n0+b-1} to t_{n0+b} (1 <= n0, n0 + batch - 1 <= N_t).

@@ -18,6 +18,15 @@
 // L2 in 64-wide K-atoms through a two-stage ring.  Per step HBM sees U read once and X written once
 // (plus g and u_target), and one launch does what four did.
 //
+// Pair form (P = 256): a cluster of two CTAs shares each slice.  CTA r computes rows
+// 128r..128r+127 of every product (its half of the fixed matrix streams through its ring; the
+// accumulator takes 256 TMEM columns), drains them into its own copy of the next Data operand and
+// sends that half to the peer's copy with one bulk shared::cluster copy per K-atom.  Each CTA first
+// multiplies the Data half it wrote itself, then the half the peer sent, so the exchange overlaps
+// half of the next product; every product and drain takes half the time of the one-CTA form.  The
+// products' completion is signalled to both CTAs (multicast commit), so no drain overwrites Data
+// the peer's products still read.
+//
 // Roles: warps 0-3 drain the accumulator (TMEM lanes 32w..32w+31 of every 128-row half); warp 4
 // issues TMA (lane 0) and prefetches g / u_target into L2 (all lanes); warp 5 issues the MMAs.
 // Every wait is bounded; on a timeout the kernel records the error, lets its own copies and
@@ -32,23 +41,30 @@ namespace {
 constexpr int THREADS = 192;
 constexpr int HALF_BYTES = 128 * 128;  // 128 rows x 128 bytes: one M-half of a K-atom
 
-template <int P> struct Geo {
+template <int P, bool PAIR> struct Geo {
     static constexpr int NH = P / 128;             // 128-row halves of M
+    static constexpr int NHL = PAIR ? 1 : NH;      // halves computed by this CTA
     static constexpr int NATOM = P / 64;           // K-atoms of 64 BF16
     static constexpr int ATOM = P * 128;           // bytes of one K-atom of a P-row operand
     static constexpr int DATA = NATOM * ATOM;      // the slice operand, P^2 BF16
-    static constexpr int RING = 2 * ATOM;
-    static constexpr int TMEM_COLS = NH * P;       // 128 or 512
+    // ring of fixed-matrix K-atoms: two whole atoms, or (pair) this CTA's half of all four, so that
+    // a phase's two passes over K load each atom once
+    static constexpr int OSTAGES = PAIR ? NATOM : 2;
+    static constexpr int OSTAGE = PAIR ? HALF_BYTES : ATOM;
+    static constexpr int RING = OSTAGES * OSTAGE;
+    static constexpr int TMEM_COLS = NHL * P;      // 128, 512, or 256 (pair)
     static constexpr int STAGE_ROW = P * 4;        // FP32 output staging: bytes per row
     static constexpr int SMEM = 1024 + DATA + RING + 128 + 2 * P * 4 + 64;
     static_assert(4 * 32 * STAGE_ROW <= DATA + RING, "output staging must fit in the operand space");
+    static_assert(!PAIR || P == 256, "pair form: two 128-row halves");
+    static_assert(2 * OSTAGES + 6 <= 16, "barrier block");
 };
 
 // byte offset of element (row r, column k) in a K-major, 128-byte-swizzled P-row operand:
 // K-atom k/64 is P rows x 128 bytes, rows in 1024-byte groups of 8, 16-byte chunks XOR (r % 8)
 template <int P>
 __device__ __forceinline__ uint32_t sw128(int r, int k) {
-    return (uint32_t)((k >> 6) * Geo<P>::ATOM + (r >> 3) * 1024 + (r & 7) * 128 +
+    return (uint32_t)((k >> 6) * (P * 128) + (r >> 3) * 1024 + (r & 7) * 128 +
                       ((((k & 63) >> 3) ^ (r & 7)) << 4) + ((k & 7) << 1));
 }
 
@@ -87,39 +103,42 @@ __device__ __forceinline__ void bf16x8_to_f32(const uint4& u, float (&f)[8]) {
     }
 }
 
-template <int P>
+template <int P, bool PAIR>
 __global__ void __launch_bounds__(THREADS, 1)
 k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ CUtensorMap mO1,
              const __grid_constant__ CUtensorMap mO2, const __grid_constant__ CUtensorMap mO3,
              const __grid_constant__ CUtensorMap mO4, FusedStepArgs p) {
-    using G = Geo<P>;
+    using G = Geo<P, PAIR>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sD = smem;                                  // slice operand (Data)
     uint8_t* sO = smem + G::DATA;                        // ring of fixed-matrix K-atoms (Op)
     uint64_t* bar = (uint64_t*)(sO + G::RING);
-    uint64_t* ofull = bar;                               // [2] Op atom landed
-    uint64_t* oempty = bar + 2;                          // [2] Op atom consumed
-    uint64_t* dfull = bar + 4;                           // U landed
-    uint64_t* dready = bar + 5;                          // the next Data written by the drain warps
-    uint64_t* accf = bar + 6;                            // a phase's products complete
-    uint64_t* fin = bar + 7;                             // error path: outstanding products complete
-    uint32_t* tmem_slot = (uint32_t*)(bar + 8);
+    uint64_t* ofull = bar;                               // [OSTAGES] Op atom landed
+    uint64_t* oempty = bar + G::OSTAGES;                 // [OSTAGES] Op atom consumed
+    uint64_t* dfull = bar + 2 * G::OSTAGES;              // U landed
+    uint64_t* dready = dfull + 1;                        // the next Data written by the drain warps
+    uint64_t* accf = dfull + 2;                          // a phase's products complete (pair: both CTAs')
+    uint64_t* fin = dfull + 3;                           // error path: outstanding products complete
+    uint64_t* rfull = dfull + 4;                         // pair: the peer's half of the next Data landed
+    uint32_t* tmem_slot = (uint32_t*)(dfull + 5);
     float* s_lx = (float*)(bar + 16);                    // K_x lambda_x[a], P floats
     float* s_ly = s_lx + P;                              // K_y lambda_y[q]
     double* red = (double*)(s_ly + P);                   // 4 partial sums
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int b = blockIdx.x;
+    const int rk = PAIR ? (int)tc::cluster_ctarank() : 0;   // pair: the 128-row half of this CTA
+    const int b = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
     const int nchain = p.nchain;
     const int nphase = 4 * nchain;                       // phases of all chained steps
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < 2; ++s) { tc::mbar_init(&ofull[s], 1); tc::mbar_init(&oempty[s], 1); }
+        for (int s = 0; s < G::OSTAGES; ++s) { tc::mbar_init(&ofull[s], 1); tc::mbar_init(&oempty[s], 1); }
         tc::mbar_init(dfull, 1);
         tc::mbar_init(dready, 128);
-        tc::mbar_init(accf, 1);
+        tc::mbar_init(accf, PAIR ? 2 : 1);
         tc::mbar_init(fin, 1);
+        tc::mbar_init(rfull, 1);
         tc::mbar_fence_init();
     }
     for (int i = threadIdx.x; i < P; i += THREADS) {
@@ -128,7 +147,9 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
     }
     if (threadIdx.x < 4) red[threadIdx.x] = 0.0;
     if (warp == 0) tc::tmem_alloc(tmem_slot, G::TMEM_COLS);
-    __syncthreads();
+    // pair: the peer's barriers are initialised before either CTA signals the other
+    if constexpr (PAIR) tc::cluster_sync();
+    else __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -160,46 +181,94 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
             bool ok = true;
             int issued = 0;
             for (int gi = 0; gi < nphase * G::NATOM && ok; ++gi) {
-                const int st = gi & 1;
-                if (gi >= 2) ok = tc::mbar_wait(&oempty[st], (uint32_t)((gi >> 1) - 1) & 1u, p.err, tc::ERR_WAIT_EMPTY);
+                const int st = gi % G::OSTAGES, use = gi / G::OSTAGES;
+                if (gi >= G::OSTAGES) ok = tc::mbar_wait(&oempty[st], (uint32_t)(use - 1) & 1u, p.err, tc::ERR_WAIT_EMPTY);
                 if (!ok) break;
-                tc::mbar_arrive_expect_tx(&ofull[st], (uint32_t)G::ATOM);
-                tc::tma_load_2d(sO + st * G::ATOM, maps[(gi / G::NATOM) & 3], &ofull[st], (gi % G::NATOM) * 64, 0);
+                tc::mbar_arrive_expect_tx(&ofull[st], (uint32_t)G::OSTAGE);
+                // pair: rows 128 rk.. of the matrix (a map with 128-row boxes)
+                tc::tma_load_2d(sO + st * G::OSTAGE, maps[(gi / G::NATOM) & 3], &ofull[st], (gi % G::NATOM) * 64,
+                                PAIR ? 128 * rk : 0);
                 ++issued;
             }
             // own copies in flight must land before the CTA's shared memory goes away
             tc::mbar_wait(dfull, 0, p.err, tc::ERR_WAIT_FULL);
-            for (int gi = issued - 2 < 0 ? 0 : issued - 2; gi < issued; ++gi)
-                tc::mbar_wait(&ofull[gi & 1], (uint32_t)(gi >> 1) & 1u, p.err, tc::ERR_WAIT_FULL);
+            for (int gi = issued - G::OSTAGES < 0 ? 0 : issued - G::OSTAGES; gi < issued; ++gi)
+                tc::mbar_wait(&ofull[gi % G::OSTAGES], (uint32_t)(gi / G::OSTAGES) & 1u, p.err, tc::ERR_WAIT_FULL);
         }
     } else if (warp == 5) {
         if (lane == 0) {
-            const uint32_t idesc = tc::idesc_f32acc(1u, 128, P);
             bool ok = tc::mbar_wait(dfull, 0, p.err, tc::ERR_WAIT_FULL);
             bool any = false;
-            for (int ph = 0; ph < nphase && ok; ++ph) {
-                // the Data of phase ph > 0 is written by the drain of phase ph - 1
-                if (ph > 0) ok = tc::mbar_wait(dready, (uint32_t)(ph - 1) & 1u, p.err, tc::ERR_WAIT_FULL);
-                if (!ok) break;
-                tc::tc_fence_after();
-                for (int t = 0; t < G::NATOM && ok; ++t) {
-                    const int gi = ph * G::NATOM + t, st = gi & 1;
-                    ok = tc::mbar_wait(&ofull[st], (uint32_t)(gi >> 1) & 1u, p.err, tc::ERR_WAIT_FULL);
+            if constexpr (!PAIR) {
+                const uint32_t idesc = tc::idesc_f32acc(1u, 128, P);
+                for (int ph = 0; ph < nphase && ok; ++ph) {
+                    // the Data of phase ph > 0 is written by the drain of phase ph - 1
+                    if (ph > 0) ok = tc::mbar_wait(dready, (uint32_t)(ph - 1) & 1u, p.err, tc::ERR_WAIT_FULL);
                     if (!ok) break;
                     tc::tc_fence_after();
+                    for (int t = 0; t < G::NATOM && ok; ++t) {
+                        const int gi = ph * G::NATOM + t, st = gi & 1;
+                        ok = tc::mbar_wait(&ofull[st], (uint32_t)(gi >> 1) & 1u, p.err, tc::ERR_WAIT_FULL);
+                        if (!ok) break;
+                        tc::tc_fence_after();
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t bd = tc::smem_desc_sw128(sD + t * G::ATOM + kk * 32);
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t bd = tc::smem_desc_sw128(sD + t * G::ATOM + kk * 32);
 #pragma unroll
-                        for (int h = 0; h < G::NH; ++h) {
-                            const uint64_t ad = tc::smem_desc_sw128(sO + st * G::ATOM + h * HALF_BYTES + kk * 32);
-                            tc::mma<0>(tmem + (uint32_t)(h * P), ad, bd, idesc, (t > 0 || kk > 0) ? 1u : 0u);
+                            for (int h = 0; h < G::NH; ++h) {
+                                const uint64_t ad = tc::smem_desc_sw128(sO + st * G::ATOM + h * HALF_BYTES + kk * 32);
+                                tc::mma<0>(tmem + (uint32_t)(h * P), ad, bd, idesc, (t > 0 || kk > 0) ? 1u : 0u);
+                            }
+                        }
+                        any = true;
+                        tc::mma_commit(&oempty[st]);
+                    }
+                    if (ok) tc::mma_commit(accf);
+                }
+            } else {
+                // rows 128 rk.. of D = Op Data^T in two passes over K: output columns (Data rows) of
+                // this CTA's half, written by its own drain, then those of the peer's half, sent by
+                // the peer.  Accumulator columns n = Data row n (256 columns).
+                const uint32_t idesc = tc::idesc_f32acc(1u, 128, 128);
+                // rfull phase i brings the peer's half of the Data of product i + 1; `armed`: the
+                // expectation of the phase that has not been waited for yet
+                bool armed = false;
+                if (nphase > 1) { tc::mbar_arrive_expect_tx(rfull, (uint32_t)(G::DATA / 2)); armed = true; }
+                int rphase = 0;
+                for (int ph = 0; ph < nphase && ok; ++ph) {
+                    if (ph > 0) ok = tc::mbar_wait(dready, (uint32_t)(ph - 1) & 1u, p.err, tc::ERR_WAIT_FULL);
+                    if (!ok) break;
+                    tc::tc_fence_after();
+                    for (int pass = 0; pass < 2 && ok; ++pass) {
+                        const int hn = pass == 0 ? rk : 1 - rk;     // Data rows 128 hn..
+                        if (pass == 1 && ph > 0) {
+                            ok = tc::mbar_wait(rfull, (uint32_t)rphase & 1u, p.err, tc::ERR_WAIT_FULL);
+                            if (!ok) break;
+                            armed = false;
+                            ++rphase;
+                            tc::tc_fence_after();
+                            if (ph + 1 < nphase) { tc::mbar_arrive_expect_tx(rfull, (uint32_t)(G::DATA / 2)); armed = true; }
+                        }
+                        for (int t = 0; t < G::NATOM && ok; ++t) {
+                            if (pass == 0) {
+                                ok = tc::mbar_wait(&ofull[t], (uint32_t)ph & 1u, p.err, tc::ERR_WAIT_FULL);
+                                if (!ok) break;
+                                tc::tc_fence_after();
+                            }
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint64_t ad = tc::smem_desc_sw128(sO + t * G::OSTAGE + kk * 32);
+                                const uint64_t bd = tc::smem_desc_sw128(sD + t * G::ATOM + hn * HALF_BYTES + kk * 32);
+                                tc::mma<0>(tmem + (uint32_t)(hn * 128), ad, bd, idesc, (t > 0 || kk > 0) ? 1u : 0u);
+                            }
+                            any = true;
+                            if (pass == 1) tc::mma_commit(&oempty[t]);
                         }
                     }
-                    any = true;
-                    tc::mma_commit(&oempty[st]);
+                    if (ok) tc::mma_commit_mc(accf, (uint16_t)3u);
                 }
-                if (ok) tc::mma_commit(accf);
+                // error path: a copy the peer may still send must land before shared memory goes away
+                if (!ok && armed) tc::mbar_wait(rfull, (uint32_t)rphase & 1u, p.err, tc::ERR_WAIT_FULL);
             }
             if (!ok && any) {  // products still running must finish before TMEM is freed
                 tc::mma_commit(fin);
@@ -225,8 +294,9 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
             // 2/d - 1 = (1 - tau sigma)/(1 + tau sigma) for Crank-Nicolson
             const float dtb = (float)p.dt[p.n0 + b * p.dn - 1 + k];
             const float cst = p.scheme == SCHEME_BE ? dtb : 0.5f * dtb;
-            for (int h = 0; h < G::NH; ++h) {
-                const int row = h * 128 + warp * 32 + lane;  // M index held by this thread
+            for (int h = 0; h < G::NHL; ++h) {
+                const int hh = PAIR ? rk : h;                 // 128-row half of M
+                const int row = hh * 128 + warp * 32 + lane;  // M index held by this thread
                 const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * P);
                 if (ph < 3) {
                     const float Bq = fmaf(cst, s_ly[row], 1.f);
@@ -295,7 +365,7 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                     constexpr int ITER = CPR;               // 32 rows x CPR chunks over 32 lanes
                     constexpr int UNR = 8;
                     __nv_bfloat16* __restrict__ dst = dst0 + (long long)k * p.dst_kstride;
-                    const int rbase = h * 128 + warp * 32;
+                    const int rbase = hh * 128 + warp * 32;
                     const bool want_sq = ut && p.partial;
                     float sqf = 0.f;   // FP32 over this lane's 8 x ITER values (the FP64 pipe is ~1/64 rate)
                     for (int i0 = 0; i0 < ITER; i0 += UNR) {
@@ -339,15 +409,29 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 tc::tc_fence_before();
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(dready)) : "memory");
+                if constexpr (PAIR) {
+                    // this CTA's half of the next Data (rows 128 rk.., 16 KB in each K-atom) to the
+                    // same place in the peer's copy, once all four drain warps have written it (the
+                    // arrivals above; a bounded wait, not a barrier a timed-out warp could miss)
+                    if (threadIdx.x == 0 && tc::mbar_wait(dready, (uint32_t)gph & 1u, p.err, tc::ERR_WAIT_FULL)) {
+                        const uint32_t peer = (uint32_t)(1 - rk);
+                        const uint32_t rbar = tc::mapa_shared(tc::smem_u32(rfull), peer);
+#pragma unroll
+                        for (int t = 0; t < G::NATOM; ++t) {
+                            const uint32_t src = sD_u + (uint32_t)(t * G::ATOM + rk * HALF_BYTES);
+                            tc::bulk_copy_to_cluster(tc::mapa_shared(src, peer), src, (uint32_t)HALF_BYTES, rbar);
+                        }
+                    }
+                }
             }
             if (ph == 3 && !last) {
                 // while the next step's first product runs: copy this warp's rows of the new Data
                 // (exactly this step's BF16 output) to global memory, one row per warp instruction,
                 // and bring the right-hand side two steps ahead into L2
                 __nv_bfloat16* __restrict__ dst = dst0 + (long long)k * p.dst_kstride;
-                for (int h = 0; h < G::NH; ++h)
+                for (int h = 0; h < G::NHL; ++h)
                     for (int r = 0; r < 32; ++r) {
-                        const int row = h * 128 + warp * 32 + r;
+                        const int row = (PAIR ? rk : h) * 128 + warp * 32 + r;
                         for (int c = lane; c < P / 8; c += 32) {
                             uint4 o;
                             asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
@@ -366,19 +450,48 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
         if (lane == 0) red[warp] = sq;
     }
     tc::tc_fence_before();
-    __syncthreads();
-    if (p.partial && threadIdx.x == 0) p.partial[b] = red[0] + red[1] + red[2] + red[3];
+    if constexpr (PAIR) {
+        // both CTAs' partial sums are final; CTA 0 adds the peer's, which stays valid until the
+        // second barrier
+        tc::cluster_sync();
+        if (p.partial && threadIdx.x == 0 && rk == 0) {
+            double sp = red[0] + red[1] + red[2] + red[3];
+            const uint32_t pr = tc::mapa_shared(tc::smem_u32(red), 1u);
+            for (int w = 0; w < 4; ++w) sp += tc::ld_cluster_f64(pr + 8u * (uint32_t)w);
+            p.partial[b] = sp;
+        }
+        tc::cluster_sync();
+    } else {
+        __syncthreads();
+        if (p.partial && threadIdx.x == 0) p.partial[b] = red[0] + red[1] + red[2] + red[3];
+    }
     if (warp == 0) {
         tc::tc_fence_after();
         tc::tmem_dealloc(tmem, G::TMEM_COLS);
     }
 }
 
-template <int P>
+template <int P, bool PAIR>
 sfde_status launch(sfde_ctx* c, const CUtensorMap& U, const CUtensorMap& O1, const CUtensorMap& O2,
                    const CUtensorMap& O3, const CUtensorMap& O4, const FusedStepArgs& a, cudaStream_t s) {
     const int slot = c ? sfde_prof_begin(c) : -1;
-    k_fused_step<P><<<a.batch, THREADS, Geo<P>::SMEM, s>>>(U, O1, O2, O3, O4, a);
+    if constexpr (PAIR) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)(2 * a.batch));
+        cfg.blockDim = dim3(THREADS);
+        cfg.dynamicSmemBytes = Geo<P, PAIR>::SMEM;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        SFDE_CUDA(cudaLaunchKernelEx(&cfg, k_fused_step<P, PAIR>, U, O1, O2, O3, O4, a));
+    } else {
+        k_fused_step<P, PAIR><<<a.batch, THREADS, Geo<P, PAIR>::SMEM, s>>>(U, O1, O2, O3, O4, a);
+    }
     if (c) {
         // per slice: the input once, the output and right-hand side of every chained step
         const double nb = a.batch, nx = c->x.n, ny = c->y.n, nk = a.nchain;
@@ -396,19 +509,27 @@ sfde_status launch(sfde_ctx* c, const CUtensorMap& U, const CUtensorMap& O1, con
 bool sfde_fused_supported(int kind, int Px, int Py) { return kind == 0 && Px == Py && (Px == 128 || Px == 256); }
 
 sfde_status sfde_fused_prepare() {
-    SFDE_CUDA(cudaFuncSetAttribute(k_fused_step<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<128>::SMEM));
-    SFDE_CUDA(cudaFuncSetAttribute(k_fused_step<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<256>::SMEM));
+    SFDE_CUDA(cudaFuncSetAttribute(k_fused_step<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   Geo<128, false>::SMEM));
+    SFDE_CUDA(cudaFuncSetAttribute(k_fused_step<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   Geo<256, false>::SMEM));
+    SFDE_CUDA(cudaFuncSetAttribute(k_fused_step<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   Geo<256, true>::SMEM));
     return SFDE_OK;
 }
 
-sfde_status sfde_fused_step(sfde_ctx* c, int P, const CUtensorMap& U, const CUtensorMap& O1, const CUtensorMap& O2,
-                            const CUtensorMap& O3, const CUtensorMap& O4, const FusedStepArgs& a, cudaStream_t s) {
+bool sfde_fused_pair_supported(int P) { return P == 256; }
+
+sfde_status sfde_fused_step(sfde_ctx* c, int P, bool pair, const CUtensorMap& U, const CUtensorMap& O1,
+                            const CUtensorMap& O2, const CUtensorMap& O3, const CUtensorMap& O4, const FusedStepArgs& a,
+                            cudaStream_t s) {
     if (a.batch < 1) return SFDE_OK;
     if (!a.dst || !a.dt || !a.lamx || !a.lamy || !a.err || a.nchain < 1 || (a.ut && a.nchain != 1) ||
         a.batch > 65535 * 1024)
         return SFDE_EINVAL;
     if (((uintptr_t)a.dst | (uintptr_t)a.g | (uintptr_t)a.ut) & 15) return SFDE_EINVAL;
-    if (P == 128) return launch<128>(c, U, O1, O2, O3, O4, a, s);
-    if (P == 256) return launch<256>(c, U, O1, O2, O3, O4, a, s);
+    if (pair && P != 256) return SFDE_EINVAL;
+    if (P == 128) return launch<128, false>(c, U, O1, O2, O3, O4, a, s);
+    if (P == 256) return pair ? launch<256, true>(c, U, O1, O2, O3, O4, a, s) : launch<256, false>(c, U, O1, O2, O3, O4, a, s);
     return SFDE_EINVAL;
 }

@@ -251,12 +251,17 @@ sfde_status sfde_tc_map_slices(CUtensorMap* map, const void* base, int esz, int 
 }
 
 sfde_status sfde_tc_map_matrix(CUtensorMap* map, const void* matT, int esz, int K, int N) {
+    return sfde_tc_map_matrix_rows(map, matT, esz, K, N, sfde_tc_tile_n(N));
+}
+
+sfde_status sfde_tc_map_matrix_rows(CUtensorMap* map, const void* matT, int esz, int K, int N, int rows) {
+    if (rows < 1 || rows > 256) return SFDE_EINVAL;
     auto fn = encode_fn();
     if (!fn) return SFDE_EUNSUPPORTED;
     const CUtensorMapDataType dt = esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)N};
     cuuint64_t strides[1] = {(cuuint64_t)K * esz};
-    cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)sfde_tc_tile_n(N)};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, dt, 2, const_cast<void*>(matT), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

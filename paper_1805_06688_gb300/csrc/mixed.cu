@@ -95,6 +95,10 @@ struct SfdeMixed {
     void *WTx = nullptr, *WTy = nullptr, *Vx = nullptr, *Vy = nullptr, *VTx = nullptr, *VTy = nullptr;
     float *lamx = nullptr, *lamy = nullptr;
     CUtensorMap mWTx, mWTy, mVx, mVy, mVTx, mVTy;
+    // the same matrices in 128-row boxes: the pair form of the fused step (P = 256)
+    bool pair_ok = false;
+    int nsm = 0;
+    CUtensorMap hWTx, hWTy, hVx, hVy, hVTx, hVTy;
     std::vector<LpLevel> lev;
     void *T1 = nullptr, *T2 = nullptr, *T3 = nullptr;
     size_t ws = 0;
@@ -189,6 +193,20 @@ sfde_status setup_mixed(sfde_ctx* c, int kind, int m, int max_levels, int min_co
     SFDE_TRY(sfde_tc_map_matrix(&M->mVy, M->Vy, M->esz, Py, Py));
     SFDE_TRY(sfde_tc_map_matrix(&M->mVTx, M->VTx, M->esz, Px, Px));
     SFDE_TRY(sfde_tc_map_matrix(&M->mVTy, M->VTy, M->esz, Py, Py));
+    M->pair_ok = kind == 0 && Px == Py && sfde_fused_pair_supported(Px);
+    if (M->pair_ok) {
+        SFDE_TRY(sfde_tc_map_matrix_rows(&M->hWTx, M->WTx, M->esz, Px, Px, 128));
+        SFDE_TRY(sfde_tc_map_matrix_rows(&M->hWTy, M->WTy, M->esz, Py, Py, 128));
+        SFDE_TRY(sfde_tc_map_matrix_rows(&M->hVx, M->Vx, M->esz, Px, Px, 128));
+        SFDE_TRY(sfde_tc_map_matrix_rows(&M->hVy, M->Vy, M->esz, Py, Py, 128));
+        SFDE_TRY(sfde_tc_map_matrix_rows(&M->hVTx, M->VTx, M->esz, Px, Px, 128));
+        SFDE_TRY(sfde_tc_map_matrix_rows(&M->hVTy, M->VTy, M->esz, Py, Py, 128));
+    }
+    {
+        int dev = 0;
+        SFDE_CUDA(cudaGetDevice(&dev));
+        SFDE_CUDA(cudaDeviceGetAttribute(&M->nsm, cudaDevAttrMultiProcessorCount, dev));
+    }
     SFDE_CUDA(cudaMalloc(&M->err, sizeof(int)));
     SFDE_CUDA(cudaMemsetAsync(M->err, 0, sizeof(int), c->stream));
     // inner hierarchy
@@ -270,8 +288,14 @@ struct LpEngine {
             a.lamx = M->lamx; a.lamy = M->lamy; a.kx = (float)c->kx; a.ky = (float)c->ky;
             a.dt = dt; a.n0 = n0; a.dn = dn; a.scheme = solve ? SCHEME_SOLVE : sch;
             a.err = M->err;
-            SFDE_TRY(sfde_fused_step(c, Px, a1, solve ? M->mVTx : M->mWTx, solve ? M->mVTy : M->mWTy, M->mVx,
-                                     M->mVy, a, c->stream));
+            // two CTAs per slice where the slices leave SMs idle (or when forced)
+            const bool pair = M->pair_ok && (c->fused_pair == 2 || (c->fused_pair == 1 && 2 * batch <= M->nsm));
+            if (pair)
+                SFDE_TRY(sfde_fused_step(c, Px, true, a1, solve ? M->hVTx : M->hWTx, solve ? M->hVTy : M->hWTy,
+                                         M->hVx, M->hVy, a, c->stream));
+            else
+                SFDE_TRY(sfde_fused_step(c, Px, false, a1, solve ? M->mVTx : M->mWTx, solve ? M->mVTy : M->mWTy,
+                                         M->mVx, M->mVy, a, c->stream));
             steps += (long long)batch * nchain;
             if (npart) *npart = batch;
             return SFDE_OK;
@@ -488,7 +512,8 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
     const int K = o->inner_cycles > 0 ? o->inner_cycles : (kind == 0 ? 4 : 5);
     // the inner solve is captured once as CUDA graphs and replayed; eager while kernels are timed
     const bool use_graph = !c->prof.on;
-    const long long key = ((long long)M->fused << 20) | ((long long)E.scheme << 4) | (long long)o->relax;
+    const long long key = ((long long)c->fused_pair << 24) | ((long long)M->fused << 20) |
+                          ((long long)E.scheme << 4) | (long long)o->relax;
     long long graph_steps = 0;
 
     mgrit_stats S{};
@@ -626,6 +651,12 @@ extern "C" sfde_status sfde_debug_set_residual_digits(sfde_ctx* c, int nd) {
 extern "C" sfde_status sfde_debug_set_fused_step(sfde_ctx* c, int enable) {
     if (!c) return SFDE_EINVAL;
     c->fused_step = enable ? 1 : 0;
+    return SFDE_OK;
+}
+
+extern "C" sfde_status sfde_debug_set_fused_pair(sfde_ctx* c, int mode) {
+    if (!c || mode < 0 || mode > 2) return SFDE_EINVAL;
+    c->fused_pair = mode;
     return SFDE_OK;
 }
 

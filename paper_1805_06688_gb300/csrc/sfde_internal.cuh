@@ -103,6 +103,7 @@ struct sfde_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     struct SfdeMixed* mixed = nullptr;  // tensor-core operands and inner hierarchy (mixed.cu)
     int fused_step = 1;         // BF16 steps as one fused kernel where the padded sizes allow it
+    int fused_pair = 1;         // fused steps on two CTAs per slice: 0 never, 1 when 2 batch <= SMs, 2 always
     int resid_digits = 0;       // digits of the tensor-core residual: 0 per iteration, else 4..7 fixed
     SfdeProf prof;
     size_t P2() const { return (size_t)x.P * (size_t)y.P; }
@@ -161,6 +162,8 @@ int sfde_tc_tile_n(int cout);
 sfde_status sfde_tc_prepare();
 sfde_status sfde_tc_map_slices(CUtensorMap* map, const void* base, int esz, int K, int R, int ds, long long nslices);
 sfde_status sfde_tc_map_matrix(CUtensorMap* map, const void* matT, int esz, int K, int N);
+// as sfde_tc_map_matrix with boxes of `rows` rows (<= 256)
+sfde_status sfde_tc_map_matrix_rows(CUtensorMap* map, const void* matT, int esz, int K, int N, int rows);
 // c may be NULL (no accounting); nr, nc, nout: unpadded extents of one slice product
 sfde_status sfde_tc_gemm(sfde_ctx* c, int kind, int epi, const CUtensorMap& A, const CUtensorMap& B, const TcArgs& p,
                          cudaStream_t s, int nr = 0, int nc = 0, int nout = 0);
@@ -188,9 +191,12 @@ inline int sfde_mixed_kind(const sfde_ctx* c) {
     return (sfde_fused_supported(0, c->x.P, c->y.P) && c->nt <= 1024) ? 0 : 1;
 }
 sfde_status sfde_fused_prepare();
-// O1, O2: W_x^T, W_y^T (V_x^T, V_y^T for the solve); O3, O4: V_x, V_y -- K-major P x P BF16 maps.
-sfde_status sfde_fused_step(sfde_ctx* c, int P, const CUtensorMap& U, const CUtensorMap& O1, const CUtensorMap& O2,
-                            const CUtensorMap& O3, const CUtensorMap& O4, const FusedStepArgs& a, cudaStream_t s);
+// O1, O2: W_x^T, W_y^T (V_x^T, V_y^T for the solve); O3, O4: V_x, V_y -- K-major P x P BF16 maps
+// with boxes of 64 x P (one CTA per slice) or 64 x 128 (pair: two CTAs per slice, P = 256).
+bool sfde_fused_pair_supported(int P);
+sfde_status sfde_fused_step(sfde_ctx* c, int P, bool pair, const CUtensorMap& U, const CUtensorMap& O1,
+                            const CUtensorMap& O2, const CUtensorMap& O3, const CUtensorMap& O4, const FusedStepArgs& a,
+                            cudaStream_t s);
 
 // ---- FP64-accurate slice GEMM on the BF16 tensor cores (ozaki.cu)
 #define SFDE_OZ_DIGITS 6

@@ -204,3 +204,62 @@ def test_chained_steps(scheme, nx, ny, batch, nchain):
                 assert rel <= 5 * u * (k + 1), (b, k, rel)
         d = np.sqrt(np.sum((x1[b, 0] - x0[b, 0]) ** 2) / np.sum(x0[b, 0] ** 2))
         assert d <= u / 2, (b, d)
+
+
+def set_pair(P, mode):
+    L = sfde.lib()
+    L.sfde_debug_set_fused_pair.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert L.sfde_debug_set_fused_pair(P.ctx, mode) == 0
+
+
+@pytest.mark.parametrize("nx,ny,batch,nchain", [(255, 255, 3, 1), (230, 200, 2, 7), (255, 240, 90, 2)])
+def test_pair_form_equals_one_cta(nx, ny, batch, nchain):
+    """Two CTAs per slice (each computing half the rows of every product, the halves exchanged
+    through distributed shared memory) round exactly the same sums as one CTA per slice: the
+    accumulation order of every output element is the same, so the results are identical, for the
+    three step kinds, with right-hand side and target, and along chains."""
+    n0 = 1
+    nt = n0 + batch * nchain + 1
+    t = time_grid(nt, 1.0, "graded")
+    P = sfde.Problem(0.65, 0.85, 1.3, 0.4, nx, ny, t, precision=sfde.PREC_MIXED_BF16)
+    rng = np.random.default_rng(nx + ny + batch)
+    U = rng.standard_normal((batch, ny, nx))
+    g = 0.2 * rng.standard_normal((batch, nchain, ny, nx))
+    res = {}
+    for mode in (0, 2):
+        set_pair(P, mode)
+        out = []
+        if nchain == 1:
+            for scheme in (0, 1, 2):
+                st, x, _ = lp_step(P, 1, scheme, U, n0)
+                assert st == 0, sfde.sfde_strerror(st)
+                out.append(x)
+            st, x, n2 = lp_step(P, 1, 0, U, n0, g[:, 0], 0.5 * U)
+            assert st == 0, sfde.sfde_strerror(st)
+            out += [x, np.array([n2])]
+        else:
+            for scheme in (0, 1):
+                st, x = lp_chain(P, 1, scheme, U, nchain, n0, g)
+                assert st == 0, sfde.sfde_strerror(st)
+                out.append(x)
+        res[mode] = out
+    for a, b in zip(res[0], res[2]):
+        assert np.array_equal(a, b), np.abs(a - b).max()
+
+
+def test_mixed_bf16_solve_pair_form():
+    """A whole mixed-precision solve at P = 256 with every fused step on two CTAs per slice reaches
+    the FP64 answer, as with one CTA per slice."""
+    nx, ny, nt = 255, 255, 64
+    t = time_grid(nt, 1.0, "uniform")
+    psi = sine_mode_nodal(sine_mode_amplitudes(4), nx, ny)
+    O = osfde.SFDE(0.6, 0.9, 1.0, 0.5, nx, ny, t)
+    ref = osfde.seq_timestep(O, psi)
+    for mode in (2, 0):
+        P = sfde.Problem(0.6, 0.9, 1.0, 0.5, nx, ny, t, precision=sfde.PREC_MIXED_BF16)
+        P.set_initial(psi)
+        set_pair(P, mode)
+        U = np.zeros((nt + 1, ny, nx))
+        _, stats = P.mgrit(U=U, m=8, max_levels=4, coarse=sfde.COARSE_BE, rel_tol=1e-10, max_iter=60)
+        assert stats.converged
+        assert np.abs(U - ref).max() <= 1e-8 * np.abs(ref).max(), mode
