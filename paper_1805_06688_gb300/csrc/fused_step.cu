@@ -27,8 +27,10 @@
 // products' completion is signalled to both CTAs (multicast commit), so no drain overwrites Data
 // the peer's products still read.
 //
-// Roles: warps 0-3 drain the accumulator (TMEM lanes 32w..32w+31 of every 128-row half); warp 4
-// issues TMA (lane 0) and prefetches g / u_target into L2 (all lanes); warp 5 issues the MMAs.
+// Roles: warps 0-7 drain the accumulator (warp w: TMEM lanes 32 (w % 4).. of every 128-row half,
+// one half of the columns; two drain warps per scheduler keep the drain from stalling on latency);
+// warp 8 issues TMA (lane 0) and prefetches g / u_target into L2 (all lanes); warp 9 issues the
+// MMAs.
 // Every wait is bounded; on a timeout the kernel records the error, lets its own copies and
 // products finish (bounded), frees TMEM and returns.
 #include <cuda_bf16.h>
@@ -38,7 +40,8 @@
 
 namespace {
 
-constexpr int THREADS = 192;
+constexpr int NDRAIN = 8;                       // drain warps 0-7; warp 8 TMA, warp 9 MMA
+constexpr int THREADS = 32 * (NDRAIN + 2);
 constexpr int HALF_BYTES = 128 * 128;  // 128 rows x 128 bytes: one M-half of a K-atom
 
 template <int P, bool PAIR> struct Geo {
@@ -53,9 +56,9 @@ template <int P, bool PAIR> struct Geo {
     static constexpr int OSTAGE = PAIR ? HALF_BYTES : ATOM;
     static constexpr int RING = OSTAGES * OSTAGE;
     static constexpr int TMEM_COLS = NHL * P;      // 128, 512, or 256 (pair)
-    static constexpr int STAGE_ROW = P * 4;        // FP32 output staging: bytes per row
-    static constexpr int SMEM = 1024 + DATA + RING + 128 + 2 * P * 4 + 64;
-    static_assert(4 * 32 * STAGE_ROW <= DATA + RING, "output staging must fit in the operand space");
+    static constexpr int STAGE_ROW = P / 2 * 4;    // FP32 output staging: bytes per half-row
+    static constexpr int SMEM = 1024 + DATA + RING + 128 + 2 * P * 4 + 128;
+    static_assert(NDRAIN * 32 * STAGE_ROW <= DATA + RING, "output staging must fit in the operand space");
     static_assert(!PAIR || P == 256, "pair form: two 128-row halves");
     static_assert(2 * OSTAGES + 6 <= 16, "barrier block");
 };
@@ -124,7 +127,7 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
     uint32_t* tmem_slot = (uint32_t*)(dfull + 5);
     float* s_lx = (float*)(bar + 16);                    // K_x lambda_x[a], P floats
     float* s_ly = s_lx + P;                              // K_y lambda_y[q]
-    double* red = (double*)(s_ly + P);                   // 4 partial sums
+    double* red = (double*)(s_ly + P);                   // NDRAIN partial sums
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rk = PAIR ? (int)tc::cluster_ctarank() : 0;   // pair: the 128-row half of this CTA
@@ -135,7 +138,7 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
     if (threadIdx.x == 0) {
         for (int s = 0; s < G::OSTAGES; ++s) { tc::mbar_init(&ofull[s], 1); tc::mbar_init(&oempty[s], 1); }
         tc::mbar_init(dfull, 1);
-        tc::mbar_init(dready, 128);
+        tc::mbar_init(dready, 32 * NDRAIN);
         tc::mbar_init(accf, PAIR ? 2 : 1);
         tc::mbar_init(fin, 1);
         tc::mbar_init(rfull, 1);
@@ -145,7 +148,7 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
         s_lx[i] = p.kx * p.lamx[i];
         s_ly[i] = p.ky * p.lamy[i];
     }
-    if (threadIdx.x < 4) red[threadIdx.x] = 0.0;
+    if (threadIdx.x < NDRAIN) red[threadIdx.x] = 0.0;
     if (warp == 0) tc::tmem_alloc(tmem_slot, G::TMEM_COLS);
     // pair: the peer's barriers are initialised before either CTA signals the other
     if constexpr (PAIR) tc::cluster_sync();
@@ -158,7 +161,7 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
     const __nv_bfloat16* __restrict__ ut = p.ut ? (const __nv_bfloat16*)p.ut + (long long)b * p.ut_stride : nullptr;
     __nv_bfloat16* __restrict__ dst0 = (__nv_bfloat16*)p.dst + (long long)b * p.dst_stride;
 
-    if (warp == 4) {
+    if (warp == NDRAIN) {
         const int s = p.s0 + b * p.ds;
         if (lane == 0) {
             tc::prefetch_tmap(&mapU);
@@ -195,7 +198,7 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
             for (int gi = issued - G::OSTAGES < 0 ? 0 : issued - G::OSTAGES; gi < issued; ++gi)
                 tc::mbar_wait(&ofull[gi % G::OSTAGES], (uint32_t)(gi / G::OSTAGES) & 1u, p.err, tc::ERR_WAIT_FULL);
         }
-    } else if (warp == 5) {
+    } else if (warp == NDRAIN + 1) {
         if (lane == 0) {
             bool ok = tc::mbar_wait(dfull, 0, p.err, tc::ERR_WAIT_FULL);
             bool any = false;
@@ -276,19 +279,33 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
             }
         }
     } else {
-        // ---- warps 0-3: accumulator -> next Data operand (phases 1-3 of a step, and phase 4 of a
-        // step followed by another) or output (phase 4 of the last step)
+        // ---- warps 0-7: accumulator -> next Data operand (phases 1-3 of a step, and phase 4 of a
+        // step followed by another) or output (phase 4 of the last step).  Warp w reads TMEM lanes
+        // 32 (w % 4).. (the lanes its warp index may access) and columns cb.. cb + CW - 1 of them.
+        constexpr int CW = P / 2;                         // accumulator columns per drain warp
+        const int lq = warp & 3, cb = (warp >> 2) * CW;
         const bool cn = p.scheme == SCHEME_CN;
         double sq = 0.0;
         bool ok = true;
         const uint32_t sD_u = tc::smem_u32(sD);
+        // accumulator columns are read 32 at a time (the register budget of ten warps)
+        constexpr int CH = 32;
+        // right-hand side of a chained step, CH columns of this thread's row, loaded one chunk ahead
+        // of its use (the first chunk while the products run): the drain never waits on a load
+        uint4 gq[CH / 8];
+        auto load_g = [&](const __nv_bfloat16* __restrict__ gk, int h, int c0) {
+            const __nv_bfloat16* src = gk + (size_t)((PAIR ? rk : h) * 128 + lq * 32 + lane) * P + cb + c0;
+#pragma unroll
+            for (int u = 0; u < CH / 8; ++u) gq[u] = __ldg((const uint4*)(src + 8 * u));
+        };
         for (int gph = 0; gph < nphase; ++gph) {
             const int ph = gph & 3, k = gph >> 2;
+            const bool last = k == nchain - 1;
+            const __nv_bfloat16* __restrict__ g = g0 ? g0 + (long long)k * p.g_kstride : nullptr;
+            if (ph == 3 && !last && g) load_g(g, 0, 0);
             ok = ok && __all_sync(0xffffffffu, tc::mbar_wait(accf, (uint32_t)gph & 1u, p.err, tc::ERR_WAIT_ACC));
             tc::tc_fence_after();
             if (!ok) break;
-            const bool last = k == nchain - 1;
-            const __nv_bfloat16* __restrict__ g = g0 ? g0 + (long long)k * p.g_kstride : nullptr;
             // modal factor of this step: d_qa = 1 + c sigma_qa, sigma_qa = K_x lambda_x[a] + K_y lambda_y[q],
             // c = tau = dt/2 (Crank-Nicolson, solve) or dt (backward Euler); f = 1/d, and
             // 2/d - 1 = (1 - tau sigma)/(1 + tau sigma) for Crank-Nicolson
@@ -296,21 +313,21 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
             const float cst = p.scheme == SCHEME_BE ? dtb : 0.5f * dtb;
             for (int h = 0; h < G::NHL; ++h) {
                 const int hh = PAIR ? rk : h;                 // 128-row half of M
-                const int row = hh * 128 + warp * 32 + lane;  // M index held by this thread
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * P);
+                const int row = hh * 128 + lq * 32 + lane;    // M index held by this thread
+                const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(h * P + cb);
                 if (ph < 3) {
                     const float Bq = fmaf(cst, s_ly[row], 1.f);
-                    for (int c0 = 0; c0 < P; c0 += 64) {
-                        uint32_t v[64];
-                        tc::tmem_ld64(taddr + (uint32_t)c0, v);
-                        float x[64];
+                    for (int c0 = 0; c0 < CW; c0 += CH) {
+                        uint32_t v[CH];
+                        tc::tmem_ld32(taddr + (uint32_t)c0, v);
+                        float x[CH];
 #pragma unroll
-                        for (int j = 0; j < 64; ++j) x[j] = __uint_as_float(v[j]);
-                        if (ph == 1) {  // D2[q = row][a = c0 + j] times f(sigma_qa)
+                        for (int j = 0; j < CH; ++j) x[j] = __uint_as_float(v[j]);
+                        if (ph == 1) {  // D2[q = row][a = cb + c0 + j] times f(sigma_qa)
 #pragma unroll
-                            for (int j = 0; j < 64; j += 2) {
+                            for (int j = 0; j < CH; j += 2) {
                                 // one reciprocal for two modes: 1/d0 = d1 / (d0 d1), 1/d1 = d0 / (d0 d1)
-                                const float d0 = fmaf(cst, s_lx[c0 + j], Bq), d1 = fmaf(cst, s_lx[c0 + j + 1], Bq);
+                                const float d0 = fmaf(cst, s_lx[cb + c0 + j], Bq), d1 = fmaf(cst, s_lx[cb + c0 + j + 1], Bq);
                                 const float r = rcp_approx(d0 * d1);
                                 float f0 = d1 * r, f1 = d0 * r;
                                 if (cn) { f0 = fmaf(2.f, f0, -1.f); f1 = fmaf(2.f, f1, -1.f); }
@@ -319,64 +336,74 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                             }
                         }
 #pragma unroll
-                        for (int u = 0; u < 8; ++u)
-                            st_shared_v4(sD_u + sw128<P>(row, c0 + 8 * u), pack_bf16x2(x[8 * u], x[8 * u + 1]),
+                        for (int u = 0; u < CH / 8; ++u)
+                            st_shared_v4(sD_u + sw128<P>(row, cb + c0 + 8 * u), pack_bf16x2(x[8 * u], x[8 * u + 1]),
                                          pack_bf16x2(x[8 * u + 2], x[8 * u + 3]), pack_bf16x2(x[8 * u + 4], x[8 * u + 5]),
                                          pack_bf16x2(x[8 * u + 6], x[8 * u + 7]));
                     }
                 } else if (!last) {
                     // chained: X[j = row][i] + g -> BF16, the next step's Data (row j, K = i) and this
                     // step's output; the output is copied to global memory after the next step starts
-                    const __nv_bfloat16* grow = g ? g + (size_t)row * P : nullptr;
-                    for (int c0 = 0; c0 < P; c0 += 64) {
-                        uint4 gv[8];
+                    for (int c0 = 0; c0 < CW; c0 += CH) {
+                        uint4 gv[CH / 8];
 #pragma unroll
-                        for (int u = 0; u < 8; ++u)
-                            gv[u] = grow ? __ldg((const uint4*)(grow + c0 + 8 * u)) : make_uint4(0, 0, 0, 0);
-                        uint32_t v[64];
-                        tc::tmem_ld64(taddr + (uint32_t)c0, v);
+                        for (int u = 0; u < CH / 8; ++u) gv[u] = g ? gq[u] : make_uint4(0, 0, 0, 0);
+                        if (g) {
+                            if (c0 + CH < CW) load_g(g, h, c0 + CH);
+                            else if (h + 1 < G::NHL) load_g(g, h + 1, 0);
+                        }
+                        uint32_t v[CH];
+                        tc::tmem_ld32(taddr + (uint32_t)c0, v);
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
+                        for (int u = 0; u < CH / 8; ++u) {
                             float gf[8];
                             bf16x8_to_f32(gv[u], gf);
                             float x[8];
 #pragma unroll
                             for (int q = 0; q < 8; ++q) x[q] = __uint_as_float(v[8 * u + q]) + gf[q];
-                            st_shared_v4(sD_u + sw128<P>(row, c0 + 8 * u), pack_bf16x2(x[0], x[1]), pack_bf16x2(x[2], x[3]),
-                                         pack_bf16x2(x[4], x[5]), pack_bf16x2(x[6], x[7]));
+                            st_shared_v4(sD_u + sw128<P>(row, cb + c0 + 8 * u), pack_bf16x2(x[0], x[1]),
+                                         pack_bf16x2(x[2], x[3]), pack_bf16x2(x[4], x[5]), pack_bf16x2(x[6], x[7]));
                         }
                     }
                 } else {
-                    // stage this warp's 32 rows (j) in FP32, 16-byte chunks XOR (row % 8), then write
-                    // X + g - u_target with whole-row coalesced accesses
-                    const uint32_t stg = sD_u + (uint32_t)(warp * 32 * G::STAGE_ROW);
-                    for (int c0 = 0; c0 < P; c0 += 64) {
-                        uint32_t v[64];
-                        tc::tmem_ld64(taddr + (uint32_t)c0, v);
+                    // stage this warp's 32 rows (j) x CW columns in FP32, 16-byte chunks XOR (row % 8),
+                    // then write X + g - u_target with coalesced half-row accesses
+                    constexpr int CPR = CW / 8;             // 8-column chunks per half-row
+                    constexpr int ITER = CPR;               // 32 rows x CPR chunks over 32 lanes
+                    constexpr int UNR = 4;
+                    const int rbase = hh * 128 + lq * 32;
+                    // g and u_target in groups of UNR chunks, each group loaded one group ahead (the
+                    // first before the staging)
+                    auto load_grp = [&](int i0, uint4 (&gg)[UNR], uint4 (&uu)[UNR]) {
 #pragma unroll
-                        for (int u = 0; u < 16; ++u) {
+                        for (int kk = 0; kk < UNR; ++kk) {
+                            const int e = (i0 + kk) * 32 + lane, rr = e / CPR, cc = e % CPR;
+                            const size_t off = (size_t)(rbase + rr) * P + cb + cc * 8;
+                            gg[kk] = g ? __ldg((const uint4*)(g + off)) : make_uint4(0, 0, 0, 0);
+                            uu[kk] = ut ? __ldg((const uint4*)(ut + off)) : make_uint4(0, 0, 0, 0);
+                        }
+                    };
+                    uint4 gv[UNR], uv[UNR];
+                    load_grp(0, gv, uv);
+                    const uint32_t stg = sD_u + (uint32_t)(warp * 32 * G::STAGE_ROW);
+                    for (int c0 = 0; c0 < CW; c0 += CH) {
+                        uint32_t v[CH];
+                        tc::tmem_ld32(taddr + (uint32_t)c0, v);
+#pragma unroll
+                        for (int u = 0; u < CH / 4; ++u) {
                             const int ch = (c0 >> 2) + u;
                             st_shared_v4(stg + (uint32_t)(lane * G::STAGE_ROW + ((ch ^ (lane & 7)) << 4)), v[4 * u],
                                          v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
                         }
                     }
                     __syncwarp();
-                    constexpr int CPR = P / 8;              // 8-column chunks per row
-                    constexpr int ITER = CPR;               // 32 rows x CPR chunks over 32 lanes
-                    constexpr int UNR = 8;
                     __nv_bfloat16* __restrict__ dst = dst0 + (long long)k * p.dst_kstride;
-                    const int rbase = hh * 128 + warp * 32;
                     const bool want_sq = ut && p.partial;
                     float sqf = 0.f;   // FP32 over this lane's 8 x ITER values (the FP64 pipe is ~1/64 rate)
                     for (int i0 = 0; i0 < ITER; i0 += UNR) {
-                        uint4 gv[UNR], uv[UNR];
-#pragma unroll
-                        for (int kk = 0; kk < UNR; ++kk) {
-                            const int e = (i0 + kk) * 32 + lane, rr = e / CPR, cc = e % CPR;
-                            const size_t off = (size_t)(rbase + rr) * P + cc * 8;
-                            gv[kk] = g ? __ldg((const uint4*)(g + off)) : make_uint4(0, 0, 0, 0);
-                            uv[kk] = ut ? __ldg((const uint4*)(ut + off)) : make_uint4(0, 0, 0, 0);
-                        }
+                        uint4 gn[UNR], un[UNR];
+                        const bool more = i0 + UNR < ITER;
+                        if (more) load_grp(i0 + UNR, gn, un);
 #pragma unroll
                         for (int kk = 0; kk < UNR; ++kk) {
                             const int e = (i0 + kk) * 32 + lane, rr = e / CPR, cc = e % CPR;
@@ -397,7 +424,11 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                             o.y = pack_bf16x2(xf[2], xf[3]);
                             o.z = pack_bf16x2(xf[4], xf[5]);
                             o.w = pack_bf16x2(xf[6], xf[7]);
-                            *(uint4*)(dst + (size_t)(rbase + rr) * P + cc * 8) = o;
+                            *(uint4*)(dst + (size_t)(rbase + rr) * P + cb + cc * 8) = o;
+                        }
+                        if (more) {
+#pragma unroll
+                            for (int kk = 0; kk < UNR; ++kk) { gv[kk] = gn[kk]; uv[kk] = un[kk]; }
                         }
                     }
                     sq += (double)sqf;
@@ -411,7 +442,7 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(dready)) : "memory");
                 if constexpr (PAIR) {
                     // this CTA's half of the next Data (rows 128 rk.., 16 KB in each K-atom) to the
-                    // same place in the peer's copy, once all four drain warps have written it (the
+                    // same place in the peer's copy, once all drain warps have written it (the
                     // arrivals above; a bounded wait, not a barrier a timed-out warp could miss)
                     if (threadIdx.x == 0 && tc::mbar_wait(dready, (uint32_t)gph & 1u, p.err, tc::ERR_WAIT_FULL)) {
                         const uint32_t peer = (uint32_t)(1 - rk);
@@ -425,24 +456,26 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                 }
             }
             if (ph == 3 && !last) {
-                // while the next step's first product runs: copy this warp's rows of the new Data
-                // (exactly this step's BF16 output) to global memory, one row per warp instruction,
-                // and bring the right-hand side two steps ahead into L2
+                // while the next step's first product runs: copy this warp's part of the new Data
+                // (exactly this step's BF16 output) to global memory, coalesced half-rows, and bring
+                // the right-hand side two steps ahead into L2
                 __nv_bfloat16* __restrict__ dst = dst0 + (long long)k * p.dst_kstride;
-                for (int h = 0; h < G::NHL; ++h)
-                    for (int r = 0; r < 32; ++r) {
-                        const int row = (PAIR ? rk : h) * 128 + warp * 32 + r;
-                        for (int c = lane; c < P / 8; c += 32) {
-                            uint4 o;
-                            asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
-                                         : "=r"(o.x), "=r"(o.y), "=r"(o.z), "=r"(o.w)
-                                         : "r"(sD_u + sw128<P>(row, 8 * c)) : "memory");
-                            *(uint4*)(dst + (size_t)row * P + 8 * c) = o;
-                        }
+                constexpr int CPR = CW / 8;
+                for (int h = 0; h < G::NHL; ++h) {
+                    const int rbase = (PAIR ? rk : h) * 128 + lq * 32;
+#pragma unroll 4
+                    for (int e = lane; e < 32 * CPR; e += 32) {
+                        const int row = rbase + e / CPR, col = cb + 8 * (e % CPR);
+                        uint4 o;
+                        asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                                     : "=r"(o.x), "=r"(o.y), "=r"(o.z), "=r"(o.w)
+                                     : "r"(sD_u + sw128<P>(row, col)) : "memory");
+                        *(uint4*)(dst + (size_t)row * P + col) = o;
                     }
+                }
                 if (g0 && k + 2 < nchain) {
                     const char* gn = (const char*)(g0 + (long long)(k + 2) * p.g_kstride);
-                    for (int e = warp * 32 + lane; e < P * P * 2 / 128; e += 128) prefetch_l2(gn + (size_t)e * 128);
+                    for (int e = warp * 32 + lane; e < P * P * 2 / 128; e += 32 * NDRAIN) prefetch_l2(gn + (size_t)e * 128);
                 }
             }
         }
@@ -455,15 +488,19 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
         // second barrier
         tc::cluster_sync();
         if (p.partial && threadIdx.x == 0 && rk == 0) {
-            double sp = red[0] + red[1] + red[2] + red[3];
+            double sp = 0.0;
             const uint32_t pr = tc::mapa_shared(tc::smem_u32(red), 1u);
-            for (int w = 0; w < 4; ++w) sp += tc::ld_cluster_f64(pr + 8u * (uint32_t)w);
+            for (int w = 0; w < NDRAIN; ++w) sp += red[w] + tc::ld_cluster_f64(pr + 8u * (uint32_t)w);
             p.partial[b] = sp;
         }
         tc::cluster_sync();
     } else {
         __syncthreads();
-        if (p.partial && threadIdx.x == 0) p.partial[b] = red[0] + red[1] + red[2] + red[3];
+        if (p.partial && threadIdx.x == 0) {
+            double sp = 0.0;
+            for (int w = 0; w < NDRAIN; ++w) sp += red[w];
+            p.partial[b] = sp;
+        }
     }
     if (warp == 0) {
         tc::tc_fence_after();
