@@ -193,16 +193,37 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
             tc::tc_fence_after();
             const uint8_t* sX = smem + st * STAGE;
             const uint8_t* sM = sX + S * XTILE;
-            for (int i = 0; i < nprod; ++i) {
-                const int dp = prod_entry<INT_OUT>(i, 0) - 1, dq = prod_entry<INT_OUT>(i, 1) - 1;
-                const int a = prod_entry<INT_OUT>(i, 2);
-                // the first product of an accumulator in a group's first chunk overwrites it
-                const bool first = group_start && (i == 0 || prod_entry<INT_OUT>(i - 1, 2) != a);
+            if constexpr (INT_OUT) {
+                // X digit p against matrix digits q = q0 .. q0 + Q - 1 in one product: the matrix
+                // planes lie one after another (Q BN rows) and accumulator d = p + q sits at
+                // columns (d - 2) BN, so the Q products land in Q consecutive accumulators.  The
+                // products of p = 1 reach every accumulator and overwrite them at a group's start.
+                for (int pp = 1; pp <= nd; ++pp) {
+                    const int qmax = nd + 1 - pp;
+                    for (int q0 = 1; q0 <= qmax; q0 += 256 / BN) {
+                        const int Q = min(256 / BN, qmax - q0 + 1);
+                        const uint32_t idq = tc::idesc_f32acc(1u, BM, Q * BN);
 #pragma unroll
-                for (int kk = 0; kk < KC / 16; ++kk) {
-                    const uint64_t ad = tc::smem_desc_sw64(sX + dp * XTILE + kk * 32);
-                    const uint64_t bd = tc::smem_desc_sw64(sM + dq * MTILE + kk * 32);
-                    tc::mma<0>(tmem + (uint32_t)(a * BN), ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+                        for (int kk = 0; kk < KC / 16; ++kk) {
+                            const uint64_t ad = tc::smem_desc_sw64(sX + (pp - 1) * XTILE + kk * 32);
+                            const uint64_t bd = tc::smem_desc_sw64(sM + (q0 - 1) * MTILE + kk * 32);
+                            tc::mma<0>(tmem + (uint32_t)((pp + q0 - 2) * BN), ad, bd, idq,
+                                       (group_start && pp == 1 && kk == 0) ? 0u : 1u);
+                        }
+                    }
+                }
+            } else {
+                for (int i = 0; i < nprod; ++i) {
+                    const int dp = prod_entry<INT_OUT>(i, 0) - 1, dq = prod_entry<INT_OUT>(i, 1) - 1;
+                    const int a = prod_entry<INT_OUT>(i, 2);
+                    // the first product of an accumulator in a group's first chunk overwrites it
+                    const bool first = group_start && (i == 0 || prod_entry<INT_OUT>(i - 1, 2) != a);
+#pragma unroll
+                    for (int kk = 0; kk < KC / 16; ++kk) {
+                        const uint64_t ad = tc::smem_desc_sw64(sX + dp * XTILE + kk * 32);
+                        const uint64_t bd = tc::smem_desc_sw64(sM + dq * MTILE + kk * 32);
+                        tc::mma<0>(tmem + (uint32_t)(a * BN), ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+                    }
                 }
             }
             any = true;
