@@ -57,6 +57,13 @@ sfde_status sfde_debug_residual(sfde_ctx* ctx, const double* U, int use_tensor_c
 sfde_status sfde_debug_set_residual_digits(sfde_ctx* ctx, int nd);
 
 /*
+ * Time points per pass of the tensor-core residual (Eq. (2.4)): 0 (default) the scratch size, else
+ * at most that.  Smaller passes keep the digit planes and products of a pass in L2.  Takes effect at
+ * the next residual.
+ */
+sfde_status sfde_debug_set_resid_chunk(sfde_ctx* ctx, int n);
+
+/*
  * Whether the BF16 mixed-precision solver runs each spectral step as one fused kernel (the four
  * products of Sec. 2's fast diagonalisation chained on chip; P_x = P_y in {128, 256}) or as four
  * tensor-core slice GEMMs.  Default 1; the two give the same arithmetic up to the order of FP32

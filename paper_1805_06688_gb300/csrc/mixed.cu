@@ -654,6 +654,12 @@ extern "C" sfde_status sfde_debug_set_fused_step(sfde_ctx* c, int enable) {
     return SFDE_OK;
 }
 
+extern "C" sfde_status sfde_debug_set_resid_chunk(sfde_ctx* c, int n) {
+    if (!c || n < 0) return SFDE_EINVAL;
+    c->resid_chunk = n;
+    return SFDE_OK;
+}
+
 extern "C" sfde_status sfde_debug_set_fused_pair(sfde_ctx* c, int mode) {
     if (!c || mode < 0 || mode > 2) return SFDE_EINVAL;
     c->fused_pair = mode;

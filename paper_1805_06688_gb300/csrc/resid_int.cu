@@ -301,8 +301,9 @@ sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int cou
     sfde_prof_end(c, slot, 5, 0.0, 8.0 * nxy * (count + 1));
     sfde_count_launch(c);
     int total = 0;
-    for (int b0 = 0; b0 < count; b0 += (int)c->ws_slices) {
-        const int nb = std::min(count - b0, (int)c->ws_slices);
+    const int chunk = c->resid_chunk > 0 ? std::min(c->resid_chunk, (int)c->ws_slices) : (int)c->ws_slices;
+    for (int b0 = 0; b0 < count; b0 += chunk) {
+        const int nb = std::min(count - b0, chunk);
         const int n0 = n_first + b0;
         const long long plane = (long long)nb * Px * Py;
         dim3 grid(Px / 32, Py / 32, nb), block(32, 8);

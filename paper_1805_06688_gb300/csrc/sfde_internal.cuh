@@ -105,6 +105,7 @@ struct sfde_ctx {
     int fused_step = 1;         // BF16 steps as one fused kernel where the padded sizes allow it
     int fused_pair = 1;         // fused steps on two CTAs per slice: 0 never, 1 when 2 batch <= SMs, 2 always
     int resid_digits = 0;       // digits of the tensor-core residual: 0 per iteration, else 4..7 fixed
+    int resid_chunk = 0;        // time points per pass of the tensor-core residual (0: ws_slices)
     SfdeProf prof;
     size_t P2() const { return (size_t)x.P * (size_t)y.P; }
 };
