@@ -107,7 +107,7 @@ KERNEL_SOURCES = {
     "k_slice_gemm_fp64": ("step_fp64.cu",),
     "k_tc_slice_gemm": ("gemm_tc.cu", "tc_common.cuh"),
     "k_fused_step": ("fused_step.cu", "tc_common.cuh"),
-    "k_ozaki_slice_gemm": ("ozaki.cu", "tc_common.cuh"),
+    "k_digit_gemm_int": ("ozaki.cu", "tc_common.cuh"),
     "k_split_pair+k_combine_int": ("resid_int.cu",),
 }
 
@@ -197,7 +197,7 @@ KERNEL_CLASSES = (  # the library's accounting classes (include/sfde.h, sfde_pro
     ("k_slice_gemm_fp64", "FP64 slice GEMM of the space-time residual", "alu"),
     ("k_tc_slice_gemm", "tcgen05 slice GEMM of a low-precision step (BF16/TF32)", "tc"),
     ("k_fused_step", "fused BF16 spectral step: four tcgen05 products per slice on chip", "tc"),
-    ("k_ozaki_slice_gemm", "digit-split residual products: 28 BF16 tcgen05 products, exact int64", "tc"),
+    ("k_digit_gemm_int", "digit-split residual products: up to 28 BF16 tcgen05 products, exact int64", "tc"),
     ("k_split_pair+k_combine_int", "integer residual assembly (exponents, digits, combination)", "hbm"),
 )
 

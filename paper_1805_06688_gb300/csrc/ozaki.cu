@@ -47,10 +47,11 @@ template <> struct Plan<false> {
     static constexpr int S = 6, NPROD = 21, NACC = 12, BN = 32, STAGES = 3, KGROUP = 256;
 };
 template <> struct Plan<true> {
-    static constexpr int S = 7, NPROD = 28, NACC = 7, BN = 64, STAGES = 2, KGROUP = 128;
+    static constexpr int S = 7, BN = 64, STAGES = 2, KGROUP = 128;
 };
 
-// accumulator a -> digit sum d = p + q of its products, and the product list (p, q, a), grouped by a
+// FP64-output plan: accumulator a -> digit sum d = p + q of its products, and the product list
+// (p, q, a), grouped by a (the integer plan needs no table: accumulator d - 2 holds digit sum d)
 __constant__ int c6_acc_d[12] = {2, 3, 4, 4, 5, 5, 6, 6, 6, 7, 7, 7};
 __constant__ int c6_prod[21][3] = {
     {1, 1, 0},
@@ -60,28 +61,6 @@ __constant__ int c6_prod[21][3] = {
     {1, 5, 6}, {2, 4, 6}, {3, 3, 7}, {4, 2, 7}, {5, 1, 8},
     {1, 6, 9}, {2, 5, 9}, {3, 4, 10}, {4, 3, 10}, {5, 2, 11}, {6, 1, 11},
 };
-__constant__ int c7_acc_d[7] = {2, 3, 4, 5, 6, 7, 8};
-__constant__ int c7_prod[28][3] = {
-    {1, 1, 0},
-    {1, 2, 1}, {2, 1, 1},
-    {1, 3, 2}, {2, 2, 2}, {3, 1, 2},
-    {1, 4, 3}, {2, 3, 3}, {3, 2, 3}, {4, 1, 3},
-    {1, 5, 4}, {2, 4, 4}, {3, 3, 4}, {4, 2, 4}, {5, 1, 4},
-    {1, 6, 5}, {2, 5, 5}, {3, 4, 5}, {4, 3, 5}, {5, 2, 5}, {6, 1, 5},
-    {1, 7, 6}, {2, 6, 6}, {3, 5, 6}, {4, 4, 6}, {5, 3, 6}, {6, 2, 6}, {7, 1, 6},
-};
-
-// table entries with the plan chosen at compile time (direct constant-bank reads, no generic loads)
-template <bool INT_OUT>
-__device__ __forceinline__ int prod_entry(int i, int k) {
-    if constexpr (INT_OUT) return c7_prod[i][k];
-    else return c6_prod[i][k];
-}
-template <bool INT_OUT>
-__device__ __forceinline__ int acc_digit_sum(int a) {
-    if constexpr (INT_OUT) return c7_acc_d[a];
-    else return c6_acc_d[a];
-}
 
 template <bool INT_OUT>
 constexpr int mtile() { return Plan<INT_OUT>::BN * KC * 2; }   // one digit plane of the matrix tile
@@ -107,16 +86,14 @@ __device__ __forceinline__ double pow2(int e) {  // exact 2^e for normal range
     return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-// INT_OUT: write sum_{p+q<=8} 2^{-8(p+q)} sum_k d_p c_q as one int64 in units of 2^{zshift-52}
-// (exact up to the rounding of the p + q >= 7 terms to that unit; |value| <= 2^58); otherwise FP64
-// scaled by the row and column exponents (p + q <= 7).
+// FP64 output: sum_{p+q<=7} 2^{-8(p+q)} sum_k d_p c_q scaled by the row and column exponents.
 // Roles: warp 4 lane 0 issues TMA, warp 5 lane 0 issues the MMAs, warps 0-3 drain the
-// accumulators (TMEM lanes 32w..32w+31), also between K groups while the other two roles run on.
+// accumulators (TMEM lanes 32w..32w+31).
 constexpr int OZ_THREADS = 192;
 
-template <bool INT_OUT>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapM, OzArgs p) {
+    constexpr bool INT_OUT = false;
     constexpr int S = Plan<INT_OUT>::S, NPROD = Plan<INT_OUT>::NPROD, NACC = Plan<INT_OUT>::NACC;
     constexpr int BN = Plan<INT_OUT>::BN, STAGES = Plan<INT_OUT>::STAGES, KGROUP = Plan<INT_OUT>::KGROUP;
     constexpr int MTILE = BN * KC * 2;
@@ -137,13 +114,8 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
     const int n0 = blockIdx.x * BN;
     const long long Mtot = (long long)p.batch * p.R;
     const int nchunks = (p.K + KC - 1) / KC;
-    // digits in use: the 7-digit plan's products and accumulators are ordered by digit sum, so the
-    // plan for nd digits (products with p + q <= nd + 1) is a prefix of both lists
-    const int nd = INT_OUT ? p.nd : S;
-    const int nprod = INT_OUT ? nd * (nd + 1) / 2 : NPROD;
-    const int nacc = INT_OUT ? nd : NACC;          // integer plan: one accumulator per digit sum
-    constexpr int CPG = KGROUP / KC;          // chunks per K group
-    const int ngroups = (nchunks + CPG - 1) / CPG;
+    const int nd = S, nprod = NPROD;
+    constexpr int CPG = KGROUP / KC;          // chunks per K group (K <= 256: one group)
 
     if (threadIdx.x == 0) {
         for (int st = 0; st < STAGES; ++st) { tc::mbar_init(&full[st], 1); tc::mbar_init(&empty[st], 1); }
@@ -193,37 +165,16 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
             tc::tc_fence_after();
             const uint8_t* sX = smem + st * STAGE;
             const uint8_t* sM = sX + S * XTILE;
-            if constexpr (INT_OUT) {
-                // X digit p against matrix digits q = q0 .. q0 + Q - 1 in one product: the matrix
-                // planes lie one after another (Q BN rows) and accumulator d = p + q sits at
-                // columns (d - 2) BN, so the Q products land in Q consecutive accumulators.  The
-                // products of p = 1 reach every accumulator and overwrite them at a group's start.
-                for (int pp = 1; pp <= nd; ++pp) {
-                    const int qmax = nd + 1 - pp;
-                    for (int q0 = 1; q0 <= qmax; q0 += 256 / BN) {
-                        const int Q = min(256 / BN, qmax - q0 + 1);
-                        const uint32_t idq = tc::idesc_f32acc(1u, BM, Q * BN);
+            for (int i = 0; i < nprod; ++i) {
+                const int dp = c6_prod[i][0] - 1, dq = c6_prod[i][1] - 1;
+                const int a = c6_prod[i][2];
+                // the first product of an accumulator in a group's first chunk overwrites it
+                const bool first = group_start && (i == 0 || c6_prod[i - 1][2] != a);
 #pragma unroll
-                        for (int kk = 0; kk < KC / 16; ++kk) {
-                            const uint64_t ad = tc::smem_desc_sw64(sX + (pp - 1) * XTILE + kk * 32);
-                            const uint64_t bd = tc::smem_desc_sw64(sM + (q0 - 1) * MTILE + kk * 32);
-                            tc::mma<0>(tmem + (uint32_t)((pp + q0 - 2) * BN), ad, bd, idq,
-                                       (group_start && pp == 1 && kk == 0) ? 0u : 1u);
-                        }
-                    }
-                }
-            } else {
-                for (int i = 0; i < nprod; ++i) {
-                    const int dp = prod_entry<INT_OUT>(i, 0) - 1, dq = prod_entry<INT_OUT>(i, 1) - 1;
-                    const int a = prod_entry<INT_OUT>(i, 2);
-                    // the first product of an accumulator in a group's first chunk overwrites it
-                    const bool first = group_start && (i == 0 || prod_entry<INT_OUT>(i - 1, 2) != a);
-#pragma unroll
-                    for (int kk = 0; kk < KC / 16; ++kk) {
-                        const uint64_t ad = tc::smem_desc_sw64(sX + dp * XTILE + kk * 32);
-                        const uint64_t bd = tc::smem_desc_sw64(sM + dq * MTILE + kk * 32);
-                        tc::mma<0>(tmem + (uint32_t)(a * BN), ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
-                    }
+                for (int kk = 0; kk < KC / 16; ++kk) {
+                    const uint64_t ad = tc::smem_desc_sw64(sX + dp * XTILE + kk * 32);
+                    const uint64_t bd = tc::smem_desc_sw64(sM + dq * MTILE + kk * 32);
+                    tc::mma<0>(tmem + (uint32_t)(a * BN), ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
                 }
             }
             any = true;
@@ -238,57 +189,6 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
 
     if (warp >= 4) {
         // producer and MMA warps: nothing to drain
-    } else if constexpr (INT_OUT) {
-        const long long m = m0 + warp * 32 + lane;
-        // zt: running sums over the K groups in units of 2^-52; per group and 16-column slice, z holds
-        // the digit sums d <= 6 (units 2^-52, exact) and zl d = 7, 8 (units 2^-64, exact), folded into
-        // zt with one rounding per group (at most half a unit each)
-        long long zt[BN];
-#pragma unroll
-        for (int j = 0; j < BN; ++j) zt[j] = 0;
-        bool acc_ok = true;
-        for (int grp = 0; grp < ngroups; ++grp) {
-            acc_ok = __all_sync(0xffffffffu, tc::mbar_wait(accf, (uint32_t)grp & 1u, p.err, tc::ERR_WAIT_ACC));
-            tc::tc_fence_after();
-            if (!acc_ok) break;
-#pragma unroll
-            for (int qs = 0; qs < BN / 16; ++qs) {
-                long long z[16], zl[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) { z[j] = 0; zl[j] = 0; }
-#pragma unroll 1
-                for (int a = 0; a < nacc; ++a) {
-                    uint32_t v[16];
-                    tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * BN + qs * 16), v);
-                    const int d = acc_digit_sum<INT_OUT>(a);
-                    const int sh = d <= 6 ? 52 - 8 * d : 8 * (8 - d);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const long long sv = (long long)__float2int_rn(__uint_as_float(v[j]));  // exact, |sv| <= 2^24
-                        if (d <= 6) z[j] += sv << sh;
-                        else zl[j] += sv << sh;
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < 16; ++j) zt[qs * 16 + j] += z[j] + ((zl[j] + 2048) >> 12);
-            }
-            if (grp + 1 < ngroups) {
-                tc::tc_fence_before();
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(tfree)) : "memory");
-            }
-        }
-        if (acc_ok && m < Mtot) {
-            const long long b = m / p.R;
-            const int r = (int)(m % p.R);
-            long long* out = (long long*)p.out + b * p.out_stride + r;
-            const int zs = p.zshift;
-#pragma unroll
-            for (int j = 0; j < BN; ++j) {
-                long long y = zt[j];
-                if (zs > 0) y = (y + (1ll << (zs - 1))) >> zs;
-                if (n0 + j < p.N) out[(long long)(n0 + j) * p.R] = y;
-            }
-        }
     } else if (__all_sync(0xffffffffu, tc::mbar_wait(accf, 0, p.err, tc::ERR_WAIT_ACC))) {
         // FP64 output (K <= 256: one group)
         tc::tc_fence_after();
@@ -302,7 +202,7 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
         for (int a = 0; a < NACC; ++a) {
             uint32_t v[32];
             tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * BN), v);
-            const int d = acc_digit_sum<INT_OUT>(a);
+            const int d = c6_acc_d[a];
 #pragma unroll
             for (int j = 0; j < BN; ++j) {
                 const long long s = (long long)__float2ll_rn(__uint_as_float(v[j]));  // exact integer
@@ -321,6 +221,188 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
                 const int e = er + p.me[n];
                 const double y = (double)zhi[j] * pow2(e - 40) + (double)zlo[j] * pow2(e - 56);
                 out[(long long)n * p.R] = y;
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// Integer-output digit GEMM, persistent: CTA c takes tiles c, c + gridDim.x, ... of 128 rows x BN
+// columns (columns fastest, so concurrent CTAs share X digit planes in L2).  Warp NDW issues TMA
+// and streams chunks across tiles; warp NDW + 1 issues the MMAs; warps 0..NDW-1 drain, warp w
+// reading TMEM lanes 32 (w % 4).. (the lanes its warp index may access) and BN / 2 columns.  While
+// the drain folds a K group and stores a finished tile, the producer loads the next chunks, and
+// the next tile's products start as soon as the accumulators are read.
+constexpr int DG_NDW = 8;
+constexpr int DG_THREADS = 32 * (DG_NDW + 2);
+
+__global__ void __launch_bounds__(DG_THREADS, 1)
+k_digit_gemm_int(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapM, OzArgs p) {
+    using PL = Plan<true>;
+    constexpr int S = PL::S, BN = PL::BN, STAGES = PL::STAGES, KGROUP = PL::KGROUP;
+    constexpr int MTILE = BN * KC * 2;
+    constexpr int STAGE = S * (XTILE + MTILE);
+    constexpr int CW = BN / 2;                          // columns per drain warp
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accf = empty + STAGES;                    // a K group's products complete
+    uint64_t* fin = accf + 1;                           // error path: outstanding products complete
+    uint64_t* tfree = fin + 1;                          // a K group's accumulators have been read
+    uint32_t* tmem_slot = (uint32_t*)(tfree + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long Mtot = (long long)p.batch * p.R;
+    const int ntn = (p.N + BN - 1) / BN;
+    const long long ntiles = (long long)ntn * ((Mtot + BM - 1) / BM);
+    const int nchunks = (p.K + KC - 1) / KC;
+    constexpr int CPG = KGROUP / KC;
+    const int ngroups = (nchunks + CPG - 1) / CPG;
+    const int nd = p.nd;
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < STAGES; ++st) { tc::mbar_init(&full[st], 1); tc::mbar_init(&empty[st], 1); }
+        tc::mbar_init(accf, 1);
+        tc::mbar_init(fin, 1);
+        tc::mbar_init(tfree, 32 * DG_NDW);
+        tc::mbar_fence_init();
+        tc::prefetch_tmap(&mapX);
+        tc::prefetch_tmap(&mapM);
+    }
+    if (warp == 0) tc::tmem_alloc(tmem_slot, TMEM_COLS);
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == DG_NDW) {
+        if (lane == 0) {
+            bool ok = true;
+            long long cnt = 0;
+            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const long long m0 = (t / ntn) * BM;
+                const int n0 = (int)(t % ntn) * BN;
+                const int b0 = (int)(m0 / p.R), r0 = (int)(m0 % p.R);
+                for (int c = 0; c < nchunks && ok; ++c, ++cnt) {
+                    const int st = (int)(cnt % STAGES);
+                    if (cnt >= STAGES)
+                        ok = tc::mbar_wait(&empty[st], (uint32_t)(cnt / STAGES - 1) & 1u, p.err, tc::ERR_WAIT_EMPTY);
+                    if (!ok) break;
+                    uint8_t* sX = smem + st * STAGE;
+                    uint8_t* sM = sX + S * XTILE;
+                    tc::mbar_arrive_expect_tx(&full[st], (uint32_t)(nd * (XTILE + MTILE)));
+                    for (int d = 0; d < nd; ++d) {
+                        tc::tma_load_4d(sX + d * XTILE, &mapX, &full[st], c * KC, r0, b0, d);
+                        tc::tma_load_3d(sM + d * MTILE, &mapM, &full[st], c * KC, n0, d);
+                    }
+                }
+            }
+            // own copies in flight must land before the CTA's shared memory goes away
+            for (long long c = cnt - STAGES < 0 ? 0 : cnt - STAGES; c < cnt; ++c)
+                tc::mbar_wait(&full[c % STAGES], (uint32_t)(c / STAGES) & 1u, p.err, tc::ERR_WAIT_FULL);
+        }
+    } else if (warp == DG_NDW + 1) {
+        if (lane == 0) {
+            bool ok = true, any = false;
+            long long cnt = 0, G = 0;
+            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int c = 0; c < nchunks && ok; ++c, ++cnt) {
+                    const int st = (int)(cnt % STAGES);
+                    const bool group_start = c % CPG == 0;
+                    // a K group overwrites the accumulators once the drain warps have read the last
+                    if (group_start && G > 0) ok = tc::mbar_wait(tfree, (uint32_t)(G - 1) & 1u, p.err, tc::ERR_WAIT_ACC);
+                    if (!ok) break;
+                    ok = tc::mbar_wait(&full[st], (uint32_t)(cnt / STAGES) & 1u, p.err, tc::ERR_WAIT_FULL);
+                    if (!ok) break;
+                    tc::tc_fence_after();
+                    const uint8_t* sX = smem + st * STAGE;
+                    const uint8_t* sM = sX + S * XTILE;
+                    // X digit p against matrix digits q0 .. q0 + Q - 1 in one product (the matrix
+                    // planes lie one after another; accumulator d = p + q sits at columns (d - 2) BN);
+                    // the products of p = 1 reach every accumulator and overwrite them at a group's
+                    // start
+                    for (int pp = 1; pp <= nd; ++pp) {
+                        const int qmax = nd + 1 - pp;
+                        for (int q0 = 1; q0 <= qmax; q0 += 256 / BN) {
+                            const int Q = min(256 / BN, qmax - q0 + 1);
+                            const uint32_t idq = tc::idesc_f32acc(1u, BM, Q * BN);
+#pragma unroll
+                            for (int kk = 0; kk < KC / 16; ++kk) {
+                                const uint64_t ad = tc::smem_desc_sw64(sX + (pp - 1) * XTILE + kk * 32);
+                                const uint64_t bd = tc::smem_desc_sw64(sM + (q0 - 1) * MTILE + kk * 32);
+                                tc::mma<0>(tmem + (uint32_t)((pp + q0 - 2) * BN), ad, bd, idq,
+                                           (group_start && pp == 1 && kk == 0) ? 0u : 1u);
+                            }
+                        }
+                    }
+                    any = true;
+                    tc::mma_commit(&empty[st]);
+                    if (c % CPG == CPG - 1 || c == nchunks - 1) { tc::mma_commit(accf); ++G; }
+                }
+            }
+            if (!ok && any) {  // products still running must finish before TMEM is freed
+                tc::mma_commit(fin);
+                tc::mbar_wait(fin, 0, p.err, tc::ERR_WAIT_ACC);
+            }
+        }
+    } else {
+        const int lq = warp & 3, cb = (warp >> 2) * CW;
+        const int zs = p.zshift;
+        bool ok = true;
+        long long G = 0;
+        for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const long long m = (t / ntn) * BM + lq * 32 + lane;
+            const int n0 = (int)(t % ntn) * BN;
+            // zt: running sums over the K groups in units of 2^-52; per group and 16-column slice, z
+            // holds the digit sums d <= 6 (units 2^-52, exact) and zl d = 7, 8 (units 2^-64, exact),
+            // folded into zt with one rounding per group (at most half a unit each)
+            long long zt[CW];
+#pragma unroll
+            for (int j = 0; j < CW; ++j) zt[j] = 0;
+            for (int grp = 0; grp < ngroups; ++grp, ++G) {
+                ok = __all_sync(0xffffffffu, tc::mbar_wait(accf, (uint32_t)G & 1u, p.err, tc::ERR_WAIT_ACC));
+                tc::tc_fence_after();
+                if (!ok) break;
+#pragma unroll
+                for (int qs = 0; qs < CW / 16; ++qs) {
+                    long long z[16], zl[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) { z[j] = 0; zl[j] = 0; }
+#pragma unroll 1
+                    for (int a = 0; a < nd; ++a) {
+                        uint32_t v[16];
+                        tc::tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(a * BN + cb + qs * 16), v);
+                        const int d = a + 2;
+                        const int sh = d <= 6 ? 52 - 8 * d : 8 * (8 - d);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const long long sv = (long long)__float2int_rn(__uint_as_float(v[j]));  // exact, |sv| < 2^24
+                            if (d <= 6) z[j] += sv << sh;
+                            else zl[j] += sv << sh;
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) zt[qs * 16 + j] += z[j] + ((zl[j] + 2048) >> 12);
+                }
+                tc::tc_fence_before();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(tfree)) : "memory");
+            }
+            // the next tile's products run while this one is stored
+            if (ok && m < Mtot) {
+                const long long b = m / p.R;
+                const int r = (int)(m % p.R);
+                long long* out = (long long*)p.out + b * p.out_stride + r;
+#pragma unroll
+                for (int j = 0; j < CW; ++j) {
+                    long long y = zt[j];
+                    if (zs > 0) y = (y + (1ll << (zs - 1))) >> zs;
+                    if (n0 + cb + j < p.N) out[(long long)(n0 + cb + j) * p.R] = y;
+                }
             }
         }
     }
@@ -524,9 +606,9 @@ sfde_status sfde_oz_split_matrix(const double* Mat, int K, int N, OzMatrix* out,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return SFDE_EINVAL;
-    SFDE_CUDA(cudaFuncSetAttribute(k_ozaki_slice_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SFDE_CUDA(cudaFuncSetAttribute(k_ozaki_slice_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem_bytes<false>()));
-    SFDE_CUDA(cudaFuncSetAttribute(k_ozaki_slice_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SFDE_CUDA(cudaFuncSetAttribute(k_digit_gemm_int, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem_bytes<true>()));
     return SFDE_OK;
 }
@@ -560,13 +642,25 @@ sfde_status launch_oz(sfde_ctx* c, const CUtensorMap& mapX, const OzMatrix& M, c
                       int nr, int nc, int nout) {
     const long long mt = ((long long)a.batch * a.R + BM - 1) / BM;
     if (mt > 65535) return SFDE_EINVAL;
-    dim3 grid((M.N + Plan<INT_OUT>::BN - 1) / Plan<INT_OUT>::BN, (unsigned)mt);
+    const int ntn = (M.N + Plan<INT_OUT>::BN - 1) / Plan<INT_OUT>::BN;
     const int slot = sfde_prof_begin(c);
-    k_ozaki_slice_gemm<INT_OUT><<<grid, OZ_THREADS, smem_bytes<INT_OUT>(), s>>>(mapX, M.map, a);
+    if constexpr (INT_OUT) {
+        static int nsm = 0;
+        if (!nsm) {
+            int dev = 0;
+            SFDE_CUDA(cudaGetDevice(&dev));
+            SFDE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        }
+        const long long ntiles = mt * ntn;
+        k_digit_gemm_int<<<(unsigned)std::min<long long>(ntiles, nsm), DG_THREADS, smem_bytes<true>(), s>>>(mapX, M.map,
+                                                                                                       a);
+    } else {
+        k_ozaki_slice_gemm<<<dim3(ntn, (unsigned)mt), OZ_THREADS, smem_bytes<false>(), s>>>(mapX, M.map, a);
+    }
     // tensor work: the digit products of 2 R K N flops each; bytes: the digit planes of X in use,
     // the matrix digits and the output (8 bytes per element) once
     const int S = INT_OUT ? a.nd : Plan<false>::S;
-    const int NPROD = INT_OUT ? a.nd * (a.nd + 1) / 2 : Plan<false>::NPROD;
+    const int NPROD = INT_OUT ? a.nd * (a.nd + 1) / 2 : Plan<false>::NPROD;   // digit products
     sfde_prof_end(c, slot, 4, (double)NPROD * 2.0 * a.batch * nr * nc * nout,
                   2.0 * S * ((double)a.batch * nr * nc + (double)nc * nout) + 8.0 * a.batch * nr * nout);
     sfde_count_launch(c);
