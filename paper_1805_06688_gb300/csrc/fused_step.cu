@@ -441,16 +441,17 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                 tc::tc_fence_before();
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(dready)) : "memory");
                 if constexpr (PAIR) {
-                    // this CTA's half of the next Data (rows 128 rk.., 16 KB in each K-atom) to the
-                    // same place in the peer's copy, once all drain warps have written it (the
-                    // arrivals above; a bounded wait, not a barrier a timed-out warp could miss)
-                    if (threadIdx.x == 0 && tc::mbar_wait(dready, (uint32_t)gph & 1u, p.err, tc::ERR_WAIT_FULL)) {
+                    // this warp's part of the next Data (rows 128 rk + 32 lq.., K-atoms of columns
+                    // cb..: 4 KB each) to the same place in the peer's copy, as soon as the warp has
+                    // written it
+                    __syncwarp();
+                    if (lane == 0) {
                         const uint32_t peer = (uint32_t)(1 - rk);
                         const uint32_t rbar = tc::mapa_shared(tc::smem_u32(rfull), peer);
 #pragma unroll
-                        for (int t = 0; t < G::NATOM; ++t) {
-                            const uint32_t src = sD_u + (uint32_t)(t * G::ATOM + rk * HALF_BYTES);
-                            tc::bulk_copy_to_cluster(tc::mapa_shared(src, peer), src, (uint32_t)HALF_BYTES, rbar);
+                        for (int t = cb / 64; t < (cb + CW) / 64; ++t) {
+                            const uint32_t src = sD_u + (uint32_t)(t * G::ATOM + rk * HALF_BYTES + lq * 4096);
+                            tc::bulk_copy_to_cluster(tc::mapa_shared(src, peer), src, 4096u, rbar);
                         }
                     }
                 }
