@@ -9,13 +9,14 @@
 //   1. per time point, E_n with max |U_n| < 2^{E_n} (an integer max over the bit patterns);
 //   2. per pair (n-1, n) with E = max(E_{n-1}, E_n): the fixed-point values fix(u) = round(u 2^{54-E})
 //      (|fix| <= 2^54) and V = fix(U_{n-1}) + fix(U_n), exact, written as seven balanced base-256
-//      digits of 2V (BF16-exact, no remainder) in row-major and in transposed order;
+//      digits of V (BF16-exact, no remainder) in row-major and in transposed order;
 //   3. Z1 = V (K_x h_y/6 A_x) and Z2 = (K_y h_x/6 A_y) V on the tensor cores (ozaki.cu, 28 digit
 //      products), each an int64 in units of 2^{-52} of the operands' scales;
 //   4. with the mass matrices M = (h/6) tridiag(1, 4, 1) in both directions (they commute with the
 //      products: A_y (V M_x) = (A_y V) M_x),
 //          K V = (1,4,1)_y Z1 + (1,4,1)_x Z2      (integer, aligned to a common power of two),
-//          M_h (U_{n-1} - U_n) = (h_x h_y / 36) (1,4,1)_y (1,4,1)_x (fix(U_{n-1}) - fix(U_n)),
+//          M_h (U_{n-1} - U_n) = (h_x h_y / 36) (1,4,1)_y (1,4,1)_x du,  du = fix(U_{n-1}) - fix(U_n)
+//      (du written by step 2 as int64),
 //      and rho = F + c_m S9 - tau c_s S in FP64: two FMAs per element (the int64 -> FP64
 //      conversions are built from bits); the sum of rho^2 is taken over the stored FP32 values.
 // The fixed-point grid of a pair is 2^{E-54}: values far below the slice maximum keep an absolute
@@ -85,47 +86,54 @@ __device__ __forceinline__ void split7(long long x, uint16_t (&bf)[ND]) {
     for (int p = 1; p < ND; ++p) bf[p] = bf16_of_int((int)((unsigned long long)(xp >> (T - 8 * (p + 1))) & 255u) - 128);
 }
 
-// V = fix(U_{n-1}) + fix(U_n) for one 32 x 32 tile of pair b (n = n0 + b): the digits of V
-// row-major [b][j][i] (rows of the A_x product) and transposed [b][i][j] (rows of the A_y product).
+// V = fix(U_{n-1}) + fix(U_n) and du = fix(U_{n-1}) - fix(U_n) for one 32 x 32 tile of pair b
+// (n = n0 + b): the digits of V row-major [b][j][i] (rows of the A_x product) and transposed
+// [b][i][j] (rows of the A_y product), du as int64 [b][j][i] (the mass term).  Thread t takes four
+// consecutive columns 4 (t % 8).. of row t / 8, so every access moves 8 or 16 bytes.
 __global__ void __launch_bounds__(256) k_split_pair(const double* __restrict__ U, const int* __restrict__ En, int n0,
                                                     int Px, int Py, uint16_t* __restrict__ dV, uint16_t* __restrict__ dVt,
-                                                    long long plane, int nd) {
-    __shared__ uint16_t dt[ND][32][34];   // digits, [p][i][j]
+                                                    long long* __restrict__ du, long long plane, int nd) {
+    __shared__ uint16_t dt[ND][32][34];   // digits [p][i][j]
     const int b = blockIdx.z, n = n0 + b;
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int q = threadIdx.x & 7, r = threadIdx.x >> 3;
     const int E = max(En[n - 1], En[n]);
     const size_t P2 = (size_t)Px * Py;
-    const unsigned long long* Un = (const unsigned long long*)(U + (size_t)n * P2);
-    const unsigned long long* Um = (const unsigned long long*)(U + (size_t)(n - 1) * P2);
-    unsigned long long un[4], um[4];   // all loads first: their latencies overlap
+    const size_t e = (size_t)(j0 + r) * Px + i0 + 4 * q;
+    const ulonglong2* Un = (const ulonglong2*)(U + (size_t)n * P2 + e);
+    const ulonglong2* Um = (const ulonglong2*)(U + (size_t)(n - 1) * P2 + e);
+    const ulonglong2 n01 = __ldg(Un), n23 = __ldg(Un + 1), m01 = __ldg(Um), m23 = __ldg(Um + 1);
+    const unsigned long long un[4] = {n01.x, n01.y, n23.x, n23.y}, um[4] = {m01.x, m01.y, m23.x, m23.y};
+    uint16_t bf[4][ND];
+    long long d4[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const size_t e = (size_t)(j0 + ty + 8 * k) * Px + i0 + tx;
-        un[k] = __ldg(Un + e);
-        um[k] = __ldg(Um + e);
+    for (int c = 0; c < 4; ++c) {
+        const long long fm = fixp(um[c], E), fn = fixp(un[c], E);
+        d4[c] = fm - fn;
+        split7<56>(fm + fn, bf[c]);     // |V| <= 2^55: every digit within [-128, 128], exact
     }
+    const size_t o = (size_t)b * P2 + e;
+    *(longlong2*)(du + o) = make_longlong2(d4[0], d4[1]);
+    *(longlong2*)(du + o + 2) = make_longlong2(d4[2], d4[3]);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int jj = ty + 8 * k;
-        const size_t e = (size_t)(j0 + jj) * Px + i0 + tx;
-        uint16_t bf[ND];
-        split7<56>(fixp(un[k], E) + fixp(um[k], E), bf);     // |V| <= 2^55: every digit within [-128, 128], exact
-        const size_t o = (size_t)b * P2 + e;
+    for (int p = 0; p < ND; ++p)
+        if (p < nd) {
+            uint2 w;
+            w.x = (uint32_t)bf[0][p] | ((uint32_t)bf[1][p] << 16);
+            w.y = (uint32_t)bf[2][p] | ((uint32_t)bf[3][p] << 16);
+            *(uint2*)(dV + p * plane + o) = w;
 #pragma unroll
-        for (int p = 0; p < ND; ++p)
-            if (p < nd) {
-                dV[p * plane + o] = bf[p];
-                dt[p][tx][jj] = bf[p];
-            }
-    }
+            for (int c = 0; c < 4; ++c) dt[p][4 * q + c][r] = bf[c][p];
+        }
     __syncthreads();
-    for (int ii = ty; ii < 32; ii += 8) {
-        const size_t o = ((size_t)b * Px + i0 + ii) * Py + j0 + tx;
+    // transposed: row i = i0 + r, columns j = j0 + 4q .. 4q + 3
+    const size_t ot = (size_t)b * P2 + (size_t)(i0 + r) * Py + j0 + 4 * q;
 #pragma unroll
-        for (int p = 0; p < ND; ++p)
-            if (p < nd) dVt[p * plane + o] = dt[p][ii][tx];
-    }
+    for (int p = 0; p < ND; ++p)
+        if (p < nd) {
+            const uint32_t* s2 = (const uint32_t*)&dt[p][r][4 * q];
+            *(uint2*)(dVt + p * plane + ot) = make_uint2(s2[0], s2[1]);
+        }
 }
 
 // Exact int64 -> FP64 conversion, round to nearest even, from integer operations (the conversion
@@ -157,18 +165,21 @@ __device__ __forceinline__ long long rshr(long long x, int k) {
 
 // rho for one 32 x 32 tile of pair b.  Z1 = T1[b][i][j] counts 2^{E+ex-50+zsx} and Z2 = T3[b][j][i]
 // counts 2^{E+ey-50+zsy} (V / 2^56 times the matrix over 2^e, in units of 2^{zs-52} with zs the
-// product's shift for its contraction length), fixed-point values count 2^{E-54}.  |Z| <= 2^58, so
-// (1,4,1) Z stays below 2^61, and both terms are halved at least once before they are added.  Writes rho (BF16 or TF32-rounded FP32), zero
-// outside the interior nodes, and one FP64 sum of rho^2 per block.
+// product's shift for its contraction length), du = fix(U_{n-1}) - fix(U_n) counts 2^{E-54}.
+// |Z| <= 2^58, so (1,4,1) Z stays below 2^61, and both terms are halved at least once before they
+// are added.  The mass stencil (1,4,1)_y (1,4,1)_x is applied separably (rows first, in shared
+// memory).  Writes rho (BF16 or TF32-rounded FP32), zero outside the interior nodes, and one FP64
+// sum of rho^2 per block.
 template <typename OT>
 __global__ void __launch_bounds__(256, 3) k_combine_int(
-    const long long* __restrict__ T1, const long long* __restrict__ T3, const double* __restrict__ U,
+    const long long* __restrict__ T1, const long long* __restrict__ T3, const long long* __restrict__ DU,
     const int* __restrict__ En, int n0, int Px, int Py, int nx, int ny, double cmass, int ex, int ey, int zsx, int zsy,
     const double* __restrict__ dt, int rank, const double* __restrict__ time_w, const double* __restrict__ bxn,
     const double* __restrict__ byn, OT* __restrict__ rout, long long rout_stride, double* __restrict__ partial) {
     __shared__ long long t1[32][35];      // Z1 rows i0.., columns j0-1 .. j0+32
     __shared__ long long t3[32][35];      // Z2 rows j0.., columns i0-1 .. i0+32
-    __shared__ long long du[34][35];      // fix(U_{n-1}) - fix(U_n), rows j0-1.., columns i0-1..
+    __shared__ long long du[34][35];      // du, rows j0-1.., columns i0-1..
+    __shared__ long long rs[34][33];      // (1,4,1)_x du, rows j0-1.., columns i0..
     __shared__ double red[8];
     __shared__ double cst[2];             // c_m 2^{E-54}, -tau 2^u
     const int b = blockIdx.z, n = n0 + b;
@@ -180,10 +191,8 @@ __global__ void __launch_bounds__(256, 3) k_combine_int(
     // counts, register staging), so their latencies overlap
     const long long* T1b = T1 + (size_t)b * P2;
     const long long* T3b = T3 + (size_t)b * P2;
-    const unsigned long long* Un = (const unsigned long long*)(U + (size_t)n * P2);
-    const unsigned long long* Um = (const unsigned long long*)(U + (size_t)(n - 1) * P2);
-    long long a1[4][2], a3[4][2];
-    unsigned long long um[5][2], un[5][2];
+    const long long* DUb = DU + (size_t)b * P2;
+    long long a1[4][2], a3[4][2], ad[5][2];
 #pragma unroll
     for (int k = 0; k < 4; ++k)
 #pragma unroll
@@ -197,12 +206,10 @@ __global__ void __launch_bounds__(256, 3) k_combine_int(
     for (int k = 0; k < 5; ++k)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int r = ty + 8 * k, c = tx + 32 * h;
-            const int j = j0 + r - 1, i = i0 + c - 1;
-            const bool in = r < 34 && c < 34 && j >= 0 && j < Py && i >= 0 && i < Px;
-            const size_t e = in ? (size_t)j * Px + i : 0;
-            um[k][h] = in ? __ldg(Um + e) : 0ull;
-            un[k][h] = in ? __ldg(Un + e) : 0ull;
+            const int rr = ty + 8 * k, c = tx + 32 * h;
+            const int j = j0 + rr - 1, i = i0 + c - 1;
+            const bool in = rr < 34 && c < 34 && j >= 0 && j < Py && i >= 0 && i < Px;
+            ad[k][h] = in ? __ldg(DUb + (size_t)j * Px + i) : 0;     // zero outside the grid
         }
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -216,14 +223,16 @@ __global__ void __launch_bounds__(256, 3) k_combine_int(
     for (int k = 0; k < 5; ++k)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int r = ty + 8 * k, c = tx + 32 * h;
-            if (r < 34 && c < 34) du[r][c] = fixp(um[k][h], E) - fixp(un[k][h], E);   // fix(0) = 0
+            const int rr = ty + 8 * k, c = tx + 32 * h;
+            if (rr < 34 && c < 34) du[rr][c] = ad[k][h];
         }
     const int u1 = E + ex - 50 + zsx, u2 = E + ey - 50 + zsy, u = max(u1, u2) + 1;
     if (tx == 0 && ty == 0) {
         cst[0] = ldexp(cmass, E - 54);
         cst[1] = ldexp(-0.5 * dt[n - 1], u);
     }
+    __syncthreads();
+    for (int rr = ty; rr < 34; rr += 8) rs[rr][tx] = du[rr][tx] + 4 * du[rr][tx + 1] + du[rr][tx + 2];
     __syncthreads();
     const double cm = cst[0], cs = cst[1];
     const bool finite = E < 1024;
@@ -236,12 +245,7 @@ __global__ void __launch_bounds__(256, 3) k_combine_int(
             const long long k1 = t1[tx][jj] + 4 * t1[tx][jj + 1] + t1[tx][jj + 2];
             const long long k2 = t3[jj][tx] + 4 * t3[jj][tx + 1] + t3[jj][tx + 2];
             const long long st = rshr(k1, u - u1) + rshr(k2, u - u2);
-            long long s9 = 0;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const long long row = du[jj + a][tx] + 4 * du[jj + a][tx + 1] + du[jj + a][tx + 2];
-                s9 += a == 1 ? 4 * row : row;
-            }
+            const long long s9 = rs[jj][tx] + 4 * rs[jj + 1][tx] + rs[jj + 2][tx];
             double f = 0.0;
             for (int q = 0; q < rank; ++q)
                 f += time_w[(size_t)(n - 1) * rank + q] * byn[(size_t)q * Py + j] * bxn[(size_t)q * Px + i];
@@ -307,9 +311,11 @@ sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int cou
         const int n0 = n_first + b0;
         const long long plane = (long long)nb * Px * Py;
         dim3 grid(Px / 32, Py / 32, nb), block(32, 8);
+        long long* du = (long long*)c->T2;   // fix(U_{n-1}) - fix(U_n), int64 per element
         slot = sfde_prof_begin(c);
-        k_split_pair<<<grid, block, 0, c->stream>>>(U, En, n0, Px, Py, (uint16_t*)dV, (uint16_t*)dVt, plane, nd);
-        sfde_prof_end(c, slot, 5, 0.0, (16.0 + 4.0 * nd) * nxy * nb);   // U pair in, 2 x nd digit planes out
+        k_split_pair<<<grid, 256, 0, c->stream>>>(U, En, n0, Px, Py, (uint16_t*)dV, (uint16_t*)dVt, du, plane, nd);
+        // U pair in, 2 x nd digit planes and du out
+        sfde_prof_end(c, slot, 5, 0.0, (16.0 + 4.0 * nd + 8.0) * nxy * nb);
         sfde_count_launch(c);
         SFDE_TRY(sfde_oz_gemm_int(c, dV, plane, Py, Px, nb, Ax, (long long*)c->T1, (long long)P2, err, c->y.n,
                                   c->x.n, c->x.n, nd));
@@ -322,17 +328,17 @@ sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int cou
         slot = sfde_prof_begin(c);
         if (out_kind == 0)
             k_combine_int<__nv_bfloat16><<<grid, block, 0, c->stream>>>(
-                (const long long*)c->T1, (const long long*)c->T3, U, En, n0, Px, Py, c->x.n, c->y.n, cmass,
+                (const long long*)c->T1, (const long long*)c->T3, du, En, n0, Px, Py, c->x.n, c->y.n, cmass,
                 Ax.e_uniform, Ay.e_uniform, sfde_oz_int_shift(Px), sfde_oz_int_shift(Py), c->dt0, c->rank,
                 c->time_w, c->bxn, c->byn, (__nv_bfloat16*)ro,
                 rout_stride, partial + total);
         else
             k_combine_int<float><<<grid, block, 0, c->stream>>>(
-                (const long long*)c->T1, (const long long*)c->T3, U, En, n0, Px, Py, c->x.n, c->y.n, cmass,
+                (const long long*)c->T1, (const long long*)c->T3, du, En, n0, Px, Py, c->x.n, c->y.n, cmass,
                 Ax.e_uniform, Ay.e_uniform, sfde_oz_int_shift(Px), sfde_oz_int_shift(Py), c->dt0, c->rank,
                 c->time_w, c->bxn, c->byn, (float*)ro, rout_stride,
                 partial + total);
-        sfde_prof_end(c, slot, 5, 0.0, (16.0 + 16.0 + (double)esz) * nxy * nb);   // Z1, Z2, U pair in, rho out
+        sfde_prof_end(c, slot, 5, 0.0, (16.0 + 8.0 + (double)esz) * nxy * nb);   // Z1, Z2, du in, rho out
         sfde_count_launch(c);
         total += blocks;
     }
