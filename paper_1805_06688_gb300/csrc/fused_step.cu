@@ -50,15 +50,16 @@ template <int P, bool PAIR> struct Geo {
     static constexpr int NATOM = P / 64;           // K-atoms of 64 BF16
     static constexpr int ATOM = P * 128;           // bytes of one K-atom of a P-row operand
     static constexpr int DATA = NATOM * ATOM;      // the slice operand, P^2 BF16
-    // ring of fixed-matrix K-atoms: two whole atoms, or (pair) this CTA's half of all four, so that
-    // a phase's two passes over K load each atom once
+    // operand rows held by this CTA: all P, or (pair) its 128-row half, K-atoms of 16 KB
+    static constexpr int DATA_L = PAIR ? NATOM * HALF_BYTES : DATA;
+    // ring of fixed-matrix K-atoms: two whole atoms, or (pair) this CTA's half of all four
     static constexpr int OSTAGES = PAIR ? NATOM : 2;
     static constexpr int OSTAGE = PAIR ? HALF_BYTES : ATOM;
     static constexpr int RING = OSTAGES * OSTAGE;
     static constexpr int TMEM_COLS = NHL * P;      // 128, 512, or 256 (pair)
     static constexpr int STAGE_ROW = P / 2 * 4;    // FP32 output staging: bytes per half-row
-    static constexpr int SMEM = 1024 + DATA + RING + 128 + 2 * P * 4 + 128;
-    static_assert(NDRAIN * 32 * STAGE_ROW <= DATA + RING, "output staging must fit in the operand space");
+    static constexpr int SMEM = 1024 + DATA_L + RING + 128 + 2 * P * 4 + 128;
+    static_assert(NDRAIN * 32 * STAGE_ROW <= DATA_L + RING, "output staging must fit in the operand space");
     static_assert(!PAIR || P == 256, "pair form: two 128-row halves");
     static_assert(2 * OSTAGES + 6 <= 16, "barrier block");
 };
@@ -114,17 +115,18 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
     using G = Geo<P, PAIR>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* sD = smem;                                  // slice operand (Data)
-    uint8_t* sO = smem + G::DATA;                        // ring of fixed-matrix K-atoms (Op)
+    uint8_t* sD = smem;                                  // slice operand (Data), this CTA's rows
+    uint8_t* sO = smem + G::DATA_L;                      // ring of fixed-matrix K-atoms (Op)
     uint64_t* bar = (uint64_t*)(sO + G::RING);
+    // pair: the even CTA's ofull, dfull, dready count both CTAs' loads and drains (its MMA thread
+    // issues the products of the pair); oempty and accf are signalled to both CTAs
     uint64_t* ofull = bar;                               // [OSTAGES] Op atom landed
     uint64_t* oempty = bar + G::OSTAGES;                 // [OSTAGES] Op atom consumed
     uint64_t* dfull = bar + 2 * G::OSTAGES;              // U landed
     uint64_t* dready = dfull + 1;                        // the next Data written by the drain warps
-    uint64_t* accf = dfull + 2;                          // a phase's products complete (pair: both CTAs')
+    uint64_t* accf = dfull + 2;                          // a phase's products complete
     uint64_t* fin = dfull + 3;                           // error path: outstanding products complete
-    uint64_t* rfull = dfull + 4;                         // pair: the peer's half of the next Data landed
-    uint32_t* tmem_slot = (uint32_t*)(dfull + 5);
+    uint32_t* tmem_slot = (uint32_t*)(dfull + 4);
     float* s_lx = (float*)(bar + 16);                    // K_x lambda_x[a], P floats
     float* s_ly = s_lx + P;                              // K_y lambda_y[q]
     double* red = (double*)(s_ly + P);                   // NDRAIN partial sums
@@ -138,10 +140,9 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
     if (threadIdx.x == 0) {
         for (int s = 0; s < G::OSTAGES; ++s) { tc::mbar_init(&ofull[s], 1); tc::mbar_init(&oempty[s], 1); }
         tc::mbar_init(dfull, 1);
-        tc::mbar_init(dready, 32 * NDRAIN);
-        tc::mbar_init(accf, PAIR ? 2 : 1);
+        tc::mbar_init(dready, (PAIR ? 2 : 1) * 32 * NDRAIN);
+        tc::mbar_init(accf, 1);
         tc::mbar_init(fin, 1);
-        tc::mbar_init(rfull, 1);
         tc::mbar_fence_init();
     }
     for (int i = threadIdx.x; i < P; i += THREADS) {
@@ -149,7 +150,10 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
         s_ly[i] = p.ky * p.lamy[i];
     }
     if (threadIdx.x < NDRAIN) red[threadIdx.x] = 0.0;
-    if (warp == 0) tc::tmem_alloc(tmem_slot, G::TMEM_COLS);
+    if (warp == 0) {
+        if constexpr (PAIR) tc::tmem_alloc_pair(tmem_slot, G::TMEM_COLS);
+        else tc::tmem_alloc(tmem_slot, G::TMEM_COLS);
+    }
     // pair: the peer's barriers are initialised before either CTA signals the other
     if constexpr (PAIR) tc::cluster_sync();
     else __syncthreads();
@@ -163,13 +167,20 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
 
     if (warp == NDRAIN) {
         const int s = p.s0 + b * p.ds;
+        // pair: every load of either CTA completes on the even CTA's barrier
+        const uint32_t lead_dfull = PAIR ? tc::mapa_shared(tc::smem_u32(dfull), 0u) : 0u;
         if (lane == 0) {
             tc::prefetch_tmap(&mapU);
-            tc::mbar_arrive_expect_tx(dfull, (uint32_t)G::DATA);
+            if (rk == 0) tc::mbar_arrive_expect_tx(dfull, (uint32_t)G::DATA);
             for (int t = 0; t < G::NATOM; ++t)
-                for (int h = 0; h < G::NH; ++h)
-                    tc::tma_load_4d(sD + t * G::ATOM + h * HALF_BYTES, &mapU, dfull, t * 64, h * 128, p.s0 % p.ds,
-                                    s / p.ds);
+                for (int h = 0; h < G::NHL; ++h) {
+                    if constexpr (PAIR)
+                        tc::tma_load_4d_pair(sD + t * HALF_BYTES, &mapU, lead_dfull, t * 64, 128 * rk, p.s0 % p.ds,
+                                             s / p.ds);
+                    else
+                        tc::tma_load_4d(sD + t * G::ATOM + h * HALF_BYTES, &mapU, dfull, t * 64, h * 128,
+                                        p.s0 % p.ds, s / p.ds);
+                }
         }
         __syncwarp();
         // the right-hand sides of the first two steps and u_target are read only by late drains:
@@ -187,20 +198,29 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                 const int st = gi % G::OSTAGES, use = gi / G::OSTAGES;
                 if (gi >= G::OSTAGES) ok = tc::mbar_wait(&oempty[st], (uint32_t)(use - 1) & 1u, p.err, tc::ERR_WAIT_EMPTY);
                 if (!ok) break;
-                tc::mbar_arrive_expect_tx(&ofull[st], (uint32_t)G::OSTAGE);
-                // pair: rows 128 rk.. of the matrix (a map with 128-row boxes)
-                tc::tma_load_2d(sO + st * G::OSTAGE, maps[(gi / G::NATOM) & 3], &ofull[st], (gi % G::NATOM) * 64,
-                                PAIR ? 128 * rk : 0);
+                if constexpr (PAIR) {
+                    // rows 128 rk.. of the matrix (a map with 128-row boxes)
+                    if (rk == 0) tc::mbar_arrive_expect_tx(&ofull[st], (uint32_t)(2 * G::OSTAGE));
+                    tc::tma_load_2d_pair(sO + st * G::OSTAGE, maps[(gi / G::NATOM) & 3],
+                                         tc::mapa_shared(tc::smem_u32(&ofull[st]), 0u), (gi % G::NATOM) * 64, 128 * rk);
+                } else {
+                    tc::mbar_arrive_expect_tx(&ofull[st], (uint32_t)G::OSTAGE);
+                    tc::tma_load_2d(sO + st * G::OSTAGE, maps[(gi / G::NATOM) & 3], &ofull[st], (gi % G::NATOM) * 64, 0);
+                }
                 ++issued;
             }
-            // own copies in flight must land before the CTA's shared memory goes away
-            tc::mbar_wait(dfull, 0, p.err, tc::ERR_WAIT_FULL);
-            for (int gi = issued - G::OSTAGES < 0 ? 0 : issued - G::OSTAGES; gi < issued; ++gi)
-                tc::mbar_wait(&ofull[gi % G::OSTAGES], (uint32_t)(gi / G::OSTAGES) & 1u, p.err, tc::ERR_WAIT_FULL);
+            // own copies in flight must land before the CTA's shared memory goes away (pair: the
+            // even CTA waits for both CTAs' loads, and the odd CTA stays until the even one has)
+            if (rk == 0) {
+                tc::mbar_wait(dfull, 0, p.err, tc::ERR_WAIT_FULL);
+                for (int gi = issued - G::OSTAGES < 0 ? 0 : issued - G::OSTAGES; gi < issued; ++gi)
+                    tc::mbar_wait(&ofull[gi % G::OSTAGES], (uint32_t)(gi / G::OSTAGES) & 1u, p.err, tc::ERR_WAIT_FULL);
+            }
         }
     } else if (warp == NDRAIN + 1) {
-        if (lane == 0) {
-            bool ok = tc::mbar_wait(dfull, 0, p.err, tc::ERR_WAIT_FULL);
+        if (lane == 0 && rk == 0) {
+            bool ok = PAIR ? tc::mbar_wait_cluster(dfull, 0, p.err, tc::ERR_WAIT_FULL)
+                           : tc::mbar_wait(dfull, 0, p.err, tc::ERR_WAIT_FULL);
             bool any = false;
             if constexpr (!PAIR) {
                 const uint32_t idesc = tc::idesc_f32acc(1u, 128, P);
@@ -228,50 +248,36 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                     }
                     if (ok) tc::mma_commit(accf);
                 }
-            } else {
-                // rows 128 rk.. of D = Op Data^T in two passes over K: output columns (Data rows) of
-                // this CTA's half, written by its own drain, then those of the peer's half, sent by
-                // the peer.  Accumulator columns n = Data row n (256 columns).
-                const uint32_t idesc = tc::idesc_f32acc(1u, 128, 128);
-                // rfull phase i brings the peer's half of the Data of product i + 1; `armed`: the
-                // expectation of the phase that has not been waited for yet
-                bool armed = false;
-                if (nphase > 1) { tc::mbar_arrive_expect_tx(rfull, (uint32_t)(G::DATA / 2)); armed = true; }
-                int rphase = 0;
+            } else if (rk == 0) {
+                // the pair's products: D = Op Data^T, M = 256 (rows 128 r.. of Op and of D in CTA r),
+                // N = 256 (Data rows 128 r.. in CTA r); each CTA's drain writes exactly its own Data
+                // rows, so nothing is exchanged
+                const uint32_t idesc = tc::idesc_f32acc(1u, 256, 256);
                 for (int ph = 0; ph < nphase && ok; ++ph) {
-                    if (ph > 0) ok = tc::mbar_wait(dready, (uint32_t)(ph - 1) & 1u, p.err, tc::ERR_WAIT_FULL);
+                    // both CTAs' drains of phase ph - 1
+                    if (ph > 0) ok = tc::mbar_wait_cluster(dready, (uint32_t)(ph - 1) & 1u, p.err, tc::ERR_WAIT_FULL);
                     if (!ok) break;
                     tc::tc_fence_after();
-                    for (int pass = 0; pass < 2 && ok; ++pass) {
-                        const int hn = pass == 0 ? rk : 1 - rk;     // Data rows 128 hn..
-                        if (pass == 1 && ph > 0) {
-                            ok = tc::mbar_wait(rfull, (uint32_t)rphase & 1u, p.err, tc::ERR_WAIT_FULL);
-                            if (!ok) break;
-                            armed = false;
-                            ++rphase;
-                            tc::tc_fence_after();
-                            if (ph + 1 < nphase) { tc::mbar_arrive_expect_tx(rfull, (uint32_t)(G::DATA / 2)); armed = true; }
-                        }
-                        for (int t = 0; t < G::NATOM && ok; ++t) {
-                            if (pass == 0) {
-                                ok = tc::mbar_wait(&ofull[t], (uint32_t)ph & 1u, p.err, tc::ERR_WAIT_FULL);
-                                if (!ok) break;
-                                tc::tc_fence_after();
-                            }
+                    for (int t = 0; t < G::NATOM && ok; ++t) {
+                        ok = tc::mbar_wait_cluster(&ofull[t], (uint32_t)ph & 1u, p.err, tc::ERR_WAIT_FULL);
+                        if (!ok) break;
+                        tc::tc_fence_after();
 #pragma unroll
-                            for (int kk = 0; kk < 4; ++kk) {
-                                const uint64_t ad = tc::smem_desc_sw128(sO + t * G::OSTAGE + kk * 32);
-                                const uint64_t bd = tc::smem_desc_sw128(sD + t * G::ATOM + hn * HALF_BYTES + kk * 32);
-                                tc::mma<0>(tmem + (uint32_t)(hn * 128), ad, bd, idesc, (t > 0 || kk > 0) ? 1u : 0u);
-                            }
-                            any = true;
-                            if (pass == 1) tc::mma_commit(&oempty[t]);
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t ad = tc::smem_desc_sw128(sO + t * G::OSTAGE + kk * 32);
+                            const uint64_t bd = tc::smem_desc_sw128(sD + t * HALF_BYTES + kk * 32);
+                            tc::mma_pair(tmem, ad, bd, idesc, (t > 0 || kk > 0) ? 1u : 0u);
                         }
+                        any = true;
+                        tc::mma_commit_pair_mc(&oempty[t], (uint16_t)3u);
                     }
-                    if (ok) tc::mma_commit_mc(accf, (uint16_t)3u);
+                    if (ok) tc::mma_commit_pair_mc(accf, (uint16_t)3u);
                 }
-                // error path: a copy the peer may still send must land before shared memory goes away
-                if (!ok && armed) tc::mbar_wait(rfull, (uint32_t)rphase & 1u, p.err, tc::ERR_WAIT_FULL);
+                if (!ok && any) {  // products still running must finish before TMEM is freed
+                    tc::mma_commit_pair(fin);
+                    tc::mbar_wait(fin, 0, p.err, tc::ERR_WAIT_ACC);
+                }
+                any = false;
             }
             if (!ok && any) {  // products still running must finish before TMEM is freed
                 tc::mma_commit(fin);
@@ -288,6 +294,11 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
         double sq = 0.0;
         bool ok = true;
         const uint32_t sD_u = tc::smem_u32(sD);
+        // byte offset of Data row `row` (a row of this CTA), column k in sD
+        auto dofs = [&](int row, int k) -> uint32_t {
+            if constexpr (PAIR) return sw128<128>(row - 128 * rk, k);
+            else return sw128<P>(row, k);
+        };
         // accumulator columns are read 32 at a time (the register budget of ten warps)
         constexpr int CH = 32;
         // right-hand side of a chained step, CH columns of this thread's row, loaded one chunk ahead
@@ -337,7 +348,7 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                         }
 #pragma unroll
                         for (int u = 0; u < CH / 8; ++u)
-                            st_shared_v4(sD_u + sw128<P>(row, cb + c0 + 8 * u), pack_bf16x2(x[8 * u], x[8 * u + 1]),
+                            st_shared_v4(sD_u + dofs(row, cb + c0 + 8 * u), pack_bf16x2(x[8 * u], x[8 * u + 1]),
                                          pack_bf16x2(x[8 * u + 2], x[8 * u + 3]), pack_bf16x2(x[8 * u + 4], x[8 * u + 5]),
                                          pack_bf16x2(x[8 * u + 6], x[8 * u + 7]));
                     }
@@ -361,7 +372,7 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                             float x[8];
 #pragma unroll
                             for (int q = 0; q < 8; ++q) x[q] = __uint_as_float(v[8 * u + q]) + gf[q];
-                            st_shared_v4(sD_u + sw128<P>(row, cb + c0 + 8 * u), pack_bf16x2(x[0], x[1]),
+                            st_shared_v4(sD_u + dofs(row, cb + c0 + 8 * u), pack_bf16x2(x[0], x[1]),
                                          pack_bf16x2(x[2], x[3]), pack_bf16x2(x[4], x[5]), pack_bf16x2(x[6], x[7]));
                         }
                     }
@@ -439,21 +450,11 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                 // generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 tc::tc_fence_before();
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(dready)) : "memory");
-                if constexpr (PAIR) {
-                    // this warp's part of the next Data (rows 128 rk + 32 lq.., K-atoms of columns
-                    // cb..: 4 KB each) to the same place in the peer's copy, as soon as the warp has
-                    // written it
-                    __syncwarp();
-                    if (lane == 0) {
-                        const uint32_t peer = (uint32_t)(1 - rk);
-                        const uint32_t rbar = tc::mapa_shared(tc::smem_u32(rfull), peer);
-#pragma unroll
-                        for (int t = cb / 64; t < (cb + CW) / 64; ++t) {
-                            const uint32_t src = sD_u + (uint32_t)(t * G::ATOM + rk * HALF_BYTES + lq * 4096);
-                            tc::bulk_copy_to_cluster(tc::mapa_shared(src, peer), src, 4096u, rbar);
-                        }
-                    }
+                if (rk == 0) {
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(dready)) : "memory");
+                } else {
+                    // pair: the odd CTA's rows are read by the even CTA's products
+                    tc::mbar_arrive_cluster(tc::mapa_shared(tc::smem_u32(dready), 0u));
                 }
             }
             if (ph == 3 && !last) {
@@ -470,7 +471,7 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                         uint4 o;
                         asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
                                      : "=r"(o.x), "=r"(o.y), "=r"(o.z), "=r"(o.w)
-                                     : "r"(sD_u + sw128<P>(row, col)) : "memory");
+                                     : "r"(sD_u + dofs(row, col)) : "memory");
                         *(uint4*)(dst + (size_t)row * P + col) = o;
                     }
                 }
@@ -505,7 +506,8 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
     }
     if (warp == 0) {
         tc::tc_fence_after();
-        tc::tmem_dealloc(tmem, G::TMEM_COLS);
+        if constexpr (PAIR) tc::tmem_dealloc_pair(tmem, G::TMEM_COLS);
+        else tc::tmem_dealloc(tmem, G::TMEM_COLS);
     }
 }
 
