@@ -72,11 +72,12 @@ sfde_status sfde_debug_set_resid_chunk(sfde_ctx* ctx, int n);
 sfde_status sfde_debug_set_fused_step(sfde_ctx* ctx, int enable);
 
 /*
- * How the fused kernel spreads a slice over the GPU (P_x = P_y = 256): 0 one CTA per slice, 1
- * (default) a cluster of two CTAs per slice -- each computing half the rows of every product and
- * exchanging its half of each intermediate through distributed shared memory -- when twice the
- * number of slices of a launch fits on the SMs, 2 always the pair.  The two forms give identical
- * results.  Takes effect at the next mgrit_solve or debug step.
+ * How the fused kernel spreads slices over the GPU (P_x = P_y = 256): 0 one CTA per slice; 1
+ * (default) a CTA pair per slice (each CTA holding half the rows of every operand, the products
+ * issued over the pair) when twice the number of slices of a launch fits on the SMs, else a CTA
+ * pair per two slices (one slice's products run while the other's accumulator is drained); 2 always
+ * a pair per slice; 3 always a pair per two slices.  All forms give identical results.  Takes effect
+ * at the next mgrit_solve or debug step.
  */
 sfde_status sfde_debug_set_fused_pair(sfde_ctx* ctx, int mode);
 

@@ -288,13 +288,16 @@ struct LpEngine {
             a.lamx = M->lamx; a.lamy = M->lamy; a.kx = (float)c->kx; a.ky = (float)c->ky;
             a.dt = dt; a.n0 = n0; a.dn = dn; a.scheme = solve ? SCHEME_SOLVE : sch;
             a.err = M->err;
-            // two CTAs per slice where the slices leave SMs idle (or when forced)
-            const bool pair = M->pair_ok && (c->fused_pair == 2 || (c->fused_pair == 1 && 2 * batch <= M->nsm));
-            if (pair)
-                SFDE_TRY(sfde_fused_step(c, Px, true, a1, solve ? M->hVTx : M->hWTx, solve ? M->hVTy : M->hWTy,
+            // a CTA pair per slice where the slices leave SMs idle, else a pair per two slices (one
+            // slice's products run while the other drains); one CTA per slice when pairs are off
+            int form = 0;
+            if (M->pair_ok && c->fused_pair != 0)
+                form = c->fused_pair == 2 ? 1 : c->fused_pair == 3 ? 2 : (2 * batch <= M->nsm ? 1 : 2);
+            if (form)
+                SFDE_TRY(sfde_fused_step(c, Px, form, a1, solve ? M->hVTx : M->hWTx, solve ? M->hVTy : M->hWTy,
                                          M->hVx, M->hVy, a, c->stream));
             else
-                SFDE_TRY(sfde_fused_step(c, Px, false, a1, solve ? M->mVTx : M->mWTx, solve ? M->mVTy : M->mWTy,
+                SFDE_TRY(sfde_fused_step(c, Px, 0, a1, solve ? M->mVTx : M->mWTx, solve ? M->mVTy : M->mWTy,
                                          M->mVx, M->mVy, a, c->stream));
             steps += (long long)batch * nchain;
             if (npart) *npart = batch;
@@ -661,7 +664,7 @@ extern "C" sfde_status sfde_debug_set_resid_chunk(sfde_ctx* c, int n) {
 }
 
 extern "C" sfde_status sfde_debug_set_fused_pair(sfde_ctx* c, int mode) {
-    if (!c || mode < 0 || mode > 2) return SFDE_EINVAL;
+    if (!c || mode < 0 || mode > 3) return SFDE_EINVAL;
     c->fused_pair = mode;
     return SFDE_OK;
 }

@@ -103,7 +103,8 @@ struct sfde_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     struct SfdeMixed* mixed = nullptr;  // tensor-core operands and inner hierarchy (mixed.cu)
     int fused_step = 1;         // BF16 steps as one fused kernel where the padded sizes allow it
-    int fused_pair = 1;         // fused steps on two CTAs per slice: 0 never, 1 when 2 batch <= SMs, 2 always
+    int fused_pair = 1;         // fused step form: 0 one CTA per slice, 1 auto (a CTA pair per slice when
+                                // 2 batch <= SMs, else per two slices), 2 pair per slice, 3 pair per two slices
     int resid_digits = 0;       // digits of the tensor-core residual: 0 per iteration, else 4..7 fixed
     int resid_chunk = 0;        // time points per pass of the tensor-core residual (0: ws_slices)
     SfdeProf prof;
@@ -193,9 +194,10 @@ inline int sfde_mixed_kind(const sfde_ctx* c) {
 }
 sfde_status sfde_fused_prepare();
 // O1, O2: W_x^T, W_y^T (V_x^T, V_y^T for the solve); O3, O4: V_x, V_y -- K-major P x P BF16 maps
-// with boxes of 64 x P (one CTA per slice) or 64 x 128 (pair: two CTAs per slice, P = 256).
+// with boxes of 64 x P (form 0: one CTA per slice) or 64 x 128 (P = 256, a CTA pair per one slice,
+// form 1, or per two slices, form 2).
 bool sfde_fused_pair_supported(int P);
-sfde_status sfde_fused_step(sfde_ctx* c, int P, bool pair, const CUtensorMap& U, const CUtensorMap& O1,
+sfde_status sfde_fused_step(sfde_ctx* c, int P, int form, const CUtensorMap& U, const CUtensorMap& O1,
                             const CUtensorMap& O2, const CUtensorMap& O3, const CUtensorMap& O4, const FusedStepArgs& a,
                             cudaStream_t s);
 
