@@ -163,13 +163,51 @@ __device__ __forceinline__ long long rshr(long long x, int k) {
     return (x + (1ll << (k - 1))) >> k;
 }
 
+// c = m 2^e exactly (normal c; m a signed integer of at most 53 bits), or m = 0
+__device__ __forceinline__ void split_double(double c, long long& m, int& e) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(c);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    if (ex == 0) { m = 0; e = 0; return; }
+    const long long mm = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+    m = (b >> 63) ? -mm : mm;
+    e = ex - 1075;
+}
+
+// round-to-nearest-even FP32 of x 2^e (x a 128-bit integer) from integer operations
+__device__ __forceinline__ float i128_to_f32(__int128 x, int e) {
+    if (x == 0) return 0.f;
+    const bool neg = x < 0;
+    const unsigned __int128 a = neg ? (unsigned __int128)0 - (unsigned __int128)x : (unsigned __int128)x;
+    const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+    const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+    unsigned int m;
+    int ex = 0;
+    if (msb <= 23) {
+        m = (unsigned int)lo;
+    } else {
+        const int sh = msb - 24;                                  // keep 24 bits and the round bit
+        const unsigned int m25 = (unsigned int)(a >> sh);
+        const bool sticky = (a & ((((unsigned __int128)1) << sh) - 1)) != 0;
+        m = m25 >> 1;
+        if ((m25 & 1u) && (sticky || (m & 1u))) ++m;                // m <= 2^24: exact in FP32
+        ex = sh + 1;
+    }
+    const float r = ldexpf((float)m, ex + e);
+    return neg ? -r : r;
+}
+
 // rho for one 32 x 32 tile of pair b.  Z1 = T1[b][i][j] counts 2^{E+ex-50+zsx} and Z2 = T3[b][j][i]
 // counts 2^{E+ey-50+zsy} (V / 2^56 times the matrix over 2^e, in units of 2^{zs-52} with zs the
 // product's shift for its contraction length), du = fix(U_{n-1}) - fix(U_n) counts 2^{E-54}.
 // |Z| <= 2^58, so (1,4,1) Z stays below 2^61, and both terms are halved at least once before they
 // are added.  The mass stencil (1,4,1)_y (1,4,1)_x is applied separably (rows first, in shared
-// memory).  Writes rho (BF16 or TF32-rounded FP32), zero outside the interior nodes, and one FP64
-// sum of rho^2 per block.
+// memory).  Without a load term rho = c_m S9 + c_s S is formed in integers: c_m and c_s are FP64
+// numbers, i.e. 53-bit integers times powers of two, so both products are exact 128-bit integers;
+// they are brought to a common power of two (exact unless the two units differ by more than 2^11,
+// when the finer term keeps its bits down to 2^-60 of the coarser unit, far below the fixed-point
+// grid's own resolution) and added, then rounded once to FP32 -- no FP64 arithmetic per element
+// (the FP64 pipe runs at about 1/64 of the FP32 rate).  With a load term the FP64 form is kept.  Writes rho (BF16 or TF32-rounded FP32),
+// zero outside the interior nodes, and one FP64 sum of rho^2 per block.
 template <typename OT>
 __global__ void __launch_bounds__(256, 3) k_combine_int(
     const long long* __restrict__ T1, const long long* __restrict__ T3, const long long* __restrict__ DU,
@@ -182,6 +220,8 @@ __global__ void __launch_bounds__(256, 3) k_combine_int(
     __shared__ long long rs[34][33];      // (1,4,1)_x du, rows j0-1.., columns i0..
     __shared__ double red[8];
     __shared__ double cst[2];             // c_m 2^{E-54}, -tau 2^u
+    __shared__ long long cmi[2];          // their integer mantissas (c = m 2^e)
+    __shared__ int csh[5];                // per term: left shift, right shift; common exponent
     const int b = blockIdx.z, n = n0 + b;
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -230,29 +270,45 @@ __global__ void __launch_bounds__(256, 3) k_combine_int(
     if (tx == 0 && ty == 0) {
         cst[0] = ldexp(cmass, E - 54);
         cst[1] = ldexp(-0.5 * dt[n - 1], u);
+        // |S9| < 2^61, |S| < 2^62, |m| < 2^53: products below 2^115, 12 bits of headroom in 128
+        int em, es;
+        split_double(cst[0], cmi[0], em);
+        split_double(cst[1], cmi[1], es);
+        const int ec = max(max(em, es) - 12, min(em, es));
+        csh[0] = max(em - ec, 0); csh[1] = min(max(ec - em, 0), 127);
+        csh[2] = max(es - ec, 0); csh[3] = min(max(ec - es, 0), 127);
+        csh[4] = ec;
     }
     __syncthreads();
     for (int rr = ty; rr < 34; rr += 8) rs[rr][tx] = du[rr][tx] + 4 * du[rr][tx + 1] + du[rr][tx + 2];
     __syncthreads();
     const double cm = cst[0], cs = cst[1];
+    const long long mm = cmi[0], ms = cmi[1];
+    const int lm = csh[0], rm = csh[1], ls = csh[2], rsd = csh[3], ec = csh[4];
     const bool finite = E < 1024;
     const int i = i0 + tx;
     float sq = 0.f;   // of the stored values; the norm only decides when the iteration stops
     for (int jj = ty; jj < 32; jj += 8) {
         const int j = j0 + jj;
-        double rho = 0.0;
+        float rf = 0.f;
         if (i < nx && j < ny) {
             const long long k1 = t1[tx][jj] + 4 * t1[tx][jj + 1] + t1[tx][jj + 2];
             const long long k2 = t3[jj][tx] + 4 * t3[jj][tx + 1] + t3[jj][tx + 2];
             const long long st = rshr(k1, u - u1) + rshr(k2, u - u2);
             const long long s9 = rs[jj][tx] + 4 * rs[jj + 1][tx] + rs[jj + 2][tx];
-            double f = 0.0;
-            for (int q = 0; q < rank; ++q)
-                f += time_w[(size_t)(n - 1) * rank + q] * byn[(size_t)q * Py + j] * bxn[(size_t)q * Px + i];
-            rho = fma(cm, i64_to_f64(s9), rank > 0 ? fma(cs, i64_to_f64(st), f) : cs * i64_to_f64(st));
-            if (!finite) rho = __longlong_as_double(0x7FF8000000000000ll);
+            if (rank > 0) {
+                double f = 0.0;
+                for (int q = 0; q < rank; ++q)
+                    f += time_w[(size_t)(n - 1) * rank + q] * byn[(size_t)q * Py + j] * bxn[(size_t)q * Px + i];
+                rf = (float)fma(cm, i64_to_f64(s9), fma(cs, i64_to_f64(st), f));
+            } else {
+                __int128 tm = (__int128)s9 * mm, ts = (__int128)st * ms;
+                tm = rm ? (tm >> rm) : (tm << lm);
+                ts = rsd ? (ts >> rsd) : (ts << ls);
+                rf = i128_to_f32(tm + ts, ec);
+            }
+            if (!finite) rf = __int_as_float(0x7FC00000);
         }
-        const float rf = (float)rho;
         sq = fmaf(rf, rf, sq);
         OT* o = rout + (size_t)b * rout_stride + (size_t)j * Px + i;
         if (sizeof(OT) == 2) *o = (OT)__float2bfloat16_rn(rf);
