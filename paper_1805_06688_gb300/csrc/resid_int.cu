@@ -209,7 +209,7 @@ __device__ __forceinline__ float i128_to_f32(__int128 x, int e) {
 // (the FP64 pipe runs at about 1/64 of the FP32 rate).  With a load term the FP64 form is kept.  Writes rho (BF16 or TF32-rounded FP32),
 // zero outside the interior nodes, and one FP64 sum of rho^2 per block.
 template <typename OT>
-__global__ void __launch_bounds__(256, 3) k_combine_int(
+__global__ void __launch_bounds__(256, 4) k_combine_int(
     const long long* __restrict__ T1, const long long* __restrict__ T3, const long long* __restrict__ DU,
     const int* __restrict__ En, int n0, int Px, int Py, int nx, int ny, double cmass, int ex, int ey, int zsx, int zsy,
     const double* __restrict__ dt, int rank, const double* __restrict__ time_w, const double* __restrict__ bxn,
