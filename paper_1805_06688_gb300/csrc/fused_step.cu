@@ -58,12 +58,14 @@ template <int P, bool PAIR, int SPP> struct Geo {
     static constexpr int OSTAGE = PAIR ? HALF_BYTES : ATOM;
     static constexpr int RING = OSTAGES * OSTAGE;
     static constexpr int TMEM_COLS = SPP * NHL * P;   // 128, 512, 256 (pair) or 512 (pair, two slices)
+    // pair per slice: the right-hand side of a chained step, this CTA's rows, staged by TMA
+    static constexpr int GSTAGE = (PAIR && SPP == 1) ? DATA_L : 0;
     static constexpr int STAGE_ROW = P / 2 * 4;    // FP32 output staging: bytes per half-row
-    static constexpr int SMEM = 1024 + SPP * DATA_L + RING + 128 + 2 * P * 4 + SPP * NDRAIN * 8 + 64;
+    static constexpr int SMEM = 1024 + SPP * DATA_L + RING + GSTAGE + 192 + 2 * P * 4 + SPP * NDRAIN * 8 + 64;
     static_assert(SPP == 2 || NDRAIN * 32 * STAGE_ROW <= DATA_L + RING,
                   "output staging must fit in the operand space");
     static_assert(!PAIR || P == 256, "pair form: two 128-row halves");
-    static_assert(2 * OSTAGES + 3 * SPP + 1 <= 15, "barrier block");
+    static_assert(2 * OSTAGES + 3 * SPP + 3 <= 23, "barrier block");
 };
 
 // byte offset of element (row r, column k) in a K-major, 128-byte-swizzled P-row operand:
@@ -113,13 +115,14 @@ template <int P, bool PAIR, int SPP>
 __global__ void __launch_bounds__(THREADS, 1)
 k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ CUtensorMap mO1,
              const __grid_constant__ CUtensorMap mO2, const __grid_constant__ CUtensorMap mO3,
-             const __grid_constant__ CUtensorMap mO4, FusedStepArgs p) {
+             const __grid_constant__ CUtensorMap mO4, const __grid_constant__ CUtensorMap mapG, FusedStepArgs p) {
     using G = Geo<P, PAIR, SPP>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sD0 = smem;                                 // slice operands (Data), this CTA's rows, G::DATA_L each
     uint8_t* sO = smem + SPP * G::DATA_L;                // ring of fixed-matrix K-atoms (Op)
-    uint64_t* bar = (uint64_t*)(sO + G::RING);
+    uint8_t* sG = sO + G::RING;                          // pair per slice: staged right-hand side
+    uint64_t* bar = (uint64_t*)(sG + G::GSTAGE);
     // pair: the even CTA's ofull, dfull, dready count both CTAs' loads and drains (its MMA thread
     // issues the products of the pair); oempty and accf are signalled to both CTAs
     uint64_t* ofull = bar;                               // [OSTAGES] Op atom landed
@@ -128,8 +131,10 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
     uint64_t* dready = dfull + SPP;                      // [SPP] the next Data written by the drain warps
     uint64_t* accf = dready + SPP;                       // [SPP] a phase's products complete
     uint64_t* fin = accf + SPP;                          // error path: outstanding products complete
-    uint32_t* tmem_slot = (uint32_t*)(bar + 15);
-    float* s_lx = (float*)(bar + 16);                    // K_x lambda_x[a], P floats
+    uint64_t* gfull = fin + 1;                           // staged right-hand side landed
+    uint64_t* gfree = fin + 2;                           // staged right-hand side consumed
+    uint32_t* tmem_slot = (uint32_t*)(bar + 23);
+    float* s_lx = (float*)(bar + 24);                    // K_x lambda_x[a], P floats
     float* s_ly = s_lx + P;                              // K_y lambda_y[q]
     double* red = (double*)(s_ly + P);                   // [SPP][NDRAIN] partial sums
 
@@ -140,6 +145,7 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
     const int ns = min(SPP, p.batch - b0);
     const int nchain = p.nchain;
     const int nphase = 4 * nchain;                       // phases of all chained steps
+    const bool gstage = G::GSTAGE > 0 && p.g_tma && p.g && nchain > 1;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < G::OSTAGES; ++s) { tc::mbar_init(&ofull[s], 1); tc::mbar_init(&oempty[s], 1); }
@@ -149,6 +155,8 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
             tc::mbar_init(&accf[s], 1);
         }
         tc::mbar_init(fin, 1);
+        tc::mbar_init(gfull, 1);
+        tc::mbar_init(gfree, NDRAIN);
         tc::mbar_fence_init();
     }
     for (int i = threadIdx.x; i < P; i += THREADS) {
@@ -305,6 +313,21 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                     tc::mbar_wait(fin, 0, p.err, tc::ERR_WAIT_ACC);
                 }
             }
+        } else if (gstage && lane == 1) {
+            // (an arm of its own: neither this loop nor the MMA issue waits for the other to finish)
+            // the right-hand side of chained step k (this CTA's 128 rows, 4 K-atoms of 16 KB), once
+            // the drain of step k - 1 has read the previous one; the last step reads g directly
+            bool ok = true;
+            int issued = 0;
+            for (int k = 0; k < nchain - 1 && ok; ++k) {
+                if (k > 0) ok = tc::mbar_wait(gfree, (uint32_t)(k - 1) & 1u, p.err, tc::ERR_WAIT_EMPTY);
+                if (!ok) break;
+                tc::mbar_arrive_expect_tx(gfull, (uint32_t)G::GSTAGE);
+                for (int t = 0; t < G::NATOM; ++t)
+                    tc::tma_load_4d(sG + t * HALF_BYTES, &mapG, gfull, t * 64, 128 * rk, 0, b0 * p.g_tds + k);
+                ++issued;
+            }
+            if (issued > 0) tc::mbar_wait(gfull, (uint32_t)(issued - 1) & 1u, p.err, tc::ERR_WAIT_FULL);
         }
     } else {
         // ---- warps 0-7: accumulator -> next Data operand (phases 1-3 of a step, and phase 4 of a
@@ -342,7 +365,9 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                 __nv_bfloat16* __restrict__ dst0 = dstsl(s);
                 const __nv_bfloat16* __restrict__ g = g0 ? g0 + (long long)k * p.g_kstride : nullptr;
                 const uint32_t sD_u = tc::smem_u32(sD0 + s * G::DATA_L);
-                if (ph == 3 && !last && g) load_g(g, 0, 0);
+                const bool gsm = gstage && ph == 3 && !last;    // g of this chained step staged in sG
+                if (ph == 3 && !last && g && !gsm) load_g(g, 0, 0);
+                if (gsm) ok = ok && __all_sync(0xffffffffu, tc::mbar_wait(gfull, (uint32_t)k & 1u, p.err, tc::ERR_WAIT_FULL));
                 ok = ok && __all_sync(0xffffffffu, tc::mbar_wait(&accf[s], (uint32_t)gph & 1u, p.err, tc::ERR_WAIT_ACC));
                 tc::tc_fence_after();
                 if (!ok) break;
@@ -387,11 +412,21 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                         // step's output; the output is copied to global memory after the next step starts
                         for (int c0 = 0; c0 < CW; c0 += CH) {
                             uint4 gv[CH / 8];
+                            if (gsm) {
+                                // staged: same 128-row swizzled layout as the operand (row - 128 rk)
+                                const uint32_t gb = tc::smem_u32(sG);
 #pragma unroll
-                            for (int u = 0; u < CH / 8; ++u) gv[u] = g ? gq[u] : make_uint4(0, 0, 0, 0);
-                            if (g) {
-                                if (c0 + CH < CW) load_g(g, h, c0 + CH);
-                                else if (h + 1 < G::NHL) load_g(g, h + 1, 0);
+                                for (int u = 0; u < CH / 8; ++u)
+                                    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                                                 : "=r"(gv[u].x), "=r"(gv[u].y), "=r"(gv[u].z), "=r"(gv[u].w)
+                                                 : "r"(gb + dofs(row, cb + c0 + 8 * u)) : "memory");
+                            } else {
+#pragma unroll
+                                for (int u = 0; u < CH / 8; ++u) gv[u] = g ? gq[u] : make_uint4(0, 0, 0, 0);
+                                if (g) {
+                                    if (c0 + CH < CW) load_g(g, h, c0 + CH);
+                                    else if (h + 1 < G::NHL) load_g(g, h + 1, 0);
+                                }
                             }
                             uint32_t v[CH];
                             tc::tmem_ld32(taddr + (uint32_t)c0, v);
@@ -524,6 +559,10 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                         tc::mbar_arrive_cluster(tc::mapa_shared(tc::smem_u32(&dready[s]), 0u));
                     }
                 }
+                if (gsm) {
+                    __syncwarp();
+                    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(gfree)) : "memory");
+                }
                 if (ph == 3 && !last) {
                     // while the next step's first product runs: copy this warp's part of the new Data
                     // (exactly this step's BF16 output) to global memory, coalesced half-rows, and bring
@@ -588,7 +627,8 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
 
 template <int P, bool PAIR, int SPP>
 sfde_status launch(sfde_ctx* c, const CUtensorMap& U, const CUtensorMap& O1, const CUtensorMap& O2,
-                   const CUtensorMap& O3, const CUtensorMap& O4, const FusedStepArgs& a, cudaStream_t s) {
+                   const CUtensorMap& O3, const CUtensorMap& O4, const CUtensorMap& Gm, const FusedStepArgs& a,
+                   cudaStream_t s) {
     const int slot = c ? sfde_prof_begin(c) : -1;
     if constexpr (PAIR) {
         cudaLaunchConfig_t cfg{};
@@ -603,9 +643,9 @@ sfde_status launch(sfde_ctx* c, const CUtensorMap& U, const CUtensorMap& O1, con
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        SFDE_CUDA(cudaLaunchKernelEx(&cfg, k_fused_step<P, PAIR, SPP>, U, O1, O2, O3, O4, a));
+        SFDE_CUDA(cudaLaunchKernelEx(&cfg, k_fused_step<P, PAIR, SPP>, U, O1, O2, O3, O4, Gm, a));
     } else {
-        k_fused_step<P, PAIR, SPP><<<a.batch, THREADS, Geo<P, PAIR, SPP>::SMEM, s>>>(U, O1, O2, O3, O4, a);
+        k_fused_step<P, PAIR, SPP><<<a.batch, THREADS, Geo<P, PAIR, SPP>::SMEM, s>>>(U, O1, O2, O3, O4, Gm, a);
     }
     if (c) {
         // per slice: the input once, the output and right-hand side of every chained step
@@ -638,19 +678,19 @@ sfde_status sfde_fused_prepare() {
 bool sfde_fused_pair_supported(int P) { return P == 256; }
 
 sfde_status sfde_fused_step(sfde_ctx* c, int P, int form, const CUtensorMap& U, const CUtensorMap& O1,
-                            const CUtensorMap& O2, const CUtensorMap& O3, const CUtensorMap& O4, const FusedStepArgs& a,
-                            cudaStream_t s) {
+                            const CUtensorMap& O2, const CUtensorMap& O3, const CUtensorMap& O4, const CUtensorMap& Gm,
+                            const FusedStepArgs& a, cudaStream_t s) {
     if (a.batch < 1) return SFDE_OK;
     if (!a.dst || !a.dt || !a.lamx || !a.lamy || !a.err || a.nchain < 1 || (a.ut && a.nchain != 1) ||
         a.batch > 65535 * 1024)
         return SFDE_EINVAL;
     if (((uintptr_t)a.dst | (uintptr_t)a.g | (uintptr_t)a.ut) & 15) return SFDE_EINVAL;
     if (form < 0 || form > 2 || (form > 0 && P != 256)) return SFDE_EINVAL;
-    if (P == 128) return launch<128, false, 1>(c, U, O1, O2, O3, O4, a, s);
+    if (P == 128) return launch<128, false, 1>(c, U, O1, O2, O3, O4, Gm, a, s);
     if (P == 256) {
-        if (form == 1) return launch<256, true, 1>(c, U, O1, O2, O3, O4, a, s);
-        if (form == 2) return launch<256, true, 2>(c, U, O1, O2, O3, O4, a, s);
-        return launch<256, false, 1>(c, U, O1, O2, O3, O4, a, s);
+        if (form == 1) return launch<256, true, 1>(c, U, O1, O2, O3, O4, Gm, a, s);
+        if (form == 2) return launch<256, true, 2>(c, U, O1, O2, O3, O4, Gm, a, s);
+        return launch<256, false, 1>(c, U, O1, O2, O3, O4, Gm, a, s);
     }
     return SFDE_EINVAL;
 }

@@ -293,12 +293,20 @@ struct LpEngine {
             int form = 0;
             if (M->pair_ok && c->fused_pair != 0)
                 form = c->fused_pair == 2 ? 1 : c->fused_pair == 3 ? 2 : (2 * batch <= M->nsm ? 1 : 2);
+            // pair per slice, chained with a right-hand side: g through a tensor map of its slices
+            // (slice b dn + k from g), staged in shared memory ahead of the drain that adds it
+            CUtensorMap gm = a1;
+            if (form == 1 && g && nchain > 1) {
+                SFDE_TRY(map_for(M, g, Py, Px, 1, (long long)(batch - 1) * dn + nchain, &gm));
+                a.g_tma = 1;
+                a.g_tds = dn;
+            }
             if (form)
                 SFDE_TRY(sfde_fused_step(c, Px, form, a1, solve ? M->hVTx : M->hWTx, solve ? M->hVTy : M->hWTy,
-                                         M->hVx, M->hVy, a, c->stream));
+                                         M->hVx, M->hVy, gm, a, c->stream));
             else
                 SFDE_TRY(sfde_fused_step(c, Px, 0, a1, solve ? M->mVTx : M->mWTx, solve ? M->mVTy : M->mWTy,
-                                         M->mVx, M->mVy, a, c->stream));
+                                         M->mVx, M->mVy, gm, a, c->stream));
             steps += (long long)batch * nchain;
             if (npart) *npart = batch;
             return SFDE_OK;

@@ -178,6 +178,9 @@ struct FusedStepArgs {
     long long dst_kstride;                //   k*dst_kstride (elements)
     const void* g; long long g_stride;    // added to the output (or nullptr); step k: + k*g_kstride
     long long g_kstride;
+    int g_tma;                            // pair per slice, chained: g also through the tensor map
+                                          //   of the g slices (slice b*g_tds + k), staged in shared memory
+    int g_tds;
     const void* ut; long long ut_stride;  // subtracted; sum of squares per slice into partial[b]
     double* partial;                      // batch entries (or nullptr)
     const float* lamx; const float* lamy; float kx, ky;
@@ -198,8 +201,8 @@ sfde_status sfde_fused_prepare();
 // form 1, or per two slices, form 2).
 bool sfde_fused_pair_supported(int P);
 sfde_status sfde_fused_step(sfde_ctx* c, int P, int form, const CUtensorMap& U, const CUtensorMap& O1,
-                            const CUtensorMap& O2, const CUtensorMap& O3, const CUtensorMap& O4, const FusedStepArgs& a,
-                            cudaStream_t s);
+                            const CUtensorMap& O2, const CUtensorMap& O3, const CUtensorMap& O4, const CUtensorMap& Gm,
+                            const FusedStepArgs& a, cudaStream_t s);
 
 // ---- FP64-accurate slice GEMM on the BF16 tensor cores (ozaki.cu)
 #define SFDE_OZ_DIGITS 6
