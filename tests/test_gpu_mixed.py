@@ -55,15 +55,16 @@ def test_mixed_manufactured(name, prec):
 
 @pytest.mark.parametrize("name,prec", PRECS)
 def test_mixed_sine_N255_Nt1024_full_size(name, prec):
-    """The benchmarked workload in the bench's configuration, against the exact sequential
-    solution at sampled time points (space-time max norm)."""
+    """The benchmarked workload in the bench's configuration (relative residual 1e-8), against the
+    exact sequential solution at sampled time points: space-time max-norm error <= 1e-8 of max|u|
+    (measured 3.7e-10)."""
     w = WORKLOADS["sine_N255_Nt1024"]
     t = w.t()
     psi = w.initial()
     P = sfde.Problem(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t, precision=prec)
     P.set_initial(psi)
     U = torch.zeros((w.nt + 1, w.ny, w.nx), dtype=torch.float64, device="cuda")
-    _, st = P.mgrit(U=U, m=w.m, max_levels=32, coarse=sfde.COARSE_AUTO, rel_tol=1e-10, max_iter=100)
+    _, st = P.mgrit(U=U, m=w.m, max_levels=32, coarse=sfde.COARSE_AUTO, rel_tol=1e-8, max_iter=100)
     assert st.converged
     O = osfde.SFDE(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t)
     keep = [1, 7, 8, 100, 513, 1024]
