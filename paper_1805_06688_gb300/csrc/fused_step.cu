@@ -18,14 +18,16 @@
 // L2 in 64-wide K-atoms through a two-stage ring.  Per step HBM sees U read once and X written once
 // (plus g and u_target), and one launch does what four did.
 //
-// Pair form (P = 256): a cluster of two CTAs shares each slice.  CTA r computes rows
-// 128r..128r+127 of every product (its half of the fixed matrix streams through its ring; the
-// accumulator takes 256 TMEM columns), drains them into its own copy of the next Data operand and
-// sends that half to the peer's copy with one bulk shared::cluster copy per K-atom.  Each CTA first
-// multiplies the Data half it wrote itself, then the half the peer sent, so the exchange overlaps
-// half of the next product; every product and drain takes half the time of the one-CTA form.  The
-// products' completion is signalled to both CTAs (multicast commit), so no drain overwrites Data
-// the peer's products still read.
+// Pair forms (P = 256, clusters of two CTAs, tcgen05.mma.cta_group::2): CTA r holds rows
+// 128r..128r+127 of every operand -- its half of each fixed matrix streams through its ring, its
+// half of the slice operand sits in its shared memory -- and the even CTA issues M = N = 256
+// products over the pair: rows 128r.. of D land in CTA r's TMEM, which are exactly the Data rows CTA
+// r must hold for the next product, so nothing is exchanged.  The loads and drains of both CTAs
+// complete on the even CTA's barriers; its commits reach both CTAs (multicast), so no drain
+// overwrites Data a product still reads.  With one slice per pair a chained step's right-hand side
+// is staged in shared memory by TMA; with two slices per pair (launches with more slices than half
+// the SMs) the phases of the two slices alternate, so one slice's products run while the other's
+// accumulator is drained.  All forms round the same sums in the same order.
 //
 // Roles: warps 0-7 drain the accumulator (warp w: TMEM lanes 32 (w % 4).. of every 128-row half,
 // one half of the columns; two drain warps per scheduler keep the drain from stalling on latency);

@@ -150,16 +150,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                  : "memory");
 }
 
-// As mma_commit, arriving on the mbarrier at the same shared-memory offset in every CTA of the
-// cluster whose bit is set in cta_mask.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t cta_mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
-        "h"(cta_mask)
-        : "memory");
-}
-
 // ---- CTA pairs (cta_group::2): one MMA over two SMs.  Rows 0..127 of A and of D in the even CTA
 // of the pair, rows 128..255 in the odd one; B split along N the same way; every operand at the
 // same shared-memory / TMEM address in both CTAs.  Both CTAs allocate and free the TMEM together;
@@ -267,16 +257,6 @@ __device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
 // form, so that warps need not be converged)
 __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
-}
-
-// bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from this CTA's shared memory
-// to a shared::cluster address; completes as transaction bytes on the mbarrier at `mbar` (a
-// shared::cluster address in the destination CTA)
-__device__ __forceinline__ void bulk_copy_to_cluster(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t mbar) {
-    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     dst),
-                 "r"(src), "r"(bytes), "r"(mbar)
-                 : "memory");
 }
 
 __device__ __forceinline__ double ld_cluster_f64(uint32_t addr) {
