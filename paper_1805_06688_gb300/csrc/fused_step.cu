@@ -444,40 +444,66 @@ k_fused_step(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ C
                             }
                         }
                     } else if constexpr (SPP == 2) {
-                        // last step, two slices per pair (the operand space holds the other slice, so
-                        // nothing is staged): X + g - u_target straight from the accumulator, one row
-                        // per thread, 16-byte pieces
+                        // last step, two slices per pair: staged in FP32 through this slice's own
+                        // operand space (free once its last products are done; the other slice's
+                        // stays in use), 64 columns per round, each warp reading back only what it
+                        // staged; then X + g - u_target written with coalesced accesses
+                        constexpr int HC = 64;                  // columns per round
+                        constexpr int SROW = HC * 4;            // staging bytes per row
+                        constexpr int CPR = HC / 8;             // 8-column chunks per row segment
+                        constexpr int UNR = 4;
+                        static_assert(NDRAIN * 32 * SROW <= G::DATA_L, "staging fits in one slice operand");
+                        const uint32_t stg = sD_u + (uint32_t)(warp * 32 * SROW);
+                        const int rbase = hh * 128 + lq * 32;
                         __nv_bfloat16* __restrict__ dst = dst0 + (long long)k * p.dst_kstride;
                         const bool want_sq = ut && p.partial;
                         float sqf = 0.f;
-                        for (int c0 = 0; c0 < CW; c0 += CH) {
-                            const size_t off = (size_t)row * P + cb + c0;
-                            uint4 gv[CH / 8], uv[CH / 8];
+                        for (int r2 = 0; r2 < CW / HC; ++r2) {
+                            const int cbase = cb + r2 * HC;
+                            for (int c0 = 0; c0 < HC; c0 += CH) {
+                                uint32_t v[CH];
+                                tc::tmem_ld32(taddr + (uint32_t)(r2 * HC + c0), v);
 #pragma unroll
-                            for (int u = 0; u < CH / 8; ++u) {
-                                gv[u] = g ? __ldg((const uint4*)(g + off + 8 * u)) : make_uint4(0, 0, 0, 0);
-                                uv[u] = ut ? __ldg((const uint4*)(ut + off + 8 * u)) : make_uint4(0, 0, 0, 0);
-                            }
-                            uint32_t v[CH];
-                            tc::tmem_ld32(taddr + (uint32_t)c0, v);
-#pragma unroll
-                            for (int u = 0; u < CH / 8; ++u) {
-                                float gf[8], uf[8], xf[8];
-                                bf16x8_to_f32(gv[u], gf);
-                                bf16x8_to_f32(uv[u], uf);
-#pragma unroll
-                                for (int q = 0; q < 8; ++q) xf[q] = __uint_as_float(v[8 * u + q]) + gf[q] - uf[q];
-                                if (want_sq) {
-#pragma unroll
-                                    for (int q = 0; q < 8; ++q) sqf = fmaf(xf[q], xf[q], sqf);
+                                for (int u = 0; u < CH / 4; ++u) {
+                                    const int ch = (c0 >> 2) + u;
+                                    st_shared_v4(stg + (uint32_t)(lane * SROW + ((ch ^ (lane & 7)) << 4)), v[4 * u],
+                                                 v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
                                 }
-                                uint4 o;
-                                o.x = pack_bf16x2(xf[0], xf[1]);
-                                o.y = pack_bf16x2(xf[2], xf[3]);
-                                o.z = pack_bf16x2(xf[4], xf[5]);
-                                o.w = pack_bf16x2(xf[6], xf[7]);
-                                *(uint4*)(dst + off + 8 * u) = o;
                             }
+                            __syncwarp();
+                            for (int i0 = 0; i0 < CPR; i0 += UNR) {   // 32 rows x CPR chunks over 32 lanes
+                                uint4 gv[UNR], uv[UNR];
+#pragma unroll
+                                for (int kk = 0; kk < UNR; ++kk) {
+                                    const int e = (i0 + kk) * 32 + lane, rr = e / CPR, cc = e % CPR;
+                                    const size_t off = (size_t)(rbase + rr) * P + cbase + cc * 8;
+                                    gv[kk] = g ? __ldg((const uint4*)(g + off)) : make_uint4(0, 0, 0, 0);
+                                    uv[kk] = ut ? __ldg((const uint4*)(ut + off)) : make_uint4(0, 0, 0, 0);
+                                }
+#pragma unroll
+                                for (int kk = 0; kk < UNR; ++kk) {
+                                    const int e = (i0 + kk) * 32 + lane, rr = e / CPR, cc = e % CPR;
+                                    const float4 x0 = ld_shared_f4(stg + (uint32_t)(rr * SROW + (((2 * cc) ^ (rr & 7)) << 4)));
+                                    const float4 x1 = ld_shared_f4(stg + (uint32_t)(rr * SROW + (((2 * cc + 1) ^ (rr & 7)) << 4)));
+                                    float xf[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                                    float gf[8], uf[8];
+                                    bf16x8_to_f32(gv[kk], gf);
+                                    bf16x8_to_f32(uv[kk], uf);
+#pragma unroll
+                                    for (int q = 0; q < 8; ++q) xf[q] += gf[q] - uf[q];
+                                    if (want_sq) {
+#pragma unroll
+                                        for (int q = 0; q < 8; ++q) sqf = fmaf(xf[q], xf[q], sqf);
+                                    }
+                                    uint4 o;
+                                    o.x = pack_bf16x2(xf[0], xf[1]);
+                                    o.y = pack_bf16x2(xf[2], xf[3]);
+                                    o.z = pack_bf16x2(xf[4], xf[5]);
+                                    o.w = pack_bf16x2(xf[6], xf[7]);
+                                    *(uint4*)(dst + (size_t)(rbase + rr) * P + cbase + cc * 8) = o;
+                                }
+                            }
+                            __syncwarp();
                         }
                         sq[s] += (double)sqf;
                     } else {
