@@ -61,11 +61,27 @@ __global__ void k_lp_axpy_strided(T* y, long long ys, const T* x, long long xs, 
         y[sl * ys + e] = to_lp<T>((double)lp_f(y[sl * ys + e]) + (double)lp_f(x[sl * xs + e]));
 }
 
-// U += E in FP64 for n elements (the refinement update)
+// U += E in FP64 for n elements (the refinement update), four per thread and iteration (n a
+// multiple of 4, U 16-byte and E 8-byte aligned: whole padded slices)
 template <typename T>
 __global__ void k_add_correction(double* U, const T* E, size_t n) {
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-        U[e] += (double)lp_f(E[e]);
+    const size_t n4 = n / 4;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += (size_t)gridDim.x * blockDim.x) {
+        double2* u = (double2*)(U + 4 * e);
+        double2 a = u[0], b = u[1];
+        float x0, x1, x2, x3;
+        if constexpr (sizeof(T) == 2) {
+            const uint2 w = __ldg((const uint2*)(E + 4 * e));
+            x0 = __uint_as_float(w.x << 16); x1 = __uint_as_float(w.x & 0xFFFF0000u);
+            x2 = __uint_as_float(w.y << 16); x3 = __uint_as_float(w.y & 0xFFFF0000u);
+        } else {
+            const float4 w = __ldg((const float4*)(E + 4 * e));
+            x0 = w.x; x1 = w.y; x2 = w.z; x3 = w.w;
+        }
+        a.x += (double)x0; a.y += (double)x1; b.x += (double)x2; b.y += (double)x3;
+        u[0] = a;
+        u[1] = b;
+    }
 }
 
 unsigned grid_for(size_t n) {
