@@ -232,6 +232,11 @@ sfde_status setup_mixed(sfde_ctx* c, int kind, int m, int max_levels, int min_co
     while ((int)M->lev.size() < max_levels) {
         const LpLevel& F = M->lev.back();
         if (F.N % m != 0 || F.N / m < min_coarse) break;
+        // a coarse level whose sequential sweep (N steps, one chained launch) is no longer than its
+        // own relaxation (FCF: 2m - 1 steps, C-point residual: 1, final F-relaxation: m - 1) plus
+        // the sweep of the level below is solved directly: the inner V-cycle's critical path gets
+        // shorter and its coarse solve exact
+        if (M->lev.size() > 1 && F.N <= 3 * m - 1 + F.N / m) break;
         LpLevel G;
         G.N = F.N / m;
         G.t.resize(G.N + 1);
@@ -424,6 +429,10 @@ struct LpEngine {
     sfde_status coarsest(int l) {
         LpLevel& Lv = M->lev[l];
         SFDE_CUDA(cudaMemcpyAsync(Lv.u, Lv.g, P2() * M->esz, cudaMemcpyDeviceToDevice, c->stream));
+        // u_n = Phi(u_{n-1}) + g_n, n = 1..N: the fused kernel chains all N steps in one launch
+        if (M->fused)
+            return step(Lv.u, Lv.nalloc, 0, 1, 1, false, l == 0 ? SCHEME_CN : scheme, Lv.dt, 1, 1, slice(Lv.u, 1), 1,
+                        slice(Lv.g, 1), nullptr, nullptr, nullptr, Lv.N);
         for (int n = 1; n <= Lv.N; ++n)
             SFDE_TRY(lstep(l, 1, n - 1, 1, n, 1, slice(Lv.u, n), 1, nullptr, nullptr, nullptr));
         return SFDE_OK;
