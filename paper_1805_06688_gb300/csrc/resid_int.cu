@@ -173,26 +173,15 @@ __device__ __forceinline__ void split_double(double c, long long& m, int& e) {
     e = ex - 1075;
 }
 
-// round-to-nearest-even FP32 of x 2^e (x a 128-bit integer) from integer operations
-__device__ __forceinline__ float i128_to_f32(__int128 x, int e) {
-    if (x == 0) return 0.f;
+// FP32 of x 2^e (x a 128-bit integer, 2^e = s1 s2 given as two FP32 powers of two) within 1.5 ulp:
+// |x| = hi 2^64 + lo with both halves converted (each rounded once, no cancellation: same sign) and
+// added by one FMA; the powers of two scale exactly unless the result leaves the normal range
+__device__ __forceinline__ float i128_to_f32(__int128 x, float s1, float s2) {
     const bool neg = x < 0;
     const unsigned __int128 a = neg ? (unsigned __int128)0 - (unsigned __int128)x : (unsigned __int128)x;
-    const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
-    const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
-    unsigned int m;
-    int ex = 0;
-    if (msb <= 23) {
-        m = (unsigned int)lo;
-    } else {
-        const int sh = msb - 24;                                  // keep 24 bits and the round bit
-        const unsigned int m25 = (unsigned int)(a >> sh);
-        const bool sticky = (a & ((((unsigned __int128)1) << sh) - 1)) != 0;
-        m = m25 >> 1;
-        if ((m25 & 1u) && (sticky || (m & 1u))) ++m;                // m <= 2^24: exact in FP32
-        ex = sh + 1;
-    }
-    const float r = ldexpf((float)m, ex + e);
+    const float hf = __ull2float_rn((unsigned long long)(a >> 64));
+    const float lf = __ull2float_rn((unsigned long long)a);
+    const float r = fmaf(hf, 18446744073709551616.0f, lf) * s1 * s2;
     return neg ? -r : r;
 }
 
@@ -202,11 +191,13 @@ __device__ __forceinline__ float i128_to_f32(__int128 x, int e) {
 // |Z| <= 2^58, so (1,4,1) Z stays below 2^61, and both terms are halved at least once before they
 // are added.  The mass stencil (1,4,1)_y (1,4,1)_x is applied separably (rows first, in shared
 // memory).  Without a load term rho = c_m S9 + c_s S is formed in integers: c_m and c_s are FP64
-// numbers, i.e. 53-bit integers times powers of two, so both products are exact 128-bit integers;
-// they are brought to a common power of two (exact unless the two units differ by more than 2^11,
-// when the finer term keeps its bits down to 2^-60 of the coarser unit, far below the fixed-point
-// grid's own resolution) and added, then rounded once to FP32 -- no FP64 arithmetic per element
-// (the FP64 pipe runs at about 1/64 of the FP32 rate).  With a load term the FP64 form is kept.  Writes rho (BF16 or TF32-rounded FP32),
+// numbers, i.e. 53-bit integers times powers of two.  Both are brought to a common power of two
+// 2^ec by shifting the mantissa of the coarser one left by up to 10 bits (below 2^63), so both
+// products are exact 128-bit integers below 2^126 with no shift per element (when the two units
+// differ by more than 2^10 the finer product is shifted right, keeping its bits down to 2^-62 of
+// the coarser unit, far below the fixed-point grid's own resolution), added exactly, and converted
+// to FP32 within 1.5 ulp -- no FP64 arithmetic per element (the FP64 pipe runs at about 1/64 of
+// the FP32 rate).  With a load term the FP64 form is kept.  Writes rho (BF16 or TF32-rounded FP32),
 // zero outside the interior nodes, and one FP64 sum of rho^2 per block.
 template <typename OT>
 __global__ void __launch_bounds__(256, 4) k_combine_int(
@@ -220,8 +211,9 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
     __shared__ long long rs[34][33];      // (1,4,1)_x du, rows j0-1.., columns i0..
     __shared__ double red[8];
     __shared__ double cst[2];             // c_m 2^{E-54}, -tau 2^u
-    __shared__ long long cmi[2];          // their integer mantissas (c = m 2^e)
-    __shared__ int csh[5];                // per term: left shift, right shift; common exponent
+    __shared__ long long cmi[2];          // their integer mantissas, shifted to the unit 2^ec
+    __shared__ int csh[2];                // per term: right shift of the product
+    __shared__ float csc[2];              // 2^ec as two FP32 powers of two
     const int b = blockIdx.z, n = n0 + b;
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -270,21 +262,29 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
     if (tx == 0 && ty == 0) {
         cst[0] = ldexp(cmass, E - 54);
         cst[1] = ldexp(-0.5 * dt[n - 1], u);
-        // |S9| < 2^61, |S| < 2^62, |m| < 2^53: products below 2^115, 12 bits of headroom in 128
+        // |S9| < 2^61, |S| < 2^62, |m| < 2^53 shifted left by at most 10 bits: products below 2^125
+        long long mm, ms;
         int em, es;
-        split_double(cst[0], cmi[0], em);
-        split_double(cst[1], cmi[1], es);
-        const int ec = max(max(em, es) - 12, min(em, es));
-        csh[0] = max(em - ec, 0); csh[1] = min(max(ec - em, 0), 127);
-        csh[2] = max(es - ec, 0); csh[3] = min(max(ec - es, 0), 127);
-        csh[4] = ec;
+        split_double(cst[0], mm, em);
+        split_double(cst[1], ms, es);
+        if (mm == 0) em = es;
+        if (ms == 0) es = em;
+        const int ec = max(em, es) - 10;
+        cmi[0] = em >= ec ? (long long)((unsigned long long)mm << (em - ec)) : mm;
+        cmi[1] = es >= ec ? (long long)((unsigned long long)ms << (es - ec)) : ms;
+        csh[0] = em >= ec ? 0 : min(ec - em, 127);
+        csh[1] = es >= ec ? 0 : min(ec - es, 127);
+        const int e1 = min(max(ec, -126), 127);
+        csc[0] = ldexpf(1.0f, e1);
+        csc[1] = ldexpf(1.0f, min(max(ec - e1, -126), 127));
     }
     __syncthreads();
     for (int rr = ty; rr < 34; rr += 8) rs[rr][tx] = du[rr][tx] + 4 * du[rr][tx + 1] + du[rr][tx + 2];
     __syncthreads();
     const double cm = cst[0], cs = cst[1];
     const long long mm = cmi[0], ms = cmi[1];
-    const int lm = csh[0], rm = csh[1], ls = csh[2], rsd = csh[3], ec = csh[4];
+    const int rm = csh[0], rsd = csh[1];
+    const float sc1 = csc[0], sc2 = csc[1];
     const bool finite = E < 1024;
     const int i = i0 + tx;
     float sq = 0.f;   // of the stored values; the norm only decides when the iteration stops
@@ -303,9 +303,9 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
                 rf = (float)fma(cm, i64_to_f64(s9), fma(cs, i64_to_f64(st), f));
             } else {
                 __int128 tm = (__int128)s9 * mm, ts = (__int128)st * ms;
-                tm = rm ? (tm >> rm) : (tm << lm);
-                ts = rsd ? (ts >> rsd) : (ts << ls);
-                rf = i128_to_f32(tm + ts, ec);
+                if (rm) tm >>= rm;     // block-uniform, zero unless the units differ by more than 2^10
+                if (rsd) ts >>= rsd;
+                rf = i128_to_f32(tm + ts, sc1, sc2);
             }
             if (!finite) rf = __int_as_float(0x7FC00000);
         }
