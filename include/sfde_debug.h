@@ -82,6 +82,17 @@ sfde_status sfde_debug_set_fused_step(sfde_ctx* ctx, int enable);
 sfde_status sfde_debug_set_fused_pair(sfde_ctx* ctx, int mode);
 
 /*
+ * Whether the mixed-precision solver's inner V-cycles run the F-relaxations of the coarse levels
+ * (l >= 1) and the coarsest level's sequential sweep in the eigenbasis of the step (as mode 3 of
+ * sfde_debug_lp_chain: the right-hand sides transformed once per level visit, each sweep one
+ * transform of the C-point values, an elementwise FP32 recurrence over the interval and one
+ * inverse transform of all F-points) instead of chained fused steps.  Default 1; both compute
+ * u_{im+j} = Phi(u_{im+j-1}) + g_{im+j} (Algorithm 1's F-relaxation), rounded differently.  Takes
+ * effect at the next mgrit_solve.  enable: 0 or 1, else SFDE_EINVAL.
+ */
+sfde_status sfde_debug_set_modal_chains(sfde_ctx* ctx, int enable);
+
+/*
  * One batched low-precision step of the mixed-precision solver (ctx precision must be MIXED_BF16
  * or MIXED_TF32):  out[b] = Phi(U[b]) + g[b] - ut[b],  b = 0..batch-1, slice b stepped from
  * t_{n0+b-1} to t_{n0+b} (1 <= n0, n0 + batch - 1 <= N_t).
@@ -104,9 +115,13 @@ sfde_status sfde_debug_lp_step(sfde_ctx* ctx, int fused, int scheme, const doubl
  * step k of slice b going from t_{n0 + b*nchain + k - 1} to t_{n0 + b*nchain + k}
  * (n0 >= 1, n0 + batch*nchain - 1 <= N_t); scheme 0 Crank-Nicolson, 1 backward Euler.
  *   mode 1: one launch of the fused kernel, each CTA chaining the steps of its slice on chip;
- *   mode 2: nchain launches of the fused kernel (single steps);  mode 0: four slice GEMMs per step.
+ *   mode 2: nchain launches of the fused kernel (single steps);  mode 0: four slice GEMMs per step;
+ *   mode 3: in the eigenbasis of the step (Sec. 2's fast diagonalisation, Phi(X) = V_y [f o
+ *   (W_y^T X W_x)] V_x^T): U[b] and every g[b][k] transformed by slice GEMMs (all at once), the
+ *   recurrence x^_{k+1} = f_k o x^_k + g^[b][k] run elementwise in FP32, every x^_{k+1}
+ *   transformed back -- the chain's latency is that of four batched products, not nchain steps.
  * Modes 1 and 2 need BF16 and P_x = P_y in {128, 256} (else SFDE_EUNSUPPORTED) and give identical
- * results.  U: batch x N_y x N_x, g (may be NULL) and out: batch x nchain x N_y x N_x doubles (host
+ * results; mode 3 needs batch <= min(N_t, 512).  U: batch x N_y x N_x, g (may be NULL) and out: batch x nchain x N_y x N_x doubles (host
  * or device), rounded to the operand type on input.  Synchronous; allocates scratch.
  */
 sfde_status sfde_debug_lp_chain(sfde_ctx* ctx, int mode, int scheme, const double* U, int batch, int nchain,

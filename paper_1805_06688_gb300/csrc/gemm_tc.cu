@@ -118,7 +118,7 @@ k_tc_slice_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         const bool valid = m < Mtot;
         const long long b = valid ? m / p.R : 0;
         const int r = valid ? (int)(m % p.R) : 0;
-        T* __restrict__ out = (T*)p.out + b * p.out_stride;
+        T* __restrict__ out = (T*)p.out + (p.oskip > 0 ? b + b / p.oskip + 1 : b) * p.out_stride;
         float lx = 0.f;
         float dtf = 0.f;
         if (EPI == TC_EPI_SCALE && valid) {

@@ -84,6 +84,66 @@ __global__ void k_add_correction(double* U, const T* E, size_t n) {
     }
 }
 
+// four consecutive low-precision values <-> FP32 (8-byte BF16 / 16-byte FP32 accesses)
+__device__ __forceinline__ void ld4(const __nv_bfloat16* p, float (&v)[4]) {
+    const uint2 w = *(const uint2*)p;
+    v[0] = __uint_as_float(w.x << 16); v[1] = __uint_as_float(w.x & 0xFFFF0000u);
+    v[2] = __uint_as_float(w.y << 16); v[3] = __uint_as_float(w.y & 0xFFFF0000u);
+}
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+    const float4 w = *(const float4*)p;
+    v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
+}
+__device__ __forceinline__ void st4(__nv_bfloat16* p, const float (&v)[4]) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+    uint2 w;
+    w.x = *(const uint32_t*)&a;
+    w.y = *(const uint32_t*)&b;
+    *(uint2*)p = w;
+}
+__device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
+    *(float4*)p = make_float4(sfde_round_tf32(v[0]), sfde_round_tf32(v[1]), sfde_round_tf32(v[2]), sfde_round_tf32(v[3]));
+}
+
+// F-relaxation over intervals of `len` points in the eigenbasis of the step.  Phi(X) = V_y [f o
+// (W_y^T X W_x)] V_x^T with W^T V = I (Sec. 2's fast diagonalisation), so u_{il+j} =
+// Phi(u_{il+j-1}) + g_{il+j} reads, for transformed values, v_j = f_j o v_{j-1} + g^_{il+j}: one
+// recurrence per mode.  v_0 = Uc[i] (the transformed C-point value), g^_{il+j} = G[i gis + j + gj0], f_j the
+// modal factor of the step with dt[i dis + j - 1] (backward Euler 1/(1 + dt sigma), Crank-Nicolson
+// (1 - dt sigma/2)/(1 + dt sigma/2), sigma = K_x lambda_x + K_y lambda_y of the mode); v_j,
+// j = 1 .. len - 1, goes to Y[i (len - 1) + j - 1].  FP32 recurrence; four modes of one row per
+// thread (P_x a multiple of 4); grid.y = intervals.
+template <typename T>
+__global__ void __launch_bounds__(256) k_modal_scan(const T* __restrict__ Uc, const T* __restrict__ G, int gis, int gj0,
+                                                    T* __restrict__ Y, int len, int Px, size_t P2,
+                                                    const float* __restrict__ lamx, const float* __restrict__ lamy,
+                                                    float kx, float ky, const double* __restrict__ dt, int dis,
+                                                    int scheme) {
+    const size_t i = blockIdx.y;
+    const size_t e = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (e >= P2) return;
+    const int x = (int)(e % (size_t)Px), y = (int)(e / (size_t)Px);
+    const float sy = ky * lamy[y];
+    float sg[4], v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sg[q] = fmaf(kx, lamx[x + q], sy);
+    ld4(Uc + i * P2 + e, v);
+    const bool be = scheme == SCHEME_BE;
+    for (int j = 1; j < len; ++j) {
+        const float dtj = (float)dt[i * dis + j - 1];
+        const float cst = be ? dtj : 0.5f * dtj;
+        float gv[4];
+        ld4(G + (i * gis + j + gj0) * P2 + e, gv);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float f = 1.f / fmaf(cst, sg[q], 1.f);
+            if (!be) f = fmaf(2.f, f, -1.f);
+            v[q] = fmaf(f, v[q], gv[q]);
+        }
+        st4(Y + (i * (len - 1) + j - 1) * P2 + e, v);
+    }
+}
+
 unsigned grid_for(size_t n) {
     size_t g = (n + 255) / 256;
     return (unsigned)std::min<size_t>(std::max<size_t>(g, 1), 4 * 152);
@@ -98,6 +158,7 @@ struct LpLevel {
     double* dt = nullptr;      // device; level 0 uses ctx->dt0
     void* u = nullptr;         // (nalloc) x P^2 of T
     void* g = nullptr;
+    void* gm = nullptr;        // levels >= 1: g transformed to the eigenbasis, (N + 1) x P^2 of T
     bool own_dt = false;
 };
 
@@ -118,6 +179,7 @@ struct SfdeMixed {
     std::vector<LpLevel> lev;
     void *T1 = nullptr, *T2 = nullptr, *T3 = nullptr;
     size_t ws = 0;
+    void* mY = nullptr;        // transformed F-point values of a modal sweep (max N_l, l >= 1, slices)
     int* err = nullptr;
     std::vector<MapEntry> maps;
     // captured inner solve (CUDA graph) and what it contains
@@ -142,9 +204,9 @@ void sfde_free_mixed(sfde_ctx* c) {
     cudaFree(M->lamx); cudaFree(M->lamy);
     for (auto& L : M->lev) {
         if (L.own_dt) cudaFree(L.dt);
-        cudaFree(L.u); cudaFree(L.g);
+        cudaFree(L.u); cudaFree(L.g); cudaFree(L.gm);
     }
-    cudaFree(M->T1); cudaFree(M->T2); cudaFree(M->T3); cudaFree(M->err);
+    cudaFree(M->T1); cudaFree(M->T2); cudaFree(M->T3); cudaFree(M->mY); cudaFree(M->err);
     for (auto& g : M->inner_exec)
         if (g) cudaGraphExecDestroy(g);
     sfde_oz_free_matrix(&M->oAx);
@@ -254,6 +316,16 @@ sfde_status setup_mixed(sfde_ctx* c, int kind, int m, int max_levels, int min_co
         SFDE_CUDA(cudaMalloc(&L.g, M->esz * P2 * L.nalloc));
         SFDE_CUDA(cudaMemsetAsync(L.u, 0, M->esz * P2 * L.nalloc, c->stream));
         SFDE_CUDA(cudaMemsetAsync(L.g, 0, M->esz * P2 * L.nalloc, c->stream));
+    }
+    // modal sweeps of the coarse levels: transformed right-hand sides per level, one scratch
+    {
+        int ymax = 0;
+        for (size_t l = 1; l < M->lev.size(); ++l) {
+            LpLevel& L = M->lev[l];
+            SFDE_CUDA(cudaMalloc(&L.gm, M->esz * P2 * (size_t)(L.N + 1)));
+            ymax = std::max(ymax, L.N);
+        }
+        if (ymax > 0) SFDE_CUDA(cudaMalloc(&M->mY, M->esz * P2 * (size_t)ymax));
     }
     M->ws = (size_t)std::max(1, std::min(c->nt, 512));
     SFDE_CUDA(cudaMalloc(&M->T1, M->esz * P2 * M->ws));
@@ -381,6 +453,80 @@ struct LpEngine {
         return SFDE_OK;
     }
 
+    // W_y^T X_b W_x for the slices src0 + b ds (b < batch) of `src` (a buffer of ns slices) -> slice
+    // b dst_ds of dst: two slice GEMMs through T1, no modal factor
+    sfde_status to_modal(const void* src, long long ns, int src0, int ds, int batch, void* dst, int dst_ds) {
+        const int Px = c->x.P, Py = c->y.P;
+        const long long P2l = (long long)P2();
+        for (int b0 = 0; b0 < batch; b0 += (int)M->ws) {
+            const int nb = std::min<int>(batch - b0, (int)M->ws);
+            CUtensorMap a1, a2;
+            SFDE_TRY(map_for(M, src, Py, Px, ds, ns, &a1));
+            SFDE_TRY(map_for(M, M->T1, Px, Py, 1, (long long)M->ws, &a2));
+            TcArgs p{};   // (X W_x)^T
+            p.batch = nb; p.err = M->err;
+            p.R = Py; p.C = Px; p.Cout = Px; p.BN = sfde_tc_tile_n(Px); p.s0 = src0 + b0 * ds; p.ds = ds;
+            p.out = M->T1; p.out_stride = P2l;
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a1, M->mWTx, p, c->stream, c->y.n, c->x.n, c->x.n));
+            TcArgs q{};   // (T1 W_y)^T = W_y^T X W_x
+            q.batch = nb; q.err = M->err;
+            q.R = Px; q.C = Py; q.Cout = Py; q.BN = sfde_tc_tile_n(Py); q.s0 = 0; q.ds = 1;
+            q.out = slice(dst, (long long)b0 * dst_ds); q.out_stride = (long long)dst_ds * P2l;
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a2, M->mWTy, q, c->stream, c->x.n, c->y.n, c->y.n));
+        }
+        return SFDE_OK;
+    }
+
+    // V_y Y_b V_x^T for the slices b < batch of `src` (ns slices) -> slice b of dst, or with oskip > 0
+    // the b-th F-point, slice b + b / oskip + 1 (intervals of oskip + 1 points): two slice GEMMs
+    // through T3, in chunks of whole intervals
+    sfde_status from_modal(const void* src, long long ns, int batch, void* dst, int oskip) {
+        const int Px = c->x.P, Py = c->y.P;
+        const long long P2l = (long long)P2();
+        const int chunk = oskip > 0 ? std::max(oskip, ((int)M->ws / oskip) * oskip) : (int)M->ws;
+        if (chunk > (int)M->ws) return SFDE_EINVAL;
+        for (int b0 = 0; b0 < batch; b0 += chunk) {
+            const int nb = std::min(batch - b0, chunk);
+            CUtensorMap a3, a4;
+            SFDE_TRY(map_for(M, src, Py, Px, 1, ns, &a3));
+            SFDE_TRY(map_for(M, M->T3, Px, Py, 1, (long long)M->ws, &a4));
+            TcArgs r{};   // (Y V_x^T)^T
+            r.batch = nb; r.err = M->err;
+            r.R = Py; r.C = Px; r.Cout = Px; r.BN = sfde_tc_tile_n(Px); r.s0 = b0; r.ds = 1;
+            r.out = M->T3; r.out_stride = P2l;
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a3, M->mVx, r, c->stream, c->y.n, c->x.n, c->x.n));
+            TcArgs f{};   // (T3 V_y^T)^T = V_y Y V_x^T
+            f.batch = nb; f.err = M->err;
+            f.R = Px; f.C = Py; f.Cout = Py; f.BN = sfde_tc_tile_n(Py); f.s0 = 0; f.ds = 1;
+            f.out = slice(dst, oskip > 0 ? (long long)b0 + b0 / oskip : (long long)b0);
+            f.out_stride = P2l;
+            f.oskip = oskip;
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a4, M->mVy, f, c->stream, c->x.n, c->y.n, c->y.n));
+        }
+        return SFDE_OK;
+    }
+
+    // Y[i (len - 1) + j - 1] = v_j of the eigenbasis recurrence over `nint` intervals (k_modal_scan)
+    sfde_status modal_scan(const void* Uc, const void* G, int gis, int gj0, void* Y, int len, int nint,
+                           const double* dt, int dis, int sch) {
+        const size_t P2s = P2();
+        dim3 grid((unsigned)((P2s / 4 + 255) / 256), (unsigned)nint);
+        if (M->kind == 0)
+            k_modal_scan<__nv_bfloat16><<<grid, 256, 0, c->stream>>>(
+                (const __nv_bfloat16*)Uc, (const __nv_bfloat16*)G, gis, gj0, (__nv_bfloat16*)Y, len, c->x.P, P2s, M->lamx,
+                M->lamy, (float)c->kx, (float)c->ky, dt, dis, sch);
+        else
+            k_modal_scan<float><<<grid, 256, 0, c->stream>>>((const float*)Uc, (const float*)G, gis, gj0, (float*)Y, len,
+                                                             c->x.P, P2s, M->lamx, M->lamy, (float)c->kx,
+                                                             (float)c->ky, dt, dis, sch);
+        sfde_count_launch(c);
+        SFDE_CUDA(cudaGetLastError());
+        return SFDE_OK;
+    }
+
+    // coarse levels sweep in the eigenbasis (F-relaxation, coarsest solve)
+    bool modal(int l) const { return c->modal_chains && l >= 1 && M->lev[l].gm && M->mY; }
+
     sfde_status lstep(int l, int batch, int src0, int ds, int n0, int dn, void* dst, int dst_ds,
                       const void* ut, double* partial, int* npart) {
         LpLevel& Lv = M->lev[l];
@@ -393,6 +539,14 @@ struct LpEngine {
     sfde_status frelax(int l) {
         LpLevel& Lv = M->lev[l];
         const int nc = Lv.N / m;
+        if (modal(l)) {
+            // C-point values transformed (T2), the interval recurrences, all F-points transformed back
+            SFDE_TRY(to_modal(Lv.u, Lv.nalloc, 0, m, nc, M->T2, 1));
+            SFDE_TRY(modal_scan(M->T2, Lv.gm, m, 0, M->mY, m, nc, Lv.dt, m, scheme));
+            SFDE_TRY(from_modal(M->mY, (long long)nc * (m - 1), nc * (m - 1), Lv.u, m - 1));
+            steps += (long long)nc * (m - 1);
+            return SFDE_OK;
+        }
         if (M->fused)
             return step(Lv.u, Lv.nalloc, 0, m, nc, false, l == 0 ? SCHEME_CN : scheme, Lv.dt, 1, m, slice(Lv.u, 1), m,
                         slice(Lv.g, 1), nullptr, nullptr, nullptr, m - 1);
@@ -429,7 +583,15 @@ struct LpEngine {
     sfde_status coarsest(int l) {
         LpLevel& Lv = M->lev[l];
         SFDE_CUDA(cudaMemcpyAsync(Lv.u, Lv.g, P2() * M->esz, cudaMemcpyDeviceToDevice, c->stream));
-        // u_n = Phi(u_{n-1}) + g_n, n = 1..N: the fused kernel chains all N steps in one launch
+        // u_n = Phi(u_{n-1}) + g_n, n = 1..N: one recurrence per mode in the eigenbasis (u_0 = g_0,
+        // so its transform is the first transformed right-hand side), or the fused kernel chaining
+        // all N steps in one launch
+        if (modal(l)) {
+            SFDE_TRY(modal_scan(Lv.gm, Lv.gm, Lv.N + 1, 0, M->mY, Lv.N + 1, 1, Lv.dt, Lv.N + 1, scheme));
+            SFDE_TRY(from_modal(M->mY, Lv.N, Lv.N, Lv.u, Lv.N));
+            steps += Lv.N;
+            return SFDE_OK;
+        }
         if (M->fused)
             return step(Lv.u, Lv.nalloc, 0, 1, 1, false, l == 0 ? SCHEME_CN : scheme, Lv.dt, 1, 1, slice(Lv.u, 1), 1,
                         slice(Lv.g, 1), nullptr, nullptr, nullptr, Lv.N);
@@ -452,6 +614,8 @@ struct LpEngine {
     }
 
     sfde_status solve(int l) {
+        // the level's right-hand sides stay fixed while it is visited: transformed once
+        if (modal(l)) SFDE_TRY(to_modal(M->lev[l].g, M->lev[l].nalloc, 0, 1, M->lev[l].N + 1, M->lev[l].gm, 1));
         if (l == L - 1) return coarsest(l);
         SFDE_TRY(relaxation(l));
         SFDE_TRY(residual(l, nullptr, nullptr));
@@ -548,7 +712,7 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
     const int K = o->inner_cycles > 0 ? o->inner_cycles : (kind == 0 ? 4 : 5);
     // the inner solve is captured once as CUDA graphs and replayed; eager while kernels are timed
     const bool use_graph = !c->prof.on;
-    const long long key = ((long long)c->fused_pair << 24) | ((long long)M->fused << 20) |
+    const long long key = ((long long)c->modal_chains << 28) | ((long long)c->fused_pair << 24) | ((long long)M->fused << 20) |
                           ((long long)E.scheme << 4) | (long long)o->relax;
     long long graph_steps = 0;
 
@@ -702,6 +866,12 @@ extern "C" sfde_status sfde_debug_set_fused_pair(sfde_ctx* c, int mode) {
     return SFDE_OK;
 }
 
+extern "C" sfde_status sfde_debug_set_modal_chains(sfde_ctx* c, int enable) {
+    if (!c || enable < 0 || enable > 1) return SFDE_EINVAL;
+    c->modal_chains = enable;
+    return SFDE_OK;
+}
+
 extern "C" sfde_status sfde_debug_lp_step(sfde_ctx* c, int fused, int scheme, const double* U, int batch, int n0,
                                          const double* g, const double* ut, double* out, double* norm2) {
     if (!c || !U || !out || batch < 1 || n0 < 1 || (long long)n0 + batch - 1 > c->nt || scheme < 0 || scheme > 2)
@@ -750,22 +920,24 @@ extern "C" sfde_status sfde_debug_lp_step(sfde_ctx* c, int fused, int scheme, co
 extern "C" sfde_status sfde_debug_lp_chain(sfde_ctx* c, int mode, int scheme, const double* U, int batch, int nchain,
                                           int n0, const double* g, double* out) {
     if (!c || !U || !out || batch < 1 || nchain < 1 || n0 < 1 || scheme < 0 || scheme > 1 ||
-        (long long)n0 + (long long)batch * nchain - 1 > c->nt || mode < 0 || mode > 2)
+        (long long)n0 + (long long)batch * nchain - 1 > c->nt || mode < 0 || mode > 3)
         return SFDE_EINVAL;
     if (c->precision == SFDE_PREC_FP64) return SFDE_EINVAL;
     const int kind = sfde_mixed_kind(c);
-    if (mode != 0 && !sfde_fused_supported(kind, c->x.P, c->y.P)) return SFDE_EUNSUPPORTED;
+    if ((mode == 1 || mode == 2) && !sfde_fused_supported(kind, c->x.P, c->y.P)) return SFDE_EUNSUPPORTED;
     if (!c->mixed || c->mixed->kind != kind) SFDE_TRY(setup_mixed(c, kind, 2, 1, 1));
     SfdeMixed* M = c->mixed;
+    if (mode == 3 && (size_t)batch > M->ws) return SFDE_EINVAL;
     const size_t P2 = c->P2(), n2 = (size_t)c->x.n * c->y.n;
     const size_t nout = (size_t)batch * nchain, esz = M->esz;
     double *tu = nullptr, *tp = nullptr;
-    void *src = nullptr, *dst = nullptr, *dg = nullptr;
+    void *src = nullptr, *dst = nullptr, *dg = nullptr, *gh = nullptr, *yh = nullptr;
     sfde_status st = SFDE_OK;
     const bool saved = M->fused;
     if (cudaMalloc(&tu, sizeof(double) * n2 * nout) != cudaSuccess ||
         cudaMalloc(&tp, sizeof(double) * P2 * nout) != cudaSuccess || cudaMalloc(&src, P2 * esz * batch) != cudaSuccess ||
-        cudaMalloc(&dst, P2 * esz * (nout + nchain)) != cudaSuccess || cudaMalloc(&dg, P2 * esz * nout) != cudaSuccess)
+        cudaMalloc(&dst, P2 * esz * (nout + nchain)) != cudaSuccess || cudaMalloc(&dg, P2 * esz * nout) != cudaSuccess ||
+        (mode == 3 && (cudaMalloc(&gh, P2 * esz * nout) != cudaSuccess || cudaMalloc(&yh, P2 * esz * nout) != cudaSuccess)))
         st = SFDE_ENOMEM;
     if (st == SFDE_OK) st = load_lp(c, U, batch, tu, tp, src, kind);
     if (st == SFDE_OK && g) st = load_lp(c, g, (int)nout, tu, tp, dg, kind);
@@ -773,7 +945,16 @@ extern "C" sfde_status sfde_debug_lp_chain(sfde_ctx* c, int mode, int scheme, co
         LpEngine E{c, M, 2, 1, SFDE_RELAX_FCF, SCHEME_CN};
         const int sch = scheme == 0 ? SCHEME_CN : SCHEME_BE;
         const size_t sl = P2 * esz;
-        if (mode == 1) {   // one launch: each CTA runs the nchain steps of its slice
+        if (mode == 3) {   // eigenbasis: transforms of all inputs, recurrences, transforms back
+            st = E.to_modal(src, batch, 0, 1, batch, M->T2, 1);
+            if (st == SFDE_OK && g) st = E.to_modal(dg, (long long)nout, 0, 1, (int)nout, gh, 1);
+            if (st == SFDE_OK && !g && cudaMemsetAsync(gh, 0, P2 * esz * nout, c->stream) != cudaSuccess) st = SFDE_ECUDA;
+            // interval b: C-point U[b], F-points k = 1..nchain with g[b][k - 1] (slice b nchain + k - 1)
+            // and dt[n0 + b nchain + k - 2]
+            if (st == SFDE_OK)
+                st = E.modal_scan(M->T2, gh, nchain, -1, yh, nchain + 1, batch, c->dt0 + (n0 - 1), nchain, sch);
+            if (st == SFDE_OK) st = E.from_modal(yh, (long long)nout, (int)nout, dst, 0);
+        } else if (mode == 1) {   // one launch: each CTA runs the nchain steps of its slice
             M->fused = true;
             st = E.step(src, batch, 0, 1, batch, false, sch, c->dt0, n0, nchain, dst, nchain, g ? dg : nullptr,
                         nullptr, nullptr, nullptr, nchain);
@@ -801,6 +982,6 @@ extern "C" sfde_status sfde_debug_lp_chain(sfde_ctx* c, int mode, int scheme, co
     if (st == SFDE_OK && e != cudaSuccess) { sfde_set_last_cuda_error(e, "debug lp chain", __FILE__, __LINE__); st = SFDE_ECUDA; }
     if (st == SFDE_OK) st = check_err(M, c->stream);
     M->fused = saved;
-    cudaFree(tu); cudaFree(tp); cudaFree(src); cudaFree(dst); cudaFree(dg);
+    cudaFree(tu); cudaFree(tp); cudaFree(src); cudaFree(dst); cudaFree(dg); cudaFree(gh); cudaFree(yh);
     return st;
 }

@@ -107,6 +107,8 @@ struct sfde_ctx {
                                 // 2 batch <= SMs, else per two slices), 2 pair per slice, 3 pair per two slices
     int resid_digits = 0;       // digits of the tensor-core residual: 0 per iteration, else 4..7 fixed
     int resid_chunk = 0;        // time points per pass of the tensor-core residual (0: ws_slices)
+    int modal_chains = 1;       // coarse-level F-relaxations and coarsest sweeps of the inner V-cycles
+                                // in the step's eigenbasis (transforms, elementwise scan, inverse)
     SfdeProf prof;
     size_t P2() const { return (size_t)x.P * (size_t)y.P; }
 };
@@ -158,6 +160,8 @@ struct TcArgs {
     void* out; long long out_stride;
     TcEpi e;
     int* err;                            // device error word (bounded waits)
+    int oskip;                           // > 0: Out_b goes to slice b + b / oskip + 1 (the F-points
+                                         // of intervals of oskip + 1 points), else to slice b
 };
 
 int sfde_tc_tile_n(int cout);

@@ -173,7 +173,8 @@ def lp_chain(P, mode, scheme, U, nchain, n0, g=None):
 @pytest.mark.parametrize("nx,ny,batch,nchain", [(255, 255, 150, 2), (100, 127, 3, 3), (200, 180, 2, 15)])
 def test_chained_steps(scheme, nx, ny, batch, nchain):
     """The F-relaxation chain of one fused launch (each CTA keeps its slice on chip from step to
-    step) equals single fused launches bit for bit; it and the four-GEMM steps both follow the
+    step) equals single fused launches bit for bit; it, the four-GEMM steps and the chain run in the
+    step's eigenbasis (transforms, FP32 recurrence per mode, transforms back) all follow the
     oracle's FP64 steps.  Both propagators are contractions in the M_h-norm (Sec. 3: their modal
     factors are at most 1 in modulus), so rounding errors introduced at each step add up in that
     norm: after k + 1 steps at most 5u (k + 1).  The two low-precision paths agree to u/2 on the
@@ -190,7 +191,8 @@ def test_chained_steps(scheme, nx, ny, batch, nchain):
     st1, x1 = lp_chain(P, 1, scheme, U, nchain, n0, g)
     st2, x2 = lp_chain(P, 2, scheme, U, nchain, n0, g)
     st0, x0 = lp_chain(P, 0, scheme, U, nchain, n0, g)
-    assert st1 == 0 and st2 == 0 and st0 == 0
+    st3, x3 = lp_chain(P, 3, scheme, U, nchain, n0, g)
+    assert st1 == 0 and st2 == 0 and st0 == 0 and st3 == 0
     assert np.array_equal(x1, x2)
     u = 2.0 ** -9
     for b in range(batch):
@@ -199,7 +201,7 @@ def test_chained_steps(scheme, nx, ny, batch, nchain):
             n = n0 + b * nchain + k
             x = O.propagate(x, O.t[n] - O.t[n - 1], "cn" if scheme == 0 else "be") + g[b, k]
             mref = mnorm(O, x)
-            for xs in (x1, x0):
+            for xs in (x1, x0, x3):
                 rel = mnorm(O, xs[b, k] - x) / mref
                 assert rel <= 5 * u * (k + 1), (b, k, rel)
         d = np.sqrt(np.sum((x1[b, 0] - x0[b, 0]) ** 2) / np.sum(x0[b, 0] ** 2))

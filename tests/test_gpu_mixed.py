@@ -1,6 +1,8 @@
 """Mixed-precision MGRIT (BF16 / TF32 tensor-core V-cycles inside FP64 iterative refinement)
 against the FP64 oracle.  Acceptance: max-norm error <= 1e-8 relative to the max norm of the
 space-time solution, at every time point, against the exact sequential solution of Eq. (2.4)."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -22,14 +24,20 @@ def _err(U, ref):
     return float(np.abs(U - ref).max() / np.abs(ref).max())
 
 
+@pytest.mark.parametrize("modal", [1, 0])
 @pytest.mark.parametrize("name,prec", PRECS)
 @pytest.mark.parametrize("nx,ny,nt,m,grid,levels", [(20, 13, 64, 4, "graded", 3), (31, 31, 64, 4, "uniform", 2),
                                                      (100, 70, 96, 4, "uniform", 8)])
-def test_mixed_matches_sequential(name, prec, nx, ny, nt, m, grid, levels):
+def test_mixed_matches_sequential(name, prec, nx, ny, nt, m, grid, levels, modal):
+    """Mixed precision against the oracle's sequential solution, with the coarse levels' sweeps in the
+    step's eigenbasis (modal 1, the default) and as chains of steps (modal 0)."""
     t = time_grid(nt, 1.0, grid)
     F, _ = gaussian_bump_forcing(5, nx, ny, t)
     psi = sine_mode_nodal(sine_mode_amplitudes(4), nx, ny)
     P = sfde.Problem(0.6, 0.9, 1.0, 0.5, nx, ny, t, precision=prec)
+    L = sfde.lib()
+    L.sfde_debug_set_modal_chains.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert L.sfde_debug_set_modal_chains(P.ctx, modal) == 0
     P.set_initial(psi)
     P.set_forcing(F)
     U = np.zeros((nt + 1, ny, nx))
