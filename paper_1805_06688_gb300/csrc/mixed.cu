@@ -129,18 +129,28 @@ __global__ void __launch_bounds__(256) k_modal_scan(const T* __restrict__ Uc, co
     for (int q = 0; q < 4; ++q) sg[q] = fmaf(kx, lamx[x + q], sy);
     ld4(Uc + i * P2 + e, v);
     const bool be = scheme == SCHEME_BE;
-    for (int j = 1; j < len; ++j) {
-        const float dtj = (float)dt[i * dis + j - 1];
-        const float cst = be ? dtj : 0.5f * dtj;
-        float gv[4];
-        ld4(G + (i * gis + j + gj0) * P2 + e, gv);
+    // eight steps at a time: their right-hand sides are loaded before the first is used, so the
+    // load latencies overlap instead of adding up along the recurrence
+    for (int j0 = 1; j0 < len; j0 += 8) {
+        float gv[8][4], cst[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float f = 1.f / fmaf(cst, sg[q], 1.f);
-            if (!be) f = fmaf(2.f, f, -1.f);
-            v[q] = fmaf(f, v[q], gv[q]);
-        }
-        st4(Y + (i * (len - 1) + j - 1) * P2 + e, v);
+        for (int u = 0; u < 8; ++u)
+            if (j0 + u < len) {
+                const float dtj = (float)dt[i * dis + j0 + u - 1];
+                cst[u] = be ? dtj : 0.5f * dtj;
+                ld4(G + (i * gis + j0 + u + gj0) * P2 + e, gv[u]);
+            }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (j0 + u < len) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float f = 1.f / fmaf(cst[u], sg[q], 1.f);
+                    if (!be) f = fmaf(2.f, f, -1.f);
+                    v[q] = fmaf(f, v[q], gv[u][q]);
+                }
+                st4(Y + (i * (len - 1) + j0 + u - 1) * P2 + e, v);
+            }
     }
 }
 
@@ -195,6 +205,8 @@ struct SfdeMixed {
     int* oz_E = nullptr;
     // each BF16 step as one fused four-product kernel (P_x = P_y in {128, 256})
     bool fused = false;
+    // the fine level's modal buffers exist (its F-relaxations in the eigenbasis too)
+    bool modal_fine = false;
 };
 
 void sfde_free_mixed(sfde_ctx* c) {
@@ -244,12 +256,14 @@ sfde_status map_for(SfdeMixed* M, const void* ptr, int R, int C, int ds, long lo
 
 sfde_status setup_mixed(sfde_ctx* c, int kind, int m, int max_levels, int min_coarse) {
     SfdeMixed* M = c->mixed;
-    if (M && M->kind == kind && M->m == m && M->max_levels == max_levels && M->min_coarse == min_coarse)
+    if (M && M->kind == kind && M->m == m && M->max_levels == max_levels && M->min_coarse == min_coarse &&
+        M->modal_fine == (c->modal_chains == 2))
         return SFDE_OK;
     sfde_free_mixed(c);
     M = new SfdeMixed();
     c->mixed = M;
     M->kind = kind; M->esz = kind == 0 ? 2 : 4; M->m = m; M->max_levels = max_levels; M->min_coarse = min_coarse;
+    M->modal_fine = c->modal_chains == 2;
     SFDE_TRY(sfde_tc_prepare());
     SFDE_TRY(sfde_fused_prepare());
     const int Px = c->x.P, Py = c->y.P;
@@ -317,10 +331,11 @@ sfde_status setup_mixed(sfde_ctx* c, int kind, int m, int max_levels, int min_co
         SFDE_CUDA(cudaMemsetAsync(L.u, 0, M->esz * P2 * L.nalloc, c->stream));
         SFDE_CUDA(cudaMemsetAsync(L.g, 0, M->esz * P2 * L.nalloc, c->stream));
     }
-    // modal sweeps of the coarse levels: transformed right-hand sides per level, one scratch
+    // modal sweeps of the coarse levels (and of the fine level when asked): transformed right-hand
+    // sides per level, one scratch
     {
         int ymax = 0;
-        for (size_t l = 1; l < M->lev.size(); ++l) {
+        for (size_t l = M->modal_fine ? 0 : 1; l < M->lev.size(); ++l) {
             LpLevel& L = M->lev[l];
             SFDE_CUDA(cudaMalloc(&L.gm, M->esz * P2 * (size_t)(L.N + 1)));
             ymax = std::max(ymax, L.N);
@@ -525,7 +540,7 @@ struct LpEngine {
     }
 
     // coarse levels sweep in the eigenbasis (F-relaxation, coarsest solve)
-    bool modal(int l) const { return c->modal_chains && l >= 1 && M->lev[l].gm && M->mY; }
+    bool modal(int l) const { return c->modal_chains && (l >= 1 || c->modal_chains == 2) && M->lev[l].gm && M->mY; }
 
     sfde_status lstep(int l, int batch, int src0, int ds, int n0, int dn, void* dst, int dst_ds,
                       const void* ut, double* partial, int* npart) {
@@ -542,7 +557,7 @@ struct LpEngine {
         if (modal(l)) {
             // C-point values transformed (T2), the interval recurrences, all F-points transformed back
             SFDE_TRY(to_modal(Lv.u, Lv.nalloc, 0, m, nc, M->T2, 1));
-            SFDE_TRY(modal_scan(M->T2, Lv.gm, m, 0, M->mY, m, nc, Lv.dt, m, scheme));
+            SFDE_TRY(modal_scan(M->T2, Lv.gm, m, 0, M->mY, m, nc, Lv.dt, m, l == 0 ? SCHEME_CN : scheme));
             SFDE_TRY(from_modal(M->mY, (long long)nc * (m - 1), nc * (m - 1), Lv.u, m - 1));
             steps += (long long)nc * (m - 1);
             return SFDE_OK;
@@ -587,7 +602,8 @@ struct LpEngine {
         // so its transform is the first transformed right-hand side), or the fused kernel chaining
         // all N steps in one launch
         if (modal(l)) {
-            SFDE_TRY(modal_scan(Lv.gm, Lv.gm, Lv.N + 1, 0, M->mY, Lv.N + 1, 1, Lv.dt, Lv.N + 1, scheme));
+            SFDE_TRY(modal_scan(Lv.gm, Lv.gm, Lv.N + 1, 0, M->mY, Lv.N + 1, 1, Lv.dt, Lv.N + 1,
+                                l == 0 ? SCHEME_CN : scheme));
             SFDE_TRY(from_modal(M->mY, Lv.N, Lv.N, Lv.u, Lv.N));
             steps += Lv.N;
             return SFDE_OK;
@@ -639,6 +655,8 @@ sfde_status enqueue_inner_part(sfde_ctx* c, SfdeMixed* M, LpEngine& E, double* U
         SFDE_TRY(E.step(L0.g, L0.nalloc, 1, 1, c->nt, true, SCHEME_SOLVE, c->dt0, 1, 1, E.slice(L0.g, 1), 1,
                         nullptr, nullptr, nullptr, nullptr));
         SFDE_CUDA(cudaMemsetAsync(L0.u, 0, P2 * M->esz * L0.nalloc, c->stream));
+        // fixed for all V-cycles of this refinement step: transformed once
+        if (E.modal(0)) SFDE_TRY(E.to_modal(L0.g, L0.nalloc, 0, 1, L0.N + 1, L0.gm, 1));
         return SFDE_OK;
     }
     if (part == 1) {
@@ -867,7 +885,7 @@ extern "C" sfde_status sfde_debug_set_fused_pair(sfde_ctx* c, int mode) {
 }
 
 extern "C" sfde_status sfde_debug_set_modal_chains(sfde_ctx* c, int enable) {
-    if (!c || enable < 0 || enable > 1) return SFDE_EINVAL;
+    if (!c || enable < 0 || enable > 2) return SFDE_EINVAL;
     c->modal_chains = enable;
     return SFDE_OK;
 }
