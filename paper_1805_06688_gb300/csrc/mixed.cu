@@ -257,13 +257,13 @@ sfde_status map_for(SfdeMixed* M, const void* ptr, int R, int C, int ds, long lo
 sfde_status setup_mixed(sfde_ctx* c, int kind, int m, int max_levels, int min_coarse) {
     SfdeMixed* M = c->mixed;
     if (M && M->kind == kind && M->m == m && M->max_levels == max_levels && M->min_coarse == min_coarse &&
-        M->modal_fine == (c->modal_chains == 2))
+        M->modal_fine == (c->modal_chains == 2 || (c->modal_chains == 3 && kind == 0)))
         return SFDE_OK;
     sfde_free_mixed(c);
     M = new SfdeMixed();
     c->mixed = M;
     M->kind = kind; M->esz = kind == 0 ? 2 : 4; M->m = m; M->max_levels = max_levels; M->min_coarse = min_coarse;
-    M->modal_fine = c->modal_chains == 2;
+    M->modal_fine = c->modal_chains == 2 || (c->modal_chains == 3 && kind == 0);
     SFDE_TRY(sfde_tc_prepare());
     SFDE_TRY(sfde_fused_prepare());
     const int Px = c->x.P, Py = c->y.P;
@@ -540,7 +540,7 @@ struct LpEngine {
     }
 
     // coarse levels sweep in the eigenbasis (F-relaxation, coarsest solve)
-    bool modal(int l) const { return c->modal_chains && (l >= 1 || c->modal_chains == 2) && M->lev[l].gm && M->mY; }
+    bool modal(int l) const { return c->modal_chains && (l >= 1 || M->modal_fine) && M->lev[l].gm && M->mY; }
 
     sfde_status lstep(int l, int batch, int src0, int ds, int n0, int dn, void* dst, int dst_ds,
                       const void* ut, double* partial, int* npart) {
@@ -885,7 +885,7 @@ extern "C" sfde_status sfde_debug_set_fused_pair(sfde_ctx* c, int mode) {
 }
 
 extern "C" sfde_status sfde_debug_set_modal_chains(sfde_ctx* c, int enable) {
-    if (!c || enable < 0 || enable > 2) return SFDE_EINVAL;
+    if (!c || enable < 0 || enable > 3) return SFDE_EINVAL;
     c->modal_chains = enable;
     return SFDE_OK;
 }

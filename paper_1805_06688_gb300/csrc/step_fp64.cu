@@ -200,11 +200,19 @@ __global__ void __launch_bounds__(256) k_slice_gemm_fp64(GemmParams p) {
     }
 }
 
-// Fixed-order sum of the per-CTA partials (deterministic norms).
+// Fixed-order sum of the per-CTA partials (deterministic norms).  Each thread keeps eight partial
+// sums, so eight loads are in flight at a time.
 __global__ void k_reduce_partials(const double* partial, int n, double* out) {
     __shared__ double s[1024];
-    double v = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v += partial[i];
+    double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const int step = blockDim.x * 8;
+    int i0 = threadIdx.x;
+    for (; i0 + 7 * (int)blockDim.x < n; i0 += step)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] += partial[i0 + k * blockDim.x];
+    for (int k = 0; k < 8; ++k)
+        if (i0 + k * (int)blockDim.x < n) a[k] += partial[i0 + k * blockDim.x];
+    double v = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
     s[threadIdx.x] = v;
     __syncthreads();
     for (int k = blockDim.x / 2; k > 0; k >>= 1) {

@@ -24,13 +24,14 @@ def _err(U, ref):
     return float(np.abs(U - ref).max() / np.abs(ref).max())
 
 
-@pytest.mark.parametrize("modal", [1, 0, 2])
+@pytest.mark.parametrize("modal", [3, 1, 0, 2])
 @pytest.mark.parametrize("name,prec", PRECS)
 @pytest.mark.parametrize("nx,ny,nt,m,grid,levels", [(20, 13, 64, 4, "graded", 3), (31, 31, 64, 4, "uniform", 2),
                                                      (100, 70, 96, 4, "uniform", 8)])
 def test_mixed_matches_sequential(name, prec, nx, ny, nt, m, grid, levels, modal):
     """Mixed precision against the oracle's sequential solution, with the coarse levels' sweeps in the
-    step's eigenbasis (modal 1, the default), every level's (modal 2) and none (modal 0)."""
+    step's eigenbasis (modal 1), every level's (modal 2), by operand type (modal 3, the default: all
+    levels with BF16, the coarse ones with TF32) and none (modal 0)."""
     t = time_grid(nt, 1.0, grid)
     F, _ = gaussian_bump_forcing(5, nx, ny, t)
     psi = sine_mode_nodal(sine_mode_amplitudes(4), nx, ny)
@@ -52,10 +53,10 @@ def test_modal_chains_setting_range():
     P = sfde.Problem(0.6, 0.9, 1.0, 0.5, 31, 31, time_grid(16, 1.0, "uniform"), precision=sfde.PREC_MIXED_BF16)
     L = sfde.lib()
     L.sfde_debug_set_modal_chains.argtypes = [ctypes.c_void_p, ctypes.c_int]
-    assert L.sfde_debug_set_modal_chains(P.ctx, 3) == sfde.SFDE_EINVAL
+    assert L.sfde_debug_set_modal_chains(P.ctx, 4) == sfde.SFDE_EINVAL
     assert L.sfde_debug_set_modal_chains(P.ctx, -1) == sfde.SFDE_EINVAL
     assert L.sfde_debug_set_modal_chains(None, 1) == sfde.SFDE_EINVAL
-    for v in (0, 2, 1):
+    for v in (0, 2, 1, 3):
         assert L.sfde_debug_set_modal_chains(P.ctx, v) == 0
 
 
