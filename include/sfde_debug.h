@@ -86,9 +86,9 @@ sfde_status sfde_debug_set_fused_pair(sfde_ctx* ctx, int mode);
  * sequential sweep in the eigenbasis of the step (as mode 3 of sfde_debug_lp_chain: the right-hand
  * sides transformed once per level visit, each sweep one transform of the C-point values, an
  * elementwise FP32 recurrence over the interval and one inverse transform of all F-points) instead
- * of as chained fused steps.  enable 1: the coarse levels l >= 1; 2: every level, the fine one too
- * (its buffers, two more copies of the fine level's low-precision vector, are allocated at the next
- * solve); 3 (default): 2 with BF16 operands (whose chained steps round most), 1 with TF32; 0: none.  Both forms compute u_{im+j} = Phi(u_{im+j-1}) + g_{im+j} (Algorithm 1's
+ * of as chained fused steps.  enable 1 (default): the coarse levels l >= 1; 2: every level, the fine
+ * one too (its buffers, two more copies of the fine level's low-precision vector, are allocated at
+ * the next solve); 3: 2 with BF16 operands (whose chained steps round most), 1 with TF32; 0: none.  Both forms compute u_{im+j} = Phi(u_{im+j-1}) + g_{im+j} (Algorithm 1's
  * F-relaxation), rounded differently.  Takes effect at the next mgrit_solve; other values give
  * SFDE_EINVAL.
  */

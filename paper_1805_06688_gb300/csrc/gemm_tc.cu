@@ -3,8 +3,7 @@
 //
 // One CTA computes a 128 x BN tile of the stacked product (rows = batch slices x R rows each):
 //   * warp 0 / lane 0 streams K-blocks of 128 bytes (64 BF16 or 32 FP32 values) of X and of Mat^T
-//     into a 2-stage ring of 128-byte-swizzled shared-memory tiles with TMA (96 KB at BN = 256, so two
-//     CTAs share an SM and one's epilogue runs beside the other's products);
+//     into a 4-stage ring of 128-byte-swizzled shared-memory tiles with TMA;
 //   * warp 1 / lane 0 issues four tcgen05.mma (K = 16 BF16 / 8 TF32 each) per K-block into the TMEM
 //     accumulator and releases the stage with tcgen05.commit;
 //   * all four warps read the accumulator back (tcgen05.ld, 32 lanes x 32 columns at a time), apply
@@ -23,7 +22,7 @@
 namespace {
 
 constexpr int BM = 128;
-constexpr int STAGES = 2;     // 2 x (16 + 32) KB at BN = 256: two CTAs per SM, one's epilogue beside the other's products
+constexpr int STAGES = 4;
 constexpr int A_STAGE_BYTES = BM * 128;
 constexpr int TMEM_COLS = 256;
 

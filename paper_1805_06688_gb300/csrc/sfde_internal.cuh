@@ -107,7 +107,7 @@ struct sfde_ctx {
                                 // 2 batch <= SMs, else per two slices), 2 pair per slice, 3 pair per two slices
     int resid_digits = 0;       // digits of the tensor-core residual: 0 per iteration, else 4..7 fixed
     int resid_chunk = 0;        // time points per pass of the tensor-core residual (0: ws_slices)
-    int modal_chains = 3;       // 1: coarse-level F-relaxations and coarsest sweeps of the inner
+    int modal_chains = 1;       // 1: coarse-level F-relaxations and coarsest sweeps of the inner
                                 // V-cycles in the step's eigenbasis (transforms, elementwise scan,
                                 // inverse); 2: the fine level's F-relaxations too; 3: as 2 with BF16
                                 // operands, as 1 with TF32; 0: none

@@ -30,7 +30,7 @@ def _err(U, ref):
                                                      (100, 70, 96, 4, "uniform", 8)])
 def test_mixed_matches_sequential(name, prec, nx, ny, nt, m, grid, levels, modal):
     """Mixed precision against the oracle's sequential solution, with the coarse levels' sweeps in the
-    step's eigenbasis (modal 1), every level's (modal 2), by operand type (modal 3, the default: all
+    step's eigenbasis (modal 1, the default), every level's (modal 2), by operand type (modal 3: all
     levels with BF16, the coarse ones with TF32) and none (modal 0)."""
     t = time_grid(nt, 1.0, grid)
     F, _ = gaussian_bump_forcing(5, nx, ny, t)
