@@ -554,7 +554,8 @@ struct LpEngine {
     sfde_status frelax(int l) {
         LpLevel& Lv = M->lev[l];
         const int nc = Lv.N / m;
-        if (modal(l)) {
+        // (the C-point transforms go to T2, ws slices: more intervals than that keep chained steps)
+        if (modal(l) && nc <= (int)M->ws && m - 1 <= (int)M->ws) {
             // C-point values transformed (T2), the interval recurrences, all F-points transformed back
             SFDE_TRY(to_modal(Lv.u, Lv.nalloc, 0, m, nc, M->T2, 1));
             SFDE_TRY(modal_scan(M->T2, Lv.gm, m, 0, M->mY, m, nc, Lv.dt, m, l == 0 ? SCHEME_CN : scheme));
@@ -604,7 +605,7 @@ struct LpEngine {
         if (modal(l)) {
             SFDE_TRY(modal_scan(Lv.gm, Lv.gm, Lv.N + 1, 0, M->mY, Lv.N + 1, 1, Lv.dt, Lv.N + 1,
                                 l == 0 ? SCHEME_CN : scheme));
-            SFDE_TRY(from_modal(M->mY, Lv.N, Lv.N, Lv.u, Lv.N));
+            SFDE_TRY(from_modal(M->mY, Lv.N, Lv.N, slice(Lv.u, 1), 0));   // v_j -> u_j, j = 1..N
             steps += Lv.N;
             return SFDE_OK;
         }
