@@ -88,6 +88,30 @@ def test_spectral_recurrence_equals_stepping():
         assert np.abs(sp[n] - seq[n]).max() <= 1e-13 * np.abs(seq).max()
 
 
+@pytest.mark.parametrize("scheme", ["cn", "be"])
+def test_frelaxation_in_the_eigenbasis(scheme):
+    """The identity the modal sweeps rest on: with W = M V (so W^T V = I, V^T M V = I), the chain
+    u_j = Psi_j(u_{j-1}) + g_j of an F-relaxation (Algorithm 1, propagators (3.2)/(3.4)) is, for
+    v = W_y^T u W_x, the per-mode recurrence v_j = lambda_j o v_{j-1} + W_y^T g_j W_x with the
+    eigenvalues lambda of Eq. (3.7) -- checked against dense solves of the assembled Kronecker
+    system on a graded grid, so a transposed W, a missing mass factor or the wrong eigenvalue
+    (CN against BE) fails."""
+    P = _prob(nx=6, ny=5, nt=7, grid="graded")
+    rng = np.random.default_rng(11 if scheme == "cn" else 12)
+    u = rng.standard_normal((5, 6))
+    g = rng.standard_normal((P.nt, 5, 6))
+    lx, Vx, ly, Vy = P.eig()
+    Wx, Wy = P.Mx @ Vx, P.My @ Vy
+    assert np.abs(Wx.T @ Vx - np.eye(6)).max() < 1e-12 and np.abs(Wy.T @ Vy - np.eye(5)).max() < 1e-12
+    sig = P.sigma()
+    v = Wy.T @ u @ Wx
+    for j in range(1, P.nt + 1):
+        dt = P.t[j] - P.t[j - 1]
+        u = P.propagate(u, dt, scheme, dense=True) + g[j - 1]
+        v = sfde.modal_lambda(sig, dt, scheme) * v + Wy.T @ g[j - 1] @ Wx
+        assert np.abs(Vy @ v @ Vx.T - u).max() <= 1e-12 * np.abs(u).max(), j
+
+
 def _example41_errors(beta, gamma, kx, ky, Ms):
     errs = []
     for M in Ms:
