@@ -257,6 +257,23 @@ def roofline_from_profile(prof, precision: str):
     return roofline, kernels
 
 
+# ----------------------------------------------------------------------------- ranks
+
+def whole_job_rate(seconds_local: float, units_local: float, world: int, device=None):
+    """Whole-job throughput over `world` ranks: the units all ranks processed over the slowest
+    rank's time (max over ranks, one all-reduce each; `device` holds the reduction tensors: the
+    rank's GPU under NCCL, the CPU under gloo).  Returns (units per second, max seconds)."""
+    if world <= 1:
+        return units_local / seconds_local, seconds_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds_local], dtype=torch.float64, device=device)
+    u = torch.tensor([units_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item())
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def run_ours(args, w):
@@ -310,13 +327,9 @@ def run_ours(args, w):
         ev1.record(stream)
         torch.cuda.synchronize(dev)
     barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
     launches = P.profile_read().kernel_launches
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * w.space_time_updates / (ms * 1e-3)
+    value, sec = whole_job_rate(ev0.elapsed_time(ev1) * 1e-3 / args.steps, w.space_time_updates, world, dev)
+    ms = 1e3 * sec
 
     # dominant kernel: per-launch CUDA-event durations over one more solve
     P.profile_enable(True)
@@ -335,12 +348,8 @@ def run_ours(args, w):
         P.set_initial(psi_host)
         P.mgrit(U_T=UT_host, **kw)
     torch.cuda.synchronize(dev)
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": world * w.space_time_updates / e2e_s, "unit": UNIT,
+    e2e_rate, _ = whole_job_rate((time.perf_counter() - t0) / args.steps, w.space_time_updates, world, dev)
+    e2e = {"value": e2e_rate, "unit": UNIT,
            "h2d_bytes_per_step": psi_host.numel() * 8, "d2h_bytes_per_step": UT_host.numel() * 8}
 
     # comparators on the same GPU: FP64 sequential time stepping, and FP64 MGRIT (one solve)
