@@ -18,6 +18,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <new>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -207,6 +208,8 @@ struct SfdeMixed {
     bool fused = false;
     // the fine level's modal buffers exist (its F-relaxations in the eigenbasis too)
     bool modal_fine = false;
+    // every buffer and map of the setup is in place
+    bool ready = false;
 };
 
 void sfde_free_mixed(sfde_ctx* c) {
@@ -254,13 +257,25 @@ sfde_status map_for(SfdeMixed* M, const void* ptr, int R, int C, int ds, long lo
     return SFDE_OK;
 }
 
+sfde_status setup_mixed_body(sfde_ctx* c, int kind, int m, int max_levels, int min_coarse);
+
+// Operands, maps and the inner hierarchy for (kind, m, levels), kept while those stay the same.  A
+// setup that fails part-way is freed whole, so no later call finds a half-built one.
 sfde_status setup_mixed(sfde_ctx* c, int kind, int m, int max_levels, int min_coarse) {
     SfdeMixed* M = c->mixed;
-    if (M && M->kind == kind && M->m == m && M->max_levels == max_levels && M->min_coarse == min_coarse &&
-        M->modal_fine == (c->modal_chains == 2 || (c->modal_chains == 3 && kind == 0)))
+    if (M && M->ready && M->kind == kind && M->m == m && M->max_levels == max_levels &&
+        M->min_coarse == min_coarse && M->modal_fine == (c->modal_chains == 2 || (c->modal_chains == 3 && kind == 0)))
         return SFDE_OK;
     sfde_free_mixed(c);
-    M = new SfdeMixed();
+    const sfde_status st = setup_mixed_body(c, kind, m, max_levels, min_coarse);
+    if (st == SFDE_OK) c->mixed->ready = true;
+    else sfde_free_mixed(c);
+    return st;
+}
+
+sfde_status setup_mixed_body(sfde_ctx* c, int kind, int m, int max_levels, int min_coarse) {
+    SfdeMixed* M = new (std::nothrow) SfdeMixed();
+    if (!M) return SFDE_ENOMEM;
     c->mixed = M;
     M->kind = kind; M->esz = kind == 0 ? 2 : 4; M->m = m; M->max_levels = max_levels; M->min_coarse = min_coarse;
     M->modal_fine = c->modal_chains == 2 || (c->modal_chains == 3 && kind == 0);
