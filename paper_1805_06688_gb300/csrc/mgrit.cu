@@ -32,6 +32,7 @@ sfde_status build_levels(sfde_ctx* c, int m, int max_levels, int min_coarse) {
     if (!c->levels.empty() && c->lev_m == m && c->lev_max == max_levels && c->lev_min == min_coarse)
         return SFDE_OK;
     free_levels(c);
+    c->lev_m = 0;   // set again only once every level is in place: a failed build is never reused
     const size_t P2 = c->P2();
     SfdeLevel L0;
     L0.N = c->nt;
