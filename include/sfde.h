@@ -19,7 +19,8 @@
  * as needed.  All device work runs on the stream given at setup; every call below returns
  * only after that work is finished (synchronous).
  *
- * Errors: every call returns an sfde_status; nothing throws across the ABI.  After
+ * Errors: every call returns an sfde_status; nothing throws across the ABI (a host
+ * allocation or thread start that fails inside a call returns SFDE_ENOMEM).  After
  * SFDE_ECUDA the context must be destroyed.  A context is not thread-safe; distinct
  * contexts are independent.  Ownership: inputs are copied during the call; outputs are
  * caller-allocated; the context owns all internal device memory and frees it in

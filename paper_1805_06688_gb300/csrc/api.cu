@@ -119,9 +119,9 @@ const char* sfde_strerror(sfde_status s) {
     return "unknown status";
 }
 
-sfde_status sfde_setup(double beta, double gamma, double kx, double ky, const double omega[4],
-                       int nx, int ny, const double* t, int nt, const sfde_opts* opts,
-                       sfde_ctx** out) {
+static sfde_status setup_impl(double beta, double gamma, double kx, double ky, const double omega[4],
+                              int nx, int ny, const double* t, int nt, const sfde_opts* opts,
+                              sfde_ctx** out) {
     if (!out) return SFDE_EINVAL;
     *out = nullptr;
     if (!(beta > 0.5 && beta <= 1.0) || !(gamma > 0.5 && gamma <= 1.0)) return SFDE_EINVAL;
@@ -140,34 +140,45 @@ sfde_status sfde_setup(double beta, double gamma, double kx, double ky, const do
     if (!c) return SFDE_ENOMEM;
     c->kx = kx; c->ky = ky; c->nt = nt;
     memcpy(c->omega, om, sizeof(om));
-    c->t.assign(t, t + nt + 1);
     c->precision = prec;
     c->stream = opts ? (cudaStream_t)opts->stream : nullptr;
     sfde_status st = SFDE_OK;
-    do {
-        if ((st = sfde_setup_direction(c->x, nx, beta, om[1] - om[0], c->stream)) != SFDE_OK) break;
-        if ((st = sfde_setup_direction(c->y, ny, gamma, om[3] - om[2], c->stream)) != SFDE_OK) break;
-        std::vector<double> dt(nt);
-        for (int n = 0; n < nt; ++n) dt[n] = t[n + 1] - t[n];
-        cudaError_t e;
+    try {   // a host allocation that throws frees the partial context before the status is returned
+        c->t.assign(t, t + nt + 1);
+        do {
+            if ((st = sfde_setup_direction(c->x, nx, beta, om[1] - om[0], c->stream)) != SFDE_OK) break;
+            if ((st = sfde_setup_direction(c->y, ny, gamma, om[3] - om[2], c->stream)) != SFDE_OK) break;
+            std::vector<double> dt(nt);
+            for (int n = 0; n < nt; ++n) dt[n] = t[n + 1] - t[n];
+            cudaError_t e;
 #define SC(x) if ((e = (x)) != cudaSuccess) { sfde_set_last_cuda_error(e, #x, __FILE__, __LINE__); st = (e == cudaErrorMemoryAllocation) ? SFDE_ENOMEM : SFDE_ECUDA; break; }
-        SC(cudaMalloc(&c->dt0, sizeof(double) * nt));
-        SC(cudaMemcpy(c->dt0, dt.data(), sizeof(double) * nt, cudaMemcpyHostToDevice));
-        SC(cudaMalloc(&c->U0, sizeof(double) * c->P2()));
-        SC(cudaMemsetAsync(c->U0, 0, sizeof(double) * c->P2(), c->stream));
-        SC(cudaMalloc(&c->scalar, sizeof(double) * 4));
-        SC(cudaMallocHost(&c->host_scalar, sizeof(double) * 4));
-        SC(cudaEventCreate(&c->ev0));
-        SC(cudaEventCreate(&c->ev1));
-        SC(cudaStreamSynchronize(c->stream));
+            SC(cudaMalloc(&c->dt0, sizeof(double) * nt));
+            SC(cudaMemcpy(c->dt0, dt.data(), sizeof(double) * nt, cudaMemcpyHostToDevice));
+            SC(cudaMalloc(&c->U0, sizeof(double) * c->P2()));
+            SC(cudaMemsetAsync(c->U0, 0, sizeof(double) * c->P2(), c->stream));
+            SC(cudaMalloc(&c->scalar, sizeof(double) * 4));
+            SC(cudaMallocHost(&c->host_scalar, sizeof(double) * 4));
+            SC(cudaEventCreate(&c->ev0));
+            SC(cudaEventCreate(&c->ev1));
+            SC(cudaStreamSynchronize(c->stream));
 #undef SC
-    } while (0);
+        } while (0);
+    } catch (...) {
+        free_ctx(c);
+        throw;
+    }
     if (st != SFDE_OK) {
         free_ctx(c);
         return st;
     }
     *out = c;
     return SFDE_OK;
+}
+
+sfde_status sfde_setup(double beta, double gamma, double kx, double ky, const double omega[4],
+                       int nx, int ny, const double* t, int nt, const sfde_opts* opts,
+                       sfde_ctx** out) {
+    return sfde_no_throw([&] { return setup_impl(beta, gamma, kx, ky, omega, nx, ny, t, nt, opts, out); });
 }
 
 sfde_status sfde_set_initial(sfde_ctx* c, const double* psi0) {
@@ -185,8 +196,8 @@ sfde_status sfde_set_initial(sfde_ctx* c, const double* psi0) {
     return st;
 }
 
-sfde_status sfde_set_forcing(sfde_ctx* c, int rank, const double* time_w, const double* bx,
-                             const double* by) {
+static sfde_status set_forcing_impl(sfde_ctx* c, int rank, const double* time_w, const double* bx,
+                                    const double* by) {
     if (!c || rank < 0 || rank > SFDE_MAX_RANK) return SFDE_EINVAL;
     cudaFree(c->time_w); cudaFree(c->px); cudaFree(c->py); cudaFree(c->bxn); cudaFree(c->byn);
     c->time_w = c->px = c->py = c->bxn = c->byn = nullptr;
@@ -218,6 +229,11 @@ sfde_status sfde_set_forcing(sfde_ctx* c, int rank, const double* time_w, const 
     cudaFree(bxd);
     cudaFree(byd);
     return st;
+}
+
+sfde_status sfde_set_forcing(sfde_ctx* c, int rank, const double* time_w, const double* bx,
+                             const double* by) {
+    return sfde_no_throw([&] { return set_forcing_impl(c, rank, time_w, bx, by); });
 }
 
 static sfde_status write_outputs(sfde_ctx* c, double* U, double* U_T) {
@@ -261,8 +277,8 @@ static sfde_status write_outputs(sfde_ctx* c, double* U, double* U_T) {
     return SFDE_OK;
 }
 
-sfde_status mgrit_solve(sfde_ctx* c, const mgrit_opts* opts, double* U, double* U_T,
-                        mgrit_stats* stats) {
+static sfde_status mgrit_solve_impl(sfde_ctx* c, const mgrit_opts* opts, double* U, double* U_T,
+                                    mgrit_stats* stats) {
     if (!c) return SFDE_EINVAL;
     mgrit_opts o;
     if (opts) {
@@ -286,13 +302,22 @@ sfde_status mgrit_solve(sfde_ctx* c, const mgrit_opts* opts, double* U, double* 
     return wo != SFDE_OK ? wo : st;
 }
 
-sfde_status seq_timestep(sfde_ctx* c, double* U, double* U_T, double* seconds) {
+sfde_status mgrit_solve(sfde_ctx* c, const mgrit_opts* opts, double* U, double* U_T,
+                        mgrit_stats* stats) {
+    return sfde_no_throw([&] { return mgrit_solve_impl(c, opts, U, U_T, stats); });
+}
+
+static sfde_status seq_timestep_impl(sfde_ctx* c, double* U, double* U_T, double* seconds) {
     if (!c) return SFDE_EINVAL;
     SFDE_TRY(sfde_seq_fp64(c, seconds));
     return write_outputs(c, U, U_T);
 }
 
-sfde_status sfde_step_batch(sfde_ctx* c, int n0, int dn, int batch, const double* in, double* out) {
+sfde_status seq_timestep(sfde_ctx* c, double* U, double* U_T, double* seconds) {
+    return sfde_no_throw([&] { return seq_timestep_impl(c, U, U_T, seconds); });
+}
+
+static sfde_status step_batch_impl(sfde_ctx* c, int n0, int dn, int batch, const double* in, double* out) {
     if (!c || !in || !out || batch < 1) return SFDE_EINVAL;
     long long last = (long long)n0 + (long long)(batch - 1) * dn;
     if (n0 < 1 || n0 > c->nt || last < 1 || last > c->nt) return SFDE_EINVAL;
@@ -324,6 +349,10 @@ done:
 #undef SC
     cudaFree(tin); cudaFree(tout); cudaFree(pin); cudaFree(pout);
     return st;
+}
+
+sfde_status sfde_step_batch(sfde_ctx* c, int n0, int dn, int batch, const double* in, double* out) {
+    return sfde_no_throw([&] { return step_batch_impl(c, n0, dn, batch, in, out); });
 }
 
 sfde_status sfde_get_operator(sfde_ctx* c, int dir, double* coeffs, double* lambda, double* V) {

@@ -19,8 +19,8 @@
 
 #include "sfde_internal.cuh"
 
-extern "C" sfde_status sfde_batch_solve(int n, sfde_ctx* const* ctxs, const mgrit_opts* opts, double* const* U_T,
-                                       mgrit_stats* stats, sfde_status* status) {
+static sfde_status batch_solve_impl(int n, sfde_ctx* const* ctxs, const mgrit_opts* opts, double* const* U_T,
+                                    mgrit_stats* stats, sfde_status* status) {
     if (n < 1 || !ctxs) return SFDE_EINVAL;
     std::unordered_set<const sfde_ctx*> seen;
     for (int i = 0; i < n; ++i)
@@ -64,7 +64,14 @@ extern "C" sfde_status sfde_batch_solve(int n, sfde_ctx* const* ctxs, const mgri
         const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
         const int nth = std::max(1, std::min({n, 16, hw}));
         std::vector<std::thread> pool;
-        for (int t = 1; t < nth; ++t) pool.emplace_back(work);
+        pool.reserve(nth);
+        for (int t = 1; t < nth; ++t) {
+            try {
+                pool.emplace_back(work);
+            } catch (...) {   // no more threads: those running (and this one) take the remaining instances
+                break;
+            }
+        }
         work();
         for (auto& t : pool) t.join();
         for (int i = 0; i < n; ++i)
@@ -78,4 +85,9 @@ extern "C" sfde_status sfde_batch_solve(int n, sfde_ctx* const* ctxs, const mgri
         }
     if (status) std::copy(st.begin(), st.end(), status);
     return first;
+}
+
+extern "C" sfde_status sfde_batch_solve(int n, sfde_ctx* const* ctxs, const mgrit_opts* opts, double* const* U_T,
+                                       mgrit_stats* stats, sfde_status* status) {
+    return sfde_no_throw([&] { return batch_solve_impl(n, ctxs, opts, U_T, stats, status); });
 }

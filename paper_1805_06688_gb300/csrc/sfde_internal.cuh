@@ -166,6 +166,17 @@ struct TcArgs {
                                          // of intervals of oskip + 1 points), else to slice b
 };
 
+// Runs f() and returns its status; a C++ exception from host code (an allocation, a thread that
+// cannot start) becomes SFDE_ENOMEM, so nothing throws across the C ABI.
+template <typename F>
+sfde_status sfde_no_throw(F&& f) noexcept {
+    try {
+        return f();
+    } catch (...) {
+        return SFDE_ENOMEM;
+    }
+}
+
 int sfde_tc_tile_n(int cout);
 sfde_status sfde_tc_prepare();
 sfde_status sfde_tc_map_slices(CUtensorMap* map, const void* base, int esz, int K, int R, int ds, long long nslices);
