@@ -111,6 +111,24 @@ sfde_status sfde_debug_lp_step(sfde_ctx* ctx, int fused, int scheme, const doubl
                                const double* g, const double* ut, double* out, double* norm2);
 
 /*
+ * Host rules of the mixed-precision solver, callable without a GPU.
+ *
+ * sfde_debug_inner_levels: the time points per level of the inner V-cycles' hierarchy for N_t =
+ * nt (Algorithm 1's coarsening by m, levels kept while m divides the level and the coarse level has
+ * at least min_coarse points, at most max_levels; a coarse level whose direct sweep of N steps is
+ * no longer than relaxing it, 3m - 1 steps, plus the sweep below is the coarsest).  Writes the
+ * first min(cap, levels) sizes to `sizes` (host) and the number of levels to *count.
+ * SFDE_EINVAL for nt < 1, m < 2, max_levels < 1, min_coarse < 1, cap < 0, count NULL, or sizes NULL
+ * with cap > 0.
+ *
+ * sfde_debug_residual_digits: digits per operand (4..7) of the tensor-core residual of a
+ * refinement step whose previous residual norm is prev, the first being res0: the fewest with
+ * 2^{9-8 nd} <= 1e-5 prev / res0 (4 when prev or res0 is not positive).  SFDE_EINVAL if nd is NULL.
+ */
+sfde_status sfde_debug_inner_levels(int nt, int m, int max_levels, int min_coarse, int* sizes, int cap, int* count);
+sfde_status sfde_debug_residual_digits(double prev, double res0, int* nd);
+
+/*
  * nchain consecutive low-precision steps from each of `batch` slices (ctx precision MIXED_BF16 or
  * MIXED_TF32), as in the F-relaxation of Algorithm 1:
  *   x_0 = U[b],  x_{k+1} = Phi(x_k) + g[b][k],  out[b][k] = x_{k+1},  k = 0..nchain-1,

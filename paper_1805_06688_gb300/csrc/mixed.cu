@@ -257,6 +257,34 @@ sfde_status map_for(SfdeMixed* M, const void* ptr, int R, int C, int ds, long lo
     return SFDE_OK;
 }
 
+// Time points per level of the inner hierarchy: coarsen by m while the level divides, the coarse
+// level keeps at least min_coarse points and max_levels allows it.  A coarse level whose direct
+// sweep (N steps) is no longer than relaxing it (FCF: 2m - 1 steps, C-point residual: 1, final
+// F-relaxation: m - 1) plus the sweep of the level below is the coarsest: the inner V-cycle's
+// critical path gets shorter and its coarse solve exact.
+std::vector<int> inner_level_sizes(int nt, int m, int max_levels, int min_coarse) {
+    std::vector<int> n{nt};
+    while ((int)n.size() < max_levels) {
+        const int N = n.back();
+        if (N % m != 0 || N / m < min_coarse) break;
+        if (n.size() > 1 && N <= 3 * m - 1 + N / m) break;
+        n.push_back(N / m);
+    }
+    return n;
+}
+
+// Digits per operand of the tensor-core residual: the refinement needs the residual to a fraction
+// of its own size only, about 1e-5 ||rho_{k-1}|| (relative to the first residual res0, a wide
+// margin); the digit products of nd digits are accurate to about 2^{9-8 nd} of the operands' scale.
+// The first residual (prev = 0) takes 4.
+int residual_digits_for(double prev, double res0) {
+    if (!(prev > 0.0) || !(res0 > 0.0)) return 4;
+    const double need = 1e-5 * prev / res0;
+    int nd = 4;
+    while (nd < 7 && ldexp(1.0, 9 - 8 * nd) > need) ++nd;
+    return nd;
+}
+
 sfde_status setup_mixed_body(sfde_ctx* c, int kind, int m, int max_levels, int min_coarse);
 
 // Operands, maps and the inner hierarchy for (kind, m, levels), kept while those stay the same.  A
@@ -317,27 +345,24 @@ sfde_status setup_mixed_body(sfde_ctx* c, int kind, int m, int max_levels, int m
     SFDE_CUDA(cudaMalloc(&M->err, sizeof(int)));
     SFDE_CUDA(cudaMemsetAsync(M->err, 0, sizeof(int), c->stream));
     // inner hierarchy
-    LpLevel L0;
-    L0.N = c->nt; L0.t = c->t; L0.dt = c->dt0;
-    M->lev.push_back(L0);
-    while ((int)M->lev.size() < max_levels) {
-        const LpLevel& F = M->lev.back();
-        if (F.N % m != 0 || F.N / m < min_coarse) break;
-        // a coarse level whose sequential sweep (N steps, one chained launch) is no longer than its
-        // own relaxation (FCF: 2m - 1 steps, C-point residual: 1, final F-relaxation: m - 1) plus
-        // the sweep of the level below is solved directly: the inner V-cycle's critical path gets
-        // shorter and its coarse solve exact
-        if (M->lev.size() > 1 && F.N <= 3 * m - 1 + F.N / m) break;
-        LpLevel G;
-        G.N = F.N / m;
+    const std::vector<int> sizes = inner_level_sizes(c->nt, m, max_levels, min_coarse);
+    for (size_t l = 0; l < sizes.size(); ++l) {
+        M->lev.emplace_back();
+        LpLevel& G = M->lev.back();
+        G.N = sizes[l];
+        if (l == 0) {
+            G.t = c->t;
+            G.dt = c->dt0;
+            continue;
+        }
+        const LpLevel& F = M->lev[l - 1];
         G.t.resize(G.N + 1);
         for (int k = 0; k <= G.N; ++k) G.t[k] = F.t[(size_t)k * m];
         std::vector<double> dt(G.N);
         for (int k = 0; k < G.N; ++k) dt[k] = G.t[k + 1] - G.t[k];
+        G.own_dt = true;
         SFDE_CUDA(cudaMalloc(&G.dt, sizeof(double) * G.N));
         SFDE_CUDA(cudaMemcpy(G.dt, dt.data(), sizeof(double) * G.N, cudaMemcpyHostToDevice));
-        G.own_dt = true;
-        M->lev.push_back(G);
     }
     for (auto& L : M->lev) {
         L.nalloc = ((long long)(L.N + 1 + m - 1) / m) * m + m;
@@ -765,22 +790,13 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
     LpLevel& L0 = M->lev[0];
     sfde_status rc = SFDE_OK;
     long long inner_total = 0;
-    // digits of the tensor-core residual: the refinement needs the residual to a fraction of its own
-    // size only, about 1e-5 ||rho_{k-1}|| (scale: the first residual, with a wide margin); the digit
-    // products of nd digits are accurate to about 2^{9-8 nd} of the operands' scale.  A residual
-    // that passes the stopping test with fewer than 7 digits is recomputed with all 7.
-    auto digits_for = [&](double prev) {
-        if (prev <= 0.0 || S.res0 <= 0.0) return 4;
-        const double need = 1e-5 * prev / S.res0;
-        int nd = 4;
-        while (nd < 7 && ldexp(1.0, 9 - 8 * nd) > need) ++nd;
-        return nd;
-    };
+    // digits of the tensor-core residual per refinement step (residual_digits_for); a residual that
+    // passes the stopping test with fewer than 7 digits is recomputed with all 7
     double prev_nrm = 0.0;
     long long digit_products = 0;
     for (int it = 1; it <= o->max_iter; ++it) {
         // 1. FP64 residual of Eq. (2.4) at n = 1..N_t, stored low precision in g_0[n]
-        int nd = c->resid_digits ? c->resid_digits : digits_for(it == 1 ? 0.0 : prev_nrm);
+        int nd = c->resid_digits ? c->resid_digits : residual_digits_for(it == 1 ? 0.0 : prev_nrm, S.res0);
         double nrm = 0.0;
         for (;;) {
             int np = 0;
@@ -897,6 +913,24 @@ extern "C" sfde_status sfde_debug_set_resid_chunk(sfde_ctx* c, int n) {
 extern "C" sfde_status sfde_debug_set_fused_pair(sfde_ctx* c, int mode) {
     if (!c || mode < 0 || mode > 3) return SFDE_EINVAL;
     c->fused_pair = mode;
+    return SFDE_OK;
+}
+
+extern "C" sfde_status sfde_debug_inner_levels(int nt, int m, int max_levels, int min_coarse, int* sizes, int cap,
+                                              int* count) {
+    if (nt < 1 || m < 2 || max_levels < 1 || min_coarse < 1 || cap < 0 || !count || (cap > 0 && !sizes))
+        return SFDE_EINVAL;
+    return sfde_no_throw([&] {
+        const std::vector<int> n = inner_level_sizes(nt, m, max_levels, min_coarse);
+        *count = (int)n.size();
+        for (int l = 0; l < std::min(cap, (int)n.size()); ++l) sizes[l] = n[l];
+        return SFDE_OK;
+    });
+}
+
+extern "C" sfde_status sfde_debug_residual_digits(double prev, double res0, int* nd) {
+    if (!nd) return SFDE_EINVAL;
+    *nd = residual_digits_for(prev, res0);
     return SFDE_OK;
 }
 

@@ -70,3 +70,55 @@ def test_batch_solve_argument_validation_needs_no_gpu():
     assert L.sfde_batch_solve(0, None, None, None, None, None) == sfde.SFDE_EINVAL
     arr = (C.c_void_p * 2)(None, None)
     assert L.sfde_batch_solve(2, arr, None, None, None, None) == sfde.SFDE_EINVAL
+
+
+def _inner_levels(L, nt, m, max_levels=32, min_coarse=2):
+    sizes = (ctypes.c_int * 16)()
+    count = ctypes.c_int()
+    st = L.sfde_debug_inner_levels(nt, m, max_levels, min_coarse, sizes, 16, ctypes.byref(count))
+    return st, list(sizes[:min(count.value, 16)])
+
+
+def test_inner_hierarchy_rule_needs_no_gpu():
+    """The mixed solver's inner hierarchy (host rule): coarsen by m while it divides and the coarse
+    level keeps min_coarse points; stop at a coarse level whose direct sweep (N steps) is no longer
+    than relaxing it (3m - 1 steps) plus the sweep below."""
+    sfde = _library()
+    L = sfde.lib()
+    L.sfde_debug_inner_levels.argtypes = [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                                                ctypes.POINTER(ctypes.c_int)]
+    # the benchmark: 1024 -> 128 -> 16 (16 <= 23 + 2 stops there, 128 > 23 + 16 does not)
+    assert _inner_levels(L, 1024, 8) == (0, [1024, 128, 16])
+    assert _inner_levels(L, 4096, 16) == (0, [4096, 256, 16])
+    assert _inner_levels(L, 64, 4, max_levels=3) == (0, [64, 16, 4])
+    assert _inner_levels(L, 96, 4, max_levels=8) == (0, [96, 24, 6])      # 6 is not divisible by 4
+    assert _inner_levels(L, 1024, 8, max_levels=2) == (0, [1024, 128])
+    assert _inner_levels(L, 1024, 8, max_levels=1) == (0, [1024])
+    assert _inner_levels(L, 100, 8) == (0, [100])                          # m does not divide N_t
+    assert _inner_levels(L, 64, 8, min_coarse=16) == (0, [64])             # 8 < min_coarse
+    assert _inner_levels(L, 64, 4, max_levels=8) == (0, [64, 16, 4])       # 16 > 11 + 4: relaxed
+    for bad in ((0, 8, 32, 2), (64, 1, 32, 2), (64, 4, 0, 2), (64, 4, 8, 0)):
+        assert _inner_levels(L, *bad)[0] == sfde.SFDE_EINVAL
+
+
+def test_residual_digits_rule_needs_no_gpu():
+    """Digits per operand of the tensor-core residual: the fewest nd in 4..7 whose products are
+    accurate to 2^{9-8nd} <= 1e-5 prev / res0."""
+    sfde = _library()
+    L = sfde.lib()
+    L.sfde_debug_residual_digits.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
+
+    def nd(prev, res0):
+        v = ctypes.c_int()
+        assert L.sfde_debug_residual_digits(prev, res0, ctypes.byref(v)) == 0
+        return v.value
+
+    assert nd(0.0, 1.0) == 4 and nd(1.0, 0.0) == 4 and nd(float("nan"), 1.0) == 4
+    assert nd(1.0, 1.0) == 4          # need 1e-5: 2^-23 = 1.2e-7 suffices
+    assert nd(2e-2, 1.0) == 4         # need 2e-7: 2^-23 = 1.2e-7 suffices
+    assert nd(1e-2, 1.0) == 5         # need 1e-7: 2^-23 just too coarse
+    assert nd(1e-3, 1.0) == 5         # need 1e-8: 2^-23 too coarse, 2^-31 = 4.7e-10
+    assert nd(1e-6, 1.0) == 6         # need 1e-11: 2^-39 = 1.8e-12
+    assert nd(1e-9, 1.0) == 7         # need 1e-14: 2^-47 = 7.1e-15
+    assert nd(1e-20, 1.0) == 7        # capped
+    assert nd(3e-4, 3.0) == nd(1e-4, 1.0)
