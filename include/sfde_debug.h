@@ -126,6 +126,18 @@ sfde_status sfde_debug_lp_step(sfde_ctx* ctx, int fused, int scheme, const doubl
  * 2^{9-8 nd} <= 1e-5 prev / res0 (4 when prev or res0 is not positive).  SFDE_EINVAL if nd is NULL.
  */
 sfde_status sfde_debug_inner_levels(int nt, int m, int max_levels, int min_coarse, int* sizes, int cap, int* count);
+
+/*
+ * Theorem 3.1's two-level bound (Eq. (3.11)) as the solver evaluates it to choose the coarse
+ * propagator under SFDE_COARSE_AUTO, without a GPU: the maximum over the modes sigma = K_x lx[i] +
+ * K_y ly[j] of (lam+)^m |(lam+)^m - mu++| (1 - (mu*)^{N_c - 1}) / (1 - mu*), with lam+ the largest
+ * |fine CN factor| over the steps of t, mu++ the smallest and mu* the largest |coarse factor| over
+ * the m-coarsened steps (coarse SFDE_COARSE_CN or SFDE_COARSE_BE), eigenvalues of Eq. (3.7).
+ * lx: nx, ly: ny generalised eigenvalues (host); t: nt + 1 increasing time points (host).  *out is
+ * +infinity when m does not divide nt or the coarse grid has fewer than two intervals.
+ */
+sfde_status sfde_debug_tub_bound(const double* lx, int nx, const double* ly, int ny, double kx, double ky,
+                                 const double* t, int nt, int m, int coarse, double* out);
 sfde_status sfde_debug_residual_digits(double prev, double res0, int* nd);
 
 /*

@@ -215,6 +215,18 @@ sfde_status sfde_level0(sfde_ctx* c, double** u) {
     return SFDE_OK;
 }
 
+extern "C" sfde_status sfde_debug_tub_bound(const double* lx, int nx, const double* ly, int ny, double kx, double ky,
+                                           const double* t, int nt, int m, int coarse, double* out) {
+    if (!lx || !ly || !t || !out || nx < 1 || ny < 1 || nt < 1 || m < 2 ||
+        (coarse != SFDE_COARSE_CN && coarse != SFDE_COARSE_BE))
+        return SFDE_EINVAL;
+    return sfde_no_throw([&] {
+        *out = tub_bound_host(std::vector<double>(lx, lx + nx), std::vector<double>(ly, ly + ny), nx, ny, kx, ky,
+                              std::vector<double>(t, t + nt + 1), m, coarse);
+        return SFDE_OK;
+    });
+}
+
 // Coarse propagator for this solve: the requested one, or for AUTO the paper's CN rediscretisation
 // when Theorem 3.1's bound (3.11) on the actual eigenvalues is below 1, backward Euler otherwise.
 sfde_status sfde_choose_coarse(sfde_ctx* c, int m, int requested, int* coarse, double* tub) {

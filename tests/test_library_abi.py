@@ -122,3 +122,35 @@ def test_residual_digits_rule_needs_no_gpu():
     assert nd(1e-9, 1.0) == 7         # need 1e-14: 2^-47 = 7.1e-15
     assert nd(1e-20, 1.0) == 7        # capped
     assert nd(3e-4, 3.0) == nd(1e-4, 1.0)
+
+
+@pytest.mark.parametrize("grid,m,coarse", [("uniform", 8, "cn"), ("uniform", 4, "be"), ("graded", 4, "cn"),
+                                           ("graded", 8, "be")])
+def test_theorem31_bound_matches_oracle(grid, m, coarse):
+    """The Theorem 3.1 bound (3.11) that picks the coarse propagator under COARSE_AUTO (host code of
+    the library, extremes over the steps) equals the oracle's evaluation over every step size."""
+    import numpy as np
+    from oracle import analysis
+    from oracle import sfde as osfde
+    from sfde_workloads import time_grid
+    sfde = _library()
+    L = sfde.lib()
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.sfde_debug_tub_bound.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+    nt = 64
+    t = time_grid(nt, 1.0, grid)
+    P = osfde.SFDE(0.7, 0.85, 1.3, 0.6, 23, 17, t)
+    lx, _, ly, _ = P.eig()
+    ref = analysis.tub_bound(P.sigma(), t, m, coarse)
+    out = ctypes.c_double()
+    c = {"cn": sfde.COARSE_CN, "be": sfde.COARSE_BE}[coarse]
+    st = L.sfde_debug_tub_bound(np.ascontiguousarray(lx).ctypes.data_as(dp), len(lx),
+                                np.ascontiguousarray(ly).ctypes.data_as(dp), len(ly), 1.3, 0.6,
+                                np.ascontiguousarray(t).ctypes.data_as(dp), nt, m, c, ctypes.byref(out))
+    assert st == 0
+    assert abs(out.value - ref) <= 1e-12 * max(1.0, abs(ref)), (out.value, ref)
+    st = L.sfde_debug_tub_bound(np.ascontiguousarray(lx).ctypes.data_as(dp), len(lx),
+                                np.ascontiguousarray(ly).ctypes.data_as(dp), len(ly), 1.3, 0.6,
+                                np.ascontiguousarray(t).ctypes.data_as(dp), nt, m, 7, ctypes.byref(out))
+    assert st == sfde.SFDE_EINVAL
