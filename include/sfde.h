@@ -42,7 +42,7 @@ typedef enum {
     SFDE_ECUDA = 3,         /* a CUDA runtime call or kernel failed; context unusable    */
     SFDE_ENOCONV = 4,       /* no convergence within max_iter, or a non-finite residual  */
     SFDE_ETIMEOUT = 5,      /* a bounded device wait ran out                             */
-    SFDE_EUNSUPPORTED = 6,  /* option not available in this build                        */
+    SFDE_EUNSUPPORTED = 6,  /* option or size the library does not provide               */
     SFDE_ESCRATCH = 7       /* request larger than the fixed scratch of sfde_step_batch_noalloc */
 } sfde_status;
 
