@@ -3,14 +3,15 @@
 // The iterate U (all time points) is FP64.  One outer iteration
 //   1. forms the space-time residual of Eq. (2.4) to FP64 accuracy,
 //          rho_n = F_n + B_n U_{n-1} - S_n U_n = F_n + M_h (U_{n-1} - U_n) - tau_n K (U_{n-1} + U_n),
-//      (P <= 256: exact integer arithmetic around two digit-split tensor-core products per time
-//      point, resid_int.cu; larger P: FP64 slice GEMMs) and its norm, and stores rho in BF16/FP32;
+//      (P <= 256 or a multiple of 256 up to 1024: exact integer arithmetic around two digit-split
+//      tensor-core products per time point, resid_int.cu; other P: FP64 slice GEMMs) and its norm,
+//      and stores rho in BF16/FP32;
 //   2. turns it into the right-hand side of the correction system in Psi form, g_n = S_n^{-1} rho_n
-//      (the fast-diagonalisation solve, four tensor-core slice GEMMs per time point), so that the
+//      (the fast-diagonalisation solve, one batched spectral step in solve mode), so that the
 //      correction E solves E_n = Psi_n E_{n-1} + g_n, E_0 = 0 -- the system of Eq. (3.1) again;
-//   3. runs V-cycles of Algorithm 1 on that system with every step a tensor-core spectral step
-//      (BF16 or TF32 operands, FP32 accumulation) until the inner C-point residual has dropped by
-//      `inner_tol`;
+//   3. runs K V-cycles of Algorithm 1 on that system (K = 4 BF16, 5 TF32, or mgrit_opts.inner_cycles)
+//      with every step a tensor-core spectral step (BF16 or TF32 operands, FP32 accumulation); the
+//      coarse levels' sweeps run in the step's eigenbasis;
 //   4. adds E to U in FP64.
 // The low-precision V-cycles converge to the fixed point of the rounded propagator, whose distance
 // from the exact correction (about 2e-2 relative for BF16 and 3e-3 for TF32 at the benchmark sizes)
