@@ -10,15 +10,17 @@
 //   2. per pair (n-1, n) with E = max(E_{n-1}, E_n): the fixed-point values fix(u) = round(u 2^{54-E})
 //      (|fix| <= 2^54) and V = fix(U_{n-1}) + fix(U_n), exact, written as seven balanced base-256
 //      digits of V (BF16-exact, no remainder) in row-major and in transposed order;
-//   3. Z1 = V (K_x h_y/6 A_x) and Z2 = (K_y h_x/6 A_y) V on the tensor cores (ozaki.cu, 28 digit
-//      products), each an int64 in units of 2^{-52} of the operands' scales;
+//   3. Z1 = V (K_x h_y/6 A_x) and Z2 = (K_y h_x/6 A_y) V on the tensor cores (ozaki.cu, up to 28
+//      digit products: 4 to 7 digits per operand as the refinement step needs), each an int64 in
+//      units of 2^{-52} of the operands' scales;
 //   4. with the mass matrices M = (h/6) tridiag(1, 4, 1) in both directions (they commute with the
 //      products: A_y (V M_x) = (A_y V) M_x),
 //          K V = (1,4,1)_y Z1 + (1,4,1)_x Z2      (integer, aligned to a common power of two),
 //          M_h (U_{n-1} - U_n) = (h_x h_y / 36) (1,4,1)_y (1,4,1)_x du,  du = fix(U_{n-1}) - fix(U_n)
 //      (du written by step 2 as int64),
-//      and rho = F + c_m S9 - tau c_s S in FP64: two FMAs per element (the int64 -> FP64
-//      conversions are built from bits); the sum of rho^2 is taken over the stored FP32 values.
+//      and rho = c_m S9 - tau c_s S formed exactly in 128-bit integers and converted to FP32 (with a
+//      load term F: rho = F + c_m S9 - tau c_s S in FP64, two FMAs per element, the int64 -> FP64
+//      conversions built from bits); the sum of rho^2 is taken over the stored FP32 values.
 // The fixed-point grid of a pair is 2^{E-54}: values far below the slice maximum keep an absolute
 // accuracy of 2^{-55} max|U|, the scale at which an FP64 product's rounding errors enter the residual.
 #include <cuda_bf16.h>
