@@ -112,11 +112,11 @@ def test_frelaxation_in_the_eigenbasis(scheme):
         assert np.abs(Vy @ v @ Vx.T - u).max() <= 1e-12 * np.abs(u).max(), j
 
 
-def _example41_errors(beta, gamma, kx, ky, Ms):
+def _example41_errors(beta, gamma, kx, ky, Ms, grid="uniform", eps=None):
     errs = []
     for M in Ms:
         n = M - 1
-        t = time_grid(M, 1.0)
+        t = time_grid(M, 1.0, grid, eps=eps)
         P = sfde.SFDE(beta, gamma, kx, ky, n, n, t)
         U0 = manufactured_initial(n, n, "10exp(-t)")
         F = manufactured_forcing(n, n, t, beta, gamma, kx, ky, "10exp(-t)")
@@ -133,6 +133,21 @@ def test_saturation_error_order_example_4_1(pair):
     tab = json.load(open(GOLDEN))["table1"]
     b, g = (float(v) for v in pair.replace("beta", "").split("_gamma"))
     errs = _example41_errors(b, g, 2.0, 0.5, tab["M"])
+    rates = np.log2(errs[:-1] / errs[1:])
+    assert np.all(rates > 1.75) and np.all(rates < 2.3), rates
+    ratio = errs / np.array(tab[pair])
+    assert np.all(ratio > 0.5) and np.all(ratio < 1.6), ratio
+
+
+@pytest.mark.parametrize("pair", ["beta0.6_gamma0.7", "beta0.95_gamma0.65", "beta0.8_gamma0.8"])
+def test_saturation_error_order_piecewise_uniform_grid(pair):
+    """Example 4.1 on the piecewise uniform partition of Sec. 4.1 (Table 3 setting: N = 1/h,
+    eps = 2^-6, K_x = 3.0, K_y = 7.5): the O(h^2 + tau^2) order carries over to the nonuniform
+    steps, and the errors are of the printed magnitude (printed for P1 triangles; this is the
+    tensor-product operator)."""
+    tab = json.load(open(GOLDEN))["table3"]
+    b, g = (float(v) for v in pair.replace("beta", "").split("_gamma"))
+    errs = _example41_errors(b, g, 3.0, 7.5, tab["M"], "shishkin", tab["eps"])
     rates = np.log2(errs[:-1] / errs[1:])
     assert np.all(rates > 1.75) and np.all(rates < 2.3), rates
     ratio = errs / np.array(tab[pair])
