@@ -243,6 +243,38 @@ typedef struct {
 sfde_status sfde_profile_enable(sfde_ctx* ctx, int enable);
 sfde_status sfde_profile_read(sfde_ctx* ctx, sfde_profile* out);
 
+/*
+ * Execution choices of the mixed-precision solver.  They change its speed, not its fixed point:
+ * every choice solves the same system to the same tolerance (results agree to rounding).
+ */
+typedef struct {
+    int fused_pair;      /* fused BF16 step at P = 256: 1 a CTA pair per slice where 2 x batch <= SMs,
+                            else per two slices (default); 2 always per slice; 3 always per two
+                            slices; 0 one CTA per slice                                        */
+    int modal_chains;    /* F-relaxations in the step's eigenbasis: 1 coarse levels (default),
+                            2 every level, 3 every level with BF16 operands, 0 none            */
+    int inner_cycles;    /* V-cycles per refinement step when mgrit_opts.inner_cycles is 0;
+                            0 = 4 (BF16) / 5 (TF32)                                           */
+    double ms;           /* measured solve time of this choice (milliseconds; 0 = unmeasured)  */
+} sfde_tuning;
+
+/*
+ * sfde_set_tuning -- applies t to ctx for the following solves.  SFDE_EINVAL for a NULL argument
+ * or a field out of the ranges above (inner_cycles 0..64).
+ *
+ * sfde_autotune -- picks the fastest of a small fixed set of choices for this context's problem
+ * (padded sizes, N_t, time grid, precision) and the given options: each candidate is applied and
+ * timed over one untimed and two timed full solves (device time, the smaller counted); only
+ * candidates whose solves converge count.  The winner is applied to ctx and returned in *out (may
+ * be NULL).  With cache_path (may be NULL) the choice is first looked up in that text file (lines
+ * "<key> <fused_pair> <modal_chains> <inner_cycles> <ms>", the last line for the key counts) and,
+ * when measured, appended to it.  The context's iterate is overwritten by the trial solves.  FP64
+ * contexts have nothing to tune: *out receives the current settings and SFDE_OK is returned.
+ * Returns the status of the last trial when no candidate converged (settings left unchanged).
+ */
+sfde_status sfde_set_tuning(sfde_ctx* ctx, const sfde_tuning* t);
+sfde_status sfde_autotune(sfde_ctx* ctx, const mgrit_opts* opts, const char* cache_path, sfde_tuning* out);
+
 void sfde_destroy(sfde_ctx* ctx);
 const char* sfde_strerror(sfde_status status);
 

@@ -141,6 +141,19 @@ sfde_status sfde_debug_tub_bound(const double* lx, int nx, const double* ly, int
 sfde_status sfde_debug_residual_digits(double prev, double res0, int* nd);
 
 /*
+ * Host parts of sfde_autotune, callable without a GPU.
+ * sfde_debug_tune_pick: *best = the index of the candidate with the smallest positive finite ms
+ *   (the first on ties), -1 when none has one.  SFDE_EINVAL for n < 0 or NULL pointers (c may be
+ *   NULL when n = 0).
+ * sfde_debug_tune_cache: store != 0 appends the line for (key, *t) to the text file at path;
+ *   store == 0 reads the last valid line for key into *t and sets *found (0 when the file or the
+ *   key is missing; malformed lines and out-of-range fields are skipped).  key: 1..255 characters
+ *   without white space, else SFDE_EINVAL; SFDE_EINVAL too when the file cannot be written.
+ */
+sfde_status sfde_debug_tune_pick(const sfde_tuning* c, int n, int* best);
+sfde_status sfde_debug_tune_cache(const char* path, const char* key, int store, sfde_tuning* t, int* found);
+
+/*
  * nchain consecutive low-precision steps from each of `batch` slices (ctx precision MIXED_BF16 or
  * MIXED_TF32), as in the F-relaxation of Algorithm 1:
  *   x_0 = U[b],  x_{k+1} = Phi(x_k) + g[b][k],  out[b][k] = x_{k+1},  k = 0..nchain-1,

@@ -12,5 +12,6 @@ from ._binding import (  # noqa: F401
     COARSE_AUTO, SfdeError, MgritOpts, MgritStats, SfdeOpts, lib, library_path, exported_symbols,
     sfde_setup, sfde_set_initial, sfde_set_forcing, mgrit_solve, seq_timestep, sfde_step_batch,
     sfde_get_operator, sfde_profile_enable, sfde_profile_read, SfdeProfile, sfde_destroy,
-    sfde_strerror, make_opts, Problem, sfde_batch_solve, batch_solve,
+    sfde_strerror, make_opts, Problem, sfde_batch_solve, batch_solve, SfdeTuning, sfde_set_tuning,
+    sfde_autotune,
 )

@@ -21,7 +21,7 @@ HISTORY_MAX = 512
 exported_symbols = (
     "sfde_setup", "sfde_set_initial", "sfde_set_forcing", "mgrit_solve", "seq_timestep",
     "sfde_step_batch", "sfde_step_batch_noalloc", "sfde_get_operator", "sfde_profile_enable", "sfde_profile_read",
-    "sfde_destroy", "sfde_strerror", "sfde_batch_solve",
+    "sfde_destroy", "sfde_strerror", "sfde_batch_solve", "sfde_set_tuning", "sfde_autotune",
 )
 
 
@@ -49,6 +49,11 @@ class MgritOpts(C.Structure):
                 ("relax", C.c_int), ("coarse", C.c_int), ("max_iter", C.c_int),
                 ("rel_tol", C.c_double), ("abs_tol", C.c_double), ("init_seed", C.c_uint64),
                 ("inner_cycles", C.c_int)]
+
+
+class SfdeTuning(C.Structure):
+    _fields_ = [("fused_pair", C.c_int), ("modal_chains", C.c_int), ("inner_cycles", C.c_int),
+                ("ms", C.c_double)]
 
 
 class MgritStats(C.Structure):
@@ -87,6 +92,8 @@ def lib() -> C.CDLL:
         L.sfde_profile_read.argtypes = [vp, C.POINTER(SfdeProfile)]
         L.sfde_batch_solve.argtypes = [ip, C.POINTER(vp), C.POINTER(MgritOpts), C.POINTER(vp),
                                        C.POINTER(MgritStats), C.POINTER(ip)]
+        L.sfde_set_tuning.argtypes = [vp, C.POINTER(SfdeTuning)]
+        L.sfde_autotune.argtypes = [vp, C.POINTER(MgritOpts), C.c_char_p, C.POINTER(SfdeTuning)]
         L.sfde_destroy.argtypes = [vp]
         L.sfde_destroy.restype = None
         L.sfde_strerror.argtypes = [ip]
@@ -206,6 +213,18 @@ def sfde_profile_read(ctx) -> SfdeProfile:
     return p
 
 
+def sfde_set_tuning(ctx, fused_pair=1, modal_chains=1, inner_cycles=0):
+    t = SfdeTuning(int(fused_pair), int(modal_chains), int(inner_cycles), 0.0)
+    _check(lib().sfde_set_tuning(ctx, C.byref(t)), "sfde_set_tuning")
+
+
+def sfde_autotune(ctx, opts: MgritOpts, cache_path=None) -> SfdeTuning:
+    t = SfdeTuning()
+    path = None if cache_path is None else os.fsencode(cache_path)
+    _check(lib().sfde_autotune(ctx, C.byref(opts), path, C.byref(t)), "sfde_autotune")
+    return t
+
+
 def sfde_destroy(ctx):
     if ctx:
         lib().sfde_destroy(ctx)
@@ -256,6 +275,14 @@ class Problem:
 
     def operator(self, direction):
         return sfde_get_operator(self.ctx, direction, self.nx if direction == 0 else self.ny)
+
+    def set_tuning(self, fused_pair=1, modal_chains=1, inner_cycles=0):
+        sfde_set_tuning(self.ctx, fused_pair, modal_chains, inner_cycles)
+
+    def autotune(self, cache_path=None, **kw) -> SfdeTuning:
+        """Times the solver's execution choices on this problem with the options ``kw`` (as for
+        ``mgrit``) and keeps the fastest; overwrites the iterate."""
+        return sfde_autotune(self.ctx, make_opts(**kw), cache_path)
 
     def profile_enable(self, enable=True):
         sfde_profile_enable(self.ctx, enable)

@@ -769,7 +769,8 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
     // floor (about 2e-2 BF16, 3e-3 TF32) at MGRIT contraction ~0.3 per V-cycle.  (Raising K when the
     // refinement contracts slowly does not help: there the floor itself is high -- rounding
     // accumulated over long stiff runs -- and more V-cycles only add time.)
-    const int K = o->inner_cycles > 0 ? o->inner_cycles : (kind == 0 ? 4 : 5);
+    const int K = o->inner_cycles > 0 ? o->inner_cycles
+                : c->inner_cycles_tuned > 0 ? c->inner_cycles_tuned : (kind == 0 ? 4 : 5);
     // the inner solve is captured once as CUDA graphs and replayed; eager while kernels are timed
     const bool use_graph = !c->prof.on;
     const long long key = ((long long)c->modal_chains << 28) | ((long long)c->fused_pair << 24) | ((long long)M->fused << 20) |

@@ -107,6 +107,8 @@ struct sfde_ctx {
                                 // 2 batch <= SMs, else per two slices), 2 pair per slice, 3 pair per two slices
     int resid_digits = 0;       // digits of the tensor-core residual: 0 per iteration, else 4..7 fixed
     int resid_chunk = 0;        // time points per pass of the tensor-core residual (0: ws_slices)
+    int inner_cycles_tuned = 0; // V-cycles per refinement step when mgrit_opts.inner_cycles is 0
+                                // (0: the built-in 4 / 5); set by sfde_set_tuning / sfde_autotune
     int modal_chains = 1;       // 1: coarse-level F-relaxations and coarsest sweeps of the inner
                                 // V-cycles in the step's eigenbasis (transforms, elementwise scan,
                                 // inverse); 2: the fine level's F-relaxations too; 3: as 2 with BF16

@@ -154,3 +154,70 @@ def test_theorem31_bound_matches_oracle(grid, m, coarse):
                                 np.ascontiguousarray(ly).ctypes.data_as(dp), len(ly), 1.3, 0.6,
                                 np.ascontiguousarray(t).ctypes.data_as(dp), nt, m, 7, ctypes.byref(out))
     assert st == sfde.SFDE_EINVAL
+
+
+def _tuning_lib():
+    sfde = _library()
+    L = sfde.lib()
+    tp = ctypes.POINTER(sfde.SfdeTuning)
+    L.sfde_debug_tune_pick.argtypes = [tp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.sfde_debug_tune_cache.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int, tp,
+                                        ctypes.POINTER(ctypes.c_int)]
+    return sfde, L
+
+
+def test_autotune_pick_needs_no_gpu():
+    """The autotuner keeps the fastest measured choice: smallest positive finite time, the first on
+    ties; unmeasured (0), failed (inf, nan) and negative entries never win."""
+    sfde, L = _tuning_lib()
+    T = sfde.SfdeTuning
+
+    def pick(times):
+        arr = (T * max(1, len(times)))(*[T(1, 1, 0, v) for v in times])
+        best = ctypes.c_int()
+        assert L.sfde_debug_tune_pick(arr, len(times), ctypes.byref(best)) == 0
+        return best.value
+
+    assert pick([]) == -1
+    assert pick([0.0, 0.0]) == -1
+    assert pick([5.0, 3.0, 4.0]) == 1
+    assert pick([3.0, 5.0, 3.0]) == 0
+    assert pick([float("inf"), float("nan"), -1.0, 0.0, 7.5]) == 4
+    assert L.sfde_debug_tune_pick(None, 2, ctypes.byref(ctypes.c_int())) == sfde.SFDE_EINVAL
+
+
+def test_autotune_cache_file_needs_no_gpu(tmp_path):
+    """The tuning cache: one text line per measurement, the last valid line for a key counts,
+    other keys and malformed or out-of-range lines are ignored, a missing file is a miss."""
+    sfde, L = _tuning_lib()
+    T = sfde.SfdeTuning
+    path = str(tmp_path / "tune.txt").encode()
+    found = ctypes.c_int(7)
+    t = T()
+    assert L.sfde_debug_tune_cache(path, b"P256x256_nt1024", 0, ctypes.byref(t), ctypes.byref(found)) == 0
+    assert found.value == 0
+    for key, v in ((b"P256x256_nt1024", T(1, 1, 0, 55.4)), (b"P512x512_nt2048", T(1, 3, 5, 900.0)),
+                   (b"P256x256_nt1024", T(3, 3, 0, 52.4))):
+        assert L.sfde_debug_tune_cache(path, key, 1, ctypes.byref(v), None) == 0
+    with open(path, "a") as f:
+        f.write("P256x256_nt1024 9 1 0 1.0\n")        # fused_pair out of range: skipped
+        f.write("P256x256_nt1024 1 1\n")              # malformed: skipped
+        f.write("\n")
+    assert L.sfde_debug_tune_cache(path, b"P256x256_nt1024", 0, ctypes.byref(t), ctypes.byref(found)) == 0
+    assert found.value == 1 and (t.fused_pair, t.modal_chains, t.inner_cycles) == (3, 3, 0)
+    assert abs(t.ms - 52.4) < 1e-9
+    assert L.sfde_debug_tune_cache(path, b"P512x512_nt2048", 0, ctypes.byref(t), ctypes.byref(found)) == 0
+    assert found.value == 1 and (t.fused_pair, t.modal_chains, t.inner_cycles) == (1, 3, 5)
+    assert L.sfde_debug_tune_cache(path, b"P128x128_nt64", 0, ctypes.byref(t), ctypes.byref(found)) == 0
+    assert found.value == 0
+    bad = T(1, 4, 0, 1.0)
+    assert L.sfde_debug_tune_cache(path, b"k", 1, ctypes.byref(bad), None) == sfde.SFDE_EINVAL
+    assert L.sfde_debug_tune_cache(path, b"two words", 0, ctypes.byref(t), ctypes.byref(found)) == sfde.SFDE_EINVAL
+    assert L.sfde_debug_tune_cache(path, b"", 0, ctypes.byref(t), ctypes.byref(found)) == sfde.SFDE_EINVAL
+
+
+def test_set_tuning_and_autotune_validate_arguments_without_gpu():
+    sfde, L = _tuning_lib()
+    t = sfde.SfdeTuning(1, 1, 0, 0.0)
+    assert L.sfde_set_tuning(None, ctypes.byref(t)) == sfde.SFDE_EINVAL
+    assert L.sfde_autotune(None, None, None, None) == sfde.SFDE_EINVAL
