@@ -97,6 +97,15 @@ sfde_status sfde_set_initial(sfde_ctx* ctx, const double* psi0);
 sfde_status sfde_set_forcing(sfde_ctx* ctx, int rank, const double* time_w, const double* bx,
                              const double* by);
 
+/*
+ * Dense (non-separable) load vectors (Sec. 2, below Eq. (2.4)): F holds N_t x N_y x N_x doubles,
+ * F[((n-1)*N_y + j)*N_x + i] = (f, phi_i phi_j) integrated over I_n, n = 1..N_t; host or device,
+ * copied during the call.  NULL clears the load.  Replaces any load set before (separable or
+ * dense), as sfde_set_forcing replaces a dense one.  The library keeps F and its eigenbasis
+ * transform V_y^T F_n V_x on the device (2 N_t P_x P_y doubles).  SFDE_ENOMEM if they do not fit.
+ */
+sfde_status sfde_set_forcing_dense(sfde_ctx* ctx, const double* F);
+
 typedef enum { SFDE_RELAX_FCF = 0, SFDE_RELAX_F = 1 } sfde_relax;
 typedef enum {
     SFDE_COARSE_CN = 0,    /* rediscretisation with the same Crank-Nicolson-type step, Eq. (3.4) */
@@ -113,11 +122,25 @@ typedef struct {
     int coarse;          /* sfde_coarse                                                       */
     int max_iter;        /* >= 1                                                              */
     double rel_tol;      /* stop when ||r||_2 <= max(rel_tol*||r_first||_2, abs_tol); r is the  */
-    double abs_tol;      /* C-point residual Phi_{km}(u_{km-1}) - u_{km} over all level-0 C-points */
+    double abs_tol;      /* C-point residual Phi_{km}(u_{km-1}) - u_{km} over all level-0 C-points
+                            (or, see stop_kind, the space-time residual)                       */
     uint64_t init_seed;  /* 0: zero initial guess; else SplitMix64 uniform[-1,1) values at
                             t_1..t_N, value index (n*N_y + j)*N_x + i (Sec. 3.2)              */
     int inner_cycles;    /* mixed precision only: low-precision V-cycles per FP64 refinement step
                             (0 = default: 4 for BF16, 5 for TF32)                             */
+    int skip_first_down; /* 1: the option "skip work on the first down cycle" (Sec. 3.2): the first
+                            V-cycle relaxes on no level on its way down -- the coarse right-hand
+                            side is the injected C-point residual of the initial guess -- and runs
+                            the coarsest solve and the up-cycle as usual.  That iteration applies no
+                            stopping test; the C-point reference norm is then the second
+                            iteration's.  In the mixed forms it applies to the first V-cycle of every
+                            inner solve (each starts from a zero correction).  0: off.          */
+    int stop_kind;       /* residual of the stopping test: 0 the form's own (FP64: the C-point
+                            residual above; mixed: the space-time residual below); 1 the space-time
+                            residual of Eq. (2.4), rho_n = F_n + B_n u_{n-1} - S_n u_n over
+                            n = 1..N_t, in FP64, relative to rho of the initial guess -- the same
+                            test in every form.  The FP64 form evaluates it after the relaxation,
+                            where every F-point's row of Eq. (3.1) holds and rho_{km} = S_{km} r_k. */
 } mgrit_opts;
 
 #define SFDE_HISTORY_MAX 512
@@ -202,8 +225,12 @@ sfde_status sfde_step_batch(sfde_ctx* ctx, int n0, int dn, int batch, const doub
  * stream before reading `out`.  All calls, from every context on a device, share the one array:
  * calls whose work overlaps on the GPU (different streams, or different host threads) race and must
  * be serialised by the caller.  Each call writes every scratch element it reads, so no clearing is
- * needed between calls.  On the first call for a device (with that device current) the library looks
- * up the array's device address once and caches it; make that first call before any stream capture.
+ * needed between calls.  The device that was current when the context was set up must be current
+ * for the call (SFDE_EINVAL otherwise): the array's address differs per device.  On the first call
+ * for a device the library looks up the array's device address once and caches it; make that first
+ * call before any stream capture.  The cached address assumes the device is not reset
+ * (cudaDeviceReset) while the library is loaded; a call that fails with SFDE_ECUDA drops the cached
+ * address so that the next call looks it up again.
  */
 #define SFDE_NOALLOC_SCRATCH_DOUBLES (5u * 262144u)
 sfde_status sfde_step_batch_noalloc(sfde_ctx* ctx, int n0, int dn, int batch, const double* in,
@@ -263,7 +290,8 @@ typedef struct {
  * or a field out of the ranges above (inner_cycles 0..64).
  *
  * sfde_autotune -- picks the fastest of a small fixed set of choices for this context's problem
- * (padded sizes, N_t, time grid, precision) and the given options: each candidate is applied and
+ * (cache key: padded sizes, fractional orders, K_x, K_y, N_t, T, step spread and a hash of the time
+ * points, precision) and the given options: each candidate is applied and
  * timed over one untimed and two timed full solves (device time, the smaller counted); only
  * candidates whose solves converge count.  The winner is applied to ctx and returned in *out (may
  * be NULL).  With cache_path (may be NULL) the choice is first looked up in that text file (lines

@@ -23,7 +23,14 @@ Algorithm 1 with the readings used throughout this project:
   an F-relaxation; on level 0 F-points are refreshed by the next iteration's relaxation
   (the remark after Algorithm 1);
 * stopping: ||r||_2 over all level-0 C-points <= max(rel_tol * ||r^(first)||_2, abs_tol), tested
-  right after the level-0 residual (so the returned iterate is F-consistent).
+  right after the level-0 residual (so the returned iterate is F-consistent); or (stop="sform")
+  the norm of the space-time residual rho_n = F_n + B_n u_{n-1} - S_n u_n over n = 1..N_t (the rows
+  of Eq. (3.1) multiplied by S_n), relative to that of the initial guess, tested at the same place;
+* skip_first_down (the option of Sec. 3.2): on the first iteration the down-cycle does no
+  relaxation on any level -- the coarse right-hand side is the injected C-point residual of the
+  initial guess (on levels >= 1, whose guess is zero, that is the injected right-hand side) -- and
+  the coarsest solve and the up-cycle run as usual; that iteration applies no stopping test, and the
+  C-point reference norm is the second iteration's.
 """
 from __future__ import annotations
 
@@ -93,10 +100,28 @@ class MGRITResult:
         return float(np.mean(r)) if r else float("nan")
 
 
+def space_time_residual(prob: SFDE, U, forcing=None):
+    """rho_n = F_n + B_n U_{n-1} - S_n U_n, n = 1..N_t: the residual of the fully discrete scheme
+    Eq. (2.4) at every time point (row n of the block system Eq. (3.1), multiplied by S_n).
+    Returns an (N_t, N_y, N_x) array."""
+    U = np.asarray(U, dtype=np.float64)
+    out = np.empty((prob.nt,) + U.shape[1:])
+    for n in range(1, prob.nt + 1):
+        tau = 0.5 * (prob.t[n] - prob.t[n - 1])
+        r = prob.apply_B(U[n - 1], tau) - prob.apply_S(U[n], tau)
+        if forcing is not None:
+            r = r + forcing.dense(n)
+        out[n - 1] = r
+    return out
+
+
 def mgrit(prob: SFDE, U0, forcing=None, m: int = 2, max_levels: int = 32, min_coarse: int = 2,
           coarse: str = "cn", relax: str = "FCF", rel_tol: float = 1e-10, abs_tol: float = 0.0,
-          max_iter: int = 100, init_seed: int = 0, dense: bool = False) -> MGRITResult:
+          max_iter: int = 100, init_seed: int = 0, dense: bool = False, skip_first_down: bool = False,
+          stop: str = "cpoint") -> MGRITResult:
     """Algorithm 1 in nodal coordinates.  Returns all time points U[0..N_t]."""
+    if stop not in ("cpoint", "sform"):
+        raise ValueError(stop)
     levels = build_levels(prob.t, m, max_levels, min_coarse)
     L = len(levels)
     counter = [0]
@@ -136,38 +161,53 @@ def mgrit(prob: SFDE, U0, forcing=None, m: int = 2, max_levels: int = 32, min_co
             r[k] = phi(l, k * m, u[k * m - 1], g) - u[k * m]
         return r
 
-    def solve(l, u, g):
-        """Approximately solve the level-l system (recursive part of Algorithm 1)."""
+    def solve(l, u, g, skip=False):
+        """Approximately solve the level-l system (recursive part of Algorithm 1); with skip the
+        down-cycle does no relaxation."""
         N = len(levels[l]) - 1
         if l == L - 1:
             u[0] = g[0]
             for n in range(1, N + 1):
                 u[n] = phi(l, n, u[n - 1], g)
             return
-        relaxation(l, u, g)
+        if not skip:
+            relaxation(l, u, g)
         r = residual(l, u, g)
         v = np.zeros_like(r)
-        solve(l + 1, v, r)
+        solve(l + 1, v, r, skip)
         u[::m] += v
         frelax(l, u, g)
+
+    def sform_norm(u):
+        rho = space_time_residual(prob, u, forcing)
+        return float(np.sqrt(np.sum(rho * rho)))
 
     u = initial_guess(np.asarray(U0, dtype=np.float64), prob.nt, init_seed)
     if L == 1:
         solve(0, u, u[:1])
         return MGRITResult(u, [0.0], 1, 1, True, counter[0])
     hist = []
+    ref = sform_norm(u) if stop == "sform" else None
     converged = False
     it = 0
     for it in range(1, max_iter + 1):
-        relaxation(0, u, None)
+        skip = skip_first_down and it == 1
+        if not skip:
+            relaxation(0, u, None)
         r = residual(0, u, None)
-        nrm = float(np.sqrt(np.sum(r * r)))
+        nrm = sform_norm(u) if stop == "sform" else float(np.sqrt(np.sum(r * r)))
         hist.append(nrm)
-        if nrm <= max(rel_tol * hist[0], abs_tol) or not np.isfinite(nrm):
-            converged = bool(np.isfinite(nrm))
+        if not np.isfinite(nrm):
             break
+        # a skipped iteration's residual is that of the unrelaxed guess: no stopping test there, and
+        # the C-point reference is the first norm computed after a relaxation
+        if not skip:
+            first = ref if stop == "sform" else hist[1 if skip_first_down else 0]
+            if nrm <= max(rel_tol * first, abs_tol):
+                converged = True
+                break
         v = np.zeros_like(r)
-        solve(1, v, r)
+        solve(1, v, r, skip)
         u[::m] += v
     return MGRITResult(u, hist, it, L, converged, counter[0])
 

@@ -22,6 +22,7 @@ exported_symbols = (
     "sfde_setup", "sfde_set_initial", "sfde_set_forcing", "mgrit_solve", "seq_timestep",
     "sfde_step_batch", "sfde_step_batch_noalloc", "sfde_get_operator", "sfde_profile_enable", "sfde_profile_read",
     "sfde_destroy", "sfde_strerror", "sfde_batch_solve", "sfde_set_tuning", "sfde_autotune",
+    "sfde_set_forcing_dense",
 )
 
 
@@ -48,7 +49,7 @@ class MgritOpts(C.Structure):
     _fields_ = [("m", C.c_int), ("max_levels", C.c_int), ("min_coarse", C.c_int),
                 ("relax", C.c_int), ("coarse", C.c_int), ("max_iter", C.c_int),
                 ("rel_tol", C.c_double), ("abs_tol", C.c_double), ("init_seed", C.c_uint64),
-                ("inner_cycles", C.c_int)]
+                ("inner_cycles", C.c_int), ("skip_first_down", C.c_int), ("stop_kind", C.c_int)]
 
 
 class SfdeTuning(C.Structure):
@@ -83,6 +84,7 @@ def lib() -> C.CDLL:
                                  C.POINTER(SfdeOpts), C.POINTER(vp)]
         L.sfde_set_initial.argtypes = [vp, vp]
         L.sfde_set_forcing.argtypes = [vp, ip, vp, vp, vp]
+        L.sfde_set_forcing_dense.argtypes = [vp, vp]
         L.mgrit_solve.argtypes = [vp, C.POINTER(MgritOpts), vp, vp, C.POINTER(MgritStats)]
         L.seq_timestep.argtypes = [vp, vp, vp, dp]
         L.sfde_step_batch.argtypes = [vp, ip, ip, ip, vp, vp]
@@ -121,6 +123,56 @@ def _ptr(a):
     raise TypeError(f"unsupported array type {type(a)}")
 
 
+# (nx, ny, nt) of every live context, keyed by its address: the C side cannot check buffer sizes
+_CTX_DIMS: dict[int, tuple[int, int, int]] = {}
+
+
+def _ctx_key(ctx) -> int:
+    return int(ctx.value if isinstance(ctx, C.c_void_p) else ctx or 0)
+
+
+def _extent(a):
+    """(address, bytes, is_device, device index) of a NumPy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data, a.nbytes, False, None
+    if hasattr(a, "data_ptr"):
+        nbytes = a.numel() * a.element_size()
+        return a.data_ptr(), nbytes, bool(a.is_cuda), (a.device.index if a.is_cuda else None)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check_step_buffers(ctx, batch: int, src, dst, device_only: bool, where: str):
+    """Refuse, before any call into C, step buffers that the kernels would read or write past their
+    end (fewer than batch x N_y x N_x doubles), that overlap, or (device_only) that are not CUDA
+    tensors on the current device."""
+    dims = _CTX_DIMS.get(_ctx_key(ctx))
+    if dims is None:
+        raise ValueError(f"{where}: unknown or destroyed context")
+    if src is None or dst is None:
+        raise ValueError(f"{where}: src and dst are required")
+    nx, ny, _ = dims
+    need = int(batch) * nx * ny * 8
+    if int(batch) < 1:
+        raise ValueError(f"{where}: batch must be >= 1")
+    exts = []
+    for name, a in (("src", src), ("dst", dst)):
+        _ptr(a)  # dtype and contiguity
+        addr, nbytes, is_dev, dev = _extent(a)
+        if nbytes < need:
+            raise ValueError(f"{where}: {name} holds {nbytes // 8} doubles, needs batch x N_y x N_x = {need // 8}")
+        if device_only:
+            import torch
+            if not is_dev:
+                raise ValueError(f"{where}: {name} must be a CUDA tensor")
+            if dev != torch.cuda.current_device():
+                raise ValueError(f"{where}: {name} is on cuda:{dev}, the current device is "
+                                 f"cuda:{torch.cuda.current_device()}")
+        exts.append((addr, addr + need, is_dev))
+    (a0, a1, da), (b0, b1, db) = exts
+    if da == db and a0 < b1 and b0 < a1:
+        raise ValueError(f"{where}: src and dst overlap")
+
+
 def _check(status: int, where: str, allow=(SFDE_OK,)):
     if status not in allow:
         raise SfdeError(status, where)
@@ -141,6 +193,7 @@ def sfde_setup(beta, gamma, kx, ky, omega, nx, ny, t, precision=PREC_FP64, strea
                           t.ctypes.data_as(C.POINTER(C.c_double)), len(t) - 1, C.byref(opts),
                           C.byref(ctx))
     _check(st, "sfde_setup")
+    _CTX_DIMS[_ctx_key(ctx)] = (int(nx), int(ny), len(t) - 1)
     return ctx
 
 
@@ -151,6 +204,19 @@ def sfde_set_initial(ctx, psi0):
 def sfde_set_forcing(ctx, rank, time_w=None, bx=None, by=None):
     return _check(lib().sfde_set_forcing(ctx, int(rank), _ptr(time_w), _ptr(bx), _ptr(by)),
                   "sfde_set_forcing")
+
+
+def sfde_set_forcing_dense(ctx, F=None):
+    """F: (N_t, N_y, N_x) float64 (host or device), or None to clear the load."""
+    if F is not None:
+        dims = _CTX_DIMS.get(_ctx_key(ctx))
+        if dims is None:
+            raise ValueError("sfde_set_forcing_dense: unknown or destroyed context")
+        nx, ny, nt = dims
+        _ptr(F)
+        if tuple(F.shape) != (nt, ny, nx):
+            raise ValueError(f"sfde_set_forcing_dense: F has shape {tuple(F.shape)}, needs {(nt, ny, nx)}")
+    return _check(lib().sfde_set_forcing_dense(ctx, _ptr(F)), "sfde_set_forcing_dense")
 
 
 def mgrit_solve(ctx, opts: MgritOpts | None, U=None, U_T=None, check=True):
@@ -184,13 +250,19 @@ def sfde_batch_solve(ctxs, opts: MgritOpts | None, U_T=None, check=True):
 
 
 def sfde_step_batch(ctx, n0, dn, batch, src, dst):
+    """src, dst: at least batch x N_y x N_x doubles each, host or device, not overlapping
+    (ValueError otherwise, before any call into the library)."""
+    _check_step_buffers(ctx, batch, src, dst, False, "sfde_step_batch")
     return _check(lib().sfde_step_batch(ctx, int(n0), int(dn), int(batch), _ptr(src), _ptr(dst)),
                   "sfde_step_batch")
 
 
 def sfde_step_batch_noalloc(ctx, n0, dn, batch, src, dst):
     """Queue the batched step on the context's stream using the library's fixed device scratch
-    (no device allocation); src and dst must be device tensors.  Returns the raw status."""
+    (no device allocation).  src and dst: CUDA tensors on the current device holding at least
+    batch x N_y x N_x doubles each, not overlapping (ValueError otherwise, before any call into the
+    library).  Returns the raw status."""
+    _check_step_buffers(ctx, batch, src, dst, True, "sfde_step_batch_noalloc")
     return lib().sfde_step_batch_noalloc(ctx, int(n0), int(dn), int(batch), _ptr(src), _ptr(dst))
 
 
@@ -227,6 +299,7 @@ def sfde_autotune(ctx, opts: MgritOpts, cache_path=None) -> SfdeTuning:
 
 def sfde_destroy(ctx):
     if ctx:
+        _CTX_DIMS.pop(_ctx_key(ctx), None)
         lib().sfde_destroy(ctx)
 
 
@@ -235,10 +308,15 @@ def batch_solve(problems, U_T=None, check=True, **kw):
     return sfde_batch_solve([p.ctx for p in problems], make_opts(**kw), U_T, check=check)
 
 
+STOP_NATIVE, STOP_SFORM = 0, 1
+
+
 def make_opts(m=2, max_levels=64, min_coarse=2, relax=RELAX_FCF, coarse=COARSE_AUTO, max_iter=100,
-              rel_tol=1e-10, abs_tol=0.0, init_seed=0, inner_cycles=0) -> MgritOpts:
+              rel_tol=1e-10, abs_tol=0.0, init_seed=0, inner_cycles=0, skip_first_down=False,
+              stop_kind=STOP_NATIVE) -> MgritOpts:
     return MgritOpts(int(m), int(max_levels), int(min_coarse), int(relax), int(coarse),
-                     int(max_iter), float(rel_tol), float(abs_tol), int(init_seed), int(inner_cycles))
+                     int(max_iter), float(rel_tol), float(abs_tol), int(init_seed), int(inner_cycles),
+                     int(bool(skip_first_down)), int(stop_kind))
 
 
 class Problem:
@@ -263,6 +341,10 @@ class Problem:
         bx = np.ascontiguousarray(forcing.bx, dtype=np.float64)
         by = np.ascontiguousarray(forcing.by, dtype=np.float64)
         sfde_set_forcing(self.ctx, tw.shape[1], tw, bx, by)
+
+    def set_forcing_dense(self, F):
+        """F: (N_t, N_y, N_x) array of load vectors (host or device), or None."""
+        sfde_set_forcing_dense(self.ctx, F)
 
     def mgrit(self, U=None, U_T=None, check=True, **kw):
         return mgrit_solve(self.ctx, make_opts(**kw), U, U_T, check=check)

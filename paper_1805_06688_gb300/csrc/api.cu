@@ -93,7 +93,7 @@ static void free_ctx(sfde_ctx* c) {
     sfde_free_direction(c->x);
     sfde_free_direction(c->y);
     cudaFree(c->dt0); cudaFree(c->U0); cudaFree(c->time_w); cudaFree(c->px); cudaFree(c->py);
-    cudaFree(c->bxn); cudaFree(c->byn);
+    cudaFree(c->bxn); cudaFree(c->byn); cudaFree(c->Fd); cudaFree(c->Fh);
     cudaFree(c->T1); cudaFree(c->T2); cudaFree(c->T3); cudaFree(c->partial); cudaFree(c->scalar);
     if (c->host_scalar) cudaFreeHost(c->host_scalar);
     if (c->prof.ev[0])
@@ -142,6 +142,11 @@ static sfde_status setup_impl(double beta, double gamma, double kx, double ky, c
     memcpy(c->omega, om, sizeof(om));
     c->precision = prec;
     c->stream = opts ? (cudaStream_t)opts->stream : nullptr;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return SFDE_ECUDA;
+    }
     sfde_status st = SFDE_OK;
     try {   // a host allocation that throws frees the partial context before the status is returned
         c->t.assign(t, t + nt + 1);
@@ -200,7 +205,8 @@ static sfde_status set_forcing_impl(sfde_ctx* c, int rank, const double* time_w,
                                     const double* by) {
     if (!c || rank < 0 || rank > SFDE_MAX_RANK) return SFDE_EINVAL;
     cudaFree(c->time_w); cudaFree(c->px); cudaFree(c->py); cudaFree(c->bxn); cudaFree(c->byn);
-    c->time_w = c->px = c->py = c->bxn = c->byn = nullptr;
+    cudaFree(c->Fd); cudaFree(c->Fh);
+    c->time_w = c->px = c->py = c->bxn = c->byn = c->Fd = c->Fh = nullptr;
     c->rank = 0;
     if (rank == 0) return SFDE_OK;
     if (!time_w || !bx || !by) return SFDE_EINVAL;
@@ -234,6 +240,42 @@ static sfde_status set_forcing_impl(sfde_ctx* c, int rank, const double* time_w,
 sfde_status sfde_set_forcing(sfde_ctx* c, int rank, const double* time_w, const double* bx,
                              const double* by) {
     return sfde_no_throw([&] { return set_forcing_impl(c, rank, time_w, bx, by); });
+}
+
+// F_n, n = 1..N_t, padded into c->Fd; V_y^T F_n V_x into c->Fh (the load of the spectral step);
+// staged through a temporary of at most 128 unpadded slices
+static sfde_status set_forcing_dense_impl(sfde_ctx* c, const double* F) {
+    if (!c) return SFDE_EINVAL;
+    SFDE_TRY(set_forcing_impl(c, 0, nullptr, nullptr, nullptr));   // drops any load
+    if (!F) return SFDE_OK;
+    const size_t n2 = (size_t)c->x.n * c->y.n, P2 = c->P2();
+    SFDE_TRY(sfde_ensure_workspace(c, std::min<size_t>((size_t)c->nt, 128)));
+    const int chunk = (int)std::min<size_t>(c->ws_slices, 128);
+    double* tmp = nullptr;
+    cudaError_t e = cudaMalloc(&c->Fd, sizeof(double) * P2 * c->nt);
+    if (e == cudaSuccess) e = cudaMalloc(&c->Fh, sizeof(double) * P2 * c->nt);
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, sizeof(double) * n2 * chunk);
+    sfde_status st = e == cudaSuccess ? SFDE_OK : SFDE_ENOMEM;
+    for (int n0 = 0; n0 < c->nt && st == SFDE_OK; n0 += chunk) {
+        const int nb = std::min(chunk, c->nt - n0);
+        st = sfde_copy_in(tmp, F + (size_t)n0 * n2, sizeof(double) * n2 * nb, c->stream);
+        if (st == SFDE_OK) sfde_launch_pad(tmp, c->Fd + (size_t)n0 * P2, c->y.n, c->x.n, c->y.P, c->x.P, nb, c->stream);
+        // the pad kernel must finish reading tmp before the next chunk's copy overwrites it: both
+        // are on the same stream, in order
+    }
+    if (st == SFDE_OK) st = sfde_two_sided_fp64(c, c->Fd, c->nt, c->x.V, c->y.V, c->Fh);
+    const cudaError_t se = cudaStreamSynchronize(c->stream);
+    if (st == SFDE_OK && se != cudaSuccess) { sfde_set_last_cuda_error(se, "set_forcing_dense", __FILE__, __LINE__); st = SFDE_ECUDA; }
+    cudaFree(tmp);
+    if (st != SFDE_OK) {
+        cudaFree(c->Fd); cudaFree(c->Fh);
+        c->Fd = c->Fh = nullptr;
+    }
+    return st;
+}
+
+sfde_status sfde_set_forcing_dense(sfde_ctx* c, const double* F) {
+    return sfde_no_throw([&] { return set_forcing_dense_impl(c, F); });
 }
 
 static sfde_status write_outputs(sfde_ctx* c, double* U, double* U_T) {
@@ -286,12 +328,14 @@ static sfde_status mgrit_solve_impl(sfde_ctx* c, const mgrit_opts* opts, double*
     } else {
         o.m = 2; o.max_levels = 64; o.min_coarse = 2; o.relax = SFDE_RELAX_FCF;
         o.coarse = SFDE_COARSE_AUTO; o.max_iter = 100; o.rel_tol = 1e-10; o.abs_tol = 0.0; o.init_seed = 0;
-        o.inner_cycles = 0;
+        o.inner_cycles = 0; o.skip_first_down = 0; o.stop_kind = 0;
     }
     if (o.m < 2 || o.max_levels < 1 || o.min_coarse < 1 || o.max_iter < 1) return SFDE_EINVAL;
     if (o.relax != SFDE_RELAX_FCF && o.relax != SFDE_RELAX_F) return SFDE_EINVAL;
     if (o.coarse < SFDE_COARSE_CN || o.coarse > SFDE_COARSE_AUTO) return SFDE_EINVAL;
     if (!(o.rel_tol >= 0.0) || !(o.abs_tol >= 0.0) || o.inner_cycles < 0) return SFDE_EINVAL;
+    if (o.skip_first_down != 0 && o.skip_first_down != 1) return SFDE_EINVAL;
+    if (o.stop_kind != 0 && o.stop_kind != 1) return SFDE_EINVAL;
     sfde_status st;
     if (c->precision == SFDE_PREC_FP64)
         st = sfde_mgrit_fp64(c, &o, stats);

@@ -64,19 +64,29 @@ bool cache_append(const char* path, const char* key, const sfde_tuning& t) {
     return fclose(f) == 0 && w > 0;
 }
 
-// what decides the best choice: padded sizes, time grid (N_t, T, spread of the steps), precision,
-// and the options that shape the V-cycle and its stopping point
+// what decides the best choice: padded sizes, the operator (fractional orders, diffusivities: they set
+// the spectra and so the contraction of the refinement), the time grid (N_t, T, spread of the steps
+// and a hash of every time point), precision, and the options that shape the V-cycle and its
+// stopping point
 std::string tune_key(const sfde_ctx* c, const mgrit_opts& o) {
     double dmin = INFINITY, dmax = 0.0;
-    for (int n = 1; n <= c->nt; ++n) {
-        const double d = c->t[n] - c->t[n - 1];
-        dmin = std::min(dmin, d);
-        dmax = std::max(dmax, d);
+    uint64_t h = 1469598103934665603ull;   // FNV-1a over the bytes of t_0..t_N
+    for (int n = 0; n <= c->nt; ++n) {
+        if (n > 0) {
+            const double d = c->t[n] - c->t[n - 1];
+            dmin = std::min(dmin, d);
+            dmax = std::max(dmax, d);
+        }
+        unsigned char bytes[sizeof(double)];
+        memcpy(bytes, &c->t[n], sizeof(double));
+        for (unsigned char by : bytes) { h ^= by; h *= 1099511628211ull; }
     }
     char b[256];
-    snprintf(b, sizeof b, "P%dx%d_nt%d_T%.6g_dr%.3g_p%d_m%d_L%d_c%d_r%d_co%d_tol%.2g_ic%d", c->x.P, c->y.P, c->nt,
-             c->t[c->nt], dmax / dmin, c->precision, o.m, o.max_levels, o.min_coarse, o.relax, o.coarse, o.rel_tol,
-             o.inner_cycles);
+    snprintf(b, sizeof b,
+             "P%dx%d_nt%d_T%.6g_dr%.3g_th%016llx_b%.6g_g%.6g_kx%.6g_ky%.6g_p%d_m%d_L%d_c%d_r%d_co%d_tol%.2g_ic%d_sk%d_st%d",
+             c->x.P, c->y.P, c->nt, c->t[c->nt], dmax / dmin, (unsigned long long)h, c->x.rho, c->y.rho, c->kx, c->ky,
+             c->precision, o.m, o.max_levels, o.min_coarse, o.relax, o.coarse, o.rel_tol, o.inner_cycles,
+             o.skip_first_down, o.stop_kind);
     return b;
 }
 

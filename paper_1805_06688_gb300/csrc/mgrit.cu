@@ -64,6 +64,7 @@ struct Engine {
     sfde_ctx* c;
     int m, L, relax, scheme;
     long long steps = 0;
+    bool skip = false;   // down-cycle without relaxation (the first iteration with skip_first_down)
 
     size_t P2() const { return c->P2(); }
 
@@ -143,7 +144,7 @@ struct Engine {
 
     sfde_status solve(int l) {
         if (l == L - 1) return coarsest(l);
-        SFDE_TRY(relaxation(l));
+        if (!skip) SFDE_TRY(relaxation(l));
         SFDE_TRY(residual(l, false, nullptr));
         SFDE_CUDA(cudaMemsetAsync(c->levels[l + 1].u, 0, sizeof(double) * P2() * (c->levels[l + 1].N + 1), c->stream));
         SFDE_TRY(solve(l + 1));
@@ -272,21 +273,41 @@ sfde_status sfde_mgrit_fp64(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) {
         S.iters = 1;
         S.converged = 1;
     } else {
+        // space-time (S-form) stopping test: relative to the residual of the initial guess
+        double sref = 0.0;
+        if (o->stop_kind == 1) {
+            double r2 = 0.0;
+            SFDE_TRY(sfde_residual_norm2_fp64(c, L0.u, &r2));
+            sref = sqrt(r2);
+        }
+        const int nc = c->nt / o->m;
         for (int it = 1; it <= o->max_iter; ++it) {
-            SFDE_TRY(E.relaxation(0));
+            const bool skip = o->skip_first_down && it == 1;
+            if (!skip) SFDE_TRY(E.relaxation(0));
             int np = 0;
             SFDE_TRY(E.residual(0, true, &np));
             double r2 = 0.0;
             SFDE_TRY(sfde_reduce_partials(c, np, &r2));
-            double nrm = sqrt(r2);
+            if (o->stop_kind == 1) {
+                // after a relaxation every F-point's row of Eq. (3.1) holds, so rho vanishes there
+                // and rho_{km} = S_{km} r_k at the C-points (r_k was just injected into level 1)
+                if (skip) SFDE_TRY(sfde_residual_norm2_fp64(c, L0.u, &r2));
+                else SFDE_TRY(sfde_apply_S_norm2(c, c->levels[1].g + P2, (long long)P2, nc, o->m, o->m, &r2));
+            }
+            const double nrm = sqrt(r2);
             if (it - 1 < SFDE_HISTORY_MAX) S.history[it - 1] = nrm;
-            if (it == 1) S.res0 = nrm;
+            // the reference: the initial guess's space-time residual, or the first C-point norm
+            // computed after a relaxation (a skipped iteration's residual is the unrelaxed guess's)
+            if (o->stop_kind == 1) S.res0 = sref;
+            else if (it == (o->skip_first_down ? 2 : 1)) S.res0 = nrm;
             S.res_final = nrm;
             S.iters = it;
             if (!isfinite(nrm)) { rc = SFDE_ENOCONV; break; }
-            if (nrm <= std::max(o->rel_tol * S.res0, o->abs_tol)) { S.converged = 1; break; }
+            if (!skip && nrm <= std::max(o->rel_tol * S.res0, o->abs_tol)) { S.converged = 1; break; }
             SFDE_CUDA(cudaMemsetAsync(c->levels[1].u, 0, sizeof(double) * P2 * (c->levels[1].N + 1), c->stream));
+            E.skip = skip;
             SFDE_TRY(E.solve(1));
+            E.skip = false;
             SFDE_TRY(E.correct(0));
         }
         if (!S.converged && rc == SFDE_OK) rc = SFDE_ENOCONV;

@@ -196,9 +196,10 @@ struct SfdeMixed {
     std::vector<MapEntry> maps;
     // captured inner solve (CUDA graph) and what it contains
     cudaStream_t cap = nullptr;
-    // the inner solve in three captured parts: prologue, one V-cycle (replayed K-1 times), epilogue
-    cudaGraphExec_t inner_exec[3] = {nullptr, nullptr, nullptr};
-    long long inner_key = -1, inner_launches[3] = {0, 0, 0}, inner_steps[3] = {0, 0, 0};
+    // the inner solve in captured parts: prologue, one V-cycle (replayed K-1 times), epilogue, and
+    // the first V-cycle without down-cycle relaxation (skip_first_down)
+    cudaGraphExec_t inner_exec[4] = {nullptr, nullptr, nullptr, nullptr};
+    long long inner_key = -1, inner_launches[4] = {0, 0, 0, 0}, inner_steps[4] = {0, 0, 0, 0};
     // FP64-accurate residual in integer arithmetic around tensor-core products (P <= 256 or a
     // multiple of 256 up to 1024)
     bool use_oz = false;
@@ -413,6 +414,7 @@ struct LpEngine {
     SfdeMixed* M;
     int m, L, relax, scheme;
     long long steps = 0;
+    bool skip = false;   // down-cycle without relaxation (first V-cycle with skip_first_down)
 
     size_t P2() const { return c->P2(); }
     char* slice(void* base, long long s) const { return (char*)base + (size_t)s * P2() * M->esz; }
@@ -675,7 +677,7 @@ struct LpEngine {
         // the level's right-hand sides stay fixed while it is visited: transformed once
         if (modal(l)) SFDE_TRY(to_modal(M->lev[l].g, M->lev[l].nalloc, 0, 1, M->lev[l].N + 1, M->lev[l].gm, 1));
         if (l == L - 1) return coarsest(l);
-        SFDE_TRY(relaxation(l));
+        if (!skip) SFDE_TRY(relaxation(l));
         SFDE_TRY(residual(l, nullptr, nullptr));
         SFDE_CUDA(cudaMemsetAsync(M->lev[l + 1].u, 0, P2() * M->esz * (M->lev[l + 1].N + 1), c->stream));
         SFDE_TRY(solve(l + 1));
@@ -684,11 +686,13 @@ struct LpEngine {
     }
 };
 
-// Steps 2-4 of one outer iteration, queued on c->stream without any host synchronisation, in three
+// Steps 2-4 of one outer iteration, queued on c->stream without any host synchronisation, in
 // parts: (0) g_n = S_n^{-1} rho_n (rho already in g_0[1..N]) and E = 0; (1) one V-cycle on
 // E_n = Psi_n E_{n-1} + g_n up to the C-point correction; (2) the relaxation of the last V-cycle (so
-// E is F-consistent; the sequential solve when there is one level) and U += E in FP64.  K V-cycles
-// are part 0, K-1 times part 1, part 2.
+// E is F-consistent; the sequential solve when there is one level) and U += E in FP64; (3) part 1
+// without relaxation on the down-cycle (the first V-cycle under skip_first_down: E = 0, so the
+// coarse right-hand sides are the injected g).  K V-cycles are part 0, K-1 times part 1 (the first
+// of them part 3 with skip_first_down), part 2.
 sfde_status enqueue_inner_part(sfde_ctx* c, SfdeMixed* M, LpEngine& E, double* U, int kind, int part) {
     LpLevel& L0 = M->lev[0];
     const size_t P2 = c->P2();
@@ -701,11 +705,15 @@ sfde_status enqueue_inner_part(sfde_ctx* c, SfdeMixed* M, LpEngine& E, double* U
         if (E.modal(0)) SFDE_TRY(E.to_modal(L0.g, L0.nalloc, 0, 1, L0.N + 1, L0.gm, 1));
         return SFDE_OK;
     }
-    if (part == 1) {
-        SFDE_TRY(E.relaxation(0));
-        SFDE_TRY(E.residual(0, nullptr, nullptr));
-        SFDE_CUDA(cudaMemsetAsync(M->lev[1].u, 0, P2 * M->esz * (M->lev[1].N + 1), c->stream));
-        SFDE_TRY(E.solve(1));
+    if (part == 1 || part == 3) {
+        E.skip = part == 3;
+        sfde_status st = E.skip ? SFDE_OK : E.relaxation(0);
+        if (st == SFDE_OK) st = E.residual(0, nullptr, nullptr);
+        if (st == SFDE_OK && cudaMemsetAsync(M->lev[1].u, 0, P2 * M->esz * (M->lev[1].N + 1), c->stream) != cudaSuccess)
+            st = SFDE_ECUDA;
+        if (st == SFDE_OK) st = E.solve(1);
+        E.skip = false;
+        SFDE_TRY(st);
         return E.correct(0);
     }
     if (E.L == 1) SFDE_TRY(E.coarsest(0));
@@ -773,8 +781,9 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
                 : c->inner_cycles_tuned > 0 ? c->inner_cycles_tuned : (kind == 0 ? 4 : 5);
     // the inner solve is captured once as CUDA graphs and replayed; eager while kernels are timed
     const bool use_graph = !c->prof.on;
-    const long long key = ((long long)c->modal_chains << 28) | ((long long)c->fused_pair << 24) | ((long long)M->fused << 20) |
-                          ((long long)E.scheme << 4) | (long long)o->relax;
+    const long long key = ((long long)o->skip_first_down << 32) | ((long long)c->modal_chains << 28) |
+                          ((long long)c->fused_pair << 24) | ((long long)M->fused << 20) | ((long long)E.scheme << 4) |
+                          (long long)o->relax;
     long long graph_steps = 0;
 
     mgrit_stats S{};
@@ -831,19 +840,21 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
             if (M->inner_key != key) {
                 for (auto& g : M->inner_exec)
                     if (g) { cudaGraphExecDestroy(g); g = nullptr; }
-                for (int part = 0; part < 3; ++part)
-                    if (part != 1 || L > 1) SFDE_TRY(capture_inner_part(c, M, E, U, kind, part));
+                for (int part = 0; part < 4; ++part)
+                    if ((part != 1 || L > 1) && (part != 3 || (L > 1 && o->skip_first_down)))
+                        SFDE_TRY(capture_inner_part(c, M, E, U, kind, part));
                 M->inner_key = key;
             }
             for (int r = 0; r < Kr + 1; ++r) {
-                const int part = r == 0 ? 0 : (r == Kr ? 2 : 1);
+                const int part = r == 0 ? 0 : (r == Kr ? 2 : (r == 1 && o->skip_first_down ? 3 : 1));
                 SFDE_CUDA(cudaGraphLaunch(M->inner_exec[part], c->stream));
                 sfde_count_launch(c, (int)M->inner_launches[part]);
                 graph_steps += M->inner_steps[part];
             }
         } else {
             SFDE_TRY(enqueue_inner_part(c, M, E, U, kind, 0));
-            for (int k = 1; k < Kr; ++k) SFDE_TRY(enqueue_inner_part(c, M, E, U, kind, 1));
+            for (int k = 1; k < Kr; ++k)
+                SFDE_TRY(enqueue_inner_part(c, M, E, U, kind, k == 1 && o->skip_first_down ? 3 : 1));
             SFDE_TRY(enqueue_inner_part(c, M, E, U, kind, 2));
         }
         inner_total += Kr;

@@ -206,7 +206,8 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
     const long long* __restrict__ T1, const long long* __restrict__ T3, const long long* __restrict__ DU,
     const int* __restrict__ En, int n0, int Px, int Py, int nx, int ny, double cmass, int ex, int ey, int zsx, int zsy,
     const double* __restrict__ dt, int rank, const double* __restrict__ time_w, const double* __restrict__ bxn,
-    const double* __restrict__ byn, OT* __restrict__ rout, long long rout_stride, double* __restrict__ partial) {
+    const double* __restrict__ byn, const double* __restrict__ Fd, OT* __restrict__ rout, long long rout_stride,
+    double* __restrict__ partial) {
     __shared__ long long t1[32][35];      // Z1 rows i0.., columns j0-1 .. j0+32
     __shared__ long long t3[32][35];      // Z2 rows j0.., columns i0-1 .. i0+32
     __shared__ long long du[34][35];      // du, rows j0-1.., columns i0-1..
@@ -298,8 +299,8 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
             const long long k2 = t3[jj][tx] + 4 * t3[jj][tx + 1] + t3[jj][tx + 2];
             const long long st = rshr(k1, u - u1) + rshr(k2, u - u2);
             const long long s9 = rs[jj][tx] + 4 * rs[jj + 1][tx] + rs[jj + 2][tx];
-            if (rank > 0) {
-                double f = 0.0;
+            if (rank > 0 || Fd) {
+                double f = Fd ? Fd[(size_t)(n - 1) * P2 + (size_t)j * Px + i] : 0.0;
                 for (int q = 0; q < rank; ++q)
                     f += time_w[(size_t)(n - 1) * rank + q] * byn[(size_t)q * Py + j] * bxn[(size_t)q * Px + i];
                 rf = (float)fma(cm, i64_to_f64(s9), fma(cs, i64_to_f64(st), f));
@@ -388,13 +389,13 @@ sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int cou
             k_combine_int<__nv_bfloat16><<<grid, block, 0, c->stream>>>(
                 (const long long*)c->T1, (const long long*)c->T3, du, En, n0, Px, Py, c->x.n, c->y.n, cmass,
                 Ax.e_uniform, Ay.e_uniform, sfde_oz_int_shift(Px), sfde_oz_int_shift(Py), c->dt0, c->rank,
-                c->time_w, c->bxn, c->byn, (__nv_bfloat16*)ro,
+                c->time_w, c->bxn, c->byn, c->Fd, (__nv_bfloat16*)ro,
                 rout_stride, partial + total);
         else
             k_combine_int<float><<<grid, block, 0, c->stream>>>(
                 (const long long*)c->T1, (const long long*)c->T3, du, En, n0, Px, Py, c->x.n, c->y.n, cmass,
                 Ax.e_uniform, Ay.e_uniform, sfde_oz_int_shift(Px), sfde_oz_int_shift(Py), c->dt0, c->rank,
-                c->time_w, c->bxn, c->byn, (float*)ro, rout_stride,
+                c->time_w, c->bxn, c->byn, c->Fd, (float*)ro, rout_stride,
                 partial + total);
         sfde_prof_end(c, slot, 5, 0.0, (16.0 + 8.0 + (double)esz) * nxy * nb);   // Z1, Z2, du in, rho out
         sfde_count_launch(c);

@@ -80,6 +80,7 @@ struct sfde_ctx {
     double* dt0 = nullptr;      // level-0 step sizes (device)
     int precision = SFDE_PREC_FP64;
     cudaStream_t stream = nullptr;
+    int device = 0;             // CUDA device that was current at setup (all of the context's memory)
     // data
     double* U0 = nullptr;       // padded psi_0 (device, Py x Px)
     int rank = 0;
@@ -88,6 +89,8 @@ struct sfde_ctx {
     double* py = nullptr;       // rank x Py : V_y^T b_y^r (device)
     double* bxn = nullptr;      // rank x Px : nodal load factors b_x^r, zero padded (device)
     double* byn = nullptr;      // rank x Py (device)
+    double* Fd = nullptr;       // dense load (sfde_set_forcing_dense): N_t padded slices F_n (device)
+    double* Fh = nullptr;       // the same in the eigenbasis, V_y^T F_n V_x (device)
     // workspace for batched steps
     size_t ws_slices = 0;
     double* T1 = nullptr;       // ws_slices x P^2 scratch
@@ -146,6 +149,14 @@ sfde_status sfde_step_fp64_into(sfde_ctx* c, const StepBatch& sb, double* T1, do
 // per-CTA sums of rho^2 in partial.
 sfde_status sfde_residual_fp64(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
                                long long rout_stride, int out_kind, double* partial, int* n_partials);
+// Out_b = My^T X_b Mx for count padded FP64 slices (Out may not alias X)
+sfde_status sfde_two_sided_fp64(sfde_ctx* c, const double* X, int count, const double* Mx, const double* My,
+                                double* Out);
+// sum over n = 1..N_t of ||rho_n||^2 (the residual above, nothing stored)
+sfde_status sfde_residual_norm2_fp64(sfde_ctx* c, const double* U, double* norm2);
+// sum over b < count of ||S_{n0 + b dn} R_b||^2, R_b = R + b r_stride (padded slices)
+sfde_status sfde_apply_S_norm2(sfde_ctx* c, const double* R, long long r_stride, int count, int n0, int dn,
+                               double* norm2);
 
 // ---- tensor-core slice GEMM (gemm_tc.cu)
 enum { SCHEME_SOLVE = 2 };  // modal factor 1/(1 + tau sigma): the solve S^{-1} alone

@@ -17,11 +17,13 @@
 // FP64 pipe; tiles are sized so that even a batch of one slice fills all SMs.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "sfde_internal.cuh"
 
 namespace {
 
-enum Epi { EPI_STORE = 0, EPI_MODAL = 1, EPI_FINAL = 2, EPI_RESID_BF16 = 3, EPI_RESID_F32 = 4 };
+enum Epi { EPI_STORE = 0, EPI_MODAL = 1, EPI_FINAL = 2, EPI_RESID_BF16 = 3, EPI_RESID_F32 = 4, EPI_RESID_NONE = 5 };
 
 struct GemmParams {
     const double* X; long long x_stride; int R, C;
@@ -33,13 +35,17 @@ struct GemmParams {
     const double* lamx; const double* lamy; double kx, ky;
     const double* dt; int n0, dn, scheme;
     int rank; const double* time_w; const double* px; const double* py;
+    const double* Fh;          // dense load in the eigenbasis, V_y^T F_n V_x (slice n-1), or null
+    const double* Fd;          // dense nodal load F_n (slice n-1, padded), or null (EPI_RESID_*)
     // EPI_FINAL
     const double* g; long long g_stride;
     const double* utgt; long long utgt_stride;
     double* partial;
     // EPI_RESID_*: space-time residual rho_n = F_n + M_h (U_{n-1} - U_n) - tau_n K (U_{n-1} + U_n)
+    // for slice b: U_n = Ucur + b u_stride, U_{n-1} = Uprev + b u_stride (Uprev may be null: zero),
+    // n = n0 + b tdn; F_n only when load is set
     const double* t1;          // (V A_x)^T slices, Px x Py
-    const double* U;           // FP64 iterate, slice n at U + n * P2
+    const double* Ucur; const double* Uprev; long long u_stride; int tdn; int load;
     const double* bxn; const double* byn;   // nodal load factors (padded)
     double hx, hy;
     int Px, Py, nx, ny;
@@ -51,6 +57,7 @@ constexpr int BK = 16;
 template <int EPI> struct ResidOut { using T = double; };
 template <> struct ResidOut<EPI_RESID_BF16> { using T = __nv_bfloat16; };
 template <> struct ResidOut<EPI_RESID_F32> { using T = float; };
+constexpr bool is_resid(int e) { return e == EPI_RESID_BF16 || e == EPI_RESID_F32 || e == EPI_RESID_NONE; }
 
 __device__ __forceinline__ void store_as(__nv_bfloat16* p, double v) { *p = __float2bfloat16_rn((float)v); }
 __device__ __forceinline__ void store_as(float* p, double v) { *p = sfde_round_tf32((float)v); }
@@ -138,16 +145,17 @@ __global__ void __launch_bounds__(256) k_slice_gemm_fp64(GemmParams p) {
                              p.px[(size_t)q * p.R + r];
                     v += f / (1.0 + 0.5 * dt * sig);
                 }
+                if (p.Fh) v += p.Fh[(size_t)(tn - 1) * ((size_t)p.R * p.Cout) + o] / (1.0 + 0.5 * dt * sig);
             } else if (EPI == EPI_FINAL) {
                 if (p.g) v += p.g[b * p.g_stride + o];
                 if (p.utgt) {
                     v -= p.utgt[b * p.utgt_stride + o];
                     sq += v * v;
                 }
-            } else if (EPI == EPI_RESID_BF16 || EPI == EPI_RESID_F32) {
+            } else if (is_resid(EPI)) {
                 // element (j = n, i = r) of slice b; acc = (A_y (V M_x))[j][i]
                 const int i = r, j = n;
-                const int tn = p.n0 + (int)b;            // time index of this residual
+                const int tn = p.n0 + (int)b * p.tdn;    // time index of this residual
                 const double tau = 0.5 * p.dt[tn - 1];
                 const size_t P2 = (size_t)p.Px * p.Py;
                 const double* T1 = p.t1 + (size_t)b * P2 + (size_t)i * p.Py;   // row i of (V A_x)^T
@@ -156,8 +164,8 @@ __global__ void __launch_bounds__(256) k_slice_gemm_fp64(GemmParams p) {
                 if (j > 0) y1 += T1[j - 1];
                 if (j + 1 < p.Py) y1 += T1[j + 1];
                 const double stiff = p.kx * my * y1 + p.ky * v;
-                const double* Ua = p.U + (size_t)(tn - 1) * P2;
-                const double* Ub = p.U + (size_t)tn * P2;
+                const double* Ua = p.Uprev ? p.Uprev + b * p.u_stride : nullptr;
+                const double* Ub = p.Ucur + b * p.u_stride;
                 const double wx[3] = {p.hx / 6.0, 4.0 * p.hx / 6.0, p.hx / 6.0};
                 const double wy[3] = {my, 4.0 * my, my};
                 double mass = 0.0;
@@ -171,25 +179,30 @@ __global__ void __launch_bounds__(256) k_slice_gemm_fp64(GemmParams p) {
                         const int ii = i + cc;
                         if (ii < 0 || ii >= p.Px) continue;
                         const size_t e = (size_t)jj * p.Px + ii;
-                        row += wx[cc + 1] * (Ua[e] - Ub[e]);
+                        row += wx[cc + 1] * ((Ua ? Ua[e] : 0.0) - Ub[e]);
                     }
                     mass += wy[a + 1] * row;
                 }
                 double f = 0.0;
-                for (int q = 0; q < p.rank; ++q)
-                    f += p.time_w[(size_t)(tn - 1) * p.rank + q] * p.byn[(size_t)q * p.Py + j] * p.bxn[(size_t)q * p.Px + i];
+                if (p.load) {
+                    for (int q = 0; q < p.rank; ++q)
+                        f += p.time_w[(size_t)(tn - 1) * p.rank + q] * p.byn[(size_t)q * p.Py + j] * p.bxn[(size_t)q * p.Px + i];
+                    if (p.Fd) f += p.Fd[(size_t)(tn - 1) * P2 + (size_t)j * p.Px + i];
+                }
                 // padded rows/columns are not unknowns: the stencils above reach one past the last
                 // interior node, so the residual is defined as zero there
                 const double rho = (i < p.nx && j < p.ny) ? f + mass - tau * stiff : 0.0;
                 sq += rho * rho;
-                using OT = typename ResidOut<EPI>::T;
-                store_as((OT*)p.rout + b * p.out_stride + o, rho);
+                if (EPI != EPI_RESID_NONE) {
+                    using OT = typename ResidOut<EPI>::T;
+                    store_as((OT*)p.rout + b * p.out_stride + o, rho);
+                }
                 continue;
             }
             p.Out[b * p.out_stride + o] = v;
         }
     }
-    if ((EPI == EPI_FINAL || EPI == EPI_RESID_BF16 || EPI == EPI_RESID_F32) && p.partial) {
+    if ((EPI == EPI_FINAL || is_resid(EPI)) && p.partial) {
         red[threadIdx.x] = sq;
         __syncthreads();
         for (int s = 128; s > 0; s >>= 1) {
@@ -239,7 +252,7 @@ void launch_T(sfde_ctx* c, int T, const GemmParams& p, int nr, int nc, int nout)
     else if (T == 32) k_slice_gemm_fp64<32, EPI><<<grid, 256, 0, c->stream>>>(p);
     else k_slice_gemm_fp64<16, EPI><<<grid, 256, 0, c->stream>>>(p);
     const double b = p.batch;
-    sfde_prof_end(c, slot, (EPI == EPI_RESID_BF16 || EPI == EPI_RESID_F32 || p.X2) ? 1 : 0, 2.0 * b * nr * nc * nout,
+    sfde_prof_end(c, slot, (is_resid(EPI) || p.X2) ? 1 : 0, 2.0 * b * nr * nc * nout,
                   8.0 * (b * nr * nc + b * nr * nout + (double)nc * nout + (EPI == EPI_FINAL && p.utgt ? b * nr * nout : 0.0)));
     sfde_count_launch(c);
 }
@@ -277,6 +290,7 @@ sfde_status sfde_step_fp64(sfde_ctx* c, const StepBatch& sb, int* n_partials) {
         q.lamx = c->x.lam; q.lamy = c->y.lam; q.kx = c->kx; q.ky = c->ky;
         q.dt = sb.dt; q.n0 = sb.n0 + b0 * sb.dn; q.dn = sb.dn; q.scheme = sb.scheme;
         q.rank = (sb.level0 ? c->rank : 0); q.time_w = c->time_w; q.px = c->px; q.py = c->py;
+        q.Fh = sb.level0 ? c->Fh : nullptr;
         launch_T<EPI_MODAL>(c, choose_tile((long long)nb * Px, Py, pmin), q, c->x.n, c->y.n, c->y.n);
         // G3: T3 = (T2 V_x^T)^T
         GemmParams r{};
@@ -333,6 +347,7 @@ sfde_status sfde_step_fp64_into(sfde_ctx* c, const StepBatch& sb, double* T1, do
     q.lamx = c->x.lam; q.lamy = c->y.lam; q.kx = c->kx; q.ky = c->ky;
     q.dt = sb.dt; q.n0 = sb.n0; q.dn = sb.dn; q.scheme = sb.scheme;
     q.rank = (sb.level0 ? c->rank : 0); q.time_w = c->time_w; q.px = c->px; q.py = c->py;
+    q.Fh = sb.level0 ? c->Fh : nullptr;
     launch_plain<EPI_MODAL>(choose_tile((long long)nb * Px, Py, pmin), q, c->stream);
     GemmParams r{};
     r.batch = nb; r.X = T2; r.x_stride = P2; r.R = Py; r.C = Px;
@@ -348,22 +363,24 @@ sfde_status sfde_step_fp64_into(sfde_ctx* c, const StepBatch& sb, double* T1, do
 
 namespace {
 
-// T2_b = ((U_n + U_{n-1}) M_x)^T for a batch of consecutive n: the x-direction mass stencil
-// (h_x/6)(v_{i-1} + 4 v_i + v_{i+1}) fused with the sum of two time slices and a tile transpose.
-__global__ void k_mass_x_transpose(const double* Un, const double* Um, double* T2, int Px, int Py, double hx) {
+// T2_b = ((U_n + U_{n-1}) M_x)^T for a batch of slices (stride us; Um may be null: zero): the
+// x-direction mass stencil (h_x/6)(v_{i-1} + 4 v_i + v_{i+1}) fused with the sum of two time slices
+// and a tile transpose.
+__global__ void k_mass_x_transpose(const double* Un, const double* Um, long long us, double* T2, int Px, int Py,
+                                   double hx) {
     __shared__ double tile[32][35];
     const size_t P2 = (size_t)Px * Py;
     const size_t sl = blockIdx.z;
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
-    const double* a = Un + sl * P2;
-    const double* b = Um + sl * P2;
+    const double* a = Un + sl * us;
+    const double* b = Um ? Um + sl * us : nullptr;
     // rows j0..j0+31, columns i0-1..i0+32 (halo) into tile[j][1 + i]
     for (int jj = threadIdx.y; jj < 32; jj += blockDim.y) {
         const int j = j0 + jj;
         for (int ii = threadIdx.x; ii < 34; ii += 32) {
             const int i = i0 + ii - 1;
             double v = 0.0;
-            if (i >= 0 && i < Px) v = a[(size_t)j * Px + i] + b[(size_t)j * Px + i];
+            if (i >= 0 && i < Px) v = a[(size_t)j * Px + i] + (b ? b[(size_t)j * Px + i] : 0.0);
             tile[jj][ii] = v;
         }
     }
@@ -380,11 +397,17 @@ __global__ void k_mass_x_transpose(const double* Un, const double* Um, double* T
 
 void sfde_launch_mass_x_transpose(const double* Un, const double* Um, double* T2, int Px, int Py, double hx,
                                   int nb, cudaStream_t s) {
-    k_mass_x_transpose<<<dim3(Px / 32, Py / 32, nb), dim3(32, 8), 0, s>>>(Un, Um, T2, Px, Py, hx);
+    k_mass_x_transpose<<<dim3(Px / 32, Py / 32, nb), dim3(32, 8), 0, s>>>(Un, Um, (long long)Px * Py, T2, Px, Py, hx);
 }
 
-sfde_status sfde_residual_fp64(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
-                               long long rout_stride, int out_kind, double* partial, int* n_partials) {
+namespace {
+
+// rho_b = [F_n] + M_h (Uprev_b - Ucur_b) - tau_n K (Uprev_b + Ucur_b) for slices b < count,
+// Ucur_b = Ucur + b u_stride, Uprev_b = Uprev + b u_stride (Uprev null: zero), n = n0 + b tdn, in
+// chunks of the FP64 workspace; out_kind 0 BF16, 1 FP32, 2 none (sums of squares only)
+sfde_status resid_general(sfde_ctx* c, const double* Ucur, const double* Uprev, long long u_stride, int n0,
+                          int tdn, int count, bool load, void* rout, long long rout_stride, int out_kind,
+                          double* partial, int* n_partials) {
     const int Px = c->x.P, Py = c->y.P;
     const size_t P2 = c->P2();
     const int pmin = Px < Py ? Px : Py;
@@ -393,34 +416,103 @@ sfde_status sfde_residual_fp64(sfde_ctx* c, const double* U, int n_first, int co
     for (int b0 = 0; b0 < count; b0 += (int)c->ws_slices) {
         int nb = count - b0;
         if (nb > (int)c->ws_slices) nb = (int)c->ws_slices;
-        const int n0 = n_first + b0;
+        const double* ucur = Ucur + (size_t)b0 * u_stride;
+        const double* uprev = Uprev ? Uprev + (size_t)b0 * u_stride : nullptr;
         // (V A_x)^T with V = U_n + U_{n-1} formed while loading
         GemmParams p{};
-        p.batch = nb; p.X = U + (size_t)n0 * P2; p.X2 = U + (size_t)(n0 - 1) * P2; p.x_stride = (long long)P2;
+        p.batch = nb; p.X = ucur; p.X2 = uprev; p.x_stride = u_stride;
         p.R = Py; p.C = Px; p.Mat = c->x.A; p.Cout = Px; p.Out = c->T1; p.out_stride = (long long)P2;
         launch_T<EPI_STORE>(c, choose_tile((long long)nb * Py, Px, pmin), p, c->y.n, c->x.n, c->x.n);
         // ((U_n + U_{n-1}) M_x)^T
-        k_mass_x_transpose<<<dim3(Px / 32, Py / 32, nb), dim3(32, 8), 0, c->stream>>>(
-            U + (size_t)n0 * P2, U + (size_t)(n0 - 1) * P2, c->T2, Px, Py, c->x.h);
+        k_mass_x_transpose<<<dim3(Px / 32, Py / 32, nb), dim3(32, 8), 0, c->stream>>>(ucur, uprev, u_stride, c->T2, Px,
+                                                                                        Py, c->x.h);
         sfde_count_launch(c);
         // A_y (V M_x), then the residual epilogue
         GemmParams q{};
         q.batch = nb; q.X = c->T2; q.x_stride = (long long)P2; q.R = Px; q.C = Py;
         q.Mat = c->y.A; q.Cout = Py; q.out_stride = rout_stride;
-        q.kx = c->kx; q.ky = c->ky; q.dt = c->dt0; q.n0 = n0;
-        q.rank = c->rank; q.time_w = c->time_w; q.bxn = c->bxn; q.byn = c->byn;
-        q.t1 = c->T1; q.U = U; q.hx = c->x.h; q.hy = c->y.h; q.Px = Px; q.Py = Py;
+        q.kx = c->kx; q.ky = c->ky; q.dt = c->dt0; q.n0 = n0 + b0 * tdn; q.tdn = tdn;
+        q.load = load ? 1 : 0;
+        q.rank = c->rank; q.time_w = c->time_w; q.bxn = c->bxn; q.byn = c->byn; q.Fd = c->Fd;
+        q.t1 = c->T1; q.Ucur = ucur; q.Uprev = uprev; q.u_stride = u_stride;
+        q.hx = c->x.h; q.hy = c->y.h; q.Px = Px; q.Py = Py;
         q.nx = c->x.n; q.ny = c->y.n;
-        q.rout = (char*)rout + (size_t)b0 * rout_stride * esz;
+        q.rout = rout ? (char*)rout + (size_t)b0 * rout_stride * esz : nullptr;
         const int T = choose_tile((long long)nb * Px, Py, pmin);
         const long long ctas = (((long long)nb * Px + T - 1) / T) * (Py / T);
         if ((size_t)(total + ctas) > c->partial_cap) return SFDE_EINVAL;
         q.partial = partial + total;
         if (out_kind == 0) launch_T<EPI_RESID_BF16>(c, T, q, c->x.n, c->y.n, c->y.n);
-        else launch_T<EPI_RESID_F32>(c, T, q, c->x.n, c->y.n, c->y.n);
+        else if (out_kind == 1) launch_T<EPI_RESID_F32>(c, T, q, c->x.n, c->y.n, c->y.n);
+        else launch_T<EPI_RESID_NONE>(c, T, q, c->x.n, c->y.n, c->y.n);
         total += (int)ctas;
     }
     SFDE_CUDA(cudaGetLastError());
     if (n_partials) *n_partials = total;
+    return SFDE_OK;
+}
+
+}  // namespace
+
+sfde_status sfde_residual_fp64(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
+                               long long rout_stride, int out_kind, double* partial, int* n_partials) {
+    const size_t P2 = c->P2();
+    return resid_general(c, U + (size_t)n_first * P2, U + (size_t)(n_first - 1) * P2, (long long)P2, n_first, 1, count,
+                         true, rout, rout_stride, out_kind, partial, n_partials);
+}
+
+sfde_status sfde_residual_norm2_fp64(sfde_ctx* c, const double* U, double* norm2) {
+    const size_t P2 = c->P2();
+    double acc = 0.0;
+    const int chunk = (int)c->ws_slices;
+    for (int n = 1; n <= c->nt; n += chunk) {
+        const int cnt = std::min(chunk, c->nt - n + 1);
+        int np = 0;
+        SFDE_TRY(resid_general(c, U + (size_t)n * P2, U + (size_t)(n - 1) * P2, (long long)P2, n, 1, cnt, true,
+                               nullptr, 0, 2, c->partial, &np));
+        double r2 = 0.0;
+        SFDE_TRY(sfde_reduce_partials(c, np, &r2));
+        acc += r2;
+    }
+    *norm2 = acc;
+    return SFDE_OK;
+}
+
+sfde_status sfde_apply_S_norm2(sfde_ctx* c, const double* R, long long r_stride, int count, int n0, int dn,
+                               double* norm2) {
+    double acc = 0.0;
+    const int chunk = (int)c->ws_slices;
+    for (int b = 0; b < count; b += chunk) {
+        const int cnt = std::min(chunk, count - b);
+        int np = 0;
+        SFDE_TRY(resid_general(c, R + (size_t)b * r_stride, nullptr, r_stride, n0 + b * dn, dn, cnt, false, nullptr, 0,
+                               2, c->partial, &np));
+        double r2 = 0.0;
+        SFDE_TRY(sfde_reduce_partials(c, np, &r2));
+        acc += r2;
+    }
+    *norm2 = acc;
+    return SFDE_OK;
+}
+
+// Out_b = My^T X_b Mx for count padded slices (FP64, two slice products through the workspace T1);
+// Out may not alias X.
+sfde_status sfde_two_sided_fp64(sfde_ctx* c, const double* X, int count, const double* Mx, const double* My,
+                                double* Out) {
+    const int Px = c->x.P, Py = c->y.P;
+    const long long P2 = (long long)c->P2();
+    const int pmin = Px < Py ? Px : Py;
+    for (int b0 = 0; b0 < count; b0 += (int)c->ws_slices) {
+        const int nb = std::min(count - b0, (int)c->ws_slices);
+        GemmParams p{};   // (X Mx)^T
+        p.batch = nb; p.X = X + (size_t)b0 * P2; p.x_stride = P2; p.R = Py; p.C = Px;
+        p.Mat = Mx; p.Cout = Px; p.Out = c->T1; p.out_stride = P2;
+        launch_T<EPI_STORE>(c, choose_tile((long long)nb * Py, Px, pmin), p, c->y.n, c->x.n, c->x.n);
+        GemmParams q{};   // ((X Mx)^T My)^T = My^T X Mx
+        q.batch = nb; q.X = c->T1; q.x_stride = P2; q.R = Px; q.C = Py;
+        q.Mat = My; q.Cout = Py; q.Out = Out + (size_t)b0 * P2; q.out_stride = P2;
+        launch_T<EPI_STORE>(c, choose_tile((long long)nb * Px, Py, pmin), q, c->x.n, c->y.n, c->y.n);
+    }
+    SFDE_CUDA(cudaGetLastError());
     return SFDE_OK;
 }

@@ -219,6 +219,52 @@ def gaussian_bump_forcing(seed: int, nx: int, ny: int, t: np.ndarray,
     return Forcing(tw[:, None].copy(), bx[None, :], by[None, :]), (x0, y0, s)
 
 
+@dataclass
+class DenseForcing:
+    """Load vectors given slice by slice: F[n-1] = F_n, shape (N_t, N_y, N_x) (no structure)."""
+    F: np.ndarray
+
+    def dense(self, n: int) -> np.ndarray:
+        """F_n as an (N_y, N_x) array (n = 1..N_t)."""
+        return self.F[n - 1]
+
+
+_GL5_X, _GL5_W = np.polynomial.legendre.leggauss(5)
+
+
+def moving_bump_dense_forcing(seed: int, nx: int, ny: int, t: np.ndarray, speed: float | None = None,
+                              omega=(0.0, 1.0, 0.0, 1.0)):
+    """Non-separable load of f = exp(-((x - x0 - v t)^2 + (y - y0)^2) / (2 s^2)), a bump moving in x.
+
+    x0, y0 ~ U(0.3, 0.7), s ~ U(0.05, 0.15) and v ~ U(-0.3, 0.3) (relative to Omega, unless ``speed``
+    is given) are drawn with PCG64(seed).  F_n[j, i] = by[j] * int_{I_n} (f_x(., t), phi_i) dt with the
+    space integral by 10-point Gauss-Legendre per element and the time integral by 5-point
+    Gauss-Legendre per step.  Returns (DenseForcing, (x0, y0, s, v)).
+    """
+    rng = np.random.default_rng(seed)
+    x0r, y0r = rng.uniform(0.3, 0.7, size=2)
+    s = float(rng.uniform(0.05, 0.15))
+    vr = float(rng.uniform(-0.3, 0.3)) if speed is None else float(speed)
+    a, b, c, d = omega
+    x0, y0, v = a + x0r * (b - a), c + y0r * (d - c), vr * (b - a)
+    hx, hy = (b - a) / (nx + 1), (d - c) / (ny + 1)
+    x = interior_nodes(nx, a, b)
+    y = interior_nodes(ny, c, d)
+    by = _hat_load_gauss(lambda z: np.exp(-(z - y0) ** 2 / (2 * s * s)), y, hy)
+    t = np.asarray(t, dtype=np.float64)
+    nt = len(t) - 1
+    F = np.empty((nt, ny, nx))
+    for n in range(1, nt + 1):
+        lo, hi = t[n - 1], t[n]
+        fx = np.zeros(nx)
+        for q in range(5):
+            tq = 0.5 * (lo + hi) + 0.5 * (hi - lo) * _GL5_X[q]
+            cx = x0 + v * tq
+            fx += 0.5 * (hi - lo) * _GL5_W[q] * _hat_load_gauss(lambda z: np.exp(-(z - cx) ** 2 / (2 * s * s)), x, hx)
+        F[n - 1] = by[:, None] * fx[None, :]
+    return DenseForcing(F), (x0, y0, s, v)
+
+
 # ----------------------------------------------------------------------------- workloads
 
 @dataclass

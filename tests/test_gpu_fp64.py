@@ -178,3 +178,85 @@ def test_edge_cases_and_errors():
     # step index out of range
     with pytest.raises(sfde.SfdeError):
         P.step_batch(64, 1, np.zeros((2, 16, 16)), np.zeros((2, 16, 16)))
+
+
+@pytest.mark.parametrize("stop", ["cpoint", "sform"])
+@pytest.mark.parametrize("skip", [False, True])
+def test_skip_first_down_and_space_time_stop_match_oracle(skip, stop):
+    """The skip-first-down option (Sec. 3.2) and the space-time (S-form) stopping test against the
+    oracle's Algorithm 1 with the same options: same iteration count, residual history and iterate.
+    The GPU evaluates the S-form norm after a relaxation at the C-points only (rho_km = S_km r_k,
+    the F-point rows being satisfied); the oracle sums the full space-time residual."""
+    nx, ny, nt, m = 20, 13, 64, 4
+    t = time_grid(nt, 1.0, "graded")
+    F, _ = gaussian_bump_forcing(5, nx, ny, t)
+    psi = sine_mode_nodal(sine_mode_amplitudes(4), nx, ny)
+    P, O = make(0.6, 0.9, 1.0, 0.5, nx, ny, t, forcing=F, psi0=psi)
+    U = np.zeros((nt + 1, ny, nx))
+    _, st = P.mgrit(U=U, m=m, max_levels=3, coarse=sfde.COARSE_BE, rel_tol=1e-11, max_iter=60,
+                    skip_first_down=skip, stop_kind=sfde.STOP_SFORM if stop == "sform" else sfde.STOP_NATIVE)
+    ref = omgrit.mgrit(O, psi, F, m=m, max_levels=3, coarse="be", rel_tol=1e-11, max_iter=60,
+                       skip_first_down=skip, stop=stop)
+    assert st.converged and ref.converged
+    assert st.iters == ref.iters, (st.iters, ref.iters)
+    h = st.residual_history()
+    top = max(ref.history)
+    for k, (a, b) in enumerate(zip(h, ref.history)):
+        assert abs(a - b) <= 1e-9 * top, (k, a, b)
+    assert relerr(U, ref.U) < 1e-10
+    if stop == "sform":
+        # the reference norm is the initial guess's space-time residual
+        rho0 = omgrit.space_time_residual(O, omgrit.initial_guess(psi, nt), F)
+        assert abs(st.res0 - np.sqrt((rho0 ** 2).sum())) <= 1e-12 * st.res0
+
+
+def test_options_validation():
+    P, _ = make(0.6, 0.9, 1.0, 0.5, 8, 8, time_grid(16))
+    for kw in (dict(skip_first_down=2), dict(stop_kind=2), dict(stop_kind=-1)):
+        opts = sfde.make_opts(m=4, **{k: 0 for k in kw})
+        for k, v in kw.items():
+            setattr(opts, k, v)
+        st = sfde.lib().mgrit_solve(P.ctx, sfde._binding.C.byref(opts), None, None, None)
+        assert st == sfde.SFDE_EINVAL, kw
+
+
+def test_dense_forcing_matches_oracle():
+    """sfde_set_forcing_dense (a non-separable load, a bump moving in x): the single step, sequential
+    stepping and FP64 MGRIT against the oracle with the same load; clearing and replacing the load."""
+    from sfde_workloads import moving_bump_dense_forcing
+    nx, ny, nt = 40, 33, 24
+    t = time_grid(nt, 1.0, "graded")
+    D, _ = moving_bump_dense_forcing(7, nx, ny, t)
+    psi = sine_mode_nodal(sine_mode_amplitudes(3), nx, ny)
+    P, O = make(0.7, 0.85, 1.3, 0.4, nx, ny, t, psi0=psi)
+    P.set_forcing_dense(torch.from_numpy(D.F).cuda())
+    rng = np.random.default_rng(1)
+    src = rng.standard_normal((5, ny, nx))
+    dst = np.zeros_like(src)
+    P.step_batch(2, 4, src, dst)
+    for b in range(5):
+        n = 2 + 4 * b
+        assert relerr(dst[b], O.step(src[b], n, D.dense(n))) < 1e-11, b
+    U = np.zeros((nt + 1, ny, nx))
+    P.seq(U)
+    ref = osfde.seq_timestep(O, psi, D)
+    assert relerr(U, ref) < 1e-11
+    U[:] = 0
+    _, st = P.mgrit(U=U, m=4, max_levels=3, coarse=sfde.COARSE_BE, rel_tol=1e-11, max_iter=60)
+    r = omgrit.mgrit(O, psi, D, m=4, max_levels=3, coarse="be", rel_tol=1e-11, max_iter=60)
+    assert st.iters == r.iters and relerr(U, r.U) < 1e-10
+    # cleared: no load
+    P.set_forcing_dense(None)
+    P.seq(U)
+    assert relerr(U, osfde.seq_timestep(O, psi)) < 1e-11
+    # a separable load replaces a dense one, and a dense one a separable one
+    F, _ = gaussian_bump_forcing(2, nx, ny, t)
+    P.set_forcing_dense(D.F)
+    P.set_forcing(F)
+    P.seq(U)
+    assert relerr(U, osfde.seq_timestep(O, psi, F)) < 1e-11
+    P.set_forcing_dense(D.F)
+    P.seq(U)
+    assert relerr(U, ref) < 1e-11
+    with pytest.raises(ValueError):
+        P.set_forcing_dense(D.F[:-1])

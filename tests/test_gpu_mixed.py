@@ -134,3 +134,43 @@ def test_mixed_adaptive_and_exact_residual_digits_agree():
         _, st = P.mgrit(U=U, m=4, max_levels=8, coarse=sfde.COARSE_BE, rel_tol=1e-11, max_iter=60)
         assert st.converged
         assert _err(U, ref) < 1e-8, (nd, st.iters, _err(U, ref))
+
+
+@pytest.mark.parametrize("name,prec", PRECS)
+def test_mixed_skip_first_down_and_space_time_stop(name, prec):
+    """Mixed precision with the first V-cycle of every inner solve skipping its down-cycle
+    relaxation (a separately captured graph), stopping on the space-time residual: the result still
+    matches the exact sequential solution to 1e-8, at every time point."""
+    nx, ny, nt = 100, 70, 96
+    t = time_grid(nt, 1.0, "uniform")
+    F, _ = gaussian_bump_forcing(5, nx, ny, t)
+    psi = sine_mode_nodal(sine_mode_amplitudes(4), nx, ny)
+    ref = osfde.seq_timestep(osfde.SFDE(0.6, 0.9, 1.0, 0.5, nx, ny, t), psi, F)
+    P = sfde.Problem(0.6, 0.9, 1.0, 0.5, nx, ny, t, precision=prec)
+    P.set_initial(psi)
+    P.set_forcing(F)
+    for skip in (True, False):
+        U = np.zeros((nt + 1, ny, nx))
+        _, st = P.mgrit(U=U, m=4, max_levels=8, coarse=sfde.COARSE_BE, rel_tol=1e-11, max_iter=60,
+                        skip_first_down=skip, stop_kind=sfde.STOP_SFORM)
+        assert st.converged
+        assert _err(U, ref) < 1e-8, (skip, st.iters, _err(U, ref))
+
+
+@pytest.mark.parametrize("name,prec", PRECS)
+def test_mixed_dense_forcing(name, prec):
+    """Mixed precision with a dense (non-separable) load: the FP64 residual adds F_n slice by slice;
+    the result matches the exact sequential solution to 1e-8 at every time point."""
+    from sfde_workloads import moving_bump_dense_forcing
+    nx, ny, nt = 100, 70, 96
+    t = time_grid(nt, 1.0, "graded")
+    D, _ = moving_bump_dense_forcing(11, nx, ny, t)
+    psi = sine_mode_nodal(sine_mode_amplitudes(4), nx, ny)
+    ref = osfde.seq_timestep(osfde.SFDE(0.6, 0.9, 1.0, 0.5, nx, ny, t), psi, D)
+    P = sfde.Problem(0.6, 0.9, 1.0, 0.5, nx, ny, t, precision=prec)
+    P.set_initial(psi)
+    P.set_forcing_dense(D.F)
+    U = np.zeros((nt + 1, ny, nx))
+    _, st = P.mgrit(U=U, m=4, max_levels=8, coarse=sfde.COARSE_BE, rel_tol=1e-11, max_iter=60)
+    assert st.converged
+    assert _err(U, ref) < 1e-8, (st.iters, _err(U, ref))

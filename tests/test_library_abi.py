@@ -221,3 +221,35 @@ def test_set_tuning_and_autotune_validate_arguments_without_gpu():
     t = sfde.SfdeTuning(1, 1, 0, 0.0)
     assert L.sfde_set_tuning(None, ctypes.byref(t)) == sfde.SFDE_EINVAL
     assert L.sfde_autotune(None, None, None, None) == sfde.SFDE_EINVAL
+
+
+def test_step_buffer_checks_refuse_bad_input_without_gpu():
+    """The binding refuses, before any call into C, step buffers that are too short, overlap, or (for
+    the no-allocation entry point) are not CUDA tensors: the C side cannot know buffer sizes, and a
+    short buffer would be read or written past its end by the pad and unpad kernels."""
+    import numpy as np
+    from paper_1805_06688_gb300 import _binding as B
+    key = 0x7F00DEAD0000
+    B._CTX_DIMS[key] = (5, 4, 8)            # nx, ny, nt of a stand-in context (no GPU needed)
+    try:
+        ok = np.zeros((2, 4, 5))
+        short = np.zeros((1, 4, 5))
+        with pytest.raises(ValueError, match="needs"):
+            B.sfde_step_batch(key, 1, 1, 2, short, ok)
+        with pytest.raises(ValueError, match="needs"):
+            B.sfde_step_batch(key, 1, 1, 2, ok, short)
+        with pytest.raises(ValueError, match="overlap"):
+            B.sfde_step_batch(key, 1, 1, 1, ok, ok)
+        with pytest.raises(ValueError, match="overlap"):
+            flat = np.zeros(3 * 20)
+            B.sfde_step_batch(key, 1, 1, 2, flat[:40], flat[20:])
+        with pytest.raises(ValueError, match="batch"):
+            B.sfde_step_batch(key, 1, 1, 0, ok, ok.copy())
+        with pytest.raises(ValueError, match="CUDA"):
+            B.sfde_step_batch_noalloc(key, 1, 1, 1, ok, ok.copy())
+        with pytest.raises(ValueError, match="float64"):
+            B.sfde_step_batch(key, 1, 1, 1, ok.astype(np.float32), ok.copy())
+        with pytest.raises(ValueError, match="unknown"):
+            B.sfde_step_batch(key + 8, 1, 1, 1, ok, ok.copy())
+    finally:
+        B._CTX_DIMS.pop(key, None)

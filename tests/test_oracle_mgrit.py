@@ -107,3 +107,84 @@ def test_stiff_crank_nicolson_bound_exceeds_one():
     P = sfde.SFDE(0.6, 0.9, 1.0, 0.5, n, n, t)
     assert analysis.tub_bound(P.sigma(), t, 8, "cn") > 1.0
     assert analysis.tub_bound(P.sigma(), t, 8, "be") < analysis.tub_bound(P.sigma(), t, 8, "cn")
+
+
+def test_tub_bound_single_mode_by_hand():
+    """Eq. (3.11) for one mode on a uniform grid, evaluated by hand in rationals.
+
+    sigma = 1, dt = 1/2, m = 2, N_t = 8 (N_c = 4): lambda = (2 - 1/2)/(2 + 1/2) = 3/5,
+    mu (CN, coarse step 1) = (2 - 1)/(2 + 1) = 1/3, so the bound is
+    (3/5)^2 |(3/5)^2 - 1/3| (1 - (1/3)^3)/(1 - 1/3) = 9/25 * 2/75 * 13/9 = 26/1875.
+    sigma = 10: lambda = (2 - 5)/(2 + 5) = -3/7 (lambda^dagger = 3/7), mu = (2 - 10)/(2 + 10) = -2/3
+    (mu^ddagger = -2/3, mu^* = 2/3): (3/7)^2 |(3/7)^2 + 2/3| (1 - (2/3)^3)/(1/3) = 2375/7203.
+    Both modes together: the larger, 2375/7203.  Backward-Euler coarse propagator, sigma = 1:
+    mu = 1/(1 + 1) = 1/2: 9/25 |9/25 - 1/2| (1 - 1/8)/(1/2) = 9/25 * 7/50 * 7/4 = 441/5000."""
+    from fractions import Fraction as Fr
+    t = np.linspace(0.0, 4.0, 9)          # dt = 1/2
+    assert analysis.tub_bound(np.array([1.0]), t, 2, "cn") == pytest.approx(float(Fr(26, 1875)), rel=1e-14)
+    assert analysis.tub_bound(np.array([10.0]), t, 2, "cn") == pytest.approx(float(Fr(2375, 7203)), rel=1e-14)
+    assert analysis.tub_bound(np.array([1.0, 10.0]), t, 2, "cn") == pytest.approx(float(Fr(2375, 7203)), rel=1e-14)
+    assert analysis.tub_bound(np.array([1.0]), t, 2, "be") == pytest.approx(float(Fr(441, 5000)), rel=1e-14)
+
+
+def test_space_time_residual_against_assembled_kronecker_rows():
+    """rho_n = F_n + B_n U_{n-1} - S_n U_n evaluated with the assembled Kronecker matrices of
+    Eq. (2.4) (row-major vec), on an arbitrary field; and zero (to rounding) on the sequential
+    solution, which satisfies every row of Eq. (3.1)."""
+    P, U0, F = _small(nt=6, grid="graded", nx=4, ny=3)
+    rng = np.random.default_rng(3)
+    U = rng.standard_normal((7, 3, 4))
+    rho = mgrit.space_time_residual(P, U, F)
+    Mk = np.kron(P.My, P.Mx)
+    Kk = P.kx * np.kron(P.My, P.Ax) + P.ky * np.kron(P.Ay, P.Mx)
+    for n in range(1, 7):
+        tau = 0.5 * (P.t[n] - P.t[n - 1])
+        want = F.dense(n).reshape(-1) + (Mk - tau * Kk) @ U[n - 1].reshape(-1) - (Mk + tau * Kk) @ U[n].reshape(-1)
+        np.testing.assert_allclose(rho[n - 1].reshape(-1), want, rtol=0, atol=1e-14 * np.abs(want).max())
+    seq = sfde.seq_timestep(P, U0, F, dense=True)
+    assert np.abs(mgrit.space_time_residual(P, seq, F)).max() < 1e-14 * np.abs(seq).max()
+
+
+def test_sform_residual_of_f_consistent_iterate_is_S_times_cpoint_residual():
+    """After FCF (or F) relaxation every F-point satisfies its row of Eq. (3.1), so the space-time
+    residual vanishes there and equals S_{km} r_k at the C-points, r_k = Phi_{km}(u_{km-1}) - u_{km}
+    (S_n Phi_n(v) = B_n v + F_n): the identity the GPU's FP64 S-form stopping test uses."""
+    P, U0, F = _small(nt=16, grid="graded", nx=5, ny=4)
+    m = 4
+    r = mgrit.mgrit(P, U0, F, m=m, max_levels=2, rel_tol=0.0, max_iter=1, init_seed=5, dense=True)
+    u = r.U.copy()
+    # one more FCF relaxation of the returned iterate, as the solver does before its test
+    for sweep in ("F", "C", "F"):
+        for n in range(1, 17):
+            if (sweep == "F") == (n % m != 0):
+                u[n] = P.step(u[n - 1], n, F.dense(n), dense=True)
+    rho = mgrit.space_time_residual(P, u, F)
+    scale = np.abs(rho).max()
+    for n in range(1, 17):
+        if n % m:
+            assert np.abs(rho[n - 1]).max() < 1e-13 * scale, n
+        else:
+            rk = P.step(u[n - 1], n, F.dense(n), dense=True) - u[n]
+            tau = 0.5 * (P.t[n] - P.t[n - 1])
+            np.testing.assert_allclose(rho[n - 1], P.apply_S(rk, tau), rtol=0, atol=1e-13 * scale)
+
+
+@pytest.mark.parametrize("stop", ["cpoint", "sform"])
+def test_skip_first_down_keeps_the_fixed_point(stop):
+    """With the first down-cycle skipped (Sec. 3.2), the iteration still converges to sequential
+    stepping, and its first iteration runs only the level-0 C-point residual steps, the coarse
+    levels' residual steps and the coarsest sweep on the way down, plus the up-cycle's F-relaxations:
+    no relaxation on the down-cycle."""
+    P, U0, F = _small(nt=32, grid="graded")
+    seq = sfde.seq_timestep(P, U0, F, dense=True)
+    r = mgrit.mgrit(P, U0, F, m=2, max_levels=3, rel_tol=1e-12, max_iter=60, dense=True,
+                    skip_first_down=True, stop=stop)
+    assert r.converged
+    assert np.abs(r.U - seq).max() <= 1e-10 * np.abs(seq).max()
+    one = mgrit.mgrit(P, U0, F, m=2, max_levels=3, rel_tol=0.0, max_iter=1, skip_first_down=True, stop=stop)
+    # levels 32 -> 16 -> 8: residual steps 16 (level 0) + 8 (level 1), coarsest 8 steps,
+    # up-cycle F-relaxation of level 1 (8 steps); no F/C relaxation on levels 0 and 1 going down
+    assert one.step_solves == 16 + 8 + 8 + 8
+    full = mgrit.mgrit(P, U0, F, m=2, max_levels=3, rel_tol=0.0, max_iter=1, stop=stop)
+    # FCF on level 0 (16 + 16 + 16) and level 1 (8 + 8 + 8) on the way down in addition
+    assert full.step_solves == one.step_solves + 48 + 24

@@ -152,3 +152,43 @@ def test_saturation_error_order_piecewise_uniform_grid(pair):
     assert np.all(rates > 1.75) and np.all(rates < 2.3), rates
     ratio = errs / np.array(tab[pair])
     assert np.all(ratio > 0.5) and np.all(ratio < 1.6), ratio
+
+
+def test_moving_bump_load_reduces_to_the_separable_bump():
+    """The dense load of a bump at rest (speed 0) is the separable Gaussian bump's space factors
+    times the step length (the time integral of 1): pins the space-time quadrature of the dense load."""
+    from sfde_workloads import moving_bump_dense_forcing
+    from sfde_workloads.generate import _hat_load_gauss, interior_nodes
+    t = time_grid(12, 1.0, "graded")
+    D, (x0, y0, s, v) = moving_bump_dense_forcing(4, 9, 7, t, speed=0.0)
+    assert v == 0.0
+    bx = _hat_load_gauss(lambda z: np.exp(-(z - x0) ** 2 / (2 * s * s)), interior_nodes(9, 0.0, 1.0), 0.1)
+    by = _hat_load_gauss(lambda z: np.exp(-(z - y0) ** 2 / (2 * s * s)), interior_nodes(7, 0.0, 1.0), 0.125)
+    for n in range(1, 13):
+        np.testing.assert_allclose(D.dense(n), (t[n] - t[n - 1]) * np.outer(by, bx), rtol=1e-14, atol=0)
+
+
+def test_moving_bump_load_time_integral_is_exact_for_a_linear_path():
+    """For a bump moving at speed v the x-factor integrates exp(-(x - x0 - v t)^2/(2 s^2)) over each
+    step; with the 5-point Gauss rule in t this matches an adaptive quadrature of the same integrand
+    at one node to 1e-12 (the integrand is smooth in t)."""
+    from scipy.integrate import quad
+    from sfde_workloads import moving_bump_dense_forcing
+    t = time_grid(6)
+    D, (x0, y0, s, v) = moving_bump_dense_forcing(8, 15, 3, t)
+    assert v != 0.0
+    h = 1.0 / 16
+    i, j, n = 6, 1, 3                      # node x_7, y_2, step 3
+    xi, yj = (i + 1) * h, (j + 1) * 0.25
+
+    def hat(z, c, w):
+        return max(0.0, 1.0 - abs(z - c) / w)
+
+    def fx(tt):
+        return quad(lambda z: np.exp(-(z - x0 - v * tt) ** 2 / (2 * s * s)) * hat(z, xi, h), xi - h, xi + h,
+                    points=[xi], epsabs=1e-15, epsrel=1e-13)[0]
+
+    gy = quad(lambda z: np.exp(-(z - y0) ** 2 / (2 * s * s)) * hat(z, yj, 0.25), yj - 0.25, yj + 0.25, points=[yj],
+              epsabs=1e-15, epsrel=1e-13)[0]
+    want = gy * quad(fx, t[n - 1], t[n], epsabs=1e-15, epsrel=1e-13)[0]
+    assert abs(D.dense(n)[j, i] - want) <= 1e-9 * abs(want)

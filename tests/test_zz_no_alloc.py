@@ -51,9 +51,16 @@ def test_noalloc_rejects_requests_beyond_the_scratch():
     out = torch.zeros_like(src)
     st = sfde.sfde_step_batch_noalloc(P.ctx, 1, 1, limit_batch + 1, src, out)
     assert st == sfde.SFDE_ESCRATCH
-    # host buffers are refused (the entry point never stages through a temporary device copy)
+    # host buffers are refused (the entry point never stages through a temporary device copy): by
+    # the binding before the call, and by the C entry point itself
     host = np.zeros((1, n, n))
-    assert sfde.sfde_step_batch_noalloc(P.ctx, 1, 1, 1, host, host.copy()) == sfde.SFDE_EINVAL
+    with pytest.raises(ValueError):
+        sfde.sfde_step_batch_noalloc(P.ctx, 1, 1, 1, host, host.copy())
+    host2 = host.copy()
+    assert sfde.lib().sfde_step_batch_noalloc(P.ctx, 1, 1, 1, host.ctypes.data, host2.ctypes.data) == sfde.SFDE_EINVAL
+    # a batch larger than the tensors hold is refused by the binding
+    with pytest.raises(ValueError):
+        sfde.sfde_step_batch_noalloc(P.ctx, 1, 1, 2, src[:1], out[:1])
     # at the limit it runs
     ok = sfde.sfde_step_batch_noalloc(P.ctx, 1, 1, limit_batch, src[:limit_batch], out[:limit_batch])
     assert ok == sfde.SFDE_OK
