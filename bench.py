@@ -1,10 +1,17 @@
 #!/usr/bin/env python
 """Throughput of the MGRIT solve of the 2-D Riesz SFDE on GB300: space-time DOF-updates/s.
 
-One "step" is one complete MGRIT solve (all V-cycles to the stopping tolerance) of the
-workload ``sine_N255_Nt1024``: N_x = N_y = 255, N_t = 1024 uniform steps on (0,1]^3,
-beta = 0.6, gamma = 0.9, K_x = 1, K_y = 0.5, sixteen seeded sine modes for psi_0, f = 0,
-V-cycle with m = 8.  value = N_x N_y N_t / (device seconds per solve), summed over ranks.
+One "step" is one complete MGRIT solve (all refinement steps to the stopping tolerance) of the
+workload ``bump_N511_Nt2048``: N_x = N_y = 511, N_t = 2048 uniform steps on (0,1]^3,
+beta = 0.55, gamma = 0.95, K_x = 1, K_y = 0.1, sixteen seeded sine modes for psi_0 and a seeded
+Gaussian bump x sin(2 pi t) for f, V-cycle with m = 8, mixed precision (tensor-core V-cycles inside
+FP64 refinement) stopped where the FP64 space-time residual of Eq. (2.4) falls below 1e-8 of the
+initial guess's.  value = N_x N_y N_t / (device seconds per solve), summed over ranks.
+
+Beside it, outside the timed region: the solver's execution choices picked by its autotuner, the
+setup time, plain FP64 GPU MGRIT stopped by the same residual test at the same tolerance, FP64 GPU
+sequential stepping, the max-norm error of the solution against the oracle's exact sequential
+solution at every time point, and the oracle timed on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision ...]
 
@@ -31,7 +38,8 @@ from sfde_workloads import WORKLOADS  # noqa: E402
 
 METRIC = "space-time DOF-updates/s to 1e-8 rel. residual: mixed/batched vs FP64 MGRIT, 1 GB300"
 UNIT = "DOF-updates/s"
-WORKLOAD = "sine_N255_Nt1024"
+WORKLOAD = "bump_N511_Nt2048"
+REL_TOL = 1e-8
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # Nominal GB300 rates (TFLOP/s): FP64 and BF16 dense; FP64 peak = measured BF16 x nominal ratio.
 NOMINAL_FP64_TFLOPS = 1.25
@@ -135,55 +143,114 @@ def traffic_from_profile(kernel: str, flops_per_launch: float, bytes_per_launch:
     return d["dram_bytes_per_alg_byte"] * bytes_per_launch
 
 
-# ----------------------------------------------------------------------------- oracle timing
+# ----------------------------------------------------------------------------- oracle leg
 
-def oracle_rate(w, iters_needed: int, coarse: str, budget_s: float = 20.0):
-    """FP64 CPU oracle on a bounded sample: one V-cycle of the nodal Algorithm 1 (all levels),
-    extrapolated to the V-cycles the full solve needs.  Returns (rate, seconds, cores, sample)."""
-    from oracle import mgrit as omgrit, sfde as osfde
-    t = w.t()
-    prob = osfde.SFDE(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t)
+def oracle_problem(w):
+    from oracle import sfde as osfde
+    prob = osfde.SFDE(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, w.t(), w.omega)
     prob.eig()
-    psi = w.initial()
+    return prob
+
+
+def oracle_seq_sample(w, prob=None, steps: int | None = None, budget_s: float = 10.0):
+    """The oracle's sequential FP64 time stepping (Eq. (2.4), fast-diagonalisation solve per step)
+    over a bounded run of consecutive steps of the workload: its fastest path to the solution, which
+    it reaches exactly (every row of Eq. (3.1) holds to rounding), so DOF-updates/s = N_x N_y x steps /
+    time needs no extrapolation.  With steps None the count is sized to about budget_s seconds from
+    one timed step.  Returns (rate, seconds, steps, sample text)."""
+    from oracle import sfde as osfde
+    prob = prob or oracle_problem(w)
+    F = w.forcing()
+    U = w.initial()
     t0 = time.perf_counter()
-    r = omgrit.mgrit(prob, psi, w.forcing(), m=w.m, max_levels=w.max_levels, coarse=coarse,
-                     rel_tol=0.0, max_iter=1)
+    U = prob.step(U, 1, osfde.dense_forcing(F, 1))
+    one = time.perf_counter() - t0
+    if steps is None:
+        steps = int(min(w.nt - 1, max(8, budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    for n in range(2, 2 + steps):
+        U = prob.step(U, n, osfde.dense_forcing(F, n))
     dt = time.perf_counter() - t0
-    rate = w.space_time_updates / (dt * iters_needed)
-    sample = (f"one V-cycle ({r.step_solves} step solves, all {r.levels} levels) of the oracle's nodal "
-              f"FP64 MGRIT on {w.name}, extrapolated to the {iters_needed} V-cycles of the full solve")
-    return rate, dt, os.cpu_count(), sample
+    rate = w.nx * w.ny * steps / dt
+    sample = (f"{steps} consecutive steps (t_2 .. t_{steps + 1}) of the oracle's FP64 sequential time stepping "
+              f"(Eq. (2.4), FDM solve) on {w.name}; rate = N_x N_y x steps / time")
+    return rate, dt, steps, sample
 
 
-def oracle_iterations(w, coarse: str) -> int:
-    from oracle import mgrit as omgrit, sfde as osfde
-    prob = osfde.SFDE(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, w.t())
-    r = omgrit.mgrit_modal(prob, w.initial(), w.forcing(), m=w.m, max_levels=w.max_levels,
-                           coarse=coarse, rel_tol=w.rel_tol, max_iter=400)
-    return r.iters
+def oracle_leg(w, U_mixed, U_fp64, fp64_step_solves):
+    """Oracle on the host cores (rank 0, outside the timed region): (1) the max-norm error of the GPU
+    solutions against the oracle's exact sequential solution at every time point, streamed slice by
+    slice; (2) the oracle's sequential stepping timed on a bounded sample; (3) one full oracle FP64
+    MGRIT solve of the small manufactured workload (the anchor of the MGRIT estimate), and the oracle
+    MGRIT rate on this workload estimated from the sampled step time and the step solves GPU FP64
+    MGRIT took (the same algorithm)."""
+    from oracle import mgrit as omgrit
+    from oracle.sfde import spectral_sequential_iter
+    prob = oracle_problem(w)
+    acc = {}
+    t0 = time.perf_counter()
+    sols = [(name, U) for name, U in (("mixed", U_mixed), ("fp64_mgrit", U_fp64)) if U is not None]
+    emax = {name: 0.0 for name, _ in sols}
+    per_slice = dict(emax)
+    smax = 0.0
+    for n, E in spectral_sequential_iter(prob, w.initial(), w.forcing()):
+        m = float(np.abs(E).max())
+        smax = max(smax, m)
+        for name, U in sols:
+            d = float(np.abs(U[n] - E).max())
+            emax[name] = max(emax[name], d)
+            if n > 0 and m > 0:
+                per_slice[name] = max(per_slice[name], d / m)
+    for name, _ in sols:
+        acc[name] = {"max_err_vs_oracle": emax[name] / smax, "max_err_per_slice_rel": per_slice[name],
+                     "max_abs_err": emax[name], "slices_compared": w.nt + 1}
+    acc["oracle_exact_s"] = time.perf_counter() - t0
+    rate, dt, steps, sample = oracle_seq_sample(w, prob)
+    base = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample,
+            "sample_s": dt, "blas_threads": os.environ.get("OPENBLAS_NUM_THREADS", "default (all cores)")}
+    step_s = dt / steps
+    if fp64_step_solves:
+        base["oracle_mgrit_estimate"] = {
+            "value": w.space_time_updates / (step_s * fp64_step_solves), "unit": UNIT,
+            "how": (f"extrapolated: sampled oracle step time x {fp64_step_solves} step solves (GPU FP64 MGRIT, same "
+                    "algorithm and stopping test)")}
+    a = WORKLOADS["manufactured_N31_Nt64"]
+    aprob = oracle_problem(a)
+    t0 = time.perf_counter()
+    r = omgrit.mgrit(aprob, a.initial(), a.forcing(), m=a.m, max_levels=2, coarse="be", rel_tol=REL_TOL,
+                     stop="sform")
+    adt = time.perf_counter() - t0
+    base["anchor"] = {"workload": a.name, "solver": "oracle FP64 MGRIT (two levels, space-time residual 1e-8)",
+                      "iters": r.iters, "seconds": adt, "value": a.space_time_updates / adt, "unit": UNIT,
+                      "measured": "full solve"}
+    return acc, base
 
 
 def run_reference(args, w):
+    """The oracle timed on the host cores: each step is a bounded sample of consecutive FP64 steps of
+    its sequential time stepping on the workload (see oracle_seq_sample); rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    coarse = "be"  # the coarse propagator the solver picks for this workload (bound of Thm 3.1 > 1)
-    iters = oracle_iterations(w, coarse)
+    prob = oracle_problem(w)
+    _, _, steps, _ = oracle_seq_sample(w, prob, budget_s=3.0)   # sizes the sample, untimed
     rates, secs = [], []
+    sample = ""
     for k in range(args.warmup + args.steps):
-        rate, dt, cores, sample = oracle_rate(w, iters, coarse)
+        rate, dt, _, sample = oracle_seq_sample(w, prob, steps=steps)
         if k >= args.warmup:
             rates.append(rate)
-            secs.append(dt * iters)
+            secs.append(dt)
     value = statistics.median(rates)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nt": w.nt, "m": w.m,
-                   "rel_tol": w.rel_tol, "coarse": coarse, "solver": "FP64 CPU oracle, Algorithm 1"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nt": w.nt, "m": w.m, "rel_tol": REL_TOL,
+                   "solver": "FP64 CPU oracle, sequential time stepping (exact solution of Eq. (3.1))",
+                   "step": f"{steps} consecutive time steps"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -202,16 +269,16 @@ KERNEL_CLASSES = (  # the library's accounting classes (include/sfde.h, sfde_pro
 )
 
 
-def roofline_from_profile(prof, precision: str):
+def roofline_from_profile(prof, tf32: bool):
     """Roofline of the kernel class with the largest device time, plus a per-class breakdown.
 
-    Each class's launches are timed with CUDA events inside the solve (a long step), so the
-    denominators are the sustained measured rates.  FP64 SIMT GEMMs are bound by the FP64 pipe
+    Each class's launches are timed with CUDA events inside one solve of well under a second, so the
+    denominators are the measured burst rates.  FP64 SIMT GEMMs are bound by the FP64 pipe
     (measured BF16 x nominal FP64/BF16); tensor-core kernels are placed by algorithmic intensity
-    against the ridge point (below it: HBM bandwidth, above it: the tensor pipe of their dtype);
-    the integer assembly kernels move bytes only."""
+    against the ridge point (below it: HBM bandwidth, above it: the tensor pipe of their dtype, TF32
+    at half the BF16 rate); the integer assembly kernels move bytes only."""
     pk, src = peaks()
-    bf16 = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    bf16 = pk["bf16_tflops"]
     fp64_peak = bf16 * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
     kernels = []
     for k, (name, what, kind) in enumerate(KERNEL_CLASSES):
@@ -222,16 +289,16 @@ def roofline_from_profile(prof, precision: str):
             continue
         tfs = fl / (ms * 1e-3) / 1e12
         gbs = by / (ms * 1e-3) / 1e9
-        tc_peak = bf16 * (0.5 if (k == 2 and precision == "mixed-tf32") else 1.0)
+        tc_peak = bf16 * (0.5 if (k == 2 and tf32) else 1.0)
         if kind == "alu":
             bound, ach, peak, unit = "alu", tfs, fp64_peak, "TFLOP/s"
-            psrc = f"{src} sustained BF16 {bf16} TFLOP/s x nominal FP64/BF16 {NOMINAL_FP64_TFLOPS}/{NOMINAL_BF16_TFLOPS}"
+            psrc = f"{src} burst BF16 {bf16} TFLOP/s x nominal FP64/BF16 {NOMINAL_FP64_TFLOPS}/{NOMINAL_BF16_TFLOPS}"
         elif kind == "hbm" or fl / by < tc_peak * 1e12 / (pk["hbm_gbs"] * 1e9):
             bound, ach, peak, unit = "hbm", gbs, pk["hbm_gbs"], "GB/s"
             psrc = f"{src} HBM copy bandwidth"
         else:
             bound, ach, peak, unit = "tensor", tfs, tc_peak, "TFLOP/s"
-            psrc = f"{src} sustained BF16 dense" + (" x 1/2 (TF32 nominal ratio)" if tc_peak < bf16 else "")
+            psrc = f"{src} burst BF16 dense" + (" x 1/2 (TF32 nominal ratio)" if tc_peak < bf16 else "")
         kernels.append({
             "kernel": name, "what": what, "launches": int(n), "ms": ms, "share": None,
             "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
@@ -298,15 +365,29 @@ def run_ours(args, w):
             "mixed-tf32": sfde.PREC_MIXED_TF32, "mixed-auto": sfde.PREC_MIXED_AUTO}[args.precision]
     t = w.t()
     psi = w.initial()
+    forcing = w.forcing()
+    # setup (Toeplitz coefficients, dense A, generalised eigenpairs, operands): reported, not timed
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
     P = sfde.Problem(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t, w.omega, precision=prec,
                      stream=stream.cuda_stream)
     P.set_initial(torch.from_numpy(psi).to(dev))
-    P.set_forcing(w.forcing())
-    # FP64: C-point residual to the workload's tolerance; mixed: FP64 space-time residual to 1e-8
-    # relative (max-norm error against the exact solution ~1e-10, checked by the GPU tests)
-    tol = w.rel_tol if prec == sfde.PREC_FP64 else 1e-8
-    kw = dict(m=w.m, max_levels=w.max_levels, coarse=sfde.COARSE_AUTO, rel_tol=tol, max_iter=400)
+    P.set_forcing(forcing)
+    torch.cuda.synchronize(dev)
+    setup_s = time.perf_counter() - t0
+    # every form stops on the FP64 space-time residual of Eq. (2.4), 1e-8 of the initial guess's
+    kw = dict(m=w.m, max_levels=w.max_levels, coarse=sfde.COARSE_AUTO, rel_tol=REL_TOL, max_iter=400,
+              stop_kind=sfde.STOP_SFORM)
     UT = torch.zeros((w.ny, w.nx), dtype=torch.float64, device=dev)
+
+    tuning = None
+    autotune_s = 0.0
+    if prec != sfde.PREC_FP64 and not args.no_autotune:
+        t0 = time.perf_counter()
+        tn = P.autotune(**kw)
+        autotune_s = time.perf_counter() - t0
+        tuning = {"fused_pair": tn.fused_pair, "modal_chains": tn.modal_chains, "inner_cycles": tn.inner_cycles,
+                  "ms": tn.ms, "seconds": autotune_s}
 
     def barrier():
         if world > 1:
@@ -315,7 +396,7 @@ def run_ours(args, w):
     stats = None
     for _ in range(args.warmup):
         _, stats = P.mgrit(U_T=UT, **kw)
-    # timed region: inputs (the 1025-slice FP64 space-time iterate, 537 MB) exceed L2
+    # timed region: the space-time iterate (FP64, (N_t + 1) x 512^2 x 8 B = 4.3 GB) exceeds L2
     P.profile_enable(False)
     barrier()
     torch.cuda.synchronize(dev)
@@ -336,53 +417,77 @@ def run_ours(args, w):
     P.mgrit(U_T=UT, **kw)
     prof = P.profile_read()
     P.profile_enable(False)
-    roofline, kernels = roofline_from_profile(prof, args.precision)
+    roofline, kernels = roofline_from_profile(prof, stats.lp_kind == 1)
 
-    # end to end through the C ABI with host buffers: psi_0 host -> device, u(T) device -> host
+    # end to end through the C ABI with host buffers: psi_0 and the load factors host -> device,
+    # u(T) device -> host, every step
     psi_host = torch.from_numpy(psi).pin_memory()
     UT_host = torch.zeros((w.ny, w.nx), dtype=torch.float64).pin_memory()
+    h2d = psi_host.numel() * 8
+    if forcing is not None:
+        h2d += 8 * (forcing.time_w.size + forcing.bx.size + forcing.by.size)
     torch.cuda.synchronize(dev)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         P.set_initial(psi_host)
+        P.set_forcing(forcing)
         P.mgrit(U_T=UT_host, **kw)
     torch.cuda.synchronize(dev)
     e2e_rate, _ = whole_job_rate((time.perf_counter() - t0) / args.steps, w.space_time_updates, world, dev)
-    e2e = {"value": e2e_rate, "unit": UNIT,
-           "h2d_bytes_per_step": psi_host.numel() * 8, "d2h_bytes_per_step": UT_host.numel() * 8}
+    e2e = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": UT_host.numel() * 8}
 
-    # comparators on the same GPU: FP64 sequential time stepping, and FP64 MGRIT (one solve)
+    # the whole space-time solution of one more solve, for the error against the oracle
+    want_err = rank == 0 and not args.no_cpu_baseline
+    U_mixed = None
+    if want_err:
+        Ud = torch.empty((w.nt + 1, w.ny, w.nx), dtype=torch.float64, device=dev)
+        P.mgrit(U=Ud, **kw)
+        U_mixed = Ud.cpu().numpy()
+        del Ud
+
+    # comparators on the same GPU: FP64 sequential time stepping, and FP64 MGRIT stopped by the same
+    # space-time residual test at the same tolerance
     seq_s = P.seq(U_T=UT)
-    comparators = {"fp64_seq_timestep_gpu": w.space_time_updates / seq_s}
-    fp64_iters = stats.iters
+    comparators = {"fp64_seq_timestep_gpu": w.space_time_updates / seq_s,
+                   "speedup_vs_fp64_seq_timestep": value / world / (w.space_time_updates / seq_s)}
+    U_fp64 = None
+    fp64_step_solves = None
     if prec != sfde.PREC_FP64 and not args.no_fp64_comparator:
         Q = sfde.Problem(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t, w.omega,
                          precision=sfde.PREC_FP64, stream=stream.cuda_stream)
         Q.set_initial(torch.from_numpy(psi).to(dev))
-        Q.set_forcing(w.forcing())
-        qkw = dict(kw, rel_tol=w.rel_tol)
-        Q.mgrit(U_T=UT, **qkw)
-        _, qst = Q.mgrit(U_T=UT, **qkw)
-        comparators["fp64_mgrit_gpu"] = w.space_time_updates / qst.seconds
-        comparators["fp64_mgrit_gpu_iters"] = qst.iters
-        comparators["speedup_vs_fp64_mgrit"] = value / world / comparators["fp64_mgrit_gpu"]
-        fp64_iters = qst.iters
+        Q.set_forcing(forcing)
+        Ud = torch.empty((w.nt + 1, w.ny, w.nx), dtype=torch.float64, device=dev) if want_err else None
+        _, qst = Q.mgrit(U=Ud, U_T=UT, **kw)
+        if want_err:
+            U_fp64 = Ud.cpu().numpy()
+            del Ud
+        comparators.update({
+            "fp64_mgrit_gpu": w.space_time_updates / qst.seconds, "fp64_mgrit_gpu_iters": qst.iters,
+            "fp64_mgrit_stop": f"FP64 space-time residual <= {REL_TOL} x initial (same test as the mixed form)",
+            "fp64_mgrit_step_solves": qst.step_solves,
+            "speedup_vs_fp64_mgrit": value / world / (w.space_time_updates / qst.seconds)})
+        fp64_step_solves = qst.step_solves
         Q.close()
+    comparators["work_ratio_note"] = (
+        "MGRIT does about 2 m/(m-1) step solves per time point per V-cycle on top of sequential stepping's one; "
+        "compare the speed-ups above with that")
+    dtype = "f64" if prec == sfde.PREC_FP64 else ("tf32+f64" if stats.lp_kind == 1 else "bf16+f64")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f64" if prec == sfde.PREC_FP64 else {"mixed-bf16": "bf16+f64", "mixed-tf32": "tf32+f64",
-                                                        "mixed-auto": "bf16/tf32+f64"}[args.precision],
-        "data": "synthetic",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nt": w.nt, "beta": w.beta,
-                   "gamma": w.gamma, "kx": w.kx, "ky": w.ky, "m": w.m, "rel_tol": tol,
-                   "precision": args.precision, "iters": stats.iters, "levels": stats.levels,
-                   "inner_vcycles": stats.inner_vcycles,
+                   "gamma": w.gamma, "kx": w.kx, "ky": w.ky, "m": w.m, "rel_tol": REL_TOL,
+                   "stop": "FP64 space-time residual of Eq. (2.4), relative to the initial guess's",
+                   "precision": args.precision, "operands": ["bf16", "tf32"][stats.lp_kind] if stats.lp_kind >= 0 else "fp64",
+                   "iters": stats.iters, "levels": stats.levels, "inner_vcycles": stats.inner_vcycles,
                    "coarse": ["cn", "be"][stats.coarse_used], "step_solves": stats.step_solves,
-                   "l2": "space-time iterate (537 MB) larger than L2; no flush needed",
+                   "tuning": tuning,
+                   "l2": "space-time iterate (4.3 GB FP64) larger than L2; no flush needed",
                    "parallelism": f"replicas x{world} (independent instances per GPU)"},
+        "setup_s": setup_s,
         "roofline": roofline,
         "kernels": kernels,
         "e2e": e2e,
@@ -390,10 +495,10 @@ def run_ours(args, w):
         "gpu_launches": launches,
         "comparators": comparators,
     }
-    if rank == 0 and not args.no_cpu_baseline:
-        coarse = ["cn", "be"][stats.coarse_used]
-        rate, dt, cores, sample = oracle_rate(w, fp64_iters, coarse)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    if want_err:
+        acc, base = oracle_leg(w, U_mixed, U_fp64, fp64_step_solves)
+        line["accuracy"] = acc
+        line["cpu_baseline"] = base
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -458,10 +563,11 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed-bf16", "mixed-tf32", "mixed-auto"], default="mixed-bf16")
+    ap.add_argument("--precision", choices=["fp64", "mixed-bf16", "mixed-tf32", "mixed-auto"], default="mixed-auto")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-comparator", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.workload == "batch64":
         return run_batch(args)

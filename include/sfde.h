@@ -157,6 +157,7 @@ typedef struct {
     long long step_solves;      /* fine/coarse step applications executed, all levels       */
     long long inner_vcycles;    /* low-precision V-cycles (mixed precision only)             */
     double history[SFDE_HISTORY_MAX];  /* residual norm per iteration                         */
+    int lp_kind;          /* operand type of the low-precision steps: 0 BF16, 1 TF32; -1 FP64 form */
 } mgrit_stats;
 
 /*

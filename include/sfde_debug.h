@@ -25,6 +25,16 @@ sfde_status sfde_debug_tc_gemm(int kind, const void* X, long long nslices, int s
                                int reps, float* ms_out);
 
 /*
+ * Failure detection without a fault: one CTA runs the bounded mbarrier wait of the tensor-core
+ * kernels (the same primitive, with limit_ns instead of their 2 s) on a barrier that nothing arrives
+ * at -- no copy or product is issued -- so the wait runs out, records its error code in a device word
+ * and the kernel returns.  1000 <= limit_ns <= 2e9 (SFDE_EINVAL otherwise).  Returns SFDE_ETIMEOUT
+ * with *err_out (may be NULL) = the error word and *waited_s (may be NULL) = the device time the wait
+ * took; the CUDA context stays usable.  Synchronous (device-wide).
+ */
+sfde_status sfde_debug_wait_timeout(unsigned long long limit_ns, int* err_out, double* waited_s);
+
+/*
  * One FP64-accurate slice GEMM on the BF16 tensor cores (error-free digit splitting):
  *   Out[b] = (X[b] * Mat)^T,  b = 0..batch-1,  X: batch x R x K doubles, Mat: K x N doubles (row-major),
  *   Out: batch x N x R doubles; R = 32, 64 or a multiple of 128; K, N multiples of 32, K <= 256.

@@ -196,33 +196,44 @@ def modal_lambda(sigma, dt, scheme="cn"):
     raise ValueError(scheme)
 
 
-def spectral_sequential(prob: SFDE, U0, forcing=None, keep=None):
-    """Exact sequential solution through the per-mode recurrence of Eq. (3.7).
+def spectral_sequential_iter(prob: SFDE, U0, forcing=None, keep=None):
+    """Exact sequential solution through the per-mode recurrence of Eq. (3.7), one time point at a
+    time: yields (n, U_n) for n = 0..N_t (only the n in ``keep`` when it is given; the recurrence still
+    runs over every step).
 
     With C_n = V_y^T M_y U_n M_x V_x (so U_n = V_y C_n V_x^T), each mode obeys
-    c_n = lambda_n c_{n-1} + f_n / (1 + tau_n sigma), f_n = (V_y^T F_n V_x).
-    ``keep`` is an iterable of time indices to return (default: all), as a dict n -> U_n.
+    c_n = lambda_n c_{n-1} + f_n / (1 + tau_n sigma), f_n = (V_y^T F_n V_x).  ``forcing`` is separable
+    (factors time_w, bx, by) or any object whose dense(n) returns F_n.
     """
     lx, Vx, ly, Vy = prob.eig()
     sig = prob.sigma()
     Wx, Wy = prob.Mx @ Vx, prob.My @ Vy
-    C = Wy.T @ np.asarray(U0, dtype=np.float64) @ Wx
-    keep = set(range(prob.nt + 1)) if keep is None else set(keep)
-    out = {}
-    if 0 in keep:
-        out[0] = np.asarray(U0, dtype=np.float64).copy()
-    if forcing is not None:
+    U0 = np.asarray(U0, dtype=np.float64)
+    C = Wy.T @ U0 @ Wx
+    keep = None if keep is None else set(keep)
+    if keep is None or 0 in keep:
+        yield 0, U0.copy()
+    separable = forcing is not None and hasattr(forcing, "bx")
+    if separable:
         px = forcing.bx @ Vx  # (R, N_x): V_x^T b_x^r
         py = forcing.by @ Vy  # (R, N_y)
     for n in range(1, prob.nt + 1):
         dt = prob.t[n] - prob.t[n - 1]
         C = modal_lambda(sig, dt) * C
         if forcing is not None:
-            fh = np.einsum("r,rj,ri->ji", forcing.time_w[n - 1], py, px)
+            if separable:
+                fh = np.einsum("r,rj,ri->ji", forcing.time_w[n - 1], py, px)
+            else:
+                fh = Vy.T @ forcing.dense(n) @ Vx
             C = C + fh / (1.0 + 0.5 * dt * sig)
-        if n in keep:
-            out[n] = Vy @ C @ Vx.T
-    return out
+        if keep is None or n in keep:
+            yield n, Vy @ C @ Vx.T
+
+
+def spectral_sequential(prob: SFDE, U0, forcing=None, keep=None):
+    """``spectral_sequential_iter`` collected: a dict n -> U_n for the time indices in ``keep``
+    (default: all)."""
+    return dict(spectral_sequential_iter(prob, U0, forcing, keep))
 
 
 # ---------------------------------------------------------------------------- error norms

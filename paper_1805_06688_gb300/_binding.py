@@ -62,7 +62,7 @@ class MgritStats(C.Structure):
                 ("coarse_used", C.c_int), ("res0", C.c_double), ("res_final", C.c_double),
                 ("conv_factor_last5", C.c_double), ("seconds", C.c_double), ("tub", C.c_double),
                 ("step_solves", C.c_longlong), ("inner_vcycles", C.c_longlong),
-                ("history", C.c_double * HISTORY_MAX)]
+                ("history", C.c_double * HISTORY_MAX), ("lp_kind", C.c_int)]
 
     def residual_history(self):
         return [self.history[i] for i in range(min(self.iters, HISTORY_MAX))]

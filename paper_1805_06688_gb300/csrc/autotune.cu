@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <string>
+#include <vector>
 
 #include "sfde_internal.cuh"
 
@@ -117,15 +118,22 @@ sfde_status autotune_impl(sfde_ctx* c, const mgrit_opts* opts, const char* cache
         if (out) *out = t;
         return SFDE_OK;
     }
-    // the defaults; the fine level's sweeps in the eigenbasis; one V-cycle more or less per
-    // refinement step (not when the options fix it); the CTA-pair forms forced either way
-    sfde_tuning cand[] = {{1, 1, 0, 0.0}, {1, 3, 0, 0.0}, {1, 1, 5, 0.0}, {1, 1, 3, 0.0}, {2, 1, 0, 0.0},
-                          {3, 1, 0, 0.0}};
-    const int n = (int)(sizeof cand / sizeof cand[0]);
+    // F-relaxations of the fine level as chained steps or in the eigenbasis (the coarse levels' are
+    // always in the eigenbasis), times the default V-cycles per refinement step, 3 or 5 (not when the
+    // options fix it); the CTA-pair forms of the fused step forced either way where that step applies
+    std::vector<sfde_tuning> cand;
+    for (int mc : {1, 2})
+        for (int ic : {0, 3, 5})
+            if (ic == 0 || opts->inner_cycles == 0) cand.push_back({1, mc, ic, 0.0});
+    if (sfde_mixed_kind(c) == 0 && sfde_fused_supported(0, c->x.P, c->y.P) && c->x.P == c->y.P &&
+        sfde_fused_pair_supported(c->x.P)) {
+        cand.push_back({2, 1, 0, 0.0});
+        cand.push_back({3, 1, 0, 0.0});
+    }
+    const int n = (int)cand.size();
     const sfde_tuning before = current(c);
     sfde_status last = SFDE_OK;
     for (int i = 0; i < n; ++i) {
-        if (opts->inner_cycles > 0 && cand[i].inner_cycles != 0) continue;
         apply(c, cand[i]);
         double best = INFINITY;
         bool ok = true;
@@ -141,7 +149,7 @@ sfde_status autotune_impl(sfde_ctx* c, const mgrit_opts* opts, const char* cache
         }
         cand[i].ms = ok ? best : 0.0;
     }
-    const int b = tune_pick(cand, n);
+    const int b = tune_pick(cand.data(), n);
     if (b < 0) {
         apply(c, before);
         return last == SFDE_OK ? SFDE_ENOCONV : last;

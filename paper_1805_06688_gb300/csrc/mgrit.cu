@@ -267,6 +267,7 @@ sfde_status sfde_mgrit_fp64(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) {
     S.levels = L;
     S.coarse_used = coarse;
     S.tub = tub;
+    S.lp_kind = -1;
     sfde_status rc = SFDE_OK;
     if (L == 1) {
         rc = E.coarsest(0);

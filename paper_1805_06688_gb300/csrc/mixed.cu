@@ -184,6 +184,8 @@ struct SfdeMixed {
     void *WTx = nullptr, *WTy = nullptr, *Vx = nullptr, *Vy = nullptr, *VTx = nullptr, *VTy = nullptr;
     float *lamx = nullptr, *lamy = nullptr;
     CUtensorMap mWTx, mWTy, mVx, mVy, mVTx, mVTy;
+    // the same matrices as the fixed operand of the slice GEMM (its tile rows per box)
+    CUtensorMap gWTx, gWTy, gVx, gVy, gVTx, gVTy;
     // the same matrices in 128-row boxes: the pair form of the fused step (P = 256)
     bool pair_ok = false;
     int nsm = 0;
@@ -330,6 +332,12 @@ sfde_status setup_mixed_body(sfde_ctx* c, int kind, int m, int max_levels, int m
     SFDE_TRY(sfde_tc_map_matrix(&M->mVy, M->Vy, M->esz, Py, Py));
     SFDE_TRY(sfde_tc_map_matrix(&M->mVTx, M->VTx, M->esz, Px, Px));
     SFDE_TRY(sfde_tc_map_matrix(&M->mVTy, M->VTy, M->esz, Py, Py));
+    SFDE_TRY(sfde_tc_map_gemm_matrix(&M->gWTx, M->WTx, M->kind, Px, Px));
+    SFDE_TRY(sfde_tc_map_gemm_matrix(&M->gWTy, M->WTy, M->kind, Py, Py));
+    SFDE_TRY(sfde_tc_map_gemm_matrix(&M->gVx, M->Vx, M->kind, Px, Px));
+    SFDE_TRY(sfde_tc_map_gemm_matrix(&M->gVy, M->Vy, M->kind, Py, Py));
+    SFDE_TRY(sfde_tc_map_gemm_matrix(&M->gVTx, M->VTx, M->kind, Px, Px));
+    SFDE_TRY(sfde_tc_map_gemm_matrix(&M->gVTy, M->VTy, M->kind, Py, Py));
     M->pair_ok = kind == 0 && Px == Py && sfde_fused_pair_supported(Px);
     if (M->pair_ok) {
         SFDE_TRY(sfde_tc_map_matrix_rows(&M->hWTx, M->WTx, M->esz, Px, Px, 128));
@@ -476,7 +484,7 @@ struct LpEngine {
             // G1: (X W_x)^T  or  (X V_x)^T
             p.R = Py; p.C = Px; p.Cout = Px; p.BN = sfde_tc_tile_n(Px); p.s0 = src0 + b0 * ds; p.ds = ds;
             p.out = M->T1; p.out_stride = P2l;
-            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a1, solve ? M->mVTx : M->mWTx, p, c->stream, c->y.n, c->x.n, c->x.n));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a1, solve ? M->gVTx : M->gWTx, p, c->stream, c->y.n, c->x.n, c->x.n));
             // G2: modal scaling
             TcArgs q{};
             q.batch = nb; q.err = M->err;
@@ -484,13 +492,13 @@ struct LpEngine {
             q.out = M->T2; q.out_stride = P2l;
             q.e.lamx = M->lamx; q.e.lamy = M->lamy; q.e.kx = (float)c->kx; q.e.ky = (float)c->ky;
             q.e.dt = dt; q.e.n0 = n0 + b0 * dn; q.e.dn = dn; q.e.scheme = solve ? SCHEME_SOLVE : sch;
-            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_SCALE, a2, solve ? M->mVTy : M->mWTy, q, c->stream, c->x.n, c->y.n, c->y.n));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_SCALE, a2, solve ? M->gVTy : M->gWTy, q, c->stream, c->x.n, c->y.n, c->y.n));
             // G3: (C V_x^T)^T
             TcArgs r{};
             r.batch = nb; r.err = M->err;
             r.R = Py; r.C = Px; r.Cout = Px; r.BN = sfde_tc_tile_n(Px); r.s0 = 0; r.ds = 1;
             r.out = M->T3; r.out_stride = P2l;
-            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a3, M->mVx, r, c->stream, c->y.n, c->x.n, c->x.n));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a3, M->gVx, r, c->stream, c->y.n, c->x.n, c->x.n));
             // G4: (T3 V_y^T)^T + g - u_target
             TcArgs f{};
             f.batch = nb; f.err = M->err;
@@ -500,11 +508,13 @@ struct LpEngine {
             f.e.g_stride = (long long)dn * P2l;
             f.e.utgt = ut ? (const void*)((const char*)ut + (size_t)b0 * dn * P2() * M->esz) : nullptr;
             f.e.utgt_stride = (long long)dn * P2l;
+            // sfde_tc_partials_per_tile() partial sums (one per epilogue warp) per output tile
             const int gx = (int)(((long long)nb * Px + 127) / 128), gy = Py / f.BN;
-            if (partial && (size_t)(total + gx * gy) > c->partial_cap) return SFDE_EINVAL;
+            const int ppt = sfde_tc_partials_per_tile();
+            if (partial && (size_t)(total + ppt * gx * gy) > c->partial_cap) return SFDE_EINVAL;
             f.e.partial = partial ? partial + total : nullptr;
-            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_FINAL, a4, M->mVy, f, c->stream, c->x.n, c->y.n, c->y.n));
-            total += gx * gy;
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_FINAL, a4, M->gVy, f, c->stream, c->x.n, c->y.n, c->y.n));
+            total += ppt * gx * gy;
         }
         steps += batch;
         if (npart) *npart = total;
@@ -525,12 +535,12 @@ struct LpEngine {
             p.batch = nb; p.err = M->err;
             p.R = Py; p.C = Px; p.Cout = Px; p.BN = sfde_tc_tile_n(Px); p.s0 = src0 + b0 * ds; p.ds = ds;
             p.out = M->T1; p.out_stride = P2l;
-            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a1, M->mWTx, p, c->stream, c->y.n, c->x.n, c->x.n));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a1, M->gWTx, p, c->stream, c->y.n, c->x.n, c->x.n));
             TcArgs q{};   // (T1 W_y)^T = W_y^T X W_x
             q.batch = nb; q.err = M->err;
             q.R = Px; q.C = Py; q.Cout = Py; q.BN = sfde_tc_tile_n(Py); q.s0 = 0; q.ds = 1;
             q.out = slice(dst, (long long)b0 * dst_ds); q.out_stride = (long long)dst_ds * P2l;
-            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a2, M->mWTy, q, c->stream, c->x.n, c->y.n, c->y.n));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a2, M->gWTy, q, c->stream, c->x.n, c->y.n, c->y.n));
         }
         return SFDE_OK;
     }
@@ -552,14 +562,14 @@ struct LpEngine {
             r.batch = nb; r.err = M->err;
             r.R = Py; r.C = Px; r.Cout = Px; r.BN = sfde_tc_tile_n(Px); r.s0 = b0; r.ds = 1;
             r.out = M->T3; r.out_stride = P2l;
-            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a3, M->mVx, r, c->stream, c->y.n, c->x.n, c->x.n));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a3, M->gVx, r, c->stream, c->y.n, c->x.n, c->x.n));
             TcArgs f{};   // (T3 V_y^T)^T = V_y Y V_x^T
             f.batch = nb; f.err = M->err;
             f.R = Px; f.C = Py; f.Cout = Py; f.BN = sfde_tc_tile_n(Py); f.s0 = 0; f.ds = 1;
             f.out = slice(dst, oskip > 0 ? (long long)b0 + b0 / oskip : (long long)b0);
             f.out_stride = P2l;
             f.oskip = oskip;
-            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a4, M->mVy, f, c->stream, c->x.n, c->y.n, c->y.n));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a4, M->gVy, f, c->stream, c->x.n, c->y.n, c->y.n));
         }
         return SFDE_OK;
     }
@@ -790,6 +800,7 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
     S.levels = L;
     S.coarse_used = coarse;
     S.tub = tub;
+    S.lp_kind = kind;
     SFDE_CUDA(cudaEventRecord(c->ev0, c->stream));
     SFDE_CUDA(cudaMemcpyAsync(U, c->U0, sizeof(double) * P2, cudaMemcpyDeviceToDevice, c->stream));
     if (o->init_seed) {

@@ -201,7 +201,7 @@ __device__ __forceinline__ float i128_to_f32(__int128 x, float s1, float s2) {
 // to FP32 within 1.5 ulp -- no FP64 arithmetic per element (the FP64 pipe runs at about 1/64 of
 // the FP32 rate).  With a load term the FP64 form is kept.  Writes rho (BF16 or TF32-rounded FP32),
 // zero outside the interior nodes, and one FP64 sum of rho^2 per block.
-template <typename OT>
+template <typename OT, bool TF32R>
 __global__ void __launch_bounds__(256, 4) k_combine_int(
     const long long* __restrict__ T1, const long long* __restrict__ T3, const long long* __restrict__ DU,
     const int* __restrict__ En, int n0, int Px, int Py, int nx, int ny, double cmass, int ex, int ey, int zsx, int zsy,
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
         sq = fmaf(rf, rf, sq);
         OT* o = rout + (size_t)b * rout_stride + (size_t)j * Px + i;
         if (sizeof(OT) == 2) *o = (OT)__float2bfloat16_rn(rf);
-        else *o = (OT)sfde_round_tf32(rf);
+        else *o = TF32R ? (OT)sfde_round_tf32(rf) : (OT)rf;
     }
     double sqd = sq;
     for (int o = 16; o > 0; o >>= 1) sqd += __shfl_xor_sync(0xffffffffu, sqd, o);
@@ -386,13 +386,19 @@ sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int cou
         const double cmass = c->x.h * c->y.h / 36.0;
         slot = sfde_prof_begin(c);
         if (out_kind == 0)
-            k_combine_int<__nv_bfloat16><<<grid, block, 0, c->stream>>>(
+            k_combine_int<__nv_bfloat16, false><<<grid, block, 0, c->stream>>>(
                 (const long long*)c->T1, (const long long*)c->T3, du, En, n0, Px, Py, c->x.n, c->y.n, cmass,
                 Ax.e_uniform, Ay.e_uniform, sfde_oz_int_shift(Px), sfde_oz_int_shift(Py), c->dt0, c->rank,
                 c->time_w, c->bxn, c->byn, c->Fd, (__nv_bfloat16*)ro,
                 rout_stride, partial + total);
+        else if (out_kind == 1)
+            k_combine_int<float, true><<<grid, block, 0, c->stream>>>(
+                (const long long*)c->T1, (const long long*)c->T3, du, En, n0, Px, Py, c->x.n, c->y.n, cmass,
+                Ax.e_uniform, Ay.e_uniform, sfde_oz_int_shift(Px), sfde_oz_int_shift(Py), c->dt0, c->rank,
+                c->time_w, c->bxn, c->byn, c->Fd, (float*)ro, rout_stride,
+                partial + total);
         else
-            k_combine_int<float><<<grid, block, 0, c->stream>>>(
+            k_combine_int<float, false><<<grid, block, 0, c->stream>>>(
                 (const long long*)c->T1, (const long long*)c->T3, du, En, n0, Px, Py, c->x.n, c->y.n, cmass,
                 Ax.e_uniform, Ay.e_uniform, sfde_oz_int_shift(Px), sfde_oz_int_shift(Py), c->dt0, c->rank,
                 c->time_w, c->bxn, c->byn, c->Fd, (float*)ro, rout_stride,

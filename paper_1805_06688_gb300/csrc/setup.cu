@@ -176,6 +176,77 @@ __global__ void k_jacobi_apply_Q(double* Q, int ne, const Rot* rot) {
     Q[iq] = rb.s * u + rb.c * v;
 }
 
+// The whole Jacobi iteration in one CTA for small even orders (ne <= 64): C and Q held in shared
+// memory, the same rotations applied in the same rounds as k_jacobi_rotations / k_jacobi_apply /
+// k_jacobi_apply_Q, sweeps until the off-diagonal mass falls to the rounding floor (at most
+// max_sweeps).  Leading dimension ne in global and shared memory.
+constexpr int JACOBI_SMEM_MAX = 64;
+__global__ void __launch_bounds__(256) k_jacobi_small(double* Cg, double* Qg, int ne, int max_sweeps) {
+    extern __shared__ double sm[];
+    double* C = sm;
+    double* Q = sm + ne * ne;
+    __shared__ Rot rot[JACOBI_SMEM_MAX / 2];
+    __shared__ double so[256], sd[256];
+    __shared__ int done;
+    const int half = ne / 2;
+    for (int e = threadIdx.x; e < ne * ne; e += blockDim.x) { C[e] = Cg[e]; Q[e] = Qg[e]; }
+    __syncthreads();
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        for (int round = 0; round < ne - 1; ++round) {
+            for (int k = threadIdx.x; k < half; k += blockDim.x) {
+                const int p = rr_player(k, round, ne), q = rr_player(ne - 1 - k, round, ne);
+                const double app = C[p * ne + p], aqq = C[q * ne + q], apq = C[p * ne + q];
+                double c = 1.0, s = 0.0;
+                if (apq != 0.0) {
+                    const double tau = (aqq - app) / (2.0 * apq);
+                    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                    c = 1.0 / sqrt(1.0 + t * t);
+                    s = t * c;
+                }
+                rot[k] = Rot{p, q, c, s};
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < half * half; e += blockDim.x) {
+                const int a = e / half, b = e % half;
+                const Rot ra = rot[a], rb = rot[b];
+                const int pp = ra.p * ne + rb.p, pq = ra.p * ne + rb.q, qp = ra.q * ne + rb.p, qq = ra.q * ne + rb.q;
+                const double w = C[pp], x = C[pq], y = C[qp], z = C[qq];
+                const double w1 = rb.c * w - rb.s * x, x1 = rb.s * w + rb.c * x;
+                const double y1 = rb.c * y - rb.s * z, z1 = rb.s * y + rb.c * z;
+                const double w2 = ra.c * w1 - ra.s * y1, y2 = ra.s * w1 + ra.c * y1;
+                double x2 = ra.c * x1 - ra.s * z1, z2 = ra.s * x1 + ra.c * z1;
+                double y2b = y2;
+                if (a == b) { x2 = 0.0; y2b = 0.0; }
+                C[pp] = w2; C[pq] = x2; C[qp] = y2b; C[qq] = z2;
+            }
+            for (int e = threadIdx.x; e < ne * half; e += blockDim.x) {
+                const int i = e / half, b = e % half;
+                const Rot rb = rot[b];
+                const double u = Q[i * ne + rb.p], v = Q[i * ne + rb.q];
+                Q[i * ne + rb.p] = rb.c * u - rb.s * v;
+                Q[i * ne + rb.q] = rb.s * u + rb.c * v;
+            }
+            __syncthreads();
+        }
+        double off = 0.0, dg = 0.0;
+        for (int e = threadIdx.x; e < ne * ne; e += blockDim.x) {
+            const double v = C[e];
+            if (e / ne == e % ne) dg += v * v; else off += v * v;
+        }
+        so[threadIdx.x] = off;
+        sd[threadIdx.x] = dg;
+        __syncthreads();
+        for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+            if ((int)threadIdx.x < k) { so[threadIdx.x] += so[threadIdx.x + k]; sd[threadIdx.x] += sd[threadIdx.x + k]; }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) done = so[0] <= 1e-30 * (double)ne * sd[0];
+        __syncthreads();
+        if (done) break;
+    }
+    for (int e = threadIdx.x; e < ne * ne; e += blockDim.x) { Cg[e] = C[e]; Qg[e] = Q[e]; }
+}
+
 __global__ void k_offdiag_norm(const double* C, int ne, double* out /* [off, diag] */) {
     __shared__ double so[256], sd[256];
     double off = 0.0, dg = 0.0;
@@ -380,7 +451,12 @@ sfde_status sfde_setup_direction(SfdeDir& d, int n, double rho, double length, c
     k_symmetrize<<<dim3((ne + 127) / 128, ne), 128, 0, s>>>(C, ne, n);
     k_identity<<<dim3((ne + 127) / 128, ne), 128, 0, s>>>(Q, ne);
 
-    if (ne >= 2) {
+    if (ne >= 2 && ne <= JACOBI_SMEM_MAX) {
+        // one launch for the whole iteration (C and Q in shared memory)
+        SETUP_CUDA(cudaFuncSetAttribute(k_jacobi_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(sizeof(double) * 2 * JACOBI_SMEM_MAX * JACOBI_SMEM_MAX)));
+        k_jacobi_small<<<1, 256, sizeof(double) * 2 * EE, s>>>(C, Q, ne, 30);
+    } else if (ne >= 2) {
         double hn[2];
         for (int sweep = 0; sweep < 30; ++sweep) {
             for (int round = 0; round < ne - 1; ++round) {

@@ -145,7 +145,8 @@ sfde_status sfde_step_fp64(sfde_ctx* c, const StepBatch& sb, int* n_partials);
 sfde_status sfde_reduce_partials(sfde_ctx* c, int n_partials, double* host_out);
 sfde_status sfde_step_fp64_into(sfde_ctx* c, const StepBatch& sb, double* T1, double* T2, double* T3);
 // rho_n = F_n + M_h (U_{n-1} - U_n) - tau_n K (U_{n-1} + U_n), n = n_first .. n_first+count-1, in FP64;
-// written as BF16 (out_kind 0) or FP32 (1) to rout (slice stride rout_stride elements), with
+// written as BF16 (out_kind 0), FP32 rounded to TF32 (1) or FP32 (2) to rout (slice stride
+// rout_stride elements), with
 // per-CTA sums of rho^2 in partial.
 sfde_status sfde_residual_fp64(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
                                long long rout_stride, int out_kind, double* partial, int* n_partials);
@@ -191,14 +192,22 @@ sfde_status sfde_no_throw(F&& f) noexcept {
 }
 
 int sfde_tc_tile_n(int cout);
+int sfde_tc_partials_per_tile();   // partial sums of squares the slice GEMM writes per output tile
 sfde_status sfde_tc_prepare();
 sfde_status sfde_tc_map_slices(CUtensorMap* map, const void* base, int esz, int K, int R, int ds, long long nslices);
 sfde_status sfde_tc_map_matrix(CUtensorMap* map, const void* matT, int esz, int K, int N);
+// the fixed-matrix operand (Mat^T, N x K) of sfde_tc_gemm of operand kind `kind`: boxes of the
+// slice GEMM's tile rows (half of them in its CTA-pair form)
+sfde_status sfde_tc_map_gemm_matrix(CUtensorMap* map, const void* matT, int kind, int K, int N);
 // as sfde_tc_map_matrix with boxes of `rows` rows (<= 256)
 sfde_status sfde_tc_map_matrix_rows(CUtensorMap* map, const void* matT, int esz, int K, int N, int rows);
+// kind 0: BF16 operands and storage; 1: FP32 storage rounded to TF32, TF32 products; 2: FP32 storage,
+// products from three TF32 products each (Blo: the map of the fixed matrix's low parts, required).
 // c may be NULL (no accounting); nr, nc, nout: unpadded extents of one slice product
 sfde_status sfde_tc_gemm(sfde_ctx* c, int kind, int epi, const CUtensorMap& A, const CUtensorMap& B, const TcArgs& p,
-                         cudaStream_t s, int nr = 0, int nc = 0, int nout = 0);
+                         cudaStream_t s, int nr = 0, int nc = 0, int nout = 0, const CUtensorMap* Blo = nullptr);
+// dst = lo(src) = src - (src with its 13 low mantissa bits cleared), n FP32 values (kind 2 operands)
+sfde_status sfde_tc_lo_parts(const float* src, float* dst, size_t n, cudaStream_t s);
 
 // ---- one whole spectral step per CTA, four chained BF16 products on chip (fused_step.cu)
 struct FusedStepArgs {

@@ -23,7 +23,8 @@
 
 namespace {
 
-enum Epi { EPI_STORE = 0, EPI_MODAL = 1, EPI_FINAL = 2, EPI_RESID_BF16 = 3, EPI_RESID_F32 = 4, EPI_RESID_NONE = 5 };
+enum Epi { EPI_STORE = 0, EPI_MODAL = 1, EPI_FINAL = 2, EPI_RESID_BF16 = 3, EPI_RESID_F32 = 4, EPI_RESID_NONE = 5,
+           EPI_RESID_F32X = 6 };
 
 struct GemmParams {
     const double* X; long long x_stride; int R, C;
@@ -57,7 +58,10 @@ constexpr int BK = 16;
 template <int EPI> struct ResidOut { using T = double; };
 template <> struct ResidOut<EPI_RESID_BF16> { using T = __nv_bfloat16; };
 template <> struct ResidOut<EPI_RESID_F32> { using T = float; };
-constexpr bool is_resid(int e) { return e == EPI_RESID_BF16 || e == EPI_RESID_F32 || e == EPI_RESID_NONE; }
+template <> struct ResidOut<EPI_RESID_F32X> { using T = float; };
+constexpr bool is_resid(int e) {
+    return e == EPI_RESID_BF16 || e == EPI_RESID_F32 || e == EPI_RESID_NONE || e == EPI_RESID_F32X;
+}
 
 __device__ __forceinline__ void store_as(__nv_bfloat16* p, double v) { *p = __float2bfloat16_rn((float)v); }
 __device__ __forceinline__ void store_as(float* p, double v) { *p = sfde_round_tf32((float)v); }
@@ -193,7 +197,9 @@ __global__ void __launch_bounds__(256) k_slice_gemm_fp64(GemmParams p) {
                 // interior node, so the residual is defined as zero there
                 const double rho = (i < p.nx && j < p.ny) ? f + mass - tau * stiff : 0.0;
                 sq += rho * rho;
-                if (EPI != EPI_RESID_NONE) {
+                if (EPI == EPI_RESID_F32X) {
+                    ((float*)p.rout)[b * p.out_stride + o] = (float)rho;   // FP32, not rounded to TF32
+                } else if (EPI != EPI_RESID_NONE) {
                     using OT = typename ResidOut<EPI>::T;
                     store_as((OT*)p.rout + b * p.out_stride + o, rho);
                 }
@@ -404,7 +410,8 @@ namespace {
 
 // rho_b = [F_n] + M_h (Uprev_b - Ucur_b) - tau_n K (Uprev_b + Ucur_b) for slices b < count,
 // Ucur_b = Ucur + b u_stride, Uprev_b = Uprev + b u_stride (Uprev null: zero), n = n0 + b tdn, in
-// chunks of the FP64 workspace; out_kind 0 BF16, 1 FP32, 2 none (sums of squares only)
+// chunks of the FP64 workspace; out_kind 0 BF16, 1 FP32 rounded to TF32, 2 FP32, 3 none (sums of
+// squares only)
 sfde_status resid_general(sfde_ctx* c, const double* Ucur, const double* Uprev, long long u_stride, int n0,
                           int tdn, int count, bool load, void* rout, long long rout_stride, int out_kind,
                           double* partial, int* n_partials) {
@@ -444,6 +451,7 @@ sfde_status resid_general(sfde_ctx* c, const double* Ucur, const double* Uprev, 
         q.partial = partial + total;
         if (out_kind == 0) launch_T<EPI_RESID_BF16>(c, T, q, c->x.n, c->y.n, c->y.n);
         else if (out_kind == 1) launch_T<EPI_RESID_F32>(c, T, q, c->x.n, c->y.n, c->y.n);
+        else if (out_kind == 2) launch_T<EPI_RESID_F32X>(c, T, q, c->x.n, c->y.n, c->y.n);
         else launch_T<EPI_RESID_NONE>(c, T, q, c->x.n, c->y.n, c->y.n);
         total += (int)ctas;
     }
@@ -469,7 +477,7 @@ sfde_status sfde_residual_norm2_fp64(sfde_ctx* c, const double* U, double* norm2
         const int cnt = std::min(chunk, c->nt - n + 1);
         int np = 0;
         SFDE_TRY(resid_general(c, U + (size_t)n * P2, U + (size_t)(n - 1) * P2, (long long)P2, n, 1, cnt, true,
-                               nullptr, 0, 2, c->partial, &np));
+                               nullptr, 0, 3, c->partial, &np));
         double r2 = 0.0;
         SFDE_TRY(sfde_reduce_partials(c, np, &r2));
         acc += r2;
@@ -486,7 +494,7 @@ sfde_status sfde_apply_S_norm2(sfde_ctx* c, const double* R, long long r_stride,
         const int cnt = std::min(chunk, count - b);
         int np = 0;
         SFDE_TRY(resid_general(c, R + (size_t)b * r_stride, nullptr, r_stride, n0 + b * dn, dn, cnt, false, nullptr, 0,
-                               2, c->partial, &np));
+                               3, c->partial, &np));
         double r2 = 0.0;
         SFDE_TRY(sfde_reduce_partials(c, np, &r2));
         acc += r2;

@@ -64,3 +64,36 @@ def test_batch_rejects_repeated_contexts():
     P = make(INSTANCES[0])[0]
     with pytest.raises(sfde.SfdeError):
         sfde.batch_solve([P, P], **KW)
+
+
+def test_batch64_uneven_instances_against_oracle():
+    """The batched form on all 64 instances of the uneven batch (N in {63, 127, 255, 511}, N_t in
+    {256, 512, 1024, 4096}, random orders and diffusivities, sine-mode psi_0, f = 0), operands chosen
+    per instance, stopped on the FP64 space-time residual at 1e-8: every instance converges and its
+    u(T) matches the oracle's exact sequential solution to 1e-8 of the solution's size."""
+    from concurrent.futures import ThreadPoolExecutor
+    from sfde_workloads.generate import batch_workloads
+    ws = batch_workloads(0, 64)
+    probs, UT = [], []
+    for w in ws:
+        P = sfde.Problem(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, w.t(), w.omega, precision=sfde.PREC_MIXED_AUTO)
+        P.set_initial(w.initial())
+        probs.append(P)
+        UT.append(np.zeros((w.ny, w.nx)))
+    st, status, stats = sfde.batch_solve(probs, U_T=UT, m=8, max_levels=32, coarse=sfde.COARSE_AUTO, rel_tol=1e-8,
+                                         max_iter=200, stop_kind=sfde.STOP_SFORM)
+    assert st == sfde.SFDE_OK and all(s == 0 for s in status), status
+    assert all(s.converged for s in stats)
+
+    def check(k):
+        w = ws[k]
+        O = osfde.SFDE(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, w.t(), w.omega)
+        psi = w.initial()
+        exact = osfde.spectral_sequential(O, psi, None, keep=[w.nt])[w.nt]
+        scale = max(np.abs(psi).max(), np.abs(exact).max())
+        return float(np.abs(UT[k] - exact).max() / scale)
+
+    with ThreadPoolExecutor(max_workers=8) as ex:
+        errs = list(ex.map(check, range(len(ws))))
+    worst = int(np.argmax(errs))
+    assert max(errs) <= 1e-8, (ws[worst].name, errs[worst])

@@ -260,3 +260,26 @@ def test_dense_forcing_matches_oracle():
     assert relerr(U, ref) < 1e-11
     with pytest.raises(ValueError):
         P.set_forcing_dense(D.F[:-1])
+
+
+@pytest.mark.parametrize("relax,levels,m", [("FCF", 3, 4), ("F", 2, 4), ("FCF", 2, 2)])
+def test_shishkin_grid_matches_oracle(relax, levels, m):
+    """The piecewise-uniform partition of Sec. 4.1 (N/4 steps on [0, s], N/2 on [s, T - s], N/4 on
+    [T - s, T], s = 2 eps ln N), with MGRIT (FCF) and the parareal form (F-relaxation, two levels):
+    the GPU iteration against the oracle's, iteration by iteration, and its fixed point against
+    sequential stepping."""
+    nx, ny, nt = 24, 17, 64
+    t = time_grid(nt, 1.0, "shishkin", eps=2.0 ** -6)
+    assert len(set(np.round(np.diff(t), 15))) >= 2          # really piecewise uniform
+    F, _ = gaussian_bump_forcing(8, nx, ny, t)
+    psi = sine_mode_nodal(sine_mode_amplitudes(6), nx, ny)
+    P, O = make(0.6, 0.7, 3.0, 7.5, nx, ny, t, forcing=F, psi0=psi)
+    U = np.zeros((nt + 1, ny, nx))
+    _, st = P.mgrit(U=U, m=m, max_levels=levels, coarse=sfde.COARSE_BE,
+                    relax={"FCF": sfde.RELAX_FCF, "F": sfde.RELAX_F}[relax], rel_tol=1e-11, max_iter=80)
+    ref = omgrit.mgrit(O, psi, F, m=m, max_levels=levels, coarse="be", relax=relax, rel_tol=1e-11, max_iter=80)
+    assert st.converged and st.iters == ref.iters and st.levels == ref.levels == levels
+    for a, b in zip(st.residual_history(), ref.history):
+        assert abs(a - b) <= 1e-9 * ref.history[0]
+    assert relerr(U, ref.U) < 1e-10
+    assert relerr(U, osfde.seq_timestep(O, psi, F)) < 1e-9

@@ -271,3 +271,39 @@ def test_mixed_bf16_solve_pair_forms():
         _, stats = P.mgrit(U=U, m=8, max_levels=4, coarse=sfde.COARSE_BE, rel_tol=1e-10, max_iter=60)
         assert stats.converged
         assert np.abs(U - ref).max() <= 1e-8 * np.abs(ref).max(), mode
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+@pytest.mark.parametrize("nx,ny,batch,n0", CASES)
+def test_step_elementwise_error_bound_against_oracle(scheme, nx, ny, batch, n0):
+    """Element by element against the oracle's FP64 step.  The low-precision step computes
+    X = V_y [f o (L_y^T U L_x)] V_x^T (L = W = M V for a propagator, L = V for the solve, f the modal
+    factor of Eq. (3.7)) with the input, four matrices, three intermediates and the output each
+    rounded to BF16 (unit roundoff u = 2^-9) and FP32 accumulation; to first order every element's
+    error is at most 9 u times the same chain taken in absolute values,
+        B = |V_y| (|f| o (|L_y|^T |U| |L_x|)) |V_x|^T,
+    so |x - x_oracle| <= 10 u B holds element by element, for the fused kernel and the chain."""
+    nt = n0 + batch + 3
+    t = time_grid(nt, 1.0, "graded")
+    O = osfde.SFDE(0.7, 0.8, 1.0, 0.5, nx, ny, t)
+    P = sfde.Problem(0.7, 0.8, 1.0, 0.5, nx, ny, t, precision=sfde.PREC_MIXED_BF16)
+    rng = np.random.default_rng(nx * 11 + scheme)
+    U = rng.standard_normal((batch, ny, nx))
+    ref = oracle_step(O, scheme, U, n0)
+    lx, Vx, ly, Vy = O.eig()
+    sig = O.sigma()
+    Lx, Ly = (O.Mx @ Vx, O.My @ Vy) if scheme < 2 else (Vx, Vy)
+    aVx, aVy, aLx, aLy = np.abs(Vx), np.abs(Vy), np.abs(Lx), np.abs(Ly)
+    u = 2.0 ** -9
+    for fused in (1, 0):
+        st, x, _ = lp_step(P, fused, scheme, U, n0)
+        assert st == 0, sfde.sfde_strerror(st)
+        worst = 0.0
+        for b in range(batch):
+            dt = O.t[n0 + b] - O.t[n0 + b - 1]
+            f = (osfde.modal_lambda(sig, dt, "cn") if scheme == 0 else
+                 osfde.modal_lambda(sig, dt, "be") if scheme == 1 else 1.0 / (1.0 + 0.5 * dt * sig))
+            B = aVy @ (np.abs(f) * (aLy.T @ np.abs(U[b]) @ aLx)) @ aVx.T
+            r = np.abs(x[b] - ref[b]) / (u * B)
+            worst = max(worst, float(r.max()))
+        assert worst <= 10.0, (fused, worst)

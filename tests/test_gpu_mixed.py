@@ -73,11 +73,26 @@ def test_mixed_manufactured(name, prec):
     assert st.converged and _err(U, ref) < 1e-8
 
 
+def _all_slice_errors(U, O, psi, F):
+    """Max-norm error of every time slice of U (a device tensor) against the oracle's exact
+    sequential solution, streamed slice by slice: (max |U - u| / max |u| over space-time,
+    max over n >= 1 of max |U_n - u_n| / max |u_n|)."""
+    Uh = U.cpu().numpy()
+    emax = smax = per = 0.0
+    for n, E in osfde.spectral_sequential_iter(O, psi, F):
+        d, m = float(np.abs(Uh[n] - E).max()), float(np.abs(E).max())
+        emax, smax = max(emax, d), max(smax, m)
+        if n > 0 and m > 0:
+            per = max(per, d / m)
+    return emax / smax, per
+
+
 @pytest.mark.parametrize("name,prec", PRECS)
 def test_mixed_sine_N255_Nt1024_full_size(name, prec):
-    """The benchmarked workload in the bench's configuration (relative residual 1e-8), against the
-    exact sequential solution at sampled time points: space-time max-norm error <= 1e-8 of max|u|
-    (measured 3.7e-10)."""
+    """The N = 255 workload (f = 0, u decays by about 1e-7 up to T) at full size, stopped on the FP64
+    space-time residual at 1e-8, against the exact sequential solution at all 1025 time points:
+    space-time max-norm error <= 1e-8 of max|u|; the error relative to each slice's own maximum is
+    bounded too (the late slices are 1e-7 of the first)."""
     w = WORKLOADS["sine_N255_Nt1024"]
     t = w.t()
     psi = w.initial()
@@ -87,31 +102,34 @@ def test_mixed_sine_N255_Nt1024_full_size(name, prec):
     _, st = P.mgrit(U=U, m=w.m, max_levels=32, coarse=sfde.COARSE_AUTO, rel_tol=1e-8, max_iter=100)
     assert st.converged
     O = osfde.SFDE(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t)
-    keep = [1, 7, 8, 100, 513, 1024]
-    exact = osfde.spectral_sequential(O, psi, None, keep=keep)
-    scale = np.abs(psi).max()
-    for n in keep:
-        assert np.abs(U[n].cpu().numpy() - exact[n]).max() < 1e-8 * scale, n
+    glob, per = _all_slice_errors(U, O, psi, None)
+    print(f"sine_N255_Nt1024 {name}: space-time {glob:.2e}, worst slice-relative {per:.2e}")
+    assert glob < 1e-8, glob
+    assert per < 1e-4, per
 
 
-def test_mixed_bump_N511_Nt2048_full_size():
+@pytest.mark.parametrize("name,prec", PRECS)
+def test_mixed_bump_N511_Nt2048_full_size(name, prec):
     """The N = 511 workload (padded P = 512: four-GEMM tensor-core steps and the K-grouped integer
-    residual), mixed BF16 to 1e-8, against the exact sequential solution at sampled time points."""
+    residual), stopped on the FP64 space-time residual at 1e-8 with the fine level's F-relaxations in
+    the eigenbasis and 3 V-cycles per refinement step (the benchmark's tuned choice), against the exact
+    sequential solution at all 2049 time points."""
     w = WORKLOADS["bump_N511_Nt2048"]
     t = w.t()
     psi, F = w.initial(), w.forcing()
-    P = sfde.Problem(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t, precision=sfde.PREC_MIXED_BF16)
+    P = sfde.Problem(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t, precision=prec)
     P.set_initial(psi)
     P.set_forcing(F)
+    P.set_tuning(fused_pair=1, modal_chains=2, inner_cycles=3)
     U = torch.zeros((w.nt + 1, w.ny, w.nx), dtype=torch.float64, device="cuda")
-    _, st = P.mgrit(U=U, m=w.m, max_levels=32, coarse=sfde.COARSE_AUTO, rel_tol=w.rel_tol, max_iter=100)
+    _, st = P.mgrit(U=U, m=w.m, max_levels=32, coarse=sfde.COARSE_AUTO, rel_tol=1e-8, max_iter=100,
+                    stop_kind=sfde.STOP_SFORM)
     assert st.converged
     O = osfde.SFDE(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t)
-    keep = [1, 9, 512, 1500, 2048]
-    exact = osfde.spectral_sequential(O, psi, F, keep=keep)
-    scale = max(np.abs(exact[n]).max() for n in keep)
-    for n in keep:
-        assert np.abs(U[n].cpu().numpy() - exact[n]).max() < 1e-8 * scale, n
+    glob, per = _all_slice_errors(U, O, psi, F)
+    print(f"bump_N511_Nt2048 {name}: space-time {glob:.2e}, worst slice-relative {per:.2e}")
+    assert glob < 1e-8, glob
+    assert per < 1e-6, per
 
 
 def test_mixed_adaptive_and_exact_residual_digits_agree():
@@ -174,3 +192,51 @@ def test_mixed_dense_forcing(name, prec):
     _, st = P.mgrit(U=U, m=4, max_levels=8, coarse=sfde.COARSE_BE, rel_tol=1e-11, max_iter=60)
     assert st.converged
     assert _err(U, ref) < 1e-8, (st.iters, _err(U, ref))
+
+
+@pytest.mark.parametrize("name,prec", PRECS)
+def test_mixed_shishkin_grid(name, prec):
+    """Mixed precision on the piecewise-uniform partition of Sec. 4.1 (three different step sizes,
+    so the fine propagator changes along the grid): exact sequential solution to 1e-8 at every
+    time point."""
+    nx, ny, nt = 100, 70, 128
+    t = time_grid(nt, 1.0, "shishkin", eps=2.0 ** -6)
+    F, _ = gaussian_bump_forcing(5, nx, ny, t)
+    psi = sine_mode_nodal(sine_mode_amplitudes(4), nx, ny)
+    ref = osfde.seq_timestep(osfde.SFDE(0.6, 0.7, 3.0, 7.5, nx, ny, t), psi, F)
+    P = sfde.Problem(0.6, 0.7, 3.0, 7.5, nx, ny, t, precision=prec)
+    P.set_initial(psi)
+    P.set_forcing(F)
+    U = np.zeros((nt + 1, ny, nx))
+    _, st = P.mgrit(U=U, m=4, max_levels=8, coarse=sfde.COARSE_AUTO, rel_tol=1e-11, max_iter=60)
+    assert st.converged
+    assert _err(U, ref) < 1e-8, (st.iters, _err(U, ref))
+
+
+def test_mixed_graded_N1023_Nt4096_full_size():
+    """The largest workload: 1023^2 nodes (padded P = 1024, dense 1023 x 1023 Toeplitz matrices),
+    4096 steps on the graded grid t_n = (n/N)^2 (the fine propagator changes at every step), m = 16,
+    operands chosen by SFDE_PREC_MIXED_AUTO (TF32 here), stopped on the FP64 space-time residual at
+    1e-8.  Against the exact sequential solution at every C-point of the fine level (every 16th time
+    point) and at the first 16 steps, where the grid's steps are smallest."""
+    w = WORKLOADS["graded_N1023_Nt4096"]
+    t = w.t()
+    psi, F = w.initial(), w.forcing()
+    P = sfde.Problem(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t, precision=sfde.PREC_MIXED_AUTO)
+    P.set_initial(psi)
+    P.set_forcing(F)
+    U = torch.zeros((w.nt + 1, w.ny, w.nx), dtype=torch.float64, device="cuda")
+    _, st = P.mgrit(U=U, m=w.m, max_levels=32, coarse=sfde.COARSE_AUTO, rel_tol=1e-8, max_iter=100,
+                    stop_kind=sfde.STOP_SFORM)
+    assert st.converged and st.lp_kind == 1
+    keep = sorted(set(range(0, w.nt + 1, w.m)) | set(range(1, 17)))
+    Uk = U[torch.tensor(keep, device="cuda")].cpu().numpy()
+    del U
+    pos = {n: k for k, n in enumerate(keep)}
+    O = osfde.SFDE(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t)
+    emax = smax = 0.0
+    for n, E in osfde.spectral_sequential_iter(O, psi, F, keep=keep):
+        emax = max(emax, float(np.abs(Uk[pos[n]] - E).max()))
+        smax = max(smax, float(np.abs(E).max()))
+    print(f"graded_N1023_Nt4096: {st.iters} refinement steps, error {emax / smax:.2e} of max|u|")
+    assert emax <= 1e-8 * smax, emax / smax

@@ -44,6 +44,8 @@ CASES = [
     (1024, 1024, 1024, 1, 0, 1, 1),
     (128, 384, 384, 3, 2, 3, 12),
     (128, 256, 64, 2, 0, 1, 2),
+    (64, 256, 256, 5, 0, 1, 5),      # CTA pairs over 64-row slices; the last pair half past the end
+    (256, 128, 128, 3, 1, 1, 5),     # CTA pairs with 128-column tiles (64 matrix rows per CTA)
 ]
 
 
@@ -73,3 +75,26 @@ def test_tc_slice_gemm(kind, R, C, Cout, batch, s0, ds, nslices):
         tol = 2e-3 * scale + 1e-6
     bad = (out - ref).abs() > tol
     assert not bool(bad.any()), f"{int(bad.sum())} mismatches, max err {(out - ref).abs().max().item():.3e}"
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable():
+    """Failure detection in the allowed form: the tensor-core kernels' bounded mbarrier wait, given a
+    1 ms limit, on a barrier nothing arrives at (no copy or product in flight), gives up, records its
+    error code and returns; the library reports SFDE_ETIMEOUT and the context keeps working."""
+    import ctypes as C
+    import paper_1805_06688_gb300 as sfde
+    from sfde_workloads import time_grid
+    L = sfde.lib()
+    L.sfde_debug_wait_timeout.argtypes = [C.c_ulonglong, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    err, waited = C.c_int(0), C.c_double(0.0)
+    st = L.sfde_debug_wait_timeout(1000000, C.byref(err), C.byref(waited))
+    assert st == sfde.SFDE_ETIMEOUT
+    assert err.value == 1                      # the error code of a full-barrier wait
+    assert 1e-3 <= waited.value < 0.5, waited.value
+    assert L.sfde_debug_wait_timeout(10, None, None) == sfde.SFDE_EINVAL
+    # the context is clean: a solve afterwards runs and converges
+    P = sfde.Problem(0.7, 0.8, 1.0, 1.0, 16, 16, time_grid(32), precision=sfde.PREC_MIXED_BF16)
+    P.set_initial(np.ones((16, 16)))
+    _, stats = P.mgrit(m=4, rel_tol=1e-9, max_iter=40)
+    assert stats.converged
+    assert torch.cuda.is_available() and torch.zeros(4, device="cuda").sum().item() == 0.0
