@@ -269,14 +269,15 @@ KERNEL_CLASSES = (  # the library's accounting classes (include/sfde.h, sfde_pro
 )
 
 
-def roofline_from_profile(prof, tf32: bool):
+def roofline_from_profile(prof, lp_kind: int):
     """Roofline of the kernel class with the largest device time, plus a per-class breakdown.
 
     Each class's launches are timed with CUDA events inside one solve of well under a second, so the
     denominators are the measured burst rates.  FP64 SIMT GEMMs are bound by the FP64 pipe
     (measured BF16 x nominal FP64/BF16); tensor-core kernels are placed by algorithmic intensity
     against the ridge point (below it: HBM bandwidth, above it: the tensor pipe of their dtype, TF32
-    at half the BF16 rate); the integer assembly kernels move bytes only."""
+    at half the BF16 rate, an FP32 product of the three-product form at a sixth: three TF32 products);
+    the integer assembly kernels move bytes only."""
     pk, src = peaks()
     bf16 = pk["bf16_tflops"]
     fp64_peak = bf16 * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
@@ -289,7 +290,7 @@ def roofline_from_profile(prof, tf32: bool):
             continue
         tfs = fl / (ms * 1e-3) / 1e12
         gbs = by / (ms * 1e-3) / 1e9
-        tc_peak = bf16 * (0.5 if (k == 2 and tf32) else 1.0)
+        tc_peak = bf16 * ({1: 0.5, 2: 0.5 / 3.0}.get(lp_kind, 1.0) if k == 2 else 1.0)
         if kind == "alu":
             bound, ach, peak, unit = "alu", tfs, fp64_peak, "TFLOP/s"
             psrc = f"{src} burst BF16 {bf16} TFLOP/s x nominal FP64/BF16 {NOMINAL_FP64_TFLOPS}/{NOMINAL_BF16_TFLOPS}"
@@ -298,7 +299,9 @@ def roofline_from_profile(prof, tf32: bool):
             psrc = f"{src} HBM copy bandwidth"
         else:
             bound, ach, peak, unit = "tensor", tfs, tc_peak, "TFLOP/s"
-            psrc = f"{src} burst BF16 dense" + (" x 1/2 (TF32 nominal ratio)" if tc_peak < bf16 else "")
+            psrc = f"{src} burst BF16 dense" + ({1: " x 1/2 (TF32 nominal ratio)",
+                                                   2: " x 1/2 (TF32 nominal ratio) / 3 (TF32 products per FP32 product)"}
+                                                  .get(lp_kind, "") if k == 2 else "")
         kernels.append({
             "kernel": name, "what": what, "launches": int(n), "ms": ms, "share": None,
             "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
@@ -361,8 +364,8 @@ def run_ours(args, w):
         build()
 
     stream = torch.cuda.current_stream(dev)
-    prec = {"fp64": sfde.PREC_FP64, "mixed-bf16": sfde.PREC_MIXED_BF16,
-            "mixed-tf32": sfde.PREC_MIXED_TF32, "mixed-auto": sfde.PREC_MIXED_AUTO}[args.precision]
+    prec = {"fp64": sfde.PREC_FP64, "mixed-bf16": sfde.PREC_MIXED_BF16, "mixed-tf32": sfde.PREC_MIXED_TF32,
+            "mixed-fp32": sfde.PREC_MIXED_FP32, "mixed-auto": sfde.PREC_MIXED_AUTO}[args.precision]
     t = w.t()
     psi = w.initial()
     forcing = w.forcing()
@@ -417,7 +420,7 @@ def run_ours(args, w):
     P.mgrit(U_T=UT, **kw)
     prof = P.profile_read()
     P.profile_enable(False)
-    roofline, kernels = roofline_from_profile(prof, stats.lp_kind == 1)
+    roofline, kernels = roofline_from_profile(prof, stats.lp_kind)
 
     # end to end through the C ABI with host buffers: psi_0 and the load factors host -> device,
     # u(T) device -> host, every step
@@ -473,7 +476,7 @@ def run_ours(args, w):
     comparators["work_ratio_note"] = (
         "MGRIT does about 2 m/(m-1) step solves per time point per V-cycle on top of sequential stepping's one; "
         "compare the speed-ups above with that")
-    dtype = "f64" if prec == sfde.PREC_FP64 else ("tf32+f64" if stats.lp_kind == 1 else "bf16+f64")
+    dtype = "f64" if prec == sfde.PREC_FP64 else ["bf16+f64", "tf32+f64", "fp32(3xtf32)+f64"][stats.lp_kind]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -481,7 +484,8 @@ def run_ours(args, w):
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nt": w.nt, "beta": w.beta,
                    "gamma": w.gamma, "kx": w.kx, "ky": w.ky, "m": w.m, "rel_tol": REL_TOL,
                    "stop": "FP64 space-time residual of Eq. (2.4), relative to the initial guess's",
-                   "precision": args.precision, "operands": ["bf16", "tf32"][stats.lp_kind] if stats.lp_kind >= 0 else "fp64",
+                   "precision": args.precision,
+                   "operands": ["bf16", "tf32", "fp32 (3 tf32 products)"][stats.lp_kind] if stats.lp_kind >= 0 else "fp64",
                    "iters": stats.iters, "levels": stats.levels, "inner_vcycles": stats.inner_vcycles,
                    "coarse": ["cn", "be"][stats.coarse_used], "step_solves": stats.step_solves,
                    "tuning": tuning,
@@ -519,8 +523,8 @@ def run_batch(args):
         from paper_1805_06688_gb300.build import build
         build()
     ws = batch_workloads(0, 64)
-    pname = "mixed-auto" if args.precision == "mixed-bf16" else args.precision
-    prec = {"mixed-bf16": sfde.PREC_MIXED_BF16, "mixed-tf32": sfde.PREC_MIXED_TF32,
+    pname = args.precision
+    prec = {"mixed-bf16": sfde.PREC_MIXED_BF16, "mixed-tf32": sfde.PREC_MIXED_TF32, "mixed-fp32": sfde.PREC_MIXED_FP32,
             "mixed-auto": sfde.PREC_MIXED_AUTO}[pname]
     t0 = time.perf_counter()
     probs = []
@@ -529,7 +533,7 @@ def run_batch(args):
         P.set_initial(w.initial())
         probs.append(P)
     setup_s = time.perf_counter() - t0
-    kw = dict(m=8, max_levels=32, coarse=sfde.COARSE_AUTO, rel_tol=1e-8, max_iter=400)
+    kw = dict(m=8, max_levels=32, coarse=sfde.COARSE_AUTO, rel_tol=REL_TOL, max_iter=400, stop_kind=sfde.STOP_SFORM)
     dofs = sum(w.space_time_updates for w in ws)
     for _ in range(args.warmup):
         sfde.batch_solve(probs, **kw)
@@ -563,7 +567,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed-bf16", "mixed-tf32", "mixed-auto"], default="mixed-auto")
+    ap.add_argument("--precision", choices=["fp64", "mixed-bf16", "mixed-tf32", "mixed-fp32", "mixed-auto"],
+                    default="mixed-auto")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-comparator", action="store_true")

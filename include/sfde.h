@@ -54,7 +54,12 @@ typedef enum {
     SFDE_PREC_MIXED_BF16 = 1,  /* inner V-cycles on BF16 tensor cores (FP32 accumulate), FP64
                                   space-time residual and iterative refinement                    */
     SFDE_PREC_MIXED_TF32 = 2,  /* as above with TF32 operands                                     */
-    SFDE_PREC_MIXED_AUTO = 3   /* BF16 where the fused BF16 step applies (padded P_x = P_y in
+    SFDE_PREC_MIXED_FP32 = 3,  /* as above with FP32 operands and levels: every product formed from
+                                  three TF32 tensor-core products (high and low parts of both
+                                  operands, about 2^-20 relative), three times the tensor work of
+                                  TF32 for corrections about 2^10 times more accurate, so fewer
+                                  refinement steps (no counterpart in the paper)                 */
+    SFDE_PREC_MIXED_AUTO = 4   /* BF16 where the fused BF16 step applies (padded P_x = P_y in
                                   {128, 256}) and N_t <= 1024, else TF32: the low-precision fixed
                                   point drifts with the rounding accumulated over N_t nearly undamped
                                   steps, and TF32 rounds 4x finer (no counterpart in the paper) */
@@ -127,7 +132,7 @@ typedef struct {
     uint64_t init_seed;  /* 0: zero initial guess; else SplitMix64 uniform[-1,1) values at
                             t_1..t_N, value index (n*N_y + j)*N_x + i (Sec. 3.2)              */
     int inner_cycles;    /* mixed precision only: low-precision V-cycles per FP64 refinement step
-                            (0 = default: 4 for BF16, 5 for TF32)                             */
+                            (0 = default: 4 for BF16, 5 for TF32, 3 for FP32)                 */
     int skip_first_down; /* 1: the option "skip work on the first down cycle" (Sec. 3.2): the first
                             V-cycle relaxes on no level on its way down -- the coarse right-hand
                             side is the injected C-point residual of the initial guess -- and runs
@@ -157,7 +162,8 @@ typedef struct {
     long long step_solves;      /* fine/coarse step applications executed, all levels       */
     long long inner_vcycles;    /* low-precision V-cycles (mixed precision only)             */
     double history[SFDE_HISTORY_MAX];  /* residual norm per iteration                         */
-    int lp_kind;          /* operand type of the low-precision steps: 0 BF16, 1 TF32; -1 FP64 form */
+    int lp_kind;          /* operand type of the low-precision steps: 0 BF16, 1 TF32, 2 FP32 (three
+                             TF32 products); -1 FP64 form                                     */
 } mgrit_stats;
 
 /*

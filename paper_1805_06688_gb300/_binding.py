@@ -12,7 +12,7 @@ library_path = os.path.join(HERE, "libsfde.so")
 (SFDE_OK, SFDE_EINVAL, SFDE_ENOMEM, SFDE_ECUDA, SFDE_ENOCONV, SFDE_ETIMEOUT, SFDE_EUNSUPPORTED,
  SFDE_ESCRATCH) = range(8)
 NOALLOC_SCRATCH_DOUBLES = 5 * 262144
-PREC_FP64, PREC_MIXED_BF16, PREC_MIXED_TF32, PREC_MIXED_AUTO = 0, 1, 2, 3
+PREC_FP64, PREC_MIXED_BF16, PREC_MIXED_TF32, PREC_MIXED_FP32, PREC_MIXED_AUTO = 0, 1, 2, 3, 4
 RELAX_FCF, RELAX_F = 0, 1
 COARSE_CN, COARSE_BE, COARSE_AUTO = 0, 1, 2
 HISTORY_MAX = 512

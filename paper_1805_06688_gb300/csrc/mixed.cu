@@ -31,11 +31,17 @@ void sfde_launch_fill_random(double* u, int nt, int ny, int nx, int Py, int Px, 
 
 namespace {
 
+// Storage of the low-precision levels by operand kind: BF16 (kind 0); FP32 rounded to TF32, the
+// values the TF32 tensor cores read (kind 1); FP32 (kind 2, the three-product FP32 form), a 4-byte
+// type of its own so that every kernel below stores it without the TF32 rounding.
+struct F32 { float v; };
 template <typename T> __device__ __forceinline__ T to_lp(double v);
 template <> __device__ __forceinline__ __nv_bfloat16 to_lp<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
 template <> __device__ __forceinline__ float to_lp<float>(double v) { return sfde_round_tf32((float)v); }
+template <> __device__ __forceinline__ F32 to_lp<F32>(double v) { return F32{(float)v}; }
 __device__ __forceinline__ float lp_f(__nv_bfloat16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ float lp_f(float v) { return v; }
+__device__ __forceinline__ float lp_f(F32 v) { return v.v; }
 
 template <typename T>
 __global__ void k_to_lp(const double* src, T* dst, size_t n) {
@@ -77,7 +83,7 @@ __global__ void k_add_correction(double* U, const T* E, size_t n) {
             x0 = __uint_as_float(w.x << 16); x1 = __uint_as_float(w.x & 0xFFFF0000u);
             x2 = __uint_as_float(w.y << 16); x3 = __uint_as_float(w.y & 0xFFFF0000u);
         } else {
-            const float4 w = __ldg((const float4*)(E + 4 * e));
+            const float4 w = __ldg((const float4*)(const void*)(E + 4 * e));
             x0 = w.x; x1 = w.y; x2 = w.z; x3 = w.w;
         }
         a.x += (double)x0; a.y += (double)x1; b.x += (double)x2; b.y += (double)x3;
@@ -96,6 +102,7 @@ __device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
     const float4 w = *(const float4*)p;
     v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
 }
+__device__ __forceinline__ void ld4(const F32* p, float (&v)[4]) { ld4((const float*)p, v); }
 __device__ __forceinline__ void st4(__nv_bfloat16* p, const float (&v)[4]) {
     const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
     uint2 w;
@@ -106,6 +113,7 @@ __device__ __forceinline__ void st4(__nv_bfloat16* p, const float (&v)[4]) {
 __device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
     *(float4*)p = make_float4(sfde_round_tf32(v[0]), sfde_round_tf32(v[1]), sfde_round_tf32(v[2]), sfde_round_tf32(v[3]));
 }
+__device__ __forceinline__ void st4(F32* p, const float (&v)[4]) { *(float4*)p = make_float4(v[0], v[1], v[2], v[3]); }
 
 // F-relaxation over intervals of `len` points in the eigenbasis of the step.  Phi(X) = V_y [f o
 // (W_y^T X W_x)] V_x^T with W^T V = I (Sec. 2's fast diagonalisation), so u_{il+j} =
@@ -186,6 +194,9 @@ struct SfdeMixed {
     CUtensorMap mWTx, mWTy, mVx, mVy, mVTx, mVTy;
     // the same matrices as the fixed operand of the slice GEMM (its tile rows per box)
     CUtensorMap gWTx, gWTy, gVx, gVy, gVTx, gVTy;
+    // kind 2: their low parts (FP32 products from three TF32 products) and maps
+    void *lWTx = nullptr, *lWTy = nullptr, *lVx = nullptr, *lVy = nullptr, *lVTx = nullptr, *lVTy = nullptr;
+    CUtensorMap oWTx, oWTy, oVx, oVy, oVTx, oVTy;
     // the same matrices in 128-row boxes: the pair form of the fused step (P = 256)
     bool pair_ok = false;
     int nsm = 0;
@@ -220,6 +231,7 @@ void sfde_free_mixed(sfde_ctx* c) {
     SfdeMixed* M = c->mixed;
     if (!M) return;
     cudaFree(M->WTx); cudaFree(M->WTy); cudaFree(M->Vx); cudaFree(M->Vy); cudaFree(M->VTx); cudaFree(M->VTy);
+    cudaFree(M->lWTx); cudaFree(M->lWTy); cudaFree(M->lVx); cudaFree(M->lVy); cudaFree(M->lVTx); cudaFree(M->lVTy);
     cudaFree(M->lamx); cudaFree(M->lamy);
     for (auto& L : M->lev) {
         if (L.own_dt) cudaFree(L.dt);
@@ -244,9 +256,18 @@ sfde_status lp_copy(sfde_ctx* c, const double* src, void** dst, size_t n, int ki
     const size_t esz = kind == 0 ? 2 : 4;
     SFDE_CUDA(cudaMalloc(dst, esz * n));
     if (kind == 0) k_to_lp<__nv_bfloat16><<<grid_for(n), 256, 0, c->stream>>>(src, (__nv_bfloat16*)*dst, n);
-    else k_to_lp<float><<<grid_for(n), 256, 0, c->stream>>>(src, (float*)*dst, n);
+    else if (kind == 1) k_to_lp<float><<<grid_for(n), 256, 0, c->stream>>>(src, (float*)*dst, n);
+    else k_to_lp<F32><<<grid_for(n), 256, 0, c->stream>>>(src, (F32*)*dst, n);
     sfde_count_launch(c);
     SFDE_CUDA(cudaGetLastError());
+    return SFDE_OK;
+}
+
+// kind 2: the low parts of an FP32 operand copy (the third product of the FP32 form)
+sfde_status lo_copy(sfde_ctx* c, const void* src, void** dst, size_t n) {
+    SFDE_CUDA(cudaMalloc(dst, sizeof(float) * n));
+    SFDE_TRY(sfde_tc_lo_parts((const float*)src, (float*)*dst, n, c->stream));
+    sfde_count_launch(c);
     return SFDE_OK;
 }
 
@@ -338,6 +359,20 @@ sfde_status setup_mixed_body(sfde_ctx* c, int kind, int m, int max_levels, int m
     SFDE_TRY(sfde_tc_map_gemm_matrix(&M->gVy, M->Vy, M->kind, Py, Py));
     SFDE_TRY(sfde_tc_map_gemm_matrix(&M->gVTx, M->VTx, M->kind, Px, Px));
     SFDE_TRY(sfde_tc_map_gemm_matrix(&M->gVTy, M->VTy, M->kind, Py, Py));
+    if (kind == 2) {
+        SFDE_TRY(lo_copy(c, M->WTx, &M->lWTx, (size_t)Px * Px));
+        SFDE_TRY(lo_copy(c, M->WTy, &M->lWTy, (size_t)Py * Py));
+        SFDE_TRY(lo_copy(c, M->Vx, &M->lVx, (size_t)Px * Px));
+        SFDE_TRY(lo_copy(c, M->Vy, &M->lVy, (size_t)Py * Py));
+        SFDE_TRY(lo_copy(c, M->VTx, &M->lVTx, (size_t)Px * Px));
+        SFDE_TRY(lo_copy(c, M->VTy, &M->lVTy, (size_t)Py * Py));
+        SFDE_TRY(sfde_tc_map_gemm_matrix(&M->oWTx, M->lWTx, 2, Px, Px));
+        SFDE_TRY(sfde_tc_map_gemm_matrix(&M->oWTy, M->lWTy, 2, Py, Py));
+        SFDE_TRY(sfde_tc_map_gemm_matrix(&M->oVx, M->lVx, 2, Px, Px));
+        SFDE_TRY(sfde_tc_map_gemm_matrix(&M->oVy, M->lVy, 2, Py, Py));
+        SFDE_TRY(sfde_tc_map_gemm_matrix(&M->oVTx, M->lVTx, 2, Px, Px));
+        SFDE_TRY(sfde_tc_map_gemm_matrix(&M->oVTy, M->lVTy, 2, Py, Py));
+    }
     M->pair_ok = kind == 0 && Px == Py && sfde_fused_pair_supported(Px);
     if (M->pair_ok) {
         SFDE_TRY(sfde_tc_map_matrix_rows(&M->hWTx, M->WTx, M->esz, Px, Px, 128));
@@ -484,7 +519,7 @@ struct LpEngine {
             // G1: (X W_x)^T  or  (X V_x)^T
             p.R = Py; p.C = Px; p.Cout = Px; p.BN = sfde_tc_tile_n(Px); p.s0 = src0 + b0 * ds; p.ds = ds;
             p.out = M->T1; p.out_stride = P2l;
-            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a1, solve ? M->gVTx : M->gWTx, p, c->stream, c->y.n, c->x.n, c->x.n));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a1, solve ? M->gVTx : M->gWTx, p, c->stream, c->y.n, c->x.n, c->x.n, M->kind == 2 ? (solve ? &M->oVTx : &M->oWTx) : nullptr));
             // G2: modal scaling
             TcArgs q{};
             q.batch = nb; q.err = M->err;
@@ -492,13 +527,13 @@ struct LpEngine {
             q.out = M->T2; q.out_stride = P2l;
             q.e.lamx = M->lamx; q.e.lamy = M->lamy; q.e.kx = (float)c->kx; q.e.ky = (float)c->ky;
             q.e.dt = dt; q.e.n0 = n0 + b0 * dn; q.e.dn = dn; q.e.scheme = solve ? SCHEME_SOLVE : sch;
-            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_SCALE, a2, solve ? M->gVTy : M->gWTy, q, c->stream, c->x.n, c->y.n, c->y.n));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_SCALE, a2, solve ? M->gVTy : M->gWTy, q, c->stream, c->x.n, c->y.n, c->y.n, M->kind == 2 ? (solve ? &M->oVTy : &M->oWTy) : nullptr));
             // G3: (C V_x^T)^T
             TcArgs r{};
             r.batch = nb; r.err = M->err;
             r.R = Py; r.C = Px; r.Cout = Px; r.BN = sfde_tc_tile_n(Px); r.s0 = 0; r.ds = 1;
             r.out = M->T3; r.out_stride = P2l;
-            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a3, M->gVx, r, c->stream, c->y.n, c->x.n, c->x.n));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a3, M->gVx, r, c->stream, c->y.n, c->x.n, c->x.n, M->kind == 2 ? &M->oVx : nullptr));
             // G4: (T3 V_y^T)^T + g - u_target
             TcArgs f{};
             f.batch = nb; f.err = M->err;
@@ -513,7 +548,7 @@ struct LpEngine {
             const int ppt = sfde_tc_partials_per_tile();
             if (partial && (size_t)(total + ppt * gx * gy) > c->partial_cap) return SFDE_EINVAL;
             f.e.partial = partial ? partial + total : nullptr;
-            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_FINAL, a4, M->gVy, f, c->stream, c->x.n, c->y.n, c->y.n));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_FINAL, a4, M->gVy, f, c->stream, c->x.n, c->y.n, c->y.n, M->kind == 2 ? &M->oVy : nullptr));
             total += ppt * gx * gy;
         }
         steps += batch;
@@ -535,12 +570,12 @@ struct LpEngine {
             p.batch = nb; p.err = M->err;
             p.R = Py; p.C = Px; p.Cout = Px; p.BN = sfde_tc_tile_n(Px); p.s0 = src0 + b0 * ds; p.ds = ds;
             p.out = M->T1; p.out_stride = P2l;
-            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a1, M->gWTx, p, c->stream, c->y.n, c->x.n, c->x.n));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a1, M->gWTx, p, c->stream, c->y.n, c->x.n, c->x.n, M->kind == 2 ? &M->oWTx : nullptr));
             TcArgs q{};   // (T1 W_y)^T = W_y^T X W_x
             q.batch = nb; q.err = M->err;
             q.R = Px; q.C = Py; q.Cout = Py; q.BN = sfde_tc_tile_n(Py); q.s0 = 0; q.ds = 1;
             q.out = slice(dst, (long long)b0 * dst_ds); q.out_stride = (long long)dst_ds * P2l;
-            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a2, M->gWTy, q, c->stream, c->x.n, c->y.n, c->y.n));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a2, M->gWTy, q, c->stream, c->x.n, c->y.n, c->y.n, M->kind == 2 ? &M->oWTy : nullptr));
         }
         return SFDE_OK;
     }
@@ -562,14 +597,14 @@ struct LpEngine {
             r.batch = nb; r.err = M->err;
             r.R = Py; r.C = Px; r.Cout = Px; r.BN = sfde_tc_tile_n(Px); r.s0 = b0; r.ds = 1;
             r.out = M->T3; r.out_stride = P2l;
-            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a3, M->gVx, r, c->stream, c->y.n, c->x.n, c->x.n));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a3, M->gVx, r, c->stream, c->y.n, c->x.n, c->x.n, M->kind == 2 ? &M->oVx : nullptr));
             TcArgs f{};   // (T3 V_y^T)^T = V_y Y V_x^T
             f.batch = nb; f.err = M->err;
             f.R = Px; f.C = Py; f.Cout = Py; f.BN = sfde_tc_tile_n(Py); f.s0 = 0; f.ds = 1;
             f.out = slice(dst, oskip > 0 ? (long long)b0 + b0 / oskip : (long long)b0);
             f.out_stride = P2l;
             f.oskip = oskip;
-            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a4, M->gVy, f, c->stream, c->x.n, c->y.n, c->y.n));
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a4, M->gVy, f, c->stream, c->x.n, c->y.n, c->y.n, M->kind == 2 ? &M->oVy : nullptr));
         }
         return SFDE_OK;
     }
@@ -583,10 +618,14 @@ struct LpEngine {
             k_modal_scan<__nv_bfloat16><<<grid, 256, 0, c->stream>>>(
                 (const __nv_bfloat16*)Uc, (const __nv_bfloat16*)G, gis, gj0, (__nv_bfloat16*)Y, len, c->x.P, P2s, M->lamx,
                 M->lamy, (float)c->kx, (float)c->ky, dt, dis, sch);
-        else
+        else if (M->kind == 1)
             k_modal_scan<float><<<grid, 256, 0, c->stream>>>((const float*)Uc, (const float*)G, gis, gj0, (float*)Y, len,
                                                              c->x.P, P2s, M->lamx, M->lamy, (float)c->kx,
                                                              (float)c->ky, dt, dis, sch);
+        else
+            k_modal_scan<F32><<<grid, 256, 0, c->stream>>>((const F32*)Uc, (const F32*)G, gis, gj0, (F32*)Y, len, c->x.P,
+                                                           P2s, M->lamx, M->lamy, (float)c->kx, (float)c->ky, dt, dis,
+                                                           sch);
         sfde_count_launch(c);
         SFDE_CUDA(cudaGetLastError());
         return SFDE_OK;
@@ -643,8 +682,10 @@ struct LpEngine {
         LpLevel& Cv = M->lev[l + 1];
         if (M->kind == 0)
             k_lp_diff<__nv_bfloat16><<<grid_for(P2()), 256, 0, c->stream>>>((__nv_bfloat16*)Cv.g, (const __nv_bfloat16*)Lv.g, (const __nv_bfloat16*)Lv.u, P2());
-        else
+        else if (M->kind == 1)
             k_lp_diff<float><<<grid_for(P2()), 256, 0, c->stream>>>((float*)Cv.g, (const float*)Lv.g, (const float*)Lv.u, P2());
+        else
+            k_lp_diff<F32><<<grid_for(P2()), 256, 0, c->stream>>>((F32*)Cv.g, (const F32*)Lv.g, (const F32*)Lv.u, P2());
         sfde_count_launch(c);
         return lstep(l, Lv.N / m, m - 1, m, m, m, slice(Cv.g, 1), 1, slice(Lv.u, m), partial, npart);
     }
@@ -676,8 +717,10 @@ struct LpEngine {
         dim3 grid(grid_for(P2()) < 64 ? grid_for(P2()) : 64, Cv.N + 1);
         if (M->kind == 0)
             k_lp_axpy_strided<__nv_bfloat16><<<grid, 256, 0, c->stream>>>((__nv_bfloat16*)Lv.u, (long long)m * P2(), (const __nv_bfloat16*)Cv.u, (long long)P2(), P2());
-        else
+        else if (M->kind == 1)
             k_lp_axpy_strided<float><<<grid, 256, 0, c->stream>>>((float*)Lv.u, (long long)m * P2(), (const float*)Cv.u, (long long)P2(), P2());
+        else
+            k_lp_axpy_strided<F32><<<grid, 256, 0, c->stream>>>((F32*)Lv.u, (long long)m * P2(), (const F32*)Cv.u, (long long)P2(), P2());
         sfde_count_launch(c);
         SFDE_CUDA(cudaGetLastError());
         return SFDE_OK;
@@ -731,7 +774,7 @@ sfde_status enqueue_inner_part(sfde_ctx* c, SfdeMixed* M, LpEngine& E, double* U
     const size_t n = P2 * (size_t)c->nt;
     if (kind == 0)
         k_add_correction<__nv_bfloat16><<<grid_for(n), 256, 0, c->stream>>>(U + P2, (const __nv_bfloat16*)E.slice(L0.u, 1), n);
-    else
+    else   // FP32 storage (kinds 1 and 2) read as FP32
         k_add_correction<float><<<grid_for(n), 256, 0, c->stream>>>(U + P2, (const float*)E.slice(L0.u, 1), n);
     sfde_count_launch(c);
     SFDE_CUDA(cudaGetLastError());
@@ -784,11 +827,12 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
     SFDE_TRY(sfde_choose_coarse(c, o->m, o->coarse, &coarse, &tub));
     LpEngine E{c, M, o->m, L, o->relax, coarse == SFDE_COARSE_CN ? SCHEME_CN : SCHEME_BE};
     // inner V-cycles per refinement step: enough for the inner error to reach the low-precision
-    // floor (about 2e-2 BF16, 3e-3 TF32) at MGRIT contraction ~0.3 per V-cycle.  (Raising K when the
+    // floor (about 2e-2 BF16, 3e-3 TF32) at MGRIT contraction ~0.3 per V-cycle; with FP32 products
+    // the floor is far lower and 3 V-cycles set the contraction.  (Raising K when the
     // refinement contracts slowly does not help: there the floor itself is high -- rounding
     // accumulated over long stiff runs -- and more V-cycles only add time.)
     const int K = o->inner_cycles > 0 ? o->inner_cycles
-                : c->inner_cycles_tuned > 0 ? c->inner_cycles_tuned : (kind == 0 ? 4 : 5);
+                : c->inner_cycles_tuned > 0 ? c->inner_cycles_tuned : (kind == 0 ? 4 : kind == 1 ? 5 : 3);
     // the inner solve is captured once as CUDA graphs and replayed; eager while kernels are timed
     const bool use_graph = !c->prof.on;
     const long long key = ((long long)o->skip_first_down << 32) | ((long long)c->modal_chains << 28) |
@@ -910,7 +954,8 @@ sfde_status load_lp(sfde_ctx* c, const double* in, int batch, double* tmp_unp, d
     sfde_launch_pad(tmp_unp, tmp_pad, c->y.n, c->x.n, c->y.P, c->x.P, batch, c->stream);
     const size_t n = P2 * batch;
     if (kind == 0) k_to_lp<__nv_bfloat16><<<grid_for(n), 256, 0, c->stream>>>(tmp_pad, (__nv_bfloat16*)out, n);
-    else k_to_lp<float><<<grid_for(n), 256, 0, c->stream>>>(tmp_pad, (float*)out, n);
+    else if (kind == 1) k_to_lp<float><<<grid_for(n), 256, 0, c->stream>>>(tmp_pad, (float*)out, n);
+    else k_to_lp<F32><<<grid_for(n), 256, 0, c->stream>>>(tmp_pad, (F32*)out, n);
     SFDE_CUDA(cudaGetLastError());
     return SFDE_OK;
 }

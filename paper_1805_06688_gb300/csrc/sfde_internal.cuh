@@ -227,11 +227,12 @@ struct FusedStepArgs {
     int* err;                             // device error word (bounded waits)
 };
 bool sfde_fused_supported(int kind, int Px, int Py);
-// low-precision operand kind of a mixed-precision context: 0 BF16, 1 TF32 (SFDE_PREC_MIXED_AUTO
-// resolved by size and length, see include/sfde.h)
+// low-precision operand kind of a mixed-precision context: 0 BF16, 1 TF32, 2 FP32 from three TF32
+// products (SFDE_PREC_MIXED_AUTO resolved by size and length, see include/sfde.h)
 inline int sfde_mixed_kind(const sfde_ctx* c) {
     if (c->precision == SFDE_PREC_MIXED_BF16) return 0;
     if (c->precision == SFDE_PREC_MIXED_TF32) return 1;
+    if (c->precision == SFDE_PREC_MIXED_FP32) return 2;
     return (sfde_fused_supported(0, c->x.P, c->y.P) && c->nt <= 1024) ? 0 : 1;
 }
 sfde_status sfde_fused_prepare();

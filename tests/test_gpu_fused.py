@@ -307,3 +307,35 @@ def test_step_elementwise_error_bound_against_oracle(scheme, nx, ny, batch, n0):
             r = np.abs(x[b] - ref[b]) / (u * B)
             worst = max(worst, float(r.max()))
         assert worst <= 10.0, (fused, worst)
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+@pytest.mark.parametrize("nx,ny,batch,n0", [(255, 255, 40, 30), (200, 230, 6, 1), (511, 300, 5, 2)])
+def test_fp32_step_elementwise_error_bound(scheme, nx, ny, batch, n0):
+    """The FP32 form's step (four slice GEMMs, each product from three TF32 products, FP32
+    intermediates) element by element against the oracle: the same first-order bound as for BF16 with
+    the unit roundoff of the FP32 products, u = 2^-20 (the dropped lo x lo term and the low parts read
+    as TF32), |x - x_oracle| <= 10 u B."""
+    nt = n0 + batch + 3
+    t = time_grid(nt, 1.0, "graded")
+    O = osfde.SFDE(0.7, 0.8, 1.0, 0.5, nx, ny, t)
+    P = sfde.Problem(0.7, 0.8, 1.0, 0.5, nx, ny, t, precision=sfde.PREC_MIXED_FP32)
+    rng = np.random.default_rng(nx * 13 + scheme)
+    U = rng.standard_normal((batch, ny, nx))
+    ref = oracle_step(O, scheme, U, n0)
+    st, x, _ = lp_step(P, 0, scheme, U, n0)
+    assert st == 0, sfde.sfde_strerror(st)
+    lx, Vx, ly, Vy = O.eig()
+    sig = O.sigma()
+    Lx, Ly = (O.Mx @ Vx, O.My @ Vy) if scheme < 2 else (Vx, Vy)
+    u = 2.0 ** -20
+    worst = 0.0
+    for b in range(batch):
+        dt = O.t[n0 + b] - O.t[n0 + b - 1]
+        f = (osfde.modal_lambda(sig, dt, "cn") if scheme == 0 else
+             osfde.modal_lambda(sig, dt, "be") if scheme == 1 else 1.0 / (1.0 + 0.5 * dt * sig))
+        B = np.abs(Vy) @ (np.abs(f) * (np.abs(Ly).T @ np.abs(U[b]) @ np.abs(Lx))) @ np.abs(Vx).T
+        worst = max(worst, float((np.abs(x[b] - ref[b]) / (u * B)).max()))
+    assert worst <= 10.0, worst
+    # and far below the TF32 form's error
+    assert rel_fro(x, ref).max() <= 2.0 ** -16, rel_fro(x, ref).max()

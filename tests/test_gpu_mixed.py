@@ -17,7 +17,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 import paper_1805_06688_gb300 as sfde  # noqa: E402
 
-PRECS = [("bf16", sfde.PREC_MIXED_BF16), ("tf32", sfde.PREC_MIXED_TF32)]
+PRECS = [("bf16", sfde.PREC_MIXED_BF16), ("tf32", sfde.PREC_MIXED_TF32), ("fp32", sfde.PREC_MIXED_FP32)]
 
 
 def _err(U, ref):

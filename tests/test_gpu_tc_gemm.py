@@ -49,9 +49,11 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 @pytest.mark.parametrize("R,C,Cout,batch,s0,ds,nslices", CASES)
 def test_tc_slice_gemm(kind, R, C, Cout, batch, s0, ds, nslices):
+    """kind 0: BF16 operands and output; 1: TF32 products, output rounded to TF32; 2: FP32 products
+    formed from three TF32 products (about 2^-20 relative each), FP32 output."""
     g = torch.Generator(device="cuda").manual_seed(R * 7 + C + Cout + batch + kind)
     dt = torch.bfloat16 if kind == 0 else torch.float32
     X = torch.randn((nslices, R, C), device="cuda", generator=g).to(dt)
@@ -61,7 +63,7 @@ def test_tc_slice_gemm(kind, R, C, Cout, batch, s0, ds, nslices):
     idx = torch.arange(batch, device="cuda") * ds + s0
     Xd = X[idx].double()
     Md = Mat.double()
-    if kind == 1:  # TF32 keeps 10 explicit mantissa bits
+    if kind == 1:  # TF32 keeps 10 explicit mantissa bits (kind 2 uses the FP32 values themselves)
         def tf32(t):
             i = t.float().view(torch.int32)
             return (i & ~0x1FFF).view(torch.float32).double()
@@ -71,8 +73,11 @@ def test_tc_slice_gemm(kind, R, C, Cout, batch, s0, ds, nslices):
     if kind == 0:
         # output is rounded to BF16: 2^-8 relative, plus FP32 accumulation
         tol = 2.0 ** -8 * ref.abs() + 1e-5 * scale
-    else:
+    elif kind == 1:
         tol = 2e-3 * scale + 1e-6
+    else:
+        # three-product FP32: 2^-19 of each product, FP32 accumulation over C terms, FP32 output
+        tol = (2.0 ** -19 + C * 2.0 ** -24) * scale + 2.0 ** -23 * ref.abs()
     bad = (out - ref).abs() > tol
     assert not bool(bad.any()), f"{int(bad.sum())} mismatches, max err {(out - ref).abs().max().item():.3e}"
 
