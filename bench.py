@@ -387,7 +387,7 @@ def run_ours(args, w):
     autotune_s = 0.0
     if prec != sfde.PREC_FP64 and not args.no_autotune:
         t0 = time.perf_counter()
-        tn = P.autotune(**kw)
+        tn = P.autotune(cache_path=args.tune_cache, **kw)
         autotune_s = time.perf_counter() - t0
         tuning = {"fused_pair": tn.fused_pair, "modal_chains": tn.modal_chains, "inner_cycles": tn.inner_cycles,
                   "ms": tn.ms, "seconds": autotune_s}
@@ -405,11 +405,13 @@ def run_ours(args, w):
     torch.cuda.synchronize(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")   # lets a profiler list the timed solves' launches alone
         ev0.record(stream)
         for _ in range(args.steps):
             _, stats = P.mgrit(U_T=UT, **kw)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
+        torch.cuda.nvtx.range_pop()
     barrier()
     launches = P.profile_read().kernel_launches
     value, sec = whole_job_rate(ev0.elapsed_time(ev1) * 1e-3 / args.steps, w.space_time_updates, world, dev)
@@ -573,6 +575,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-comparator", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tune-cache", default=None, help="autotuner cache file (a stored choice is applied untimed)")
     args = ap.parse_args()
     if args.workload == "batch64":
         return run_batch(args)

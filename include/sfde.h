@@ -120,7 +120,8 @@ typedef enum {
 } sfde_coarse;
 
 typedef struct {
-    int m;               /* coarsening factor, >= 2                                           */
+    int m;               /* coarsening factor, >= 2; 0: chosen per problem by the two-level analysis
+                            of Sec. 3.3 (see sfde_choose_coarsening)                          */
     int max_levels;      /* >= 1; levels are added while N_l % m == 0 and N_l/m >= min_coarse   */
     int min_coarse;      /* >= 1                                                              */
     int relax;           /* sfde_relax (Step 1 of Algorithm 1)                                */
@@ -164,7 +165,30 @@ typedef struct {
     double history[SFDE_HISTORY_MAX];  /* residual norm per iteration                         */
     int lp_kind;          /* operand type of the low-precision steps: 0 BF16, 1 TF32, 2 FP32 (three
                              TF32 products); -1 FP64 form                                     */
+    int m_used;           /* coarsening factor of the solve (the chosen one when opts.m was 0)   */
 } mgrit_stats;
+
+/*
+ * Two-level convergence analysis (Sec. 3.3), evaluated on the device over every mode of the
+ * problem.
+ *
+ * sfde_two_level_bound -- Theorem 3.1's bound, Eq. (3.11), for coarsening factor m and the coarse
+ * propagator `coarse` (SFDE_COARSE_CN: the paper's rediscretisation, Eq. (3.4); SFDE_COARSE_BE):
+ *   max over modes w of (lam+)^m |(lam+)^m - mu++| (1 - (mu*)^{N_c - 1}) / (1 - mu*),
+ * with the fine-step eigenvalues of Eq. (3.7) (lam+: their largest magnitude over the fine steps),
+ * the coarse propagator's (mu++: smallest, mu*: largest magnitude over the coarse steps),
+ * sigma_w = K_x lambda_x + K_y lambda_y from the setup's eigenvalues, N_c = N_t / m.
+ * SFDE_EINVAL unless m >= 2 divides N_t with N_t / m >= 2.  *bound is host memory.
+ *
+ * sfde_choose_coarsening -- the m that mgrit_solve uses when mgrit_opts.m is 0: among
+ * m in {2, 4, 8, 16, 32} dividing N_t with at least two coarse intervals, the least estimated work to
+ * rel_tol, taking the bound b(m) of the coarse propagator in use (`coarse` as in mgrit_opts; AUTO
+ * resolved per m) as the contraction per iteration: ceil(log rel_tol / log b(m)) iterations of about
+ * 2 m / (m - 1) step solves per time point.  Candidates with b(m) >= 1 are left out (all of them: the
+ * largest valid m); ties go to the larger m.
+ */
+sfde_status sfde_two_level_bound(sfde_ctx* ctx, int m, int coarse, double* bound);
+sfde_status sfde_choose_coarsening(sfde_ctx* ctx, int coarse, double rel_tol, int* m);
 
 /*
  * mgrit_solve -- Algorithm 1: V-cycles of FCF (or F) relaxation, injection of the C-point
@@ -212,6 +236,17 @@ sfde_status seq_timestep(sfde_ctx* ctx, double* U, double* U_T, double* seconds)
  */
 sfde_status sfde_step_batch(sfde_ctx* ctx, int n0, int dn, int batch, const double* in,
                             double* out);
+
+/*
+ * sfde_propagate_batch -- the coarse propagators of Algorithm 1 (Sec. 3.1) with a right-hand side,
+ * for `batch` fields with their own step sizes (coarse levels of a time-sharded V-cycle):
+ *   out[b] = Psi(dts[b]) in[b] + g[b],  Psi(dt) = (M_h + dt/2 K)^{-1} (M_h - dt/2 K)  (scheme
+ *   SFDE_COARSE_CN, Eq. (3.4)) or (M_h + dt K)^{-1} M_h  (SFDE_COARSE_BE); no load term.
+ * dts: host, batch step sizes > 0; in, g (may be NULL: zero), out: batch x N_y x N_x doubles, host or
+ * device, out not overlapping in or g.  Synchronous.  SFDE_EINVAL for another scheme or a step <= 0.
+ */
+sfde_status sfde_propagate_batch(sfde_ctx* ctx, int scheme, const double* dts, int batch, const double* in,
+                                 const double* g, double* out);
 
 /*
  * sfde_step_batch_noalloc -- the same computation as sfde_step_batch, without allocating any device

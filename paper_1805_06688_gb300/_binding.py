@@ -22,7 +22,7 @@ exported_symbols = (
     "sfde_setup", "sfde_set_initial", "sfde_set_forcing", "mgrit_solve", "seq_timestep",
     "sfde_step_batch", "sfde_step_batch_noalloc", "sfde_get_operator", "sfde_profile_enable", "sfde_profile_read",
     "sfde_destroy", "sfde_strerror", "sfde_batch_solve", "sfde_set_tuning", "sfde_autotune",
-    "sfde_set_forcing_dense",
+    "sfde_set_forcing_dense", "sfde_two_level_bound", "sfde_choose_coarsening", "sfde_propagate_batch",
 )
 
 
@@ -62,7 +62,7 @@ class MgritStats(C.Structure):
                 ("coarse_used", C.c_int), ("res0", C.c_double), ("res_final", C.c_double),
                 ("conv_factor_last5", C.c_double), ("seconds", C.c_double), ("tub", C.c_double),
                 ("step_solves", C.c_longlong), ("inner_vcycles", C.c_longlong),
-                ("history", C.c_double * HISTORY_MAX), ("lp_kind", C.c_int)]
+                ("history", C.c_double * HISTORY_MAX), ("lp_kind", C.c_int), ("m_used", C.c_int)]
 
     def residual_history(self):
         return [self.history[i] for i in range(min(self.iters, HISTORY_MAX))]
@@ -85,10 +85,13 @@ def lib() -> C.CDLL:
         L.sfde_set_initial.argtypes = [vp, vp]
         L.sfde_set_forcing.argtypes = [vp, ip, vp, vp, vp]
         L.sfde_set_forcing_dense.argtypes = [vp, vp]
+        L.sfde_two_level_bound.argtypes = [vp, ip, ip, dp]
+        L.sfde_choose_coarsening.argtypes = [vp, ip, C.c_double, C.POINTER(ip)]
         L.mgrit_solve.argtypes = [vp, C.POINTER(MgritOpts), vp, vp, C.POINTER(MgritStats)]
         L.seq_timestep.argtypes = [vp, vp, vp, dp]
         L.sfde_step_batch.argtypes = [vp, ip, ip, ip, vp, vp]
         L.sfde_step_batch_noalloc.argtypes = [vp, ip, ip, ip, vp, vp]
+        L.sfde_propagate_batch.argtypes = [vp, ip, dp, ip, vp, vp, vp]
         L.sfde_get_operator.argtypes = [vp, ip, vp, vp, vp]
         L.sfde_profile_enable.argtypes = [vp, ip]
         L.sfde_profile_read.argtypes = [vp, C.POINTER(SfdeProfile)]
@@ -257,6 +260,18 @@ def sfde_step_batch(ctx, n0, dn, batch, src, dst):
                   "sfde_step_batch")
 
 
+def sfde_propagate_batch(ctx, scheme, dts, src, dst, g=None):
+    """dst[b] = Psi(dts[b]) src[b] + g[b] (coarse propagator CN or BE, no load); src, g, dst: at least
+    len(dts) x N_y x N_x doubles each (ValueError otherwise, before any call into the library)."""
+    dts = np.ascontiguousarray(dts, dtype=np.float64)
+    batch = len(dts)
+    _check_step_buffers(ctx, batch, src, dst, False, "sfde_propagate_batch")
+    if g is not None:
+        _check_step_buffers(ctx, batch, g, dst, False, "sfde_propagate_batch")
+    return _check(lib().sfde_propagate_batch(ctx, int(scheme), dts.ctypes.data_as(C.POINTER(C.c_double)), batch,
+                                             _ptr(src), _ptr(g), _ptr(dst)), "sfde_propagate_batch")
+
+
 def sfde_step_batch_noalloc(ctx, n0, dn, batch, src, dst):
     """Queue the batched step on the context's stream using the library's fixed device scratch
     (no device allocation).  src and dst: CUDA tensors on the current device holding at least
@@ -341,6 +356,19 @@ class Problem:
         bx = np.ascontiguousarray(forcing.bx, dtype=np.float64)
         by = np.ascontiguousarray(forcing.by, dtype=np.float64)
         sfde_set_forcing(self.ctx, tw.shape[1], tw, bx, by)
+
+    def two_level_bound(self, m, coarse=COARSE_CN):
+        """Theorem 3.1's bound (Eq. (3.11)) for coarsening factor m, evaluated on the device."""
+        b = C.c_double()
+        _check(lib().sfde_two_level_bound(self.ctx, int(m), int(coarse), C.byref(b)), "sfde_two_level_bound")
+        return b.value
+
+    def choose_coarsening(self, coarse=COARSE_AUTO, rel_tol=1e-10):
+        """The coarsening factor mgrit uses with m = 0."""
+        m = C.c_int()
+        _check(lib().sfde_choose_coarsening(self.ctx, int(coarse), float(rel_tol), C.byref(m)),
+               "sfde_choose_coarsening")
+        return m.value
 
     def set_forcing_dense(self, F):
         """F: (N_t, N_y, N_x) array of load vectors (host or device), or None."""

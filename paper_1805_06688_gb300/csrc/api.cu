@@ -95,6 +95,7 @@ static void free_ctx(sfde_ctx* c) {
     cudaFree(c->dt0); cudaFree(c->U0); cudaFree(c->time_w); cudaFree(c->px); cudaFree(c->py);
     cudaFree(c->bxn); cudaFree(c->byn); cudaFree(c->Fd); cudaFree(c->Fh);
     cudaFree(c->T1); cudaFree(c->T2); cudaFree(c->T3); cudaFree(c->partial); cudaFree(c->scalar);
+    cudaFree(c->bound_partial);
     if (c->host_scalar) cudaFreeHost(c->host_scalar);
     if (c->prof.ev[0])
         for (int i = 0; i < 2 * SfdeProf::CAP; ++i) cudaEventDestroy(c->prof.ev[i]);
@@ -330,17 +331,19 @@ static sfde_status mgrit_solve_impl(sfde_ctx* c, const mgrit_opts* opts, double*
         o.coarse = SFDE_COARSE_AUTO; o.max_iter = 100; o.rel_tol = 1e-10; o.abs_tol = 0.0; o.init_seed = 0;
         o.inner_cycles = 0; o.skip_first_down = 0; o.stop_kind = 0;
     }
-    if (o.m < 2 || o.max_levels < 1 || o.min_coarse < 1 || o.max_iter < 1) return SFDE_EINVAL;
+    if ((o.m != 0 && o.m < 2) || o.max_levels < 1 || o.min_coarse < 1 || o.max_iter < 1) return SFDE_EINVAL;
     if (o.relax != SFDE_RELAX_FCF && o.relax != SFDE_RELAX_F) return SFDE_EINVAL;
     if (o.coarse < SFDE_COARSE_CN || o.coarse > SFDE_COARSE_AUTO) return SFDE_EINVAL;
     if (!(o.rel_tol >= 0.0) || !(o.abs_tol >= 0.0) || o.inner_cycles < 0) return SFDE_EINVAL;
     if (o.skip_first_down != 0 && o.skip_first_down != 1) return SFDE_EINVAL;
     if (o.stop_kind != 0 && o.stop_kind != 1) return SFDE_EINVAL;
+    if (o.m == 0) SFDE_TRY(sfde_choose_m(c, o.coarse, o.rel_tol, &o.m));   // two-level analysis picks m
     sfde_status st;
     if (c->precision == SFDE_PREC_FP64)
         st = sfde_mgrit_fp64(c, &o, stats);
     else
         st = sfde_mgrit_mixed(c, &o, stats);
+    if (stats) stats->m_used = o.m;
     if (st != SFDE_OK && st != SFDE_ENOCONV) return st;
     sfde_status wo = write_outputs(c, U, U_T);
     return wo != SFDE_OK ? wo : st;
@@ -397,6 +400,57 @@ done:
 
 sfde_status sfde_step_batch(sfde_ctx* c, int n0, int dn, int batch, const double* in, double* out) {
     return sfde_no_throw([&] { return step_batch_impl(c, n0, dn, batch, in, out); });
+}
+
+static sfde_status propagate_batch_impl(sfde_ctx* c, int scheme, const double* dts, int batch, const double* in,
+                                        const double* g, double* out) {
+    if (!c || !dts || !in || !out || batch < 1 || (scheme != SFDE_COARSE_CN && scheme != SFDE_COARSE_BE))
+        return SFDE_EINVAL;
+    for (int b = 0; b < batch; ++b)
+        if (!(dts[b] > 0.0) || !isfinite(dts[b])) return SFDE_EINVAL;
+    const size_t n2 = (size_t)c->x.n * c->y.n, P2 = c->P2();
+    SFDE_TRY(sfde_ensure_workspace(c, (size_t)batch));
+    double *tin = nullptr, *pin = nullptr, *pout = nullptr, *tout = nullptr, *pg = nullptr, *ddt = nullptr;
+    sfde_status st = SFDE_OK;
+    cudaError_t e;
+#define SC(x) if ((e = (x)) != cudaSuccess) { sfde_set_last_cuda_error(e, #x, __FILE__, __LINE__); st = SFDE_ECUDA; goto done; }
+    SC(cudaMalloc(&tin, sizeof(double) * n2 * batch));
+    SC(cudaMalloc(&tout, sizeof(double) * n2 * batch));
+    SC(cudaMalloc(&pin, sizeof(double) * P2 * batch));
+    SC(cudaMalloc(&pout, sizeof(double) * P2 * batch));
+    SC(cudaMalloc(&ddt, sizeof(double) * batch));
+    SC(cudaMemcpyAsync(ddt, dts, sizeof(double) * batch, cudaMemcpyHostToDevice, c->stream));
+    if ((st = sfde_copy_in(tin, in, sizeof(double) * n2 * batch, c->stream)) != SFDE_OK) goto done;
+    sfde_launch_pad(tin, pin, c->y.n, c->x.n, c->y.P, c->x.P, batch, c->stream);
+    if (g) {
+        SC(cudaMalloc(&pg, sizeof(double) * P2 * batch));
+        if ((st = sfde_copy_in(tout, g, sizeof(double) * n2 * batch, c->stream)) != SFDE_OK) goto done;
+        sfde_launch_pad(tout, pg, c->y.n, c->x.n, c->y.P, c->x.P, batch, c->stream);
+    }
+    {
+        StepBatch sb{};
+        sb.batch = batch;
+        sb.src = pin; sb.src_stride = (long long)P2;
+        sb.dst = pout; sb.dst_stride = (long long)P2;
+        sb.g = pg; sb.g_stride = (long long)P2;
+        sb.dt = ddt; sb.n0 = 1; sb.dn = 1;   // slice b takes dt[b]
+        sb.scheme = scheme == SFDE_COARSE_CN ? SCHEME_CN : SCHEME_BE;
+        sb.level0 = false;
+        if ((st = sfde_step_fp64(c, sb, nullptr)) != SFDE_OK) goto done;
+    }
+    sfde_launch_unpad(pout, tout, c->y.n, c->x.n, c->y.P, c->x.P, batch, c->stream);
+    if ((st = sfde_copy_out(out, tout, sizeof(double) * n2 * batch, c->stream)) != SFDE_OK) goto done;
+    SC(cudaGetLastError());
+    SC(cudaStreamSynchronize(c->stream));
+done:
+#undef SC
+    cudaFree(tin); cudaFree(tout); cudaFree(pin); cudaFree(pout); cudaFree(pg); cudaFree(ddt);
+    return st;
+}
+
+sfde_status sfde_propagate_batch(sfde_ctx* c, int scheme, const double* dts, int batch, const double* in,
+                                 const double* g, double* out) {
+    return sfde_no_throw([&] { return propagate_batch_impl(c, scheme, dts, batch, in, g, out); });
 }
 
 sfde_status sfde_get_operator(sfde_ctx* c, int dir, double* coeffs, double* lambda, double* V) {

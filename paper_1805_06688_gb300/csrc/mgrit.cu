@@ -228,18 +228,6 @@ extern "C" sfde_status sfde_debug_tub_bound(const double* lx, int nx, const doub
     });
 }
 
-// Coarse propagator for this solve: the requested one, or for AUTO the paper's CN rediscretisation
-// when Theorem 3.1's bound (3.11) on the actual eigenvalues is below 1, backward Euler otherwise.
-sfde_status sfde_choose_coarse(sfde_ctx* c, int m, int requested, int* coarse, double* tub) {
-    std::vector<double> lx(c->x.n), ly(c->y.n);
-    SFDE_CUDA(cudaMemcpy(lx.data(), c->x.lam, sizeof(double) * c->x.n, cudaMemcpyDeviceToHost));
-    SFDE_CUDA(cudaMemcpy(ly.data(), c->y.lam, sizeof(double) * c->y.n, cudaMemcpyDeviceToHost));
-    *tub = tub_bound_host(lx, ly, c->x.n, c->y.n, c->kx, c->ky, c->t, m, SFDE_COARSE_CN);
-    *coarse = requested;
-    if (requested == SFDE_COARSE_AUTO) *coarse = (*tub < 1.0) ? SFDE_COARSE_CN : SFDE_COARSE_BE;
-    return SFDE_OK;
-}
-
 sfde_status sfde_mgrit_fp64(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) {
     SFDE_TRY(build_levels(c, o->m, o->max_levels, o->min_coarse));
     const int L = (int)c->levels.size();

@@ -99,6 +99,7 @@ struct sfde_ctx {
     double* partial = nullptr;  // per-CTA partial sums for deterministic norms
     size_t partial_cap = 0;
     double* scalar = nullptr;   // device scalar (norm^2)
+    double* bound_partial = nullptr;  // block maxima of the two-level bound (analysis.cu)
     double* host_scalar = nullptr;  // pinned
     // level hierarchy (built by mgrit_solve)
     std::vector<SfdeLevel> levels;
@@ -293,7 +294,11 @@ void sfde_launch_mass_x_transpose(const double* Un, const double* Um, double* T2
 sfde_status sfde_mgrit_fp64(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st);
 sfde_status sfde_seq_fp64(sfde_ctx* c, double* seconds);
 sfde_status sfde_ensure_workspace(sfde_ctx* c, size_t slices);
+// two-level analysis (analysis.cu): Theorem 3.1's bound on the device, the coarse propagator of
+// SFDE_COARSE_AUTO, the coarsening factor of mgrit_opts.m = 0
+sfde_status sfde_tub_bound_device(sfde_ctx* c, int m, int coarse, double* out);
 sfde_status sfde_choose_coarse(sfde_ctx* c, int m, int requested, int* coarse, double* tub);
+sfde_status sfde_choose_m(sfde_ctx* c, int requested_coarse, double rel_tol, int* m_out);
 
 // ---- kernel accounting (api.cu)
 int sfde_prof_begin(sfde_ctx* c);                               // slot or -1 when timing is off

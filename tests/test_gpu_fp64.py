@@ -283,3 +283,89 @@ def test_shishkin_grid_matches_oracle(relax, levels, m):
         assert abs(a - b) <= 1e-9 * ref.history[0]
     assert relerr(U, ref.U) < 1e-10
     assert relerr(U, osfde.seq_timestep(O, psi, F)) < 1e-9
+
+
+@pytest.mark.parametrize("grid", ["uniform", "graded", "shishkin"])
+def test_two_level_bound_on_device_matches_oracle(grid):
+    """Theorem 3.1's bound (Eq. (3.11)) evaluated on the device over every mode equals the oracle's
+    evaluation over every step size, for several m and both coarse propagators."""
+    from oracle import analysis
+    nt = 64
+    t = time_grid(nt, 1.0, grid, eps=2.0 ** -6 if grid == "shishkin" else None)
+    P, O = make(0.7, 0.85, 1.3, 0.6, 47, 33, t)
+    for m in (2, 4, 8, 16):
+        for coarse, name in ((sfde.COARSE_CN, "cn"), (sfde.COARSE_BE, "be")):
+            got = P.two_level_bound(m, coarse)
+            ref = analysis.tub_bound(O.sigma(), t, m, name)
+            assert abs(got - ref) <= 1e-12 * max(1.0, abs(ref)), (m, name, got, ref)
+    with pytest.raises(sfde.SfdeError):
+        P.two_level_bound(3)            # 3 does not divide 64
+
+
+def test_coarsening_factor_chosen_by_the_two_level_analysis():
+    """mgrit_opts.m = 0: the coarsening factor is the argmin over m in {2, 4, 8, 16, 32} of
+    ceil(log tol / log b(m)) * 2 m / (m - 1), b(m) the bound of the coarse propagator in use (AUTO: CN
+    where its bound is below 1), computed here from the oracle's bounds; the solve with m = 0 uses it
+    and still reaches the oracle's sequential solution."""
+    import math
+    from oracle import analysis
+    nx, ny, nt = 24, 20, 128
+    t = time_grid(nt)
+    F, _ = gaussian_bump_forcing(3, nx, ny, t)
+    psi = sine_mode_nodal(sine_mode_amplitudes(2), nx, ny)
+    for beta, gamma, kx, ky in ((0.7, 0.8, 1.0, 1.0), (0.6, 0.9, 0.05, 0.02)):
+        P, O = make(beta, gamma, kx, ky, nx, ny, t, forcing=F, psi0=psi)
+        tol = 1e-10
+        best, best_cost = None, math.inf
+        for m in (2, 4, 8, 16, 32):
+            bcn = analysis.tub_bound(O.sigma(), t, m, "cn")
+            b = bcn if bcn < 1.0 else analysis.tub_bound(O.sigma(), t, m, "be")
+            if not b < 1.0:
+                continue
+            cost = max(1.0, math.ceil(math.log(tol) / math.log(b))) * 2.0 * m / (m - 1)
+            if cost <= best_cost:
+                best, best_cost = m, cost
+        assert P.choose_coarsening(sfde.COARSE_AUTO, tol) == best, (beta, gamma, kx, ky)
+        U = np.zeros((nt + 1, ny, nx))
+        _, st = P.mgrit(U=U, m=0, max_levels=32, coarse=sfde.COARSE_AUTO, rel_tol=tol, max_iter=100)
+        assert st.converged and st.m_used == best
+        assert relerr(U, osfde.seq_timestep(O, psi, F)) < 1e-9
+
+
+def test_propagate_batch_matches_oracle():
+    """sfde_propagate_batch: the coarse propagators (Eq. (3.4) and the backward-Euler one) with their
+    own step sizes and a right-hand side, against the oracle."""
+    nx, ny = 40, 27
+    t = time_grid(8)
+    P, O = make(0.65, 0.9, 1.2, 0.3, nx, ny, t)
+    rng = np.random.default_rng(9)
+    V, G = rng.standard_normal((3, ny, nx)), rng.standard_normal((3, ny, nx))
+    dts = np.array([0.01, 0.5, 2.0])
+    for scheme, name in ((sfde.COARSE_CN, "cn"), (sfde.COARSE_BE, "be")):
+        out = np.zeros_like(V)
+        sfde.sfde_propagate_batch(P.ctx, scheme, dts, V, out, G)
+        for b in range(3):
+            assert relerr(out[b], O.propagate(V[b], dts[b], name) + G[b]) < 1e-11, (name, b)
+        sfde.sfde_propagate_batch(P.ctx, scheme, dts, V, out)
+        assert relerr(out[1], O.propagate(V[1], dts[1], name)) < 1e-11
+    with pytest.raises(sfde.SfdeError):
+        sfde.sfde_propagate_batch(P.ctx, sfde.COARSE_BE, np.array([0.1, -1.0, 0.1]), V, np.zeros_like(V))
+
+
+def test_time_sharded_driver_with_library_steps_matches_mgrit_solve():
+    """The time-sharded driver on one rank with the library's steps (sfde_step_batch for the fine
+    level, sfde_propagate_batch for the coarse ones) reproduces mgrit_solve's FP64 iteration."""
+    from paper_1805_06688_gb300.timeshard import LibraryStepper, time_sharded_mgrit
+    nx, ny, nt, m = 30, 22, 64, 4
+    t = time_grid(nt, 1.0, "graded")
+    F, _ = gaussian_bump_forcing(4, nx, ny, t)
+    psi = sine_mode_nodal(sine_mode_amplitudes(7), nx, ny)
+    P, O = make(0.6, 0.9, 1.0, 0.5, nx, ny, t, forcing=F, psi0=psi)
+    U = np.zeros((nt + 1, ny, nx))
+    _, st = P.mgrit(U=U, m=m, max_levels=3, coarse=sfde.COARSE_BE, rel_tol=1e-11, max_iter=60)
+    res = time_sharded_mgrit(LibraryStepper(P, sfde.COARSE_BE), t, torch.from_numpy(psi).cuda(), m, max_levels=3,
+                             rel_tol=1e-11, max_iter=60)
+    assert res.converged and res.iters == st.iters and res.lo == 0 and res.hi == nt
+    for a, b in zip(res.history, st.residual_history()):
+        assert abs(a - b) <= 1e-10 * st.res0
+    assert relerr(res.U.cpu().numpy(), U) < 1e-11
