@@ -341,8 +341,12 @@ typedef struct {
  * when measured, appended to it.  The context's iterate is overwritten by the trial solves.  FP64
  * contexts have nothing to tune: *out receives the current settings and SFDE_OK is returned.
  * Returns the status of the last trial when no candidate converged (settings left unchanged).
+ *
+ * sfde_get_tuning -- writes the choices ctx currently applies to *out (ms = 0).  SFDE_EINVAL for a
+ * NULL argument.
  */
 sfde_status sfde_set_tuning(sfde_ctx* ctx, const sfde_tuning* t);
+sfde_status sfde_get_tuning(const sfde_ctx* ctx, sfde_tuning* out);
 sfde_status sfde_autotune(sfde_ctx* ctx, const mgrit_opts* opts, const char* cache_path, sfde_tuning* out);
 
 void sfde_destroy(sfde_ctx* ctx);

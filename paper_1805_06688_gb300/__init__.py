@@ -13,5 +13,5 @@ from ._binding import (  # noqa: F401
     sfde_setup, sfde_set_initial, sfde_set_forcing, mgrit_solve, seq_timestep, sfde_step_batch,
     sfde_get_operator, sfde_profile_enable, sfde_profile_read, SfdeProfile, sfde_destroy,
     sfde_strerror, make_opts, Problem, sfde_batch_solve, batch_solve, SfdeTuning, sfde_set_tuning,
-    sfde_autotune, STOP_NATIVE, STOP_SFORM, sfde_set_forcing_dense, sfde_propagate_batch,
+    sfde_autotune, sfde_get_tuning, STOP_NATIVE, STOP_SFORM, sfde_set_forcing_dense, sfde_propagate_batch,
 )

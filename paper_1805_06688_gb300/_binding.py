@@ -21,7 +21,7 @@ HISTORY_MAX = 512
 exported_symbols = (
     "sfde_setup", "sfde_set_initial", "sfde_set_forcing", "mgrit_solve", "seq_timestep",
     "sfde_step_batch", "sfde_step_batch_noalloc", "sfde_get_operator", "sfde_profile_enable", "sfde_profile_read",
-    "sfde_destroy", "sfde_strerror", "sfde_batch_solve", "sfde_set_tuning", "sfde_autotune",
+    "sfde_destroy", "sfde_strerror", "sfde_batch_solve", "sfde_set_tuning", "sfde_get_tuning", "sfde_autotune",
     "sfde_set_forcing_dense", "sfde_two_level_bound", "sfde_choose_coarsening", "sfde_propagate_batch",
 )
 
@@ -99,6 +99,7 @@ def lib() -> C.CDLL:
                                        C.POINTER(MgritStats), C.POINTER(ip)]
         L.sfde_set_tuning.argtypes = [vp, C.POINTER(SfdeTuning)]
         L.sfde_autotune.argtypes = [vp, C.POINTER(MgritOpts), C.c_char_p, C.POINTER(SfdeTuning)]
+        L.sfde_get_tuning.argtypes = [vp, C.POINTER(SfdeTuning)]
         L.sfde_destroy.argtypes = [vp]
         L.sfde_destroy.restype = None
         L.sfde_strerror.argtypes = [ip]
@@ -305,6 +306,12 @@ def sfde_set_tuning(ctx, fused_pair=1, modal_chains=1, inner_cycles=0):
     _check(lib().sfde_set_tuning(ctx, C.byref(t)), "sfde_set_tuning")
 
 
+def sfde_get_tuning(ctx) -> SfdeTuning:
+    t = SfdeTuning()
+    _check(lib().sfde_get_tuning(ctx, C.byref(t)), "sfde_get_tuning")
+    return t
+
+
 def sfde_autotune(ctx, opts: MgritOpts, cache_path=None) -> SfdeTuning:
     t = SfdeTuning()
     path = None if cache_path is None else os.fsencode(cache_path)
@@ -388,6 +395,9 @@ class Problem:
 
     def set_tuning(self, fused_pair=1, modal_chains=1, inner_cycles=0):
         sfde_set_tuning(self.ctx, fused_pair, modal_chains, inner_cycles)
+
+    def tuning(self) -> SfdeTuning:
+        return sfde_get_tuning(self.ctx)
 
     def autotune(self, cache_path=None, **kw) -> SfdeTuning:
         """Times the solver's execution choices on this problem with the options ``kw`` (as for

@@ -168,6 +168,12 @@ extern "C" sfde_status sfde_set_tuning(sfde_ctx* c, const sfde_tuning* t) {
     return SFDE_OK;
 }
 
+extern "C" sfde_status sfde_get_tuning(const sfde_ctx* c, sfde_tuning* out) {
+    if (!c || !out) return SFDE_EINVAL;
+    *out = current(c);
+    return SFDE_OK;
+}
+
 extern "C" sfde_status sfde_autotune(sfde_ctx* c, const mgrit_opts* opts, const char* cache_path, sfde_tuning* out) {
     return sfde_no_throw([&] { return autotune_impl(c, opts, cache_path, out); });
 }

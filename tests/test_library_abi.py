@@ -221,6 +221,8 @@ def test_set_tuning_and_autotune_validate_arguments_without_gpu():
     t = sfde.SfdeTuning(1, 1, 0, 0.0)
     assert L.sfde_set_tuning(None, ctypes.byref(t)) == sfde.SFDE_EINVAL
     assert L.sfde_autotune(None, None, None, None) == sfde.SFDE_EINVAL
+    L.sfde_get_tuning.argtypes = [ctypes.c_void_p, ctypes.POINTER(sfde.SfdeTuning)]
+    assert L.sfde_get_tuning(None, ctypes.byref(t)) == sfde.SFDE_EINVAL
 
 
 def test_step_buffer_checks_refuse_bad_input_without_gpu():
