@@ -11,6 +11,7 @@ caller hands to a solver, i.e.
   (defined below Eq. (2.4): f^n_j = int_{I_n} (f, phi_j) dt) for the manufactured solution of
   Example 4.1 and for the Gaussian-bump source, and dense (non-separable) load vectors of a moving
   bump;
+* load vectors of the manufactured solution against the P1-triangle hats of Sec. 2;
 * the benchmark workloads (sizes, orders, diffusivities, seeds).
 
 Every random draw comes from ``numpy.random.default_rng(seed)`` on the host and
@@ -19,5 +20,6 @@ is passed to both solvers as data.
 from .generate import (  # noqa: F401
     Workload, workload, WORKLOADS, time_grid, sine_mode_amplitudes, sine_mode_nodal,
     manufactured_initial, manufactured_forcing, manufactured_exact, gaussian_bump_forcing,
-    interior_nodes, Forcing, DenseForcing, moving_bump_dense_forcing,
+    interior_nodes, Forcing, DenseForcing, moving_bump_dense_forcing, LowRankDenseForcing,
+    p1_manufactured_forcing,
 )

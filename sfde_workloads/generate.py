@@ -265,6 +265,73 @@ def moving_bump_dense_forcing(seed: int, nx: int, ny: int, t: np.ndarray, speed:
     return DenseForcing(F), (x0, y0, s, v)
 
 
+# ----------------------------------------------------------------------------- P1-triangle loads
+
+@dataclass
+class LowRankDenseForcing:
+    """Load vectors F_n = sum_r time_w[n-1, r] G[r] with full spatial patterns G[r] of shape
+    (N_y, N_x): the load of a source sum_r c_r(t) g_r(x, y) against hats that are not tensor
+    products (the P1 triangles of Sec. 2)."""
+    time_w: np.ndarray   # (N_t, R)
+    G: np.ndarray        # (R, N_y, N_x)
+
+    def dense(self, n: int) -> np.ndarray:
+        return np.tensordot(self.time_w[n - 1], self.G, axes=1)
+
+    def all(self) -> np.ndarray:
+        """Every F_n, shape (N_t, N_y, N_x)."""
+        return np.tensordot(self.time_w, self.G, axes=1)
+
+
+_GL20_X, _GL20_W = np.polynomial.legendre.leggauss(20)
+
+
+def _p1_hat_load(Ga, b, xa: np.ndarray, ha: float, yb: np.ndarray, hb: float) -> np.ndarray:
+    """(a(x) b(y), phi_ij) for the P1 hats of the triangulation with south-west to north-east
+    diagonals, result[j, i] for x_i in xa, y_j in yb; Ga is a second antiderivative of a (Ga'' = a).
+
+    In local coordinates s = (x - x_i)/h_a, r = (y - y_j)/h_b the hat is max(0, 1 - max(|s|, |r|, |s - r|)).
+    At fixed r it is, in s, a trapezoid with kinks at r - 1, 0, r, 1 (r > 0) or -1, r, 0, 1 + r (r < 0),
+    so its integral against a is exact by two integrations by parts (sum over the kinks of the slope
+    jump times Ga).  The remaining integral over r is a 20-point Gauss-Legendre rule on (-1, 0) and on
+    (0, 1), with b evaluated along the r direction (b smooth in the cases used here).
+    """
+    out = np.zeros((len(yb), len(xa)))
+    for lo in (-1.0, 0.0):
+        r = lo + 0.5 * (_GL20_X + 1.0)
+        w = 0.5 * _GL20_W
+        X = xa[:, None]
+        R = r[None, :]
+        if lo == 0.0:
+            J = (Ga(X + (R - 1.0) * ha) - Ga(X) - Ga(X + R * ha) + Ga(X + ha)) / ha
+        else:
+            J = (Ga(X - ha) - Ga(X + R * ha) - Ga(X) + Ga(X + (1.0 + R) * ha)) / ha
+        B = b(yb[:, None] + r[None, :] * hb)
+        out += hb * (B * w[None, :]) @ J.T
+    return out
+
+
+def _w(z):
+    return (z - z * z) ** 2
+
+
+def p1_manufactured_forcing(nx: int, ny: int, t: np.ndarray, beta: float, gamma: float, kx: float, ky: float,
+                            time_factor: str = "10exp(-t)") -> LowRankDenseForcing:
+    """Load vectors of the manufactured solution u = T(t) w(x) w(y) (Example 4.1, T = 10 e^{-t}) against
+    the P1 hats: f = T' w(x) w(y) + T [K_x S_beta(x) w(y) + K_y w(x) S_gamma(y)].  Every term is a product
+    a(x) b(y); the factor with the weak boundary singularity (S_rho, the Riesz derivative of w) is
+    integrated exactly in its own direction (``_p1_hat_load``), the smooth one by Gauss-Legendre.  Time
+    integrals are exact.  Domain (0, 1)^2."""
+    hx, hy = 1.0 / (nx + 1), 1.0 / (ny + 1)
+    x = interior_nodes(nx, 0.0, 1.0)
+    y = interior_nodes(ny, 0.0, 1.0)
+    L_ww = _p1_hat_load(_w_antider, _w, x, hx, y, hy)
+    L_sw = _p1_hat_load(_riesz_w_antider(beta), _w, x, hx, y, hy)
+    L_ws = _p1_hat_load(_riesz_w_antider(gamma), _w, y, hy, x, hx).T   # singular factor in y
+    dT, iT, _ = _time_poly_weights(np.asarray(t, dtype=np.float64), time_factor)
+    return LowRankDenseForcing(np.stack([dT, iT, iT], axis=1), np.stack([L_ww, kx * L_sw, ky * L_ws]))
+
+
 # ----------------------------------------------------------------------------- workloads
 
 @dataclass
