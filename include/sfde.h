@@ -65,9 +65,22 @@ typedef enum {
                                   steps, and TF32 rounds 4x finer (no counterpart in the paper) */
 } sfde_precision;
 
+/* Spatial matrices of the fully discrete scheme (2.4). */
+typedef enum {
+    SFDE_OP_TENSOR = 0,   /* tensor-product (Kronecker) form with the 1-D linear-element matrices:
+                             S_n U = M_y U M_x + tau_n (K_x M_y U A_x + K_y A_y U M_x); steps by fast
+                             diagonalisation (every precision)                                    */
+    SFDE_OP_P1 = 1        /* the P1-triangle matrices printed in Sec. 2: the block-tridiagonal mass
+                             M_h (7-point stencil) and the block-Toeplitz A_x^beta, A_y^gamma (the
+                             latter through the permutation P_pi); steps by conjugate gradients
+                             preconditioned with the tensor-product solve, to 1e-13 relative residual
+                             per slice; FP64 precision only                                       */
+} sfde_operator;
+
 typedef struct {
     int precision;     /* sfde_precision                                                   */
     void* stream;      /* cudaStream_t for all device work; NULL = the legacy default stream */
+    int operator_kind; /* sfde_operator (SFDE_OP_P1 requires SFDE_PREC_FP64, else SFDE_EUNSUPPORTED) */
 } sfde_opts;
 
 /*
@@ -178,7 +191,9 @@ typedef struct {
  * with the fine-step eigenvalues of Eq. (3.7) (lam+: their largest magnitude over the fine steps),
  * the coarse propagator's (mu++: smallest, mu*: largest magnitude over the coarse steps),
  * sigma_w = K_x lambda_x + K_y lambda_y from the setup's eigenvalues, N_c = N_t / m.
- * SFDE_EINVAL unless m >= 2 divides N_t with N_t / m >= 2.  *bound is host memory.
+ * SFDE_EINVAL unless m >= 2 divides N_t with N_t / m >= 2.  *bound is host memory.  For an
+ * SFDE_OP_P1 context the modes are those of the tensor-product operator (its preconditioner,
+ * spectrally equivalent within a factor of about 4): an estimate, not the P1 spectrum.
  *
  * sfde_choose_coarsening -- the m that mgrit_solve uses when mgrit_opts.m is 0: among
  * m in {2, 4, 8, 16, 32} dividing N_t with at least two coarse intervals, the least estimated work to
@@ -272,7 +287,8 @@ sfde_status sfde_propagate_batch(sfde_ctx* ctx, int scheme, const double* dts, i
  * for a device the library looks up the array's device address once and caches it; make that first
  * call before any stream capture.  The cached address assumes the device is not reset
  * (cudaDeviceReset) while the library is loaded; a call that fails with SFDE_ECUDA drops the cached
- * address so that the next call looks it up again.
+ * address so that the next call looks it up again.  SFDE_OP_P1 contexts: SFDE_EUNSUPPORTED (their
+ * conjugate-gradient step needs a workspace).
  */
 #define SFDE_NOALLOC_SCRATCH_DOUBLES (5u * 262144u)
 sfde_status sfde_step_batch_noalloc(sfde_ctx* ctx, int n0, int dn, int batch, const double* in,
@@ -282,7 +298,8 @@ sfde_status sfde_step_batch_noalloc(sfde_ctx* ctx, int n0, int dn, int batch, co
  *   coeffs : N doubles a_0..a_{N-1} of the Toeplitz stiffness (may be NULL)
  *   lambda : N generalised eigenvalues (may be NULL)
  *   V      : N x N doubles, V[i*N + k] = component i of eigenvector k (may be NULL)
- * Host pointers. */
+ * Host pointers.  These are the tensor-product operator's data (for an SFDE_OP_P1 context: those of
+ * its preconditioner). */
 sfde_status sfde_get_operator(sfde_ctx* ctx, int dir, double* coeffs, double* lambda, double* V);
 
 /*
@@ -291,7 +308,8 @@ sfde_status sfde_get_operator(sfde_ctx* ctx, int dir, double* coeffs, double* la
  * is additionally bracketed by CUDA events on the context's stream, and its device time and
  * algorithmic work (flops of the products with unpadded sizes; bytes each launch must move at
  * least once) are accumulated per kernel class:
- *   0 = FP64 slice GEMM of a step (2 n_R n_C n_out flops per product),
+ *   0 = FP64 slice GEMM of a step (2 n_R n_C n_out flops per product; for the P1 operator the
+ *       block-Toeplitz products with 3 n_C),
  *   1 = FP64 slice GEMM of the space-time residual (P > 256),
  *   2 = tensor-core slice GEMM of a low-precision step (BF16/TF32; four per step),
  *   3 = fused low-precision step (BF16; 4 n_x n_y (n_x + n_y) flops per slice),

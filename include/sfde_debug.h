@@ -182,6 +182,20 @@ sfde_status sfde_debug_tune_cache(const char* path, const char* key, int store, 
 sfde_status sfde_debug_lp_chain(sfde_ctx* ctx, int mode, int scheme, const double* U, int batch, int nchain,
                                 int n0, const double* g, double* out);
 
+/*
+ * P1-triangle operator (Sec. 2) hooks.
+ * sfde_debug_p1_entries -- the printed Toeplitz entries as the library evaluates them (host only):
+ *   a1[l] = a^{1,rho}_{k,k+l}, a2_upper[l] = a^{2,rho}_{k,k+l}, a2_lower[m] = a^{2,rho}_{p+m,p}
+ *   (a2_lower[0] = 0), l, m < n; for l >= 16 through a binomial series of the differences.
+ * sfde_debug_p1_apply_S -- out_b = (M_h + tau_n K) U_b, n = n0 + b dn, tau_n = (t_n - t_{n-1})/2, for
+ *   batch unpadded device slices U (N_y x N_x each) of an SFDE_OP_P1 context; synchronous.
+ * sfde_debug_p1_cg_stats -- conjugate-gradient iterations of the last step batch, their total and
+ *   the number of step batches solved (any pointer may be NULL).
+ */
+sfde_status sfde_debug_p1_entries(int n, double rho, double* a1, double* a2_upper, double* a2_lower);
+sfde_status sfde_debug_p1_apply_S(sfde_ctx* ctx, const double* U, int batch, int n0, int dn, double* out);
+sfde_status sfde_debug_p1_cg_stats(sfde_ctx* ctx, int* last, long long* total, long long* solves);
+
 #ifdef __cplusplus
 }
 #endif

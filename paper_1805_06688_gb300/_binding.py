@@ -15,6 +15,7 @@ NOALLOC_SCRATCH_DOUBLES = 5 * 262144
 PREC_FP64, PREC_MIXED_BF16, PREC_MIXED_TF32, PREC_MIXED_FP32, PREC_MIXED_AUTO = 0, 1, 2, 3, 4
 RELAX_FCF, RELAX_F = 0, 1
 COARSE_CN, COARSE_BE, COARSE_AUTO = 0, 1, 2
+OP_TENSOR, OP_P1 = 0, 1
 HISTORY_MAX = 512
 
 # every entry point declared in include/sfde.h (checked by the tests)
@@ -42,7 +43,7 @@ class SfdeError(RuntimeError):
 
 
 class SfdeOpts(C.Structure):
-    _fields_ = [("precision", C.c_int), ("stream", C.c_void_p)]
+    _fields_ = [("precision", C.c_int), ("stream", C.c_void_p), ("operator_kind", C.c_int)]
 
 
 class MgritOpts(C.Structure):
@@ -187,10 +188,10 @@ def sfde_strerror(status: int) -> str:
     return lib().sfde_strerror(int(status)).decode()
 
 
-def sfde_setup(beta, gamma, kx, ky, omega, nx, ny, t, precision=PREC_FP64, stream=None):
+def sfde_setup(beta, gamma, kx, ky, omega, nx, ny, t, precision=PREC_FP64, stream=None, operator=OP_TENSOR):
     t = np.ascontiguousarray(t, dtype=np.float64)
     om = np.ascontiguousarray(omega, dtype=np.float64)
-    opts = SfdeOpts(int(precision), stream)
+    opts = SfdeOpts(int(precision), stream, int(operator))
     ctx = C.c_void_p()
     st = lib().sfde_setup(float(beta), float(gamma), float(kx), float(ky),
                           om.ctypes.data_as(C.POINTER(C.c_double)), int(nx), int(ny),
@@ -345,11 +346,11 @@ class Problem:
     """Owning wrapper around one ``sfde_ctx`` (destroyed with the object)."""
 
     def __init__(self, beta, gamma, kx, ky, nx, ny, t, omega=(0.0, 1.0, 0.0, 1.0),
-                 precision=PREC_FP64, stream=None):
+                 precision=PREC_FP64, stream=None, operator=OP_TENSOR):
         self.nx, self.ny = int(nx), int(ny)
         self.t = np.ascontiguousarray(t, dtype=np.float64)
         self.nt = len(self.t) - 1
-        self.ctx = sfde_setup(beta, gamma, kx, ky, omega, nx, ny, self.t, precision, stream)
+        self.ctx = sfde_setup(beta, gamma, kx, ky, omega, nx, ny, self.t, precision, stream, operator)
 
     def set_initial(self, psi0):
         sfde_set_initial(self.ctx, psi0)

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsfde.so")
 SOURCES = ["api.cu", "setup.cu", "step_fp64.cu", "mgrit.cu", "mixed.cu", "gemm_tc.cu", "noalloc.cu", "ozaki.cu",
-           "fused_step.cu", "resid_int.cu", "batch.cu", "autotune.cu", "analysis.cu"]
+           "fused_step.cu", "resid_int.cu", "batch.cu", "autotune.cu", "analysis.cu", "p1.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-v"]

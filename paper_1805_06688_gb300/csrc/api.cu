@@ -90,6 +90,7 @@ static void free_ctx(sfde_ctx* c) {
     cudaStreamSynchronize(c->stream);
     sfde_free_levels(c);
     sfde_free_mixed(c);
+    sfde_p1_free(c);
     sfde_free_direction(c->x);
     sfde_free_direction(c->y);
     cudaFree(c->dt0); cudaFree(c->U0); cudaFree(c->time_w); cudaFree(c->px); cudaFree(c->py);
@@ -136,12 +137,16 @@ static sfde_status setup_impl(double beta, double gamma, double kx, double ky, c
         if (!(t[n] > t[n - 1]) || !isfinite(t[n])) return SFDE_EINVAL;
     int prec = opts ? opts->precision : SFDE_PREC_FP64;
     if (prec < SFDE_PREC_FP64 || prec > SFDE_PREC_MIXED_AUTO) return SFDE_EINVAL;
+    const int op = opts ? opts->operator_kind : SFDE_OP_TENSOR;
+    if (op != SFDE_OP_TENSOR && op != SFDE_OP_P1) return SFDE_EINVAL;
+    if (op == SFDE_OP_P1 && prec != SFDE_PREC_FP64) return SFDE_EUNSUPPORTED;
 
     sfde_ctx* c = new (std::nothrow) sfde_ctx();
     if (!c) return SFDE_ENOMEM;
     c->kx = kx; c->ky = ky; c->nt = nt;
     memcpy(c->omega, om, sizeof(om));
     c->precision = prec;
+    c->op_kind = op;
     c->stream = opts ? (cudaStream_t)opts->stream : nullptr;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         cudaGetLastError();
@@ -154,6 +159,7 @@ static sfde_status setup_impl(double beta, double gamma, double kx, double ky, c
         do {
             if ((st = sfde_setup_direction(c->x, nx, beta, om[1] - om[0], c->stream)) != SFDE_OK) break;
             if ((st = sfde_setup_direction(c->y, ny, gamma, om[3] - om[2], c->stream)) != SFDE_OK) break;
+            if (op == SFDE_OP_P1 && (st = sfde_p1_setup(c)) != SFDE_OK) break;
             std::vector<double> dt(nt);
             for (int n = 0; n < nt; ++n) dt[n] = t[n + 1] - t[n];
             cudaError_t e;
@@ -386,7 +392,7 @@ static sfde_status step_batch_impl(sfde_ctx* c, int n0, int dn, int batch, const
         sb.src = pin; sb.src_stride = (long long)P2;
         sb.dst = pout; sb.dst_stride = (long long)P2;
         sb.dt = c->dt0; sb.n0 = n0; sb.dn = dn; sb.scheme = SCHEME_CN; sb.level0 = true;
-        if ((st = sfde_step_fp64(c, sb, nullptr)) != SFDE_OK) goto done;
+        if ((st = sfde_step_any(c, sb, nullptr)) != SFDE_OK) goto done;
     }
     sfde_launch_unpad(pout, tout, c->y.n, c->x.n, c->y.P, c->x.P, batch, c->stream);
     if ((st = sfde_copy_out(out, tout, sizeof(double) * n2 * batch, c->stream)) != SFDE_OK) goto done;
@@ -436,7 +442,7 @@ static sfde_status propagate_batch_impl(sfde_ctx* c, int scheme, const double* d
         sb.dt = ddt; sb.n0 = 1; sb.dn = 1;   // slice b takes dt[b]
         sb.scheme = scheme == SFDE_COARSE_CN ? SCHEME_CN : SCHEME_BE;
         sb.level0 = false;
-        if ((st = sfde_step_fp64(c, sb, nullptr)) != SFDE_OK) goto done;
+        if ((st = sfde_step_any(c, sb, nullptr)) != SFDE_OK) goto done;
     }
     sfde_launch_unpad(pout, tout, c->y.n, c->x.n, c->y.P, c->x.P, batch, c->stream);
     if ((st = sfde_copy_out(out, tout, sizeof(double) * n2 * batch, c->stream)) != SFDE_OK) goto done;

@@ -85,7 +85,7 @@ struct Engine {
         sb.level0 = (l == 0);
         sb.norm_partial = partial;
         steps += batch;
-        return sfde_step_fp64(c, sb, npart);
+        return sfde_step_any(c, sb, npart);
     }
 
     sfde_status frelax(int l) {

@@ -48,6 +48,7 @@ void forget_scratch(int dev) {
 
 sfde_status step_batch_noalloc_impl(sfde_ctx* c, int n0, int dn, int batch, const double* in, double* out) {
     if (!c || !in || !out || batch < 1) return SFDE_EINVAL;
+    if (c->op_kind != SFDE_OP_TENSOR) return SFDE_EUNSUPPORTED;   // the P1 step's CG needs a workspace
     const long long last = (long long)n0 + (long long)(batch - 1) * dn;
     if (n0 < 1 || n0 > c->nt || last < 1 || last > c->nt) return SFDE_EINVAL;
     // the scratch address is per device: the context's device must be the current one, or the

@@ -106,6 +106,8 @@ struct sfde_ctx {
     int lev_m = 0, lev_max = 0, lev_min = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     struct SfdeMixed* mixed = nullptr;  // tensor-core operands and inner hierarchy (mixed.cu)
+    int op_kind = SFDE_OP_TENSOR;       // sfde_operator: the spatial matrices of the steps
+    struct SfdeP1* p1 = nullptr;        // P1-triangle matrices and CG workspace (p1.cu)
     int fused_step = 1;         // BF16 steps as one fused kernel where the padded sizes allow it
     int fused_pair = 1;         // fused step form: 0 one CTA per slice, 1 auto (a CTA pair per slice when
                                 // 2 batch <= SMs, else per two slices), 2 pair per slice, 3 pair per two slices
@@ -151,6 +153,21 @@ sfde_status sfde_step_fp64_into(sfde_ctx* c, const StepBatch& sb, double* T1, do
 // per-CTA sums of rho^2 in partial.
 sfde_status sfde_residual_fp64(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
                                long long rout_stride, int out_kind, double* partial, int* n_partials);
+// X_b = S^{-1} R_b by fast diagonalisation with the tensor-product matrices, S of step scheme
+// SCHEME_SOLVE (M + dt/2 K) or SCHEME_SOLVE_BE (M + dt K), dt = dt[n0 + b dn - 1]; batch <= ws_slices
+sfde_status sfde_fdm_solve_fp64(sfde_ctx* c, const double* R, long long r_stride, double* X, long long x_stride,
+                                int batch, const double* dt, int n0, int dn, int scheme);
+// ---- P1-triangle operator (p1.cu)
+sfde_status sfde_p1_setup(sfde_ctx* c);
+void sfde_p1_free(sfde_ctx* c);
+sfde_status sfde_step_p1(sfde_ctx* c, const StepBatch& sb, int* n_partials);
+sfde_status sfde_residual_norm2_p1(sfde_ctx* c, const double* U, double* norm2);
+sfde_status sfde_apply_S_norm2_p1(sfde_ctx* c, const double* R, long long r_stride, int count, int n0, int dn,
+                                  double* norm2);
+// the batched FP64 step of the context's operator
+inline sfde_status sfde_step_any(sfde_ctx* c, const StepBatch& sb, int* n_partials) {
+    return c->op_kind == SFDE_OP_P1 ? sfde_step_p1(c, sb, n_partials) : sfde_step_fp64(c, sb, n_partials);
+}
 // Out_b = My^T X_b Mx for count padded FP64 slices (Out may not alias X)
 sfde_status sfde_two_sided_fp64(sfde_ctx* c, const double* X, int count, const double* Mx, const double* My,
                                 double* Out);
@@ -161,7 +178,8 @@ sfde_status sfde_apply_S_norm2(sfde_ctx* c, const double* R, long long r_stride,
                                double* norm2);
 
 // ---- tensor-core slice GEMM (gemm_tc.cu)
-enum { SCHEME_SOLVE = 2 };  // modal factor 1/(1 + tau sigma): the solve S^{-1} alone
+enum { SCHEME_SOLVE = 2,      // modal factor 1/(1 + dt sigma / 2): the solve S^{-1} alone (CN's S)
+       SCHEME_SOLVE_BE = 3 };  // modal factor 1/(1 + dt sigma): the backward-Euler S^{-1} alone
 enum { TC_EPI_STORE = 0, TC_EPI_SCALE = 1, TC_EPI_FINAL = 2 };
 
 struct TcEpi {

@@ -138,7 +138,9 @@ __global__ void __launch_bounds__(256) k_slice_gemm_fp64(GemmParams p) {
                 if (p.scheme == SCHEME_CN) {
                     double ts = 0.5 * dt * sig;
                     lt = (1.0 - ts) / (1.0 + ts);
-                } else {
+                } else if (p.scheme == SCHEME_SOLVE) {
+                    lt = 1.0 / (1.0 + 0.5 * dt * sig);
+                } else {   // SCHEME_BE, SCHEME_SOLVE_BE
                     lt = 1.0 / (1.0 + dt * sig);
                 }
                 v *= lt;
@@ -470,6 +472,7 @@ sfde_status sfde_residual_fp64(sfde_ctx* c, const double* U, int n_first, int co
 }
 
 sfde_status sfde_residual_norm2_fp64(sfde_ctx* c, const double* U, double* norm2) {
+    if (c->op_kind == SFDE_OP_P1) return sfde_residual_norm2_p1(c, U, norm2);
     const size_t P2 = c->P2();
     double acc = 0.0;
     const int chunk = (int)c->ws_slices;
@@ -488,6 +491,7 @@ sfde_status sfde_residual_norm2_fp64(sfde_ctx* c, const double* U, double* norm2
 
 sfde_status sfde_apply_S_norm2(sfde_ctx* c, const double* R, long long r_stride, int count, int n0, int dn,
                                double* norm2) {
+    if (c->op_kind == SFDE_OP_P1) return sfde_apply_S_norm2_p1(c, R, r_stride, count, n0, dn, norm2);
     double acc = 0.0;
     const int chunk = (int)c->ws_slices;
     for (int b = 0; b < count; b += chunk) {
@@ -500,6 +504,37 @@ sfde_status sfde_apply_S_norm2(sfde_ctx* c, const double* R, long long r_stride,
         acc += r2;
     }
     *norm2 = acc;
+    return SFDE_OK;
+}
+
+// X_b = S^{-1} R_b = V_y [ (V_y^T R_b V_x) / (1 + c dt sigma) ] V_x^T (c = 1/2 for SCHEME_SOLVE, 1 for
+// SCHEME_SOLVE_BE): the four products of the spectral step with V in place of W on the input side and
+// no load; intermediates in the workspace T1..T3 (batch <= ws_slices).
+sfde_status sfde_fdm_solve_fp64(sfde_ctx* c, const double* R, long long r_stride, double* X, long long x_stride,
+                                int batch, const double* dt, int n0, int dn, int scheme) {
+    if (batch > (int)c->ws_slices || (scheme != SCHEME_SOLVE && scheme != SCHEME_SOLVE_BE)) return SFDE_EINVAL;
+    const int Px = c->x.P, Py = c->y.P;
+    const long long P2 = (long long)c->P2();
+    const int pmin = Px < Py ? Px : Py;
+    GemmParams p{};
+    p.batch = batch; p.X = R; p.x_stride = r_stride; p.R = Py; p.C = Px;
+    p.Mat = c->x.V; p.Cout = Px; p.Out = c->T1; p.out_stride = P2;
+    launch_T<EPI_STORE>(c, choose_tile((long long)batch * Py, Px, pmin), p, c->y.n, c->x.n, c->x.n);
+    GemmParams q{};
+    q.batch = batch; q.X = c->T1; q.x_stride = P2; q.R = Px; q.C = Py;
+    q.Mat = c->y.V; q.Cout = Py; q.Out = c->T2; q.out_stride = P2;
+    q.lamx = c->x.lam; q.lamy = c->y.lam; q.kx = c->kx; q.ky = c->ky;
+    q.dt = dt; q.n0 = n0; q.dn = dn; q.scheme = scheme;
+    launch_T<EPI_MODAL>(c, choose_tile((long long)batch * Px, Py, pmin), q, c->x.n, c->y.n, c->y.n);
+    GemmParams r{};
+    r.batch = batch; r.X = c->T2; r.x_stride = P2; r.R = Py; r.C = Px;
+    r.Mat = c->x.VT; r.Cout = Px; r.Out = c->T3; r.out_stride = P2;
+    launch_T<EPI_STORE>(c, choose_tile((long long)batch * Py, Px, pmin), r, c->y.n, c->x.n, c->x.n);
+    GemmParams f{};
+    f.batch = batch; f.X = c->T3; f.x_stride = P2; f.R = Px; f.C = Py;
+    f.Mat = c->y.VT; f.Cout = Py; f.Out = X; f.out_stride = x_stride;
+    launch_T<EPI_FINAL>(c, choose_tile((long long)batch * Px, Py, pmin), f, c->x.n, c->y.n, c->y.n);
+    SFDE_CUDA(cudaGetLastError());
     return SFDE_OK;
 }
 

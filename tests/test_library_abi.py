@@ -255,3 +255,43 @@ def test_step_buffer_checks_refuse_bad_input_without_gpu():
             B.sfde_step_batch(key + 8, 1, 1, 1, ok, ok.copy())
     finally:
         B._CTX_DIMS.pop(key, None)
+
+
+@pytest.mark.parametrize("rho", [0.55, 0.75, 0.95, 1.0])
+def test_p1_entries_match_the_printed_formulas_without_gpu(rho):
+    """The library's evaluation of the printed A_1 / A_2 entries of Sec. 2 (direct sums for offsets
+    below 16, a binomial series of the differences above) against the oracle's 40-digit evaluation
+    of the printed formulas, up to offset 1100."""
+    import numpy as np
+    from oracle import p1
+    sfde = _library()
+    L = sfde.lib()
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.sfde_debug_p1_entries.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, dp]
+    n = 1100
+    a1, up, lo = np.zeros(n), np.zeros(n), np.zeros(n)
+    assert L.sfde_debug_p1_entries(n, rho, a1.ctypes.data_as(dp), up.ctypes.data_as(dp), lo.ctypes.data_as(dp)) == 0
+    idx = sorted(set(list(range(0, 40)) + list(range(40, n, 37)) + [n - 1]))
+    scale = abs(p1.a1(0, rho))
+    for l in idx:
+        ref = (p1.a1(l, rho), p1.a2_upper(l, rho), p1.a2_lower(l, rho) if l else 0.0)
+        for got, want in zip((a1[l], up[l], lo[l]), ref):
+            assert abs(got - want) <= 3e-12 * abs(want) + 1e-15 * scale, (l, got, want)
+    assert L.sfde_debug_p1_entries(0, rho, a1.ctypes.data_as(dp), up.ctypes.data_as(dp), lo.ctypes.data_as(dp)) == \
+        sfde.SFDE_EINVAL
+
+
+def test_p1_operator_options_are_validated_without_gpu():
+    """operator_kind outside {0, 1} is invalid; the P1 operator runs in FP64 only."""
+    import numpy as np
+    sfde = _library()
+    L = sfde.lib()
+    t = np.linspace(0, 1, 5)
+    om = np.array([0.0, 1.0, 0.0, 1.0])
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    ctx = ctypes.c_void_p()
+    for prec, op, want in ((0, 2, sfde.SFDE_EINVAL), (0, -1, sfde.SFDE_EINVAL), (1, 1, sfde.SFDE_EUNSUPPORTED),
+                           (3, 1, sfde.SFDE_EUNSUPPORTED)):
+        o = sfde.SfdeOpts(prec, None, op)
+        st = L.sfde_setup(0.7, 0.8, 1.0, 1.0, dp(om), 5, 5, dp(t), 4, ctypes.byref(o), ctypes.byref(ctx))
+        assert st == want, (prec, op, st)
