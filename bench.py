@@ -266,6 +266,7 @@ KERNEL_CLASSES = (  # the library's accounting classes (include/sfde.h, sfde_pro
     ("k_fused_step", "fused BF16 spectral step: four tcgen05 products per slice on chip", "tc"),
     ("k_digit_gemm_int", "digit-split residual products: up to 28 BF16 tcgen05 products, exact int64", "tc"),
     ("k_split_pair+k_combine_int", "integer residual assembly (exponents, digits, combination)", "hbm"),
+    ("k_p1_gemm", "P1-triangle operator: block-Toeplitz FP64 products over three shifted slice copies", "alu"),
 )
 
 
@@ -563,6 +564,127 @@ def run_batch(args):
     return 0
 
 
+P1_WORKLOAD = "p1_example41_M32_N32768"
+
+
+def run_p1(args):
+    """The paper's own P1-triangle scheme (Sec. 2) on Example 4.1 in the setting of Table 2's last row:
+    M = 32 intervals per direction (31^2 unknowns), tau = h^3 (N = 32768 uniform steps), K_x = 3.0,
+    K_y = 7.5, beta = gamma = 0.8, solved by FP64 MGRIT on the GPU (m = 8, FCF, backward-Euler coarse
+    propagator, the space-time residual of Eq. (3.1) to 1e-10 of the initial guess's), every fine
+    step a CG solve preconditioned with the tensor-product spectral solve.  value = 31^2 x 32768 /
+    seconds per solve (CUDA events on the library's stream); accuracy: the L2 error at T = 1 against
+    the exact solution, the printed Table 2 value and the oracle's dense sequential solution."""
+    import torch
+    import paper_1805_06688_gb300 as sfde
+    from oracle import p1 as op1
+    from sfde_workloads import manufactured_exact, manufactured_initial, p1_manufactured_forcing, time_grid
+    if not os.path.exists(sfde.library_path):
+        from paper_1805_06688_gb300.build import build
+        build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    M, beta, gamma, kx, ky = 32, 0.8, 0.8, 3.0, 7.5
+    n, nt = M - 1, M ** 3
+    t = time_grid(nt)
+    F = p1_manufactured_forcing(n, n, t, beta, gamma, kx, ky)
+    Fall = F.all()
+    psi = manufactured_initial(n, n, "10exp(-t)")
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    P = sfde.Problem(beta, gamma, kx, ky, n, n, t, precision=sfde.PREC_FP64, stream=stream.cuda_stream,
+                     operator=sfde.OP_P1)
+    P.set_initial(torch.from_numpy(psi).to(dev))
+    P.set_forcing_dense(torch.from_numpy(Fall).to(dev))
+    torch.cuda.synchronize(dev)
+    setup_s = time.perf_counter() - t0
+    kw = dict(m=8, coarse=sfde.COARSE_BE, rel_tol=1e-10, max_iter=60, stop_kind=sfde.STOP_SFORM)
+    UT = torch.zeros((n, n), dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        P.mgrit(U_T=UT, **kw)
+    P.profile_enable(False)
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        torch.cuda.nvtx.range_push("timed")
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, stats = P.mgrit(U_T=UT, **kw)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        torch.cuda.nvtx.range_pop()
+    launches = P.profile_read().kernel_launches
+    sec = ev0.elapsed_time(ev1) * 1e-3 / args.steps
+    units = n * n * nt
+    value = units / sec
+    P.profile_enable(True)
+    P.mgrit(U_T=UT, **kw)
+    prof = P.profile_read()
+    P.profile_enable(False)
+    roofline, kernels = roofline_from_profile(prof, -1)
+    ut_gpu = UT.cpu().numpy()
+
+    # end to end through the C ABI with host buffers: psi_0 and every load vector in, u(T) out
+    psi_h = torch.from_numpy(psi).pin_memory()
+    F_h = torch.from_numpy(Fall).pin_memory()
+    UT_h = torch.zeros((n, n), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        P.set_initial(psi_h)
+        P.set_forcing_dense(F_h)
+        P.mgrit(U_T=UT_h, **kw)
+    torch.cuda.synchronize(dev)
+    e2e = {"value": units / ((time.perf_counter() - t0) / args.steps), "unit": UNIT,
+           "h2d_bytes_per_step": 8 * (psi.size + Fall.size), "d2h_bytes_per_step": 8 * n * n}
+
+    # comparator: GPU sequential stepping with the same P1 steps, timed on the first 2048 steps (the
+    # steps are uniform, so every step costs the same)
+    Q = sfde.Problem(beta, gamma, kx, ky, n, n, t[:2049], precision=sfde.PREC_FP64, stream=stream.cuda_stream,
+                     operator=sfde.OP_P1)
+    Q.set_initial(torch.from_numpy(psi).to(dev))
+    Q.set_forcing_dense(torch.from_numpy(np.ascontiguousarray(Fall[:2048])).to(dev))
+    Q.seq(U_T=UT)
+    seq_s = Q.seq(U_T=UT)
+    Q.close()
+    comparators = {"fp64_seq_timestep_gpu": n * n * 2048 / seq_s,
+                   "fp64_seq_timestep_gpu_sample": "first 2048 of the 32768 uniform steps",
+                   "speedup_vs_fp64_seq_timestep": value / (n * n * 2048 / seq_s),
+                   "mgrit_iters": stats.iters, "levels": stats.levels, "step_solves": stats.step_solves}
+
+    exact = lambda X, Y: manufactured_exact(X, Y, 1.0, "10exp(-t)")
+    acc = {"l2_error_gpu_T1": op1.l2_error_p1(ut_gpu, exact), "table2_printed": 1.3240e-5}
+    acc["ratio_to_printed"] = acc["l2_error_gpu_T1"] / acc["table2_printed"]
+    base = None
+    if not args.no_cpu_baseline:
+        # the oracle: dense Cholesky stepping of the same P1 scheme on the host cores, all 32768 steps
+        O = op1.P1SFDE(beta, gamma, kx, ky, n, n, t)
+        t0 = time.perf_counter()
+        ut_ref = op1.seq_timestep_p1(O, psi, F, keep_all=False)
+        cpu_s = time.perf_counter() - t0
+        acc["max_rel_diff_vs_oracle_T1"] = float(np.abs(ut_gpu - ut_ref).max() / np.abs(ut_ref).max())
+        acc["l2_error_oracle_T1"] = op1.l2_error_p1(ut_ref, exact)
+        base = {"value": units / cpu_s, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                "sample": "the whole solve: sequential stepping of the oracle's dense P1 scheme (Cholesky, "
+                          f"{cpu_s:.1f} s)"}
+    line = {
+        "metric": "space-time DOF-updates/s to 1e-10 rel. space-time residual, P1-triangle scheme (Example 4.1, "
+                  "Table 2 setting), FP64 MGRIT, 1 GB300",
+        "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sec, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": P1_WORKLOAD, "operator": "P1 triangles (Sec. 2)", "nx": n, "ny": n, "nt": nt,
+                   "beta": beta, "gamma": gamma, "kx": kx, "ky": ky, "m": 8, "coarse": "be", "rel_tol": 1e-10,
+                   "stop": "FP64 space-time residual of Eq. (3.1), relative to the initial guess's",
+                   "cg": "per step: CG to 1e-13 relative residual, preconditioned by the tensor-product spectral solve",
+                   "l2": "space-time iterate 32769 x 32^2 x 8 B = 268 MB, larger than L2"},
+        "setup_s": setup_s, "roofline": roofline, "kernels": kernels, "e2e": e2e, "clocks": clk.summary(),
+        "gpu_launches": launches, "comparators": comparators, "accuracy": acc, "cpu_baseline": base,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -579,6 +701,8 @@ def main():
     args = ap.parse_args()
     if args.workload == "batch64":
         return run_batch(args)
+    if args.workload == P1_WORKLOAD:
+        return run_p1(args)
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)

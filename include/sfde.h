@@ -308,17 +308,18 @@ sfde_status sfde_get_operator(sfde_ctx* ctx, int dir, double* coeffs, double* la
  * is additionally bracketed by CUDA events on the context's stream, and its device time and
  * algorithmic work (flops of the products with unpadded sizes; bytes each launch must move at
  * least once) are accumulated per kernel class:
- *   0 = FP64 slice GEMM of a step (2 n_R n_C n_out flops per product; for the P1 operator the
- *       block-Toeplitz products with 3 n_C),
+ *   0 = FP64 slice GEMM of a step (2 n_R n_C n_out flops per product),
  *   1 = FP64 slice GEMM of the space-time residual (P > 256),
  *   2 = tensor-core slice GEMM of a low-precision step (BF16/TF32; four per step),
  *   3 = fused low-precision step (BF16; 4 n_x n_y (n_x + n_y) flops per slice),
  *   4 = digit-split tensor-core product of the residual (BF16 digit products actually computed:
  *       28 (integer output) or 21 (FP64 output) times 2 n_R n_C n_out),
- *   5 = integer residual assembly (exponents, digit splitting, combination; bytes only).
+ *   5 = integer residual assembly (exponents, digit splitting, combination; bytes only),
+ *   6 = P1-triangle operator products (FP64; 2 n_y n_x (3 n) flops per direction and slice, n = n_x
+ *       or n_y: the block-Toeplitz contraction over three shifted copies of the slice).
  * kernel_launches counts every kernel this library launched on the context.
  */
-#define SFDE_PROF_CLASSES 6
+#define SFDE_PROF_CLASSES 7
 typedef struct {
     long long kernel_launches;
     long long launches[SFDE_PROF_CLASSES];

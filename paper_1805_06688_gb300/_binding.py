@@ -27,7 +27,8 @@ exported_symbols = (
 )
 
 
-PROF_CLASSES = 6  # see include/sfde.h: FP64 step, FP64 residual, TC GEMM, fused step, digit products, int assembly
+PROF_CLASSES = 7  # see include/sfde.h: FP64 step, FP64 residual, TC GEMM, fused step, digit products, int
+# assembly, P1 operator products
 
 
 class SfdeProfile(C.Structure):

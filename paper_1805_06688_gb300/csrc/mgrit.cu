@@ -65,6 +65,7 @@ struct Engine {
     int m, L, relax, scheme;
     long long steps = 0;
     bool skip = false;   // down-cycle without relaxation (the first iteration with skip_first_down)
+    bool warm = false;   // every level's iterate holds valid values: steps may start from them
 
     size_t P2() const { return c->P2(); }
 
@@ -84,6 +85,12 @@ struct Engine {
         sb.scheme = (l == 0) ? SCHEME_CN : scheme;
         sb.level0 = (l == 0);
         sb.norm_partial = partial;
+        if (warm) {
+            // the value being replaced (relaxation) or the target value (residual): Phi(u) + g is
+            // close to it once the iteration converges
+            sb.guess = utgt ? utgt : sb.dst;
+            sb.guess_stride = utgt ? sb.utgt_stride : sb.dst_stride;
+        }
         steps += batch;
         return sfde_step_any(c, sb, npart);
     }
@@ -233,6 +240,7 @@ sfde_status sfde_mgrit_fp64(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) {
     const int L = (int)c->levels.size();
     SFDE_TRY(sfde_ensure_workspace(c, std::max(1, c->nt / o->m)));
     Engine E{c, o->m, L, o->relax, SCHEME_CN};
+    E.warm = true;   // level 0 is initialised below, coarse levels are zeroed before each cycle
 
     int coarse = SFDE_COARSE_BE;
     double tub = 0.0;

@@ -16,9 +16,12 @@
 // The step S_n X = R (S_n = M_h + tau_n K, symmetric positive definite by Lemma 3.2) is solved by
 // CG preconditioned with the tensor-product operator's fast-diagonalisation solve at the same tau
 // (spectrally equivalent: the preconditioned spectrum lies in [0.75, 3] for the paper's orders,
-// independent of h and tau), starting from that solve of R, to a relative residual of 1e-13 per
-// slice (the paper solves with CG to 1e-9).  Every slice of a batch has its own CG scalars; the
-// iteration stops when the slowest slice has converged.
+// independent of h and tau), to a relative residual of 1e-13 per slice (the paper solves with CG to
+// 1e-9).  Inside MGRIT each solve starts from the value the iterate already holds at its time point
+// (the value a relaxation replaces, or the C-point value a residual is taken against): once the
+// iteration converges that is close to the step's result and CG needs few iterations; other solves
+// start from zero.  Every slice of a batch has its own CG scalars; the iteration stops when the
+// slowest slice has converged.
 #include <math.h>
 #include <string.h>
 
@@ -334,6 +337,23 @@ __global__ void k_p1_max_ratio(const double* rr, const double* rr0, int batch, d
     if (threadIdx.x == 0) *out = s[0];
 }
 
+// ref_b = max(ref_b, other_b): the reference of the relative stopping test
+__global__ void k_p1_max_into(double* ref, const double* other, int nb) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x)
+        ref[b] = fmax(ref[b], other[b]);
+}
+
+// X_b = guess_b (- g_b): the starting iterate of CG from an estimate of Phi(u) + g
+__global__ void k_p1_init_x(double* X, long long xs, const double* guess, long long gs, const double* g, long long ggs,
+                            size_t n) {
+    const long long b = blockIdx.y;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        double v = guess[b * gs + e];
+        if (g) v -= g[b * ggs + e];
+        X[b * xs + e] = v;
+    }
+}
+
 // dst_b = X_b (+ g_b) (- u_b), with per-CTA sums of dst^2
 __global__ void __launch_bounds__(256) k_p1_finish(const double* X, long long xs, const double* g, long long gs,
                                                    const double* ut, long long us, double* dst, long long ds, size_t n,
@@ -374,7 +394,7 @@ void launch_gemm(sfde_ctx* c, int T, const P1Args& a, int batch) {
     else k_p1_gemm<16, MODE><<<grid, 256, 0, c->stream>>>(a);
     const double nx = c->x.n, ny = c->y.n;
     const double flops = 2.0 * batch * nx * ny * 3.0 * (MODE == 0 ? nx : ny);
-    sfde_prof_end(c, slot, 0, flops, 8.0 * batch * (2.0 * nx * ny) + 8.0 * 3.0 * (MODE == 0 ? nx * nx : ny * ny));
+    sfde_prof_end(c, slot, 6, flops, 8.0 * batch * (2.0 * nx * ny) + 8.0 * 3.0 * (MODE == 0 ? nx * nx : ny * ny));
     sfde_count_launch(c);
 }
 
@@ -443,8 +463,11 @@ dim3 vec_grid(sfde_ctx* c, int nb) {
     return dim3(std::max(1u, per), (unsigned)nb);
 }
 
-// X_b = S_b^{-1} R_b for nb slices (contiguous in the workspace), S_b = M_h + taum dt[n_b-1] K
-sfde_status p1_pcg(sfde_ctx* c, int nb, const double* dt, int n0, int dn, double taum, int solve_scheme) {
+// X_b = S_b^{-1} R_b for nb slices (contiguous in the workspace), S_b = M_h + taum dt[n_b-1] K, from
+// X = guess - g when an estimate is given, else from X = 0; converged when every slice's residual is
+// below 1e-13 of the larger of its ||R|| and its initial residual
+sfde_status p1_pcg(sfde_ctx* c, int nb, const double* dt, int n0, int dn, double taum, int solve_scheme,
+                   const double* guess, long long guess_stride, const double* g, long long g_stride) {
     SfdeP1& p = *c->p1;
     const long long P2 = (long long)c->P2();
     const size_t n = c->P2();
@@ -471,10 +494,23 @@ sfde_status p1_pcg(sfde_ctx* c, int nb, const double* dt, int n0, int dn, double
         return p1_apply(c, A, nb, T, nullptr);
     };
     const dim3 vg = vec_grid(c, nb);
-    // x0 = P^{-1} R, r = R - S x0, z = P^{-1} r, p = z
-    SFDE_TRY(precond(R, X));
-    SFDE_TRY(apply_S(X, r, R, 1.0, -1.0));
+    // x0 = guess - g (or 0), r = R - S x0, z = P^{-1} r, p = z
+    if (guess) {
+        k_p1_init_x<<<vg, 256, 0, c->stream>>>(X, P2, guess, guess_stride, g, g_stride, n);
+        sfde_count_launch(c);
+        SFDE_TRY(apply_S(X, r, R, 1.0, -1.0));
+    } else {
+        SFDE_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * n * nb, c->stream));
+        SFDE_CUDA(cudaMemcpyAsync(r, R, sizeof(double) * n * nb, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    // the stopping test is relative to the larger of ||R|| and the initial residual: a zero right-hand
+    // side (a zeroed coarse iterate) with a nonzero starting value must still be solved
     launch_dot(c, R, R, nb, rr0);
+    if (guess) {
+        launch_dot(c, r, r, nb, rr);
+        k_p1_max_into<<<(nb + 255) / 256, 256, 0, c->stream>>>(rr0, rr, nb);
+        sfde_count_launch(c);
+    }
     SFDE_TRY(precond(r, z));
     SFDE_CUDA(cudaMemcpyAsync(pv, z, sizeof(double) * n * nb, cudaMemcpyDeviceToDevice, c->stream));
     launch_dot(c, r, z, nb, rz);
@@ -587,7 +623,9 @@ sfde_status sfde_step_p1(sfde_ctx* c, const StepBatch& sb, int* n_partials) {
         A.load = sb.level0 && (c->rank > 0 || c->Fd);
         A.out = R; A.os = P2;
         SFDE_TRY(p1_apply(c, A, nb, T, nullptr));
-        sfde_status st = p1_pcg(c, nb, sb.dt, n0, sb.dn, taum, cn ? SCHEME_SOLVE : SCHEME_SOLVE_BE);
+        sfde_status st = p1_pcg(c, nb, sb.dt, n0, sb.dn, taum, cn ? SCHEME_SOLVE : SCHEME_SOLVE_BE,
+                                sb.guess ? sb.guess + (long long)b0 * sb.guess_stride : nullptr, sb.guess_stride,
+                                sb.g ? sb.g + (long long)b0 * sb.g_stride : nullptr, sb.g_stride);
         if (st != SFDE_OK && st != SFDE_ENOCONV) return st;
         if (st == SFDE_ENOCONV) rc = SFDE_ENOCONV;
         const double* X = c->p1->ws + (size_t)nb * P2;     // the CG iterate

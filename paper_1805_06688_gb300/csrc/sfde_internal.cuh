@@ -142,6 +142,10 @@ struct StepBatch {
     int scheme;                // SfdeScheme
     bool level0;               // add the level-0 load F_n (if rank > 0)
     double* norm_partial;      // residual mode: per-CTA sums of squares (or nullptr)
+    // an estimate of the step's result (before g is added), slice b at guess + b*guess_stride, that
+    // iterative step solves may start from (or nullptr); guess - g is used when g is set
+    const double* guess;
+    long long guess_stride;
 };
 
 sfde_status sfde_step_fp64(sfde_ctx* c, const StepBatch& sb, int* n_partials);
