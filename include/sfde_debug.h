@@ -48,7 +48,8 @@ sfde_status sfde_debug_oz_gemm(const double* X, int batch, int R, int K, const d
  * The FP64 space-time residual of the mixed-precision solver for a given iterate (Eq. (2.4)):
  *   rho_n = F_n + B_n U_{n-1} - S_n U_n,  n = 1..N_t,
  * U: (N_t+1) x N_y x N_x doubles (host or device); rho: N_t x N_y x N_x floats (host or device),
- * rounded to TF32 as the solver stores it; *norm2 = sum of rho_n^2.  use_tensor_cores = 1 (or 7)
+ * rounded to TF32 as the solver stores it (plain FP32 for an SFDE_PREC_MIXED_FP32 context);
+ * *norm2 = sum of rho_n^2.  use_tensor_cores = 1 (or 7)
  * assembles rho in integer arithmetic around digit-split BF16 tensor-core products with seven
  * digits per operand, 4..6 with that many (operands truncated at about 2^{9-8 nd} of their scales);
  * padded 64 <= P_x, P_y <= 256 or multiples of 256 up to 1024; *norm2 from the stored FP32 values,

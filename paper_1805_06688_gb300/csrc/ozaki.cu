@@ -358,9 +358,9 @@ k_digit_gemm_int(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const long long m = (t / ntn) * BM + lq * 32 + lane;
             const int n0 = (int)(t % ntn) * BN;
-            // zt: running sums over the K groups in units of 2^-52; per group and 16-column slice, z
-            // holds the digit sums d <= 6 (units 2^-52, exact) and zl d = 7, 8 (units 2^-64, exact),
-            // folded into zt with one rounding per group (at most half a unit each)
+            // zt: running sums over the K groups in units of 2^-52, the digit sums d <= 6 added exactly;
+            // per group and 16-column slice zl holds d = 7, 8 (units 2^-64, exact), folded into zt with
+            // one rounding per group (at most half a unit each)
             long long zt[CW];
 #pragma unroll
             for (int j = 0; j < CW; ++j) zt[j] = 0;
@@ -370,24 +370,37 @@ k_digit_gemm_int(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                 if (!ok) break;
 #pragma unroll
                 for (int qs = 0; qs < CW / 16; ++qs) {
-                    long long z[16], zl[16];
+                    long long zl[16];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) { z[j] = 0; zl[j] = 0; }
-#pragma unroll 1
-                    for (int a = 0; a < nd; ++a) {
-                        uint32_t v[16];
-                        tc::tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(a * BN + cb + qs * 16), v);
+                    for (int j = 0; j < 16; ++j) zl[j] = 0;
+                    // accumulator a's 16 columns in one of two register sets: the load of a + 1 is in
+                    // flight while a is converted (the drain is otherwise a chain of load latencies)
+                    const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(cb + qs * 16);
+                    uint32_t va[16], vb[16];
+                    tc::tmem_ld16_async(base, va);
+                    tc::tmem_wait_ld();
+                    tc::reg_fence16(va);
+#pragma unroll
+                    for (int a = 0; a < Plan<true>::S; ++a) {
+                        if (a >= nd) break;
+                        uint32_t* cur = (a & 1) ? vb : va;
+                        uint32_t* nxt = (a & 1) ? va : vb;
+                        if (a + 1 < nd) tc::tmem_ld16_async(base + (uint32_t)((a + 1) * BN), nxt);
                         const int d = a + 2;
                         const int sh = d <= 6 ? 52 - 8 * d : 8 * (8 - d);
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            const long long sv = (long long)__float2int_rn(__uint_as_float(v[j]));  // exact, |sv| < 2^24
-                            if (d <= 6) z[j] += sv << sh;
+                            const long long sv = (long long)__float2int_rn(__uint_as_float(cur[j]));  // exact, |sv| < 2^24
+                            if (d <= 6) zt[qs * 16 + j] += sv << sh;
                             else zl[j] += sv << sh;
+                        }
+                        if (a + 1 < nd) {
+                            tc::tmem_wait_ld();
+                            tc::reg_fence16(nxt);
                         }
                     }
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) zt[qs * 16 + j] += z[j] + ((zl[j] + 2048) >> 12);
+                    for (int j = 0; j < 16; ++j) zt[qs * 16 + j] += (zl[j] + 2048) >> 12;
                 }
                 tc::tc_fence_before();
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(tfree)) : "memory");

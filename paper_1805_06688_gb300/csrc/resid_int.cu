@@ -158,6 +158,28 @@ __device__ __forceinline__ double i64_to_f64(long long x) {
     return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 1023) << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 
+// round(f 2^-ec) as a 128-bit integer from the bit pattern of f (integer operations only); false when
+// |f| 2^-ec would reach 2^124 (the caller then keeps the FP64 form) or f is not finite
+__device__ __forceinline__ bool f64_to_i128_scaled(double f, int ec, __int128& out) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(f);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    if (ex == 0) { out = 0; return true; }                  // zero or below 2^-1022
+    if (ex == 0x7FF) return false;
+    const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));   // f = +-m 2^{ex-1075}
+    const int sh = ex - 1075 - ec;
+    __int128 v;
+    if (sh >= 0) {
+        if (sh > 70) return false;                          // m 2^sh < 2^123: clear of 2^124
+        v = (__int128)m << sh;
+    } else if (sh > -64) {
+        v = (m + (1ll << (-sh - 1))) >> (-sh);
+    } else {
+        v = 0;
+    }
+    out = (b >> 63) ? -v : v;
+    return true;
+}
+
 // rounding arithmetic right shift (k >= 0)
 __device__ __forceinline__ long long rshr(long long x, int k) {
     if (k <= 0) return x;
@@ -199,8 +221,12 @@ __device__ __forceinline__ float i128_to_f32(__int128 x, float s1, float s2) {
 // differ by more than 2^10 the finer product is shifted right, keeping its bits down to 2^-62 of
 // the coarser unit, far below the fixed-point grid's own resolution), added exactly, and converted
 // to FP32 within 1.5 ulp -- no FP64 arithmetic per element (the FP64 pipe runs at about 1/64 of
-// the FP32 rate).  With a load term the FP64 form is kept.  Writes rho (BF16 or TF32-rounded FP32),
-// zero outside the interior nodes, and one FP64 sum of rho^2 per block.
+// the FP32 rate).  A load term F_n is formed in FP64 (one FMA per separable term, the time weight
+// times the y factor taken once per row) and added as round(F 2^-ec), a 128-bit integer in the same
+// unit (its rounding, half a unit, lies far below F's own FP64 rounding); where F 2^-ec would not fit,
+// or both slices of the pair are zero (no unit: c_m = c_s = 0), the FP64 form F + c_m S9 + c_s S is
+// kept.  Writes rho (BF16 or TF32-rounded FP32), zero outside the interior nodes, and one FP64 sum of
+// rho^2 per block.
 template <typename OT, bool TF32R>
 __global__ void __launch_bounds__(256, 4) k_combine_int(
     const long long* __restrict__ T1, const long long* __restrict__ T3, const long long* __restrict__ DU,
@@ -217,6 +243,9 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
     __shared__ long long cmi[2];          // their integer mantissas, shifted to the unit 2^ec
     __shared__ int csh[2];                // per term: right shift of the product
     __shared__ float csc[2];              // 2^ec as two FP32 powers of two
+    __shared__ int cec;                   // ec
+    __shared__ int cdeg;                  // both coefficients zero (two zero slices): no integer unit
+    __shared__ double fy[SFDE_MAX_RANK][32];   // time weight x y factor of each load term, per row
     const int b = blockIdx.z, n = n0 + b;
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -270,6 +299,7 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
         int em, es;
         split_double(cst[0], mm, em);
         split_double(cst[1], ms, es);
+        cdeg = mm == 0 && ms == 0;
         if (mm == 0) em = es;
         if (ms == 0) es = em;
         const int ec = max(em, es) - 10;
@@ -280,7 +310,13 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
         const int e1 = min(max(ec, -126), 127);
         csc[0] = ldexpf(1.0f, e1);
         csc[1] = ldexpf(1.0f, min(max(ec - e1, -126), 127));
+        cec = ec;
     }
+    if (ty == 0)
+        for (int q = 0; q < rank; ++q) {
+            const int j = j0 + tx;
+            fy[q][tx] = j < Py ? time_w[(size_t)(n - 1) * rank + q] * byn[(size_t)q * Py + j] : 0.0;
+        }
     __syncthreads();
     for (int rr = ty; rr < 34; rr += 8) rs[rr][tx] = du[rr][tx] + 4 * du[rr][tx + 1] + du[rr][tx + 2];
     __syncthreads();
@@ -290,6 +326,11 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
     const float sc1 = csc[0], sc2 = csc[1];
     const bool finite = E < 1024;
     const int i = i0 + tx;
+    const int ec = cec;
+    const bool deg = cdeg != 0;
+    double bxi[SFDE_MAX_RANK];
+#pragma unroll
+    for (int q = 0; q < SFDE_MAX_RANK; ++q) bxi[q] = (q < rank && i < Px) ? bxn[(size_t)q * Px + i] : 0.0;
     float sq = 0.f;   // of the stored values; the norm only decides when the iteration stops
     for (int jj = ty; jj < 32; jj += 8) {
         const int j = j0 + jj;
@@ -299,17 +340,20 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
             const long long k2 = t3[jj][tx] + 4 * t3[jj][tx + 1] + t3[jj][tx + 2];
             const long long st = rshr(k1, u - u1) + rshr(k2, u - u2);
             const long long s9 = rs[jj][tx] + 4 * rs[jj + 1][tx] + rs[jj + 2][tx];
+            __int128 tm = (__int128)s9 * mm, ts = (__int128)st * ms;
+            if (rm) tm >>= rm;     // block-uniform, zero unless the units differ by more than 2^10
+            if (rsd) ts >>= rsd;
+            __int128 fi = 0;
+            bool exact = true;
             if (rank > 0 || Fd) {
                 double f = Fd ? Fd[(size_t)(n - 1) * P2 + (size_t)j * Px + i] : 0.0;
-                for (int q = 0; q < rank; ++q)
-                    f += time_w[(size_t)(n - 1) * rank + q] * byn[(size_t)q * Py + j] * bxn[(size_t)q * Px + i];
-                rf = (float)fma(cm, i64_to_f64(s9), fma(cs, i64_to_f64(st), f));
-            } else {
-                __int128 tm = (__int128)s9 * mm, ts = (__int128)st * ms;
-                if (rm) tm >>= rm;     // block-uniform, zero unless the units differ by more than 2^10
-                if (rsd) ts >>= rsd;
-                rf = i128_to_f32(tm + ts, sc1, sc2);
+#pragma unroll
+                for (int q = 0; q < SFDE_MAX_RANK; ++q)
+                    if (q < rank) f = fma(fy[q][jj], bxi[q], f);
+                exact = !deg && f64_to_i128_scaled(f, ec, fi);
+                if (!exact) rf = (float)fma(cm, i64_to_f64(s9), fma(cs, i64_to_f64(st), f));
             }
+            if (exact) rf = i128_to_f32(tm + ts + fi, sc1, sc2);
             if (!finite) rf = __int_as_float(0x7FC00000);
         }
         sq = fmaf(rf, rf, sq);
@@ -420,6 +464,7 @@ extern "C" sfde_status sfde_debug_residual(sfde_ctx* c, const double* U, int use
     if (use_tensor_cores && (nd < 4 || nd > ND)) return SFDE_EINVAL;
     if (use_tensor_cores && !sfde_resid_int_supported(Px, Py)) return SFDE_EUNSUPPORTED;
     const size_t P2 = c->P2(), n2 = (size_t)c->x.n * c->y.n;
+    const int okind = c->precision == SFDE_PREC_MIXED_FP32 ? 2 : 1;   // storage as the solver keeps it
     double* u = nullptr;
     SFDE_TRY(sfde_level0(c, &u));
     SFDE_TRY(sfde_ensure_workspace(c, std::min<size_t>(c->nt, 128)));
@@ -451,9 +496,10 @@ extern "C" sfde_status sfde_debug_residual(sfde_ctx* c, const double* U, int use
         DC(cudaMalloc(&dV, sfde_resid_int_digit_bytes(Px, Py, (int)c->ws_slices)));
         DC(cudaMalloc(&dVt, sfde_resid_int_digit_bytes(Px, Py, (int)c->ws_slices)));
         DC(cudaMalloc(&En, sizeof(int) * (c->nt + 1)));
-        st = sfde_residual_int(c, u, 1, c->nt, rp, (long long)P2, 1, c->partial, &np, Ax, Ay, dV, dVt, En, err, nd);
+        st = sfde_residual_int(c, u, 1, c->nt, rp, (long long)P2, okind, c->partial, &np, Ax, Ay, dV, dVt, En, err,
+                               nd);
     } else {
-        st = sfde_residual_fp64(c, u, 1, c->nt, rp, (long long)P2, 1, c->partial, &np);
+        st = sfde_residual_fp64(c, u, 1, c->nt, rp, (long long)P2, okind, c->partial, &np);
     }
     if (st != SFDE_OK) goto done;
     if ((st = sfde_reduce_partials(c, np, norm2)) != SFDE_OK) goto done;

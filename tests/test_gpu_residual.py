@@ -134,3 +134,24 @@ def test_residual_with_fewer_digits(nd):
     ref, scale = oracle_residual(O, U, None)
     rn = np.sqrt(np.sum(ref ** 2))
     assert abs(nrm - rn) <= 2.0 ** (12 - 8 * nd) * scale + 2.0 ** -20 * rn
+
+
+def test_residual_of_a_zero_iterate_is_the_load():
+    """Pairs of zero slices have no fixed-point unit, and a tiny slice makes the unit so fine that the
+    load does not fit the 128-bit integer sum: the combination keeps the FP64 form there, so
+    rho_n = F_n (n >= 2) and rho_1 = F_1 + B_1 psi_0 (the integer form with the load) still agree with
+    the oracle to FP32 storage accuracy."""
+    nx, ny, nt = 130, 96, 5
+    t = time_grid(nt, 1.0, "uniform")
+    F, _ = gaussian_bump_forcing(3, nx, ny, t)
+    O = osfde.SFDE(0.7, 0.75, 1.0, 0.4, nx, ny, t)
+    U = np.zeros((nt + 1, ny, nx))
+    U[0] = sine_mode_nodal(sine_mode_amplitudes(2), nx, ny)
+    U[3] = 1e-300 * np.random.default_rng(4).standard_normal((ny, nx))   # tiny but nonzero
+    P = sfde.Problem(0.7, 0.75, 1.0, 0.4, nx, ny, t, precision=sfde.PREC_MIXED_FP32)   # plain FP32 output
+    P.set_forcing(F)
+    rho, nrm = gpu_residual(P, np.ascontiguousarray(U), 1)
+    ref, scale = oracle_residual(O, U, F)
+    for n in range(nt):
+        assert np.abs(rho[n] - ref[n]).max() <= 2.0 ** -20 * np.abs(ref[n]).max(), n
+    assert abs(nrm - np.sqrt(np.sum(ref ** 2))) <= 2.0 ** -20 * np.sqrt(np.sum(ref ** 2))
