@@ -235,10 +235,11 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
 // Integer-output digit GEMM, persistent: CTA c takes tiles c, c + gridDim.x, ... of 128 rows x BN
 // columns (columns fastest, so concurrent CTAs share X digit planes in L2).  Warp NDW issues TMA
 // and streams chunks across tiles; warp NDW + 1 issues the MMAs; warps 0..NDW-1 drain, warp w
-// reading TMEM lanes 32 (w % 4).. (the lanes its warp index may access) and BN / 2 columns.  While
+// reading TMEM lanes 32 (w % 4).. (the lanes its warp index may access) and BN / 4 columns.  While
 // the drain folds a K group and stores a finished tile, the producer loads the next chunks, and
-// the next tile's products start as soon as the accumulators are read.
-constexpr int DG_NDW = 8;
+// the next tile's products start as soon as the accumulators are read.  The drain of a group holds
+// the tensor pipe up, so it is spread over sixteen warps.
+constexpr int DG_NDW = 16;
 constexpr int DG_THREADS = 32 * (DG_NDW + 2);
 
 __global__ void __launch_bounds__(DG_THREADS, 1)
@@ -247,7 +248,8 @@ k_digit_gemm_int(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     constexpr int S = PL::S, BN = PL::BN, STAGES = PL::STAGES, KGROUP = PL::KGROUP;
     constexpr int MTILE = BN * KC * 2;
     constexpr int STAGE = S * (XTILE + MTILE);
-    constexpr int CW = BN / 2;                          // columns per drain warp
+    constexpr int CW = BN / (DG_NDW / 4);               // columns per drain warp (16)
+    static_assert(CW == 16, "one 16-column TMEM load per accumulator and drain warp");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE);
@@ -358,9 +360,9 @@ k_digit_gemm_int(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const long long m = (t / ntn) * BM + lq * 32 + lane;
             const int n0 = (int)(t % ntn) * BN;
-            // zt: running sums over the K groups in units of 2^-52, the digit sums d <= 6 added exactly;
-            // per group and 16-column slice zl holds d = 7, 8 (units 2^-64, exact), folded into zt with
-            // one rounding per group (at most half a unit each)
+            // zt: running sums over the K groups in units of 2^-52, the digit sums d <= 6 added exactly,
+            // d = 7 and 8 (units 2^-56 and 2^-64) combined exactly and folded in with one rounding per
+            // group (at most half a unit)
             long long zt[CW];
 #pragma unroll
             for (int j = 0; j < CW; ++j) zt[j] = 0;
@@ -368,39 +370,38 @@ k_digit_gemm_int(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                 ok = __all_sync(0xffffffffu, tc::mbar_wait(accf, (uint32_t)G & 1u, p.err, tc::ERR_WAIT_ACC));
                 tc::tc_fence_after();
                 if (!ok) break;
+                // accumulator a's 16 columns in one of two register sets: the load of a + 1 is in flight
+                // while a is converted (the drain is otherwise a chain of load latencies); accumulator 5
+                // (d = 7) stays in vb until accumulator 6 (d = 8, in va) has arrived
+                const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)cb;
+                uint32_t va[16], vb[16];
+                tc::tmem_ld16_async(base, va);
+                tc::tmem_wait_ld();
+                tc::reg_fence16(va);
 #pragma unroll
-                for (int qs = 0; qs < CW / 16; ++qs) {
-                    long long zl[16];
+                for (int a = 0; a < Plan<true>::S; ++a) {
+                    if (a >= nd) break;
+                    uint32_t* cur = (a & 1) ? vb : va;
+                    uint32_t* nxt = (a & 1) ? va : vb;
+                    if (a + 1 < nd) tc::tmem_ld16_async(base + (uint32_t)((a + 1) * BN), nxt);
+                    const int d = a + 2;
+                    if (d <= 6) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) zl[j] = 0;
-                    // accumulator a's 16 columns in one of two register sets: the load of a + 1 is in
-                    // flight while a is converted (the drain is otherwise a chain of load latencies)
-                    const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(cb + qs * 16);
-                    uint32_t va[16], vb[16];
-                    tc::tmem_ld16_async(base, va);
-                    tc::tmem_wait_ld();
-                    tc::reg_fence16(va);
-#pragma unroll
-                    for (int a = 0; a < Plan<true>::S; ++a) {
-                        if (a >= nd) break;
-                        uint32_t* cur = (a & 1) ? vb : va;
-                        uint32_t* nxt = (a & 1) ? va : vb;
-                        if (a + 1 < nd) tc::tmem_ld16_async(base + (uint32_t)((a + 1) * BN), nxt);
-                        const int d = a + 2;
-                        const int sh = d <= 6 ? 52 - 8 * d : 8 * (8 - d);
+                        for (int j = 0; j < 16; ++j)   // exact, |value| < 2^24
+                            zt[j] += (long long)__float2int_rn(__uint_as_float(cur[j])) << (52 - 8 * d);
+                    } else if (a + 1 == nd) {
+                        // the last accumulator: d = 7 alone (nd = 6), or d = 8 in va with d = 7 in vb
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            const long long sv = (long long)__float2int_rn(__uint_as_float(cur[j]));  // exact, |sv| < 2^24
-                            if (d <= 6) zt[qs * 16 + j] += sv << sh;
-                            else zl[j] += sv << sh;
-                        }
-                        if (a + 1 < nd) {
-                            tc::tmem_wait_ld();
-                            tc::reg_fence16(nxt);
+                            long long zl = (long long)__float2int_rn(__uint_as_float(vb[j])) << 8;
+                            if (d == 8) zl += (long long)__float2int_rn(__uint_as_float(va[j]));
+                            zt[j] += (zl + 2048) >> 12;
                         }
                     }
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) zt[qs * 16 + j] += (zl[j] + 2048) >> 12;
+                    if (a + 1 < nd) {
+                        tc::tmem_wait_ld();
+                        tc::reg_fence16(nxt);
+                    }
                 }
                 tc::tc_fence_before();
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(tfree)) : "memory");
