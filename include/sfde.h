@@ -59,10 +59,12 @@ typedef enum {
                                   operands, about 2^-20 relative), three times the tensor work of
                                   TF32 for corrections about 2^10 times more accurate, so fewer
                                   refinement steps (no counterpart in the paper)                 */
-    SFDE_PREC_MIXED_AUTO = 4   /* BF16 where the fused BF16 step applies (padded P_x = P_y in
-                                  {128, 256}) and N_t <= 1024, else TF32: the low-precision fixed
-                                  point drifts with the rounding accumulated over N_t nearly undamped
-                                  steps, and TF32 rounds 4x finer (no counterpart in the paper) */
+    SFDE_PREC_MIXED_AUTO = 4   /* FP32: with the inner solve held in the step's eigenbasis (the
+                                  default for FP32 storage, see sfde_tuning.modal_chains) a
+                                  refinement step costs about one FP64 residual, and FP32 corrections
+                                  need the fewest of them -- measured faster than the fused BF16
+                                  steps too (N = 255, N_t = 1024: 24.8 against 49.1 ms per solve)
+                                  (no counterpart in the paper)                                 */
 } sfde_precision;
 
 /* Spatial matrices of the fully discrete scheme (2.4). */
@@ -339,8 +341,10 @@ typedef struct {
     int fused_pair;      /* fused BF16 step at P = 256: 1 a CTA pair per slice where 2 x batch <= SMs,
                             else per two slices (default); 2 always per slice; 3 always per two
                             slices; 0 one CTA per slice                                        */
-    int modal_chains;    /* F-relaxations in the step's eigenbasis: 1 coarse levels (default),
-                            2 every level, 3 every level with BF16 operands, 0 none            */
+    int modal_chains;    /* F-relaxations in the step's eigenbasis: 1 coarse levels (the
+                            default with BF16), 2 every level, 3 every level with BF16 operands,
+                            0 none; 4 the whole inner solve in the eigenbasis (the default with
+                            TF32/FP32 working precision; as 1 with BF16)                      */
     int inner_cycles;    /* V-cycles per refinement step when mgrit_opts.inner_cycles is 0;
                             0 = 4 (BF16) / 5 (TF32)                                           */
     double ms;           /* measured solve time of this choice (milliseconds; 0 = unmeasured)  */

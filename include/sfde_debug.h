@@ -99,9 +99,14 @@ sfde_status sfde_debug_set_fused_pair(sfde_ctx* ctx, int mode);
  * elementwise FP32 recurrence over the interval and one inverse transform of all F-points) instead
  * of as chained fused steps.  enable 1 (default): the coarse levels l >= 1; 2: every level, the fine
  * one too (its buffers, two more copies of the fine level's low-precision vector, are allocated at
- * the next solve); 3: 2 with BF16 operands (whose chained steps round most), 1 with TF32; 0: none.  Both forms compute u_{im+j} = Phi(u_{im+j-1}) + g_{im+j} (Algorithm 1's
- * F-relaxation), rounded differently.  Takes effect at the next mgrit_solve; other values give
- * SFDE_EINVAL.
+ * the next solve); 3: 2 with BF16 operands (whose chained steps round most), 1 with TF32; 0: none;
+ * 4: with FP32 storage (TF32 and FP32 working precisions) the whole inner solve in the eigenbasis:
+ * the correction right-hand sides transformed once per refinement step (V_y^T rho_n V_x scaled by
+ * 1/(1 + tau_n sigma)), every level's iterate and right-hand side kept as FP32 modal values, every
+ * relaxation, residual, correction and coarsest sweep an elementwise recurrence, and the correction
+ * transformed back once (with BF16 storage 4 acts as 1).  All forms compute u_{im+j} =
+ * Phi(u_{im+j-1}) + g_{im+j} (Algorithm 1's F-relaxation), rounded differently.  Takes effect at the
+ * next mgrit_solve; other values give SFDE_EINVAL.
  */
 sfde_status sfde_debug_set_modal_chains(sfde_ctx* ctx, int enable);
 

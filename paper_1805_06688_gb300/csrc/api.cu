@@ -160,6 +160,8 @@ static sfde_status setup_impl(double beta, double gamma, double kx, double ky, c
             if ((st = sfde_setup_direction(c->x, nx, beta, om[1] - om[0], c->stream)) != SFDE_OK) break;
             if ((st = sfde_setup_direction(c->y, ny, gamma, om[3] - om[2], c->stream)) != SFDE_OK) break;
             if (op == SFDE_OP_P1 && (st = sfde_p1_setup(c)) != SFDE_OK) break;
+            // FP32 storage: the inner solve held in the step's eigenbasis by default
+            if (prec != SFDE_PREC_FP64 && sfde_mixed_kind(c) != 0) c->modal_chains = 4;
             std::vector<double> dt(nt);
             for (int n = 0; n < nt; ++n) dt[n] = t[n + 1] - t[n];
             cudaError_t e;

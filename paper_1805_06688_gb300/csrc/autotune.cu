@@ -19,7 +19,7 @@
 namespace {
 
 bool tuning_valid(const sfde_tuning& t) {
-    return t.fused_pair >= 0 && t.fused_pair <= 3 && t.modal_chains >= 0 && t.modal_chains <= 3 &&
+    return t.fused_pair >= 0 && t.fused_pair <= 3 && t.modal_chains >= 0 && t.modal_chains <= 4 &&
            t.inner_cycles >= 0 && t.inner_cycles <= 64;
 }
 
@@ -120,11 +120,17 @@ sfde_status autotune_impl(sfde_ctx* c, const mgrit_opts* opts, const char* cache
     }
     // F-relaxations of the fine level as chained steps or in the eigenbasis (the coarse levels' are
     // always in the eigenbasis), times the default V-cycles per refinement step, 3 or 5 (not when the
-    // options fix it); the CTA-pair forms of the fused step forced either way where that step applies
+    // options fix it); the whole inner solve in the eigenbasis with 3, 5, 8 or the default V-cycles;
+    // the CTA-pair forms of the fused step forced either way where that step applies
     std::vector<sfde_tuning> cand;
     for (int mc : {1, 2})
         for (int ic : {0, 3, 5})
             if (ic == 0 || opts->inner_cycles == 0) cand.push_back({1, mc, ic, 0.0});
+    // the whole inner solve in the eigenbasis (FP32 storage): its V-cycles are elementwise, so more
+    // of them per refinement step are worth a trial
+    if (sfde_mixed_kind(c) != 0)
+        for (int ic : {0, 3, 5, 8})
+            if (ic == 0 || opts->inner_cycles == 0) cand.push_back({1, 4, ic, 0.0});
     if (sfde_mixed_kind(c) == 0 && sfde_fused_supported(0, c->x.P, c->y.P) && c->x.P == c->y.P &&
         sfde_fused_pair_supported(c->x.P)) {
         cand.push_back({2, 1, 0, 0.0});

@@ -164,6 +164,85 @@ __global__ void __launch_bounds__(256) k_modal_scan(const T* __restrict__ Uc, co
     }
 }
 
+// The inner solve held in the step's eigenbasis (modal_chains 4, FP32 storage).  With the inner
+// solve's levels transformed once, every step is the per-mode recurrence v_j = f_j v_{j-1} + g_j:
+// runs over `len` points of `grid.y` groups, v_0 = U[i ucs], g_j = G[i gis + j + gj0], v_j stored to
+// Y[i yis + j + yj0], f_j the modal factor of the step with dt[i dis + j - 1] (as k_modal_scan);
+// plain FP32 stores (the values stay in the eigenbasis, nothing feeds a TF32 product step by step).
+__global__ void __launch_bounds__(256) k_modal_run(const float* __restrict__ U, long long ucs, const float* __restrict__ G,
+                                                   long long gis, long long gj0, float* __restrict__ Y, long long yis,
+                                                   long long yj0, int len, int Px, size_t P2,
+                                                   const float* __restrict__ lamx, const float* __restrict__ lamy,
+                                                   float kx, float ky, const double* __restrict__ dt, long long dis,
+                                                   int scheme) {
+    const long long i = blockIdx.y;
+    const size_t e = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (e >= P2) return;
+    const int x = (int)(e % (size_t)Px), y = (int)(e / (size_t)Px);
+    const float sy = ky * lamy[y];
+    float sg[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sg[q] = fmaf(kx, lamx[x + q], sy);
+    float4 v = *(const float4*)(U + (size_t)(i * ucs) * P2 + e);
+    const bool be = scheme == SCHEME_BE;
+    for (int j0 = 1; j0 < len; j0 += 8) {
+        float4 gv[8];
+        float cst[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (j0 + u < len) {
+                const float dtj = (float)dt[i * dis + j0 + u - 1];
+                cst[u] = be ? dtj : 0.5f * dtj;
+                gv[u] = *(const float4*)(G + (size_t)(i * gis + j0 + u + gj0) * P2 + e);
+            }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (j0 + u < len) {
+                float f[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    f[q] = 1.f / fmaf(cst[u], sg[q], 1.f);
+                    if (!be) f[q] = fmaf(2.f, f[q], -1.f);
+                }
+                v.x = fmaf(f[0], v.x, gv[u].x);
+                v.y = fmaf(f[1], v.y, gv[u].y);
+                v.z = fmaf(f[2], v.z, gv[u].z);
+                v.w = fmaf(f[3], v.w, gv[u].w);
+                *(float4*)(Y + (size_t)(i * yis + j0 + u + yj0) * P2 + e) = v;
+            }
+    }
+}
+
+// The C-point residuals of the eigenbasis recurrence, injected into the coarse level:
+// out[k - 1] = f_{km} u_{km-1} + g_{km} - u_{km}, k = 1 + blockIdx.y (plain FP32 stores)
+__global__ void __launch_bounds__(256) k_modal_resid(const float* __restrict__ u, const float* __restrict__ g,
+                                                     float* __restrict__ out, int m, int Px, size_t P2,
+                                                     const float* __restrict__ lamx, const float* __restrict__ lamy,
+                                                     float kx, float ky, const double* __restrict__ dt, int scheme) {
+    const long long k = (long long)blockIdx.y + 1, n = k * m;
+    const size_t e = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (e >= P2) return;
+    const int x = (int)(e % (size_t)Px), y = (int)(e / (size_t)Px);
+    const float sy = ky * lamy[y];
+    const float dtn = (float)dt[n - 1];
+    const bool be = scheme == SCHEME_BE;
+    const float cst = be ? dtn : 0.5f * dtn;
+    const float4 a = *(const float4*)(u + (size_t)(n - 1) * P2 + e), b = *(const float4*)(u + (size_t)n * P2 + e);
+    const float4 gg = *(const float4*)(g + (size_t)n * P2 + e);
+    float f[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        f[q] = 1.f / fmaf(cst, fmaf(kx, lamx[x + q], sy), 1.f);
+        if (!be) f[q] = fmaf(2.f, f[q], -1.f);
+    }
+    float4 r;
+    r.x = fmaf(f[0], a.x, gg.x) - b.x;
+    r.y = fmaf(f[1], a.y, gg.y) - b.y;
+    r.z = fmaf(f[2], a.z, gg.z) - b.z;
+    r.w = fmaf(f[3], a.w, gg.w) - b.w;
+    *(float4*)(out + (size_t)(k - 1) * P2 + e) = r;
+}
+
 unsigned grid_for(size_t n) {
     size_t g = (n + 255) / 256;
     return (unsigned)std::min<size_t>(std::max<size_t>(g, 1), 4 * 152);
@@ -458,6 +537,7 @@ struct LpEngine {
     int m, L, relax, scheme;
     long long steps = 0;
     bool skip = false;   // down-cycle without relaxation (first V-cycle with skip_first_down)
+    bool full = false;   // every level's u and g held in the step's eigenbasis (modal_chains 4)
 
     size_t P2() const { return c->P2(); }
     char* slice(void* base, long long s) const { return (char*)base + (size_t)s * P2() * M->esz; }
@@ -580,6 +660,48 @@ struct LpEngine {
         return SFDE_OK;
     }
 
+    // In place, slices n0 .. n0 + batch - 1 of `buf` (ns slices): X -> (V_y^T X V_x) / (1 + tau_n sigma),
+    // the right-hand side of S_n^{-1} X in the step's eigenbasis (the first two products of a solve)
+    sfde_status to_modal_solve(void* buf, long long ns, int n0, int batch) {
+        const int Px = c->x.P, Py = c->y.P;
+        const long long P2l = (long long)P2();
+        for (int b0 = 0; b0 < batch; b0 += (int)M->ws) {
+            const int nb = std::min<int>(batch - b0, (int)M->ws);
+            CUtensorMap a1, a2;
+            SFDE_TRY(map_for(M, buf, Py, Px, 1, ns, &a1));
+            SFDE_TRY(map_for(M, M->T1, Px, Py, 1, (long long)M->ws, &a2));
+            TcArgs p{};   // (X V_x)^T
+            p.batch = nb; p.err = M->err;
+            p.R = Py; p.C = Px; p.Cout = Px; p.BN = sfde_tc_tile_n(Px); p.s0 = n0 + b0; p.ds = 1;
+            p.out = M->T1; p.out_stride = P2l;
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_STORE, a1, M->gVTx, p, c->stream, c->y.n, c->x.n, c->x.n,
+                                  M->kind == 2 ? &M->oVTx : nullptr));
+            TcArgs q{};   // (T1 V_y)^T = V_y^T X V_x, scaled by 1 / (1 + tau_n sigma)
+            q.batch = nb; q.err = M->err;
+            q.R = Px; q.C = Py; q.Cout = Py; q.BN = sfde_tc_tile_n(Py); q.s0 = 0; q.ds = 1;
+            q.out = slice(buf, (long long)n0 + b0); q.out_stride = P2l;
+            q.e.lamx = M->lamx; q.e.lamy = M->lamy; q.e.kx = (float)c->kx; q.e.ky = (float)c->ky;
+            q.e.dt = c->dt0; q.e.n0 = n0 + b0; q.e.dn = 1; q.e.scheme = SCHEME_SOLVE;
+            SFDE_TRY(sfde_tc_gemm(c, M->kind, TC_EPI_SCALE, a2, M->gVTy, q, c->stream, c->x.n, c->y.n, c->y.n,
+                                  M->kind == 2 ? &M->oVTy : nullptr));
+        }
+        return SFDE_OK;
+    }
+
+    // k_modal_run over `groups` runs of `len` points (all arrays FP32 slices of the level)
+    sfde_status modal_run(const void* U, long long ucs, const void* G, long long gis, long long gj0, void* Y,
+                          long long yis, long long yj0, int len, int groups, const double* dt, long long dis,
+                          int sch) {
+        const size_t P2s = P2();
+        dim3 grid((unsigned)((P2s / 4 + 255) / 256), (unsigned)groups);
+        k_modal_run<<<grid, 256, 0, c->stream>>>((const float*)U, ucs, (const float*)G, gis, gj0, (float*)Y, yis, yj0,
+                                                 len, c->x.P, P2s, M->lamx, M->lamy, (float)c->kx, (float)c->ky, dt,
+                                                 dis, sch);
+        sfde_count_launch(c);
+        SFDE_CUDA(cudaGetLastError());
+        return SFDE_OK;
+    }
+
     // V_y Y_b V_x^T for the slices b < batch of `src` (ns slices) -> slice b of dst, or with oskip > 0
     // the b-th F-point, slice b + b / oskip + 1 (intervals of oskip + 1 points): two slice GEMMs
     // through T3, in chunks of whole intervals
@@ -646,6 +768,10 @@ struct LpEngine {
     sfde_status frelax(int l) {
         LpLevel& Lv = M->lev[l];
         const int nc = Lv.N / m;
+        if (full) {   // every interval's F-points from its C-point, in place, per mode
+            steps += (long long)nc * (m - 1);
+            return modal_run(Lv.u, m, Lv.g, m, 0, Lv.u, m, 0, m, nc, Lv.dt, m, l == 0 ? SCHEME_CN : scheme);
+        }
         // (the C-point transforms go to T2, ws slices: more intervals than that keep chained steps)
         if (modal(l) && nc <= (int)M->ws && m - 1 <= (int)M->ws) {
             // C-point values transformed (T2), the interval recurrences, all F-points transformed back
@@ -665,6 +791,11 @@ struct LpEngine {
 
     sfde_status crelax(int l) {
         LpLevel& Lv = M->lev[l];
+        if (full) {   // u_{(k+1)m} from u_{(k+1)m-1}: runs of two points starting at the last F-points
+            steps += Lv.N / m;
+            return modal_run(slice(Lv.u, m - 1), m, slice(Lv.g, m - 1), m, 0, slice(Lv.u, m - 1), m, 0, 2, Lv.N / m,
+                             Lv.dt + (m - 1), m, l == 0 ? SCHEME_CN : scheme);
+        }
         return lstep(l, Lv.N / m, m - 1, m, m, m, slice(Lv.u, m), m, nullptr, nullptr, nullptr);
     }
 
@@ -687,12 +818,29 @@ struct LpEngine {
         else
             k_lp_diff<F32><<<grid_for(P2()), 256, 0, c->stream>>>((F32*)Cv.g, (const F32*)Lv.g, (const F32*)Lv.u, P2());
         sfde_count_launch(c);
+        if (full) {
+            if (partial) return SFDE_EINVAL;   // the inner solve takes no norm
+            const size_t P2s = P2();
+            dim3 grid((unsigned)((P2s / 4 + 255) / 256), (unsigned)(Lv.N / m));
+            k_modal_resid<<<grid, 256, 0, c->stream>>>((const float*)Lv.u, (const float*)Lv.g, (float*)slice(Cv.g, 1), m,
+                                                       c->x.P, P2s, M->lamx, M->lamy, (float)c->kx, (float)c->ky,
+                                                       Lv.dt, l == 0 ? SCHEME_CN : scheme);
+            sfde_count_launch(c);
+            steps += Lv.N / m;
+            if (npart) *npart = 0;
+            SFDE_CUDA(cudaGetLastError());
+            return SFDE_OK;
+        }
         return lstep(l, Lv.N / m, m - 1, m, m, m, slice(Cv.g, 1), 1, slice(Lv.u, m), partial, npart);
     }
 
     sfde_status coarsest(int l) {
         LpLevel& Lv = M->lev[l];
         SFDE_CUDA(cudaMemcpyAsync(Lv.u, Lv.g, P2() * M->esz, cudaMemcpyDeviceToDevice, c->stream));
+        if (full) {   // u_n = f_n u_{n-1} + g_n, n = 1..N, one run from u_0 = g_0
+            steps += Lv.N;
+            return modal_run(Lv.g, 0, Lv.g, 0, 0, Lv.u, 0, 0, Lv.N + 1, 1, Lv.dt, 0, l == 0 ? SCHEME_CN : scheme);
+        }
         // u_n = Phi(u_{n-1}) + g_n, n = 1..N: one recurrence per mode in the eigenbasis (u_0 = g_0,
         // so its transform is the first transformed right-hand side), or the fused kernel chaining
         // all N steps in one launch
@@ -717,7 +865,7 @@ struct LpEngine {
         dim3 grid(grid_for(P2()) < 64 ? grid_for(P2()) : 64, Cv.N + 1);
         if (M->kind == 0)
             k_lp_axpy_strided<__nv_bfloat16><<<grid, 256, 0, c->stream>>>((__nv_bfloat16*)Lv.u, (long long)m * P2(), (const __nv_bfloat16*)Cv.u, (long long)P2(), P2());
-        else if (M->kind == 1)
+        else if (M->kind == 1 && !full)   // nodal values feed TF32 products: rounded; modal values stay FP32
             k_lp_axpy_strided<float><<<grid, 256, 0, c->stream>>>((float*)Lv.u, (long long)m * P2(), (const float*)Cv.u, (long long)P2(), P2());
         else
             k_lp_axpy_strided<F32><<<grid, 256, 0, c->stream>>>((F32*)Lv.u, (long long)m * P2(), (const F32*)Cv.u, (long long)P2(), P2());
@@ -728,7 +876,8 @@ struct LpEngine {
 
     sfde_status solve(int l) {
         // the level's right-hand sides stay fixed while it is visited: transformed once
-        if (modal(l)) SFDE_TRY(to_modal(M->lev[l].g, M->lev[l].nalloc, 0, 1, M->lev[l].N + 1, M->lev[l].gm, 1));
+        if (!full && modal(l))
+            SFDE_TRY(to_modal(M->lev[l].g, M->lev[l].nalloc, 0, 1, M->lev[l].N + 1, M->lev[l].gm, 1));
         if (l == L - 1) return coarsest(l);
         if (!skip) SFDE_TRY(relaxation(l));
         SFDE_TRY(residual(l, nullptr, nullptr));
@@ -751,6 +900,11 @@ sfde_status enqueue_inner_part(sfde_ctx* c, SfdeMixed* M, LpEngine& E, double* U
     const size_t P2 = c->P2();
     if (part == 0) {
         SFDE_CUDA(cudaMemsetAsync(L0.g, 0, P2 * M->esz, c->stream));
+        if (E.full) {   // g^_n = (V_y^T rho_n V_x) / (1 + tau_n sigma): the solve, left in the eigenbasis
+            SFDE_TRY(E.to_modal_solve(L0.g, L0.nalloc, 1, c->nt));
+            SFDE_CUDA(cudaMemsetAsync(L0.u, 0, P2 * M->esz * L0.nalloc, c->stream));
+            return SFDE_OK;
+        }
         SFDE_TRY(E.step(L0.g, L0.nalloc, 1, 1, c->nt, true, SCHEME_SOLVE, c->dt0, 1, 1, E.slice(L0.g, 1), 1,
                         nullptr, nullptr, nullptr, nullptr));
         SFDE_CUDA(cudaMemsetAsync(L0.u, 0, P2 * M->esz * L0.nalloc, c->stream));
@@ -772,10 +926,16 @@ sfde_status enqueue_inner_part(sfde_ctx* c, SfdeMixed* M, LpEngine& E, double* U
     if (E.L == 1) SFDE_TRY(E.coarsest(0));
     else SFDE_TRY(E.relaxation(0));
     const size_t n = P2 * (size_t)c->nt;
+    // with the inner solve in the eigenbasis, E_n = V_y e^_n V_x^T into g_0 (no longer needed)
+    const void* Ev = E.slice(L0.u, 1);
+    if (E.full) {
+        SFDE_TRY(E.from_modal(E.slice(L0.u, 1), L0.nalloc - 1, c->nt, E.slice(L0.g, 1), 0));
+        Ev = E.slice(L0.g, 1);
+    }
     if (kind == 0)
-        k_add_correction<__nv_bfloat16><<<grid_for(n), 256, 0, c->stream>>>(U + P2, (const __nv_bfloat16*)E.slice(L0.u, 1), n);
+        k_add_correction<__nv_bfloat16><<<grid_for(n), 256, 0, c->stream>>>(U + P2, (const __nv_bfloat16*)Ev, n);
     else   // FP32 storage (kinds 1 and 2) read as FP32
-        k_add_correction<float><<<grid_for(n), 256, 0, c->stream>>>(U + P2, (const float*)E.slice(L0.u, 1), n);
+        k_add_correction<float><<<grid_for(n), 256, 0, c->stream>>>(U + P2, (const float*)Ev, n);
     sfde_count_launch(c);
     SFDE_CUDA(cudaGetLastError());
     return SFDE_OK;
@@ -826,6 +986,7 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
     double tub = 0.0;
     SFDE_TRY(sfde_choose_coarse(c, o->m, o->coarse, &coarse, &tub));
     LpEngine E{c, M, o->m, L, o->relax, coarse == SFDE_COARSE_CN ? SCHEME_CN : SCHEME_BE};
+    E.full = c->modal_chains == 4 && kind != 0;   // BF16 storage keeps the nodal levels
     // inner V-cycles per refinement step: enough for the inner error to reach the low-precision
     // floor (about 2e-2 BF16, 3e-3 TF32) at MGRIT contraction ~0.3 per V-cycle; with FP32 products
     // the floor is far lower and 3 V-cycles set the contraction.  (Raising K when the
@@ -1004,7 +1165,7 @@ extern "C" sfde_status sfde_debug_residual_digits(double prev, double res0, int*
 }
 
 extern "C" sfde_status sfde_debug_set_modal_chains(sfde_ctx* c, int enable) {
-    if (!c || enable < 0 || enable > 3) return SFDE_EINVAL;
+    if (!c || enable < 0 || enable > 4) return SFDE_EINVAL;
     c->modal_chains = enable;
     return SFDE_OK;
 }

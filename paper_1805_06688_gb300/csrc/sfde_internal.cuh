@@ -256,7 +256,7 @@ inline int sfde_mixed_kind(const sfde_ctx* c) {
     if (c->precision == SFDE_PREC_MIXED_BF16) return 0;
     if (c->precision == SFDE_PREC_MIXED_TF32) return 1;
     if (c->precision == SFDE_PREC_MIXED_FP32) return 2;
-    return (sfde_fused_supported(0, c->x.P, c->y.P) && c->nt <= 1024) ? 0 : 1;
+    return 2;   // SFDE_PREC_MIXED_AUTO
 }
 sfde_status sfde_fused_prepare();
 // O1, O2: W_x^T, W_y^T (V_x^T, V_y^T for the solve); O3, O4: V_x, V_y -- K-major P x P BF16 maps

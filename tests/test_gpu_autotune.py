@@ -42,8 +42,10 @@ def test_autotune_applies_caches_and_keeps_the_fixed_point(prec, tmp_path):
     cache = tmp_path / "tune.txt"
     win = P.autotune(cache_path=str(cache), **OPTS)
     # a candidate of the fixed grid: eigenbasis on the coarse levels or every level, 3/5 or default
-    # V-cycles, or a forced CTA-pair form of the fused step
-    assert (win.modal_chains, win.inner_cycles) in {(1, 0), (1, 3), (1, 5), (2, 0), (2, 3), (2, 5)} or \
+    # V-cycles, the whole inner solve in the eigenbasis (FP32 storage) with 3/5/8 or default V-cycles,
+    # or a forced CTA-pair form of the fused step
+    full = {(4, 0), (4, 3), (4, 5), (4, 8)} if prec != sfde.PREC_MIXED_BF16 else set()
+    assert (win.modal_chains, win.inner_cycles) in {(1, 0), (1, 3), (1, 5), (2, 0), (2, 3), (2, 5)} | full or \
         (win.fused_pair in (2, 3) and win.modal_chains == 1 and win.inner_cycles == 0)
     assert win.ms > 0.0 and np.isfinite(win.ms)
     assert _fields(P.tuning()) == _fields(win)

@@ -24,14 +24,15 @@ def _err(U, ref):
     return float(np.abs(U - ref).max() / np.abs(ref).max())
 
 
-@pytest.mark.parametrize("modal", [3, 1, 0, 2])
+@pytest.mark.parametrize("modal", [3, 1, 0, 2, 4])
 @pytest.mark.parametrize("name,prec", PRECS)
 @pytest.mark.parametrize("nx,ny,nt,m,grid,levels", [(20, 13, 64, 4, "graded", 3), (31, 31, 64, 4, "uniform", 2),
                                                      (100, 70, 96, 4, "uniform", 8)])
 def test_mixed_matches_sequential(name, prec, nx, ny, nt, m, grid, levels, modal):
     """Mixed precision against the oracle's sequential solution, with the coarse levels' sweeps in the
     step's eigenbasis (modal 1, the default), every level's (modal 2), by operand type (modal 3: all
-    levels with BF16, the coarse ones with TF32) and none (modal 0)."""
+    levels with BF16, the coarse ones with TF32), none (modal 0), and the whole inner solve in the
+    eigenbasis (modal 4; with BF16 storage as modal 1)."""
     t = time_grid(nt, 1.0, grid)
     F, _ = gaussian_bump_forcing(5, nx, ny, t)
     psi = sine_mode_nodal(sine_mode_amplitudes(4), nx, ny)
@@ -53,10 +54,10 @@ def test_modal_chains_setting_range():
     P = sfde.Problem(0.6, 0.9, 1.0, 0.5, 31, 31, time_grid(16, 1.0, "uniform"), precision=sfde.PREC_MIXED_BF16)
     L = sfde.lib()
     L.sfde_debug_set_modal_chains.argtypes = [ctypes.c_void_p, ctypes.c_int]
-    assert L.sfde_debug_set_modal_chains(P.ctx, 4) == sfde.SFDE_EINVAL
+    assert L.sfde_debug_set_modal_chains(P.ctx, 5) == sfde.SFDE_EINVAL
     assert L.sfde_debug_set_modal_chains(P.ctx, -1) == sfde.SFDE_EINVAL
     assert L.sfde_debug_set_modal_chains(None, 1) == sfde.SFDE_EINVAL
-    for v in (0, 2, 1, 3):
+    for v in (0, 2, 1, 3, 4):
         assert L.sfde_debug_set_modal_chains(P.ctx, v) == 0
 
 
@@ -108,26 +109,29 @@ def test_mixed_sine_N255_Nt1024_full_size(name, prec):
     assert per < 1e-4, per
 
 
-@pytest.mark.parametrize("name,prec", PRECS)
-def test_mixed_bump_N511_Nt2048_full_size(name, prec):
+@pytest.mark.parametrize("name,prec,modal,ic", [(n, p, 2, 3) for n, p in PRECS] +
+                         [("tf32", sfde.PREC_MIXED_TF32, 4, 5), ("tf32", sfde.PREC_MIXED_TF32, 4, 8),
+                          ("fp32", sfde.PREC_MIXED_FP32, 4, 3)])
+def test_mixed_bump_N511_Nt2048_full_size(name, prec, modal, ic):
     """The N = 511 workload (padded P = 512: four-GEMM tensor-core steps and the K-grouped integer
     residual), stopped on the FP64 space-time residual at 1e-8 with the fine level's F-relaxations in
-    the eigenbasis and 3 V-cycles per refinement step (the benchmark's tuned choice), against the exact
-    sequential solution at all 2049 time points."""
+    the eigenbasis and 3 V-cycles per refinement step, or the whole inner solve in the eigenbasis
+    (modal 4) with 3 to 8 V-cycles, against the exact sequential solution at all 2049 time points."""
     w = WORKLOADS["bump_N511_Nt2048"]
     t = w.t()
     psi, F = w.initial(), w.forcing()
     P = sfde.Problem(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t, precision=prec)
     P.set_initial(psi)
     P.set_forcing(F)
-    P.set_tuning(fused_pair=1, modal_chains=2, inner_cycles=3)
+    P.set_tuning(fused_pair=1, modal_chains=modal, inner_cycles=ic)
     U = torch.zeros((w.nt + 1, w.ny, w.nx), dtype=torch.float64, device="cuda")
     _, st = P.mgrit(U=U, m=w.m, max_levels=32, coarse=sfde.COARSE_AUTO, rel_tol=1e-8, max_iter=100,
                     stop_kind=sfde.STOP_SFORM)
     assert st.converged
     O = osfde.SFDE(w.beta, w.gamma, w.kx, w.ky, w.nx, w.ny, t)
     glob, per = _all_slice_errors(U, O, psi, F)
-    print(f"bump_N511_Nt2048 {name}: space-time {glob:.2e}, worst slice-relative {per:.2e}")
+    print(f"bump_N511_Nt2048 {name} modal {modal} ic {ic}: {st.iters} steps, {st.seconds * 1e3:.1f} ms, "
+          f"space-time {glob:.2e}, worst slice-relative {per:.2e}")
     assert glob < 1e-8, glob
     assert per < 1e-6, per
 
@@ -216,9 +220,10 @@ def test_mixed_shishkin_grid(name, prec):
 def test_mixed_graded_N1023_Nt4096_full_size():
     """The largest workload: 1023^2 nodes (padded P = 1024, dense 1023 x 1023 Toeplitz matrices),
     4096 steps on the graded grid t_n = (n/N)^2 (the fine propagator changes at every step), m = 16,
-    operands chosen by SFDE_PREC_MIXED_AUTO (TF32 here), stopped on the FP64 space-time residual at
-    1e-8.  Against the exact sequential solution at every C-point of the fine level (every 16th time
-    point) and at the first 16 steps, where the grid's steps are smallest."""
+    operands chosen by SFDE_PREC_MIXED_AUTO (FP32 here, inner solve in the eigenbasis), stopped on the
+    FP64 space-time residual at 1e-8.  Against the exact sequential solution at every C-point of the
+    fine level (every 16th time point) and at the first 16 steps, where the grid's steps are
+    smallest."""
     w = WORKLOADS["graded_N1023_Nt4096"]
     t = w.t()
     psi, F = w.initial(), w.forcing()
@@ -228,7 +233,7 @@ def test_mixed_graded_N1023_Nt4096_full_size():
     U = torch.zeros((w.nt + 1, w.ny, w.nx), dtype=torch.float64, device="cuda")
     _, st = P.mgrit(U=U, m=w.m, max_levels=32, coarse=sfde.COARSE_AUTO, rel_tol=1e-8, max_iter=100,
                     stop_kind=sfde.STOP_SFORM)
-    assert st.converged and st.lp_kind == 1
+    assert st.converged and st.lp_kind == 2
     keep = sorted(set(range(0, w.nt + 1, w.m)) | set(range(1, 17)))
     Uk = U[torch.tensor(keep, device="cuda")].cpu().numpy()
     del U

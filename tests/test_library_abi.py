@@ -210,7 +210,7 @@ def test_autotune_cache_file_needs_no_gpu(tmp_path):
     assert found.value == 1 and (t.fused_pair, t.modal_chains, t.inner_cycles) == (1, 3, 5)
     assert L.sfde_debug_tune_cache(path, b"P128x128_nt64", 0, ctypes.byref(t), ctypes.byref(found)) == 0
     assert found.value == 0
-    bad = T(1, 4, 0, 1.0)
+    bad = T(1, 5, 0, 1.0)
     assert L.sfde_debug_tune_cache(path, b"k", 1, ctypes.byref(bad), None) == sfde.SFDE_EINVAL
     assert L.sfde_debug_tune_cache(path, b"two words", 0, ctypes.byref(t), ctypes.byref(found)) == sfde.SFDE_EINVAL
     assert L.sfde_debug_tune_cache(path, b"", 0, ctypes.byref(t), ctypes.byref(found)) == sfde.SFDE_EINVAL
