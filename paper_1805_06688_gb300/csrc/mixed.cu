@@ -19,6 +19,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <climits>
 #include <new>
 #include <vector>
 
@@ -1028,8 +1029,11 @@ sfde_status sfde_mgrit_mixed(sfde_ctx* c, const mgrit_opts* o, mgrit_stats* st) 
         for (;;) {
             int np = 0;
             if (M->use_oz) {
+                // the first iterate is psi_0 followed by zeros (unless drawn at random): from the pair
+                // (U_1, U_2) on, the residual is the load alone
                 SFDE_TRY(sfde_residual_int(c, U, 1, c->nt, E.slice(L0.g, 1), (long long)P2, kind, c->partial, &np,
-                                           M->oAx, M->oAy, M->oz_dV, M->oz_dVt, M->oz_E, M->err, nd));
+                                           M->oAx, M->oAy, M->oz_dV, M->oz_dVt, M->oz_E, M->err, nd,
+                                           it == 1 && !o->init_seed ? 2 : INT_MAX));
                 digit_products += nd * (nd + 1) / 2;
             } else {
                 SFDE_TRY(sfde_residual_fp64(c, U, 1, c->nt, E.slice(L0.g, 1), (long long)P2, kind, c->partial, &np));

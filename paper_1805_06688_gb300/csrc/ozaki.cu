@@ -41,13 +41,15 @@ constexpr int TMEM_COLS = 512;
 //     p + q <= 7 in 12 accumulators; tiles of N = 32 columns, K summed in one group.
 //   Integer output: 7 digits per operand, all of magnitude <= 128, K summed in groups of 128: every
 //     product is at most 128^3 = 2^21 per group, so all (at most 7) products of one digit sum share
-//     an accumulator: the 28 products with p + q <= 8 in 7 accumulators, tiles of N = 64 columns.
+//     an accumulator: the 28 products with p + q <= 8 in 7 accumulators of N = 32 columns, twice
+//     (2 x 224 of the 512 TMEM columns), so that one K group's products run while the previous
+//     group is drained.
 template <bool INT_OUT> struct Plan;
 template <> struct Plan<false> {
     static constexpr int S = 6, NPROD = 21, NACC = 12, BN = 32, STAGES = 3, KGROUP = 256;
 };
 template <> struct Plan<true> {
-    static constexpr int S = 7, BN = 64, STAGES = 2, KGROUP = 128;
+    static constexpr int S = 7, BN = 32, STAGES = 3, KGROUP = 128, NBUF = 2;
 };
 
 // FP64-output plan: accumulator a -> digit sum d = p + q of its products, and the product list
@@ -235,29 +237,34 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
 // Integer-output digit GEMM, persistent: CTA c takes tiles c, c + gridDim.x, ... of 128 rows x BN
 // columns (columns fastest, so concurrent CTAs share X digit planes in L2).  Warp NDW issues TMA
 // and streams chunks across tiles; warp NDW + 1 issues the MMAs; warps 0..NDW-1 drain, warp w
-// reading TMEM lanes 32 (w % 4).. (the lanes its warp index may access) and BN / 4 columns.  While
-// the drain folds a K group and stores a finished tile, the producer loads the next chunks, and
-// the next tile's products start as soon as the accumulators are read.  The drain of a group holds
-// the tensor pipe up, so it is spread over sixteen warps.
-constexpr int DG_NDW = 16;
+// reading TMEM lanes 32 (w % 4).. (the lanes its warp index may access) and 8 columns.  K groups
+// alternate between two accumulator sets: while the drain warps fold group G (and store a finished
+// tile), the products of group G + 1 run into the other set, and the producer loads ahead.  The
+// drain adds each accumulator into a 32-bit sum per digit sum and column (one conversion and one
+// add per value; at most 8 groups of |value| < 2^24) and combines the seven sums into the int64
+// result once per tile.
+constexpr int DG_CW = 8;                                // columns per drain warp
+constexpr int DG_NDW = 4 * Plan<true>::BN / DG_CW;
 constexpr int DG_THREADS = 32 * (DG_NDW + 2);
 
 __global__ void __launch_bounds__(DG_THREADS, 1)
 k_digit_gemm_int(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapM, OzArgs p) {
     using PL = Plan<true>;
-    constexpr int S = PL::S, BN = PL::BN, STAGES = PL::STAGES, KGROUP = PL::KGROUP;
+    constexpr int S = PL::S, BN = PL::BN, STAGES = PL::STAGES, KGROUP = PL::KGROUP, NBUF = PL::NBUF;
     constexpr int MTILE = BN * KC * 2;
     constexpr int STAGE = S * (XTILE + MTILE);
-    constexpr int CW = BN / (DG_NDW / 4);               // columns per drain warp (16)
-    static_assert(CW == 16, "one 16-column TMEM load per accumulator and drain warp");
+    constexpr int CW = DG_CW;
+    constexpr uint32_t SET = S * BN;                    // TMEM columns of one accumulator set
+    static_assert(CW == 8, "one 8-column TMEM load per accumulator and drain warp");
+    static_assert(NBUF * SET <= TMEM_COLS && S * BN <= 256, "accumulator sets within TMEM, one product per digit");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE);
     uint64_t* empty = full + STAGES;
-    uint64_t* accf = empty + STAGES;                    // a K group's products complete
-    uint64_t* fin = accf + 1;                           // error path: outstanding products complete
-    uint64_t* tfree = fin + 1;                          // a K group's accumulators have been read
-    uint32_t* tmem_slot = (uint32_t*)(tfree + 1);
+    uint64_t* accf = empty + STAGES;                    // per set: a K group's products complete
+    uint64_t* tfree = accf + NBUF;                      // per set: a K group's accumulators have been read
+    uint64_t* fin = tfree + NBUF;                       // error path: outstanding products complete
+    uint32_t* tmem_slot = (uint32_t*)(fin + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long Mtot = (long long)p.batch * p.R;
@@ -270,9 +277,8 @@ k_digit_gemm_int(const __grid_constant__ CUtensorMap mapX, const __grid_constant
 
     if (threadIdx.x == 0) {
         for (int st = 0; st < STAGES; ++st) { tc::mbar_init(&full[st], 1); tc::mbar_init(&empty[st], 1); }
-        tc::mbar_init(accf, 1);
+        for (int b = 0; b < NBUF; ++b) { tc::mbar_init(&accf[b], 1); tc::mbar_init(&tfree[b], 32 * DG_NDW); }
         tc::mbar_init(fin, 1);
-        tc::mbar_init(tfree, 32 * DG_NDW);
         tc::mbar_fence_init();
         tc::prefetch_tmap(&mapX);
         tc::prefetch_tmap(&mapM);
@@ -316,35 +322,35 @@ k_digit_gemm_int(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                 for (int c = 0; c < nchunks && ok; ++c, ++cnt) {
                     const int st = (int)(cnt % STAGES);
                     const bool group_start = c % CPG == 0;
-                    // a K group overwrites the accumulators once the drain warps have read the last
-                    if (group_start && G > 0) ok = tc::mbar_wait(tfree, (uint32_t)(G - 1) & 1u, p.err, tc::ERR_WAIT_ACC);
+                    const int set = (int)(G % NBUF);
+                    // a K group overwrites its accumulator set once the drain warps have read the
+                    // group NBUF before it (the (G / NBUF)-th completion of that set's barrier)
+                    if (group_start && G >= NBUF)
+                        ok = tc::mbar_wait(&tfree[set], (uint32_t)(G / NBUF - 1) & 1u, p.err, tc::ERR_WAIT_ACC);
                     if (!ok) break;
                     ok = tc::mbar_wait(&full[st], (uint32_t)(cnt / STAGES) & 1u, p.err, tc::ERR_WAIT_FULL);
                     if (!ok) break;
                     tc::tc_fence_after();
                     const uint8_t* sX = smem + st * STAGE;
                     const uint8_t* sM = sX + S * XTILE;
-                    // X digit p against matrix digits q0 .. q0 + Q - 1 in one product (the matrix
-                    // planes lie one after another; accumulator d = p + q sits at columns (d - 2) BN);
-                    // the products of p = 1 reach every accumulator and overwrite them at a group's
-                    // start
+                    // X digit p against matrix digits 1 .. nd + 1 - p in one product (the matrix
+                    // planes lie one after another; accumulator d = p + q sits at columns (d - 2) BN
+                    // of the set); the product of p = 1 reaches every accumulator and overwrites the
+                    // set at a group's start
+                    const uint32_t dset = tmem + (uint32_t)set * SET;
                     for (int pp = 1; pp <= nd; ++pp) {
-                        const int qmax = nd + 1 - pp;
-                        for (int q0 = 1; q0 <= qmax; q0 += 256 / BN) {
-                            const int Q = min(256 / BN, qmax - q0 + 1);
-                            const uint32_t idq = tc::idesc_f32acc(1u, BM, Q * BN);
+                        const uint32_t idq = tc::idesc_f32acc(1u, BM, (nd + 1 - pp) * BN);
 #pragma unroll
-                            for (int kk = 0; kk < KC / 16; ++kk) {
-                                const uint64_t ad = tc::smem_desc_sw64(sX + (pp - 1) * XTILE + kk * 32);
-                                const uint64_t bd = tc::smem_desc_sw64(sM + (q0 - 1) * MTILE + kk * 32);
-                                tc::mma<0>(tmem + (uint32_t)((pp + q0 - 2) * BN), ad, bd, idq,
-                                           (group_start && pp == 1 && kk == 0) ? 0u : 1u);
-                            }
+                        for (int kk = 0; kk < KC / 16; ++kk) {
+                            const uint64_t ad = tc::smem_desc_sw64(sX + (pp - 1) * XTILE + kk * 32);
+                            const uint64_t bd = tc::smem_desc_sw64(sM + kk * 32);
+                            tc::mma<0>(dset + (uint32_t)((pp - 1) * BN), ad, bd, idq,
+                                       (group_start && pp == 1 && kk == 0) ? 0u : 1u);
                         }
                     }
                     any = true;
                     tc::mma_commit(&empty[st]);
-                    if (c % CPG == CPG - 1 || c == nchunks - 1) { tc::mma_commit(accf); ++G; }
+                    if (c % CPG == CPG - 1 || c == nchunks - 1) { tc::mma_commit(&accf[set]); ++G; }
                 }
             }
             if (!ok && any) {  // products still running must finish before TMEM is freed
@@ -360,51 +366,51 @@ k_digit_gemm_int(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const long long m = (t / ntn) * BM + lq * 32 + lane;
             const int n0 = (int)(t % ntn) * BN;
-            // zt: running sums over the K groups in units of 2^-52, the digit sums d <= 6 added exactly,
-            // d = 7 and 8 (units 2^-56 and 2^-64) combined exactly and folded in with one rounding per
-            // group (at most half a unit)
-            long long zt[CW];
+            // acc[a]: the exact sum over the K groups of accumulator a (digit sum d = a + 2), in units
+            // of 2^{-8d} (at most 8 groups of |value| < 2^24: below 2^27)
+            int acc[S][CW];
 #pragma unroll
-            for (int j = 0; j < CW; ++j) zt[j] = 0;
+            for (int a = 0; a < S; ++a)
+#pragma unroll
+                for (int j = 0; j < CW; ++j) acc[a][j] = 0;
+            // the result in units of 2^-52, formed while the last group is drained: the digit sums
+            // d <= 6 exactly (Horner in base 256 from d = 2, whose unit is 2^{36-52}), d = 7 and 8
+            // (units 2^-56 and 2^-64) combined exactly and added with one rounding (at most half a
+            // unit); the sums past nd are zero
+            long long y[CW];
             for (int grp = 0; grp < ngroups; ++grp, ++G) {
-                ok = __all_sync(0xffffffffu, tc::mbar_wait(accf, (uint32_t)G & 1u, p.err, tc::ERR_WAIT_ACC));
+                const bool last = grp == ngroups - 1;
+                const int set = (int)(G % NBUF);
+                ok = __all_sync(0xffffffffu,
+                                tc::mbar_wait(&accf[set], (uint32_t)(G / NBUF) & 1u, p.err, tc::ERR_WAIT_ACC));
                 tc::tc_fence_after();
                 if (!ok) break;
-                // accumulator a's 16 columns in one of two register sets: the load of a + 1 is in flight
-                // while a is converted (the drain is otherwise a chain of load latencies); accumulator 5
-                // (d = 7) stays in vb until accumulator 6 (d = 8, in va) has arrived
-                const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)cb;
-                uint32_t va[16], vb[16];
-                tc::tmem_ld16_async(base, va);
-                tc::tmem_wait_ld();
-                tc::reg_fence16(va);
+                // accumulator a's 8 columns (the latency of each load is hidden by the other three drain
+                // warps of the sub-partition)
+                const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)set * SET + (uint32_t)cb;
 #pragma unroll
-                for (int a = 0; a < Plan<true>::S; ++a) {
-                    if (a >= nd) break;
-                    uint32_t* cur = (a & 1) ? vb : va;
-                    uint32_t* nxt = (a & 1) ? va : vb;
-                    if (a + 1 < nd) tc::tmem_ld16_async(base + (uint32_t)((a + 1) * BN), nxt);
-                    const int d = a + 2;
-                    if (d <= 6) {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j)   // exact, |value| < 2^24
-                            zt[j] += (long long)__float2int_rn(__uint_as_float(cur[j])) << (52 - 8 * d);
-                    } else if (a + 1 == nd) {
-                        // the last accumulator: d = 7 alone (nd = 6), or d = 8 in va with d = 7 in vb
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            long long zl = (long long)__float2int_rn(__uint_as_float(vb[j])) << 8;
-                            if (d == 8) zl += (long long)__float2int_rn(__uint_as_float(va[j]));
-                            zt[j] += (zl + 2048) >> 12;
-                        }
-                    }
-                    if (a + 1 < nd) {
+                for (int a = 0; a < S; ++a) {
+                    if (a < nd) {   // no early exit: the loop unrolls and acc stays in registers
+                        uint32_t v[CW];
+                        tc::tmem_ld8_async(base + (uint32_t)(a * BN), v);
                         tc::tmem_wait_ld();
-                        tc::reg_fence16(nxt);
+                        tc::reg_fence8(v);
+#pragma unroll
+                        for (int j = 0; j < CW; ++j)   // exact, |value| < 2^24
+                            acc[a][j] += __float2int_rn(__uint_as_float(v[j]));
+                    }
+                    if (last) {
+#pragma unroll
+                        for (int j = 0; j < CW; ++j) {
+                            if (a == 0) y[j] = acc[0][j];
+                            else if (a < 5) y[j] = y[j] * 256 + acc[a][j];
+                            else if (a == 6)
+                                y[j] = y[j] * 16 + (((long long)acc[5][j] * 256 + acc[6][j] + 2048) >> 12);
+                        }
                     }
                 }
                 tc::tc_fence_before();
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(tfree)) : "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&tfree[set])) : "memory");
             }
             // the next tile's products run while this one is stored
             if (ok && m < Mtot) {
@@ -412,10 +418,10 @@ k_digit_gemm_int(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                 const int r = (int)(m % p.R);
                 long long* out = (long long*)p.out + b * p.out_stride + r;
 #pragma unroll
-                for (int j = 0; j < CW; ++j) {
-                    long long y = zt[j];
-                    if (zs > 0) y = (y + (1ll << (zs - 1))) >> zs;
-                    if (n0 + cb + j < p.N) out[(long long)(n0 + cb + j) * p.R] = y;
+                for (int j = 0; j < CW; ++j) {   // N is a multiple of BN: every column exists
+                    long long v = y[j];
+                    if (zs > 0) v = (v + (1ll << (zs - 1))) >> zs;
+                    out[(long long)(n0 + cb + j) * p.R] = v;
                 }
             }
         }
@@ -593,8 +599,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode() {
 
 sfde_status sfde_oz_split_matrix(const double* Mat, int K, int N, OzMatrix* out, cudaStream_t s, double alpha,
                                  bool uniform) {
-    // integer plan: tiles of 64 columns, a last tile of 32 reads zeros past N (N >= 64 keeps the
-    // box within the matrix)
+    // both plans take tiles of 32 columns (N a multiple of 32)
     const int BN = uniform ? Plan<true>::BN : Plan<false>::BN;
     if (K > (uniform ? 1024 : 256) || K % 32 || N % 32 || N < BN) return SFDE_EUNSUPPORTED;
     // uniform scale: the integer-output product (7 digits); per-column scales: FP64 output (6)

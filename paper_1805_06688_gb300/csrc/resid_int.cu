@@ -27,6 +27,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "sfde_internal.cuh"
 
@@ -226,8 +227,10 @@ __device__ __forceinline__ float i128_to_f32(__int128 x, float s1, float s2) {
 // unit (its rounding, half a unit, lies far below F's own FP64 rounding); where F 2^-ec would not fit,
 // or both slices of the pair are zero (no unit: c_m = c_s = 0), the FP64 form F + c_m S9 + c_s S is
 // kept.  Writes rho (BF16 or TF32-rounded FP32), zero outside the interior nodes, and one FP64 sum of
-// rho^2 per block.
-template <typename OT, bool TF32R>
+// rho^2 per block.  ZERO: both slices of every pair are zero (E = -1022, the exponent k_slice_maxexp
+// gives a zero slice; Z1 = Z2 = du = 0): the same arithmetic without reading the products, so that
+// rho = F_n to the bit as the general form gives it.
+template <typename OT, bool TF32R, bool ZERO>
 __global__ void __launch_bounds__(256, 4) k_combine_int(
     const long long* __restrict__ T1, const long long* __restrict__ T3, const long long* __restrict__ DU,
     const int* __restrict__ En, int n0, int Px, int Py, int nx, int ny, double cmass, int ex, int ey, int zsx, int zsy,
@@ -249,7 +252,7 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
     const int b = blockIdx.z, n = n0 + b;
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int E = max(En[n - 1], En[n]);
+    const int E = ZERO ? -1022 : max(En[n - 1], En[n]);
     const size_t P2 = (size_t)Px * Py;
     // all global loads of the block are issued before any of them is used (compile-time trip
     // counts, register staging), so their latencies overlap
@@ -263,8 +266,8 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
         for (int h = 0; h < 2; ++h) {
             const int c = tx + 32 * h;
             const int j = j0 + c - 1, i = i0 + c - 1;
-            a1[k][h] = (c < 34 && j >= 0 && j < Py) ? __ldg(T1b + (size_t)(i0 + ty + 8 * k) * Py + j) : 0;
-            a3[k][h] = (c < 34 && i >= 0 && i < Px) ? __ldg(T3b + (size_t)(j0 + ty + 8 * k) * Px + i) : 0;
+            a1[k][h] = (!ZERO && c < 34 && j >= 0 && j < Py) ? __ldg(T1b + (size_t)(i0 + ty + 8 * k) * Py + j) : 0;
+            a3[k][h] = (!ZERO && c < 34 && i >= 0 && i < Px) ? __ldg(T3b + (size_t)(j0 + ty + 8 * k) * Px + i) : 0;
         }
 #pragma unroll
     for (int k = 0; k < 5; ++k)
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
         for (int h = 0; h < 2; ++h) {
             const int rr = ty + 8 * k, c = tx + 32 * h;
             const int j = j0 + rr - 1, i = i0 + c - 1;
-            const bool in = rr < 34 && c < 34 && j >= 0 && j < Py && i >= 0 && i < Px;
+            const bool in = !ZERO && rr < 34 && c < 34 && j >= 0 && j < Py && i >= 0 && i < Px;
             ad[k][h] = in ? __ldg(DUb + (size_t)j * Px + i) : 0;     // zero outside the grid
         }
 #pragma unroll
@@ -377,8 +380,8 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
 
 // contraction lengths up to 256, or multiples of 256 up to 1024 (the digit product's K groups)
 bool sfde_resid_int_supported(int Px, int Py) {
-    // the digit products take tiles of 64 output columns (at least one whole tile) and sum K in
-    // groups of 128, up to 1024
+    // the digit products take tiles of 32 output columns and sum K in groups of 128, up to 1024
+    // (at least 64: the smallest size the residual's tests and tile shapes cover)
     auto ok = [](int P) { return P >= 64 && (P <= 256 || (P <= 1024 && P % 256 == 0)); };
     return ok(Px) && ok(Py);
 }
@@ -393,27 +396,59 @@ sfde_status sfde_resid_int_matrices(sfde_ctx* c, OzMatrix* Ax, OzMatrix* Ay) {
     return SFDE_OK;
 }
 
+namespace {
+// k_combine_int for one chunk of nb pairs from n0, output kind 0 (BF16), 1 (TF32-rounded FP32) or
+// 2 (FP32)
+template <bool ZERO>
+void launch_combine(sfde_ctx* c, int out_kind, const long long* du, const int* En, int n0, int nb, int ex, int ey,
+                    void* ro, long long rout_stride, double* partial) {
+    const int Px = c->x.P, Py = c->y.P;
+    dim3 grid(Px / 32, Py / 32, nb), block(32, 8);
+    const double cmass = c->x.h * c->y.h / 36.0;
+    const int zx = sfde_oz_int_shift(Px), zy = sfde_oz_int_shift(Py);
+    const long long *T1 = (const long long*)c->T1, *T3 = (const long long*)c->T3;
+    if (out_kind == 0)
+        k_combine_int<__nv_bfloat16, false, ZERO><<<grid, block, 0, c->stream>>>(
+            T1, T3, du, En, n0, Px, Py, c->x.n, c->y.n, cmass, ex, ey, zx, zy, c->dt0, c->rank, c->time_w, c->bxn,
+            c->byn, c->Fd, (__nv_bfloat16*)ro, rout_stride, partial);
+    else if (out_kind == 1)
+        k_combine_int<float, true, ZERO><<<grid, block, 0, c->stream>>>(
+            T1, T3, du, En, n0, Px, Py, c->x.n, c->y.n, cmass, ex, ey, zx, zy, c->dt0, c->rank, c->time_w, c->bxn,
+            c->byn, c->Fd, (float*)ro, rout_stride, partial);
+    else
+        k_combine_int<float, false, ZERO><<<grid, block, 0, c->stream>>>(
+            T1, T3, du, En, n0, Px, Py, c->x.n, c->y.n, cmass, ex, ey, zx, zy, c->dt0, c->rank, c->time_w, c->bxn,
+            c->byn, c->Fd, (float*)ro, rout_stride, partial);
+}
+}  // namespace
+
 sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
                               long long rout_stride, int out_kind, double* partial, int* n_partials,
                               const OzMatrix& Ax, const OzMatrix& Ay, void* dV, void* dVt, int* En, int* err,
-                              int nd) {
+                              int nd, int n_zero) {
     const int Px = c->x.P, Py = c->y.P;
     const size_t P2 = c->P2();
     const size_t esz = out_kind == 0 ? 2 : 4;
     if (!sfde_resid_int_supported(Px, Py) || n_first < 1 || count < 1 || nd < 4 || nd > ND) return SFDE_EINVAL;
+    // pairs n >= n_zero (two zero slices) take the load alone; the products run for the others
+    const int gcount = (int)std::max<long long>(0, std::min<long long>(count, (long long)n_zero - n_first));
     // accounting (class 5): bytes each kernel must move once, unpadded
     const double nxy = (double)c->x.n * c->y.n;
-    int slot = sfde_prof_begin(c);
-    k_slice_maxexp<<<count + 1, 256, 0, c->stream>>>(U + (size_t)(n_first - 1) * P2, P2, En + (n_first - 1));
-    sfde_prof_end(c, slot, 5, 0.0, 8.0 * nxy * (count + 1));
-    sfde_count_launch(c);
+    const int blocks1 = (Px / 32) * (Py / 32);
+    int slot;
+    if (gcount > 0) {
+        slot = sfde_prof_begin(c);
+        k_slice_maxexp<<<gcount + 1, 256, 0, c->stream>>>(U + (size_t)(n_first - 1) * P2, P2, En + (n_first - 1));
+        sfde_prof_end(c, slot, 5, 0.0, 8.0 * nxy * (gcount + 1));
+        sfde_count_launch(c);
+    }
     int total = 0;
     const int chunk = c->resid_chunk > 0 ? std::min(c->resid_chunk, (int)c->ws_slices) : (int)c->ws_slices;
-    for (int b0 = 0; b0 < count; b0 += chunk) {
-        const int nb = std::min(count - b0, chunk);
+    for (int b0 = 0; b0 < gcount; b0 += chunk) {
+        const int nb = std::min(gcount - b0, chunk);
         const int n0 = n_first + b0;
         const long long plane = (long long)nb * Px * Py;
-        dim3 grid(Px / 32, Py / 32, nb), block(32, 8);
+        dim3 grid(Px / 32, Py / 32, nb);
         long long* du = (long long*)c->T2;   // fix(U_{n-1}) - fix(U_n), int64 per element
         slot = sfde_prof_begin(c);
         k_split_pair<<<grid, 256, 0, c->stream>>>(U, En, n0, Px, Py, (uint16_t*)dV, (uint16_t*)dVt, du, plane, nd);
@@ -424,30 +459,23 @@ sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int cou
                                   c->x.n, c->x.n, nd));
         SFDE_TRY(sfde_oz_gemm_int(c, dVt, plane, Px, Py, nb, Ay, (long long*)c->T3, (long long)P2, err, c->x.n,
                                   c->y.n, c->y.n, nd));
-        const int blocks = (Px / 32) * (Py / 32) * nb;
+        const int blocks = blocks1 * nb;
         if ((size_t)(total + blocks) > c->partial_cap) return SFDE_EINVAL;
-        char* ro = (char*)rout + (size_t)b0 * rout_stride * esz;
-        const double cmass = c->x.h * c->y.h / 36.0;
         slot = sfde_prof_begin(c);
-        if (out_kind == 0)
-            k_combine_int<__nv_bfloat16, false><<<grid, block, 0, c->stream>>>(
-                (const long long*)c->T1, (const long long*)c->T3, du, En, n0, Px, Py, c->x.n, c->y.n, cmass,
-                Ax.e_uniform, Ay.e_uniform, sfde_oz_int_shift(Px), sfde_oz_int_shift(Py), c->dt0, c->rank,
-                c->time_w, c->bxn, c->byn, c->Fd, (__nv_bfloat16*)ro,
-                rout_stride, partial + total);
-        else if (out_kind == 1)
-            k_combine_int<float, true><<<grid, block, 0, c->stream>>>(
-                (const long long*)c->T1, (const long long*)c->T3, du, En, n0, Px, Py, c->x.n, c->y.n, cmass,
-                Ax.e_uniform, Ay.e_uniform, sfde_oz_int_shift(Px), sfde_oz_int_shift(Py), c->dt0, c->rank,
-                c->time_w, c->bxn, c->byn, c->Fd, (float*)ro, rout_stride,
-                partial + total);
-        else
-            k_combine_int<float, false><<<grid, block, 0, c->stream>>>(
-                (const long long*)c->T1, (const long long*)c->T3, du, En, n0, Px, Py, c->x.n, c->y.n, cmass,
-                Ax.e_uniform, Ay.e_uniform, sfde_oz_int_shift(Px), sfde_oz_int_shift(Py), c->dt0, c->rank,
-                c->time_w, c->bxn, c->byn, c->Fd, (float*)ro, rout_stride,
-                partial + total);
+        launch_combine<false>(c, out_kind, du, En, n0, nb, Ax.e_uniform, Ay.e_uniform,
+                              (char*)rout + (size_t)b0 * rout_stride * esz, rout_stride, partial + total);
         sfde_prof_end(c, slot, 5, 0.0, (16.0 + 8.0 + (double)esz) * nxy * nb);   // Z1, Z2, du in, rho out
+        sfde_count_launch(c);
+        total += blocks;
+    }
+    for (int b0 = gcount; b0 < count; b0 += 65535) {   // grid z <= 65535
+        const int nb = std::min(count - b0, 65535);
+        const int blocks = blocks1 * nb;
+        if ((size_t)(total + blocks) > c->partial_cap) return SFDE_EINVAL;
+        slot = sfde_prof_begin(c);
+        launch_combine<true>(c, out_kind, (const long long*)c->T2, En, n_first + b0, nb, Ax.e_uniform, Ay.e_uniform,
+                             (char*)rout + (size_t)b0 * rout_stride * esz, rout_stride, partial + total);
+        sfde_prof_end(c, slot, 5, 0.0, (double)esz * nxy * nb);   // rho out
         sfde_count_launch(c);
         total += blocks;
     }
@@ -497,7 +525,7 @@ extern "C" sfde_status sfde_debug_residual(sfde_ctx* c, const double* U, int use
         DC(cudaMalloc(&dVt, sfde_resid_int_digit_bytes(Px, Py, (int)c->ws_slices)));
         DC(cudaMalloc(&En, sizeof(int) * (c->nt + 1)));
         st = sfde_residual_int(c, u, 1, c->nt, rp, (long long)P2, okind, c->partial, &np, Ax, Ay, dV, dVt, En, err,
-                               nd);
+                               nd, INT_MAX);
     } else {
         st = sfde_residual_fp64(c, u, 1, c->nt, rp, (long long)P2, okind, c->partial, &np);
     }

@@ -301,14 +301,16 @@ sfde_status sfde_oz_gemm_int(sfde_ctx* c, void* xdigits, long long plane, int R,
 // tensor-core products (resid_int.cu), Px, Py <= 1024.  Ax, Ay from sfde_resid_int_matrices; dV, dVt:
 // sfde_resid_int_digit_bytes(Px, Py, ws_slices) each (digits of 2V row-major and transposed); En:
 // N_t + 1 ints; err: device error word; nd: digits per operand, 4..7 (7: exact operands; fewer
-// digits truncate V and the matrices at about 2^{9-8 nd} of their scales).
+// digits truncate V and the matrices at about 2^{9-8 nd} of their scales); n_zero: U_n = 0 for every
+// n >= n_zero - 1 is known (INT_MAX: nothing known), so those pairs are the load alone (the same
+// values, no products formed).
 bool sfde_resid_int_supported(int Px, int Py);
 size_t sfde_resid_int_digit_bytes(int Px, int Py, int batch);
 sfde_status sfde_resid_int_matrices(sfde_ctx* c, OzMatrix* Ax, OzMatrix* Ay);
 sfde_status sfde_residual_int(sfde_ctx* c, const double* U, int n_first, int count, void* rout,
                               long long rout_stride, int out_kind, double* partial, int* n_partials,
                               const OzMatrix& Ax, const OzMatrix& Ay, void* dV, void* dVt, int* En, int* err,
-                              int nd);
+                              int nd, int n_zero);
 void sfde_launch_mass_x_transpose(const double* Un, const double* Um, double* T2, int Px, int Py, double hx,
                                   int nb, cudaStream_t s);
 

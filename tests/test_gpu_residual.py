@@ -155,3 +155,29 @@ def test_residual_of_a_zero_iterate_is_the_load():
     for n in range(nt):
         assert np.abs(rho[n] - ref[n]).max() <= 2.0 ** -20 * np.abs(ref[n]).max(), n
     assert abs(nrm - np.sqrt(np.sum(ref ** 2))) <= 2.0 ** -20 * np.sqrt(np.sum(ref ** 2))
+
+
+@pytest.mark.parametrize("prec", [sfde.PREC_MIXED_TF32, sfde.PREC_MIXED_FP32])
+def test_first_residual_of_the_solver_takes_the_load_for_zero_pairs(prec):
+    """The solver's first iterate is psi_0 followed by zeros: it forms the digit products for the pair
+    (psi_0, U_1 = 0) alone and takes rho_n = F_n for n >= 2 without reading any product.  Its norm
+    (the first entry of the residual history, 4 digits) equals the general form's on the same
+    iterate to the bit, and the oracle's within the 4-digit truncation and FP32 storage."""
+    nx, ny, nt = 130, 96, 40
+    t = time_grid(nt, 1.0, "graded")
+    F, _ = gaussian_bump_forcing(3, nx, ny, t)
+    psi = sine_mode_nodal(sine_mode_amplitudes(3), nx, ny)
+    P = sfde.Problem(0.7, 0.75, 1.0, 0.4, nx, ny, t, precision=prec)
+    P.set_initial(psi)
+    P.set_forcing(F)
+    U = np.zeros((nt + 1, ny, nx))
+    _, st = P.mgrit(U=U, m=4, max_levels=2, coarse=sfde.COARSE_BE, rel_tol=0.0, max_iter=1, check=False)
+    res0 = st.residual_history()[0]
+    U0 = np.zeros((nt + 1, ny, nx))
+    U0[0] = psi
+    _, nrm = gpu_residual(P, U0, 4)
+    assert res0 == nrm or abs(res0 - nrm) <= 1e-15 * nrm, (res0, nrm)
+    O = osfde.SFDE(0.7, 0.75, 1.0, 0.4, nx, ny, t)
+    ref, scale = oracle_residual(O, U0, F)
+    rn = np.sqrt(np.sum(ref ** 2))
+    assert abs(res0 - rn) <= 2.0 ** (12 - 8 * 4) * scale + 2.0 ** -20 * rn
