@@ -198,15 +198,21 @@ __device__ __forceinline__ void split_double(double c, long long& m, int& e) {
     e = ex - 1075;
 }
 
-// FP32 of x 2^e (x a 128-bit integer, 2^e = s1 s2 given as two FP32 powers of two) within 1.5 ulp:
-// |x| = hi 2^64 + lo with both halves converted (each rounded once, no cancellation: same sign) and
-// added by one FMA; the powers of two scale exactly unless the result leaves the normal range
+// FP32 of x 2^e (x a 128-bit integer, |x| < 2^127; 2^e = s1 s2 given as two FP32 powers of two)
+// within 4 ulp: the four 32-bit words of |x| are converted one by one (32-bit conversions; the
+// 64-bit ones run on the slow FP64 pipe) and summed by three FMAs from the top word down (all
+// terms of one sign: at most seven roundings of 2^-24 each, no cancellation); the powers of two
+// scale exactly unless the result leaves the normal range
 __device__ __forceinline__ float i128_to_f32(__int128 x, float s1, float s2) {
     const bool neg = x < 0;
     const unsigned __int128 a = neg ? (unsigned __int128)0 - (unsigned __int128)x : (unsigned __int128)x;
-    const float hf = __ull2float_rn((unsigned long long)(a >> 64));
-    const float lf = __ull2float_rn((unsigned long long)a);
-    const float r = fmaf(hf, 18446744073709551616.0f, lf) * s1 * s2;
+    const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+    const float w = 4294967296.0f;   // 2^32
+    float r = __uint2float_rn((unsigned)(hi >> 32));
+    r = fmaf(r, w, __uint2float_rn((unsigned)hi));
+    r = fmaf(r, w, __uint2float_rn((unsigned)(lo >> 32)));
+    r = fmaf(r, w, __uint2float_rn((unsigned)lo));
+    r = r * s1 * s2;
     return neg ? -r : r;
 }
 
@@ -221,16 +227,14 @@ __device__ __forceinline__ float i128_to_f32(__int128 x, float s1, float s2) {
 // products are exact 128-bit integers below 2^126 with no shift per element (when the two units
 // differ by more than 2^10 the finer product is shifted right, keeping its bits down to 2^-62 of
 // the coarser unit, far below the fixed-point grid's own resolution), added exactly, and converted
-// to FP32 within 1.5 ulp -- no FP64 arithmetic per element (the FP64 pipe runs at about 1/64 of
-// the FP32 rate).  A load term F_n is formed in FP64 (one FMA per separable term, the time weight
+// to FP32 within 4 ulp from 32-bit words -- no FP64 arithmetic per element (the FP64 pipe runs at
+// about 1/64 of the FP32 rate).  A load term F_n is formed in FP64 (one FMA per separable term, the time weight
 // times the y factor taken once per row) and added as round(F 2^-ec), a 128-bit integer in the same
 // unit (its rounding, half a unit, lies far below F's own FP64 rounding); where F 2^-ec would not fit,
 // or both slices of the pair are zero (no unit: c_m = c_s = 0), the FP64 form F + c_m S9 + c_s S is
 // kept.  Writes rho (BF16 or TF32-rounded FP32), zero outside the interior nodes, and one FP64 sum of
-// rho^2 per block.  ZERO: both slices of every pair are zero (E = -1022, the exponent k_slice_maxexp
-// gives a zero slice; Z1 = Z2 = du = 0): the same arithmetic without reading the products, so that
-// rho = F_n to the bit as the general form gives it.
-template <typename OT, bool TF32R, bool ZERO>
+// rho^2 per block.
+template <typename OT, bool TF32R>
 __global__ void __launch_bounds__(256, 4) k_combine_int(
     const long long* __restrict__ T1, const long long* __restrict__ T3, const long long* __restrict__ DU,
     const int* __restrict__ En, int n0, int Px, int Py, int nx, int ny, double cmass, int ex, int ey, int zsx, int zsy,
@@ -252,7 +256,7 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
     const int b = blockIdx.z, n = n0 + b;
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int E = ZERO ? -1022 : max(En[n - 1], En[n]);
+    const int E = max(En[n - 1], En[n]);
     const size_t P2 = (size_t)Px * Py;
     // all global loads of the block are issued before any of them is used (compile-time trip
     // counts, register staging), so their latencies overlap
@@ -266,8 +270,8 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
         for (int h = 0; h < 2; ++h) {
             const int c = tx + 32 * h;
             const int j = j0 + c - 1, i = i0 + c - 1;
-            a1[k][h] = (!ZERO && c < 34 && j >= 0 && j < Py) ? __ldg(T1b + (size_t)(i0 + ty + 8 * k) * Py + j) : 0;
-            a3[k][h] = (!ZERO && c < 34 && i >= 0 && i < Px) ? __ldg(T3b + (size_t)(j0 + ty + 8 * k) * Px + i) : 0;
+            a1[k][h] = (c < 34 && j >= 0 && j < Py) ? __ldg(T1b + (size_t)(i0 + ty + 8 * k) * Py + j) : 0;
+            a3[k][h] = (c < 34 && i >= 0 && i < Px) ? __ldg(T3b + (size_t)(j0 + ty + 8 * k) * Px + i) : 0;
         }
 #pragma unroll
     for (int k = 0; k < 5; ++k)
@@ -275,7 +279,7 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
         for (int h = 0; h < 2; ++h) {
             const int rr = ty + 8 * k, c = tx + 32 * h;
             const int j = j0 + rr - 1, i = i0 + c - 1;
-            const bool in = !ZERO && rr < 34 && c < 34 && j >= 0 && j < Py && i >= 0 && i < Px;
+            const bool in = rr < 34 && c < 34 && j >= 0 && j < Py && i >= 0 && i < Px;
             ad[k][h] = in ? __ldg(DUb + (size_t)j * Px + i) : 0;     // zero outside the grid
         }
 #pragma unroll
@@ -376,6 +380,61 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
     }
 }
 
+// rho_n = F_n for pairs of two zero slices (Z1 = Z2 = du = 0): with no fixed-point unit k_combine_int
+// takes its FP64 form there, F_n + 0 S9 + 0 S, i.e. F_n rounded once to FP32 (-0 read as +0); this
+// kernel gives the same values from the load alone, on the same tiles and with the same per-block sums
+// of rho^2, reading no product.
+template <typename OT, bool TF32R>
+__global__ void __launch_bounds__(256) k_load_resid(int n0, int Px, int Py, int nx, int ny, int rank,
+                                                    const double* __restrict__ time_w, const double* __restrict__ bxn,
+                                                    const double* __restrict__ byn, const double* __restrict__ Fd,
+                                                    OT* __restrict__ rout, long long rout_stride,
+                                                    double* __restrict__ partial) {
+    __shared__ double fy[SFDE_MAX_RANK][32];
+    __shared__ double red[8];
+    const int b = blockIdx.z, n = n0 + b;
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const size_t P2 = (size_t)Px * Py;
+    if (ty == 0)
+        for (int q = 0; q < rank; ++q) {
+            const int j = j0 + tx;
+            fy[q][tx] = j < Py ? time_w[(size_t)(n - 1) * rank + q] * byn[(size_t)q * Py + j] : 0.0;
+        }
+    __syncthreads();
+    const int i = i0 + tx;
+    double bxi[SFDE_MAX_RANK];
+#pragma unroll
+    for (int q = 0; q < SFDE_MAX_RANK; ++q) bxi[q] = (q < rank && i < Px) ? bxn[(size_t)q * Px + i] : 0.0;
+    float sq = 0.f;
+    for (int jj = ty; jj < 32; jj += 8) {
+        const int j = j0 + jj;
+        float rf = 0.f;
+        if (i < nx && j < ny && (rank > 0 || Fd)) {
+            double f = Fd ? Fd[(size_t)(n - 1) * P2 + (size_t)j * Px + i] : 0.0;
+#pragma unroll
+            for (int q = 0; q < SFDE_MAX_RANK; ++q)
+                if (q < rank) f = fma(fy[q][jj], bxi[q], f);
+            if ((__double_as_longlong(f) << 1) == 0) f = 0.0;   // -0 -> +0 (integer test of the bits)
+            rf = (float)f;
+        }
+        sq = fmaf(rf, rf, sq);
+        OT* o = rout + (size_t)b * rout_stride + (size_t)j * Px + i;
+        if (sizeof(OT) == 2) *o = (OT)__float2bfloat16_rn(rf);
+        else *o = TF32R ? (OT)sfde_round_tf32(rf) : (OT)rf;
+    }
+    double sqd = sq;
+    for (int o = 16; o > 0; o >>= 1) sqd += __shfl_xor_sync(0xffffffffu, sqd, o);
+    const int w = (ty * 32 + tx) >> 5;
+    if ((tx & 31) == 0) red[w] = sqd;
+    __syncthreads();
+    if (tx == 0 && ty == 0) {
+        double s = 0.0;
+        for (int k = 0; k < 8; ++k) s += red[k];
+        partial[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
+    }
+}
+
 }  // namespace
 
 // contraction lengths up to 256, or multiples of 256 up to 1024 (the digit product's K groups)
@@ -397,8 +456,8 @@ sfde_status sfde_resid_int_matrices(sfde_ctx* c, OzMatrix* Ax, OzMatrix* Ay) {
 }
 
 namespace {
-// k_combine_int for one chunk of nb pairs from n0, output kind 0 (BF16), 1 (TF32-rounded FP32) or
-// 2 (FP32)
+// k_combine_int (ZERO: k_load_resid) for one chunk of nb pairs from n0, output kind 0 (BF16),
+// 1 (TF32-rounded FP32) or 2 (FP32)
 template <bool ZERO>
 void launch_combine(sfde_ctx* c, int out_kind, const long long* du, const int* En, int n0, int nb, int ex, int ey,
                     void* ro, long long rout_stride, double* partial) {
@@ -407,16 +466,31 @@ void launch_combine(sfde_ctx* c, int out_kind, const long long* du, const int* E
     const double cmass = c->x.h * c->y.h / 36.0;
     const int zx = sfde_oz_int_shift(Px), zy = sfde_oz_int_shift(Py);
     const long long *T1 = (const long long*)c->T1, *T3 = (const long long*)c->T3;
+    if constexpr (ZERO) {
+        if (out_kind == 0)
+            k_load_resid<__nv_bfloat16, false><<<grid, block, 0, c->stream>>>(
+                n0, Px, Py, c->x.n, c->y.n, c->rank, c->time_w, c->bxn, c->byn, c->Fd, (__nv_bfloat16*)ro,
+                rout_stride, partial);
+        else if (out_kind == 1)
+            k_load_resid<float, true><<<grid, block, 0, c->stream>>>(
+                n0, Px, Py, c->x.n, c->y.n, c->rank, c->time_w, c->bxn, c->byn, c->Fd, (float*)ro, rout_stride,
+                partial);
+        else
+            k_load_resid<float, false><<<grid, block, 0, c->stream>>>(
+                n0, Px, Py, c->x.n, c->y.n, c->rank, c->time_w, c->bxn, c->byn, c->Fd, (float*)ro, rout_stride,
+                partial);
+        return;
+    }
     if (out_kind == 0)
-        k_combine_int<__nv_bfloat16, false, ZERO><<<grid, block, 0, c->stream>>>(
+        k_combine_int<__nv_bfloat16, false><<<grid, block, 0, c->stream>>>(
             T1, T3, du, En, n0, Px, Py, c->x.n, c->y.n, cmass, ex, ey, zx, zy, c->dt0, c->rank, c->time_w, c->bxn,
             c->byn, c->Fd, (__nv_bfloat16*)ro, rout_stride, partial);
     else if (out_kind == 1)
-        k_combine_int<float, true, ZERO><<<grid, block, 0, c->stream>>>(
+        k_combine_int<float, true><<<grid, block, 0, c->stream>>>(
             T1, T3, du, En, n0, Px, Py, c->x.n, c->y.n, cmass, ex, ey, zx, zy, c->dt0, c->rank, c->time_w, c->bxn,
             c->byn, c->Fd, (float*)ro, rout_stride, partial);
     else
-        k_combine_int<float, false, ZERO><<<grid, block, 0, c->stream>>>(
+        k_combine_int<float, false><<<grid, block, 0, c->stream>>>(
             T1, T3, du, En, n0, Px, Py, c->x.n, c->y.n, cmass, ex, ey, zx, zy, c->dt0, c->rank, c->time_w, c->bxn,
             c->byn, c->Fd, (float*)ro, rout_stride, partial);
 }
