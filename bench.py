@@ -560,7 +560,9 @@ def run_batch(args):
     line = {
         "metric": METRIC, "value": dofs / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16/tf32+f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "+".join(sorted({["bf16", "tf32", "fp32(3xtf32)"][s.lp_kind] for s in stats
+                                                       if s.lp_kind >= 0})) + "+f64",
+        "data": "synthetic",
         "config": {"workload": "batch64 (batch_workloads seed 0)", "instances": len(ws), "space_time_updates": dofs,
                    "m": 8, "rel_tol": 1e-8, "precision": pname, "setup_s": setup_s,
                    "converged": sum(1 for s in stats if s.converged),
