@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <climits>
 
+#include "f64_round.cuh"
 #include "sfde_internal.cuh"
 
 namespace {
@@ -380,37 +381,6 @@ __global__ void __launch_bounds__(256, 4) k_combine_int(
     }
 }
 
-// (float)(a b) as FP64 arithmetic gives it -- the exact product rounded to 53 bits, then to 24 bits,
-// both to nearest even -- from integer operations; false where an operand is not finite or is
-// subnormal, or a rounded result is not a normal number (the caller then uses FP64 arithmetic)
-__device__ __forceinline__ bool mul_f64_to_f32(double a, double b, float& out) {
-    const unsigned long long ba = (unsigned long long)__double_as_longlong(a);
-    const unsigned long long bb = (unsigned long long)__double_as_longlong(b);
-    const unsigned sgn = (unsigned)((ba ^ bb) >> 63) << 31;
-    const int ea = (int)((ba >> 52) & 0x7FF), eb = (int)((bb >> 52) & 0x7FF);
-    if (ea == 0x7FF || eb == 0x7FF) return false;
-    if ((ba << 1) == 0 || (bb << 1) == 0) { out = __uint_as_float(sgn); return true; }   // a zero factor
-    if (ea == 0 || eb == 0) return false;
-    const unsigned long long ma = (ba & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const unsigned long long mb = (bb & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const unsigned long long hi = __umul64hi(ma, mb), lo = ma * mb;   // p = hi 2^64 + lo in [2^104, 2^106)
-    const int top = (hi >> 41) ? 105 : 104;                           // position of the leading one
-    const int sh = top - 52;                                          // bits dropped: 52 or 53, all in lo
-    unsigned long long m = (hi << (64 - sh)) | (lo >> sh);            // 53 bits
-    const unsigned long long rest = lo & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-    if (rest > half || (rest == half && (m & 1))) ++m;
-    int e = top + ea + eb - 2150;                                     // the value is m 2^(e - 52)
-    if (m == (1ull << 53)) { m >>= 1; ++e; }
-    if (e + 1023 <= 0 || e + 1023 >= 2047) return false;              // not a normal FP64 number
-    const unsigned long long r = m & ((1ull << 29) - 1), h2 = 1ull << 28;
-    unsigned m24 = (unsigned)(m >> 29);
-    if (r > h2 || (r == h2 && (m24 & 1))) ++m24;
-    if (m24 == (1u << 24)) { m24 >>= 1; ++e; }
-    if (e + 127 <= 0 || e + 127 >= 255) return false;                 // not a normal FP32 number
-    out = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | (m24 & 0x7FFFFF));
-    return true;
-}
-
 // rho_n = F_n for pairs of two zero slices (Z1 = Z2 = du = 0): with no fixed-point unit k_combine_int
 // takes its FP64 form there, F_n + 0 S9 + 0 S, i.e. F_n rounded once to FP32 (-0 read as +0); this
 // kernel gives the same values from the load alone, on the same tiles and with the same per-block sums
@@ -445,7 +415,7 @@ __global__ void __launch_bounds__(256) k_load_resid(int n0, int Px, int Py, int 
         float rf = 0.f;
         if (i < nx && j < ny && (rank > 0 || Fd)) {
             float v;
-            if (rank == 1 && !Fd && mul_f64_to_f32(fy[0][jj], bxi[0], v)) {
+            if (rank == 1 && !Fd && sfde_round::mul_f64_to_f32(fy[0][jj], bxi[0], v)) {
                 rf = (__float_as_uint(v) << 1) == 0 ? 0.f : v;   // -0 -> +0
             } else {
                 double f = Fd ? Fd[(size_t)(n - 1) * P2 + (size_t)j * Px + i] : 0.0;
