@@ -51,6 +51,13 @@ template <> struct Plan<false> {
 template <> struct Plan<true> {
     static constexpr int S = 7, BN = 32, STAGES = 3, KGROUP = 128, NBUF = 2;
 };
+// Integer output with at most 4 digits per operand (the first refinement steps): 4 accumulators of
+// 64 columns, twice, fill the 512 TMEM columns; twice the columns per X tile halve its re-reads.
+struct PlanWide {
+    static constexpr int S = 4, BN = 64, STAGES = 4, KGROUP = 128, NBUF = 2;
+};
+template <class PL>
+constexpr size_t digit_smem_bytes() { return 1024 + (size_t)PL::STAGES * PL::S * (XTILE + PL::BN * KC * 2) + 256; }
 
 // FP64-output plan: accumulator a -> digit sum d = p + q of its products, and the product list
 // (p, q, a), grouped by a (the integer plan needs no table: accumulator d - 2 holds digit sum d)
@@ -239,23 +246,23 @@ k_ozaki_slice_gemm(const __grid_constant__ CUtensorMap mapX, const __grid_consta
 // and streams chunks across tiles; warp NDW + 1 issues the MMAs; warps 0..NDW-1 drain, warp w
 // reading TMEM lanes 32 (w % 4).. (the lanes its warp index may access) and 8 columns.  K groups
 // alternate between two accumulator sets: while the drain warps fold group G (and store a finished
-// tile), the products of group G + 1 run into the other set, and the producer loads ahead.  The
-// drain adds each accumulator into a 32-bit sum per digit sum and column (one conversion and one
-// add per value; at most 8 groups of |value| < 2^24) and combines the seven sums into the int64
-// result once per tile.
-constexpr int DG_CW = 8;                                // columns per drain warp
-constexpr int DG_NDW = 4 * Plan<true>::BN / DG_CW;
+// tile), the products of group G + 1 run into the other set, and the producer loads ahead.  With
+// 32-column tiles (CW = 8) the drain adds each accumulator into a 32-bit sum per digit sum and
+// column (one conversion and one add per value; at most 8 groups of |value| < 2^24) and combines the
+// sums into the int64 result once per tile; with 64-column tiles (CW = 16, at most 4 digits: digit
+// sums d <= 5) it adds each accumulator into the int64 result directly, shifted exactly.
+constexpr int DG_NDW = 16;
 constexpr int DG_THREADS = 32 * (DG_NDW + 2);
 
+template <class PL, int CW>
 __global__ void __launch_bounds__(DG_THREADS, 1)
 k_digit_gemm_int(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapM, OzArgs p) {
-    using PL = Plan<true>;
     constexpr int S = PL::S, BN = PL::BN, STAGES = PL::STAGES, KGROUP = PL::KGROUP, NBUF = PL::NBUF;
     constexpr int MTILE = BN * KC * 2;
     constexpr int STAGE = S * (XTILE + MTILE);
-    constexpr int CW = DG_CW;
     constexpr uint32_t SET = S * BN;                    // TMEM columns of one accumulator set
-    static_assert(CW == 8, "one 8-column TMEM load per accumulator and drain warp");
+    static_assert(4 * BN / CW == DG_NDW, "four lane quarters x BN / CW column blocks of drain warps");
+    static_assert((CW == 8) || (CW == 16 && S <= 4), "32-bit sums, or exact int64 shifts for d <= 5");
     static_assert(NBUF * SET <= TMEM_COLS && S * BN <= 256, "accumulator sets within TMEM, one product per digit");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -359,6 +366,7 @@ k_digit_gemm_int(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             }
         }
     } else {
+      if constexpr (CW == 8) {
         const int lq = warp & 3, cb = (warp >> 2) * CW;
         const int zs = p.zshift;
         bool ok = true;
@@ -425,6 +433,54 @@ k_digit_gemm_int(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                 }
             }
         }
+      } else {
+        const int lq = warp & 3, cb = (warp >> 2) * CW;
+        const int zs = p.zshift;
+        bool ok = true;
+        long long G = 0;
+        for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const long long m = (t / ntn) * BM + lq * 32 + lane;
+            const int n0 = (int)(t % ntn) * BN;
+            long long zt[CW];   // units of 2^-52: digit sum d = a + 2 <= 5 enters shifted by 52 - 8d, exactly
+#pragma unroll
+            for (int j = 0; j < CW; ++j) zt[j] = 0;
+            for (int grp = 0; grp < ngroups; ++grp, ++G) {
+                const int set = (int)(G % NBUF);
+                ok = __all_sync(0xffffffffu,
+                                tc::mbar_wait(&accf[set], (uint32_t)(G / NBUF) & 1u, p.err, tc::ERR_WAIT_ACC));
+                tc::tc_fence_after();
+                if (!ok) break;
+                const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)set * SET + (uint32_t)cb;
+#pragma unroll
+                for (int a = 0; a < S; ++a) {
+                    if (a < nd) {
+                        uint32_t v[CW];
+                        tc::tmem_ld8_async(base + (uint32_t)(a * BN), v);
+                        tc::tmem_ld8_async(base + (uint32_t)(a * BN) + 8u, v + 8);
+                        tc::tmem_wait_ld();
+                        tc::reg_fence8(v);
+                        tc::reg_fence8(v + 8);
+#pragma unroll
+                        for (int j = 0; j < CW; ++j)   // exact, |value| < 2^24
+                            zt[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << (52 - 8 * (a + 2));
+                    }
+                }
+                tc::tc_fence_before();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&tfree[set])) : "memory");
+            }
+            if (ok && m < Mtot) {
+                const long long b = m / p.R;
+                const int r = (int)(m % p.R);
+                long long* out = (long long*)p.out + b * p.out_stride + r;
+#pragma unroll
+                for (int j = 0; j < CW; ++j) {   // N is a multiple of BN: every column exists
+                    long long v = zt[j];
+                    if (zs > 0) v = (v + (1ll << (zs - 1))) >> zs;
+                    out[(long long)(n0 + cb + j) * p.R] = v;
+                }
+            }
+        }
+      }
     }
     tc::tc_fence_before();
     __syncthreads();
@@ -625,10 +681,21 @@ sfde_status sfde_oz_split_matrix(const double* Mat, int K, int N, OzMatrix* out,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return SFDE_EINVAL;
+    out->wide = false;
+    if (uniform && N % PlanWide::BN == 0) {   // 64-column tiles for products of at most 4 digits
+        cuuint32_t boxw[3] = {(cuuint32_t)KC, (cuuint32_t)PlanWide::BN, 1};
+        r = fn(&out->map_wide, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, out->digits, dims, strides, boxw, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return SFDE_EINVAL;
+        out->wide = true;
+    }
     SFDE_CUDA(cudaFuncSetAttribute(k_ozaki_slice_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem_bytes<false>()));
-    SFDE_CUDA(cudaFuncSetAttribute(k_digit_gemm_int, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem_bytes<true>()));
+    SFDE_CUDA(cudaFuncSetAttribute(k_digit_gemm_int<Plan<true>, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)digit_smem_bytes<Plan<true>>()));
+    SFDE_CUDA(cudaFuncSetAttribute(k_digit_gemm_int<PlanWide, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)digit_smem_bytes<PlanWide>()));
     return SFDE_OK;
 }
 
@@ -661,7 +728,10 @@ sfde_status launch_oz(sfde_ctx* c, const CUtensorMap& mapX, const OzMatrix& M, c
                       int nr, int nc, int nout) {
     const long long mt = ((long long)a.batch * a.R + BM - 1) / BM;
     if (mt > 65535) return SFDE_EINVAL;
-    const int ntn = (M.N + Plan<INT_OUT>::BN - 1) / Plan<INT_OUT>::BN;
+    // integer output with at most 4 digits: 64-column tiles where the matrix has them
+    const bool wide = INT_OUT && a.nd <= PlanWide::S && M.wide;
+    const int bn = INT_OUT ? (wide ? PlanWide::BN : Plan<true>::BN) : Plan<false>::BN;
+    const int ntn = (M.N + bn - 1) / bn;
     const int slot = sfde_prof_begin(c);
     if constexpr (INT_OUT) {
         static int nsm = 0;
@@ -670,9 +740,11 @@ sfde_status launch_oz(sfde_ctx* c, const CUtensorMap& mapX, const OzMatrix& M, c
             SFDE_CUDA(cudaGetDevice(&dev));
             SFDE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         }
-        const long long ntiles = mt * ntn;
-        k_digit_gemm_int<<<(unsigned)std::min<long long>(ntiles, nsm), DG_THREADS, smem_bytes<true>(), s>>>(mapX, M.map,
-                                                                                                       a);
+        const unsigned grid = (unsigned)std::min<long long>(mt * ntn, nsm);
+        if (wide)
+            k_digit_gemm_int<PlanWide, 16><<<grid, DG_THREADS, digit_smem_bytes<PlanWide>(), s>>>(mapX, M.map_wide, a);
+        else
+            k_digit_gemm_int<Plan<true>, 8><<<grid, DG_THREADS, digit_smem_bytes<Plan<true>>(), s>>>(mapX, M.map, a);
     } else {
         k_ozaki_slice_gemm<<<dim3(ntn, (unsigned)mt), OZ_THREADS, smem_bytes<false>(), s>>>(mapX, M.map, a);
     }

@@ -275,7 +275,9 @@ struct OzMatrix {            // a fixed K x N FP64 matrix split into SFDE_OZ_DIG
     int* exps = nullptr;     // one exponent per column (device)
     int e_uniform = 0;       // the common exponent when split with one scale for the whole matrix
     int nd = 0;              // digit planes: 7 with one scale (integer-output product), else 6
-    CUtensorMap map;
+    CUtensorMap map;         // tiles of 32 columns
+    CUtensorMap map_wide;    // tiles of 64 columns (integer output, N a multiple of 64), if wide
+    bool wide = false;
 };
 // digits of alpha * Mat; uniform: one exponent (max_kn |alpha m_kn| < 2^e) for all columns and seven
 // digits (for sfde_oz_gemm_int), else one exponent per column and six digits (for sfde_oz_gemm)
