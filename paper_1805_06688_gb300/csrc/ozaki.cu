@@ -262,7 +262,8 @@ k_digit_gemm_int(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     constexpr int STAGE = S * (XTILE + MTILE);
     constexpr uint32_t SET = S * BN;                    // TMEM columns of one accumulator set
     static_assert(4 * BN / CW == DG_NDW, "four lane quarters x BN / CW column blocks of drain warps");
-    static_assert((CW == 8) || (CW == 16 && S <= 4), "32-bit sums, or exact int64 shifts for d <= 5");
+    static_assert((CW == 8 && S == 7) || (CW == 16 && S <= 4),
+                  "32-bit sums of the 7 digit sums, or int64 shifts for d <= 5");
     static_assert(NBUF * SET <= TMEM_COLS && S * BN <= 256, "accumulator sets within TMEM, one product per digit");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -366,121 +367,123 @@ k_digit_gemm_int(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             }
         }
     } else {
-      if constexpr (CW == 8) {
-        const int lq = warp & 3, cb = (warp >> 2) * CW;
-        const int zs = p.zshift;
-        bool ok = true;
-        long long G = 0;
-        for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const long long m = (t / ntn) * BM + lq * 32 + lane;
-            const int n0 = (int)(t % ntn) * BN;
-            // acc[a]: the exact sum over the K groups of accumulator a (digit sum d = a + 2), in units
-            // of 2^{-8d} (at most 8 groups of |value| < 2^24: below 2^27)
-            int acc[S][CW];
+        if constexpr (CW == 8) {
+            const int lq = warp & 3, cb = (warp >> 2) * CW;
+            const int zs = p.zshift;
+            bool ok = true;
+            long long G = 0;
+            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const long long m = (t / ntn) * BM + lq * 32 + lane;
+                const int n0 = (int)(t % ntn) * BN;
+                // acc[a]: the exact sum over the K groups of accumulator a (digit sum d = a + 2), in units
+                // of 2^{-8d} (at most 8 groups of |value| < 2^24: below 2^27)
+                int acc[S][CW];
 #pragma unroll
-            for (int a = 0; a < S; ++a)
+                for (int a = 0; a < S; ++a)
 #pragma unroll
-                for (int j = 0; j < CW; ++j) acc[a][j] = 0;
-            // the result in units of 2^-52, formed while the last group is drained: the digit sums
-            // d <= 6 exactly (Horner in base 256 from d = 2, whose unit is 2^{36-52}), d = 7 and 8
-            // (units 2^-56 and 2^-64) combined exactly and added with one rounding (at most half a
-            // unit); the sums past nd are zero
-            long long y[CW];
-            for (int grp = 0; grp < ngroups; ++grp, ++G) {
-                const bool last = grp == ngroups - 1;
-                const int set = (int)(G % NBUF);
-                ok = __all_sync(0xffffffffu,
-                                tc::mbar_wait(&accf[set], (uint32_t)(G / NBUF) & 1u, p.err, tc::ERR_WAIT_ACC));
-                tc::tc_fence_after();
-                if (!ok) break;
-                // accumulator a's 8 columns (the latency of each load is hidden by the other three drain
-                // warps of the sub-partition)
-                const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)set * SET + (uint32_t)cb;
+                    for (int j = 0; j < CW; ++j) acc[a][j] = 0;
+                // the result in units of 2^-52, formed while the last group is drained: the digit sums
+                // d <= 6 exactly (Horner in base 256 from d = 2, whose unit is 2^{36-52}), d = 7 and 8
+                // (units 2^-56 and 2^-64) combined exactly and added with one rounding (at most half a
+                // unit); the sums past nd are zero
+                long long y[CW];
+                for (int grp = 0; grp < ngroups; ++grp, ++G) {
+                    const bool last = grp == ngroups - 1;
+                    const int set = (int)(G % NBUF);
+                    ok = __all_sync(0xffffffffu,
+                                    tc::mbar_wait(&accf[set], (uint32_t)(G / NBUF) & 1u, p.err, tc::ERR_WAIT_ACC));
+                    tc::tc_fence_after();
+                    if (!ok) break;
+                    // accumulator a's 8 columns (the latency of each load is hidden by the other three drain
+                    // warps of the sub-partition)
+                    const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)set * SET + (uint32_t)cb;
 #pragma unroll
-                for (int a = 0; a < S; ++a) {
-                    if (a < nd) {   // no early exit: the loop unrolls and acc stays in registers
-                        uint32_t v[CW];
-                        tc::tmem_ld8_async(base + (uint32_t)(a * BN), v);
-                        tc::tmem_wait_ld();
-                        tc::reg_fence8(v);
+                    for (int a = 0; a < S; ++a) {
+                        if (a < nd) {   // no early exit: the loop unrolls and acc stays in registers
+                            uint32_t v[CW];
+                            tc::tmem_ld8_async(base + (uint32_t)(a * BN), v);
+                            tc::tmem_wait_ld();
+                            tc::reg_fence8(v);
 #pragma unroll
-                        for (int j = 0; j < CW; ++j)   // exact, |value| < 2^24
-                            acc[a][j] += __float2int_rn(__uint_as_float(v[j]));
-                    }
-                    if (last) {
+                            for (int j = 0; j < CW; ++j)   // exact, |value| < 2^24
+                                acc[a][j] += __float2int_rn(__uint_as_float(v[j]));
+                        }
+                        if (last) {
 #pragma unroll
-                        for (int j = 0; j < CW; ++j) {
-                            if (a == 0) y[j] = acc[0][j];
-                            else if (a < 5) y[j] = y[j] * 256 + acc[a][j];
-                            else if (a == 6)
-                                y[j] = y[j] * 16 + (((long long)acc[5][j] * 256 + acc[6][j] + 2048) >> 12);
+                            for (int j = 0; j < CW; ++j) {
+                                if (a == 0) y[j] = acc[0][j];
+                                else if (a < 5) y[j] = y[j] * 256 + acc[a][j];
+                                else if (a == 6)
+                                    y[j] = y[j] * 16 + (((long long)acc[5][j] * 256 + acc[6][j] + 2048) >> 12);
+                            }
                         }
                     }
+                    tc::tc_fence_before();
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&tfree[set]))
+                                 : "memory");
                 }
-                tc::tc_fence_before();
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&tfree[set])) : "memory");
-            }
-            // the next tile's products run while this one is stored
-            if (ok && m < Mtot) {
-                const long long b = m / p.R;
-                const int r = (int)(m % p.R);
-                long long* out = (long long*)p.out + b * p.out_stride + r;
+                // the next tile's products run while this one is stored
+                if (ok && m < Mtot) {
+                    const long long b = m / p.R;
+                    const int r = (int)(m % p.R);
+                    long long* out = (long long*)p.out + b * p.out_stride + r;
 #pragma unroll
-                for (int j = 0; j < CW; ++j) {   // N is a multiple of BN: every column exists
-                    long long v = y[j];
-                    if (zs > 0) v = (v + (1ll << (zs - 1))) >> zs;
-                    out[(long long)(n0 + cb + j) * p.R] = v;
-                }
-            }
-        }
-      } else {
-        const int lq = warp & 3, cb = (warp >> 2) * CW;
-        const int zs = p.zshift;
-        bool ok = true;
-        long long G = 0;
-        for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const long long m = (t / ntn) * BM + lq * 32 + lane;
-            const int n0 = (int)(t % ntn) * BN;
-            long long zt[CW];   // units of 2^-52: digit sum d = a + 2 <= 5 enters shifted by 52 - 8d, exactly
-#pragma unroll
-            for (int j = 0; j < CW; ++j) zt[j] = 0;
-            for (int grp = 0; grp < ngroups; ++grp, ++G) {
-                const int set = (int)(G % NBUF);
-                ok = __all_sync(0xffffffffu,
-                                tc::mbar_wait(&accf[set], (uint32_t)(G / NBUF) & 1u, p.err, tc::ERR_WAIT_ACC));
-                tc::tc_fence_after();
-                if (!ok) break;
-                const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)set * SET + (uint32_t)cb;
-#pragma unroll
-                for (int a = 0; a < S; ++a) {
-                    if (a < nd) {
-                        uint32_t v[CW];
-                        tc::tmem_ld8_async(base + (uint32_t)(a * BN), v);
-                        tc::tmem_ld8_async(base + (uint32_t)(a * BN) + 8u, v + 8);
-                        tc::tmem_wait_ld();
-                        tc::reg_fence8(v);
-                        tc::reg_fence8(v + 8);
-#pragma unroll
-                        for (int j = 0; j < CW; ++j)   // exact, |value| < 2^24
-                            zt[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << (52 - 8 * (a + 2));
+                    for (int j = 0; j < CW; ++j) {   // N is a multiple of BN: every column exists
+                        long long v = y[j];
+                        if (zs > 0) v = (v + (1ll << (zs - 1))) >> zs;
+                        out[(long long)(n0 + cb + j) * p.R] = v;
                     }
                 }
-                tc::tc_fence_before();
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&tfree[set])) : "memory");
             }
-            if (ok && m < Mtot) {
-                const long long b = m / p.R;
-                const int r = (int)(m % p.R);
-                long long* out = (long long*)p.out + b * p.out_stride + r;
+        } else {
+            const int lq = warp & 3, cb = (warp >> 2) * CW;
+            const int zs = p.zshift;
+            bool ok = true;
+            long long G = 0;
+            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const long long m = (t / ntn) * BM + lq * 32 + lane;
+                const int n0 = (int)(t % ntn) * BN;
+                long long zt[CW];   // units of 2^-52: digit sum d = a + 2 <= 5 enters shifted by 52 - 8d, exactly
 #pragma unroll
-                for (int j = 0; j < CW; ++j) {   // N is a multiple of BN: every column exists
-                    long long v = zt[j];
-                    if (zs > 0) v = (v + (1ll << (zs - 1))) >> zs;
-                    out[(long long)(n0 + cb + j) * p.R] = v;
+                for (int j = 0; j < CW; ++j) zt[j] = 0;
+                for (int grp = 0; grp < ngroups; ++grp, ++G) {
+                    const int set = (int)(G % NBUF);
+                    ok = __all_sync(0xffffffffu,
+                                    tc::mbar_wait(&accf[set], (uint32_t)(G / NBUF) & 1u, p.err, tc::ERR_WAIT_ACC));
+                    tc::tc_fence_after();
+                    if (!ok) break;
+                    const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)set * SET + (uint32_t)cb;
+#pragma unroll
+                    for (int a = 0; a < S; ++a) {
+                        if (a < nd) {
+                            uint32_t v[CW];
+                            tc::tmem_ld8_async(base + (uint32_t)(a * BN), v);
+                            tc::tmem_ld8_async(base + (uint32_t)(a * BN) + 8u, v + 8);
+                            tc::tmem_wait_ld();
+                            tc::reg_fence8(v);
+                            tc::reg_fence8(v + 8);
+#pragma unroll
+                            for (int j = 0; j < CW; ++j)   // exact, |value| < 2^24
+                                zt[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << (52 - 8 * (a + 2));
+                        }
+                    }
+                    tc::tc_fence_before();
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&tfree[set]))
+                                 : "memory");
+                }
+                if (ok && m < Mtot) {
+                    const long long b = m / p.R;
+                    const int r = (int)(m % p.R);
+                    long long* out = (long long*)p.out + b * p.out_stride + r;
+#pragma unroll
+                    for (int j = 0; j < CW; ++j) {   // N is a multiple of BN: every column exists
+                        long long v = zt[j];
+                        if (zs > 0) v = (v + (1ll << (zs - 1))) >> zs;
+                        out[(long long)(n0 + cb + j) * p.R] = v;
+                    }
                 }
             }
         }
-      }
     }
     tc::tc_fence_before();
     __syncthreads();
