@@ -126,7 +126,7 @@ sfde_status autotune_impl(sfde_ctx* c, const mgrit_opts* opts, const char* cache
     for (int mc : {1, 2})
         for (int ic : {0, 3, 5})
             if (ic == 0 || opts->inner_cycles == 0) cand.push_back({1, mc, ic, 0.0});
-    // the whole inner solve in the eigenbasis (FP32 storage): its V-cycles are elementwise, so more
+    // the whole inner solve in the eigenbasis (FP32 or TF32 storage): its V-cycles are elementwise, so more
     // of them per refinement step are worth a trial
     if (sfde_mixed_kind(c) != 0)
         for (int ic : {0, 3, 5, 8})
