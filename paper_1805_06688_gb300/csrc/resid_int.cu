@@ -18,9 +18,11 @@
 //          K V = (1,4,1)_y Z1 + (1,4,1)_x Z2      (integer, aligned to a common power of two),
 //          M_h (U_{n-1} - U_n) = (h_x h_y / 36) (1,4,1)_y (1,4,1)_x du,  du = fix(U_{n-1}) - fix(U_n)
 //      (du written by step 2 as int64),
-//      and rho = c_m S9 - tau c_s S formed exactly in 128-bit integers and converted to FP32 (with a
-//      load term F: rho = F + c_m S9 - tau c_s S in FP64, two FMAs per element, the int64 -> FP64
-//      conversions built from bits); the sum of rho^2 is taken over the stored FP32 values.
+//      and rho = F + c_m S9 - tau c_s S formed exactly in 128-bit integers (the load F formed in
+//      FP64 and rounded to the common unit; the FP64 form where it does not fit) and converted to
+//      FP32; the sum of rho^2 is taken over the stored FP32 values.
+// Pairs of two zero slices (the first iterate's n >= 2) skip steps 2-4: their residual is the load
+// alone, written with the values the general form gives them (k_load_resid).
 // The fixed-point grid of a pair is 2^{E-54}: values far below the slice maximum keep an absolute
 // accuracy of 2^{-55} max|U|, the scale at which an FP64 product's rounding errors enter the residual.
 #include <cuda_bf16.h>
